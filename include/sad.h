@@ -1,0 +1,168 @@
+/*
+ * sad.h - C-ABI of libsad, the GB300 (sm_103a) implementation of the
+ * data-decomposition step of Sample-Align-D (Saeed & Khokhar, arXiv 0905.1744):
+ * per-sequence k-mer count vectors, the k-mer rank of every sequence against the
+ * whole set, and the regular-sampling partition of the rank-ordered set into p
+ * buckets.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Pointers named d_* are device pointers (global memory of the current CUDA
+ *   device). The caller owns every buffer; the library allocates no device
+ *   memory. Scratch space comes from the caller as a workspace (d_ws, ws_bytes),
+ *   256-byte aligned, sized with the query functions below.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   Every call is asynchronous on that stream unless it says otherwise.
+ * - Return value: a sad_status. Argument errors that the host can see are
+ *   returned at once and nothing is launched. Errors found in the data on the
+ *   device (a letter code >= alphabet, a sequence shorter than k, a workspace
+ *   too small for the data) are recorded in the workspace's status word and
+ *   reported by sad_status_read(); kernels that see a recorded error skip their
+ *   work, so outputs are then undefined.
+ * - Indices are 0-based positions in the input order. All results are
+ *   deterministic integers (floating outputs are derived views).
+ * - Layouts are row-major and densely packed.
+ */
+#ifndef SAD_H
+#define SAD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SAD_ABI_VERSION 1
+
+typedef enum sad_status {
+  SAD_OK = 0,
+  SAD_ERR_INVALID_ARGUMENT = 1, /* bad size, null pointer, misaligned buffer   */
+  SAD_ERR_WORKSPACE = 2,        /* workspace smaller than the data requires    */
+  SAD_ERR_CUDA = 3,             /* a CUDA runtime call failed                  */
+  SAD_ERR_TIMEOUT = 4,          /* a bounded device-side wait gave up          */
+  SAD_ERR_UNSUPPORTED = 5,      /* parameters outside what this build handles  */
+  SAD_ERR_BAD_INPUT = 6         /* letter code >= alphabet, or length < k      */
+} sad_status;
+
+typedef enum sad_op {
+  SAD_OP_COUNT = 0,
+  SAD_OP_RANK = 1,
+  SAD_OP_PARTITION = 2
+} sad_op;
+
+/* Human-readable name of a status code. Never NULL. */
+const char *sad_status_string(int status);
+
+/* SAD_ABI_VERSION of the loaded library. */
+int sad_abi_version(void);
+
+/*
+ * Workspace bytes an entry point needs.
+ *   op        SAD_OP_COUNT, SAD_OP_RANK or SAD_OP_PARTITION.
+ *   n_seq     number of sequences N.
+ *   k, alphabet  word length and alphabet size (eps = alphabet^k words).
+ *   p         number of buckets (SAD_OP_PARTITION only).
+ *   depth     SAD_OP_RANK only: the threshold-plane columns to reserve, as a
+ *             multiple of eps (K_cap = eps * depth rounded up to 128). The
+ *             columns kmer_rank needs are K_eff = sum over words of the largest
+ *             count of that word in any sequence; kmer_rank_plan() returns the
+ *             exact figure. depth <= 0 means 1.
+ * Returns 0 for arguments outside the supported range.
+ */
+size_t sad_workspace_bytes(int32_t op, int32_t n_seq, int32_t k, int32_t alphabet,
+                           int32_t p, int32_t depth);
+
+/*
+ * kmer_count - per-sequence k-mer count vectors (Sec. 3, "k-mer Rank": the
+ * vector c^X = (c^X_1, ..., c^X_eps) of occurrences of each of the eps = c^k
+ * words in X).
+ *   d_codes    uint8 letter codes of all sequences, concatenated; a code must be
+ *              < alphabet (SAD_ERR_BAD_INPUT otherwise).
+ *   d_offsets  int64 [n_seq + 1], sequence x is d_codes[off[x] .. off[x+1]);
+ *              non-decreasing, off[0] >= 0. Every length must be >= k.
+ *   k          1..16; alphabet 2..256; eps = alphabet^k <= 65536.
+ *   d_counts   int32 [n_seq][eps] output; word index
+ *              tau = sum_r a_r * alphabet^(k-1-r) (first letter most significant).
+ *   d_ws       workspace of sad_workspace_bytes(SAD_OP_COUNT, ...) bytes.
+ */
+int kmer_count(const uint8_t *d_codes, const int64_t *d_offsets, int32_t n_seq,
+               int32_t k, int32_t alphabet, int32_t *d_counts, void *d_ws,
+               size_t ws_bytes, void *stream);
+
+/*
+ * kmer_rank_plan - SYNCHRONOUS helper: computes on the device the number of
+ * threshold-plane columns K_eff the counts need and the workspace kmer_rank will
+ * then require. Blocks until `stream` is idle.
+ *   d_counts   int32 [n_seq][eps], as written by kmer_count.
+ *   d_ws       a workspace of at least sad_workspace_bytes(SAD_OP_RANK, n_seq,
+ *              k, alphabet, 0, 0) bytes (the fixed part; planes not needed).
+ *   k_eff_out  (nullable) receives K_eff.
+ *   ws_needed  (nullable) receives the workspace bytes kmer_rank needs.
+ */
+int kmer_rank_plan(const int32_t *d_counts, int32_t n_seq, int32_t k, int32_t alphabet,
+                   void *d_ws, size_t ws_bytes, int64_t *k_eff_out, size_t *ws_needed,
+                   void *stream);
+
+/*
+ * kmer_rank - the k-mer rank of every sequence against the whole set.
+ * Eq. 1: F(X,Y) = sum_i min(c^X_i, c^Y_i) / (min(n, m) - k + 1); Eq. 3:
+ * R_i = (1/N) sum_{j=1..N} F(i, j), j = i included, taken on F itself (the mean
+ * similarity) rather than on the distance of Eq. 2.
+ * The rank is carried exactly as a 128-bit fixed-point key
+ *     key_i = sum_j floor(S_ij * 2^64 / D_ij),
+ * S_ij = sum_i min(...) and D_ij = min(L_i, L_j) - k + 1, split into
+ * key = key_hi * 2^64 + key_lo; the float view is
+ *     rank_i = (key_hi + key_lo * 2^-64) / N   (each step rounded to nearest).
+ * Internally min(a, b) = sum_t [a >= t][b >= t] turns all pairs into one
+ * threshold-plane GEMM on the tensor cores; the N x N matrix is never stored.
+ *   d_counts   int32 [n_seq][eps] from kmer_count.
+ *   d_lengths  int32 [n_seq] sequence lengths L (residues); every
+ *              L - k + 1 must be in 1..65535 (SAD_ERR_UNSUPPORTED otherwise).
+ *   d_key_hi, d_key_lo  uint64 [n_seq] outputs.
+ *   d_rank     (nullable) float64 [n_seq] output.
+ *   d_ws       workspace; its size sets the plane capacity K_cap (see
+ *              sad_workspace_bytes / kmer_rank_plan). If K_eff > K_cap the call
+ *              records SAD_ERR_WORKSPACE and writes no keys.
+ */
+int kmer_rank(const int32_t *d_counts, const int32_t *d_lengths, int32_t n_seq,
+              int32_t k, int32_t alphabet, uint64_t *d_key_hi, uint64_t *d_key_lo,
+              double *d_rank, void *d_ws, size_t ws_bytes, void *stream);
+
+/*
+ * partition - regular-sampling sample sort of the keys into p buckets
+ * (Sec. 3.1.2 and Algorithm 2 steps 7-11, the p processors being virtual
+ * buckets on one device):
+ *   block b = input positions [floor(bN/p), floor((b+1)N/p)) is sorted by
+ *   (key, index); p-1 samples are taken per block at 0-based positions
+ *   floor(j w_b / p), j = 1..p-1; the p(p-1) samples are sorted and the pivots
+ *   are y_i = Y_{(i-1)p + floor(p/2)} (1-based), i = 1..p-1; bucket i (1-based)
+ *   receives the keys in (y_{i-1}, y_i] (Sec. 3.3.2), ties ordered by index.
+ *   d_key_hi, d_key_lo  uint64 [n_seq] keys (as from kmer_rank).
+ *   p          1 <= p <= n_seq (or n_seq == 0), p <= 4096.
+ *   d_bucket_offsets  int32 [p + 1] output (CSR offsets).
+ *   d_members  int32 [n_seq] output: input indices, bucket by bucket, each bucket
+ *              in ascending (key, index) order.
+ *   d_pivot_idx  (nullable) int32 [p - 1] output: input index of each pivot.
+ *   d_ws       workspace of sad_workspace_bytes(SAD_OP_PARTITION, ...) bytes.
+ */
+int partition(const uint64_t *d_key_hi, const uint64_t *d_key_lo, int32_t n_seq,
+              int32_t p, int32_t *d_bucket_offsets, int32_t *d_members,
+              int32_t *d_pivot_idx, void *d_ws, size_t ws_bytes, void *stream);
+
+/*
+ * sad_status_read - SYNCHRONOUS: waits for `stream`, then returns the status
+ * recorded in the workspace by the device (SAD_OK if none). With clear != 0 the
+ * recorded status is reset to SAD_OK. d_ws must be a workspace previously passed
+ * to one of the entry points above (its first 256 bytes are the header).
+ */
+int sad_status_read(void *d_ws, int32_t clear, void *stream);
+
+/* Number of kernels this library has launched in this process. */
+uint64_t sad_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SAD_H */

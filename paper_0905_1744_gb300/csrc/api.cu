@@ -1,0 +1,220 @@
+// C-ABI entry points of libsad (declared in include/sad.h): argument checks,
+// workspace layout, launch sequencing, device status readback.
+#include <atomic>
+#include <cstring>
+
+#include "rank.cuh"
+
+namespace sad {
+
+int count_launch(const uint8_t *codes, const int64_t *offsets, int32_t n, int32_t k,
+                 int32_t alphabet, int32_t eps, int32_t *counts, WsHeader *hdr,
+                 cudaStream_t st);
+int partition_launch(const uint64_t *key_hi, const uint64_t *key_lo, int32_t n, int32_t p,
+                     int32_t *bucket_offsets, int32_t *members, int32_t *pivot_idx, void *ws,
+                     cudaStream_t st);
+
+namespace {
+std::atomic<uint64_t> g_launches{0};
+
+int64_t eps_of(int32_t k, int32_t alphabet) {
+  if (k < 1 || k > 8 || alphabet < 2 || alphabet > 256) return -1;
+  int64_t e = 1;
+  for (int i = 0; i < k; ++i) {
+    e *= alphabet;
+    if (e > kMaxEps) return -1;
+  }
+  return e;
+}
+
+bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// Largest K_cap (multiple of kKChunk) whose rank layout fits in ws_bytes.
+int64_t k_cap_for(int64_t n, int64_t eps, size_t ws_bytes) {
+  const RankLayout base = rank_layout(n, eps, 0);
+  if (ws_bytes <= base.fixed_bytes) return 0;
+  int64_t k = (int64_t)((ws_bytes - base.fixed_bytes) / (size_t)(base.n_pad + 4));
+  k = k / kKChunk * kKChunk;
+  while (k > 0) {
+    const RankLayout L = rank_layout(n, eps, k);
+    if (L.fixed_bytes + (size_t)L.n_pad * (size_t)k <= ws_bytes) break;
+    k -= kKChunk;
+  }
+  return k;
+}
+
+size_t rank_bytes(int64_t n, int64_t eps, int64_t k_cap) {
+  const RankLayout L = rank_layout(n, eps, k_cap);
+  return L.fixed_bytes + (size_t)L.n_pad * (size_t)k_cap;
+}
+
+int check_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return SAD_OK;
+  cudaGetLastError();
+  return SAD_ERR_CUDA;
+}
+}  // namespace
+
+void note_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+int num_sms() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (cached[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1)
+      v = 1;
+    cached[dev] = v;
+  }
+  return cached[dev];
+}
+
+}  // namespace sad
+
+using namespace sad;
+
+extern "C" {
+
+const char *sad_status_string(int status) {
+  switch (status) {
+    case SAD_OK: return "ok";
+    case SAD_ERR_INVALID_ARGUMENT: return "invalid argument";
+    case SAD_ERR_WORKSPACE: return "workspace too small for the data";
+    case SAD_ERR_CUDA: return "CUDA runtime error";
+    case SAD_ERR_TIMEOUT: return "bounded device wait timed out";
+    case SAD_ERR_UNSUPPORTED: return "unsupported parameters";
+    case SAD_ERR_BAD_INPUT: return "bad input data (letter code >= alphabet, length < k, or "
+                                   "counts inconsistent with lengths)";
+    default: return "unknown status";
+  }
+}
+
+int sad_abi_version(void) { return SAD_ABI_VERSION; }
+
+uint64_t sad_launch_count(void) { return g_launches.load(); }
+
+size_t sad_workspace_bytes(int32_t op, int32_t n_seq, int32_t k, int32_t alphabet, int32_t p,
+                           int32_t depth) {
+  if (n_seq < 0) return 0;
+  const int64_t eps = eps_of(k, alphabet);
+  switch (op) {
+    case SAD_OP_COUNT:
+      return eps < 0 ? 0 : sizeof(WsHeader);
+    case SAD_OP_RANK: {
+      if (eps < 0) return 0;
+      if (depth <= 0) return rank_layout(n_seq, eps, 0).fixed_bytes;
+      const int64_t k_cap =
+          (int64_t)align_up((size_t)eps * (size_t)depth, (size_t)kKChunk);
+      return rank_bytes(n_seq, eps, k_cap);
+    }
+    case SAD_OP_PARTITION:
+      if (p < 1 || p > kMaxP) return 0;
+      return part_layout(n_seq, p).bytes;
+    default:
+      return 0;
+  }
+}
+
+int kmer_count(const uint8_t *d_codes, const int64_t *d_offsets, int32_t n_seq, int32_t k,
+               int32_t alphabet, int32_t *d_counts, void *d_ws, size_t ws_bytes,
+               void *stream) {
+  const int64_t eps = eps_of(k, alphabet);
+  if (n_seq < 0 || eps < 0) return eps < 0 && n_seq >= 0 ? SAD_ERR_UNSUPPORTED
+                                                           : SAD_ERR_INVALID_ARGUMENT;
+  if (!d_ws || !aligned(d_ws, 256) || ws_bytes < sizeof(WsHeader)) return SAD_ERR_INVALID_ARGUMENT;
+  if (n_seq == 0) return SAD_OK;
+  if (!d_codes || !d_offsets || !d_counts || !aligned(d_counts, 16) || !aligned(d_offsets, 8))
+    return SAD_ERR_INVALID_ARGUMENT;
+  return count_launch(d_codes, d_offsets, n_seq, k, alphabet, (int32_t)eps, d_counts,
+                      static_cast<WsHeader *>(d_ws), static_cast<cudaStream_t>(stream));
+}
+
+int kmer_rank_plan(const int32_t *d_counts, int32_t n_seq, int32_t k, int32_t alphabet,
+                   void *d_ws, size_t ws_bytes, int64_t *k_eff_out, size_t *ws_needed,
+                   void *stream) {
+  const int64_t eps = eps_of(k, alphabet);
+  if (eps < 0) return SAD_ERR_UNSUPPORTED;
+  if (n_seq < 0 || !d_ws || !aligned(d_ws, 256)) return SAD_ERR_INVALID_ARGUMENT;
+  const RankLayout L0 = rank_layout(n_seq, eps, 0);
+  if (ws_bytes < L0.fixed_bytes) return SAD_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int64_t k_eff = 0;
+  if (n_seq > 0) {
+    if (!d_counts) return SAD_ERR_INVALID_ARGUMENT;
+    const RankPtrs P = rank_ptrs(d_ws, L0);
+    int rc = rank_prep_launch(P, d_counts, nullptr, n_seq, k, (int32_t)eps, 1, st);
+    if (rc) return rc;
+    WsHeader h;
+    rc = check_cuda(cudaMemcpyAsync(&h, d_ws, sizeof(h), cudaMemcpyDeviceToHost, st));
+    if (rc) return rc;
+    rc = check_cuda(cudaStreamSynchronize(st));
+    if (rc) return rc;
+    if (h.status != 0) return h.status;
+    k_eff = h.k_eff;
+  }
+  int64_t k_pad = (int64_t)align_up((size_t)k_eff, kKChunk);
+  if (k_pad < kKChunk) k_pad = kKChunk;
+  if (k_eff_out) *k_eff_out = k_eff;
+  if (ws_needed) *ws_needed = rank_bytes(n_seq, eps, k_pad);
+  return SAD_OK;
+}
+
+int kmer_rank(const int32_t *d_counts, const int32_t *d_lengths, int32_t n_seq, int32_t k,
+              int32_t alphabet, uint64_t *d_key_hi, uint64_t *d_key_lo, double *d_rank,
+              void *d_ws, size_t ws_bytes, void *stream) {
+  const int64_t eps = eps_of(k, alphabet);
+  if (eps < 0) return SAD_ERR_UNSUPPORTED;
+  if (n_seq < 0 || !d_ws || !aligned(d_ws, 256)) return SAD_ERR_INVALID_ARGUMENT;
+  if (n_seq == 0) return SAD_OK;
+  if (!d_counts || !d_lengths || !d_key_hi || !d_key_lo) return SAD_ERR_INVALID_ARGUMENT;
+  if ((int64_t)n_seq > (int64_t)0xFFFF * kRowBlock - kNPad) return SAD_ERR_UNSUPPORTED;
+  const int64_t k_cap = k_cap_for(n_seq, eps, ws_bytes);
+  if (k_cap < kKChunk) return SAD_ERR_WORKSPACE;
+  const RankLayout L = rank_layout(n_seq, eps, k_cap);
+  const RankPtrs P = rank_ptrs(d_ws, L);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc = rank_prep_launch(P, d_counts, d_lengths, n_seq, k, (int32_t)eps, 0, st);
+  if (rc) return rc;
+  rc = rank_gemm_launch(P, n_seq, st);
+  if (rc) return rc;
+  return rank_finalize_launch(P, n_seq, d_key_hi, d_key_lo, d_rank, st);
+}
+
+int partition(const uint64_t *d_key_hi, const uint64_t *d_key_lo, int32_t n_seq, int32_t p,
+              int32_t *d_bucket_offsets, int32_t *d_members, int32_t *d_pivot_idx, void *d_ws,
+              size_t ws_bytes, void *stream) {
+  if (n_seq < 0 || p < 1 || p > kMaxP) return SAD_ERR_INVALID_ARGUMENT;
+  if (n_seq > 0 && p > n_seq) return SAD_ERR_INVALID_ARGUMENT;
+  if (!d_ws || !aligned(d_ws, 256) || !d_bucket_offsets) return SAD_ERR_INVALID_ARGUMENT;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (n_seq == 0) {
+    return check_cuda(
+        cudaMemsetAsync(d_bucket_offsets, 0, sizeof(int32_t) * (size_t)(p + 1), st));
+  }
+  if (!d_key_hi || !d_key_lo || !d_members) return SAD_ERR_INVALID_ARGUMENT;
+  if (ws_bytes < part_layout(n_seq, p).bytes) return SAD_ERR_WORKSPACE;
+  return partition_launch(d_key_hi, d_key_lo, n_seq, p, d_bucket_offsets, d_members,
+                          d_pivot_idx, d_ws, st);
+}
+
+int sad_status_read(void *d_ws, int32_t clear, void *stream) {
+  if (!d_ws) return SAD_ERR_INVALID_ARGUMENT;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int32_t h[2] = {0, 0};
+  int rc = check_cuda(cudaMemcpyAsync(h, d_ws, sizeof(h), cudaMemcpyDeviceToHost, st));
+  if (rc) return rc;
+  rc = check_cuda(cudaStreamSynchronize(st));
+  if (rc) return rc;
+  if (clear && h[0] != 0) {
+    const int32_t z[2] = {0, 0};
+    rc = check_cuda(cudaMemcpyAsync(d_ws, z, sizeof(z), cudaMemcpyHostToDevice, st));
+    if (rc) return rc;
+    rc = check_cuda(cudaStreamSynchronize(st));
+    if (rc) return rc;
+  }
+  return h[0];
+}
+
+}  // extern "C"

@@ -1,0 +1,145 @@
+// k-mer count vectors (Sec. 3, "k-mer Rank"): c^X_tau = number of windows of X
+// whose k letters spell word tau = sum_r a_r * alphabet^(k-1-r).
+//
+// One warp owns one sequence at a time. The warp reads the sequence 512 bytes
+// per step as 16-byte vectors (lane l: bytes 16l..16l+15 of the step); the k-1
+// bytes a lane's last windows run into come from the next lane by shuffle, and
+// lane 31 loads them itself. Each window's word is counted in the warp's
+// private shared-memory histogram (two 16-bit bins per 32-bit word), which is
+// then streamed out as the dense int32 row and cleared in the same pass.
+#include "sad_common.cuh"
+
+namespace sad {
+
+namespace {
+
+__device__ __forceinline__ uint4 load16_guarded(const uint8_t *codes, int64_t pos, int64_t end) {
+  // 16 bytes at pos (16-aligned); bytes at or past `end` read as zero.
+  if (pos + 16 <= end) return __ldg(reinterpret_cast<const uint4 *>(codes + pos));
+  uint32_t w[4] = {0, 0, 0, 0};
+  for (int b = 0; b < 16; ++b)
+    if (pos + b < end) w[b >> 2] |= (uint32_t)__ldg(codes + pos + b) << (8 * (b & 3));
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+__device__ __forceinline__ uint32_t byte_of(const uint32_t (&w)[8], int b) {
+  return (w[b >> 2] >> (8 * (b & 3))) & 0xFFu;
+}
+
+template <int K>
+__global__ void __launch_bounds__(128) kmer_count_kernel(const uint8_t *__restrict__ codes,
+                                                        const int64_t *__restrict__ offsets,
+                                                        int32_t n, int32_t alphabet, int32_t eps,
+                                                        int32_t *__restrict__ counts,
+                                                        WsHeader *hdr) {
+  extern __shared__ uint32_t smem[];
+  const int warps = blockDim.x >> 5;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int words = (eps + 1) >> 1;
+  uint32_t *hist = smem + (size_t)wid * words;
+  for (int i = lane; i < words; i += 32) hist[i] = 0;
+  __syncwarp();
+  const int64_t codes_end = offsets[n];
+
+  for (int64_t x = (int64_t)blockIdx.x * warps + wid; x < n; x += (int64_t)gridDim.x * warps) {
+    const int64_t s = offsets[x], e = offsets[x + 1];
+    if (s < 0 || e > codes_end || e < s) {
+      // malformed offsets: nothing is read from codes
+      if (lane == 0) record_error(hdr, SAD_ERR_INVALID_ARGUMENT, (int)x);
+    } else if (e - s < K) {
+      if (lane == 0) record_error(hdr, SAD_ERR_BAD_INPUT, (int)x);
+    } else if (e - s - K + 1 > kMaxM) {
+      // 16-bit bins: longer sequences are outside what this build handles.
+      if (lane == 0) record_error(hdr, SAD_ERR_UNSUPPORTED, (int)x);
+    } else {
+      bool bad = false;
+      for (int64_t c = s & ~(int64_t)15; c < e; c += 512) {
+        const int64_t my = c + 16 * lane;
+        uint4 v = my < e ? load16_guarded(codes, my, codes_end) : make_uint4(0, 0, 0, 0);
+        uint4 nx;
+        nx.x = __shfl_down_sync(0xffffffffu, v.x, 1);
+        nx.y = __shfl_down_sync(0xffffffffu, v.y, 1);
+        nx.z = __shfl_down_sync(0xffffffffu, v.z, 1);
+        nx.w = __shfl_down_sync(0xffffffffu, v.w, 1);
+        if (lane == 31 && K > 1)
+          nx = (my + 16 < e) ? load16_guarded(codes, my + 16, codes_end) : make_uint4(0, 0, 0, 0);
+        if (my >= e) continue;
+        const uint32_t w[8] = {v.x, v.y, v.z, v.w, nx.x, nx.y, nx.z, nx.w};
+#pragma unroll
+        for (int b = 0; b < 16; ++b) {
+          const int64_t pos = my + b;
+          if (pos >= s && pos < e && byte_of(w, b) >= (uint32_t)alphabet) bad = true;
+          if (pos >= s && pos + K <= e) {
+            uint32_t tau = 0;
+#pragma unroll
+            for (int r = 0; r < K; ++r) tau = tau * (uint32_t)alphabet + byte_of(w, b + r);
+            if (tau < (uint32_t)eps) atomicAdd(&hist[tau >> 1], 1u << (16 * (tau & 1)));
+          }
+        }
+      }
+      if (__any_sync(0xffffffffu, bad) && lane == 0) record_error(hdr, SAD_ERR_BAD_INPUT, (int)x);
+    }
+    __syncwarp();
+    int32_t *row = counts + x * (int64_t)eps;
+    if ((eps & 3) == 0) {
+      for (int q = lane; q < (eps >> 2); q += 32) {
+        const uint32_t a = hist[2 * q], b = hist[2 * q + 1];
+        hist[2 * q] = 0;
+        hist[2 * q + 1] = 0;
+        reinterpret_cast<int4 *>(row)[q] =
+            make_int4((int)(a & 0xFFFFu), (int)(a >> 16), (int)(b & 0xFFFFu), (int)(b >> 16));
+      }
+    } else {
+      for (int t = lane; t < eps; t += 32)
+        row[t] = (int)((hist[t >> 1] >> (16 * (t & 1))) & 0xFFFFu);
+      __syncwarp();
+      for (int i = lane; i < words; i += 32) hist[i] = 0;
+    }
+    __syncwarp();
+  }
+}
+
+template <int K>
+int launch_count(const uint8_t *codes, const int64_t *offsets, int32_t n, int32_t alphabet,
+                 int32_t eps, int32_t *counts, WsHeader *hdr, cudaStream_t st) {
+  const size_t per_warp = sizeof(uint32_t) * (size_t)((eps + 1) / 2);
+  int warps = (int)((96 * 1024) / per_warp);
+  warps = warps < 1 ? 1 : (warps > 4 ? 4 : warps);
+  const size_t smem = per_warp * warps;
+  if (smem > 227 * 1024) return SAD_ERR_UNSUPPORTED;
+  auto kern = kmer_count_kernel<K>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return SAD_ERR_CUDA;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem) !=
+      cudaSuccess)
+    return SAD_ERR_CUDA;
+  int64_t blocks = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
+  const int64_t need = (n + warps - 1) / warps;
+  if (blocks > need) blocks = need;
+  if (blocks < 1) blocks = 1;
+  kern<<<(unsigned)blocks, warps * 32, smem, st>>>(codes, offsets, n, alphabet, eps, counts, hdr);
+  SAD_LAUNCH_CHECK();
+  return SAD_OK;
+}
+
+}  // namespace
+
+int count_launch(const uint8_t *codes, const int64_t *offsets, int32_t n, int32_t k,
+                 int32_t alphabet, int32_t eps, int32_t *counts, WsHeader *hdr,
+                 cudaStream_t st) {
+  switch (k) {
+    case 1: return launch_count<1>(codes, offsets, n, alphabet, eps, counts, hdr, st);
+    case 2: return launch_count<2>(codes, offsets, n, alphabet, eps, counts, hdr, st);
+    case 3: return launch_count<3>(codes, offsets, n, alphabet, eps, counts, hdr, st);
+    case 4: return launch_count<4>(codes, offsets, n, alphabet, eps, counts, hdr, st);
+    case 5: return launch_count<5>(codes, offsets, n, alphabet, eps, counts, hdr, st);
+    case 6: return launch_count<6>(codes, offsets, n, alphabet, eps, counts, hdr, st);
+    case 7: return launch_count<7>(codes, offsets, n, alphabet, eps, counts, hdr, st);
+    case 8: return launch_count<8>(codes, offsets, n, alphabet, eps, counts, hdr, st);
+    default: return SAD_ERR_UNSUPPORTED;
+  }
+}
+
+}  // namespace sad

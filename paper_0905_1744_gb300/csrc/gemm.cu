@@ -1,0 +1,341 @@
+// All-pairs shared k-mer counts on the tensor cores, streamed into the rank keys.
+//
+// S = P P^T over the threshold planes (see rank_prep.cu) is computed tile by tile
+// with tcgen05.mma (kind::f8f6f4, e4m3 operands that are exactly 0 or 1, f32
+// accumulation in TMEM): every product is 0 or 1 and every partial sum an
+// integer <= min(m_i, m_j) <= 65535 < 2^24, so the accumulators hold S exactly.
+// Only the upper triangle of the stored order is visited; each accumulator tile
+// goes straight into the Eq. 1 / Eq. 3 sums and is never written out:
+//
+//   term_ij = floor(S_ij 2^64 / D_ij), D_ij = m_j for stored i <= j (rows are in
+//   decreasing length), key_i += term_ij for i <= j and key_j += term_ij for i < j.
+//
+// Terms are split into 24-bit limbs; the row sums of a tile stay in registers,
+// the column sums are reduced across the 32 lanes of a warp with a transposing
+// shuffle tree, and both are added to per-sequence 64-bit limb accumulators
+// (red.global.add.u64), which a last kernel folds into the 128-bit key.
+//
+// Persistent kernel, one CTA per SM, 8 warps:
+//   warp 0      TMA producer: 128 x 128 B tile of A (rows I) and 256 x 128 B of
+//               B (rows J) per stage, 128-byte swizzle, 4-stage mbarrier ring
+//   warp 1      MMA issuer: 4 x (M=128, N=256, K=32) per stage into one of two
+//               TMEM accumulators (2 x 256 columns), commit frees the stage
+//   warp 2      TMEM allocator
+//   warps 4-7   epilogue: tcgen05.ld of the accumulator (lane quadrant = warp % 4)
+// The double TMEM accumulator lets the epilogue of one tile overlap the MMAs of
+// the next. Every wait is bounded (globaltimer); on a timeout the CTA records
+// SAD_ERR_TIMEOUT, drains its copies and MMAs in flight, frees TMEM and returns.
+#include "rank.cuh"
+
+#include <cudaTypedefs.h>
+
+namespace sad {
+
+namespace {
+
+constexpr int kStages = 4;
+constexpr uint32_t kABytes = kRowBlock * kKChunk;
+constexpr uint32_t kBBytes = kColBlock * kKChunk;
+constexpr uint32_t kTxBytes = kABytes + kBBytes;
+constexpr int kThreads = 256;
+constexpr int kEpiThreads = 128;
+constexpr uint32_t kTmemCols = 512;
+constexpr uint64_t kWaitBudgetNs = 2000000000ull;
+
+struct GemmSmem {
+  uint8_t a[kStages][kABytes];
+  uint8_t b[kStages][kBBytes];
+  uint4 colrec[2][kColBlock];
+  int32_t colorig[2][kColBlock];
+  uint64_t full[kStages];
+  uint64_t empty[kStages];
+  uint64_t tfull[2];
+  uint64_t tempty[2];
+  uint64_t drain;
+  uint32_t tmem_base;
+  int32_t abort;
+  int32_t skip;
+  int32_t never;  // stays 0: the abort flag of the drain waits
+};
+
+constexpr size_t kGemmSmemBytes = sizeof(GemmSmem) + 1024;
+
+__device__ __forceinline__ void red_add_u64(unsigned long long *p, unsigned long long v) {
+  asm volatile("red.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// v[0] of lane L becomes the sum over the 32 lanes of column L.
+__device__ __forceinline__ void transpose_reduce32(uint32_t (&v)[32], uint32_t lane) {
+#pragma unroll
+  for (int w = 16; w >= 1; w >>= 1) {
+    const bool upper = (lane & (uint32_t)w) != 0;
+#pragma unroll
+    for (int i = 0; i < w; ++i) {
+      const uint32_t send = upper ? v[i] : v[i + w];
+      const uint32_t keep = upper ? v[i + w] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+    }
+  }
+}
+
+__device__ __forceinline__ void set_abort(GemmSmem &S, WsHeader *hdr) {
+  *reinterpret_cast<volatile int32_t *>(&S.abort) = 1;
+  record_error(hdr, SAD_ERR_TIMEOUT, (int)blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    plane_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+                      const __grid_constant__ CUtensorMap tmB, RankPtrs P, int32_t n) {
+  extern __shared__ uint8_t smem_raw[];
+  GemmSmem &S = *reinterpret_cast<GemmSmem *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  volatile int32_t *abort_flag = &S.abort;
+
+  if (threadIdx.x == 0) {
+    S.abort = 0;
+    S.never = 0;
+    S.skip = (P.hdr->status != 0) ? 1 : 0;
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&S.full[s], 1);
+      mbar_init(&S.empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&S.tfull[a], 1);
+      mbar_init(&S.tempty[a], kEpiThreads);
+    }
+    mbar_init(&S.drain, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0 && lane == 0) {
+    tma_prefetch_desc(&tmA);
+    tma_prefetch_desc(&tmB);
+  }
+  __syncthreads();
+  const bool skip = S.skip != 0;
+  if (!skip && warp == 2) {
+    tmem_alloc(&S.tmem_base, kTmemCols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = S.tmem_base;
+  const int32_t n_tiles = skip ? 0 : P.hdr->n_tiles;
+
+  if (!skip && warp == 0 && lane == 0) {
+    // ------------------------------------------------------------ producer --
+    int stage = 0;
+    uint32_t phase = 0, used = 0, par = 0;
+    bool aborted = false;
+    for (int32_t t = blockIdx.x; t < n_tiles && !aborted; t += gridDim.x) {
+      const int2 tl = P.tiles[t];
+      const int32_t I = tl.x & 0xFFFF, J = tl.x >> 16, nk = tl.y;
+      for (int32_t kc = 0; kc < nk; ++kc) {
+        if (!mbar_wait_bounded(&S.empty[stage], phase ^ 1u, abort_flag, kWaitBudgetNs)) {
+          set_abort(S, P.hdr);
+          aborted = true;
+          break;
+        }
+        mbar_arrive_expect_tx(&S.full[stage], kTxBytes);
+        tma_load_2d(S.a[stage], &tmA, &S.full[stage], kc * kKChunk, I * kRowBlock);
+        tma_load_2d(S.b[stage], &tmB, &S.full[stage], kc * kKChunk, J * kColBlock);
+        used |= 1u << stage;
+        par = (par & ~(1u << stage)) | (phase << stage);
+        if (++stage == kStages) {
+          stage = 0;
+          phase ^= 1u;
+        }
+      }
+    }
+    if (aborted || *abort_flag) {
+      // let every copy this thread started land before the CTA exits
+      for (int s = 0; s < kStages; ++s)
+        if (used & (1u << s))
+          mbar_wait_bounded(&S.full[s], (par >> s) & 1u, &S.never, kWaitBudgetNs);
+    }
+  } else if (!skip && warp == 1 && lane == 0) {
+    // ----------------------------------------------------------------- MMA --
+    const uint32_t idesc = idesc_f8_e4m3(kRowBlock, kColBlock);
+    int stage = 0;
+    uint32_t phase = 0;
+    bool aborted = false;
+    int32_t lt = 0;
+    for (int32_t t = blockIdx.x; t < n_tiles && !aborted; t += gridDim.x, ++lt) {
+      const int32_t nk = P.tiles[t].y;
+      const uint32_t acc = lt & 1, aph = (lt >> 1) & 1;
+      if (!mbar_wait_bounded(&S.tempty[acc], aph ^ 1u, abort_flag, kWaitBudgetNs)) {
+        set_abort(S, P.hdr);
+        aborted = true;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t d_tmem = tmem + acc * (uint32_t)kColBlock;
+      for (int32_t kc = 0; kc < nk; ++kc) {
+        if (!mbar_wait_bounded(&S.full[stage], phase, abort_flag, kWaitBudgetNs)) {
+          set_abort(S, P.hdr);
+          aborted = true;
+          break;
+        }
+        tc_fence_after();
+        const uint64_t adesc = sdesc_kmajor_sw128(smem_u32(S.a[stage]));
+        const uint64_t bdesc = sdesc_kmajor_sw128(smem_u32(S.b[stage]));
+#pragma unroll
+        for (int kk = 0; kk < kKChunk / 32; ++kk)
+          mma_f8(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, idesc, (kc | kk) != 0 ? 1u : 0u);
+        mma_commit(&S.empty[stage]);
+        if (++stage == kStages) {
+          stage = 0;
+          phase ^= 1u;
+        }
+      }
+      if (aborted) break;
+      mma_commit(&S.tfull[acc]);
+    }
+    if (aborted || *abort_flag) {
+      mma_commit(&S.drain);
+      mbar_wait_bounded(&S.drain, 0, &S.never, kWaitBudgetNs);
+    }
+  } else if (!skip && warp >= 4) {
+    // ------------------------------------------------------------ epilogue --
+    const uint32_t q = warp & 3;
+    const uint32_t etid = threadIdx.x - 128;
+    int32_t lt = 0;
+    for (int32_t t = blockIdx.x; t < n_tiles; t += gridDim.x, ++lt) {
+      const int2 tl = P.tiles[t];
+      const int32_t I = tl.x & 0xFFFF, J = tl.x >> 16;
+      const int buf = lt & 1;
+      for (uint32_t c = etid; c < (uint32_t)kColBlock; c += kEpiThreads) {
+        const int64_t jpos = (int64_t)J * kColBlock + c;
+        S.colrec[buf][c] = P.rec[jpos];
+        S.colorig[buf][c] = P.perm[jpos];
+      }
+      const int64_t row_pos = (int64_t)I * kRowBlock + q * 32 + lane;
+      const int32_t row_orig = P.perm[row_pos];
+      const uint32_t acc = lt & 1, aph = (lt >> 1) & 1;
+      if (!mbar_wait_bounded(&S.tfull[acc], aph, abort_flag, kWaitBudgetNs)) set_abort(S, P.hdr);
+      named_bar_sync(1, kEpiThreads);  // column records staged; abort decided
+      if (*abort_flag) break;
+      tc_fence_after();
+      const bool diag = (int64_t)I * kRowBlock + kRowBlock - 1 >= (int64_t)J * kColBlock;
+      uint32_t R0 = 0, R1 = 0, R2 = 0;
+#pragma unroll 1
+      for (int c = 0; c < kColBlock / 32; ++c) {
+        uint32_t v[32];
+        tmem_ld_32x32b_x32(tmem + ((q * 32u) << 16) + acc * (uint32_t)kColBlock + c * 32u, v);
+        tmem_ld_wait();
+        uint32_t cs[32], cq[32];
+#pragma unroll
+        for (int cc = 0; cc < 32; ++cc) {
+          const uint4 rec = S.colrec[buf][c * 32 + cc];
+          const uint32_t s = __float2uint_rn(__uint_as_float(v[cc]));
+          const uint32_t d = rec.w & 0xFFFFu;
+          const uint32_t sh1 = (rec.w >> 16) & 0xFFu, sh2 = rec.w >> 24;
+          // floor(s * 2^64 / d) = s * Q + floor(s * r / d), r = 2^64 - Q d
+          const uint32_t r = 0u - rec.x * d;
+          const uint32_t xq = s * r;
+          const uint32_t t1 = __umulhi(rec.z, xq);
+          const uint32_t qv = (t1 + ((xq - t1) >> sh1)) >> sh2;
+          const uint64_t Q = ((uint64_t)rec.y << 32) | rec.x;
+          const uint64_t lo = (uint64_t)s * Q;
+          const uint64_t lo2 = lo + qv;
+          const uint32_t hi = lo2 < lo ? 1u : 0u;
+          const uint32_t wa = (uint32_t)lo2, wb = (uint32_t)(lo2 >> 32);
+          uint32_t l0 = wa & 0xFFFFFFu;
+          uint32_t l1 = (wa >> 24) | ((wb & 0xFFFFu) << 8);
+          uint32_t l2 = (wb >> 16) | (hi << 16);
+          uint32_t sc = s, qc = qv;
+          if (diag) {
+            const int64_t jpos = (int64_t)J * kColBlock + c * 32 + cc;
+            if (row_pos > jpos) { l0 = 0; l1 = 0; l2 = 0; }
+            if (row_pos >= jpos) { sc = 0; qc = 0; }
+          }
+          R0 += l0;
+          R1 += l1;
+          R2 += l2;
+          cs[cc] = sc;
+          cq[cc] = qc;
+        }
+        transpose_reduce32(cs, lane);
+        transpose_reduce32(cq, lane);
+        const int col = c * 32 + (int)lane;
+        const int32_t jorig = S.colorig[buf][col];
+        if (jorig >= 0 && (cs[0] | cq[0]) != 0) {
+          const uint4 rec = S.colrec[buf][col];
+          const uint64_t Q = ((uint64_t)rec.y << 32) | rec.x;
+          const unsigned __int128 sum = (unsigned __int128)Q * cs[0] + cq[0];
+          unsigned long long *dst = P.acc + 3 * (int64_t)jorig;
+          red_add_u64(dst + 0, (unsigned long long)(sum & 0xFFFFFFu));
+          red_add_u64(dst + 1, (unsigned long long)((sum >> 24) & 0xFFFFFFu));
+          red_add_u64(dst + 2, (unsigned long long)(sum >> 48));
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&S.tempty[acc]);
+      if (row_orig >= 0) {
+        unsigned long long *dst = P.acc + 3 * (int64_t)row_orig;
+        red_add_u64(dst + 0, R0);
+        red_add_u64(dst + 1, R1);
+        red_add_u64(dst + 2, R2);
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (!skip && warp == 2) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+int make_plane_map(CUtensorMap *map, uint8_t *planes, int64_t n_pad, int64_t k_cap, int rows) {
+  auto fn = encode_fn();
+  if (!fn) return SAD_ERR_CUDA;
+  const cuuint64_t dims[2] = {(cuuint64_t)k_cap, (cuuint64_t)n_pad};
+  const cuuint64_t strides[1] = {(cuuint64_t)k_cap};
+  const cuuint32_t box[2] = {(cuuint32_t)kKChunk, (cuuint32_t)rows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, planes, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? SAD_OK : SAD_ERR_CUDA;
+}
+
+}  // namespace
+
+int rank_gemm_launch(const RankPtrs &P, int32_t n, cudaStream_t st) {
+  const int64_t tiles = host_tile_count(n);
+  if (tiles == 0) return SAD_OK;
+  CUtensorMap mA, mB;
+  int rc = make_plane_map(&mA, P.planes, P.n_pad, P.k_cap, kRowBlock);
+  if (rc) return rc;
+  rc = make_plane_map(&mB, P.planes, P.n_pad, P.k_cap, kColBlock);
+  if (rc) return rc;
+  static bool attr_set = false;
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(plane_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kGemmSmemBytes) != cudaSuccess)
+      return SAD_ERR_CUDA;
+    attr_set = true;
+  }
+  const int64_t grid = tiles < num_sms() ? tiles : num_sms();
+  plane_gemm_kernel<<<(unsigned)grid, kThreads, kGemmSmemBytes, st>>>(mA, mB, P, n);
+  SAD_LAUNCH_CHECK();
+  return SAD_OK;
+}
+
+}  // namespace sad

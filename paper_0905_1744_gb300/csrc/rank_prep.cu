@@ -1,0 +1,543 @@
+// Preparation of the threshold-plane GEMM behind kmer_rank.
+//
+// Eq. 1's numerator S(X,Y) = sum_tau min(c^X_tau, c^Y_tau) is rewritten with the
+// exact identity min(a, b) = sum_{t>=1} [a >= t][b >= t]: with one 0/1 column
+// per (word tau, threshold t), t = 1..T_tau, T_tau = max_x c^x_tau, the matrix
+// P[x][(tau,t)] = [c^x_tau >= t] satisfies S = P P^T. The columns are laid out
+// threshold-major: section t holds the words with T_tau >= t, so the first
+// sections are the dense ones and a tile whose rows never count any word more
+// than d times only needs the first d sections (its K extent).
+//
+// Rows are stored in order of decreasing length (the order of equal lengths is
+// free: it changes no result), so that for every stored pair i <= j the Eq. 1
+// denominator is min(L_i, L_j) - k + 1 = m_j, the column's own value.
+//
+// Kernels, in launch order:
+//   rank_init      zero the scratch regions of the workspace
+//   lengths_scan   m = L - k + 1, validation, histogram of m
+//   colmax         T_tau = max_x c^x_tau, count validation
+//   colmap         t_max, section ends, K_eff, the column -> (tau, t) map
+//   lensort_scan   exclusive prefix over m in decreasing order
+//   lensort_place  row position of every sequence, per-row division records
+//   planes         P rows in fp8 e4m3 (0x38 = 1.0, 0x00 = 0.0), block depths
+//   tiles          the upper-triangle tile list with per-tile K extent
+#include "rank.cuh"
+
+namespace sad {
+
+RankPtrs rank_ptrs(void *ws, const RankLayout &L) {
+  uint8_t *b = static_cast<uint8_t *>(ws);
+  RankPtrs P;
+  P.hdr = reinterpret_cast<WsHeader *>(b);
+  P.T = reinterpret_cast<int32_t *>(b + L.T);
+  P.secend = reinterpret_cast<int32_t *>(b + L.secend);
+  P.colmap = reinterpret_cast<int32_t *>(b + L.colmap);
+  P.thist = reinterpret_cast<int32_t *>(b + L.thist);
+  P.tau_sorted = reinterpret_cast<int32_t *>(b + L.tau_sorted);
+  P.mhist = reinterpret_cast<int32_t *>(b + L.mhist);
+  P.perm = reinterpret_cast<int32_t *>(b + L.perm);
+  P.rec = reinterpret_cast<uint4 *>(b + L.rec);
+  P.depth = reinterpret_cast<int32_t *>(b + L.depth);
+  P.tiles = reinterpret_cast<int2 *>(b + L.tiles);
+  P.acc = reinterpret_cast<unsigned long long *>(b + L.acc);
+  P.planes = b + L.planes;
+  P.n_pad = L.n_pad;
+  P.k_cap = L.k_cap;
+  return P;
+}
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ void zero_range(T *p, int64_t count, int64_t tid, int64_t nthreads) {
+  for (int64_t i = tid; i < count; i += nthreads) p[i] = T(0);
+}
+
+__global__ void rank_init_kernel(RankPtrs P, int32_t n, int32_t eps, int with_keys) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nt = (int64_t)gridDim.x * blockDim.x;
+  zero_range(P.T, eps, tid, nt);
+  zero_range(P.thist, kMaxM + 2, tid, nt);
+  zero_range(P.mhist, kMaxM + 2, tid, nt);
+  zero_range(P.secend, kMaxM + 2, tid, nt);
+  if (with_keys) {
+    zero_range(P.depth, P.n_pad / kRowBlock, tid, nt);
+    zero_range(P.acc, 3 * (int64_t)n, tid, nt);
+  }
+  if (tid == 0) {
+    P.hdr->k_eff = 0;
+    P.hdr->k_pad = 0;
+    P.hdr->t_max = 0;
+    P.hdr->n_tiles = 0;
+  }
+}
+
+__global__ void lengths_kernel(const int32_t *__restrict__ lengths, int32_t n, int32_t k,
+                               RankPtrs P) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t m = lengths[x] - k + 1;
+    if (m < 1) {
+      record_error(P.hdr, SAD_ERR_BAD_INPUT, (int)x);
+    } else if (m > kMaxM) {
+      record_error(P.hdr, SAD_ERR_UNSUPPORTED, (int)x);
+    } else {
+      atomicAdd(&P.mhist[m], 1);
+    }
+  }
+}
+
+// T_tau = max over rows of counts[x][tau]. Block (256 words) x (row slice).
+__global__ void colmax_kernel(const int32_t *__restrict__ counts, int32_t n, int32_t eps,
+                              RankPtrs P) {
+  const int32_t tau = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tau >= eps) return;
+  const int64_t per = ((int64_t)n + gridDim.y - 1) / gridDim.y;
+  const int64_t r0 = (int64_t)blockIdx.y * per;
+  int64_t r1 = r0 + per;
+  if (r1 > n) r1 = n;
+  int32_t mx = 0, mn = 0;
+  int64_t r = r0;
+  for (; r + 4 <= r1; r += 4) {
+    const int32_t a = __ldg(counts + (r + 0) * eps + tau);
+    const int32_t b = __ldg(counts + (r + 1) * eps + tau);
+    const int32_t c = __ldg(counts + (r + 2) * eps + tau);
+    const int32_t d = __ldg(counts + (r + 3) * eps + tau);
+    mx = max(mx, max(max(a, b), max(c, d)));
+    mn = min(mn, min(min(a, b), min(c, d)));
+  }
+  for (; r < r1; ++r) {
+    const int32_t a = __ldg(counts + r * eps + tau);
+    mx = max(mx, a);
+    mn = min(mn, a);
+  }
+  if (mn < 0) record_error(P.hdr, SAD_ERR_BAD_INPUT, tau);
+  if (mx > kMaxM) record_error(P.hdr, SAD_ERR_UNSUPPORTED, tau);
+  if (mx > 0) atomicMax(&P.T[tau], mx);
+}
+
+// One block of 1024 threads: histogram of T, t_max, section ends secend[t] =
+// sum_{t'<=t} #{tau : T_tau >= t'}, K_eff, words sorted by decreasing T, and
+// (unless plan_only) the column map colmap[col] = tau | t << 16.
+__global__ void __launch_bounds__(1024) colmap_kernel(RankPtrs P, int32_t eps, int plan_only) {
+  __shared__ int32_t s_tmax;
+  __shared__ int32_t s_warp[32];
+  __shared__ int32_t s_carry;
+  const int tid = threadIdx.x;
+  if (tid == 0) s_tmax = 0;
+  __syncthreads();
+  int32_t local_max = 0;
+  for (int tau = tid; tau < eps; tau += blockDim.x) {
+    const int32_t t = min(P.T[tau], kMaxM);
+    local_max = max(local_max, t);
+    atomicAdd(&P.thist[t], 1);
+  }
+  atomicMax(&s_tmax, local_max);
+  __syncthreads();
+  const int32_t tmax = s_tmax;
+  // n_t = #{tau : T_tau >= t} = suffix sum of thist; secend = prefix sum of n_t.
+  // Two sequential scans over t = tmax..1 then 1..tmax, 1024 values per step.
+  // (a) suffix sums into secend[t] (temporarily n_t)
+  if (tid == 0) s_carry = 0;
+  __syncthreads();
+  for (int base = tmax; base >= 1; base -= blockDim.x) {
+    const int t = base - tid;
+    int32_t v = t >= 1 ? P.thist[t] : 0;
+    // inclusive scan over the block in thread order
+    int32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if ((tid & 31) >= o) x += y;
+    }
+    if ((tid & 31) == 31) s_warp[tid >> 5] = x;
+    __syncthreads();
+    if (tid < 32) {
+      int32_t w = s_warp[tid];
+      for (int o = 1; o < 32; o <<= 1) {
+        int32_t y = __shfl_up_sync(0xffffffffu, w, o);
+        if (tid >= o) w += y;
+      }
+      s_warp[tid] = w;
+    }
+    __syncthreads();
+    const int32_t incl = x + ((tid >> 5) > 0 ? s_warp[(tid >> 5) - 1] : 0) + s_carry;
+    if (t >= 1) P.secend[t] = incl;  // n_t
+    __syncthreads();
+    if (tid == blockDim.x - 1) s_carry = incl;
+    __syncthreads();
+  }
+  // (b) prefix sums of n_t over t = 1..tmax into secend[t]
+  if (tid == 0) s_carry = 0;
+  __syncthreads();
+  for (int base = 1; base <= tmax; base += blockDim.x) {
+    const int t = base + tid;
+    int32_t x = t <= tmax ? P.secend[t] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if ((tid & 31) >= o) x += y;
+    }
+    if ((tid & 31) == 31) s_warp[tid >> 5] = x;
+    __syncthreads();
+    if (tid < 32) {
+      int32_t w = s_warp[tid];
+      for (int o = 1; o < 32; o <<= 1) {
+        int32_t y = __shfl_up_sync(0xffffffffu, w, o);
+        if (tid >= o) w += y;
+      }
+      s_warp[tid] = w;
+    }
+    __syncthreads();
+    const int32_t incl = x + ((tid >> 5) > 0 ? s_warp[(tid >> 5) - 1] : 0) + s_carry;
+    __syncthreads();
+    if (t <= tmax) P.secend[t] = incl;
+    if (tid == blockDim.x - 1) s_carry = incl;
+    __syncthreads();
+  }
+  if (tid == 0) P.secend[0] = 0;
+  __syncthreads();
+  const int64_t k_eff = tmax >= 1 ? (int64_t)P.secend[tmax] : 0;
+  int64_t k_pad = (k_eff + kKChunk - 1) / kKChunk * kKChunk;
+  if (k_pad < kKChunk) k_pad = kKChunk;
+  if (tid == 0) {
+    P.hdr->t_max = tmax;
+    P.hdr->k_eff = k_eff;
+    P.hdr->k_pad = (int32_t)k_pad;
+  }
+  if (plan_only) return;
+  if (k_pad > P.k_cap) {
+    if (tid == 0) record_error(P.hdr, SAD_ERR_WORKSPACE, (int)k_pad);
+    return;
+  }
+  // Words in decreasing T order (ties by word index): position of tau =
+  // #{T > T_tau} + #{tau' < tau : T_tau' = T_tau}. Chunks of 32 words per warp,
+  // warps of a chunk in order, so the order is deterministic.
+  // thist is reused as the running cursor per T value: cursor[v] = #{T > v} first.
+  __syncthreads();
+  if (tid == 0) {
+    int32_t run = 0;
+    for (int v = tmax; v >= 1; --v) {
+      const int32_t c = P.thist[v];
+      P.thist[v] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  for (int base = 0; base < eps; base += blockDim.x) {
+    const int tau = base + tid;
+    const int32_t v = tau < eps ? min(P.T[tau], kMaxM) : 0;
+    const unsigned same = __match_any_sync(0xffffffffu, v);
+    const int lane = tid & 31;
+    const int rank_in_warp = __popc(same & ((1u << lane) - 1u));
+    for (int w = 0; w < 32; ++w) {
+      if ((tid >> 5) == w && v >= 1) {
+        const int32_t pos = P.thist[v] + rank_in_warp;
+        P.tau_sorted[pos] = tau;
+        __syncwarp(same);
+        if (rank_in_warp == __popc(same) - 1) P.thist[v] = pos + 1;
+      }
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  // colmap[col] for col < K_eff: section t is the first n_t words of tau_sorted.
+  for (int64_t col = tid; col < k_eff; col += blockDim.x) {
+    int lo = 1, hi = tmax;  // smallest t with secend[t] > col
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (P.secend[mid] > col) hi = mid; else lo = mid + 1;
+    }
+    const int32_t r = (int32_t)(col - P.secend[lo - 1]);
+    P.colmap[col] = P.tau_sorted[r] | (lo << 16);
+  }
+}
+
+// Exclusive prefix over m in decreasing order: mhist[m] := #{x : m_x > m}.
+__global__ void __launch_bounds__(1024) lensort_scan_kernel(RankPtrs P) {
+  __shared__ int32_t s_warp[32];
+  __shared__ int32_t s_carry;
+  const int tid = threadIdx.x;
+  if (tid == 0) s_carry = 0;
+  __syncthreads();
+  for (int base = kMaxM; base >= 1; base -= blockDim.x) {
+    const int m = base - tid;
+    const int32_t v = m >= 1 ? P.mhist[m] : 0;
+    int32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if ((tid & 31) >= o) x += y;
+    }
+    if ((tid & 31) == 31) s_warp[tid >> 5] = x;
+    __syncthreads();
+    if (tid < 32) {
+      int32_t w = s_warp[tid];
+      for (int o = 1; o < 32; o <<= 1) {
+        int32_t y = __shfl_up_sync(0xffffffffu, w, o);
+        if (tid >= o) w += y;
+      }
+      s_warp[tid] = w;
+    }
+    __syncthreads();
+    const int32_t incl = x + ((tid >> 5) > 0 ? s_warp[(tid >> 5) - 1] : 0) + s_carry;
+    __syncthreads();
+    if (m >= 1) P.mhist[m] = incl - v;
+    if (tid == blockDim.x - 1) s_carry = incl;
+    __syncthreads();
+  }
+}
+
+// Division record for denominator d (1..65535), used by the GEMM epilogue to
+// form floor(S * 2^64 / d) = S * Q + floor(S * r / d) exactly, with
+// Q = floor((2^64 - 1) / d), r = 2^64 - Q d in [1, d], and floor(x / d) for
+// x < 2^32 by Granlund & Montgomery (1994), "Division by invariant integers
+// using multiplication", Fig. 4.1: l = ceil(log2 d),
+// m' = floor(2^32 (2^l - d) / d) + 1, t1 = umulhi(m', x),
+// q = (t1 + ((x - t1) >> min(l,1))) >> max(l-1, 0).
+__device__ __forceinline__ uint4 division_record(uint32_t d) {
+  const uint64_t Q = 0xFFFFFFFFFFFFFFFFull / d;
+  const uint32_t l = 32u - (uint32_t)__clz((int)(d - 1u));
+  const uint64_t magic = (((uint64_t)1 << 32) * (((uint64_t)1 << l) - d)) / d + 1u;
+  const uint32_t sh1 = l < 1u ? l : 1u;
+  const uint32_t sh2 = l > 0u ? l - 1u : 0u;
+  return make_uint4((uint32_t)Q, (uint32_t)(Q >> 32), (uint32_t)magic,
+                    d | (sh1 << 16) | (sh2 << 24));
+}
+
+__global__ void lensort_place_kernel(const int32_t *__restrict__ lengths, int32_t n, int32_t k,
+                                     RankPtrs P) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < P.n_pad;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    if (x < n) {
+      const int32_t m = lengths[x] - k + 1;
+      if (m < 1 || m > kMaxM) continue;  // already recorded as an error
+      const int32_t pos = atomicAdd(&P.mhist[m], 1);
+      P.perm[pos] = (int32_t)x;
+      P.rec[pos] = division_record((uint32_t)m);
+    } else {
+      P.perm[x] = -1;
+      P.rec[x] = division_record(1u);  // padding rows: S = 0, term = 0
+    }
+  }
+}
+
+// One block per stored row: stage the row's counts (as 16-bit) in shared memory,
+// write the K_pad plane bytes of the row (16 per thread per step), and raise
+// the depth of its 128-row block to the row's largest count.
+__global__ void __launch_bounds__(256) planes_kernel(const int32_t *__restrict__ counts,
+                                                     int32_t n, int32_t eps, RankPtrs P) {
+  extern __shared__ uint16_t s_cnt[];
+  __shared__ int32_t s_max, s_sum;
+  if (P.hdr->status != 0) return;
+  const int32_t k_eff = (int32_t)P.hdr->k_eff;
+  const int32_t k_pad = P.hdr->k_pad;
+  for (int64_t pos = blockIdx.x; pos < P.n_pad; pos += gridDim.x) {
+    const int32_t x = P.perm[pos];
+    uint4 *dst = reinterpret_cast<uint4 *>(P.planes + pos * P.k_cap);
+    if (x < 0) {
+      for (int c = threadIdx.x; c < k_pad / 16; c += blockDim.x) dst[c] = make_uint4(0, 0, 0, 0);
+      continue;
+    }
+    if (threadIdx.x == 0) s_max = 0;
+    if (threadIdx.x == 0) s_sum = 0;
+    const int32_t *row = counts + (int64_t)x * eps;
+    int32_t mx = 0, sum = 0;
+    for (int t = threadIdx.x; t < eps; t += blockDim.x) {
+      const int32_t c = __ldg(row + t);
+      s_cnt[t] = (uint16_t)min(max(c, 0), 0xFFFF);
+      mx = max(mx, c);
+      sum += c;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+      atomicMax(&s_max, mx);
+      atomicAdd(&s_sum, sum);
+    }
+    for (int c = threadIdx.x; c < k_pad / 16; c += blockDim.x) {
+      uint32_t w[4] = {0, 0, 0, 0};
+      const int32_t c0 = c * 16;
+      if (c0 + 16 <= k_eff) {
+        const int4 *cm = reinterpret_cast<const int4 *>(P.colmap + c0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int4 e = __ldg(cm + q);
+          const int32_t ev[4] = {e.x, e.y, e.z, e.w};
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const uint32_t tau = (uint32_t)ev[b] & 0xFFFFu, t = (uint32_t)ev[b] >> 16;
+            if ((uint32_t)s_cnt[tau] >= t) w[q] |= 0x38u << (8 * b);
+          }
+        }
+      } else {
+        for (int b = 0; b < 16; ++b) {
+          if (c0 + b < k_eff) {
+            const int32_t e = __ldg(P.colmap + c0 + b);
+            const uint32_t tau = (uint32_t)e & 0xFFFFu, t = (uint32_t)e >> 16;
+            if ((uint32_t)s_cnt[tau] >= t) w[b >> 2] |= 0x38u << (8 * (b & 3));
+          }
+        }
+      }
+      dst[c] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      atomicMax(&P.depth[pos / kRowBlock], s_max);
+      // the counts of a row must add up to its number of windows, m
+      if (s_sum != (int32_t)(P.rec[pos].w & 0xFFFFu)) record_error(P.hdr, SAD_ERR_BAD_INPUT, x);
+    }
+    __syncthreads();
+  }
+}
+
+// Upper-triangle tile list. Tile (I, J) covers stored rows [128 I, 128 I + 128)
+// and columns [256 J, 256 J + 256); it is needed when some pair i <= j lies in
+// it (128 I <= 256 J + 255) and both ranges hold real rows. Tiles are grouped by
+// kGroupCols column blocks, rows ascending inside a group, so that the tiles
+// running at the same time share their operand panels in L2. Each entry is
+// (I | J << 16, K chunks), the K extent being the end of section
+// min(depth(I), depth(J)).
+constexpr int kGroupCols = 8;
+
+__global__ void __launch_bounds__(1024) tiles_kernel(RankPtrs P, int32_t n) {
+  __shared__ int32_t s_warp[32];
+  __shared__ int32_t s_carry;
+  const int tid = threadIdx.x;
+  const int32_t R = (n + kRowBlock - 1) / kRowBlock;
+  const int32_t C = (n + kColBlock - 1) / kColBlock;
+  const int32_t nblk = (int32_t)(P.n_pad / kRowBlock);
+  const int32_t groups = (C + kGroupCols - 1) / kGroupCols;
+  if (tid == 0) s_carry = 0;
+  __syncthreads();
+  const int64_t rows_total = (int64_t)groups * R;
+  for (int64_t base = 0; base < rows_total; base += blockDim.x) {
+    const int64_t gi = base + tid;
+    int32_t g = 0, I = 0, j0 = 0, j1 = 0, cnt = 0;
+    if (gi < rows_total) {
+      g = (int32_t)(gi / R);
+      I = (int32_t)(gi % R);
+      j0 = max(g * kGroupCols, (I - 1 + 1) / 2);  // smallest J with I <= 2J + 1
+      j1 = min((g + 1) * kGroupCols, C);
+      cnt = max(0, j1 - j0);
+    }
+    int32_t x = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+      int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if ((tid & 31) >= o) x += y;
+    }
+    if ((tid & 31) == 31) s_warp[tid >> 5] = x;
+    __syncthreads();
+    if (tid < 32) {
+      int32_t w = s_warp[tid];
+      for (int o = 1; o < 32; o <<= 1) {
+        int32_t y = __shfl_up_sync(0xffffffffu, w, o);
+        if (tid >= o) w += y;
+      }
+      s_warp[tid] = w;
+    }
+    __syncthreads();
+    const int32_t incl = x + ((tid >> 5) > 0 ? s_warp[(tid >> 5) - 1] : 0) + s_carry;
+    int32_t out = incl - cnt;
+    const int32_t dI = P.depth[I];
+    for (int32_t J = j0; J < j1; ++J) {
+      const int32_t b0 = 2 * J, b1 = 2 * J + 1;
+      int32_t dJ = P.depth[b0];
+      if (b1 < nblk) dJ = max(dJ, P.depth[b1]);
+      const int32_t d = min(dI, dJ);
+      const int32_t kend = P.secend[min(d, P.hdr->t_max)];
+      P.tiles[out++] = make_int2(I | (J << 16), (kend + kKChunk - 1) / kKChunk);
+    }
+    __syncthreads();
+    if (tid == blockDim.x - 1) s_carry = incl;
+    __syncthreads();
+  }
+  if (tid == 0) P.hdr->n_tiles = s_carry;
+}
+
+// key = acc0 + acc1 2^24 + acc2 2^48 (128-bit); rank = (hi + lo 2^-64) / N.
+__global__ void finalize_kernel(RankPtrs P, int32_t n, uint64_t *__restrict__ key_hi,
+                                uint64_t *__restrict__ key_lo, double *__restrict__ rank) {
+  if (P.hdr->status != 0) return;
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned __int128 a0 = P.acc[3 * x + 0], a1 = P.acc[3 * x + 1], a2 = P.acc[3 * x + 2];
+    const unsigned __int128 key = a0 + (a1 << 24) + (a2 << 48);
+    const uint64_t hi = (uint64_t)(key >> 64), lo = (uint64_t)key;
+    key_hi[x] = hi;
+    key_lo[x] = lo;
+    if (rank) {
+      const double whole = __ull2double_rn(hi);
+      const double frac = __dmul_rn(__ull2double_rn(lo), 0x1p-64);
+      rank[x] = __ddiv_rn(__dadd_rn(whole, frac), (double)n);
+    }
+  }
+}
+
+inline unsigned grid_for(int64_t work, int threads, int cap_per_sm = 8) {
+  int64_t g = (work + threads - 1) / threads;
+  const int64_t cap = (int64_t)num_sms() * cap_per_sm;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
+}  // namespace
+
+int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *lengths,
+                     int32_t n, int32_t k, int32_t eps, int plan_only, cudaStream_t st) {
+  rank_init_kernel<<<grid_for(kMaxM + 2, 256), 256, 0, st>>>(P, n, eps, !plan_only);
+  SAD_LAUNCH_CHECK();
+  if (!plan_only) {
+    lengths_kernel<<<grid_for(n, 256), 256, 0, st>>>(lengths, n, k, P);
+    SAD_LAUNCH_CHECK();
+  }
+  {
+    dim3 g((eps + 255) / 256, 1);
+    int64_t slices = ((int64_t)num_sms() * 8 + g.x - 1) / g.x;
+    if (slices > (n + 63) / 64) slices = (n + 63) / 64;
+    if (slices < 1) slices = 1;
+    g.y = (unsigned)slices;
+    colmax_kernel<<<g, 256, 0, st>>>(counts, n, eps, P);
+    SAD_LAUNCH_CHECK();
+  }
+  colmap_kernel<<<1, 1024, 0, st>>>(P, eps, plan_only);
+  SAD_LAUNCH_CHECK();
+  if (plan_only) return SAD_OK;
+  lensort_scan_kernel<<<1, 1024, 0, st>>>(P);
+  SAD_LAUNCH_CHECK();
+  lensort_place_kernel<<<grid_for(P.n_pad, 256), 256, 0, st>>>(lengths, n, k, P);
+  SAD_LAUNCH_CHECK();
+  {
+    const size_t smem = sizeof(uint16_t) * (size_t)eps;
+    if (cudaFuncSetAttribute(planes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      return SAD_ERR_CUDA;
+    unsigned g = (unsigned)(P.n_pad < (int64_t)num_sms() * 16 ? P.n_pad : (int64_t)num_sms() * 16);
+    planes_kernel<<<g, 256, smem, st>>>(counts, n, eps, P);
+    SAD_LAUNCH_CHECK();
+  }
+  tiles_kernel<<<1, 1024, 0, st>>>(P, n);
+  SAD_LAUNCH_CHECK();
+  return SAD_OK;
+}
+
+int rank_finalize_launch(const RankPtrs &P, int32_t n, uint64_t *key_hi, uint64_t *key_lo,
+                         double *rank, cudaStream_t st) {
+  finalize_kernel<<<grid_for(n, 256), 256, 0, st>>>(P, n, key_hi, key_lo, rank);
+  SAD_LAUNCH_CHECK();
+  return SAD_OK;
+}
+
+int64_t host_tile_count(int32_t n) {
+  const int64_t R = (n + kRowBlock - 1) / kRowBlock;
+  const int64_t C = (n + kColBlock - 1) / kColBlock;
+  int64_t total = 0;
+  for (int64_t I = 0; I < R; ++I) {
+    const int64_t j0 = I / 2;  // smallest J with I <= 2J + 1
+    if (j0 < C) total += C - j0;
+  }
+  return total;
+}
+
+}  // namespace sad

@@ -1,0 +1,295 @@
+// Internal definitions shared by the libsad translation units: workspace
+// layouts, device-side status recording, launch bookkeeping and the inline-PTX
+// wrappers for mbarrier, TMA (cp.async.bulk.tensor) and tcgen05 (5th-generation
+// tensor cores with TMEM accumulators) on sm_103a.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sad.h"
+
+namespace sad {
+
+// ---------------------------------------------------------------- limits ----
+constexpr int kMaxEps = 65536;          // words per count vector
+constexpr int kMaxM = 65535;            // k-mers per sequence (L - k + 1)
+constexpr int kMaxP = 4096;             // buckets
+constexpr int kRowBlock = 128;          // GEMM tile rows (A operand, M)
+constexpr int kColBlock = 256;          // GEMM tile columns (B operand, N)
+constexpr int kKChunk = 128;            // K bytes per pipeline stage (one 128B swizzle row)
+constexpr int kNPad = 256;              // rows are padded to a multiple of this
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// --------------------------------------------------------- workspace hdr ----
+// The first 256 bytes of every workspace.
+struct WsHeader {
+  int32_t status;        // first recorded sad_status (0 = none)
+  int32_t detail;        // optional detail of the error (e.g. offending index)
+  int64_t k_eff;         // plane columns the data needs (kmer_rank)
+  int32_t k_pad;         // k_eff rounded up to kKChunk
+  int32_t t_max;         // largest count of any word in any sequence
+  int32_t n_tiles;       // GEMM tiles scheduled
+  int32_t n_valid_blocks;
+  int32_t pad[56];
+};
+static_assert(sizeof(WsHeader) == 256, "header is 256 bytes");
+
+__device__ __forceinline__ void record_error(WsHeader *h, int code, int detail = 0) {
+  if (atomicCAS(&h->status, 0, code) == 0) h->detail = detail;
+}
+
+// Offsets of the rank workspace regions (bytes from the workspace base).
+struct RankLayout {
+  size_t T, secend, colmap, thist, tau_sorted, mhist, perm, rec, depth, tiles, acc, planes;
+  size_t fixed_bytes;    // everything before the planes
+  int64_t n_pad, k_cap, max_tiles;
+};
+
+inline int64_t n_pad_of(int64_t n) { return (int64_t)align_up((size_t)(n > 0 ? n : 1), kNPad); }
+
+inline int64_t max_tiles_of(int64_t n_pad) {
+  return (n_pad / kRowBlock) * (n_pad / kColBlock);
+}
+
+inline RankLayout rank_layout(int64_t n, int64_t eps, int64_t k_cap) {
+  RankLayout L{};
+  L.n_pad = n_pad_of(n);
+  L.k_cap = k_cap;
+  L.max_tiles = max_tiles_of(L.n_pad);
+  size_t o = sizeof(WsHeader);
+  auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes, 256); return r; };
+  L.T = take(sizeof(int32_t) * eps);
+  L.secend = take(sizeof(int32_t) * (kMaxM + 2));
+  L.colmap = take(sizeof(int32_t) * (size_t)(k_cap > 0 ? k_cap : 1));
+  L.thist = take(sizeof(int32_t) * (kMaxM + 2));
+  L.tau_sorted = take(sizeof(int32_t) * eps);
+  L.mhist = take(sizeof(int32_t) * (kMaxM + 2));
+  L.perm = take(sizeof(int32_t) * L.n_pad);
+  L.rec = take(16 * (size_t)L.n_pad);
+  L.depth = take(sizeof(int32_t) * (L.n_pad / kRowBlock));
+  L.tiles = take(2 * sizeof(int32_t) * L.max_tiles);
+  L.acc = take(3 * sizeof(uint64_t) * (size_t)(n > 0 ? n : 1));
+  o = align_up(o, 1024);
+  L.fixed_bytes = o;
+  L.planes = o;
+  return L;
+}
+
+// Item of the partition: a rank key and its input index.
+struct Item {
+  uint64_t hi, lo;
+  int32_t idx;
+  int32_t pad;
+};
+
+__host__ __device__ __forceinline__ bool item_less(const Item &a, const Item &b) {
+  if (a.hi != b.hi) return a.hi < b.hi;
+  if (a.lo != b.lo) return a.lo < b.lo;
+  return a.idx < b.idx;
+}
+
+struct PartLayout {
+  size_t items, items2, samples, samples2, pos, dest, pivots;
+  size_t bytes;
+};
+
+inline PartLayout part_layout(int64_t n, int64_t p) {
+  PartLayout L{};
+  size_t o = sizeof(WsHeader);
+  auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes, 256); return r; };
+  int64_t ns = p * (p - 1);
+  L.items = take(sizeof(Item) * (size_t)(n > 0 ? n : 1));
+  L.items2 = take(sizeof(Item) * (size_t)(n > 0 ? n : 1));
+  L.samples = take(sizeof(Item) * (size_t)(ns > 0 ? ns : 1));
+  L.samples2 = take(sizeof(Item) * (size_t)(ns > 0 ? ns : 1));
+  L.pos = take(sizeof(int32_t) * (size_t)(p * p));
+  L.dest = take(sizeof(int32_t) * (size_t)(p * p));
+  L.pivots = take(sizeof(Item) * (size_t)(p > 1 ? p - 1 : 1));
+  L.bytes = o;
+  return L;
+}
+
+// ------------------------------------------------------ host bookkeeping ----
+void note_launch(int n = 1);
+int num_sms();
+
+#define SAD_LAUNCH_CHECK()                                   \
+  do {                                                       \
+    ::sad::note_launch();                                    \
+    if (cudaPeekAtLastError() != cudaSuccess) {              \
+      cudaGetLastError();                                    \
+      return SAD_ERR_CUDA;                                   \
+    }                                                        \
+  } while (0)
+
+// ------------------------------------------------------------- PTX: misc ----
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
+
+__device__ __forceinline__ bool elect_lane0() { return (threadIdx.x & 31) == 0; }
+
+// Named barrier among `count` threads (multiple of 32).
+__device__ __forceinline__ void named_bar_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// --------------------------------------------------------- PTX: mbarrier ----
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity to complete. Gives up when
+// *abort becomes non-zero or after `budget_ns` of wall time; returns false then.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  volatile int *abort, uint64_t budget_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  uint64_t t0 = globaltimer_ns();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 63) == 0) {
+      if (*abort) return false;
+      if (globaltimer_ns() - t0 > budget_ns) return false;
+    }
+  }
+}
+
+// --------------------------------------------------------------- PTX: TMA ----
+__device__ __forceinline__ void tma_load_2d(void *smem_dst, const CUtensorMap *map,
+                                            uint64_t *bar, int32_t x, int32_t y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(smem_dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap *map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+// ----------------------------------------------------------- PTX: tcgen05 ----
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(dst_smem)),
+               "r"(ncols)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, 8-bit float operands (kind::f8f6f4).
+__device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                       uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Arrive on an mbarrier once all previously issued tcgen05.mma of this thread complete.
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+// 32 lanes x 32 columns of 32-bit TMEM cells -> 32 registers per thread
+// (thread = lane = accumulator row, register r = column base + r).
+__device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+        "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+        "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+        "=r"(v[31])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld_wait() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor for a K-major operand tile stored with the
+// 128-byte swizzle (rows of 128 bytes, 8-row atoms of 1024 bytes).
+__device__ __forceinline__ uint64_t sdesc_kmajor_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address, 16-byte units
+  d |= (uint64_t)1 << 16;                     // leading byte offset (unused with SW128 K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;                     // descriptor version for tcgen05
+  d |= (uint64_t)2 << 61;                     // swizzle: 128B
+  return d;
+}
+
+// Instruction descriptor, kind::f8f6f4: D=f32, A=B=e4m3, both K-major, shape M x N.
+__host__ __device__ constexpr uint32_t idesc_f8_e4m3(int M, int N) {
+  return (1u << 4)                       // D format f32
+         | (0u << 7) | (0u << 10)        // A, B = E4M3
+         | (0u << 15) | (0u << 16)       // K-major A and B
+         | ((uint32_t)(N >> 3) << 17)    // N / 8
+         | ((uint32_t)(M >> 4) << 24);   // M / 16
+}
+
+}  // namespace sad

@@ -1,0 +1,212 @@
+"""Thin Python binding of libsad (include/sad.h).
+
+Argument marshalling only: every step runs in the CUDA library. torch tensors
+provide device memory and streams. The library is loaded on first use; if it is
+missing or fails to load, the call raises -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+OK, ERR_INVALID_ARGUMENT, ERR_WORKSPACE, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED, \
+    ERR_BAD_INPUT = range(7)
+OP_COUNT, OP_RANK, OP_PARTITION = 0, 1, 2
+
+_lib = None
+_lock = threading.Lock()
+
+
+class SadError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _load().sad_status_string(status).decode() if _lib is not None else str(status)
+        super().__init__(f"{where}: {msg} (status {status})")
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libsad.so not found at {path}: run __graft_entry__.build() "
+                               "(the CUDA library is required; there is no CPU path)")
+        lib = ctypes.CDLL(path)
+        P, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+        lib.sad_status_string.argtypes = [ctypes.c_int]
+        lib.sad_status_string.restype = ctypes.c_char_p
+        lib.sad_abi_version.restype = ctypes.c_int
+        lib.sad_launch_count.restype = ctypes.c_uint64
+        lib.sad_workspace_bytes.argtypes = [i32, i32, i32, i32, i32, i32]
+        lib.sad_workspace_bytes.restype = sz
+        lib.kmer_count.argtypes = [P, P, i32, i32, i32, P, P, sz, P]
+        lib.kmer_count.restype = ctypes.c_int
+        lib.kmer_rank_plan.argtypes = [P, i32, i32, i32, P, sz, ctypes.POINTER(i64),
+                                       ctypes.POINTER(sz), P]
+        lib.kmer_rank_plan.restype = ctypes.c_int
+        lib.kmer_rank.argtypes = [P, P, i32, i32, i32, P, P, P, P, sz, P]
+        lib.kmer_rank.restype = ctypes.c_int
+        lib.partition.argtypes = [P, P, i32, i32, P, P, P, P, sz, P]
+        lib.partition.restype = ctypes.c_int
+        lib.sad_status_read.argtypes = [P, i32, P]
+        lib.sad_status_read.restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def lib():
+    return _load()
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check(rc: int, where: str):
+    if rc != OK:
+        raise SadError(rc, where)
+
+
+def launch_count() -> int:
+    return int(_load().sad_launch_count())
+
+
+def workspace_bytes(op: int, n: int, k: int = 3, alphabet: int = 20, p: int = 1,
+                    depth: int = 1) -> int:
+    return int(_load().sad_workspace_bytes(op, n, k, alphabet, p, depth))
+
+
+class Workspace:
+    """A reusable device workspace (uint8 tensor, grown on demand)."""
+
+    def __init__(self, device=None, nbytes: int = 0):
+        self.device = torch.device(device or "cuda")
+        self.buf = None
+        if nbytes:
+            self.ensure(nbytes)
+
+    def ensure(self, nbytes: int):
+        nbytes = max(int(nbytes), 256)
+        if self.buf is None or self.buf.numel() < nbytes:
+            self.buf = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            self.clear_status()
+        return self.buf
+
+    @property
+    def nbytes(self) -> int:
+        return 0 if self.buf is None else self.buf.numel()
+
+    def clear_status(self):
+        if self.buf is not None:
+            self.buf[:8].zero_()
+
+    def status(self, clear: bool = True, stream=None) -> int:
+        return int(_load().sad_status_read(_ptr(self.buf), 1 if clear else 0, _stream(stream)))
+
+    def check(self, where: str, stream=None):
+        _check(self.status(True, stream), where)
+
+
+def kmer_count(codes: torch.Tensor, offsets: torch.Tensor, k: int = 3, alphabet: int = 20,
+               ws: Workspace | None = None, out: torch.Tensor | None = None, stream=None,
+               check: bool = True) -> torch.Tensor:
+    """int32 [N, alphabet**k] count vectors (Sec. 3, "k-mer Rank")."""
+    n = offsets.numel() - 1
+    ws = ws or Workspace(codes.device)
+    ws.ensure(workspace_bytes(OP_COUNT, n, k, alphabet))
+    if out is None:
+        out = torch.empty((n, alphabet ** k), dtype=torch.int32, device=codes.device)
+    _check(_load().kmer_count(_ptr(codes), _ptr(offsets), n, k, alphabet, _ptr(out),
+                              _ptr(ws.buf), ws.nbytes, _stream(stream)), "kmer_count")
+    if check:
+        ws.check("kmer_count", stream)
+    return out
+
+
+def kmer_rank_plan(counts: torch.Tensor, k: int = 3, alphabet: int = 20,
+                   ws: Workspace | None = None, stream=None):
+    """(K_eff, workspace bytes kmer_rank needs). Synchronous."""
+    n = counts.shape[0]
+    ws = ws or Workspace(counts.device)
+    ws.ensure(workspace_bytes(OP_RANK, n, k, alphabet, depth=0))
+    k_eff, need = ctypes.c_int64(0), ctypes.c_size_t(0)
+    _check(_load().kmer_rank_plan(_ptr(counts), n, k, alphabet, _ptr(ws.buf), ws.nbytes,
+                                  ctypes.byref(k_eff), ctypes.byref(need), _stream(stream)),
+           "kmer_rank_plan")
+    return int(k_eff.value), int(need.value)
+
+
+def kmer_rank(counts: torch.Tensor, lengths: torch.Tensor, k: int = 3, alphabet: int = 20,
+              ws: Workspace | None = None, with_rank: bool = True, stream=None,
+              out=None, check: bool = True, plan: bool = True):
+    """(key_hi uint64, key_lo uint64, rank float64 | None), Eq. 1 and Eq. 3.
+
+    With plan=True the workspace is sized exactly by kmer_rank_plan first.
+    """
+    n = counts.shape[0]
+    dev = counts.device
+    ws = ws or Workspace(dev)
+    if plan:
+        _, need = kmer_rank_plan(counts, k, alphabet, ws, stream)
+        ws.ensure(need)
+    if out is None:
+        hi = torch.empty(n, dtype=torch.uint64, device=dev)
+        lo = torch.empty(n, dtype=torch.uint64, device=dev)
+        rank = torch.empty(n, dtype=torch.float64, device=dev) if with_rank else None
+    else:
+        hi, lo, rank = out
+    lengths = lengths.to(device=dev, dtype=torch.int32).contiguous()
+    _check(_load().kmer_rank(_ptr(counts), _ptr(lengths), n, k, alphabet, _ptr(hi), _ptr(lo),
+                             _ptr(rank), _ptr(ws.buf), ws.nbytes, _stream(stream)), "kmer_rank")
+    if check:
+        ws.check("kmer_rank", stream)
+    return hi, lo, rank
+
+
+def partition(key_hi: torch.Tensor, key_lo: torch.Tensor, p: int, ws: Workspace | None = None,
+              stream=None, out=None, check: bool = True):
+    """(bucket_offsets int32 [p+1], members int32 [N], pivot_idx int32 [p-1])."""
+    n = key_hi.numel()
+    dev = key_hi.device
+    ws = ws or Workspace(dev)
+    ws.ensure(workspace_bytes(OP_PARTITION, n, p=p))
+    if out is None:
+        offs = torch.empty(p + 1, dtype=torch.int32, device=dev)
+        mem = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        piv = torch.empty(max(p - 1, 1), dtype=torch.int32, device=dev)
+    else:
+        offs, mem, piv = out
+    _check(_load().partition(_ptr(key_hi), _ptr(key_lo), n, p, _ptr(offs), _ptr(mem),
+                             _ptr(piv) if p > 1 else None, _ptr(ws.buf), ws.nbytes,
+                             _stream(stream)), "partition")
+    if check:
+        ws.check("partition", stream)
+    return offs, mem[:n], piv[:max(p - 1, 0)]
+
+
+def partition_set(codes: torch.Tensor, offsets: torch.Tensor, p: int, k: int = 3,
+                  alphabet: int = 20, ws: Workspace | None = None, stream=None):
+    """count -> rank -> partition of one sequence set on the device."""
+    ws = ws or Workspace(codes.device)
+    counts = kmer_count(codes, offsets, k, alphabet, ws=ws, stream=stream)
+    lengths = (offsets[1:] - offsets[:-1]).to(torch.int32)
+    hi, lo, rank = kmer_rank(counts, lengths, k, alphabet, ws=ws, stream=stream)
+    offs, mem, piv = partition(hi, lo, p, ws=ws, stream=stream)
+    return dict(counts=counts, key_hi=hi, key_lo=lo, rank=rank, bucket_offsets=offs,
+                members=mem, pivot_idx=piv)
