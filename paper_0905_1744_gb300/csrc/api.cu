@@ -33,7 +33,8 @@ bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) %
 int64_t k_cap_for(int64_t n, int64_t eps, size_t ws_bytes) {
   const RankLayout base = rank_layout(n, eps, 0);
   if (ws_bytes <= base.fixed_bytes) return 0;
-  int64_t k = (int64_t)((ws_bytes - base.fixed_bytes) / (size_t)(base.n_pad + 4));
+  // upper bound (the fixed part only grows with K_cap), then step down until it fits
+  int64_t k = (int64_t)((ws_bytes - base.fixed_bytes) / (size_t)base.n_pad);
   k = k / kKChunk * kKChunk;
   while (k > 0) {
     const RankLayout L = rank_layout(n, eps, k);
