@@ -1,0 +1,410 @@
+#!/usr/bin/env python3
+"""Throughput of the Sample-Align-D decomposition hot path on GB300.
+
+One step = kmer_count -> kmer_rank -> partition of one synthetic sequence set
+(default: N = 20000 protein sequences in 50 families, k = 3, p = 16) with the
+inputs already in HBM. The metric is k-mer pair comparisons per second: the
+N(N-1)/2 pairs whose shared k-mer count (Eq. 1) enters the ranks, per step time.
+
+Prints one JSON line. Extra objects:
+  roofline      the plane-GEMM kernel: algorithmic tensor work per launch over
+                its CUDA-event time, against the measured fp8 peak
+  cpu_baseline  the CPU oracle on a bounded sample of the same workload
+  e2e           the same metric through the public API with host buffers
+                (H2D of codes + offsets and D2H of the buckets and keys timed)
+  clocks        SM clocks and throttle reasons sampled during the timed region
+
+--impl reference times the CPU oracle on the same workload instead (one bounded
+sample per step). Under torchrun each rank runs an independent replica of the
+workload (the path does not shard); value is the sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_0905_1744_gb300 import datagen  # noqa: E402
+
+WORKLOADS = {
+    1: "N=200 iid protein sequences, L uniform 100-400, k=3 (8000 words), p=4",
+    2: "N=20000 sequences in 50 families (ancestor L ~ N(300,100) clipped to 50-1000, "
+       "20-40% substitutions, 2% indels of length 1-10), k=3, p=16",
+    3: "N=100000 sequences in 500 families (ancestor L log-uniform 50-2000), k=3, p=64",
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="sad", choices=["sad", "reference"])
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+# ------------------------------------------------------------------ clocks ---
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons every 200 ms while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- CPU oracle ---
+
+def oracle_sample(s, seconds: float, seed: int = 0):
+    """Time the oracle's rank on a row sample sized to ~`seconds` of CPU work.
+
+    Returns (pairs_per_s, rows, elapsed, threads). The oracle computes each
+    row's shared counts with all N sequences, so R rows stand for R/N of the
+    full rank; the full set's pair count N(N-1)/2 then takes t * N / R.
+    """
+    import oracle
+    oracle.build()
+    threads = oracle.default_threads()
+    counts = oracle.kmer_count(s.codes, s.offsets)
+    rng = np.random.default_rng(seed)
+    r0 = max(threads, 8)
+    rows = rng.choice(s.n, size=min(r0, s.n), replace=False)
+    t0 = time.perf_counter()
+    oracle.kmer_rank(counts, s.lengths, rows=rows, threads=threads)
+    t_cal = time.perf_counter() - t0
+    r = int(min(s.n, max(r0, r0 * seconds / max(t_cal, 1e-6))))
+    rows = rng.choice(s.n, size=r, replace=False)
+    t0 = time.perf_counter()
+    oracle.kmer_rank(counts, s.lengths, rows=rows, threads=threads)
+    t = time.perf_counter() - t0
+    pairs_full = s.n * (s.n - 1) / 2
+    return pairs_full / (t * s.n / r), r, t, threads
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    s = datagen.config(args.config, args.seed)
+    per_step = max(1.0, 150.0 / max(1, args.steps + args.warmup))
+    vals, rows_used, threads = [], 0, 1
+    for i in range(args.warmup + args.steps):
+        v, r, t, threads = oracle_sample(s, per_step, seed=args.seed + i)
+        if i >= args.warmup:
+            vals.append(v)
+            rows_used = r
+    value = statistics.mean(vals)
+    pairs = s.n * (s.n - 1) / 2
+    out = {
+        "impl": "reference", "metric": "k-mer pair comparisons/s", "value": value,
+        "unit": "pairs/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * pairs / value, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64/uint128 (CPU)", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.config], "N": s.n, "p": s.p, "k": 3},
+        "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": threads, "kind": "oracle",
+                         "sample": f"rank of {rows_used} random rows against all {s.n} "
+                                   f"sequences per step, extrapolated to the full set",
+                         "cpu": cpu_model()},
+        "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+# --------------------------------------------------------------------- GPU ---
+
+def gemm_traffic_per_launch(n: int, k_eff: int):
+    """Scaled DRAM traffic of the plane GEMM from the committed ncu summary, or
+    None when the kernel source changed since that capture."""
+    path = os.path.join(ROOT, "profiles", "plane_gemm_traffic.json")
+    src = os.path.join(ROOT, "paper_0905_1744_gb300", "csrc", "gemm.cu")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        with open(src, "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+    except (OSError, ValueError):
+        return None
+    if d.get("gemm_cu_sha256") != sha or d.get("N") != n:
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def run_sad(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_0905_1744_gb300 import sad
+
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    s = datagen.config(args.config, args.seed)
+    n, p = s.n, s.p
+    pairs = n * (n - 1) / 2
+    stream = torch.cuda.current_stream()
+
+    codes = torch.from_numpy(s.codes).to(dev)
+    offsets = torch.from_numpy(s.offsets).to(dev)
+    lengths = torch.from_numpy(s.lengths.astype(np.int32)).to(dev)
+    ws = sad.Workspace(dev)
+    counts = torch.empty((n, 8000), dtype=torch.int32, device=dev)
+    sad.kmer_count(codes, offsets, ws=ws, out=counts)
+    k_eff, need = sad.kmer_rank_plan(counts, ws=ws)
+    ws.ensure(max(need, sad.workspace_bytes(sad.OP_PARTITION, n, p=p)))
+    keys = (torch.empty(n, dtype=torch.uint64, device=dev),
+            torch.empty(n, dtype=torch.uint64, device=dev),
+            torch.empty(n, dtype=torch.float64, device=dev))
+    ws_part = sad.Workspace(dev, sad.workspace_bytes(sad.OP_PARTITION, n, p=p))
+    part = (torch.empty(p + 1, dtype=torch.int32, device=dev),
+            torch.empty(n, dtype=torch.int32, device=dev),
+            torch.empty(max(p - 1, 1), dtype=torch.int32, device=dev))
+
+    def step():
+        sad.kmer_count(codes, offsets, ws=ws, out=counts, check=False)
+        sad.kmer_rank(counts, lengths, ws=ws, out=keys, check=False, plan=False)
+        sad.partition(keys[0], keys[1], p, ws=ws_part, out=part, check=False)
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # 2x the 129 MB L2
+    for _ in range(args.warmup):
+        step()
+    ws.check("warmup rank")
+    ws_part.check("warmup partition")
+    info = sad.rank_info(ws)
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = sad.launch_count()
+    sad.profile(True)
+    for e0, e1 in evs:
+        flush.zero_()
+        e0.record(stream)
+        step()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    sad.profile(False)
+    launches = sad.launch_count() - launches0
+    clocks = sampler.stop()
+    gemm_ms, gemm_n = sad.profile_read()
+    ws.check("timed rank")
+    ws_part.check("timed partition")
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    ms_per_step = total_ms / args.steps
+    value = world * pairs / (ms_per_step / 1e3)
+
+    # roofline of the plane GEMM (the dominant kernel)
+    pk, pk_kind = peaks()
+    fp8_peak = 2.0 * pk["bf16_tflops_sustained"]   # e4m3 dense = 2 x bf16 (nominal ratio)
+    gemm_launch_ms = gemm_ms / max(gemm_n, 1)
+    alg_flops = 2.0 * info["k_eff"] * n * (n + 1) / 2           # S = P P^T, upper triangle
+    exec_flops = 2.0 * 128 * 256 * 128 * info["k_chunks"]        # MMA work actually issued
+    useful_flops = 2.0 * 8000 * pairs                             # Eq. 1 as written: 2 eps / pair
+    achieved = alg_flops / (gemm_launch_ms / 1e3) / 1e12
+    roofline = {
+        "bound": "tensor", "kernel": "plane_gemm_kernel (tcgen05 kind::f8f6f4)",
+        "achieved": achieved, "peak": fp8_peak, "unit": "TFLOP/s", "frac": achieved / fp8_peak,
+        "peak_source": f"{pk_kind}: 2 x bf16_tflops_sustained (e4m3/bf16 nominal ratio)",
+        "traffic": gemm_traffic_per_launch(n, info["k_eff"]),
+        "gemm_ms_per_launch": gemm_launch_ms, "gemm_share_of_step": gemm_launch_ms / ms_per_step,
+        "k_eff": info["k_eff"], "k_pad": info["k_pad"], "t_max": info["t_max"],
+        "tiles": info["tiles"],
+        "executed_tflops": exec_flops / (gemm_launch_ms / 1e3) / 1e12,
+        "executed_frac": exec_flops / (gemm_launch_ms / 1e3) / 1e12 / fp8_peak,
+        "useful_frac": useful_flops / (gemm_launch_ms / 1e3) / 1e12 / fp8_peak,
+    }
+
+    # end to end through the public API, host buffers, H2D/D2H inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        h_codes = torch.from_numpy(s.codes).pin_memory()
+        h_offs = torch.from_numpy(s.offsets).pin_memory()
+        h_mem = torch.empty(n, dtype=torch.int32).pin_memory()
+        h_boff = torch.empty(p + 1, dtype=torch.int32).pin_memory()
+        h_hi = torch.empty(n, dtype=torch.uint64).pin_memory()
+        h_lo = torch.empty(n, dtype=torch.uint64).pin_memory()
+        ws_e = sad.Workspace(dev)
+
+        def e2e_step():
+            d_codes = h_codes.to(dev, non_blocking=True)
+            d_offs = h_offs.to(dev, non_blocking=True)
+            res = sad.partition_set(d_codes, d_offs, p, ws=ws_e)
+            h_mem.copy_(res["members"], non_blocking=True)
+            h_boff.copy_(res["bucket_offsets"], non_blocking=True)
+            h_hi.copy_(res["key_hi"], non_blocking=True)
+            h_lo.copy_(res["key_lo"], non_blocking=True)
+            torch.cuda.synchronize()
+
+        for _ in range(2):
+            e2e_step()
+        reps = max(3, min(args.steps, 20))
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            e2e_step()
+        t_e2e = (time.perf_counter() - t0) / reps
+        if world > 1:
+            t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        e2e = {"value": world * pairs / t_e2e, "unit": "pairs/s",
+               "h2d_bytes_per_step": int(s.codes.nbytes + s.offsets.nbytes),
+               "d2h_bytes_per_step": int(4 * n + 4 * (p + 1) + 16 * n),
+               "ms_per_step": 1e3 * t_e2e}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, r, t, threads = oracle_sample(s, args.cpu_seconds, seed=args.seed)
+        cpu = {"value": v, "unit": "pairs/s", "cores": threads, "kind": "oracle",
+               "sample": f"rank of {r} random rows against all {n} sequences "
+                         f"({t:.1f} s), extrapolated to the full set",
+               "cpu": cpu_model()}
+
+    if rank == 0:
+        out = {
+            "metric": "k-mer pair comparisons/s", "value": value, "unit": "pairs/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "fp8_e4m3 0/1 planes, f32 acc (exact), u128 keys",
+            "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.config], "N": n, "p": p, "k": 3,
+                       "alphabet": 20, "seed": args.seed,
+                       "l2": "flushed between steps (256 MB write)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "gpu_launches": int(launches),
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clocks,
+            "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms),
+        }
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_sad(args)
+
+
+if __name__ == "__main__":
+    main()

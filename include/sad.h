@@ -18,7 +18,8 @@
  *   device (a letter code >= alphabet, a sequence shorter than k, a workspace
  *   too small for the data) are recorded in the workspace's status word and
  *   reported by sad_status_read(); kernels that see a recorded error skip their
- *   work, so outputs are then undefined.
+ *   work, so outputs are then undefined. A recorded status stays until
+ *   sad_status_read(..., clear = 1) resets it.
  * - Indices are 0-based positions in the input order. All results are
  *   deterministic integers (floating outputs are derived views).
  * - Layouts are row-major and densely packed.
@@ -42,7 +43,8 @@ typedef enum sad_status {
   SAD_ERR_CUDA = 3,             /* a CUDA runtime call failed                  */
   SAD_ERR_TIMEOUT = 4,          /* a bounded device-side wait gave up          */
   SAD_ERR_UNSUPPORTED = 5,      /* parameters outside what this build handles  */
-  SAD_ERR_BAD_INPUT = 6         /* letter code >= alphabet, or length < k      */
+  SAD_ERR_BAD_INPUT = 6         /* code >= alphabet, length < k, counts that do
+                                   not add up to L - k + 1                     */
 } sad_status;
 
 typedef enum sad_op {
@@ -67,7 +69,8 @@ int sad_abi_version(void);
  *             multiple of eps (K_cap = eps * depth rounded up to 128). The
  *             columns kmer_rank needs are K_eff = sum over words of the largest
  *             count of that word in any sequence; kmer_rank_plan() returns the
- *             exact figure. depth <= 0 means 1.
+ *             exact figure. depth <= 0 gives the fixed part only (no plane
+ *             columns), which is what kmer_rank_plan() needs.
  * Returns 0 for arguments outside the supported range.
  */
 size_t sad_workspace_bytes(int32_t op, int32_t n_seq, int32_t k, int32_t alphabet,
@@ -81,7 +84,10 @@ size_t sad_workspace_bytes(int32_t op, int32_t n_seq, int32_t k, int32_t alphabe
  *              < alphabet (SAD_ERR_BAD_INPUT otherwise).
  *   d_offsets  int64 [n_seq + 1], sequence x is d_codes[off[x] .. off[x+1]);
  *              non-decreasing, off[0] >= 0. Every length must be >= k.
- *   k          1..16; alphabet 2..256; eps = alphabet^k <= 65536.
+ *   k          1..8; alphabet 2..256; eps = alphabet^k <= 65536; every
+ *              L - k + 1 must be <= 65535 (SAD_ERR_UNSUPPORTED otherwise).
+ *   Malformed offsets (negative, decreasing, past off[n_seq]) are reported as
+ *   SAD_ERR_INVALID_ARGUMENT and no code byte outside [off[0], off[n_seq]) is read.
  *   d_counts   int32 [n_seq][eps] output; word index
  *              tau = sum_r a_r * alphabet^(k-1-r) (first letter most significant).
  *   d_ws       workspace of sad_workspace_bytes(SAD_OP_COUNT, ...) bytes.
@@ -160,6 +166,20 @@ int sad_status_read(void *d_ws, int32_t clear, void *stream);
 
 /* Number of kernels this library has launched in this process. */
 uint64_t sad_launch_count(void);
+
+/*
+ * Diagnostics.
+ * sad_rank_info - SYNCHRONOUS: after kmer_rank on `stream`, copies the plan the
+ *   device chose into info[0..6]: {status, K_eff, K_pad, t_max, tiles,
+ *   executed K chunks (sum over tiles of K extent / 128), reserved}.
+ * sad_profile - enable != 0 starts recording a CUDA event pair around every
+ *   launch of the plane GEMM kernel (on its own stream); 0 stops.
+ * sad_profile_read - SYNCHRONOUS: waits for the recorded events, returns the
+ *   summed GEMM time in milliseconds and the number of launches, and clears them.
+ */
+int sad_rank_info(void *d_ws, int64_t *info, void *stream);
+int sad_profile(int32_t enable);
+int sad_profile_read(double *gemm_ms, int64_t *gemm_launches);
 
 #ifdef __cplusplus
 }

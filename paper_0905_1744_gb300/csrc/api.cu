@@ -2,6 +2,8 @@
 // workspace layout, launch sequencing, device status readback.
 #include <atomic>
 #include <cstring>
+#include <mutex>
+#include <vector>
 
 #include "rank.cuh"
 
@@ -57,6 +59,45 @@ int check_cuda(cudaError_t e) {
 }  // namespace
 
 void note_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+namespace {
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<cudaEvent_t> g_prof_pool;                       // reusable events
+std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_prof_open;  // recorded pairs
+cudaEvent_t g_prof_pending = nullptr;
+
+cudaEvent_t prof_event() {
+  if (!g_prof_pool.empty()) {
+    cudaEvent_t e = g_prof_pool.back();
+    g_prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+}  // namespace
+
+void prof_begin(cudaStream_t st) {
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  if (!g_prof_on) return;
+  g_prof_pending = prof_event();
+  if (g_prof_pending) cudaEventRecord(g_prof_pending, st);
+}
+
+void prof_end(cudaStream_t st) {
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  if (!g_prof_on || !g_prof_pending) return;
+  cudaEvent_t e = prof_event();
+  if (!e) return;
+  cudaEventRecord(e, st);
+  g_prof_open.emplace_back(g_prof_pending, e);
+  g_prof_pending = nullptr;
+}
 
 int num_sms() {
   static int cached[64] = {0};
@@ -198,6 +239,52 @@ int partition(const uint64_t *d_key_hi, const uint64_t *d_key_lo, int32_t n_seq,
   if (ws_bytes < part_layout(n_seq, p).bytes) return SAD_ERR_WORKSPACE;
   return partition_launch(d_key_hi, d_key_lo, n_seq, p, d_bucket_offsets, d_members,
                           d_pivot_idx, d_ws, st);
+}
+
+int sad_rank_info(void *d_ws, int64_t *info, void *stream) {
+  if (!d_ws || !info) return SAD_ERR_INVALID_ARGUMENT;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  WsHeader h;
+  int rc = check_cuda(cudaMemcpyAsync(&h, d_ws, sizeof(h), cudaMemcpyDeviceToHost, st));
+  if (rc) return rc;
+  rc = check_cuda(cudaStreamSynchronize(st));
+  if (rc) return rc;
+  info[0] = h.status;
+  info[1] = h.k_eff;
+  info[2] = h.k_pad;
+  info[3] = h.t_max;
+  info[4] = h.n_tiles;
+  info[5] = (int64_t)h.k_chunks;
+  info[6] = 0;
+  return SAD_OK;
+}
+
+int sad_profile(int32_t enable) {
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  g_prof_on = enable != 0;
+  return SAD_OK;
+}
+
+int sad_profile_read(double *gemm_ms, int64_t *gemm_launches) {
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  double total = 0.0;
+  int64_t count = 0;
+  for (auto &pr : g_prof_open) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(pr.second) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) {
+      total += ms;
+      ++count;
+    } else {
+      cudaGetLastError();
+    }
+    g_prof_pool.push_back(pr.first);
+    g_prof_pool.push_back(pr.second);
+  }
+  g_prof_open.clear();
+  if (gemm_ms) *gemm_ms = total;
+  if (gemm_launches) *gemm_launches = count;
+  return SAD_OK;
 }
 
 int sad_status_read(void *d_ws, int32_t clear, void *stream) {

@@ -333,8 +333,10 @@ int rank_gemm_launch(const RankPtrs &P, int32_t n, cudaStream_t st) {
     attr_set = true;
   }
   const int64_t grid = tiles < num_sms() ? tiles : num_sms();
+  prof_begin(st);
   plane_gemm_kernel<<<(unsigned)grid, kThreads, kGemmSmemBytes, st>>>(mA, mB, P, n);
   SAD_LAUNCH_CHECK();
+  prof_end(st);
   return SAD_OK;
 }
 

@@ -69,6 +69,7 @@ __global__ void rank_init_kernel(RankPtrs P, int32_t n, int32_t eps, int with_ke
     P.hdr->k_pad = 0;
     P.hdr->t_max = 0;
     P.hdr->n_tiles = 0;
+    P.hdr->k_chunks = 0;
   }
 }
 
@@ -440,14 +441,18 @@ __global__ void __launch_bounds__(1024) tiles_kernel(RankPtrs P, int32_t n) {
     const int32_t incl = x + ((tid >> 5) > 0 ? s_warp[(tid >> 5) - 1] : 0) + s_carry;
     int32_t out = incl - cnt;
     const int32_t dI = P.depth[I];
+    unsigned long long chunks = 0;
     for (int32_t J = j0; J < j1; ++J) {
       const int32_t b0 = 2 * J, b1 = 2 * J + 1;
       int32_t dJ = P.depth[b0];
       if (b1 < nblk) dJ = max(dJ, P.depth[b1]);
       const int32_t d = min(dI, dJ);
       const int32_t kend = P.secend[min(d, P.hdr->t_max)];
-      P.tiles[out++] = make_int2(I | (J << 16), (kend + kKChunk - 1) / kKChunk);
+      const int32_t nk = max(1, (kend + kKChunk - 1) / kKChunk);
+      P.tiles[out++] = make_int2(I | (J << 16), nk);
+      chunks += (unsigned long long)nk;
     }
+    if (chunks) atomicAdd(&P.hdr->k_chunks, chunks);
     __syncthreads();
     if (tid == blockDim.x - 1) s_carry = incl;
     __syncthreads();

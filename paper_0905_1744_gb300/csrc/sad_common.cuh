@@ -33,7 +33,8 @@ struct WsHeader {
   int32_t t_max;         // largest count of any word in any sequence
   int32_t n_tiles;       // GEMM tiles scheduled
   int32_t n_valid_blocks;
-  int32_t pad[56];
+  unsigned long long k_chunks;  // sum over tiles of their K chunks (executed MMA work)
+  int32_t pad[54];
 };
 static_assert(sizeof(WsHeader) == 256, "header is 256 bytes");
 
@@ -115,6 +116,9 @@ inline PartLayout part_layout(int64_t n, int64_t p) {
 // ------------------------------------------------------ host bookkeeping ----
 void note_launch(int n = 1);
 int num_sms();
+// GEMM timing hooks (no-ops unless sad_profile(1) was called)
+void prof_begin(cudaStream_t st);
+void prof_end(cudaStream_t st);
 
 #define SAD_LAUNCH_CHECK()                                   \
   do {                                                       \

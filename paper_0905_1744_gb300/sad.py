@@ -61,6 +61,12 @@ def _load():
         lib.partition.restype = ctypes.c_int
         lib.sad_status_read.argtypes = [P, i32, P]
         lib.sad_status_read.restype = ctypes.c_int
+        lib.sad_rank_info.argtypes = [P, ctypes.POINTER(i64), P]
+        lib.sad_rank_info.restype = ctypes.c_int
+        lib.sad_profile.argtypes = [i32]
+        lib.sad_profile.restype = ctypes.c_int
+        lib.sad_profile_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
+        lib.sad_profile_read.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -210,3 +216,22 @@ def partition_set(codes: torch.Tensor, offsets: torch.Tensor, p: int, k: int = 3
     offs, mem, piv = partition(hi, lo, p, ws=ws, stream=stream)
     return dict(counts=counts, key_hi=hi, key_lo=lo, rank=rank, bucket_offsets=offs,
                 members=mem, pivot_idx=piv)
+
+
+def rank_info(ws: Workspace, stream=None) -> dict:
+    """Plan the device chose in the last kmer_rank on this workspace (synchronous)."""
+    info = (ctypes.c_int64 * 8)()
+    _check(_load().sad_rank_info(_ptr(ws.buf), info, _stream(stream)), "sad_rank_info")
+    keys = ("status", "k_eff", "k_pad", "t_max", "tiles", "k_chunks")
+    return {k: int(info[i]) for i, k in enumerate(keys)}
+
+
+def profile(enable: bool):
+    _check(_load().sad_profile(1 if enable else 0), "sad_profile")
+
+
+def profile_read():
+    """(summed plane-GEMM milliseconds, launches) since the last read (synchronous)."""
+    ms, n = ctypes.c_double(0.0), ctypes.c_int64(0)
+    _check(_load().sad_profile_read(ctypes.byref(ms), ctypes.byref(n)), "sad_profile_read")
+    return float(ms.value), int(n.value)
