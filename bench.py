@@ -155,7 +155,13 @@ class ClockSampler:
 
 # --------------------------------------------------------------- CPU oracle ---
 
-def oracle_sample(s, seconds: float, seed: int = 0):
+def oracle_counts(s):
+    import oracle
+    oracle.build()
+    return oracle.kmer_count(s.codes, s.offsets)
+
+
+def oracle_sample(s, seconds: float, seed: int = 0, counts=None):
     """Time the oracle's rank on a row sample sized to ~`seconds` of CPU work.
 
     Returns (pairs_per_s, rows, elapsed, threads). The oracle computes each
@@ -165,7 +171,8 @@ def oracle_sample(s, seconds: float, seed: int = 0):
     import oracle
     oracle.build()
     threads = oracle.default_threads()
-    counts = oracle.kmer_count(s.codes, s.offsets)
+    if counts is None:
+        counts = oracle.kmer_count(s.codes, s.offsets)
     rng = np.random.default_rng(seed)
     r0 = max(threads, 8)
     rows = rng.choice(s.n, size=min(r0, s.n), replace=False)
@@ -186,10 +193,11 @@ def run_reference(args):
     if rank != 0:
         return
     s = datagen.config(args.config, args.seed)
-    per_step = max(1.0, 150.0 / max(1, args.steps + args.warmup))
+    per_step = max(0.5, 120.0 / max(1, args.steps + args.warmup))
+    counts = oracle_counts(s)
     vals, rows_used, threads = [], 0, 1
     for i in range(args.warmup + args.steps):
-        v, r, t, threads = oracle_sample(s, per_step, seed=args.seed + i)
+        v, r, t, threads = oracle_sample(s, per_step, seed=args.seed + i, counts=counts)
         if i >= args.warmup:
             vals.append(v)
             rows_used = r
