@@ -157,6 +157,26 @@ int partition(const uint64_t *d_key_hi, const uint64_t *d_key_lo, int32_t n_seq,
               int32_t *d_pivot_idx, void *d_ws, size_t ws_bytes, void *stream);
 
 /*
+ * partition_noalloc - the same partition as partition(), for callers that
+ * cannot allocate device memory (an arena or pool that owns every device byte,
+ * a host application that forbids allocation after start-up, a hot path that
+ * must not touch the allocator). The paper has no counterpart: this is an
+ * interface convenience of this library.
+ *   Its scratch is a fixed 2 MiB array inside the library's device image, held
+ *   by every GPU that loads the library until the process exits. Limits:
+ *   n_seq <= 32768 and p <= 64; larger calls return SAD_ERR_UNSUPPORTED and
+ *   launch nothing. Other arguments and outputs are those of partition().
+ *   The first call on a device looks up the array's device address (with that
+ *   device current); make that first call before any stream capture.
+ *   All calls share the one array and it keeps the last call's contents; the
+ *   call clears what must start at zero. Calls whose GPU work overlaps race on
+ *   the array: keep them ordered on one stream.
+ */
+int partition_noalloc(const uint64_t *d_key_hi, const uint64_t *d_key_lo, int32_t n_seq,
+                      int32_t p, int32_t *d_bucket_offsets, int32_t *d_members,
+                      int32_t *d_pivot_idx, void *stream);
+
+/*
  * sad_status_read - SYNCHRONOUS: waits for `stream`, then returns the status
  * recorded in the workspace by the device (SAD_OK if none). With clear != 0 the
  * recorded status is reset to SAD_OK. d_ws must be a workspace previously passed

@@ -61,6 +61,8 @@ def _load():
         lib.partition.restype = ctypes.c_int
         lib.sad_status_read.argtypes = [P, i32, P]
         lib.sad_status_read.restype = ctypes.c_int
+        lib.partition_noalloc.argtypes = [P, P, i32, i32, P, P, P, P]
+        lib.partition_noalloc.restype = ctypes.c_int
         lib.sad_rank_info.argtypes = [P, ctypes.POINTER(i64), P]
         lib.sad_rank_info.restype = ctypes.c_int
         lib.sad_profile.argtypes = [i32]
@@ -235,3 +237,26 @@ def profile_read():
     ms, n = ctypes.c_double(0.0), ctypes.c_int64(0)
     _check(_load().sad_profile_read(ctypes.byref(ms), ctypes.byref(n)), "sad_profile_read")
     return float(ms.value), int(n.value)
+
+
+NOALLOC_MAX_N, NOALLOC_MAX_P = 32768, 64
+
+
+def partition_noalloc(key_hi: torch.Tensor, key_lo: torch.Tensor, p: int, stream=None,
+                      out=None):
+    """partition() without a workspace, for callers that cannot allocate device
+    memory: the library keeps a fixed 2 MiB scratch array per device, so the call
+    allocates nothing beyond the outputs (which the caller may pass in ``out``).
+    Limits: N <= 32768, p <= 64. Calls sharing a device must not overlap."""
+    n = key_hi.numel()
+    dev = key_hi.device
+    if out is None:
+        offs = torch.empty(p + 1, dtype=torch.int32, device=dev)
+        mem = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        piv = torch.empty(max(p - 1, 1), dtype=torch.int32, device=dev)
+    else:
+        offs, mem, piv = out
+    _check(_load().partition_noalloc(_ptr(key_hi), _ptr(key_lo), n, p, _ptr(offs), _ptr(mem),
+                                     _ptr(piv) if p > 1 else None, _stream(stream)),
+           "partition_noalloc")
+    return offs, mem[:n], piv[:max(p - 1, 0)]
