@@ -253,36 +253,42 @@ __global__ void __launch_bounds__(1024) colmap_kernel(RankPtrs P, int32_t eps, i
 }
 
 // Exclusive prefix over m in decreasing order: mhist[m] := #{x : m_x > m}.
+// Thread t owns the 64 values m = kMaxM - 64 t, ..., kMaxM - 64 t - 63 (high to
+// low); one block scan of the 1024 chunk totals gives each chunk's start.
 __global__ void __launch_bounds__(1024) lensort_scan_kernel(RankPtrs P) {
   __shared__ int32_t s_warp[32];
-  __shared__ int32_t s_carry;
+  constexpr int kPer = (kMaxM + 1023) / 1024;  // 64
   const int tid = threadIdx.x;
-  if (tid == 0) s_carry = 0;
+  const int top = kMaxM - kPer * tid;          // first (largest) m of this chunk
+  int32_t total = 0;
+  for (int i = 0; i < kPer; ++i) {
+    const int m = top - i;
+    if (m >= 1) total += P.mhist[m];
+  }
+  int32_t x = total;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if ((tid & 31) >= o) x += y;
+  }
+  if ((tid & 31) == 31) s_warp[tid >> 5] = x;
   __syncthreads();
-  for (int base = kMaxM; base >= 1; base -= blockDim.x) {
-    const int m = base - tid;
-    const int32_t v = m >= 1 ? P.mhist[m] : 0;
-    int32_t x = v;
+  if (tid < 32) {
+    int32_t w = s_warp[tid];
     for (int o = 1; o < 32; o <<= 1) {
-      int32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if ((tid & 31) >= o) x += y;
+      const int32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (tid >= o) w += y;
     }
-    if ((tid & 31) == 31) s_warp[tid >> 5] = x;
-    __syncthreads();
-    if (tid < 32) {
-      int32_t w = s_warp[tid];
-      for (int o = 1; o < 32; o <<= 1) {
-        int32_t y = __shfl_up_sync(0xffffffffu, w, o);
-        if (tid >= o) w += y;
-      }
-      s_warp[tid] = w;
+    s_warp[tid] = w;
+  }
+  __syncthreads();
+  int32_t run = x - total + ((tid >> 5) > 0 ? s_warp[(tid >> 5) - 1] : 0);
+  for (int i = 0; i < kPer; ++i) {
+    const int m = top - i;
+    if (m >= 1) {
+      const int32_t v = P.mhist[m];
+      P.mhist[m] = run;
+      run += v;
     }
-    __syncthreads();
-    const int32_t incl = x + ((tid >> 5) > 0 ? s_warp[(tid >> 5) - 1] : 0) + s_carry;
-    __syncthreads();
-    if (m >= 1) P.mhist[m] = incl - v;
-    if (tid == blockDim.x - 1) s_carry = incl;
-    __syncthreads();
   }
 }
 
@@ -320,55 +326,106 @@ __global__ void lensort_place_kernel(const int32_t *__restrict__ lengths, int32_
   }
 }
 
-// One block per stored row: stage the row's counts (as 16-bit) in shared memory,
-// write the K_pad plane bytes of the row (16 per thread per step), and raise
-// the depth of its 128-row block to the row's largest count.
+// Plane rows, kPlaneRows stored rows per block iteration: stage the rows' counts
+// (as 16-bit) in shared memory with 16-byte loads, write their K_pad plane bytes
+// 16 at a time (the column map of a chunk is read once for all the rows), raise
+// the depth of each row's 128-row block to the row's largest count, and check
+// that the row's counts add up to its number of windows m.
+constexpr int kPlaneRows = 2;
+
 __global__ void __launch_bounds__(256) planes_kernel(const int32_t *__restrict__ counts,
                                                      int32_t n, int32_t eps, RankPtrs P) {
-  extern __shared__ uint16_t s_cnt[];
-  __shared__ int32_t s_max, s_sum;
+  extern __shared__ uint16_t s_cnt[];  // [kPlaneRows][eps]
+  __shared__ int32_t s_max[kPlaneRows], s_sum[kPlaneRows];
   if (P.hdr->status != 0) return;
   const int32_t k_eff = (int32_t)P.hdr->k_eff;
   const int32_t k_pad = P.hdr->k_pad;
-  for (int64_t pos = blockIdx.x; pos < P.n_pad; pos += gridDim.x) {
-    const int32_t x = P.perm[pos];
-    uint4 *dst = reinterpret_cast<uint4 *>(P.planes + pos * P.k_cap);
-    if (x < 0) {
-      for (int c = threadIdx.x; c < k_pad / 16; c += blockDim.x) dst[c] = make_uint4(0, 0, 0, 0);
-      continue;
+  const bool vec = (eps & 3) == 0 && (reinterpret_cast<uintptr_t>(counts) & 15) == 0;
+  const int64_t groups = P.n_pad / kPlaneRows;
+  for (int64_t g = blockIdx.x; g < groups; g += gridDim.x) {
+    int32_t xs[kPlaneRows];
+#pragma unroll
+    for (int r = 0; r < kPlaneRows; ++r) xs[r] = P.perm[g * kPlaneRows + r];
+    if (threadIdx.x < kPlaneRows) {
+      s_max[threadIdx.x] = 0;
+      s_sum[threadIdx.x] = 0;
     }
-    if (threadIdx.x == 0) s_max = 0;
-    if (threadIdx.x == 0) s_sum = 0;
-    const int32_t *row = counts + (int64_t)x * eps;
-    int32_t mx = 0, sum = 0;
-    for (int t = threadIdx.x; t < eps; t += blockDim.x) {
-      const int32_t c = __ldg(row + t);
-      s_cnt[t] = (uint16_t)min(max(c, 0), 0xFFFF);
-      mx = max(mx, c);
-      sum += c;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      sum += __shfl_xor_sync(0xffffffffu, sum, o);
+#pragma unroll
+    for (int r = 0; r < kPlaneRows; ++r) {
+      uint16_t *sc = s_cnt + r * eps;
+      int32_t mx = 0, sum = 0;
+      if (xs[r] >= 0) {
+        const int32_t *row = counts + (int64_t)xs[r] * eps;
+        if (vec) {
+          const int4 *row4 = reinterpret_cast<const int4 *>(row);
+          const int q4 = eps >> 2;
+          int q = threadIdx.x;
+          for (; q + 3 * 256 < q4; q += 4 * 256) {
+            int4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = __ldg(row4 + q + u * 256);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int32_t c[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+              for (int b = 0; b < 4; ++b) {
+                sc[4 * (q + u * 256) + b] = (uint16_t)min(max(c[b], 0), 0xFFFF);
+                mx = max(mx, c[b]);
+                sum += c[b];
+              }
+            }
+          }
+          for (; q < q4; q += 256) {
+            const int4 v = __ldg(row4 + q);
+            const int32_t c[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+              sc[4 * q + b] = (uint16_t)min(max(c[b], 0), 0xFFFF);
+              mx = max(mx, c[b]);
+              sum += c[b];
+            }
+          }
+        } else {
+          for (int t = threadIdx.x; t < eps; t += blockDim.x) {
+            const int32_t c = __ldg(row + t);
+            sc[t] = (uint16_t)min(max(c, 0), 0xFFFF);
+            mx = max(mx, c);
+            sum += c;
+          }
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        sum += __shfl_xor_sync(0xffffffffu, sum, o);
+      }
+      __syncthreads();  // s_max/s_sum reset visible (first row); s_cnt complete below
+      if ((threadIdx.x & 31) == 0) {
+        atomicMax(&s_max[r], mx);
+        atomicAdd(&s_sum[r], sum);
+      }
     }
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) {
-      atomicMax(&s_max, mx);
-      atomicAdd(&s_sum, sum);
-    }
+    uint4 *dst[kPlaneRows];
+#pragma unroll
+    for (int r = 0; r < kPlaneRows; ++r)
+      dst[r] = reinterpret_cast<uint4 *>(P.planes + (g * kPlaneRows + r) * P.k_cap);
     for (int c = threadIdx.x; c < k_pad / 16; c += blockDim.x) {
-      uint32_t w[4] = {0, 0, 0, 0};
+      uint32_t w[kPlaneRows][4] = {};
       const int32_t c0 = c * 16;
       if (c0 + 16 <= k_eff) {
         const int4 *cm = reinterpret_cast<const int4 *>(P.colmap + c0);
+        int4 e4[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) e4[q] = __ldg(cm + q);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const int4 e = __ldg(cm + q);
-          const int32_t ev[4] = {e.x, e.y, e.z, e.w};
+          const int32_t ev[4] = {e4[q].x, e4[q].y, e4[q].z, e4[q].w};
 #pragma unroll
           for (int b = 0; b < 4; ++b) {
             const uint32_t tau = (uint32_t)ev[b] & 0xFFFFu, t = (uint32_t)ev[b] >> 16;
-            if ((uint32_t)s_cnt[tau] >= t) w[q] |= 0x38u << (8 * b);
+#pragma unroll
+            for (int r = 0; r < kPlaneRows; ++r)
+              if ((uint32_t)s_cnt[r * eps + tau] >= t) w[r][q] |= 0x38u << (8 * b);
           }
         }
       } else {
@@ -376,17 +433,23 @@ __global__ void __launch_bounds__(256) planes_kernel(const int32_t *__restrict__
           if (c0 + b < k_eff) {
             const int32_t e = __ldg(P.colmap + c0 + b);
             const uint32_t tau = (uint32_t)e & 0xFFFFu, t = (uint32_t)e >> 16;
-            if ((uint32_t)s_cnt[tau] >= t) w[b >> 2] |= 0x38u << (8 * (b & 3));
+#pragma unroll
+            for (int r = 0; r < kPlaneRows; ++r)
+              if ((uint32_t)s_cnt[r * eps + tau] >= t) w[r][b >> 2] |= 0x38u << (8 * (b & 3));
           }
         }
       }
-      dst[c] = make_uint4(w[0], w[1], w[2], w[3]);
+#pragma unroll
+      for (int r = 0; r < kPlaneRows; ++r)
+        dst[r][c] = xs[r] >= 0 ? make_uint4(w[r][0], w[r][1], w[r][2], w[r][3])
+                               : make_uint4(0, 0, 0, 0);
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      atomicMax(&P.depth[pos / kRowBlock], s_max);
+    if (threadIdx.x < kPlaneRows && xs[threadIdx.x] >= 0) {
+      const int64_t pos = g * kPlaneRows + threadIdx.x;
+      atomicMax(&P.depth[pos / kRowBlock], s_max[threadIdx.x]);
       // the counts of a row must add up to its number of windows, m
-      if (s_sum != (int32_t)(P.rec[pos].w & 0xFFFFu)) record_error(P.hdr, SAD_ERR_BAD_INPUT, x);
+      if (s_sum[threadIdx.x] != (int32_t)(P.rec[pos].w & 0xFFFFu))
+        record_error(P.hdr, SAD_ERR_BAD_INPUT, xs[threadIdx.x]);
     }
     __syncthreads();
   }
@@ -514,12 +577,13 @@ int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *le
   lensort_place_kernel<<<grid_for(P.n_pad, 256), 256, 0, st>>>(lengths, n, k, P);
   SAD_LAUNCH_CHECK();
   {
-    const size_t smem = sizeof(uint16_t) * (size_t)eps;
+    const size_t smem = sizeof(uint16_t) * (size_t)eps * kPlaneRows;
     if (cudaFuncSetAttribute(planes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
       return SAD_ERR_CUDA;
-    unsigned g = (unsigned)(P.n_pad < (int64_t)num_sms() * 16 ? P.n_pad : (int64_t)num_sms() * 16);
-    planes_kernel<<<g, 256, smem, st>>>(counts, n, eps, P);
+    const int64_t groups = P.n_pad / kPlaneRows;
+    const int64_t cap = (int64_t)num_sms() * 8;
+    planes_kernel<<<(unsigned)(groups < cap ? groups : cap), 256, smem, st>>>(counts, n, eps, P);
     SAD_LAUNCH_CHECK();
   }
   tiles_kernel<<<1, 1024, 0, st>>>(P, n);
