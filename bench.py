@@ -57,6 +57,8 @@ def parse():
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--depth", type=int, default=None,
+                    help="threshold-plane depth (default: the autotuner's choice)")
     return ap.parse_args()
 
 
@@ -242,7 +244,7 @@ def run_sad(args):
     import torch
     import torch.distributed as dist
 
-    from paper_0905_1744_gb300 import sad
+    from paper_0905_1744_gb300 import autotune, sad
 
     rank, world, local = dist_env()
     if world > 1:
@@ -261,8 +263,13 @@ def run_sad(args):
     ws = sad.Workspace(dev)
     counts = torch.empty((n, 8000), dtype=torch.int32, device=dev)
     sad.kmer_count(codes, offsets, ws=ws, out=counts)
-    k_eff, need = sad.kmer_rank_plan(counts, ws=ws)
-    ws.ensure(max(need, sad.workspace_bytes(sad.OP_PARTITION, n, p=p)))
+    # plane depth chosen by the autotuner (timed trials, outside the timed region)
+    if args.depth is None:
+        depth, trials = autotune.choose_depth(counts, lengths, ws, use_cache=False)
+    else:
+        depth, trials = args.depth, {}
+    plan = sad.kmer_rank_plan(counts, depth=depth, ws=ws)
+    ws.ensure(plan.ws_bytes)
     keys = (torch.empty(n, dtype=torch.uint64, device=dev),
             torch.empty(n, dtype=torch.uint64, device=dev),
             torch.empty(n, dtype=torch.float64, device=dev))
@@ -273,7 +280,7 @@ def run_sad(args):
 
     def step():
         sad.kmer_count(codes, offsets, ws=ws, out=counts, check=False)
-        sad.kmer_rank(counts, lengths, ws=ws, out=keys, check=False, plan=False)
+        sad.kmer_rank(counts, lengths, ws=ws, out=keys, check=False, plan=plan)
         sad.partition(keys[0], keys[1], p, ws=ws_part, out=part, check=False)
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # 2x the 129 MB L2
@@ -333,7 +340,8 @@ def run_sad(args):
         "traffic": gemm_traffic_per_launch(n, info["k_eff"]),
         "gemm_ms_per_launch": gemm_launch_ms, "gemm_share_of_step": gemm_launch_ms / ms_per_step,
         "k_eff": info["k_eff"], "k_pad": info["k_pad"], "t_max": info["t_max"],
-        "tiles": info["tiles"],
+        "tiles": info["tiles"], "depth": info["depth"],
+        "residual_pairs": info["residual_pairs"], "residual_tiles": info["residual_tiles"],
         "executed_tflops": exec_flops / (gemm_launch_ms / 1e3) / 1e12,
         "executed_frac": exec_flops / (gemm_launch_ms / 1e3) / 1e12 / fp8_peak,
         "useful_frac": useful_flops / (gemm_launch_ms / 1e3) / 1e12 / fp8_peak,
@@ -353,7 +361,7 @@ def run_sad(args):
         def e2e_step():
             d_codes = h_codes.to(dev, non_blocking=True)
             d_offs = h_offs.to(dev, non_blocking=True)
-            res = sad.partition_set(d_codes, d_offs, p, ws=ws_e)
+            res = sad.partition_set(d_codes, d_offs, p, ws=ws_e, depth=depth)
             h_mem.copy_(res["members"], non_blocking=True)
             h_boff.copy_(res["bucket_offsets"], non_blocking=True)
             h_hi.copy_(res["key_hi"], non_blocking=True)
@@ -398,6 +406,7 @@ def run_sad(args):
                        "l2": "flushed between steps (256 MB write)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "gpu_launches": int(launches),
+            "autotune": {"depth": depth, "trial_ms": {str(d): t for d, t in trials.items()}},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -34,7 +34,7 @@
 extern "C" {
 #endif
 
-#define SAD_ABI_VERSION 1
+#define SAD_ABI_VERSION 2
 
 typedef enum sad_status {
   SAD_OK = 0,
@@ -66,11 +66,11 @@ int sad_abi_version(void);
  *   k, alphabet  word length and alphabet size (eps = alphabet^k words).
  *   p         number of buckets (SAD_OP_PARTITION only).
  *   depth     SAD_OP_RANK only: the threshold-plane columns to reserve, as a
- *             multiple of eps (K_cap = eps * depth rounded up to 128). The
- *             columns kmer_rank needs are K_eff = sum over words of the largest
- *             count of that word in any sequence; kmer_rank_plan() returns the
- *             exact figure. depth <= 0 gives the fixed part only (no plane
- *             columns), which is what kmer_rank_plan() needs.
+ *             multiple of eps (K_cap = eps * depth rounded up to 128), with no
+ *             residual capacity: enough for kmer_rank without a plan when
+ *             K_eff = sum over words of the largest count <= K_cap.
+ *             kmer_rank_plan() gives exact sizes for any depth. depth <= 0 gives
+ *             the fixed part only, which is what kmer_rank_plan() needs.
  * Returns 0 for arguments outside the supported range.
  */
 size_t sad_workspace_bytes(int32_t op, int32_t n_seq, int32_t k, int32_t alphabet,
@@ -97,18 +97,44 @@ int kmer_count(const uint8_t *d_codes, const int64_t *d_offsets, int32_t n_seq,
                size_t ws_bytes, void *stream);
 
 /*
- * kmer_rank_plan - SYNCHRONOUS helper: computes on the device the number of
- * threshold-plane columns K_eff the counts need and the workspace kmer_rank will
- * then require. Blocks until `stream` is idle.
+ * Plan of a kmer_rank call. `depth` is chosen by the caller (an autotuner, or 0);
+ * kmer_rank_plan fills in the rest from the counts.
+ *   depth        threshold planes kept per word on the tensor cores; 0 keeps
+ *                them all. With depth D >= 1 the pairs that share a word more
+ *                than D times each get the exact remainder
+ *                sum_word max(0, min(c_x, c_y) - D) from a sparse residual step,
+ *                so the keys are identical for every depth.
+ *   t_max        largest count of any word in any sequence.
+ *   k_eff        threshold-plane columns at this depth.
+ *   list_entries (sequence, word) entries with a count above depth.
+ *   residual_pairs  pair contributions the residual step adds.
+ *   k_cap, list_cap, block_cap  capacities kmer_rank lays the workspace out
+ *                with (plane columns, residual entries, residual 128 x 256
+ *                tiles); kmer_rank_plan sets them to what the data needs.
+ *   ws_bytes     workspace bytes kmer_rank needs with this plan.
+ */
+typedef struct sad_rank_plan {
+  int32_t depth;
+  int32_t t_max;
+  int64_t k_eff;
+  int64_t list_entries;
+  int64_t residual_pairs;
+  int64_t k_cap;
+  int64_t list_cap;
+  int64_t block_cap;
+  size_t ws_bytes;
+} sad_rank_plan;
+
+/*
+ * kmer_rank_plan - SYNCHRONOUS helper: reads the counts on the device and fills
+ * `plan` (plan->depth is the input) with the sizes kmer_rank will need. Blocks
+ * until `stream` is idle.
  *   d_counts   int32 [n_seq][eps], as written by kmer_count.
  *   d_ws       a workspace of at least sad_workspace_bytes(SAD_OP_RANK, n_seq,
- *              k, alphabet, 0, 0) bytes (the fixed part; planes not needed).
- *   k_eff_out  (nullable) receives K_eff.
- *   ws_needed  (nullable) receives the workspace bytes kmer_rank needs.
+ *              k, alphabet, 0, 0) bytes (the fixed part).
  */
 int kmer_rank_plan(const int32_t *d_counts, int32_t n_seq, int32_t k, int32_t alphabet,
-                   void *d_ws, size_t ws_bytes, int64_t *k_eff_out, size_t *ws_needed,
-                   void *stream);
+                   sad_rank_plan *plan, void *d_ws, size_t ws_bytes, void *stream);
 
 /*
  * kmer_rank - the k-mer rank of every sequence against the whole set.
@@ -122,18 +148,23 @@ int kmer_rank_plan(const int32_t *d_counts, int32_t n_seq, int32_t k, int32_t al
  *     rank_i = (key_hi + key_lo * 2^-64) / N   (each step rounded to nearest).
  * Internally min(a, b) = sum_t [a >= t][b >= t] turns all pairs into one
  * threshold-plane GEMM on the tensor cores; the N x N matrix is never stored.
- *   d_counts   int32 [n_seq][eps] from kmer_count.
+ *   d_counts   int32 [n_seq][eps] from kmer_count (16-byte aligned for the
+ *              vector path).
  *   d_lengths  int32 [n_seq] sequence lengths L (residues); every
- *              L - k + 1 must be in 1..65535 (SAD_ERR_UNSUPPORTED otherwise).
+ *              L - k + 1 must be in 1..65535 (SAD_ERR_UNSUPPORTED otherwise)
+ *              and equal to the sum of the sequence's counts (SAD_ERR_BAD_INPUT).
+ *   plan       (nullable) a plan from kmer_rank_plan for these counts; NULL keeps
+ *              all planes and takes the plane capacity from ws_bytes.
  *   d_key_hi, d_key_lo  uint64 [n_seq] outputs.
  *   d_rank     (nullable) float64 [n_seq] output.
- *   d_ws       workspace; its size sets the plane capacity K_cap (see
- *              sad_workspace_bytes / kmer_rank_plan). If K_eff > K_cap the call
- *              records SAD_ERR_WORKSPACE and writes no keys.
+ *   d_ws       workspace of at least plan->ws_bytes (or, without a plan,
+ *              sad_workspace_bytes(SAD_OP_RANK, ..., depth) with
+ *              depth * eps >= K_eff). Data that need more than the capacities
+ *              record SAD_ERR_WORKSPACE and write no keys.
  */
 int kmer_rank(const int32_t *d_counts, const int32_t *d_lengths, int32_t n_seq,
-              int32_t k, int32_t alphabet, uint64_t *d_key_hi, uint64_t *d_key_lo,
-              double *d_rank, void *d_ws, size_t ws_bytes, void *stream);
+              int32_t k, int32_t alphabet, const sad_rank_plan *plan, uint64_t *d_key_hi,
+              uint64_t *d_key_lo, double *d_rank, void *d_ws, size_t ws_bytes, void *stream);
 
 /*
  * partition - regular-sampling sample sort of the keys into p buckets
@@ -190,8 +221,9 @@ uint64_t sad_launch_count(void);
 /*
  * Diagnostics.
  * sad_rank_info - SYNCHRONOUS: after kmer_rank on `stream`, copies the plan the
- *   device chose into info[0..6]: {status, K_eff, K_pad, t_max, tiles,
- *   executed K chunks (sum over tiles of K extent / 128), reserved}.
+ *   device chose into info[0..8]: {status, K_eff, K_pad, t_max, tiles,
+ *   executed K chunks (sum over tiles of K extent / 128), planes kept per word,
+ *   residual pair contributions, residual tiles}.
  * sad_profile - enable != 0 starts recording a CUDA event pair around every
  *   launch of the plane GEMM kernel (on its own stream); 0 stops.
  * sad_profile_read - SYNCHRONOUS: waits for the recorded events, returns the

@@ -31,24 +31,15 @@ int64_t eps_of(int32_t k, int32_t alphabet) {
 
 bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
-// Largest K_cap (multiple of kKChunk) whose rank layout fits in ws_bytes.
+// Largest K_cap (multiple of kKChunk) whose planes-only rank layout fits in ws_bytes.
 int64_t k_cap_for(int64_t n, int64_t eps, size_t ws_bytes) {
-  const RankLayout base = rank_layout(n, eps, 0);
+  const RankLayout base = rank_layout(n, eps, RankCaps{0, 0, 0, 0});
   if (ws_bytes <= base.fixed_bytes) return 0;
-  // upper bound (the fixed part only grows with K_cap), then step down until it fits
+  // upper bound (the layout only grows with K_cap), then step down until it fits
   int64_t k = (int64_t)((ws_bytes - base.fixed_bytes) / (size_t)base.n_pad);
   k = k / kKChunk * kKChunk;
-  while (k > 0) {
-    const RankLayout L = rank_layout(n, eps, k);
-    if (L.fixed_bytes + (size_t)L.n_pad * (size_t)k <= ws_bytes) break;
-    k -= kKChunk;
-  }
+  while (k > 0 && rank_layout(n, eps, RankCaps{0, k, 0, 0}).bytes > ws_bytes) k -= kKChunk;
   return k;
-}
-
-size_t rank_bytes(int64_t n, int64_t eps, int64_t k_cap) {
-  const RankLayout L = rank_layout(n, eps, k_cap);
-  return L.fixed_bytes + (size_t)L.n_pad * (size_t)k_cap;
 }
 
 int check_cuda(cudaError_t e) {
@@ -146,10 +137,10 @@ size_t sad_workspace_bytes(int32_t op, int32_t n_seq, int32_t k, int32_t alphabe
       return eps < 0 ? 0 : sizeof(WsHeader);
     case SAD_OP_RANK: {
       if (eps < 0) return 0;
-      if (depth <= 0) return rank_layout(n_seq, eps, 0).fixed_bytes;
+      if (depth <= 0) return rank_layout(n_seq, eps, RankCaps{0, 0, 0, 0}).fixed_bytes;
       const int64_t k_cap =
           (int64_t)align_up((size_t)eps * (size_t)depth, (size_t)kKChunk);
-      return rank_bytes(n_seq, eps, k_cap);
+      return rank_layout(n_seq, eps, RankCaps{0, k_cap, 0, 0}).bytes;
     }
     case SAD_OP_PARTITION:
       if (p < 1 || p > kMaxP) return 0;
@@ -174,47 +165,64 @@ int kmer_count(const uint8_t *d_codes, const int64_t *d_offsets, int32_t n_seq, 
 }
 
 int kmer_rank_plan(const int32_t *d_counts, int32_t n_seq, int32_t k, int32_t alphabet,
-                   void *d_ws, size_t ws_bytes, int64_t *k_eff_out, size_t *ws_needed,
-                   void *stream) {
+                   sad_rank_plan *plan, void *d_ws, size_t ws_bytes, void *stream) {
   const int64_t eps = eps_of(k, alphabet);
   if (eps < 0) return SAD_ERR_UNSUPPORTED;
-  if (n_seq < 0 || !d_ws || !aligned(d_ws, 256)) return SAD_ERR_INVALID_ARGUMENT;
-  const RankLayout L0 = rank_layout(n_seq, eps, 0);
+  if (n_seq < 0 || !plan || !d_ws || !aligned(d_ws, 256) || plan->depth < 0)
+    return SAD_ERR_INVALID_ARGUMENT;
+  const RankCaps probe{plan->depth, 0, 0, 0};
+  const RankLayout L0 = rank_layout(n_seq, eps, probe);
   if (ws_bytes < L0.fixed_bytes) return SAD_ERR_WORKSPACE;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  int64_t k_eff = 0;
+  WsHeader h{};
   if (n_seq > 0) {
     if (!d_counts) return SAD_ERR_INVALID_ARGUMENT;
     const RankPtrs P = rank_ptrs(d_ws, L0);
     int rc = rank_prep_launch(P, d_counts, nullptr, n_seq, k, (int32_t)eps, 1, st);
     if (rc) return rc;
-    WsHeader h;
     rc = check_cuda(cudaMemcpyAsync(&h, d_ws, sizeof(h), cudaMemcpyDeviceToHost, st));
     if (rc) return rc;
     rc = check_cuda(cudaStreamSynchronize(st));
     if (rc) return rc;
     if (h.status != 0) return h.status;
-    k_eff = h.k_eff;
   }
-  int64_t k_pad = (int64_t)align_up((size_t)k_eff, kKChunk);
+  int64_t k_pad = (int64_t)align_up((size_t)h.k_eff, kKChunk);
   if (k_pad < kKChunk) k_pad = kKChunk;
-  if (k_eff_out) *k_eff_out = k_eff;
-  if (ws_needed) *ws_needed = rank_bytes(n_seq, eps, k_pad);
+  const bool residual = n_seq > 0 && h.depth < h.t_max;
+  const int64_t tiles = host_tile_count(n_seq);
+  plan->t_max = h.t_max;
+  plan->k_eff = h.k_eff;
+  plan->list_entries = h.list_total;
+  plan->residual_pairs = h.pairs_total;
+  plan->k_cap = k_pad;
+  plan->list_cap = residual ? h.list_total : 0;
+  plan->block_cap = residual ? (h.pairs_total < tiles ? h.pairs_total : tiles) : 0;
+  const RankCaps caps{plan->depth, plan->k_cap, plan->list_cap, plan->block_cap};
+  plan->ws_bytes = rank_layout(n_seq, eps, caps).bytes;
   return SAD_OK;
 }
 
 int kmer_rank(const int32_t *d_counts, const int32_t *d_lengths, int32_t n_seq, int32_t k,
-              int32_t alphabet, uint64_t *d_key_hi, uint64_t *d_key_lo, double *d_rank,
-              void *d_ws, size_t ws_bytes, void *stream) {
+              int32_t alphabet, const sad_rank_plan *plan, uint64_t *d_key_hi,
+              uint64_t *d_key_lo, double *d_rank, void *d_ws, size_t ws_bytes, void *stream) {
   const int64_t eps = eps_of(k, alphabet);
   if (eps < 0) return SAD_ERR_UNSUPPORTED;
   if (n_seq < 0 || !d_ws || !aligned(d_ws, 256)) return SAD_ERR_INVALID_ARGUMENT;
   if (n_seq == 0) return SAD_OK;
   if (!d_counts || !d_lengths || !d_key_hi || !d_key_lo) return SAD_ERR_INVALID_ARGUMENT;
   if ((int64_t)n_seq > (int64_t)0xFFFF * kRowBlock - kNPad) return SAD_ERR_UNSUPPORTED;
-  const int64_t k_cap = k_cap_for(n_seq, eps, ws_bytes);
-  if (k_cap < kKChunk) return SAD_ERR_WORKSPACE;
-  const RankLayout L = rank_layout(n_seq, eps, k_cap);
+  RankCaps caps{0, 0, 0, 0};
+  if (plan) {
+    if (plan->depth < 0 || plan->k_cap < kKChunk || plan->k_cap % kKChunk != 0 ||
+        plan->list_cap < 0 || plan->block_cap < 0)
+      return SAD_ERR_INVALID_ARGUMENT;
+    caps = RankCaps{plan->depth, plan->k_cap, plan->list_cap, plan->block_cap};
+    if (rank_layout(n_seq, eps, caps).bytes > ws_bytes) return SAD_ERR_WORKSPACE;
+  } else {
+    caps.k_cap = k_cap_for(n_seq, eps, ws_bytes);
+    if (caps.k_cap < kKChunk) return SAD_ERR_WORKSPACE;
+  }
+  const RankLayout L = rank_layout(n_seq, eps, caps);
   const RankPtrs P = rank_ptrs(d_ws, L);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int rc = rank_prep_launch(P, d_counts, d_lengths, n_seq, k, (int32_t)eps, 0, st);
@@ -255,7 +263,9 @@ int sad_rank_info(void *d_ws, int64_t *info, void *stream) {
   info[3] = h.t_max;
   info[4] = h.n_tiles;
   info[5] = (int64_t)h.k_chunks;
-  info[6] = 0;
+  info[6] = h.depth;
+  info[7] = h.pairs_total;
+  info[8] = h.n_blocks;
   return SAD_OK;
 }
 

@@ -15,6 +15,10 @@
 // shuffle tree, and both are added to per-sequence 64-bit limb accumulators
 // (red.global.add.u64), which a last kernel folds into the 128-bit key.
 //
+// When the planes are cut at a depth D, the residual sum_tau max(0, min(c_i, c_j) - D)
+// of each pair arrives as a dense 128 x 256 u16 block per tile and is added to S
+// before the floor, so the key is the same as with all planes.
+//
 // Persistent kernel, one CTA per SM, 8 warps:
 //   warp 0      TMA producer: 128 x 128 B tile of A (rows I) and 256 x 128 B of
 //               B (rows J) per stage, 128-byte swizzle, 4-stage mbarrier ring
@@ -122,6 +126,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem = S.tmem_base;
   const int32_t n_tiles = skip ? 0 : P.hdr->n_tiles;
+  // counts above the plane depth come in as dense per-tile residual blocks
+  const bool residual =
+      !skip && P.depth_cap >= 1 && P.block_cap > 0 && P.hdr->depth < P.hdr->t_max;
 
   if (!skip && warp == 0 && lane == 0) {
     // ------------------------------------------------------------ producer --
@@ -218,17 +225,38 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (*abort_flag) break;
       tc_fence_after();
       const bool diag = (int64_t)I * kRowBlock + kRowBlock - 1 >= (int64_t)J * kColBlock;
+      const int32_t rblk = residual ? P.block_of[t] : -1;
+      const uint4 *rrow =
+          rblk >= 0 ? reinterpret_cast<const uint4 *>(
+                          P.rblocks + (int64_t)rblk * (kResidualBlockBytes / 4) +
+                          (q * 32 + lane) * (kColBlock / 2))
+                    : nullptr;
       uint32_t R0 = 0, R1 = 0, R2 = 0;
 #pragma unroll 1
       for (int c = 0; c < kColBlock / 32; ++c) {
         uint32_t v[32];
         tmem_ld_32x32b_x32(tmem + ((q * 32u) << 16) + acc * (uint32_t)kColBlock + c * 32u, v);
+        uint32_t rw[16];
+        if (rrow) {
+#pragma unroll
+          for (int w4 = 0; w4 < 4; ++w4) {
+            const uint4 x = __ldg(rrow + c * 4 + w4);
+            rw[4 * w4 + 0] = x.x;
+            rw[4 * w4 + 1] = x.y;
+            rw[4 * w4 + 2] = x.z;
+            rw[4 * w4 + 3] = x.w;
+          }
+        } else {
+#pragma unroll
+          for (int w = 0; w < 16; ++w) rw[w] = 0;
+        }
         tmem_ld_wait();
         uint32_t cs[32], cq[32];
 #pragma unroll
         for (int cc = 0; cc < 32; ++cc) {
           const uint4 rec = S.colrec[buf][c * 32 + cc];
-          const uint32_t s = __float2uint_rn(__uint_as_float(v[cc]));
+          const uint32_t s = __float2uint_rn(__uint_as_float(v[cc])) +
+                             ((rw[cc >> 1] >> (16 * (cc & 1))) & 0xFFFFu);
           const uint32_t d = rec.w & 0xFFFFu;
           const uint32_t sh1 = (rec.w >> 16) & 0xFFu, sh2 = rec.w >> 24;
           // floor(s * 2^64 / d) = s * Q + floor(s * r / d), r = 2^64 - Q d

@@ -19,8 +19,18 @@ struct RankPtrs {
   uint4 *rec;            // [n_pad] division record of each stored row's m
   int2 *tiles;           // [max_tiles] (I | J << 16, K chunks)
   unsigned long long *acc;  // [n][3] 24-bit-limb accumulators of the keys
-  uint8_t *planes;       // [n_pad][K_cap] fp8 threshold planes
-  int64_t n_pad, k_cap;
+  uint8_t *planes;       // [n_pad][K_cap] fp8 threshold planes (sections 1..depth)
+  // residual of the counts above the plane depth
+  int32_t *cnt_gt;       // [eps] sequences whose count of the word exceeds depth
+  int64_t *list_off;     // [eps + 1] start of each word's excess list
+  int64_t *pair_off;     // [eps + 1] start of each word's pair range
+  int32_t *cursor;       // [eps] fill cursor of the excess lists
+  int2 *lists;           // [list_cap] (stored row, count - depth)
+  int32_t *tile_of;      // [(n_pad/128) x (n_pad/256)] tile index of block (I, J)
+  int32_t *block_of;     // [max_tiles] residual block of a tile, -1 = none
+  uint32_t *rblocks;     // [block_cap][128][256] u16 residual per pair (two per word)
+  int64_t n_pad, k_cap, list_cap, block_cap;
+  int32_t depth_cap;     // 0 = all planes
 };
 
 RankPtrs rank_ptrs(void *ws, const RankLayout &L);

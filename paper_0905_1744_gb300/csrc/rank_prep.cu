@@ -12,15 +12,28 @@
 // free: it changes no result), so that for every stored pair i <= j the Eq. 1
 // denominator is min(L_i, L_j) - k + 1 = m_j, the column's own value.
 //
+// Depth cap. Only the sections t = 1..D may be kept as planes (D = the plan's
+// depth; 0 keeps all). What the planes miss is exact too:
+//   min(a, b) = sum_{t=1..D} [a >= t][b >= t] + max(0, min(a, b) - D),
+// and the second term is nonzero only for words both sequences hold more than
+// D times. Each such word gets a list of (stored row, count - D); every pair in
+// a list adds min of the two excesses to that pair's residual, which is summed
+// into a dense 128 x 256 u16 block of its GEMM tile and added to the tile's
+// accumulator in the epilogue, before the floor.
+//
 // Kernels, in launch order:
 //   rank_init      zero the scratch regions of the workspace
 //   lengths_scan   m = L - k + 1, validation, histogram of m
-//   colmax         T_tau = max_x c^x_tau, count validation
-//   colmap         t_max, section ends, K_eff, the column -> (tau, t) map
+//   colmax         T_tau = max_x c^x_tau, count validation, #{x : c^x_tau > D}
+//   colmap         t_max, section ends, K_eff at depth D, excess-list and pair
+//                  offsets, the column -> (tau, t) map
 //   lensort_scan   exclusive prefix over m in decreasing order
 //   lensort_place  row position of every sequence, per-row division records
-//   planes         P rows in fp8 e4m3 (0x38 = 1.0, 0x00 = 0.0), block depths
+//   planes         P rows in fp8 e4m3 (0x38 = 1.0, 0x00 = 0.0), block depths,
+//                  excess-list entries
 //   tiles          the upper-triangle tile list with per-tile K extent
+//   residual_*     mark the tiles the residual touches, give them blocks, zero
+//                  the blocks, add every pair's contribution
 #include "rank.cuh"
 
 namespace sad {
@@ -41,8 +54,19 @@ RankPtrs rank_ptrs(void *ws, const RankLayout &L) {
   P.tiles = reinterpret_cast<int2 *>(b + L.tiles);
   P.acc = reinterpret_cast<unsigned long long *>(b + L.acc);
   P.planes = b + L.planes;
+  P.cnt_gt = reinterpret_cast<int32_t *>(b + L.cnt_gt);
+  P.list_off = reinterpret_cast<int64_t *>(b + L.list_off);
+  P.pair_off = reinterpret_cast<int64_t *>(b + L.pair_off);
+  P.cursor = reinterpret_cast<int32_t *>(b + L.cursor);
+  P.lists = reinterpret_cast<int2 *>(b + L.lists);
+  P.tile_of = reinterpret_cast<int32_t *>(b + L.tile_of);
+  P.block_of = reinterpret_cast<int32_t *>(b + L.block_of);
+  P.rblocks = reinterpret_cast<uint32_t *>(b + L.rblocks);
   P.n_pad = L.n_pad;
-  P.k_cap = L.k_cap;
+  P.k_cap = L.caps.k_cap;
+  P.list_cap = L.caps.list_cap;
+  P.block_cap = L.caps.block_cap;
+  P.depth_cap = L.caps.depth;
   return P;
 }
 
@@ -53,6 +77,34 @@ __device__ __forceinline__ void zero_range(T *p, int64_t count, int64_t tid, int
   for (int64_t i = tid; i < count; i += nthreads) p[i] = T(0);
 }
 
+// Inclusive prefix sum of x over the block's threads in thread order; every
+// thread must call it. s_warp: 32 slots of shared memory. Returns the prefix and
+// writes the block total to *total.
+template <typename V>
+__device__ __forceinline__ V block_scan_incl(V x, V *s_warp, V *total) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  for (int o = 1; o < 32; o <<= 1) {
+    const V y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    V w = lane < nw ? s_warp[lane] : V(0);
+    for (int o = 1; o < 32; o <<= 1) {
+      const V y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    s_warp[lane] = w;
+  }
+  __syncthreads();
+  const V r = x + (wid > 0 ? s_warp[wid - 1] : V(0));
+  *total = s_warp[nw - 1];
+  __syncthreads();
+  return r;
+}
+
 __global__ void rank_init_kernel(RankPtrs P, int32_t n, int32_t eps, int with_keys) {
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nt = (int64_t)gridDim.x * blockDim.x;
@@ -60,6 +112,8 @@ __global__ void rank_init_kernel(RankPtrs P, int32_t n, int32_t eps, int with_ke
   zero_range(P.thist, kMaxM + 2, tid, nt);
   zero_range(P.mhist, kMaxM + 2, tid, nt);
   zero_range(P.secend, kMaxM + 2, tid, nt);
+  zero_range(P.cnt_gt, eps, tid, nt);
+  zero_range(P.cursor, eps, tid, nt);
   if (with_keys) {
     zero_range(P.depth, P.n_pad / kRowBlock, tid, nt);
     zero_range(P.acc, 3 * (int64_t)n, tid, nt);
@@ -70,6 +124,10 @@ __global__ void rank_init_kernel(RankPtrs P, int32_t n, int32_t eps, int with_ke
     P.hdr->t_max = 0;
     P.hdr->n_tiles = 0;
     P.hdr->k_chunks = 0;
+    P.hdr->depth = 0;
+    P.hdr->list_total = 0;
+    P.hdr->pairs_total = 0;
+    P.hdr->n_blocks = 0;
   }
 }
 
@@ -88,16 +146,18 @@ __global__ void lengths_kernel(const int32_t *__restrict__ lengths, int32_t n, i
   }
 }
 
-// T_tau = max over rows of counts[x][tau]. Block (256 words) x (row slice).
+// T_tau = max over rows of counts[x][tau] and (D >= 1) the number of rows whose
+// count exceeds D. Block (256 words) x (row slice).
 __global__ void colmax_kernel(const int32_t *__restrict__ counts, int32_t n, int32_t eps,
                               RankPtrs P) {
   const int32_t tau = blockIdx.x * blockDim.x + threadIdx.x;
   if (tau >= eps) return;
+  const int32_t D = P.depth_cap;
   const int64_t per = ((int64_t)n + gridDim.y - 1) / gridDim.y;
   const int64_t r0 = (int64_t)blockIdx.y * per;
   int64_t r1 = r0 + per;
   if (r1 > n) r1 = n;
-  int32_t mx = 0, mn = 0;
+  int32_t mx = 0, mn = 0, gt = 0;
   int64_t r = r0;
   for (; r + 4 <= r1; r += 4) {
     const int32_t a = __ldg(counts + (r + 0) * eps + tau);
@@ -106,15 +166,18 @@ __global__ void colmax_kernel(const int32_t *__restrict__ counts, int32_t n, int
     const int32_t d = __ldg(counts + (r + 3) * eps + tau);
     mx = max(mx, max(max(a, b), max(c, d)));
     mn = min(mn, min(min(a, b), min(c, d)));
+    gt += (a > D) + (b > D) + (c > D) + (d > D);
   }
   for (; r < r1; ++r) {
     const int32_t a = __ldg(counts + r * eps + tau);
     mx = max(mx, a);
     mn = min(mn, a);
+    gt += a > D;
   }
   if (mn < 0) record_error(P.hdr, SAD_ERR_BAD_INPUT, tau);
   if (mx > kMaxM) record_error(P.hdr, SAD_ERR_UNSUPPORTED, tau);
   if (mx > 0) atomicMax(&P.T[tau], mx);
+  if (D >= 1 && gt > 0) atomicAdd(&P.cnt_gt[tau], gt);
 }
 
 // One block of 1024 threads: histogram of T, t_max, section ends secend[t] =
@@ -196,17 +259,50 @@ __global__ void __launch_bounds__(1024) colmap_kernel(RankPtrs P, int32_t eps, i
   }
   if (tid == 0) P.secend[0] = 0;
   __syncthreads();
-  const int64_t k_eff = tmax >= 1 ? (int64_t)P.secend[tmax] : 0;
+  // planes kept: sections 1..dkeep; a residual exists when some count exceeds it
+  const int32_t dkeep = P.depth_cap >= 1 ? min(P.depth_cap, tmax) : tmax;
+  const bool residual = dkeep < tmax;
+  const int64_t k_eff = dkeep >= 1 ? (int64_t)P.secend[dkeep] : 0;
   int64_t k_pad = (k_eff + kKChunk - 1) / kKChunk * kKChunk;
   if (k_pad < kKChunk) k_pad = kKChunk;
+  // excess lists: list_off = prefix of cnt_gt, pair_off = prefix of c (c + 1) / 2
+  __shared__ int64_t s_warp64[32];
+  __shared__ int64_t s_l, s_p;
   if (tid == 0) {
+    s_l = 0;
+    s_p = 0;
+  }
+  __syncthreads();
+  for (int base = 0; base < eps; base += blockDim.x) {
+    const int tau = base + tid;
+    const int64_t c = (residual && tau < eps) ? (int64_t)P.cnt_gt[tau] : 0;
+    int64_t tot_l, tot_p;
+    const int64_t il = block_scan_incl<int64_t>(c, s_warp64, &tot_l);
+    const int64_t ip = block_scan_incl<int64_t>(c * (c + 1) / 2, s_warp64, &tot_p);
+    if (tau < eps) {
+      P.list_off[tau] = s_l + il - c;
+      P.pair_off[tau] = s_p + ip - c * (c + 1) / 2;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      s_l += tot_l;
+      s_p += tot_p;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    P.list_off[eps] = s_l;
+    P.pair_off[eps] = s_p;
     P.hdr->t_max = tmax;
+    P.hdr->depth = dkeep;
     P.hdr->k_eff = k_eff;
     P.hdr->k_pad = (int32_t)k_pad;
+    P.hdr->list_total = s_l;
+    P.hdr->pairs_total = s_p;
   }
   if (plan_only) return;
-  if (k_pad > P.k_cap) {
-    if (tid == 0) record_error(P.hdr, SAD_ERR_WORKSPACE, (int)k_pad);
+  if (k_pad > P.k_cap || s_l > P.list_cap || (residual && P.block_cap <= 0)) {
+    if (tid == 0) record_error(P.hdr, SAD_ERR_WORKSPACE, (int)(k_pad > P.k_cap ? k_pad : -1));
     return;
   }
   // Words in decreasing T order (ties by word index): position of tau =
@@ -340,6 +436,8 @@ __global__ void __launch_bounds__(256) planes_kernel(const int32_t *__restrict__
   if (P.hdr->status != 0) return;
   const int32_t k_eff = (int32_t)P.hdr->k_eff;
   const int32_t k_pad = P.hdr->k_pad;
+  const int32_t dkeep = P.hdr->depth;
+  const bool residual = dkeep < P.hdr->t_max;
   const bool vec = (eps & 3) == 0 && (reinterpret_cast<uintptr_t>(counts) & 15) == 0;
   const int64_t groups = P.n_pad / kPlaneRows;
   for (int64_t g = blockIdx.x; g < groups; g += gridDim.x) {
@@ -405,6 +503,20 @@ __global__ void __launch_bounds__(256) planes_kernel(const int32_t *__restrict__
       }
     }
     __syncthreads();
+    if (residual) {
+      // excess entries of both rows: (stored row, count - depth) per word above depth
+#pragma unroll
+      for (int r = 0; r < kPlaneRows; ++r) {
+        if (xs[r] < 0) continue;
+        for (int tau = threadIdx.x; tau < eps; tau += blockDim.x) {
+          const int32_t c = s_cnt[r * eps + tau];
+          if (c > dkeep) {
+            const int32_t slot = atomicAdd(&P.cursor[tau], 1);
+            P.lists[P.list_off[tau] + slot] = make_int2((int32_t)(g * kPlaneRows + r), c - dkeep);
+          }
+        }
+      }
+    }
     uint4 *dst[kPlaneRows];
 #pragma unroll
     for (int r = 0; r < kPlaneRows; ++r)
@@ -504,14 +616,18 @@ __global__ void __launch_bounds__(1024) tiles_kernel(RankPtrs P, int32_t n) {
     const int32_t incl = x + ((tid >> 5) > 0 ? s_warp[(tid >> 5) - 1] : 0) + s_carry;
     int32_t out = incl - cnt;
     const int32_t dI = P.depth[I];
+    const int32_t dkeep = P.hdr->depth;
+    const int64_t cfull = P.n_pad / kColBlock;
     unsigned long long chunks = 0;
     for (int32_t J = j0; J < j1; ++J) {
       const int32_t b0 = 2 * J, b1 = 2 * J + 1;
       int32_t dJ = P.depth[b0];
       if (b1 < nblk) dJ = max(dJ, P.depth[b1]);
-      const int32_t d = min(dI, dJ);
-      const int32_t kend = P.secend[min(d, P.hdr->t_max)];
+      const int32_t d = min(min(dI, dJ), dkeep);
+      const int32_t kend = P.secend[max(d, 0)];
       const int32_t nk = max(1, (kend + kKChunk - 1) / kKChunk);
+      P.tile_of[(int64_t)I * cfull + J] = out;
+      P.block_of[out] = 0;
       P.tiles[out++] = make_int2(I | (J << 16), nk);
       chunks += (unsigned long long)nk;
     }
@@ -521,6 +637,104 @@ __global__ void __launch_bounds__(1024) tiles_kernel(RankPtrs P, int32_t n) {
     __syncthreads();
   }
   if (tid == 0) P.hdr->n_tiles = s_carry;
+}
+
+// ------------------------------------------------------------- residual ----
+// Pair q of the residual enumeration: word tau with pair_off[tau] <= q <
+// pair_off[tau + 1], then (u, v), u <= v, with q - pair_off[tau] = v(v+1)/2 + u,
+// indices into the word's excess list. Each thread walks kPairRun consecutive
+// pairs. fn(tile, row in tile, column in tile, value) is called per pair.
+constexpr int kPairRun = 64;
+
+template <typename Fn>
+__device__ __forceinline__ void for_each_residual_pair(const RankPtrs &P, int32_t eps,
+                                                       int64_t total, Fn fn) {
+  const int64_t cfull = P.n_pad / kColBlock;
+  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kPairRun; q0 < total;
+       q0 += nthreads * kPairRun) {
+    // word holding pair q0: last tau with pair_off[tau] <= q0
+    int lo = 0, hi = eps - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (P.pair_off[mid] <= q0) lo = mid; else hi = mid - 1;
+    }
+    int tau = lo;
+    int64_t r = q0 - P.pair_off[tau];
+    int64_t v = (int64_t)((sqrt(8.0 * (double)r + 1.0) - 1.0) * 0.5);
+    while ((v + 1) * (v + 2) / 2 <= r) ++v;
+    while (v * (v + 1) / 2 > r) --v;
+    int64_t u = r - v * (v + 1) / 2;
+    const int64_t q1 = min(q0 + kPairRun, total);
+    for (int64_t q = q0; q < q1; ++q) {
+      while (q >= P.pair_off[tau + 1]) {  // next word with a non-empty list
+        ++tau;
+        u = 0;
+        v = 0;
+      }
+      const int64_t base = P.list_off[tau];
+      const int2 eu = P.lists[base + u], ev = P.lists[base + v];
+      const int32_t a = min(eu.x, ev.x), b = max(eu.x, ev.x);
+      const int32_t t = P.tile_of[(int64_t)(a / kRowBlock) * cfull + b / kColBlock];
+      fn(t, a % kRowBlock, b % kColBlock, (uint32_t)min(eu.y, ev.y));
+      if (++u > v) {
+        ++v;
+        u = 0;
+      }
+    }
+  }
+}
+
+__global__ void residual_mark_kernel(RankPtrs P, int32_t eps) {
+  if (P.hdr->status != 0 || P.hdr->depth >= P.hdr->t_max) return;
+  const int64_t total = P.hdr->pairs_total;
+  for_each_residual_pair(P, eps, total, [&](int32_t t, int32_t, int32_t, uint32_t) {
+    P.block_of[t] = 1;
+  });
+}
+
+// block_of[t] := index of tile t's residual block (tiles in list order), -1 if none.
+__global__ void __launch_bounds__(1024) residual_scan_kernel(RankPtrs P) {
+  __shared__ int32_t s_warp[32];
+  __shared__ int32_t s_carry;
+  const int32_t nt = P.hdr->n_tiles;
+  const bool on = P.hdr->status == 0 && P.hdr->depth < P.hdr->t_max;
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  for (int32_t base = 0; base < nt; base += blockDim.x) {
+    const int32_t t = base + threadIdx.x;
+    const int32_t f = (on && t < nt && P.block_of[t] == 1) ? 1 : 0;
+    int32_t tot;
+    const int32_t incl = block_scan_incl<int32_t>(f, s_warp, &tot);
+    if (t < nt) P.block_of[t] = f ? s_carry + incl - 1 : -1;
+    __syncthreads();
+    if (threadIdx.x == 0) s_carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    P.hdr->n_blocks = s_carry;
+    if (s_carry > P.block_cap) record_error(P.hdr, SAD_ERR_WORKSPACE, s_carry);
+  }
+}
+
+__global__ void residual_zero_kernel(RankPtrs P) {
+  if (P.hdr->status != 0) return;
+  const int64_t words4 = (int64_t)P.hdr->n_blocks * (int64_t)(kResidualBlockBytes / 16);
+  uint4 *p = reinterpret_cast<uint4 *>(P.rblocks);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words4;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = make_uint4(0, 0, 0, 0);
+}
+
+__global__ void residual_add_kernel(RankPtrs P, int32_t eps) {
+  if (P.hdr->status != 0 || P.hdr->depth >= P.hdr->t_max) return;
+  const int64_t total = P.hdr->pairs_total;
+  for_each_residual_pair(P, eps, total, [&](int32_t t, int32_t row, int32_t col, uint32_t val) {
+    const int64_t blk = P.block_of[t];
+    // two u16 per word; a pair's residual never exceeds 65535, so no carry crosses
+    atomicAdd(&P.rblocks[blk * (kResidualBlockBytes / 4) + row * (kColBlock / 2) + (col >> 1)],
+              val << (16 * (col & 1)));
+  });
 }
 
 // key = acc0 + acc1 2^24 + acc2 2^48 (128-bit); rank = (hi + lo 2^-64) / N.
@@ -588,6 +802,18 @@ int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *le
   }
   tiles_kernel<<<1, 1024, 0, st>>>(P, n);
   SAD_LAUNCH_CHECK();
+  if (P.depth_cap >= 1 && P.block_cap > 0) {
+    // the residual only exists when the planes are cut below the largest count
+    const unsigned g = (unsigned)num_sms() * 8;
+    residual_mark_kernel<<<g, 256, 0, st>>>(P, eps);
+    SAD_LAUNCH_CHECK();
+    residual_scan_kernel<<<1, 1024, 0, st>>>(P);
+    SAD_LAUNCH_CHECK();
+    residual_zero_kernel<<<g, 256, 0, st>>>(P);
+    SAD_LAUNCH_CHECK();
+    residual_add_kernel<<<g, 256, 0, st>>>(P, eps);
+    SAD_LAUNCH_CHECK();
+  }
   return SAD_OK;
 }
 

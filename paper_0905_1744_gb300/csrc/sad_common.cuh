@@ -28,13 +28,16 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 struct WsHeader {
   int32_t status;        // first recorded sad_status (0 = none)
   int32_t detail;        // optional detail of the error (e.g. offending index)
-  int64_t k_eff;         // plane columns the data needs (kmer_rank)
+  int64_t k_eff;         // plane columns the data needs at the chosen depth (kmer_rank)
   int32_t k_pad;         // k_eff rounded up to kKChunk
   int32_t t_max;         // largest count of any word in any sequence
   int32_t n_tiles;       // GEMM tiles scheduled
-  int32_t n_valid_blocks;
+  int32_t depth;         // planes kept per word (t_max when nothing is cut)
   unsigned long long k_chunks;  // sum over tiles of their K chunks (executed MMA work)
-  int32_t pad[54];
+  int64_t list_total;    // (sequence, word) entries with a count above depth
+  int64_t pairs_total;   // residual pair contributions
+  int32_t n_blocks;      // residual tiles (dense 128 x 256 blocks) in use
+  int32_t pad[49];
 };
 static_assert(sizeof(WsHeader) == 256, "header is 256 bytes");
 
@@ -42,11 +45,24 @@ __device__ __forceinline__ void record_error(WsHeader *h, int code, int detail =
   if (atomicCAS(&h->status, 0, code) == 0) h->detail = detail;
 }
 
+// Capacities of the data-dependent regions of a rank workspace.
+struct RankCaps {
+  int32_t depth;         // planes kept per word; 0 = all (no residual)
+  int64_t k_cap;         // plane columns
+  int64_t list_cap;      // excess entries (sequence, word) with count > depth
+  int64_t block_cap;     // residual blocks of kRowBlock x kColBlock u16
+};
+
+constexpr size_t kResidualBlockBytes = 2 * 128 * 256;  // u16 per pair of a tile
+
 // Offsets of the rank workspace regions (bytes from the workspace base).
 struct RankLayout {
-  size_t T, secend, colmap, thist, tau_sorted, mhist, perm, rec, depth, tiles, acc, planes;
-  size_t fixed_bytes;    // everything before the planes
-  int64_t n_pad, k_cap, max_tiles;
+  size_t T, secend, thist, tau_sorted, mhist, perm, rec, depth, tiles, acc, cnt_gt, list_off,
+      pair_off, cursor, tile_of, block_of, colmap, lists, planes, rblocks;
+  size_t fixed_bytes;    // everything that does not depend on the capacities
+  size_t bytes;          // total
+  int64_t n_pad, max_tiles;
+  RankCaps caps;
 };
 
 inline int64_t n_pad_of(int64_t n) { return (int64_t)align_up((size_t)(n > 0 ? n : 1), kNPad); }
@@ -55,16 +71,15 @@ inline int64_t max_tiles_of(int64_t n_pad) {
   return (n_pad / kRowBlock) * (n_pad / kColBlock);
 }
 
-inline RankLayout rank_layout(int64_t n, int64_t eps, int64_t k_cap) {
+inline RankLayout rank_layout(int64_t n, int64_t eps, const RankCaps &caps) {
   RankLayout L{};
   L.n_pad = n_pad_of(n);
-  L.k_cap = k_cap;
+  L.caps = caps;
   L.max_tiles = max_tiles_of(L.n_pad);
   size_t o = sizeof(WsHeader);
   auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes, 256); return r; };
   L.T = take(sizeof(int32_t) * eps);
   L.secend = take(sizeof(int32_t) * (kMaxM + 2));
-  L.colmap = take(sizeof(int32_t) * (size_t)(k_cap > 0 ? k_cap : 1));
   L.thist = take(sizeof(int32_t) * (kMaxM + 2));
   L.tau_sorted = take(sizeof(int32_t) * eps);
   L.mhist = take(sizeof(int32_t) * (kMaxM + 2));
@@ -73,9 +88,21 @@ inline RankLayout rank_layout(int64_t n, int64_t eps, int64_t k_cap) {
   L.depth = take(sizeof(int32_t) * (L.n_pad / kRowBlock));
   L.tiles = take(2 * sizeof(int32_t) * L.max_tiles);
   L.acc = take(3 * sizeof(uint64_t) * (size_t)(n > 0 ? n : 1));
-  o = align_up(o, 1024);
+  L.cnt_gt = take(sizeof(int32_t) * eps);
+  L.list_off = take(sizeof(int64_t) * (eps + 1));
+  L.pair_off = take(sizeof(int64_t) * (eps + 1));
+  L.cursor = take(sizeof(int32_t) * eps);
+  L.tile_of = take(sizeof(int32_t) * L.max_tiles);
+  L.block_of = take(sizeof(int32_t) * L.max_tiles);
   L.fixed_bytes = o;
+  L.colmap = take(sizeof(int32_t) * (size_t)(caps.k_cap > 0 ? caps.k_cap : 1));
+  L.lists = take(2 * sizeof(int32_t) * (size_t)(caps.list_cap > 0 ? caps.list_cap : 1));
+  o = align_up(o, 1024);
   L.planes = o;
+  o = align_up(o + (size_t)L.n_pad * (size_t)caps.k_cap, 1024);
+  L.rblocks = o;
+  o += kResidualBlockBytes * (size_t)caps.block_cap;
+  L.bytes = align_up(o, 256);
   return L;
 }
 

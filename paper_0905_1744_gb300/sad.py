@@ -22,6 +22,18 @@ _lib = None
 _lock = threading.Lock()
 
 
+class RankPlan(ctypes.Structure):
+    """sad_rank_plan: depth in; sizes and capacities out (see include/sad.h)."""
+    _fields_ = [("depth", ctypes.c_int32), ("t_max", ctypes.c_int32),
+                ("k_eff", ctypes.c_int64), ("list_entries", ctypes.c_int64),
+                ("residual_pairs", ctypes.c_int64), ("k_cap", ctypes.c_int64),
+                ("list_cap", ctypes.c_int64), ("block_cap", ctypes.c_int64),
+                ("ws_bytes", ctypes.c_size_t)]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
 class SadError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -52,10 +64,10 @@ def _load():
         lib.sad_workspace_bytes.restype = sz
         lib.kmer_count.argtypes = [P, P, i32, i32, i32, P, P, sz, P]
         lib.kmer_count.restype = ctypes.c_int
-        lib.kmer_rank_plan.argtypes = [P, i32, i32, i32, P, sz, ctypes.POINTER(i64),
-                                       ctypes.POINTER(sz), P]
+        lib.kmer_rank_plan.argtypes = [P, i32, i32, i32, ctypes.POINTER(RankPlan), P, sz, P]
         lib.kmer_rank_plan.restype = ctypes.c_int
-        lib.kmer_rank.argtypes = [P, P, i32, i32, i32, P, P, P, P, sz, P]
+        lib.kmer_rank.argtypes = [P, P, i32, i32, i32, ctypes.POINTER(RankPlan), P, P, P, P, sz,
+                                  P]
         lib.kmer_rank.restype = ctypes.c_int
         lib.partition.argtypes = [P, P, i32, i32, P, P, P, P, sz, P]
         lib.partition.restype = ctypes.c_int
@@ -147,32 +159,33 @@ def kmer_count(codes: torch.Tensor, offsets: torch.Tensor, k: int = 3, alphabet:
     return out
 
 
-def kmer_rank_plan(counts: torch.Tensor, k: int = 3, alphabet: int = 20,
-                   ws: Workspace | None = None, stream=None):
-    """(K_eff, workspace bytes kmer_rank needs). Synchronous."""
+def kmer_rank_plan(counts: torch.Tensor, k: int = 3, alphabet: int = 20, depth: int = 0,
+                   ws: Workspace | None = None, stream=None) -> RankPlan:
+    """Sizes and capacities for kmer_rank at plane depth ``depth`` (0 = all
+    planes). Synchronous."""
     n = counts.shape[0]
     ws = ws or Workspace(counts.device)
     ws.ensure(workspace_bytes(OP_RANK, n, k, alphabet, depth=0))
-    k_eff, need = ctypes.c_int64(0), ctypes.c_size_t(0)
-    _check(_load().kmer_rank_plan(_ptr(counts), n, k, alphabet, _ptr(ws.buf), ws.nbytes,
-                                  ctypes.byref(k_eff), ctypes.byref(need), _stream(stream)),
-           "kmer_rank_plan")
-    return int(k_eff.value), int(need.value)
+    plan = RankPlan(depth=int(depth))
+    _check(_load().kmer_rank_plan(_ptr(counts), n, k, alphabet, ctypes.byref(plan),
+                                  _ptr(ws.buf), ws.nbytes, _stream(stream)), "kmer_rank_plan")
+    return plan
 
 
 def kmer_rank(counts: torch.Tensor, lengths: torch.Tensor, k: int = 3, alphabet: int = 20,
               ws: Workspace | None = None, with_rank: bool = True, stream=None,
-              out=None, check: bool = True, plan: bool = True):
+              out=None, check: bool = True, plan: RankPlan | None = None, depth: int = 0):
     """(key_hi uint64, key_lo uint64, rank float64 | None), Eq. 1 and Eq. 3.
 
-    With plan=True the workspace is sized exactly by kmer_rank_plan first.
+    ``plan``: a RankPlan from kmer_rank_plan (reused as is); if None, one is made
+    here for ``depth`` (0 = all planes), which synchronises the stream.
     """
     n = counts.shape[0]
     dev = counts.device
     ws = ws or Workspace(dev)
-    if plan:
-        _, need = kmer_rank_plan(counts, k, alphabet, ws, stream)
-        ws.ensure(need)
+    if plan is None:
+        plan = kmer_rank_plan(counts, k, alphabet, depth, ws, stream)
+    ws.ensure(plan.ws_bytes)
     if out is None:
         hi = torch.empty(n, dtype=torch.uint64, device=dev)
         lo = torch.empty(n, dtype=torch.uint64, device=dev)
@@ -180,8 +193,9 @@ def kmer_rank(counts: torch.Tensor, lengths: torch.Tensor, k: int = 3, alphabet:
     else:
         hi, lo, rank = out
     lengths = lengths.to(device=dev, dtype=torch.int32).contiguous()
-    _check(_load().kmer_rank(_ptr(counts), _ptr(lengths), n, k, alphabet, _ptr(hi), _ptr(lo),
-                             _ptr(rank), _ptr(ws.buf), ws.nbytes, _stream(stream)), "kmer_rank")
+    _check(_load().kmer_rank(_ptr(counts), _ptr(lengths), n, k, alphabet, ctypes.byref(plan),
+                             _ptr(hi), _ptr(lo), _ptr(rank), _ptr(ws.buf), ws.nbytes,
+                             _stream(stream)), "kmer_rank")
     if check:
         ws.check("kmer_rank", stream)
     return hi, lo, rank
@@ -209,12 +223,13 @@ def partition(key_hi: torch.Tensor, key_lo: torch.Tensor, p: int, ws: Workspace 
 
 
 def partition_set(codes: torch.Tensor, offsets: torch.Tensor, p: int, k: int = 3,
-                  alphabet: int = 20, ws: Workspace | None = None, stream=None):
+                  alphabet: int = 20, ws: Workspace | None = None, stream=None,
+                  depth: int = 0):
     """count -> rank -> partition of one sequence set on the device."""
     ws = ws or Workspace(codes.device)
     counts = kmer_count(codes, offsets, k, alphabet, ws=ws, stream=stream)
     lengths = (offsets[1:] - offsets[:-1]).to(torch.int32)
-    hi, lo, rank = kmer_rank(counts, lengths, k, alphabet, ws=ws, stream=stream)
+    hi, lo, rank = kmer_rank(counts, lengths, k, alphabet, ws=ws, stream=stream, depth=depth)
     offs, mem, piv = partition(hi, lo, p, ws=ws, stream=stream)
     return dict(counts=counts, key_hi=hi, key_lo=lo, rank=rank, bucket_offsets=offs,
                 members=mem, pivot_idx=piv)
@@ -222,9 +237,10 @@ def partition_set(codes: torch.Tensor, offsets: torch.Tensor, p: int, k: int = 3
 
 def rank_info(ws: Workspace, stream=None) -> dict:
     """Plan the device chose in the last kmer_rank on this workspace (synchronous)."""
-    info = (ctypes.c_int64 * 8)()
+    info = (ctypes.c_int64 * 16)()
     _check(_load().sad_rank_info(_ptr(ws.buf), info, _stream(stream)), "sad_rank_info")
-    keys = ("status", "k_eff", "k_pad", "t_max", "tiles", "k_chunks")
+    keys = ("status", "k_eff", "k_pad", "t_max", "tiles", "k_chunks", "depth",
+            "residual_pairs", "residual_tiles")
     return {k: int(info[i]) for i, k in enumerate(keys)}
 
 

@@ -38,7 +38,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_host_only_queries(lib):
     lib.sad_abi_version.restype = ctypes.c_int
-    assert lib.sad_abi_version() == 1
+    assert lib.sad_abi_version() == 2
     lib.sad_status_string.restype = ctypes.c_char_p
     lib.sad_status_string.argtypes = [ctypes.c_int]
     assert lib.sad_status_string(0) == b"ok"
@@ -63,6 +63,6 @@ def test_argument_errors_need_no_gpu(lib):
     assert lib.partition(None, None, 10, 0, None, None, None, None, 0, None) == 1
     assert lib.partition(None, None, 10, 11, None, None, None, None, 0, None) == 1
     lib.kmer_rank.argtypes = [P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, P, P,
-                              ctypes.c_size_t, P]
-    assert lib.kmer_rank(None, None, 10, 9, 20, None, None, None, None, 0, None) == 5
-    assert lib.kmer_rank(None, None, -1, 3, 20, None, None, None, None, 0, None) == 1
+                              P, ctypes.c_size_t, P]
+    assert lib.kmer_rank(None, None, 10, 9, 20, None, None, None, None, None, 0, None) == 5
+    assert lib.kmer_rank(None, None, -1, 3, 20, None, None, None, None, None, 0, None) == 1

@@ -68,10 +68,10 @@ def test_count_reports_bad_input(sad):
 
 # ------------------------------------------------------------------- rank ---
 
-def check_rank(sad, oracle_mod, s, rows=None, k=3, alphabet=20):
+def check_rank(sad, oracle_mod, s, rows=None, k=3, alphabet=20, depth=0):
     counts_g = sad.kmer_count(dev(s.codes), dev(s.offsets), k, alphabet)
     lengths = dev(s.lengths.astype(np.int32))
-    hi, lo, rank = sad.kmer_rank(counts_g, lengths, k, alphabet)
+    hi, lo, rank = sad.kmer_rank(counts_g, lengths, k, alphabet, depth=depth)
     hi, lo, rank = host(hi), host(lo), host(rank)
     counts = oracle_mod.kmer_count(s.codes, s.offsets, k, alphabet)
     if rows is None:
@@ -94,24 +94,35 @@ def test_rank_sizes_and_ragged_tails(sad, oracle_mod, n):
     check_rank(sad, oracle_mod, s)
 
 
-def test_rank_family_set_several_tiles(sad, oracle_mod):
+@pytest.mark.parametrize("depth", [0, 1, 2, 3])
+def test_rank_family_set_several_tiles(sad, oracle_mod, depth):
     sets = datagen.family_set(6, 230, lambda r: int(r.integers(40, 900)), p=4, seed=3, stream=9)
-    check_rank(sad, oracle_mod, sets)
+    check_rank(sad, oracle_mod, sets, depth=depth)
 
 
-def test_rank_small_alphabet_deep_planes(sad, oracle_mod):
-    # 4 letters, k = 3: 64 words, counts up to hundreds -> many threshold sections
+@pytest.mark.parametrize("depth", [0, 1, 5, 40])
+def test_rank_small_alphabet_deep_planes(sad, oracle_mod, depth):
+    # 4 letters, k = 3: 64 words, counts up to hundreds -> many threshold sections,
+    # and a residual of long excess lists when the planes are cut
     s = datagen.random_small(300, 3, 2500, seed=11, alphabet=4)
-    check_rank(sad, oracle_mod, s, k=3, alphabet=4)
+    check_rank(sad, oracle_mod, s, k=3, alphabet=4, depth=depth)
 
 
-def test_rank_long_homopolymers_exact_accumulation(sad, oracle_mod):
+@pytest.mark.parametrize("depth", [0, 1, 7])
+def test_rank_long_homopolymers_exact_accumulation(sad, oracle_mod, depth):
     """Shared counts close to the longest supported m (S = min(m_i, m_j) up to
-    19998): the f32 tensor-core accumulation must stay exact."""
+    19998): the f32 tensor-core accumulation and the u16 residual blocks must
+    stay exact."""
     seqs = ["A" * 20000, "A" * 15000, "A" * 19999, "AC" * 6000, "A" * 3, "C" * 9000,
             "A" * 12000 + "C" * 8000]
     s = datagen.from_strings(seqs)
-    check_rank(sad, oracle_mod, s)
+    check_rank(sad, oracle_mod, s, depth=depth)
+
+
+@pytest.mark.parametrize("n,depth", [(129, 1), (257, 2), (700, 1)])
+def test_rank_depth_cap_ragged(sad, oracle_mod, n, depth):
+    s = datagen.random_small(n, 3, 900, seed=n + 17, alphabet=8)
+    check_rank(sad, oracle_mod, s, k=3, alphabet=8, depth=depth)
 
 
 def test_rank_identical_sequences_tie(sad, oracle_mod):
@@ -125,9 +136,13 @@ def test_rank_reports_workspace_too_small(sad):
     counts = sad.kmer_count(dev(s.codes), dev(s.offsets))
     ws = sad.Workspace()
     ws.ensure(sad.workspace_bytes(sad.OP_RANK, s.n, depth=0) + 600 * 520)  # K_cap = 512
+    plan = sad.kmer_rank_plan(counts, ws=ws)
+    plan.k_cap = 512                                  # too few plane columns for the data
+    ws.ensure(ws.nbytes + (4 << 20))                  # room for that layout: the device finds out
+    plan.ws_bytes = ws.nbytes
     with pytest.raises(sad.SadError) as e:
-        sad.kmer_rank(counts, dev(s.lengths.astype(np.int32)), ws=ws, plan=False)
-    assert e.value.status in (sad.ERR_WORKSPACE,)
+        sad.kmer_rank(counts, dev(s.lengths.astype(np.int32)), ws=ws, plan=plan)
+    assert e.value.status == sad.ERR_WORKSPACE
 
 
 def test_rank_rejects_inconsistent_lengths(sad):
