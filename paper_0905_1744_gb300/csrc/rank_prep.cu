@@ -128,6 +128,7 @@ __global__ void rank_init_kernel(RankPtrs P, int32_t n, int32_t eps, int with_ke
     P.hdr->list_total = 0;
     P.hdr->pairs_total = 0;
     P.hdr->n_blocks = 0;
+    P.hdr->m_max = 0;
   }
 }
 
@@ -142,6 +143,7 @@ __global__ void lengths_kernel(const int32_t *__restrict__ lengths, int32_t n, i
       record_error(P.hdr, SAD_ERR_UNSUPPORTED, (int)x);
     } else {
       atomicAdd(&P.mhist[m], 1);
+      atomicMax(&P.hdr->m_max, m);
     }
   }
 }
@@ -348,43 +350,24 @@ __global__ void __launch_bounds__(1024) colmap_kernel(RankPtrs P, int32_t eps, i
   }
 }
 
-// Exclusive prefix over m in decreasing order: mhist[m] := #{x : m_x > m}.
-// Thread t owns the 64 values m = kMaxM - 64 t, ..., kMaxM - 64 t - 63 (high to
-// low); one block scan of the 1024 chunk totals gives each chunk's start.
+// Exclusive prefix over m in decreasing order: mhist[m] := #{x : m_x > m}, for
+// m = m_max down to 1 (larger m are empty), 1024 consecutive values per step.
 __global__ void __launch_bounds__(1024) lensort_scan_kernel(RankPtrs P) {
   __shared__ int32_t s_warp[32];
-  constexpr int kPer = (kMaxM + 1023) / 1024;  // 64
+  __shared__ int32_t s_carry;
   const int tid = threadIdx.x;
-  const int top = kMaxM - kPer * tid;          // first (largest) m of this chunk
-  int32_t total = 0;
-  for (int i = 0; i < kPer; ++i) {
-    const int m = top - i;
-    if (m >= 1) total += P.mhist[m];
-  }
-  int32_t x = total;
-  for (int o = 1; o < 32; o <<= 1) {
-    const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if ((tid & 31) >= o) x += y;
-  }
-  if ((tid & 31) == 31) s_warp[tid >> 5] = x;
+  const int32_t m_max = P.hdr->m_max;
+  if (tid == 0) s_carry = 0;
   __syncthreads();
-  if (tid < 32) {
-    int32_t w = s_warp[tid];
-    for (int o = 1; o < 32; o <<= 1) {
-      const int32_t y = __shfl_up_sync(0xffffffffu, w, o);
-      if (tid >= o) w += y;
-    }
-    s_warp[tid] = w;
-  }
-  __syncthreads();
-  int32_t run = x - total + ((tid >> 5) > 0 ? s_warp[(tid >> 5) - 1] : 0);
-  for (int i = 0; i < kPer; ++i) {
-    const int m = top - i;
-    if (m >= 1) {
-      const int32_t v = P.mhist[m];
-      P.mhist[m] = run;
-      run += v;
-    }
+  for (int base = m_max; base >= 1; base -= blockDim.x) {
+    const int m = base - tid;
+    const int32_t v = m >= 1 ? P.mhist[m] : 0;
+    int32_t tot;
+    const int32_t incl = block_scan_incl<int32_t>(v, s_warp, &tot);
+    if (m >= 1) P.mhist[m] = s_carry + incl - v;
+    __syncthreads();
+    if (tid == 0) s_carry += tot;
+    __syncthreads();
   }
 }
 
@@ -640,70 +623,72 @@ __global__ void __launch_bounds__(1024) tiles_kernel(RankPtrs P, int32_t n) {
 }
 
 // ------------------------------------------------------------- residual ----
-// Pair q of the residual enumeration: word tau with pair_off[tau] <= q <
-// pair_off[tau + 1], then (u, v), u <= v, with q - pair_off[tau] = v(v+1)/2 + u,
-// indices into the word's excess list. Each thread walks kPairRun consecutive
-// pairs. fn(tile, row in tile, column in tile, value) is called per pair.
-constexpr int kPairRun = 64;
+// One block per word (grid-stride): the word's excess list (stored row, count - D)
+// is staged in shared memory in chunks, and the block's threads walk the pairs
+// (u, v), u <= v, of the list. fn(tile, row in tile, column in tile, value) is
+// called once per pair with value = min of the two excesses; u == v is the
+// sequence's own pair.
+constexpr int kListChunk = 1024;
 
 template <typename Fn>
-__device__ __forceinline__ void for_each_residual_pair(const RankPtrs &P, int32_t eps,
-                                                       int64_t total, Fn fn) {
+__device__ __forceinline__ void for_each_residual_pair(const RankPtrs &P, int32_t eps, Fn fn) {
+  __shared__ int2 s_u[kListChunk], s_v[kListChunk];
   const int64_t cfull = P.n_pad / kColBlock;
-  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t q0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kPairRun; q0 < total;
-       q0 += nthreads * kPairRun) {
-    // word holding pair q0: last tau with pair_off[tau] <= q0
-    int lo = 0, hi = eps - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (P.pair_off[mid] <= q0) lo = mid; else hi = mid - 1;
-    }
-    int tau = lo;
-    int64_t r = q0 - P.pair_off[tau];
-    int64_t v = (int64_t)((sqrt(8.0 * (double)r + 1.0) - 1.0) * 0.5);
-    while ((v + 1) * (v + 2) / 2 <= r) ++v;
-    while (v * (v + 1) / 2 > r) --v;
-    int64_t u = r - v * (v + 1) / 2;
-    const int64_t q1 = min(q0 + kPairRun, total);
-    for (int64_t q = q0; q < q1; ++q) {
-      while (q >= P.pair_off[tau + 1]) {  // next word with a non-empty list
-        ++tau;
-        u = 0;
-        v = 0;
+  for (int32_t tau = blockIdx.x; tau < eps; tau += gridDim.x) {
+    const int64_t base = P.list_off[tau];
+    const int64_t len = P.list_off[tau + 1] - base;
+    if (len == 0) continue;
+    // chunk pairs (cu, cv) of the list with cu <= cv; pairs u <= v within them
+    for (int64_t cv = 0; cv < len; cv += kListChunk) {
+      const int nv = (int)min((int64_t)kListChunk, len - cv);
+      for (int i = threadIdx.x; i < nv; i += blockDim.x) s_v[i] = P.lists[base + cv + i];
+      for (int64_t cu = 0; cu <= cv; cu += kListChunk) {
+        const int nu = (int)min((int64_t)kListChunk, len - cu);
+        __syncthreads();
+        for (int i = threadIdx.x; i < nu; i += blockDim.x) s_u[i] = P.lists[base + cu + i];
+        __syncthreads();
+        const bool same = cu == cv;
+        const int npairs = nu * nv;  // <= kListChunk^2
+        for (int e = threadIdx.x; e < npairs; e += blockDim.x) {
+          const int iu = e / nv, iv = e - iu * nv;
+          if (same && iu > iv) continue;
+          const int2 eu = same ? s_v[iu] : s_u[iu];
+          const int2 ev = s_v[iv];
+          const int32_t a = min(eu.x, ev.x), b = max(eu.x, ev.x);
+          const int32_t t = P.tile_of[(int64_t)(a / kRowBlock) * cfull + b / kColBlock];
+          fn(t, a % kRowBlock, b % kColBlock, (uint32_t)min(eu.y, ev.y));
+        }
       }
-      const int64_t base = P.list_off[tau];
-      const int2 eu = P.lists[base + u], ev = P.lists[base + v];
-      const int32_t a = min(eu.x, ev.x), b = max(eu.x, ev.x);
-      const int32_t t = P.tile_of[(int64_t)(a / kRowBlock) * cfull + b / kColBlock];
-      fn(t, a % kRowBlock, b % kColBlock, (uint32_t)min(eu.y, ev.y));
-      if (++u > v) {
-        ++v;
-        u = 0;
-      }
+      __syncthreads();
     }
   }
 }
 
-__global__ void residual_mark_kernel(RankPtrs P, int32_t eps) {
-  if (P.hdr->status != 0 || P.hdr->depth >= P.hdr->t_max) return;
-  const int64_t total = P.hdr->pairs_total;
-  for_each_residual_pair(P, eps, total, [&](int32_t t, int32_t, int32_t, uint32_t) {
-    P.block_of[t] = 1;
+__device__ __forceinline__ bool residual_on(const RankPtrs &P) {
+  return P.hdr->status == 0 && P.hdr->depth < P.hdr->t_max;
+}
+
+// Only needed when fewer residual blocks than tiles are reserved: mark the
+// tiles that some pair touches.
+__global__ void __launch_bounds__(256) residual_mark_kernel(RankPtrs P, int32_t eps) {
+  if (!residual_on(P)) return;
+  for_each_residual_pair(P, eps, [&](int32_t t, int32_t, int32_t, uint32_t) {
+    if (P.block_of[t] != 1) P.block_of[t] = 1;
   });
 }
 
-// block_of[t] := index of tile t's residual block (tiles in list order), -1 if none.
-__global__ void __launch_bounds__(1024) residual_scan_kernel(RankPtrs P) {
+// block_of[t] := index of tile t's residual block, -1 if none. With a block for
+// every tile (identity) nothing needs marking.
+__global__ void __launch_bounds__(1024) residual_scan_kernel(RankPtrs P, int identity) {
   __shared__ int32_t s_warp[32];
   __shared__ int32_t s_carry;
   const int32_t nt = P.hdr->n_tiles;
-  const bool on = P.hdr->status == 0 && P.hdr->depth < P.hdr->t_max;
+  const bool on = residual_on(P);
   if (threadIdx.x == 0) s_carry = 0;
   __syncthreads();
   for (int32_t base = 0; base < nt; base += blockDim.x) {
     const int32_t t = base + threadIdx.x;
-    const int32_t f = (on && t < nt && P.block_of[t] == 1) ? 1 : 0;
+    const int32_t f = (on && t < nt && (identity || P.block_of[t] == 1)) ? 1 : 0;
     int32_t tot;
     const int32_t incl = block_scan_incl<int32_t>(f, s_warp, &tot);
     if (t < nt) P.block_of[t] = f ? s_carry + incl - 1 : -1;
@@ -726,10 +711,9 @@ __global__ void residual_zero_kernel(RankPtrs P) {
     p[i] = make_uint4(0, 0, 0, 0);
 }
 
-__global__ void residual_add_kernel(RankPtrs P, int32_t eps) {
-  if (P.hdr->status != 0 || P.hdr->depth >= P.hdr->t_max) return;
-  const int64_t total = P.hdr->pairs_total;
-  for_each_residual_pair(P, eps, total, [&](int32_t t, int32_t row, int32_t col, uint32_t val) {
+__global__ void __launch_bounds__(256) residual_add_kernel(RankPtrs P, int32_t eps) {
+  if (!residual_on(P)) return;
+  for_each_residual_pair(P, eps, [&](int32_t t, int32_t row, int32_t col, uint32_t val) {
     const int64_t blk = P.block_of[t];
     // two u16 per word; a pair's residual never exceeds 65535, so no carry crosses
     atomicAdd(&P.rblocks[blk * (kResidualBlockBytes / 4) + row * (kColBlock / 2) + (col >> 1)],
@@ -804,14 +788,17 @@ int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *le
   SAD_LAUNCH_CHECK();
   if (P.depth_cap >= 1 && P.block_cap > 0) {
     // the residual only exists when the planes are cut below the largest count
-    const unsigned g = (unsigned)num_sms() * 8;
-    residual_mark_kernel<<<g, 256, 0, st>>>(P, eps);
+    const int identity = P.block_cap >= host_tile_count(n) ? 1 : 0;
+    const unsigned gw = (unsigned)(eps < num_sms() * 8 ? eps : num_sms() * 8);
+    if (!identity) {
+      residual_mark_kernel<<<gw, 256, 0, st>>>(P, eps);
+      SAD_LAUNCH_CHECK();
+    }
+    residual_scan_kernel<<<1, 1024, 0, st>>>(P, identity);
     SAD_LAUNCH_CHECK();
-    residual_scan_kernel<<<1, 1024, 0, st>>>(P);
+    residual_zero_kernel<<<(unsigned)num_sms() * 8, 256, 0, st>>>(P);
     SAD_LAUNCH_CHECK();
-    residual_zero_kernel<<<g, 256, 0, st>>>(P);
-    SAD_LAUNCH_CHECK();
-    residual_add_kernel<<<g, 256, 0, st>>>(P, eps);
+    residual_add_kernel<<<gw, 256, 0, st>>>(P, eps);
     SAD_LAUNCH_CHECK();
   }
   return SAD_OK;

@@ -37,7 +37,8 @@ struct WsHeader {
   int64_t list_total;    // (sequence, word) entries with a count above depth
   int64_t pairs_total;   // residual pair contributions
   int32_t n_blocks;      // residual tiles (dense 128 x 256 blocks) in use
-  int32_t pad[49];
+  int32_t m_max;         // largest m = L - k + 1 of the set
+  int32_t pad[48];
 };
 static_assert(sizeof(WsHeader) == 256, "header is 256 bytes");
 
