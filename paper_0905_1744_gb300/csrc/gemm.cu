@@ -19,13 +19,14 @@
 // of each pair arrives as a dense 128 x 256 u16 block per tile and is added to S
 // before the floor, so the key is the same as with all planes.
 //
-// Persistent kernel, one CTA per SM, 8 warps:
+// Persistent kernel, one CTA per SM, 12 warps:
 //   warp 0      TMA producer: 128 x 128 B tile of A (rows I) and 256 x 128 B of
 //               B (rows J) per stage, 128-byte swizzle, 4-stage mbarrier ring
 //   warp 1      MMA issuer: 4 x (M=128, N=256, K=32) per stage into one of two
 //               TMEM accumulators (2 x 256 columns), commit frees the stage
 //   warp 2      TMEM allocator
-//   warps 4-7   epilogue: tcgen05.ld of the accumulator (lane quadrant = warp % 4)
+//   warps 4-11  epilogue: tcgen05.ld of the accumulator (lane quadrant = warp % 4,
+//               two warps per quadrant, each on half of the 256 columns)
 // The double TMEM accumulator lets the epilogue of one tile overlap the MMAs of
 // the next. Every wait is bounded (globaltimer); on a timeout the CTA records
 // SAD_ERR_TIMEOUT, drains its copies and MMAs in flight, frees TMEM and returns.
@@ -41,8 +42,8 @@ constexpr int kStages = 4;
 constexpr uint32_t kABytes = kRowBlock * kKChunk;
 constexpr uint32_t kBBytes = kColBlock * kKChunk;
 constexpr uint32_t kTxBytes = kABytes + kBBytes;
-constexpr int kThreads = 256;
-constexpr int kEpiThreads = 128;
+constexpr int kThreads = 384;
+constexpr int kEpiThreads = 256;  // warps 4-11: two per TMEM lane quadrant
 constexpr uint32_t kTmemCols = 512;
 constexpr uint64_t kWaitBudgetNs = 2000000000ull;
 
@@ -68,10 +69,11 @@ __device__ __forceinline__ void red_add_u64(unsigned long long *p, unsigned long
   asm volatile("red.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// v[0] of lane L becomes the sum over the 32 lanes of column L.
-__device__ __forceinline__ void transpose_reduce32(uint32_t (&v)[32], uint32_t lane) {
+// Column sums of a 32 x 16 block held one row per lane (v[i] = column i): after
+// the call v[0] of lane L is the sum over all 32 lanes of column L & 15.
+__device__ __forceinline__ void transpose_reduce16(uint32_t (&v)[16], uint32_t lane) {
 #pragma unroll
-  for (int w = 16; w >= 1; w >>= 1) {
+  for (int w = 8; w >= 1; w >>= 1) {
     const bool upper = (lane & (uint32_t)w) != 0;
 #pragma unroll
     for (int i = 0; i < w; ++i) {
@@ -80,6 +82,17 @@ __device__ __forceinline__ void transpose_reduce32(uint32_t (&v)[32], uint32_t l
       v[i] = keep + __shfl_xor_sync(0xffffffffu, send, w);
     }
   }
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 16);
+}
+
+__device__ __forceinline__ void tmem_ld_32x32b_x16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+        "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
 }
 
 __device__ __forceinline__ void set_abort(GemmSmem &S, WsHeader *hdr) {
@@ -203,9 +216,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       mma_commit(&S.drain);
       mbar_wait_bounded(&S.drain, 0, &S.never, kWaitBudgetNs);
     }
-  } else if (!skip && warp >= 4) {
+  } else if (!skip && warp >= 4 && warp < 12) {
     // ------------------------------------------------------------ epilogue --
+    // warp w reads TMEM lanes 32 (w % 4).. (its quadrant) and tile columns
+    // [128 h, 128 h + 128), h = (w - 4) / 4, in sub-chunks of 16 columns.
     const uint32_t q = warp & 3;
+    const uint32_t half = (warp - 4) >> 2;
     const uint32_t etid = threadIdx.x - 128;
     int32_t lt = 0;
     for (int32_t t = blockIdx.x; t < n_tiles; t += gridDim.x, ++lt) {
@@ -219,42 +235,42 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       const int64_t row_pos = (int64_t)I * kRowBlock + q * 32 + lane;
       const int32_t row_orig = P.perm[row_pos];
+      const bool diag = (int64_t)I * kRowBlock + kRowBlock - 1 >= (int64_t)J * kColBlock;
+      const int32_t rblk = residual ? P.block_of[t] : -1;
+      // this row's residual words (two u16 per word), 16 columns = 2 uint4 per sub-chunk
+      const uint4 *rrow =
+          rblk >= 0 ? reinterpret_cast<const uint4 *>(
+                          P.rblocks + (int64_t)rblk * (kResidualBlockBytes / 4) +
+                          (q * 32 + lane) * (kColBlock / 2)) +
+                          half * (kColBlock / 2 / 8)
+                    : nullptr;
+      uint4 ra = make_uint4(0, 0, 0, 0), rb = make_uint4(0, 0, 0, 0);
+      if (rrow) {
+        ra = __ldg(rrow + 0);
+        rb = __ldg(rrow + 1);
+      }
       const uint32_t acc = lt & 1, aph = (lt >> 1) & 1;
       if (!mbar_wait_bounded(&S.tfull[acc], aph, abort_flag, kWaitBudgetNs)) set_abort(S, P.hdr);
       named_bar_sync(1, kEpiThreads);  // column records staged; abort decided
       if (*abort_flag) break;
       tc_fence_after();
-      const bool diag = (int64_t)I * kRowBlock + kRowBlock - 1 >= (int64_t)J * kColBlock;
-      const int32_t rblk = residual ? P.block_of[t] : -1;
-      const uint4 *rrow =
-          rblk >= 0 ? reinterpret_cast<const uint4 *>(
-                          P.rblocks + (int64_t)rblk * (kResidualBlockBytes / 4) +
-                          (q * 32 + lane) * (kColBlock / 2))
-                    : nullptr;
       uint32_t R0 = 0, R1 = 0, R2 = 0;
 #pragma unroll 1
-      for (int c = 0; c < kColBlock / 32; ++c) {
-        uint32_t v[32];
-        tmem_ld_32x32b_x32(tmem + ((q * 32u) << 16) + acc * (uint32_t)kColBlock + c * 32u, v);
-        uint32_t rw[16];
-        if (rrow) {
-#pragma unroll
-          for (int w4 = 0; w4 < 4; ++w4) {
-            const uint4 x = __ldg(rrow + c * 4 + w4);
-            rw[4 * w4 + 0] = x.x;
-            rw[4 * w4 + 1] = x.y;
-            rw[4 * w4 + 2] = x.z;
-            rw[4 * w4 + 3] = x.w;
-          }
-        } else {
-#pragma unroll
-          for (int w = 0; w < 16; ++w) rw[w] = 0;
+      for (int sc = 0; sc < kColBlock / 2 / 16; ++sc) {
+        const int c0 = (int)half * (kColBlock / 2) + sc * 16;
+        uint32_t v[16];
+        tmem_ld_32x32b_x16(tmem + ((q * 32u) << 16) + acc * (uint32_t)kColBlock + (uint32_t)c0,
+                           v);
+        const uint32_t rw[8] = {ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
+        if (rrow && sc + 1 < kColBlock / 2 / 16) {  // next sub-chunk's residual words
+          ra = __ldg(rrow + 2 * (sc + 1));
+          rb = __ldg(rrow + 2 * (sc + 1) + 1);
         }
         tmem_ld_wait();
-        uint32_t cs[32], cq[32];
+        uint32_t cs[16], cq[16];
 #pragma unroll
-        for (int cc = 0; cc < 32; ++cc) {
-          const uint4 rec = S.colrec[buf][c * 32 + cc];
+        for (int cc = 0; cc < 16; ++cc) {
+          const uint4 rec = S.colrec[buf][c0 + cc];
           const uint32_t s = __float2uint_rn(__uint_as_float(v[cc])) +
                              ((rw[cc >> 1] >> (16 * (cc & 1))) & 0xFFFFu);
           const uint32_t d = rec.w & 0xFFFFu;
@@ -272,30 +288,32 @@ __global__ void __launch_bounds__(kThreads, 1)
           uint32_t l0 = wa & 0xFFFFFFu;
           uint32_t l1 = (wa >> 24) | ((wb & 0xFFFFu) << 8);
           uint32_t l2 = (wb >> 16) | (hi << 16);
-          uint32_t sc = s, qc = qv;
+          uint32_t scv = s, qc = qv;
           if (diag) {
-            const int64_t jpos = (int64_t)J * kColBlock + c * 32 + cc;
+            const int64_t jpos = (int64_t)J * kColBlock + c0 + cc;
             if (row_pos > jpos) { l0 = 0; l1 = 0; l2 = 0; }
-            if (row_pos >= jpos) { sc = 0; qc = 0; }
+            if (row_pos >= jpos) { scv = 0; qc = 0; }
           }
           R0 += l0;
           R1 += l1;
           R2 += l2;
-          cs[cc] = sc;
+          cs[cc] = scv;
           cq[cc] = qc;
         }
-        transpose_reduce32(cs, lane);
-        transpose_reduce32(cq, lane);
-        const int col = c * 32 + (int)lane;
-        const int32_t jorig = S.colorig[buf][col];
-        if (jorig >= 0 && (cs[0] | cq[0]) != 0) {
-          const uint4 rec = S.colrec[buf][col];
-          const uint64_t Q = ((uint64_t)rec.y << 32) | rec.x;
-          const unsigned __int128 sum = (unsigned __int128)Q * cs[0] + cq[0];
-          unsigned long long *dst = P.acc + 3 * (int64_t)jorig;
-          red_add_u64(dst + 0, (unsigned long long)(sum & 0xFFFFFFu));
-          red_add_u64(dst + 1, (unsigned long long)((sum >> 24) & 0xFFFFFFu));
-          red_add_u64(dst + 2, (unsigned long long)(sum >> 48));
+        transpose_reduce16(cs, lane);
+        transpose_reduce16(cq, lane);
+        if (lane < 16) {
+          const int col = c0 + (int)lane;
+          const int32_t jorig = S.colorig[buf][col];
+          if (jorig >= 0 && (cs[0] | cq[0]) != 0) {
+            const uint4 rec = S.colrec[buf][col];
+            const uint64_t Q = ((uint64_t)rec.y << 32) | rec.x;
+            const unsigned __int128 sum = (unsigned __int128)Q * cs[0] + cq[0];
+            unsigned long long *dst = P.acc + 3 * (int64_t)jorig;
+            red_add_u64(dst + 0, (unsigned long long)(sum & 0xFFFFFFu));
+            red_add_u64(dst + 1, (unsigned long long)((sum >> 24) & 0xFFFFFFu));
+            red_add_u64(dst + 2, (unsigned long long)(sum >> 48));
+          }
         }
       }
       tc_fence_before();
