@@ -208,6 +208,82 @@ int partition_noalloc(const uint64_t *d_key_hi, const uint64_t *d_key_lo, int32_
                       int32_t *d_pivot_idx, void *stream);
 
 /*
+ * Batched forms: n_sets independent sequence sets processed together, the
+ * batching workload of the paper's many-set setting. The sets are laid out one
+ * after the other in every per-sequence array (set s holds the sequences
+ * [seq_begin_s, seq_begin_s + n_s), seq_begin the prefix sum of n). kmer_count
+ * already takes all sets at once (one offsets array over every sequence).
+ * The rank is block-diagonal: one persistent GEMM launch covers every set's
+ * tiles, and a set's keys depend only on its own sequences (Eq. 3 with N = n_s).
+ * The partition cuts every set into its own p_s buckets (Sec. 3.1.2 per set).
+ * After sad_batch_plan_make the two calls launch no synchronising operation, so
+ * the whole batch can be captured in a CUDA graph and replayed.
+ *
+ *   rank            depth in (see sad_rank_plan); sizes and capacities out,
+ *                   for all sets together (rank.ws_bytes: sad_batch_rank's
+ *                   workspace).
+ *   n_sets, max_p   sets and the largest p_s.
+ *   n_total, rows_total, tiles_total, tileof_total  sums over sets of n_s,
+ *                   stored rows (n_s rounded up to 256), GEMM tiles and
+ *                   tile-map entries.
+ *   sum_p, sum_p1, sum_pp1, sum_pp  sums of p_s, p_s - 1, p_s (p_s - 1), p_s^2.
+ *   part_ws_bytes   workspace bytes of sad_batch_partition.
+ */
+typedef struct sad_batch_plan {
+  sad_rank_plan rank;
+  int32_t n_sets;
+  int32_t max_p;
+  int64_t n_total;
+  int64_t rows_total;
+  int64_t tiles_total;
+  int64_t tileof_total;
+  int64_t sum_p, sum_p1, sum_pp1, sum_pp;
+  size_t part_ws_bytes;
+} sad_batch_plan;
+
+/*
+ * sad_batch_plan_make - SYNCHRONOUS: the plan of a batch.
+ *   d_counts   int32 [n_total][eps] counts of all sets (from one kmer_count).
+ *   h_n, h_p   host int32 [n_sets]: sequences and buckets per set
+ *              (1 <= p_s <= min(n_s, 4096)).
+ *   d_n        device copy of h_n.
+ *   plan       plan->rank.depth in; the rest out.
+ *   d_ws       rank workspace; if smaller than the fixed part, returns
+ *              SAD_ERR_WORKSPACE with plan->rank.ws_bytes = the bytes needed.
+ */
+int sad_batch_plan_make(const int32_t *d_counts, const int32_t *h_n, const int32_t *h_p,
+                        const int32_t *d_n, int32_t n_sets, int32_t k, int32_t alphabet,
+                        sad_batch_plan *plan, void *d_ws, size_t ws_bytes, void *stream);
+
+/*
+ * sad_batch_rank - kmer_rank of every set of the batch (Eq. 1, Eq. 3 per set).
+ *   d_counts, d_lengths  all sets' counts and lengths, set after set.
+ *   d_n        device int32 [n_sets] set sizes (as given to the plan).
+ *   d_key_hi, d_key_lo, d_rank  per-sequence outputs, set after set.
+ *   d_ws       at least plan->rank.ws_bytes.
+ */
+int sad_batch_rank(const int32_t *d_counts, const int32_t *d_lengths, const int32_t *d_n,
+                   int32_t k, int32_t alphabet, const sad_batch_plan *plan, uint64_t *d_key_hi,
+                   uint64_t *d_key_lo, double *d_rank, void *d_ws, size_t ws_bytes,
+                   void *stream);
+
+/*
+ * sad_batch_partition - partition() of every set of the batch.
+ *   d_n, d_p   device int32 [n_sets] set sizes and bucket counts.
+ *   d_bucket_offsets  int32 [sum over sets of (p_s + 1)]: set s's CSR offsets
+ *              (local, 0..n_s) start at entry sum_{s'<s} (p_s' + 1).
+ *   d_members  int32 [n_total]: set s's members (local indices) fill
+ *              [seq_begin_s, seq_begin_s + n_s).
+ *   d_pivot_idx (nullable) int32 [sum_p1]: set s's p_s - 1 pivots (local
+ *              indices) start at sum_{s'<s} (p_s' - 1).
+ *   d_ws       at least plan->part_ws_bytes.
+ */
+int sad_batch_partition(const uint64_t *d_key_hi, const uint64_t *d_key_lo, const int32_t *d_n,
+                        const int32_t *d_p, const sad_batch_plan *plan,
+                        int32_t *d_bucket_offsets, int32_t *d_members, int32_t *d_pivot_idx,
+                        void *d_ws, size_t ws_bytes, void *stream);
+
+/*
  * sad_status_read - SYNCHRONOUS: waits for `stream`, then returns the status
  * recorded in the workspace by the device (SAD_OK if none). With clear != 0 the
  * recorded status is reset to SAD_OK. d_ws must be a workspace previously passed

@@ -15,6 +15,11 @@ int count_launch(const uint8_t *codes, const int64_t *offsets, int32_t n, int32_
 int partition_launch(const uint64_t *key_hi, const uint64_t *key_lo, int32_t n, int32_t p,
                      int32_t *bucket_offsets, int32_t *members, int32_t *pivot_idx, void *ws,
                      cudaStream_t st);
+int partition_sets_launch(const uint64_t *key_hi, const uint64_t *key_lo, int32_t n_sets,
+                          const int32_t *d_n, const int32_t *d_p, int32_t n_single,
+                          int32_t p_single, const PartTotals &tot, int32_t max_p,
+                          int32_t *bucket_offsets, int32_t *members, int32_t *pivot_idx,
+                          void *ws, cudaStream_t st);
 
 namespace {
 std::atomic<uint64_t> g_launches{0};
@@ -32,13 +37,13 @@ int64_t eps_of(int32_t k, int32_t alphabet) {
 bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 // Largest K_cap (multiple of kKChunk) whose planes-only rank layout fits in ws_bytes.
-int64_t k_cap_for(int64_t n, int64_t eps, size_t ws_bytes) {
-  const RankLayout base = rank_layout(n, eps, RankCaps{0, 0, 0, 0});
+int64_t k_cap_for(const RankShape &sh, int64_t eps, size_t ws_bytes) {
+  const RankLayout base = rank_layout(sh, eps, RankCaps{0, 0, 0, 0});
   if (ws_bytes <= base.fixed_bytes) return 0;
   // upper bound (the layout only grows with K_cap), then step down until it fits
-  int64_t k = (int64_t)((ws_bytes - base.fixed_bytes) / (size_t)base.n_pad);
+  int64_t k = (int64_t)((ws_bytes - base.fixed_bytes) / (size_t)sh.rows_total);
   k = k / kKChunk * kKChunk;
-  while (k > 0 && rank_layout(n, eps, RankCaps{0, k, 0, 0}).bytes > ws_bytes) k -= kKChunk;
+  while (k > 0 && rank_layout(sh, eps, RankCaps{0, k, 0, 0}).bytes > ws_bytes) k -= kKChunk;
   return k;
 }
 
@@ -137,10 +142,11 @@ size_t sad_workspace_bytes(int32_t op, int32_t n_seq, int32_t k, int32_t alphabe
       return eps < 0 ? 0 : sizeof(WsHeader);
     case SAD_OP_RANK: {
       if (eps < 0) return 0;
-      if (depth <= 0) return rank_layout(n_seq, eps, RankCaps{0, 0, 0, 0}).fixed_bytes;
+      const RankShape sh = shape_single(n_seq);
+      if (depth <= 0) return rank_layout(sh, eps, RankCaps{0, 0, 0, 0}).fixed_bytes;
       const int64_t k_cap =
           (int64_t)align_up((size_t)eps * (size_t)depth, (size_t)kKChunk);
-      return rank_layout(n_seq, eps, RankCaps{0, k_cap, 0, 0}).bytes;
+      return rank_layout(sh, eps, RankCaps{0, k_cap, 0, 0}).bytes;
     }
     case SAD_OP_PARTITION:
       if (p < 1 || p > kMaxP) return 0;
@@ -164,21 +170,24 @@ int kmer_count(const uint8_t *d_codes, const int64_t *d_offsets, int32_t n_seq, 
                       static_cast<WsHeader *>(d_ws), static_cast<cudaStream_t>(stream));
 }
 
-int kmer_rank_plan(const int32_t *d_counts, int32_t n_seq, int32_t k, int32_t alphabet,
-                   sad_rank_plan *plan, void *d_ws, size_t ws_bytes, void *stream) {
-  const int64_t eps = eps_of(k, alphabet);
-  if (eps < 0) return SAD_ERR_UNSUPPORTED;
-  if (n_seq < 0 || !plan || !d_ws || !aligned(d_ws, 256) || plan->depth < 0)
-    return SAD_ERR_INVALID_ARGUMENT;
-  const RankCaps probe{plan->depth, 0, 0, 0};
-  const RankLayout L0 = rank_layout(n_seq, eps, probe);
-  if (ws_bytes < L0.fixed_bytes) return SAD_ERR_WORKSPACE;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
+}  // extern "C"
+
+namespace {
+
+// Plan for `sh` (one set, or a batch with per-set sizes d_n on the device).
+int rank_plan_impl(const int32_t *d_counts, const RankShape &sh, const int32_t *d_n,
+                   int64_t eps, int32_t k, sad_rank_plan *plan, void *d_ws, size_t ws_bytes,
+                   cudaStream_t st) {
+  const RankLayout L0 = rank_layout(sh, eps, RankCaps{plan->depth, 0, 0, 0});
+  if (ws_bytes < L0.fixed_bytes) {
+    plan->ws_bytes = L0.fixed_bytes;
+    return SAD_ERR_WORKSPACE;
+  }
   WsHeader h{};
-  if (n_seq > 0) {
+  if (sh.n_total > 0) {
     if (!d_counts) return SAD_ERR_INVALID_ARGUMENT;
     const RankPtrs P = rank_ptrs(d_ws, L0);
-    int rc = rank_prep_launch(P, d_counts, nullptr, n_seq, k, (int32_t)eps, 1, st);
+    int rc = rank_prep_launch(P, d_counts, nullptr, d_n, k, (int32_t)eps, 1, st);
     if (rc) return rc;
     rc = check_cuda(cudaMemcpyAsync(&h, d_ws, sizeof(h), cudaMemcpyDeviceToHost, st));
     if (rc) return rc;
@@ -188,18 +197,82 @@ int kmer_rank_plan(const int32_t *d_counts, int32_t n_seq, int32_t k, int32_t al
   }
   int64_t k_pad = (int64_t)align_up((size_t)h.k_eff, kKChunk);
   if (k_pad < kKChunk) k_pad = kKChunk;
-  const bool residual = n_seq > 0 && h.depth < h.t_max;
-  const int64_t tiles = host_tile_count(n_seq);
+  const bool residual = sh.n_total > 0 && h.depth < h.t_max;
   plan->t_max = h.t_max;
   plan->k_eff = h.k_eff;
   plan->list_entries = h.list_total;
   plan->residual_pairs = h.pairs_total;
   plan->k_cap = k_pad;
   plan->list_cap = residual ? h.list_total : 0;
-  plan->block_cap = residual ? (h.pairs_total < tiles ? h.pairs_total : tiles) : 0;
+  plan->block_cap =
+      residual ? (h.pairs_total < sh.tiles_total ? h.pairs_total : sh.tiles_total) : 0;
   const RankCaps caps{plan->depth, plan->k_cap, plan->list_cap, plan->block_cap};
-  plan->ws_bytes = rank_layout(n_seq, eps, caps).bytes;
+  plan->ws_bytes = rank_layout(sh, eps, caps).bytes;
   return SAD_OK;
+}
+
+int rank_run_impl(const int32_t *d_counts, const int32_t *d_lengths, const RankShape &sh,
+                  const int32_t *d_n, int64_t eps, int32_t k, const sad_rank_plan *plan,
+                  uint64_t *d_key_hi, uint64_t *d_key_lo, double *d_rank, void *d_ws,
+                  size_t ws_bytes, cudaStream_t st) {
+  if (sh.rows_total / kRowBlock > 0xFFFF) return SAD_ERR_UNSUPPORTED;  // 16-bit block ids
+  RankCaps caps{0, 0, 0, 0};
+  if (plan) {
+    if (plan->depth < 0 || plan->k_cap < kKChunk || plan->k_cap % kKChunk != 0 ||
+        plan->list_cap < 0 || plan->block_cap < 0)
+      return SAD_ERR_INVALID_ARGUMENT;
+    caps = RankCaps{plan->depth, plan->k_cap, plan->list_cap, plan->block_cap};
+    if (rank_layout(sh, eps, caps).bytes > ws_bytes) return SAD_ERR_WORKSPACE;
+  } else {
+    caps.k_cap = k_cap_for(sh, eps, ws_bytes);
+    if (caps.k_cap < kKChunk) return SAD_ERR_WORKSPACE;
+  }
+  const RankLayout L = rank_layout(sh, eps, caps);
+  const RankPtrs P = rank_ptrs(d_ws, L);
+  int rc = rank_prep_launch(P, d_counts, d_lengths, d_n, k, (int32_t)eps, 0, st);
+  if (rc) return rc;
+  rc = rank_gemm_launch(P, st);
+  if (rc) return rc;
+  return rank_finalize_launch(P, d_key_hi, d_key_lo, d_rank, st);
+}
+
+// Host-side shape of a batch; validates the per-set sizes.
+int batch_shape(const int32_t *h_n, const int32_t *h_p, int32_t n_sets, RankShape *sh,
+                PartTotals *pt, int32_t *max_p) {
+  if (n_sets < 1 || !h_n) return SAD_ERR_INVALID_ARGUMENT;
+  *sh = RankShape{0, 0, 0, 0, 0};
+  *pt = PartTotals{0, 0, 0, 0, 0};
+  *max_p = 1;
+  for (int32_t s = 0; s < n_sets; ++s) {
+    if (h_n[s] < 1) return SAD_ERR_INVALID_ARGUMENT;
+    shape_add_set(*sh, h_n[s]);
+    if (h_p) {
+      const int64_t p = h_p[s];
+      if (p < 1 || p > kMaxP || p > h_n[s]) return SAD_ERR_INVALID_ARGUMENT;
+      pt->n += h_n[s];
+      pt->p += p;
+      pt->p1 += p - 1;
+      pt->pp1 += p * (p - 1);
+      pt->pp += p * p;
+      if (p > *max_p) *max_p = (int32_t)p;
+    }
+  }
+  if (sh->n_total > 0x7FFFFFFF) return SAD_ERR_UNSUPPORTED;
+  return SAD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int kmer_rank_plan(const int32_t *d_counts, int32_t n_seq, int32_t k, int32_t alphabet,
+                   sad_rank_plan *plan, void *d_ws, size_t ws_bytes, void *stream) {
+  const int64_t eps = eps_of(k, alphabet);
+  if (eps < 0) return SAD_ERR_UNSUPPORTED;
+  if (n_seq < 0 || !plan || !d_ws || !aligned(d_ws, 256) || plan->depth < 0)
+    return SAD_ERR_INVALID_ARGUMENT;
+  return rank_plan_impl(d_counts, shape_single(n_seq), nullptr, eps, k, plan, d_ws, ws_bytes,
+                        static_cast<cudaStream_t>(stream));
 }
 
 int kmer_rank(const int32_t *d_counts, const int32_t *d_lengths, int32_t n_seq, int32_t k,
@@ -210,26 +283,66 @@ int kmer_rank(const int32_t *d_counts, const int32_t *d_lengths, int32_t n_seq, 
   if (n_seq < 0 || !d_ws || !aligned(d_ws, 256)) return SAD_ERR_INVALID_ARGUMENT;
   if (n_seq == 0) return SAD_OK;
   if (!d_counts || !d_lengths || !d_key_hi || !d_key_lo) return SAD_ERR_INVALID_ARGUMENT;
-  if ((int64_t)n_seq > (int64_t)0xFFFF * kRowBlock - kNPad) return SAD_ERR_UNSUPPORTED;
-  RankCaps caps{0, 0, 0, 0};
-  if (plan) {
-    if (plan->depth < 0 || plan->k_cap < kKChunk || plan->k_cap % kKChunk != 0 ||
-        plan->list_cap < 0 || plan->block_cap < 0)
-      return SAD_ERR_INVALID_ARGUMENT;
-    caps = RankCaps{plan->depth, plan->k_cap, plan->list_cap, plan->block_cap};
-    if (rank_layout(n_seq, eps, caps).bytes > ws_bytes) return SAD_ERR_WORKSPACE;
-  } else {
-    caps.k_cap = k_cap_for(n_seq, eps, ws_bytes);
-    if (caps.k_cap < kKChunk) return SAD_ERR_WORKSPACE;
-  }
-  const RankLayout L = rank_layout(n_seq, eps, caps);
-  const RankPtrs P = rank_ptrs(d_ws, L);
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  int rc = rank_prep_launch(P, d_counts, d_lengths, n_seq, k, (int32_t)eps, 0, st);
+  return rank_run_impl(d_counts, d_lengths, shape_single(n_seq), nullptr, eps, k, plan,
+                       d_key_hi, d_key_lo, d_rank, d_ws, ws_bytes,
+                       static_cast<cudaStream_t>(stream));
+}
+
+int sad_batch_plan_make(const int32_t *d_counts, const int32_t *h_n, const int32_t *h_p,
+                        const int32_t *d_n, int32_t n_sets, int32_t k, int32_t alphabet,
+                        sad_batch_plan *plan, void *d_ws, size_t ws_bytes, void *stream) {
+  const int64_t eps = eps_of(k, alphabet);
+  if (eps < 0) return SAD_ERR_UNSUPPORTED;
+  if (!plan || !h_p || !d_n || !d_ws || !aligned(d_ws, 256) || plan->rank.depth < 0)
+    return SAD_ERR_INVALID_ARGUMENT;
+  RankShape sh;
+  PartTotals pt;
+  int32_t max_p;
+  int rc = batch_shape(h_n, h_p, n_sets, &sh, &pt, &max_p);
   if (rc) return rc;
-  rc = rank_gemm_launch(P, n_seq, st);
-  if (rc) return rc;
-  return rank_finalize_launch(P, n_seq, d_key_hi, d_key_lo, d_rank, st);
+  plan->n_sets = n_sets;
+  plan->max_p = max_p;
+  plan->n_total = sh.n_total;
+  plan->rows_total = sh.rows_total;
+  plan->tiles_total = sh.tiles_total;
+  plan->tileof_total = sh.tileof_total;
+  plan->sum_p = pt.p;
+  plan->sum_p1 = pt.p1;
+  plan->sum_pp1 = pt.pp1;
+  plan->sum_pp = pt.pp;
+  plan->part_ws_bytes = part_layout_sets(n_sets, pt).bytes;
+  return rank_plan_impl(d_counts, sh, d_n, eps, k, &plan->rank, d_ws, ws_bytes,
+                        static_cast<cudaStream_t>(stream));
+}
+
+int sad_batch_rank(const int32_t *d_counts, const int32_t *d_lengths, const int32_t *d_n,
+                   int32_t k, int32_t alphabet, const sad_batch_plan *plan, uint64_t *d_key_hi,
+                   uint64_t *d_key_lo, double *d_rank, void *d_ws, size_t ws_bytes,
+                   void *stream) {
+  const int64_t eps = eps_of(k, alphabet);
+  if (eps < 0) return SAD_ERR_UNSUPPORTED;
+  if (!plan || plan->n_sets < 1 || !d_n || !d_counts || !d_lengths || !d_key_hi || !d_key_lo ||
+      !d_ws || !aligned(d_ws, 256))
+    return SAD_ERR_INVALID_ARGUMENT;
+  const RankShape sh{plan->n_sets, plan->n_total, plan->rows_total, plan->tiles_total,
+                     plan->tileof_total};
+  return rank_run_impl(d_counts, d_lengths, sh, plan->n_sets > 1 ? d_n : nullptr, eps, k,
+                       &plan->rank, d_key_hi, d_key_lo, d_rank, d_ws, ws_bytes,
+                       static_cast<cudaStream_t>(stream));
+}
+
+int sad_batch_partition(const uint64_t *d_key_hi, const uint64_t *d_key_lo, const int32_t *d_n,
+                        const int32_t *d_p, const sad_batch_plan *plan,
+                        int32_t *d_bucket_offsets, int32_t *d_members, int32_t *d_pivot_idx,
+                        void *d_ws, size_t ws_bytes, void *stream) {
+  if (!plan || plan->n_sets < 1 || !d_n || !d_p || !d_key_hi || !d_key_lo ||
+      !d_bucket_offsets || !d_members || !d_ws || !aligned(d_ws, 256))
+    return SAD_ERR_INVALID_ARGUMENT;
+  if (ws_bytes < plan->part_ws_bytes) return SAD_ERR_WORKSPACE;
+  const PartTotals pt{plan->n_total, plan->sum_p, plan->sum_p1, plan->sum_pp1, plan->sum_pp};
+  return partition_sets_launch(d_key_hi, d_key_lo, plan->n_sets, d_n, d_p, 0, 0, pt,
+                               plan->max_p, d_bucket_offsets, d_members, d_pivot_idx, d_ws,
+                               static_cast<cudaStream_t>(stream));
 }
 
 int partition(const uint64_t *d_key_hi, const uint64_t *d_key_lo, int32_t n_seq, int32_t p,

@@ -102,7 +102,7 @@ __device__ __forceinline__ void set_abort(GemmSmem &S, WsHeader *hdr) {
 
 __global__ void __launch_bounds__(kThreads, 1)
     plane_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
-                      const __grid_constant__ CUtensorMap tmB, RankPtrs P, int32_t n) {
+                      const __grid_constant__ CUtensorMap tmB, RankPtrs P) {
   extern __shared__ uint8_t smem_raw[];
   GemmSmem &S = *reinterpret_cast<GemmSmem *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -363,8 +363,8 @@ int make_plane_map(CUtensorMap *map, uint8_t *planes, int64_t n_pad, int64_t k_c
 
 }  // namespace
 
-int rank_gemm_launch(const RankPtrs &P, int32_t n, cudaStream_t st) {
-  const int64_t tiles = host_tile_count(n);
+int rank_gemm_launch(const RankPtrs &P, cudaStream_t st) {
+  const int64_t tiles = P.tiles_total;
   if (tiles == 0) return SAD_OK;
   CUtensorMap mA, mB;
   int rc = make_plane_map(&mA, P.planes, P.n_pad, P.k_cap, kRowBlock);
@@ -380,7 +380,7 @@ int rank_gemm_launch(const RankPtrs &P, int32_t n, cudaStream_t st) {
   }
   const int64_t grid = tiles < num_sms() ? tiles : num_sms();
   prof_begin(st);
-  plane_gemm_kernel<<<(unsigned)grid, kThreads, kGemmSmemBytes, st>>>(mA, mB, P, n);
+  plane_gemm_kernel<<<(unsigned)grid, kThreads, kGemmSmemBytes, st>>>(mA, mB, P);
   SAD_LAUNCH_CHECK();
   prof_end(st);
   return SAD_OK;

@@ -18,223 +18,232 @@
 // items; longer ranges sort 4096-item chunks that way and then merge runs of
 // doubling width in global memory, each item finding its place by a binary
 // search in the other run (all items differ, the index breaking ties).
-#include "sad_common.cuh"
+#include "sort.cuh"
 
 namespace sad {
 
 namespace {
 
-constexpr int kSortThreads = 1024;
-constexpr int kSmemItems = 4096;
-constexpr size_t kSortSmem = sizeof(Item) * kSmemItems;
-
-__device__ __forceinline__ Item item_inf() {
-  Item x;
-  x.hi = ~0ull;
-  x.lo = ~0ull;
-  x.idx = 0x7FFFFFFF;
-  x.pad = 0;
-  return x;
-}
-
-// Ascending bitonic sort of data[0, cnt), cnt <= kSmemItems, by the whole CTA.
-__device__ void cta_sort_small(Item *data, int cnt, Item *sm) {
-  int p2 = 1;
-  while (p2 < cnt) p2 <<= 1;
-  for (int i = threadIdx.x; i < p2; i += blockDim.x) sm[i] = i < cnt ? data[i] : item_inf();
-  __syncthreads();
-  for (int size = 2; size <= p2; size <<= 1) {
-    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int i = threadIdx.x; i < (p2 >> 1); i += blockDim.x) {
-        const int a = 2 * stride * (i / stride) + (i % stride);
-        const int b = a + stride;
-        const bool asc = (a & size) == 0;
-        const Item x = sm[a], y = sm[b];
-        if (asc ? item_less(y, x) : item_less(x, y)) {
-          sm[a] = y;
-          sm[b] = x;
-        }
-      }
-      __syncthreads();
-    }
-  }
-  for (int i = threadIdx.x; i < cnt; i += blockDim.x) data[i] = sm[i];
-  __syncthreads();
-}
-
-// Number of items of run[0, len) that are less than x.
-__device__ __forceinline__ int64_t count_less(const Item *run, int64_t len, const Item &x) {
-  int64_t lo = 0, hi = len;
-  while (lo < hi) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (item_less(run[mid], x)) lo = mid + 1; else hi = mid;
-  }
-  return lo;
-}
-
-// Number of items of run[0, len) that are not greater than x.
-__device__ __forceinline__ int64_t count_not_greater(const Item *run, int64_t len, const Item &x) {
-  int64_t lo = 0, hi = len;
-  while (lo < hi) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (!item_less(x, run[mid])) lo = mid + 1; else hi = mid;
-  }
-  return lo;
-}
-
-// Ascending sort of data[0, cnt) by one CTA; scratch holds cnt items.
-__device__ void cta_sort(Item *data, Item *scratch, int64_t cnt, Item *sm) {
-  if (cnt <= 1) return;
-  if (cnt <= kSmemItems) {
-    cta_sort_small(data, (int)cnt, sm);
-    return;
-  }
-  for (int64_t c0 = 0; c0 < cnt; c0 += kSmemItems)
-    cta_sort_small(data + c0, (int)(cnt - c0 < kSmemItems ? cnt - c0 : kSmemItems), sm);
-  Item *src = data, *dst = scratch;
-  for (int64_t w = kSmemItems; w < cnt; w <<= 1) {
-    for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-      const int64_t a0 = i / (2 * w) * (2 * w);
-      const int64_t a1 = a0 + w < cnt ? a0 + w : cnt;
-      const int64_t b1 = a0 + 2 * w < cnt ? a0 + 2 * w : cnt;
-      const Item x = src[i];
-      if (i < a1)
-        dst[i + count_less(src + a1, b1 - a1, x)] = x;
-      else
-        dst[a0 + (i - a1) + count_less(src + a0, a1 - a0, x)] = x;
-    }
-    __syncthreads();
-    Item *t = src;
-    src = dst;
-    dst = t;
-  }
-  if (src != data) {
-    for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) data[i] = src[i];
-    __syncthreads();
-  }
-}
-
 __device__ __forceinline__ int64_t block_lo(int64_t b, int64_t n, int64_t p) { return b * n / p; }
 
+// Set holding global item x: last s with sets[s].seq_begin <= x.
+__device__ __forceinline__ int32_t set_of(const PartSet *sets, int32_t n_sets, int64_t x) {
+  int lo = 0, hi = n_sets - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (sets[mid].seq_begin <= x) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// One block: the set table from per-set sizes (d_n, d_p; or the single set n1, p1)
+// and the block boundaries segoff[blk_base + b] = seq_begin + floor(b n / p).
+__global__ void __launch_bounds__(1024) part_setup_kernel(const int32_t *d_n, const int32_t *d_p,
+                                                          int32_t n_sets, int32_t n1, int32_t p1,
+                                                          PartSet *sets, int64_t *segoff) {
+  __shared__ int64_t s_warp[32];
+  __shared__ int64_t s_c[5];
+  const int tid = threadIdx.x;
+  if (tid < 5) s_c[tid] = 0;
+  __syncthreads();
+  for (int base = 0; base < n_sets; base += blockDim.x) {
+    const int s = base + tid;
+    const int64_t n = s < n_sets ? (d_n ? d_n[s] : n1) : 0;
+    const int64_t p = s < n_sets ? (d_p ? d_p[s] : p1) : 0;
+    const int64_t v[5] = {n, p, p > 0 ? p - 1 : 0, p * (p > 0 ? p - 1 : 0), p * p};
+    int64_t ex[5];
+#pragma unroll
+    for (int f = 0; f < 5; ++f) {
+      int64_t x = v[f];
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if ((tid & 31) >= o) x += y;
+      }
+      if ((tid & 31) == 31) s_warp[tid >> 5] = x;
+      __syncthreads();
+      if (tid < 32) {
+        int64_t w = s_warp[tid];
+        for (int o = 1; o < 32; o <<= 1) {
+          const int64_t y = __shfl_up_sync(0xffffffffu, w, o);
+          if (tid >= o) w += y;
+        }
+        s_warp[tid] = w;
+      }
+      __syncthreads();
+      const int64_t incl = x + ((tid >> 5) > 0 ? s_warp[(tid >> 5) - 1] : 0);
+      ex[f] = s_c[f] + incl - v[f];
+      __syncthreads();
+      if (tid == (int)blockDim.x - 1) s_c[f] += incl;
+      __syncthreads();
+    }
+    if (s < n_sets) {
+      PartSet e;
+      e.seq_begin = ex[0];
+      e.n = (int32_t)n;
+      e.p = (int32_t)p;
+      e.blk_base = ex[1];
+      e.piv_base = ex[2];
+      e.samp_base = ex[3];
+      e.pos_base = ex[4];
+      sets[s] = e;
+      for (int64_t b = 0; b <= p; ++b) segoff[e.blk_base + b] = e.seq_begin + block_lo(b, n, p);
+    }
+  }
+}
+
 __global__ void part_init_kernel(const uint64_t *__restrict__ hi, const uint64_t *__restrict__ lo,
-                                 int64_t n, Item *items) {
+                                 int64_t n, const PartSet *sets, int32_t n_sets, Item *items) {
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
        x += (int64_t)gridDim.x * blockDim.x) {
     Item it;
     it.hi = hi[x];
     it.lo = lo[x];
-    it.idx = (int32_t)x;
+    it.idx = (int32_t)(x - sets[set_of(sets, n_sets, x)].seq_begin);
     it.pad = 0;
     items[x] = it;
   }
 }
 
-// Segment s = [offs[s], offs[s+1]) if offs, else the floor block of s.
+// Segment s = items [offs[s], offs[s+1]), one block per segment.
 __global__ void __launch_bounds__(kSortThreads) seg_sort_kernel(Item *items, Item *scratch,
-                                                                 int64_t n, int32_t p,
-                                                                 const int32_t *offs) {
+                                                                 int64_t n_seg,
+                                                                 const int64_t *offs) {
   extern __shared__ Item sm[];
-  for (int32_t s = blockIdx.x; s < p; s += gridDim.x) {
-    const int64_t lo = offs ? (int64_t)offs[s] : block_lo(s, n, p);
-    const int64_t hi = offs ? (int64_t)offs[s + 1] : block_lo(s + 1, n, p);
+  for (int64_t s = blockIdx.x; s < n_seg; s += gridDim.x) {
+    const int64_t lo = offs[s], hi = offs[s + 1];
     cta_sort(items + lo, scratch + lo, hi - lo, sm);
   }
 }
 
-__global__ void __launch_bounds__(kSortThreads) samples_kernel(const Item *items, Item *Y,
-                                                                Item *Y2, Item *piv,
-                                                                int32_t *pivot_idx, int64_t n,
-                                                                int32_t p) {
+// One block per set: regular samples of the sorted blocks, sorted; pivots.
+__global__ void __launch_bounds__(kSortThreads) samples_kernel(const Item *items, Item *Y_all,
+                                                                Item *Y2_all, Item *piv_all,
+                                                                int32_t *pivot_idx,
+                                                                const PartSet *sets,
+                                                                int32_t n_sets) {
   extern __shared__ Item sm[];
-  const int64_t ns = (int64_t)p * (p - 1);
-  for (int64_t e = threadIdx.x; e < ns; e += blockDim.x) {
-    const int64_t b = e / (p - 1), j = e % (p - 1) + 1;
-    const int64_t lo = block_lo(b, n, p), w = block_lo(b + 1, n, p) - lo;
-    Y[e] = items[lo + j * w / p];
-  }
-  __syncthreads();
-  cta_sort(Y, Y2, ns, sm);
-  for (int64_t i = threadIdx.x; i < p - 1; i += blockDim.x) {
-    const Item y = Y[i * p + p / 2 - 1];  // Y_{(i)p + floor(p/2)}, 1-based
-    piv[i] = y;
-    if (pivot_idx) pivot_idx[i] = y.idx;
+  for (int32_t si = blockIdx.x; si < n_sets; si += gridDim.x) {
+    const PartSet S = sets[si];
+    const int64_t n = S.n, p = S.p;
+    if (p <= 1) continue;
+    Item *Y = Y_all + S.samp_base, *Y2 = Y2_all + S.samp_base, *piv = piv_all + S.piv_base;
+    const Item *it = items + S.seq_begin;
+    const int64_t ns = p * (p - 1);
+    for (int64_t e = threadIdx.x; e < ns; e += blockDim.x) {
+      const int64_t b = e / (p - 1), j = e % (p - 1) + 1;
+      const int64_t lo = block_lo(b, n, p), w = block_lo(b + 1, n, p) - lo;
+      Y[e] = it[lo + j * w / p];
+    }
+    __syncthreads();
+    cta_sort(Y, Y2, ns, sm);
+    for (int64_t i = threadIdx.x; i < p - 1; i += blockDim.x) {
+      const Item y = Y[i * p + p / 2 - 1];  // Y_{(i)p + floor(p/2)}, 1-based
+      piv[i] = y;
+      if (pivot_idx) pivot_idx[S.piv_base + i] = y.idx;
+    }
+    __syncthreads();
   }
 }
 
 // pos[b][i] = items of sorted block b that are <= y_i (i < p-1); pos[b][p-1] = w_b.
-__global__ void subblocks_kernel(const Item *items, const Item *piv, int32_t *pos, int64_t n,
-                                 int32_t p) {
-  const int64_t total = (int64_t)p * p;
+// blockIdx.y = set.
+__global__ void subblocks_kernel(const Item *items, const Item *piv_all, int32_t *pos_all,
+                                 const PartSet *sets) {
+  const PartSet S = sets[blockIdx.y];
+  const int64_t n = S.n, p = S.p, total = p * p;
+  const Item *it = items + S.seq_begin;
+  const Item *piv = piv_all + S.piv_base;
+  int32_t *pos = pos_all + S.pos_base;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b = e / p, i = e % p;
     const int64_t lo = block_lo(b, n, p), w = block_lo(b + 1, n, p) - lo;
-    pos[e] = (int32_t)(i == p - 1 ? w : count_not_greater(items + lo, w, piv[i]));
+    pos[e] = (int32_t)(i == p - 1 ? w : count_not_greater(it + lo, w, piv[i]));
   }
 }
 
-__global__ void __launch_bounds__(1024) bucket_scan_kernel(const int32_t *pos, int32_t *dest,
-                                                           int32_t *bucket_offsets, int32_t n,
-                                                           int32_t p) {
+// One block per set: bucket sizes, CSR offsets (local, written at blk_base + set),
+// the global start of every bucket (gbound) and of every sub-block (dest).
+__global__ void __launch_bounds__(1024) bucket_scan_kernel(const int32_t *pos_all,
+                                                           int32_t *dest_all,
+                                                           int32_t *bucket_offsets,
+                                                           int64_t *gbound,
+                                                           const PartSet *sets,
+                                                           int32_t n_sets) {
   __shared__ int32_t s_warp[32];
   __shared__ int32_t s_carry;
   const int tid = threadIdx.x;
-  if (tid == 0) s_carry = 0;
-  __syncthreads();
-  for (int base = 0; base < p; base += blockDim.x) {
-    const int i = base + tid;
-    int32_t size = 0;
-    if (i < p)
-      for (int b = 0; b < p; ++b)
-        size += pos[(int64_t)b * p + i] - (i > 0 ? pos[(int64_t)b * p + i - 1] : 0);
-    int32_t x = size;
-    for (int o = 1; o < 32; o <<= 1) {
-      const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if ((tid & 31) >= o) x += y;
-    }
-    if ((tid & 31) == 31) s_warp[tid >> 5] = x;
+  for (int32_t si = blockIdx.x; si < n_sets; si += gridDim.x) {
+    const PartSet S = sets[si];
+    const int p = S.p;
+    const int32_t *pos = pos_all + S.pos_base;
+    int32_t *dest = dest_all + S.pos_base;
+    int32_t *boff = bucket_offsets + S.blk_base + si;
+    if (tid == 0) s_carry = 0;
     __syncthreads();
-    if (tid < 32) {
-      int32_t w = s_warp[tid];
+    for (int base = 0; base < p; base += blockDim.x) {
+      const int i = base + tid;
+      int32_t size = 0;
+      if (i < p)
+        for (int b = 0; b < p; ++b)
+          size += pos[(int64_t)b * p + i] - (i > 0 ? pos[(int64_t)b * p + i - 1] : 0);
+      int32_t x = size;
       for (int o = 1; o < 32; o <<= 1) {
-        const int32_t y = __shfl_up_sync(0xffffffffu, w, o);
-        if (tid >= o) w += y;
+        const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if ((tid & 31) >= o) x += y;
       }
-      s_warp[tid] = w;
-    }
-    __syncthreads();
-    const int32_t incl = x + ((tid >> 5) > 0 ? s_warp[(tid >> 5) - 1] : 0) + s_carry;
-    if (i < p) {
-      int32_t at = incl - size;
-      bucket_offsets[i] = at;
-      for (int b = 0; b < p; ++b) {
-        dest[(int64_t)b * p + i] = at;
-        at += pos[(int64_t)b * p + i] - (i > 0 ? pos[(int64_t)b * p + i - 1] : 0);
+      if ((tid & 31) == 31) s_warp[tid >> 5] = x;
+      __syncthreads();
+      if (tid < 32) {
+        int32_t w = s_warp[tid];
+        for (int o = 1; o < 32; o <<= 1) {
+          const int32_t y = __shfl_up_sync(0xffffffffu, w, o);
+          if (tid >= o) w += y;
+        }
+        s_warp[tid] = w;
       }
+      __syncthreads();
+      const int32_t incl = x + ((tid >> 5) > 0 ? s_warp[(tid >> 5) - 1] : 0) + s_carry;
+      if (i < p) {
+        int32_t at = incl - size;
+        boff[i] = at;
+        gbound[S.blk_base + i] = S.seq_begin + at;
+        for (int b = 0; b < p; ++b) {
+          dest[(int64_t)b * p + i] = (int32_t)(S.seq_begin + at);
+          at += pos[(int64_t)b * p + i] - (i > 0 ? pos[(int64_t)b * p + i - 1] : 0);
+        }
+      }
+      __syncthreads();
+      if (tid == blockDim.x - 1) s_carry = incl;
+      __syncthreads();
     }
-    __syncthreads();
-    if (tid == blockDim.x - 1) s_carry = incl;
+    if (tid == 0) {
+      boff[p] = S.n;
+      gbound[S.blk_base + p] = S.seq_begin + S.n;
+    }
     __syncthreads();
   }
-  if (tid == 0) bucket_offsets[p] = n;
 }
 
-__global__ void scatter_kernel(const Item *items, Item *out, const int32_t *pos,
-                               const int32_t *dest, int64_t n, int32_t p) {
-  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+__global__ void scatter_kernel(const Item *items, Item *out, const int32_t *pos_all,
+                               const int32_t *dest_all, int64_t n_total, const PartSet *sets,
+                               int32_t n_sets) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n_total;
        x += (int64_t)gridDim.x * blockDim.x) {
-    int64_t b = x * p / n;
-    while (b + 1 < p && block_lo(b + 1, n, p) <= x) ++b;
-    while (b > 0 && block_lo(b, n, p) > x) --b;
-    const int64_t e = x - block_lo(b, n, p);
-    const int32_t *pb = pos + b * p;
-    int lo = 0, hi = p - 1;  // first i with e < pos[b][i]
+    const PartSet S = sets[set_of(sets, n_sets, x)];
+    const int64_t n = S.n, p = S.p, xl = x - S.seq_begin;
+    int64_t b = xl * p / n;
+    while (b + 1 < p && block_lo(b + 1, n, p) <= xl) ++b;
+    while (b > 0 && block_lo(b, n, p) > xl) --b;
+    const int64_t e = xl - block_lo(b, n, p);
+    const int32_t *pb = pos_all + S.pos_base + b * p;
+    int lo = 0, hi = (int)p - 1;  // first i with e < pos[b][i]
     while (lo < hi) {
       const int mid = (lo + hi) >> 1;
       if (e < pb[mid]) hi = mid; else lo = mid + 1;
     }
     const int64_t start = lo > 0 ? pb[lo - 1] : 0;
-    out[dest[b * p + lo] + (e - start)] = items[x];
+    out[dest_all[S.pos_base + b * p + lo] + (e - start)] = items[x];
   }
 }
 
@@ -256,11 +265,20 @@ bool g_sort_attr = false;
 
 }  // namespace
 
-int partition_launch(const uint64_t *key_hi, const uint64_t *key_lo, int32_t n, int32_t p,
-                     int32_t *bucket_offsets, int32_t *members, int32_t *pivot_idx, void *ws,
-                     cudaStream_t st) {
-  const PartLayout L = part_layout(n, p);
+// Partition of n_sets consecutive sets (sizes d_n / p per set d_p on the device; or
+// one set of n_single items into p_single buckets when d_n == nullptr). Outputs per
+// set s: bucket_offsets[blk_base_s + s ..] (p_s + 1 local offsets), members (local
+// indices, in the sets' item ranges), pivot_idx[piv_base_s ..] (p_s - 1).
+int partition_sets_launch(const uint64_t *key_hi, const uint64_t *key_lo, int32_t n_sets,
+                          const int32_t *d_n, const int32_t *d_p, int32_t n_single,
+                          int32_t p_single, const PartTotals &tot, int32_t max_p,
+                          int32_t *bucket_offsets, int32_t *members, int32_t *pivot_idx,
+                          void *ws, cudaStream_t st) {
+  const PartLayout L = part_layout_sets(n_sets, tot);
   uint8_t *b = static_cast<uint8_t *>(ws);
+  PartSet *sets = reinterpret_cast<PartSet *>(b + L.sets);
+  int64_t *segoff = reinterpret_cast<int64_t *>(b + L.segoff);
+  int64_t *gbound = reinterpret_cast<int64_t *>(b + L.gbound);
   Item *items = reinterpret_cast<Item *>(b + L.items);
   Item *items2 = reinterpret_cast<Item *>(b + L.items2);
   Item *Y = reinterpret_cast<Item *>(b + L.samples);
@@ -276,26 +294,43 @@ int partition_launch(const uint64_t *key_hi, const uint64_t *key_lo, int32_t n, 
       return SAD_ERR_CUDA;
     g_sort_attr = true;
   }
-  part_init_kernel<<<grid_for(n, 256), 256, 0, st>>>(key_hi, key_lo, n, items);
+  const int64_t n = tot.n;
+  const unsigned gsets = (unsigned)(n_sets < 65535 ? n_sets : 65535);
+  const unsigned gseg = (unsigned)(tot.p < 65535 * 4 ? tot.p : 65535 * 4);
+  part_setup_kernel<<<1, 1024, 0, st>>>(d_n, d_p, n_sets, n_single, p_single, sets, segoff);
   SAD_LAUNCH_CHECK();
-  seg_sort_kernel<<<(unsigned)p, kSortThreads, kSortSmem, st>>>(items, items2, n, p, nullptr);
+  part_init_kernel<<<grid_for(n, 256), 256, 0, st>>>(key_hi, key_lo, n, sets, n_sets, items);
   SAD_LAUNCH_CHECK();
-  if (p > 1) {
-    samples_kernel<<<1, kSortThreads, kSortSmem, st>>>(items, Y, Y2, piv, pivot_idx, n, p);
+  seg_sort_kernel<<<gseg, kSortThreads, kSortSmem, st>>>(items, items2, tot.p, segoff);
+  SAD_LAUNCH_CHECK();
+  if (max_p > 1) {
+    samples_kernel<<<gsets, kSortThreads, kSortSmem, st>>>(items, Y, Y2, piv, pivot_idx, sets,
+                                                           n_sets);
     SAD_LAUNCH_CHECK();
   }
-  subblocks_kernel<<<grid_for((int64_t)p * p, 256), 256, 0, st>>>(items, piv, pos, n, p);
+  {
+    const int64_t pp = (int64_t)max_p * max_p;
+    dim3 g((unsigned)((pp + 255) / 256 < 1024 ? (pp + 255) / 256 : 1024), (unsigned)n_sets);
+    subblocks_kernel<<<g, 256, 0, st>>>(items, piv, pos, sets);
+    SAD_LAUNCH_CHECK();
+  }
+  bucket_scan_kernel<<<gsets, 1024, 0, st>>>(pos, dest, bucket_offsets, gbound, sets, n_sets);
   SAD_LAUNCH_CHECK();
-  bucket_scan_kernel<<<1, 1024, 0, st>>>(pos, dest, bucket_offsets, n, p);
+  scatter_kernel<<<grid_for(n, 256), 256, 0, st>>>(items, items2, pos, dest, n, sets, n_sets);
   SAD_LAUNCH_CHECK();
-  scatter_kernel<<<grid_for(n, 256), 256, 0, st>>>(items, items2, pos, dest, n, p);
-  SAD_LAUNCH_CHECK();
-  seg_sort_kernel<<<(unsigned)p, kSortThreads, kSortSmem, st>>>(items2, items, n, p,
-                                                                  bucket_offsets);
+  seg_sort_kernel<<<gseg, kSortThreads, kSortSmem, st>>>(items2, items, tot.p, gbound);
   SAD_LAUNCH_CHECK();
   members_kernel<<<grid_for(n, 256), 256, 0, st>>>(items2, members, n);
   SAD_LAUNCH_CHECK();
   return SAD_OK;
+}
+
+int partition_launch(const uint64_t *key_hi, const uint64_t *key_lo, int32_t n, int32_t p,
+                     int32_t *bucket_offsets, int32_t *members, int32_t *pivot_idx, void *ws,
+                     cudaStream_t st) {
+  return partition_sets_launch(key_hi, key_lo, 1, nullptr, nullptr, n, p,
+                               part_totals_single(n, p), p, bucket_offsets, members, pivot_idx,
+                               ws, st);
 }
 
 }  // namespace sad

@@ -8,37 +8,45 @@ namespace sad {
 
 struct RankPtrs {
   WsHeader *hdr;
-  int32_t *T;            // [eps] largest count of each word
+  RankSet *sets;         // [n_sets]
+  int32_t *seq_set;      // [n_total] set of each input sequence (n_sets > 1 only)
+  int32_t *row_set;      // [rows_total] set of each stored row (n_sets > 1 only)
+  int32_t *T;            // [eps] largest count of each word over all sets
   int32_t *secend;       // [t_max + 1] end column of threshold section t
   int32_t *colmap;       // [K_cap] column -> word | threshold << 16
   int32_t *thist;        // [65537] histogram / cursor over T values
   int32_t *tau_sorted;   // [eps] words by decreasing T
-  int32_t *mhist;        // [65537] histogram / cursor over m = L - k + 1
-  int32_t *perm;         // [n_pad] stored row -> input index (-1 = padding)
-  int32_t *depth;        // [n_pad / 128] largest count in each 128-row block
-  uint4 *rec;            // [n_pad] division record of each stored row's m
-  int2 *tiles;           // [max_tiles] (I | J << 16, K chunks)
-  unsigned long long *acc;  // [n][3] 24-bit-limb accumulators of the keys
-  uint8_t *planes;       // [n_pad][K_cap] fp8 threshold planes (sections 1..depth)
-  // residual of the counts above the plane depth
-  int32_t *cnt_gt;       // [eps] sequences whose count of the word exceeds depth
-  int64_t *list_off;     // [eps + 1] start of each word's excess list
-  int64_t *pair_off;     // [eps + 1] start of each word's pair range
-  int32_t *cursor;       // [eps] fill cursor of the excess lists
+  int32_t *mhist;        // [65537] histogram / cursor over m = L - k + 1 (one set)
+  int32_t *perm;         // [rows_total] stored row -> input index (-1 = padding)
+  int32_t *depth;        // [rows_total / 128] largest count in each 128-row block
+  uint4 *rec;            // [rows_total] division record of each stored row's m
+  int2 *tiles;           // [tiles_total] (I | J << 16, K chunks), global block indices
+  unsigned long long *acc;  // [n_total][3] 24-bit-limb accumulators of the keys
+  uint8_t *planes;       // [rows_total][K_cap] fp8 threshold planes (sections 1..depth)
+  // residual of the counts above the plane depth, per (set, word)
+  int32_t *cnt_gt;       // [n_sets * eps] sequences whose count of the word exceeds depth
+  int64_t *list_off;     // [n_sets * eps + 1] start of each excess list
+  int64_t *pair_off;     // [n_sets * eps + 1] start of each list's pair range
+  int32_t *cursor;       // [n_sets * eps] fill cursor of the excess lists
   int2 *lists;           // [list_cap] (stored row, count - depth)
-  int32_t *tile_of;      // [(n_pad/128) x (n_pad/256)] tile index of block (I, J)
-  int32_t *block_of;     // [max_tiles] residual block of a tile, -1 = none
+  int32_t *tile_of;      // [tileof_total] tile index of set-local block (I, J)
+  int32_t *block_of;     // [tiles_total] residual block of a tile, -1 = none
   uint32_t *rblocks;     // [block_cap][128][256] u16 residual per pair (two per word)
-  int64_t n_pad, k_cap, list_cap, block_cap;
+  Item *sortbuf;         // [2 n_total] per-set length sort (n_sets > 1 only)
+  int64_t *scanblk;      // [2 x blocks] block totals of the excess-list scan
+  int64_t n_pad;         // rows_total: stored rows over all sets
+  int64_t n_total, n_sets, tiles_total, k_cap, list_cap, block_cap;
   int32_t depth_cap;     // 0 = all planes
 };
 
 RankPtrs rank_ptrs(void *ws, const RankLayout &L);
+// d_n: per-set sizes on the device (n_sets > 1), or nullptr for one set of n_total.
 int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *lengths,
-                     int32_t n, int32_t k, int32_t eps, int plan_only, cudaStream_t st);
-int rank_gemm_launch(const RankPtrs &P, int32_t n, cudaStream_t st);
-int rank_finalize_launch(const RankPtrs &P, int32_t n, uint64_t *key_hi, uint64_t *key_lo,
-                         double *rank, cudaStream_t st);
+                     const int32_t *d_n, int32_t k, int32_t eps, int plan_only,
+                     cudaStream_t st);
+int rank_gemm_launch(const RankPtrs &P, cudaStream_t st);
+int rank_finalize_launch(const RankPtrs &P, uint64_t *key_hi, uint64_t *key_lo, double *rank,
+                         cudaStream_t st);
 int64_t host_tile_count(int32_t n);
 
 }  // namespace sad

@@ -8,33 +8,37 @@
 // sections are the dense ones and a tile whose rows never count any word more
 // than d times only needs the first d sections (its K extent).
 //
-// Rows are stored in order of decreasing length (the order of equal lengths is
-// free: it changes no result), so that for every stored pair i <= j the Eq. 1
-// denominator is min(L_i, L_j) - k + 1 = m_j, the column's own value.
-//
 // Depth cap. Only the sections t = 1..D may be kept as planes (D = the plan's
 // depth; 0 keeps all). What the planes miss is exact too:
 //   min(a, b) = sum_{t=1..D} [a >= t][b >= t] + max(0, min(a, b) - D),
 // and the second term is nonzero only for words both sequences hold more than
-// D times. Each such word gets a list of (stored row, count - D); every pair in
-// a list adds min of the two excesses to that pair's residual, which is summed
-// into a dense 128 x 256 u16 block of its GEMM tile and added to the tile's
-// accumulator in the epilogue, before the floor.
+// D times. Each such (set, word) gets a list of (stored row, count - D); every
+// pair in a list adds min of the two excesses to that pair's residual, which is
+// summed into a dense 128 x 256 u16 block of its GEMM tile and added to the
+// tile's accumulator in the epilogue, before the floor.
+//
+// Sets. A call ranks one or more independent sets (a batch). Each set's rows are
+// stored contiguously (256-aligned) and its tiles only pair rows of that set, so
+// the GEMM is block-diagonal; the column layout is shared (T over all sets).
+// Within a set, rows are stored in order of decreasing length (the order of
+// equal lengths is free: it changes no result), so that for every stored pair
+// i <= j the Eq. 1 denominator is min(L_i, L_j) - k + 1 = m_j, the column's own.
 //
 // Kernels, in launch order:
+//   rank_setup     the set table (row, tile and tile-map bases per set)
+//   rank_setmaps   set index of every sequence and stored row (batches only)
 //   rank_init      zero the scratch regions of the workspace
-//   lengths_scan   m = L - k + 1, validation, histogram of m
+//   lengths        m = L - k + 1, validation, histogram of m (one set)
 //   colmax         T_tau = max_x c^x_tau, count validation, #{x : c^x_tau > D}
-//   colmap         t_max, section ends, K_eff at depth D, excess-list and pair
-//                  offsets, the column -> (tau, t) map
-//   lensort_scan   exclusive prefix over m in decreasing order
-//   lensort_place  row position of every sequence, per-row division records
+//   colmap         t_max, section ends, K_eff at depth D, the column map
+//   list_scan_*    offsets of the excess lists and of their pair ranges
+//   lensort_*      stored row of every sequence, per-row division records
 //   planes         P rows in fp8 e4m3 (0x38 = 1.0, 0x00 = 0.0), block depths,
 //                  excess-list entries
-//   tiles          the upper-triangle tile list with per-tile K extent
-//   residual_*     mark the tiles the residual touches, give them blocks, zero
-//                  the blocks, add every pair's contribution
+//   tiles          per set, the upper-triangle tile list with per-tile K extent
+//   residual_*     give residual blocks to tiles, zero them, add every pair
 #include "rank.cuh"
+#include "sort.cuh"
 
 namespace sad {
 
@@ -42,6 +46,9 @@ RankPtrs rank_ptrs(void *ws, const RankLayout &L) {
   uint8_t *b = static_cast<uint8_t *>(ws);
   RankPtrs P;
   P.hdr = reinterpret_cast<WsHeader *>(b);
+  P.sets = reinterpret_cast<RankSet *>(b + L.sets);
+  P.seq_set = reinterpret_cast<int32_t *>(b + L.seq_set);
+  P.row_set = reinterpret_cast<int32_t *>(b + L.row_set);
   P.T = reinterpret_cast<int32_t *>(b + L.T);
   P.secend = reinterpret_cast<int32_t *>(b + L.secend);
   P.colmap = reinterpret_cast<int32_t *>(b + L.colmap);
@@ -62,7 +69,12 @@ RankPtrs rank_ptrs(void *ws, const RankLayout &L) {
   P.tile_of = reinterpret_cast<int32_t *>(b + L.tile_of);
   P.block_of = reinterpret_cast<int32_t *>(b + L.block_of);
   P.rblocks = reinterpret_cast<uint32_t *>(b + L.rblocks);
-  P.n_pad = L.n_pad;
+  P.sortbuf = reinterpret_cast<Item *>(b + L.sortbuf);
+  P.scanblk = reinterpret_cast<int64_t *>(b + L.scanblk);
+  P.n_pad = L.shape.rows_total;
+  P.n_total = L.shape.n_total;
+  P.n_sets = L.shape.n_sets;
+  P.tiles_total = L.shape.tiles_total;
   P.k_cap = L.caps.k_cap;
   P.list_cap = L.caps.list_cap;
   P.block_cap = L.caps.block_cap;
@@ -105,18 +117,89 @@ __device__ __forceinline__ V block_scan_incl(V x, V *s_warp, V *total) {
   return r;
 }
 
-__global__ void rank_init_kernel(RankPtrs P, int32_t n, int32_t eps, int with_keys) {
+__device__ __forceinline__ int64_t dev_n_pad(int64_t n) {
+  return ((n > 0 ? n : 1) + kNPad - 1) / kNPad * kNPad;
+}
+
+__device__ __forceinline__ int64_t dev_tiles_of_set(int64_t n) {
+  const int64_t R = (n + kRowBlock - 1) / kRowBlock, C = (n + kColBlock - 1) / kColBlock;
+  int64_t total = 0;  // sum over I < R of max(0, C - floor(I / 2))
+  for (int64_t I = 0; I < R; ++I) {
+    const int64_t j0 = I / 2;
+    if (j0 < C) total += C - j0;
+  }
+  return total;
+}
+
+__device__ __forceinline__ int32_t set_of_seq(const RankPtrs &P, int64_t x) {
+  return P.n_sets > 1 ? P.seq_set[x] : 0;
+}
+
+__device__ __forceinline__ int32_t set_of_row(const RankPtrs &P, int64_t r) {
+  return P.n_sets > 1 ? P.row_set[r] : 0;
+}
+
+// One block: the set table (prefix sums of n, padded rows, tiles, tile-map size).
+__global__ void __launch_bounds__(1024) rank_setup_kernel(const int32_t *d_n, int32_t n1,
+                                                          RankPtrs P) {
+  __shared__ int64_t s_warp[32];
+  __shared__ int64_t s_c[4];
+  const int tid = threadIdx.x;
+  const int32_t S = (int32_t)P.n_sets;
+  if (tid < 4) s_c[tid] = 0;
+  __syncthreads();
+  for (int base = 0; base < S; base += blockDim.x) {
+    const int s = base + tid;
+    const int64_t n = s < S ? (d_n ? d_n[s] : n1) : 0;
+    const int64_t np = s < S ? dev_n_pad(n) : 0;
+    const int64_t v[4] = {n, np, s < S ? dev_tiles_of_set(n) : 0,
+                          (np / kRowBlock) * (np / kColBlock)};
+    int64_t ex[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      int64_t tot;
+      const int64_t incl = block_scan_incl<int64_t>(v[f], s_warp, &tot);
+      ex[f] = s_c[f] + incl - v[f];
+      __syncthreads();
+      if (tid == 0) s_c[f] += tot;
+      __syncthreads();
+    }
+    if (s < S) {
+      RankSet e;
+      e.seq_begin = ex[0];
+      e.row_base = ex[1];
+      e.tile_base = ex[2];
+      e.tileof_base = ex[3];
+      e.n = (int32_t)n;
+      e.pad = 0;
+      P.sets[s] = e;
+    }
+  }
+}
+
+// Set index of every input sequence and every stored row (batches only).
+__global__ void rank_setmaps_kernel(RankPtrs P) {
+  for (int32_t s = blockIdx.x; s < (int32_t)P.n_sets; s += gridDim.x) {
+    const RankSet e = P.sets[s];
+    for (int64_t i = threadIdx.x; i < e.n; i += blockDim.x) P.seq_set[e.seq_begin + i] = s;
+    const int64_t np = dev_n_pad(e.n);
+    for (int64_t i = threadIdx.x; i < np; i += blockDim.x) P.row_set[e.row_base + i] = s;
+  }
+}
+
+__global__ void rank_init_kernel(RankPtrs P, int32_t eps, int with_keys) {
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nt = (int64_t)gridDim.x * blockDim.x;
+  const int64_t we = P.n_sets * (int64_t)eps;
   zero_range(P.T, eps, tid, nt);
   zero_range(P.thist, kMaxM + 2, tid, nt);
   zero_range(P.mhist, kMaxM + 2, tid, nt);
   zero_range(P.secend, kMaxM + 2, tid, nt);
-  zero_range(P.cnt_gt, eps, tid, nt);
-  zero_range(P.cursor, eps, tid, nt);
+  zero_range(P.cnt_gt, we, tid, nt);
+  zero_range(P.cursor, we, tid, nt);
   if (with_keys) {
     zero_range(P.depth, P.n_pad / kRowBlock, tid, nt);
-    zero_range(P.acc, 3 * (int64_t)n, tid, nt);
+    zero_range(P.acc, 3 * P.n_total, tid, nt);
   }
   if (tid == 0) {
     P.hdr->k_eff = 0;
@@ -132,9 +215,8 @@ __global__ void rank_init_kernel(RankPtrs P, int32_t n, int32_t eps, int with_ke
   }
 }
 
-__global__ void lengths_kernel(const int32_t *__restrict__ lengths, int32_t n, int32_t k,
-                               RankPtrs P) {
-  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+__global__ void lengths_kernel(const int32_t *__restrict__ lengths, int32_t k, RankPtrs P) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < P.n_total;
        x += (int64_t)gridDim.x * blockDim.x) {
     const int32_t m = lengths[x] - k + 1;
     if (m < 1) {
@@ -142,49 +224,57 @@ __global__ void lengths_kernel(const int32_t *__restrict__ lengths, int32_t n, i
     } else if (m > kMaxM) {
       record_error(P.hdr, SAD_ERR_UNSUPPORTED, (int)x);
     } else {
-      atomicAdd(&P.mhist[m], 1);
+      if (P.n_sets == 1) atomicAdd(&P.mhist[m], 1);
       atomicMax(&P.hdr->m_max, m);
     }
   }
 }
 
-// T_tau = max over rows of counts[x][tau] and (D >= 1) the number of rows whose
-// count exceeds D. Block (256 words) x (row slice).
-__global__ void colmax_kernel(const int32_t *__restrict__ counts, int32_t n, int32_t eps,
-                              RankPtrs P) {
+// T_tau = max over rows of counts[x][tau] and (D >= 1) the number of rows of each
+// set whose count exceeds D. Block (256 words) x (row slice).
+__global__ void colmax_kernel(const int32_t *__restrict__ counts, int32_t eps, RankPtrs P) {
   const int32_t tau = blockIdx.x * blockDim.x + threadIdx.x;
   if (tau >= eps) return;
   const int32_t D = P.depth_cap;
-  const int64_t per = ((int64_t)n + gridDim.y - 1) / gridDim.y;
+  const int64_t n = P.n_total;
+  const int64_t per = (n + gridDim.y - 1) / gridDim.y;
   const int64_t r0 = (int64_t)blockIdx.y * per;
-  int64_t r1 = r0 + per;
-  if (r1 > n) r1 = n;
+  const int64_t r1 = r0 + per < n ? r0 + per : n;
   int32_t mx = 0, mn = 0, gt = 0;
+  int32_t cur = r0 < r1 ? set_of_seq(P, r0) : 0;
   int64_t r = r0;
-  for (; r + 4 <= r1; r += 4) {
-    const int32_t a = __ldg(counts + (r + 0) * eps + tau);
-    const int32_t b = __ldg(counts + (r + 1) * eps + tau);
-    const int32_t c = __ldg(counts + (r + 2) * eps + tau);
-    const int32_t d = __ldg(counts + (r + 3) * eps + tau);
-    mx = max(mx, max(max(a, b), max(c, d)));
-    mn = min(mn, min(min(a, b), min(c, d)));
-    gt += (a > D) + (b > D) + (c > D) + (d > D);
+  if (P.n_sets == 1) {
+    for (; r + 4 <= r1; r += 4) {
+      const int32_t a = __ldg(counts + (r + 0) * eps + tau);
+      const int32_t b = __ldg(counts + (r + 1) * eps + tau);
+      const int32_t c = __ldg(counts + (r + 2) * eps + tau);
+      const int32_t d = __ldg(counts + (r + 3) * eps + tau);
+      mx = max(mx, max(max(a, b), max(c, d)));
+      mn = min(mn, min(min(a, b), min(c, d)));
+      gt += (a > D) + (b > D) + (c > D) + (d > D);
+    }
   }
   for (; r < r1; ++r) {
     const int32_t a = __ldg(counts + r * eps + tau);
     mx = max(mx, a);
     mn = min(mn, a);
+    const int32_t s = set_of_seq(P, r);
+    if (s != cur) {
+      if (D >= 1 && gt) atomicAdd(&P.cnt_gt[(int64_t)cur * eps + tau], gt);
+      gt = 0;
+      cur = s;
+    }
     gt += a > D;
   }
   if (mn < 0) record_error(P.hdr, SAD_ERR_BAD_INPUT, tau);
   if (mx > kMaxM) record_error(P.hdr, SAD_ERR_UNSUPPORTED, tau);
   if (mx > 0) atomicMax(&P.T[tau], mx);
-  if (D >= 1 && gt > 0) atomicAdd(&P.cnt_gt[tau], gt);
+  if (D >= 1 && gt) atomicAdd(&P.cnt_gt[(int64_t)cur * eps + tau], gt);
 }
 
 // One block of 1024 threads: histogram of T, t_max, section ends secend[t] =
-// sum_{t'<=t} #{tau : T_tau >= t'}, K_eff, words sorted by decreasing T, and
-// (unless plan_only) the column map colmap[col] = tau | t << 16.
+// sum_{t'<=t} #{tau : T_tau >= t'}, K_eff at the depth cap, words sorted by
+// decreasing T, and (unless plan_only) the column map colmap[col] = tau | t << 16.
 __global__ void __launch_bounds__(1024) colmap_kernel(RankPtrs P, int32_t eps, int plan_only) {
   __shared__ int32_t s_tmax;
   __shared__ int32_t s_warp[32];
@@ -201,110 +291,46 @@ __global__ void __launch_bounds__(1024) colmap_kernel(RankPtrs P, int32_t eps, i
   atomicMax(&s_tmax, local_max);
   __syncthreads();
   const int32_t tmax = s_tmax;
-  // n_t = #{tau : T_tau >= t} = suffix sum of thist; secend = prefix sum of n_t.
-  // Two sequential scans over t = tmax..1 then 1..tmax, 1024 values per step.
-  // (a) suffix sums into secend[t] (temporarily n_t)
+  // n_t = #{tau : T_tau >= t} = suffix sum of thist (into secend[t]), then the
+  // prefix sums of n_t over t = 1..tmax (into secend[t]).
   if (tid == 0) s_carry = 0;
   __syncthreads();
   for (int base = tmax; base >= 1; base -= blockDim.x) {
     const int t = base - tid;
-    int32_t v = t >= 1 ? P.thist[t] : 0;
-    // inclusive scan over the block in thread order
-    int32_t x = v;
-    for (int o = 1; o < 32; o <<= 1) {
-      int32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if ((tid & 31) >= o) x += y;
-    }
-    if ((tid & 31) == 31) s_warp[tid >> 5] = x;
+    int32_t tot;
+    const int32_t incl = block_scan_incl<int32_t>(t >= 1 ? P.thist[t] : 0, s_warp, &tot);
+    if (t >= 1) P.secend[t] = s_carry + incl;  // n_t
     __syncthreads();
-    if (tid < 32) {
-      int32_t w = s_warp[tid];
-      for (int o = 1; o < 32; o <<= 1) {
-        int32_t y = __shfl_up_sync(0xffffffffu, w, o);
-        if (tid >= o) w += y;
-      }
-      s_warp[tid] = w;
-    }
-    __syncthreads();
-    const int32_t incl = x + ((tid >> 5) > 0 ? s_warp[(tid >> 5) - 1] : 0) + s_carry;
-    if (t >= 1) P.secend[t] = incl;  // n_t
-    __syncthreads();
-    if (tid == blockDim.x - 1) s_carry = incl;
+    if (tid == 0) s_carry += tot;
     __syncthreads();
   }
-  // (b) prefix sums of n_t over t = 1..tmax into secend[t]
   if (tid == 0) s_carry = 0;
   __syncthreads();
   for (int base = 1; base <= tmax; base += blockDim.x) {
     const int t = base + tid;
-    int32_t x = t <= tmax ? P.secend[t] : 0;
-    for (int o = 1; o < 32; o <<= 1) {
-      int32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if ((tid & 31) >= o) x += y;
-    }
-    if ((tid & 31) == 31) s_warp[tid >> 5] = x;
+    int32_t tot;
+    const int32_t incl = block_scan_incl<int32_t>(t <= tmax ? P.secend[t] : 0, s_warp, &tot);
+    if (t <= tmax) P.secend[t] = s_carry + incl;
     __syncthreads();
-    if (tid < 32) {
-      int32_t w = s_warp[tid];
-      for (int o = 1; o < 32; o <<= 1) {
-        int32_t y = __shfl_up_sync(0xffffffffu, w, o);
-        if (tid >= o) w += y;
-      }
-      s_warp[tid] = w;
-    }
-    __syncthreads();
-    const int32_t incl = x + ((tid >> 5) > 0 ? s_warp[(tid >> 5) - 1] : 0) + s_carry;
-    __syncthreads();
-    if (t <= tmax) P.secend[t] = incl;
-    if (tid == blockDim.x - 1) s_carry = incl;
+    if (tid == 0) s_carry += tot;
     __syncthreads();
   }
   if (tid == 0) P.secend[0] = 0;
   __syncthreads();
   // planes kept: sections 1..dkeep; a residual exists when some count exceeds it
   const int32_t dkeep = P.depth_cap >= 1 ? min(P.depth_cap, tmax) : tmax;
-  const bool residual = dkeep < tmax;
   const int64_t k_eff = dkeep >= 1 ? (int64_t)P.secend[dkeep] : 0;
   int64_t k_pad = (k_eff + kKChunk - 1) / kKChunk * kKChunk;
   if (k_pad < kKChunk) k_pad = kKChunk;
-  // excess lists: list_off = prefix of cnt_gt, pair_off = prefix of c (c + 1) / 2
-  __shared__ int64_t s_warp64[32];
-  __shared__ int64_t s_l, s_p;
   if (tid == 0) {
-    s_l = 0;
-    s_p = 0;
-  }
-  __syncthreads();
-  for (int base = 0; base < eps; base += blockDim.x) {
-    const int tau = base + tid;
-    const int64_t c = (residual && tau < eps) ? (int64_t)P.cnt_gt[tau] : 0;
-    int64_t tot_l, tot_p;
-    const int64_t il = block_scan_incl<int64_t>(c, s_warp64, &tot_l);
-    const int64_t ip = block_scan_incl<int64_t>(c * (c + 1) / 2, s_warp64, &tot_p);
-    if (tau < eps) {
-      P.list_off[tau] = s_l + il - c;
-      P.pair_off[tau] = s_p + ip - c * (c + 1) / 2;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      s_l += tot_l;
-      s_p += tot_p;
-    }
-    __syncthreads();
-  }
-  if (tid == 0) {
-    P.list_off[eps] = s_l;
-    P.pair_off[eps] = s_p;
     P.hdr->t_max = tmax;
     P.hdr->depth = dkeep;
     P.hdr->k_eff = k_eff;
     P.hdr->k_pad = (int32_t)k_pad;
-    P.hdr->list_total = s_l;
-    P.hdr->pairs_total = s_p;
   }
   if (plan_only) return;
-  if (k_pad > P.k_cap || s_l > P.list_cap || (residual && P.block_cap <= 0)) {
-    if (tid == 0) record_error(P.hdr, SAD_ERR_WORKSPACE, (int)(k_pad > P.k_cap ? k_pad : -1));
+  if (k_pad > P.k_cap) {
+    if (tid == 0) record_error(P.hdr, SAD_ERR_WORKSPACE, (int)k_pad);
     return;
   }
   // Words in decreasing T order (ties by word index): position of tau =
@@ -350,8 +376,106 @@ __global__ void __launch_bounds__(1024) colmap_kernel(RankPtrs P, int32_t eps, i
   }
 }
 
-// Exclusive prefix over m in decreasing order: mhist[m] := #{x : m_x > m}, for
-// m = m_max down to 1 (larger m are empty), 1024 consecutive values per step.
+// Offsets of the excess lists over all (set, word) entries w: list_off[w] =
+// prefix of c_w and pair_off[w] = prefix of c_w (c_w + 1) / 2, c_w = cnt_gt[w]
+// (0 when nothing is cut). Three passes: per-block totals, a scan of the block
+// totals, per-block scans with the block's carry.
+constexpr int kScanChunk = 4096;
+
+__device__ __forceinline__ bool residual_needed(const RankPtrs &P) {
+  return P.hdr->depth < P.hdr->t_max;
+}
+
+__global__ void __launch_bounds__(256) list_scan_reduce_kernel(RankPtrs P, int64_t we) {
+  __shared__ int64_t s_warp[32];
+  const bool on = residual_needed(P);
+  const int64_t b0 = (int64_t)blockIdx.x * kScanChunk;
+  int64_t sl = 0, sp = 0;
+  for (int64_t w = b0 + threadIdx.x; w < b0 + kScanChunk && w < we; w += blockDim.x) {
+    const int64_t c = on ? P.cnt_gt[w] : 0;
+    sl += c;
+    sp += c * (c + 1) / 2;
+  }
+  int64_t tl, tp;
+  block_scan_incl<int64_t>(sl, s_warp, &tl);
+  block_scan_incl<int64_t>(sp, s_warp, &tp);
+  if (threadIdx.x == 0) {
+    P.scanblk[2 * blockIdx.x] = tl;
+    P.scanblk[2 * blockIdx.x + 1] = tp;
+  }
+}
+
+__global__ void __launch_bounds__(1024) list_scan_top_kernel(RankPtrs P, int64_t nblk) {
+  __shared__ int64_t s_warp[32];
+  __shared__ int64_t s_l, s_p;
+  if (threadIdx.x == 0) {
+    s_l = 0;
+    s_p = 0;
+  }
+  __syncthreads();
+  for (int64_t base = 0; base < nblk; base += blockDim.x) {
+    const int64_t b = base + threadIdx.x;
+    const int64_t vl = b < nblk ? P.scanblk[2 * b] : 0;
+    const int64_t vp = b < nblk ? P.scanblk[2 * b + 1] : 0;
+    int64_t tl, tp;
+    const int64_t il = block_scan_incl<int64_t>(vl, s_warp, &tl);
+    const int64_t ip = block_scan_incl<int64_t>(vp, s_warp, &tp);
+    if (b < nblk) {
+      P.scanblk[2 * b] = s_l + il - vl;  // exclusive carry of block b
+      P.scanblk[2 * b + 1] = s_p + ip - vp;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_l += tl;
+      s_p += tp;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    P.hdr->list_total = s_l;
+    P.hdr->pairs_total = s_p;
+  }
+}
+
+__global__ void __launch_bounds__(256) list_scan_down_kernel(RankPtrs P, int64_t we,
+                                                             int plan_only) {
+  __shared__ int64_t s_warp[32];
+  __shared__ int64_t s_l, s_p;
+  const bool on = residual_needed(P);
+  const int64_t b0 = (int64_t)blockIdx.x * kScanChunk;
+  if (threadIdx.x == 0) {
+    s_l = P.scanblk[2 * blockIdx.x];
+    s_p = P.scanblk[2 * blockIdx.x + 1];
+  }
+  __syncthreads();
+  for (int64_t base = b0; base < b0 + kScanChunk && base < we; base += blockDim.x) {
+    const int64_t w = base + threadIdx.x;
+    const int64_t c = (on && w < we) ? P.cnt_gt[w] : 0;
+    const int64_t pc = c * (c + 1) / 2;
+    int64_t tl, tp;
+    const int64_t il = block_scan_incl<int64_t>(c, s_warp, &tl);
+    const int64_t ip = block_scan_incl<int64_t>(pc, s_warp, &tp);
+    if (w < we) {
+      P.list_off[w] = s_l + il - c;
+      P.pair_off[w] = s_p + ip - pc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_l += tl;
+      s_p += tp;
+    }
+    __syncthreads();
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+    P.list_off[we] = P.hdr->list_total;
+    P.pair_off[we] = P.hdr->pairs_total;
+    if (!plan_only && (P.hdr->list_total > P.list_cap || (on && P.block_cap <= 0)))
+      record_error(P.hdr, SAD_ERR_WORKSPACE, -1);
+  }
+}
+
+// One set: exclusive prefix over m in decreasing order, mhist[m] := #{x : m_x > m},
+// for m = m_max down to 1, 1024 consecutive values per step.
 __global__ void __launch_bounds__(1024) lensort_scan_kernel(RankPtrs P) {
   __shared__ int32_t s_warp[32];
   __shared__ int32_t s_carry;
@@ -388,11 +512,12 @@ __device__ __forceinline__ uint4 division_record(uint32_t d) {
                     d | (sh1 << 16) | (sh2 << 24));
 }
 
-__global__ void lensort_place_kernel(const int32_t *__restrict__ lengths, int32_t n, int32_t k,
+// One set: stored row of every sequence from the counting sort over m.
+__global__ void lensort_place_kernel(const int32_t *__restrict__ lengths, int32_t k,
                                      RankPtrs P) {
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < P.n_pad;
        x += (int64_t)gridDim.x * blockDim.x) {
-    if (x < n) {
+    if (x < P.n_total) {
       const int32_t m = lengths[x] - k + 1;
       if (m < 1 || m > kMaxM) continue;  // already recorded as an error
       const int32_t pos = atomicAdd(&P.mhist[m], 1);
@@ -405,15 +530,52 @@ __global__ void lensort_place_kernel(const int32_t *__restrict__ lengths, int32_
   }
 }
 
+// Batches: one block per set sorts the set's sequences by (decreasing m, index)
+// and places them (and the set's padding rows) at the set's rows.
+__global__ void __launch_bounds__(kSortThreads) lensort_sets_kernel(
+    const int32_t *__restrict__ lengths, int32_t k, RankPtrs P) {
+  extern __shared__ Item sm[];
+  Item *buf = P.sortbuf, *scratch = P.sortbuf + P.n_total;
+  for (int32_t s = blockIdx.x; s < (int32_t)P.n_sets; s += gridDim.x) {
+    const RankSet e = P.sets[s];
+    for (int64_t i = threadIdx.x; i < e.n; i += blockDim.x) {
+      const int32_t m = lengths[e.seq_begin + i] - k + 1;
+      Item it;
+      it.hi = (uint64_t)(kMaxM - min(max(m, 1), kMaxM));
+      it.lo = 0;
+      it.idx = (int32_t)i;
+      it.pad = 0;
+      buf[e.seq_begin + i] = it;
+    }
+    __syncthreads();
+    cta_sort(buf + e.seq_begin, scratch + e.seq_begin, e.n, sm);
+    const int64_t np = dev_n_pad(e.n);
+    for (int64_t i = threadIdx.x; i < np; i += blockDim.x) {
+      const int64_t row = e.row_base + i;
+      if (i < e.n) {
+        const int32_t x = buf[e.seq_begin + i].idx;
+        const int32_t m = lengths[e.seq_begin + x] - k + 1;
+        P.perm[row] = (int32_t)(e.seq_begin + x);
+        P.rec[row] = division_record((uint32_t)min(max(m, 1), kMaxM));
+      } else {
+        P.perm[row] = -1;
+        P.rec[row] = division_record(1u);
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // Plane rows, kPlaneRows stored rows per block iteration: stage the rows' counts
 // (as 16-bit) in shared memory with 16-byte loads, write their K_pad plane bytes
 // 16 at a time (the column map of a chunk is read once for all the rows), raise
-// the depth of each row's 128-row block to the row's largest count, and check
-// that the row's counts add up to its number of windows m.
+// the depth of each row's 128-row block to the row's largest count, check that
+// the row's counts add up to its number of windows m, and append its excess
+// entries (counts above the depth) to the (set, word) lists.
 constexpr int kPlaneRows = 2;
 
 __global__ void __launch_bounds__(256) planes_kernel(const int32_t *__restrict__ counts,
-                                                     int32_t n, int32_t eps, RankPtrs P) {
+                                                     int32_t eps, RankPtrs P) {
   extern __shared__ uint16_t s_cnt[];  // [kPlaneRows][eps]
   __shared__ int32_t s_max[kPlaneRows], s_sum[kPlaneRows];
   if (P.hdr->status != 0) return;
@@ -487,15 +649,17 @@ __global__ void __launch_bounds__(256) planes_kernel(const int32_t *__restrict__
     }
     __syncthreads();
     if (residual) {
-      // excess entries of both rows: (stored row, count - depth) per word above depth
+      // excess entries of the rows: (stored row, count - depth) per word above depth
 #pragma unroll
       for (int r = 0; r < kPlaneRows; ++r) {
         if (xs[r] < 0) continue;
+        const int64_t pos = g * kPlaneRows + r;
+        const int64_t wbase = (int64_t)set_of_row(P, pos) * eps;
         for (int tau = threadIdx.x; tau < eps; tau += blockDim.x) {
           const int32_t c = s_cnt[r * eps + tau];
           if (c > dkeep) {
-            const int32_t slot = atomicAdd(&P.cursor[tau], 1);
-            P.lists[P.list_off[tau] + slot] = make_int2((int32_t)(g * kPlaneRows + r), c - dkeep);
+            const int32_t slot = atomicAdd(&P.cursor[wbase + tau], 1);
+            P.lists[P.list_off[wbase + tau] + slot] = make_int2((int32_t)pos, c - dkeep);
           }
         }
       }
@@ -550,94 +714,87 @@ __global__ void __launch_bounds__(256) planes_kernel(const int32_t *__restrict__
   }
 }
 
-// Upper-triangle tile list. Tile (I, J) covers stored rows [128 I, 128 I + 128)
-// and columns [256 J, 256 J + 256); it is needed when some pair i <= j lies in
-// it (128 I <= 256 J + 255) and both ranges hold real rows. Tiles are grouped by
-// kGroupCols column blocks, rows ascending inside a group, so that the tiles
-// running at the same time share their operand panels in L2. Each entry is
-// (I | J << 16, K chunks), the K extent being the end of section
-// min(depth(I), depth(J)).
+// Upper-triangle tile list of every set (one block per set). Tile (I, J) of a
+// set covers its stored rows [128 I, 128 I + 128) and columns [256 J, 256 J + 256)
+// (set-local); it is needed when some pair i <= j lies in it (128 I <= 256 J + 255)
+// and both ranges hold real rows. Tiles are grouped by kGroupCols column blocks,
+// rows ascending inside a group, so that the tiles running at the same time share
+// their operand panels in L2. Each entry is (I | J << 16, K chunks) with global
+// block indices, the K extent being the end of section min(depth(I), depth(J), D).
 constexpr int kGroupCols = 8;
 
-__global__ void __launch_bounds__(1024) tiles_kernel(RankPtrs P, int32_t n) {
+__global__ void __launch_bounds__(1024) tiles_kernel(RankPtrs P) {
   __shared__ int32_t s_warp[32];
   __shared__ int32_t s_carry;
   const int tid = threadIdx.x;
-  const int32_t R = (n + kRowBlock - 1) / kRowBlock;
-  const int32_t C = (n + kColBlock - 1) / kColBlock;
   const int32_t nblk = (int32_t)(P.n_pad / kRowBlock);
-  const int32_t groups = (C + kGroupCols - 1) / kGroupCols;
-  if (tid == 0) s_carry = 0;
-  __syncthreads();
-  const int64_t rows_total = (int64_t)groups * R;
-  for (int64_t base = 0; base < rows_total; base += blockDim.x) {
-    const int64_t gi = base + tid;
-    int32_t g = 0, I = 0, j0 = 0, j1 = 0, cnt = 0;
-    if (gi < rows_total) {
-      g = (int32_t)(gi / R);
-      I = (int32_t)(gi % R);
-      j0 = max(g * kGroupCols, (I - 1 + 1) / 2);  // smallest J with I <= 2J + 1
-      j1 = min((g + 1) * kGroupCols, C);
-      cnt = max(0, j1 - j0);
-    }
-    int32_t x = cnt;
-    for (int o = 1; o < 32; o <<= 1) {
-      int32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if ((tid & 31) >= o) x += y;
-    }
-    if ((tid & 31) == 31) s_warp[tid >> 5] = x;
+  const int32_t dkeep = P.hdr->depth;
+  for (int32_t si = blockIdx.x; si < (int32_t)P.n_sets; si += gridDim.x) {
+    const RankSet e = P.sets[si];
+    const int32_t n = e.n;
+    const int32_t R = (n + kRowBlock - 1) / kRowBlock;
+    const int32_t C = (n + kColBlock - 1) / kColBlock;
+    const int64_t cfull = dev_n_pad(n) / kColBlock;
+    const int32_t I0 = (int32_t)(e.row_base / kRowBlock), J0 = (int32_t)(e.row_base / kColBlock);
+    const int32_t groups = (C + kGroupCols - 1) / kGroupCols;
+    if (tid == 0) s_carry = 0;
     __syncthreads();
-    if (tid < 32) {
-      int32_t w = s_warp[tid];
-      for (int o = 1; o < 32; o <<= 1) {
-        int32_t y = __shfl_up_sync(0xffffffffu, w, o);
-        if (tid >= o) w += y;
-      }
-      s_warp[tid] = w;
-    }
-    __syncthreads();
-    const int32_t incl = x + ((tid >> 5) > 0 ? s_warp[(tid >> 5) - 1] : 0) + s_carry;
-    int32_t out = incl - cnt;
-    const int32_t dI = P.depth[I];
-    const int32_t dkeep = P.hdr->depth;
-    const int64_t cfull = P.n_pad / kColBlock;
+    const int64_t rows_total = (int64_t)groups * R;
     unsigned long long chunks = 0;
-    for (int32_t J = j0; J < j1; ++J) {
-      const int32_t b0 = 2 * J, b1 = 2 * J + 1;
-      int32_t dJ = P.depth[b0];
-      if (b1 < nblk) dJ = max(dJ, P.depth[b1]);
-      const int32_t d = min(min(dI, dJ), dkeep);
-      const int32_t kend = P.secend[max(d, 0)];
-      const int32_t nk = max(1, (kend + kKChunk - 1) / kKChunk);
-      P.tile_of[(int64_t)I * cfull + J] = out;
-      P.block_of[out] = 0;
-      P.tiles[out++] = make_int2(I | (J << 16), nk);
-      chunks += (unsigned long long)nk;
+    for (int64_t base = 0; base < rows_total; base += blockDim.x) {
+      const int64_t gi = base + tid;
+      int32_t I = 0, j0 = 0, j1 = 0, cnt = 0;
+      if (gi < rows_total) {
+        const int32_t g = (int32_t)(gi / R);
+        I = (int32_t)(gi % R);
+        j0 = max(g * kGroupCols, I / 2);  // smallest J with I <= 2J + 1
+        j1 = min((g + 1) * kGroupCols, C);
+        cnt = max(0, j1 - j0);
+      }
+      int32_t tot;
+      const int32_t incl = block_scan_incl<int32_t>(cnt, s_warp, &tot);
+      int64_t out = e.tile_base + s_carry + incl - cnt;
+      const int32_t dI = P.depth[I0 + I];
+      for (int32_t J = j0; J < j1; ++J) {
+        const int32_t b0 = 2 * (J0 + J), b1 = b0 + 1;
+        int32_t dJ = P.depth[b0];
+        if (b1 < nblk) dJ = max(dJ, P.depth[b1]);
+        const int32_t d = min(min(dI, dJ), dkeep);
+        const int32_t kend = P.secend[max(d, 0)];
+        const int32_t nk = max(1, (kend + kKChunk - 1) / kKChunk);
+        P.tile_of[e.tileof_base + (int64_t)I * cfull + J] = (int32_t)out;
+        P.block_of[out] = 0;
+        P.tiles[out++] = make_int2((I0 + I) | ((J0 + J) << 16), nk);
+        chunks += (unsigned long long)nk;
+      }
+      __syncthreads();
+      if (tid == 0) s_carry += tot;
+      __syncthreads();
     }
     if (chunks) atomicAdd(&P.hdr->k_chunks, chunks);
-    __syncthreads();
-    if (tid == blockDim.x - 1) s_carry = incl;
+    if (tid == 0) atomicAdd(&P.hdr->n_tiles, s_carry);
     __syncthreads();
   }
-  if (tid == 0) P.hdr->n_tiles = s_carry;
 }
 
 // ------------------------------------------------------------- residual ----
-// One block per word (grid-stride): the word's excess list (stored row, count - D)
-// is staged in shared memory in chunks, and the block's threads walk the pairs
-// (u, v), u <= v, of the list. fn(tile, row in tile, column in tile, value) is
-// called once per pair with value = min of the two excesses; u == v is the
-// sequence's own pair.
+// One block per (set, word) (grid-stride): the excess list (stored row,
+// count - D) is staged in shared memory in chunks, and the block's threads walk
+// the pairs (u, v), u <= v, of the list. fn(tile, row in tile, column in tile,
+// value) is called once per pair with value = min of the two excesses; u == v is
+// the sequence's own pair.
 constexpr int kListChunk = 1024;
 
 template <typename Fn>
 __device__ __forceinline__ void for_each_residual_pair(const RankPtrs &P, int32_t eps, Fn fn) {
   __shared__ int2 s_u[kListChunk], s_v[kListChunk];
-  const int64_t cfull = P.n_pad / kColBlock;
-  for (int32_t tau = blockIdx.x; tau < eps; tau += gridDim.x) {
-    const int64_t base = P.list_off[tau];
-    const int64_t len = P.list_off[tau + 1] - base;
+  const int64_t we = P.n_sets * (int64_t)eps;
+  for (int64_t w = blockIdx.x; w < we; w += gridDim.x) {
+    const int64_t base = P.list_off[w];
+    const int64_t len = P.list_off[w + 1] - base;
     if (len == 0) continue;
+    const RankSet e = P.sets[w / eps];
+    const int64_t cfull = dev_n_pad(e.n) / kColBlock;
     // chunk pairs (cu, cv) of the list with cu <= cv; pairs u <= v within them
     for (int64_t cv = 0; cv < len; cv += kListChunk) {
       const int nv = (int)min((int64_t)kListChunk, len - cv);
@@ -649,14 +806,16 @@ __device__ __forceinline__ void for_each_residual_pair(const RankPtrs &P, int32_
         __syncthreads();
         const bool same = cu == cv;
         const int npairs = nu * nv;  // <= kListChunk^2
-        for (int e = threadIdx.x; e < npairs; e += blockDim.x) {
-          const int iu = e / nv, iv = e - iu * nv;
+        for (int q = threadIdx.x; q < npairs; q += blockDim.x) {
+          const int iu = q / nv, iv = q - iu * nv;
           if (same && iu > iv) continue;
           const int2 eu = same ? s_v[iu] : s_u[iu];
           const int2 ev = s_v[iv];
           const int32_t a = min(eu.x, ev.x), b = max(eu.x, ev.x);
-          const int32_t t = P.tile_of[(int64_t)(a / kRowBlock) * cfull + b / kColBlock];
-          fn(t, a % kRowBlock, b % kColBlock, (uint32_t)min(eu.y, ev.y));
+          const int64_t al = a - e.row_base, bl = b - e.row_base;
+          const int32_t t = P.tile_of[e.tileof_base + (al / kRowBlock) * cfull + bl / kColBlock];
+          fn(t, (int32_t)(al % kRowBlock), (int32_t)(bl % kColBlock),
+             (uint32_t)min(eu.y, ev.y));
         }
       }
       __syncthreads();
@@ -721,11 +880,11 @@ __global__ void __launch_bounds__(256) residual_add_kernel(RankPtrs P, int32_t e
   });
 }
 
-// key = acc0 + acc1 2^24 + acc2 2^48 (128-bit); rank = (hi + lo 2^-64) / N.
-__global__ void finalize_kernel(RankPtrs P, int32_t n, uint64_t *__restrict__ key_hi,
+// key = acc0 + acc1 2^24 + acc2 2^48 (128-bit); rank = (hi + lo 2^-64) / N of the set.
+__global__ void finalize_kernel(RankPtrs P, uint64_t *__restrict__ key_hi,
                                 uint64_t *__restrict__ key_lo, double *__restrict__ rank) {
   if (P.hdr->status != 0) return;
-  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < P.n_total;
        x += (int64_t)gridDim.x * blockDim.x) {
     const unsigned __int128 a0 = P.acc[3 * x + 0], a1 = P.acc[3 * x + 1], a2 = P.acc[3 * x + 2];
     const unsigned __int128 key = a0 + (a1 << 24) + (a2 << 48);
@@ -733,9 +892,10 @@ __global__ void finalize_kernel(RankPtrs P, int32_t n, uint64_t *__restrict__ ke
     key_hi[x] = hi;
     key_lo[x] = lo;
     if (rank) {
+      const double n = (double)P.sets[set_of_seq(P, x)].n;
       const double whole = __ull2double_rn(hi);
       const double frac = __dmul_rn(__ull2double_rn(lo), 0x1p-64);
-      rank[x] = __ddiv_rn(__dadd_rn(whole, frac), (double)n);
+      rank[x] = __ddiv_rn(__dadd_rn(whole, frac), n);
     }
   }
 }
@@ -748,14 +908,26 @@ inline unsigned grid_for(int64_t work, int threads, int cap_per_sm = 8) {
   return (unsigned)g;
 }
 
+bool g_attr_sort = false;
+
 }  // namespace
 
 int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *lengths,
-                     int32_t n, int32_t k, int32_t eps, int plan_only, cudaStream_t st) {
-  rank_init_kernel<<<grid_for(kMaxM + 2, 256), 256, 0, st>>>(P, n, eps, !plan_only);
+                     const int32_t *d_n, int32_t k, int32_t eps, int plan_only,
+                     cudaStream_t st) {
+  const int64_t n = P.n_total;
+  const unsigned gsets = (unsigned)(P.n_sets < 4096 ? P.n_sets : 4096);
+  rank_setup_kernel<<<1, 1024, 0, st>>>(d_n, (int32_t)n, P);
+  SAD_LAUNCH_CHECK();
+  if (P.n_sets > 1) {
+    rank_setmaps_kernel<<<gsets, 256, 0, st>>>(P);
+    SAD_LAUNCH_CHECK();
+  }
+  rank_init_kernel<<<grid_for(P.n_sets * (int64_t)eps + kMaxM, 256), 256, 0, st>>>(
+      P, eps, !plan_only);
   SAD_LAUNCH_CHECK();
   if (!plan_only) {
-    lengths_kernel<<<grid_for(n, 256), 256, 0, st>>>(lengths, n, k, P);
+    lengths_kernel<<<grid_for(n, 256), 256, 0, st>>>(lengths, k, P);
     SAD_LAUNCH_CHECK();
   }
   {
@@ -764,16 +936,37 @@ int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *le
     if (slices > (n + 63) / 64) slices = (n + 63) / 64;
     if (slices < 1) slices = 1;
     g.y = (unsigned)slices;
-    colmax_kernel<<<g, 256, 0, st>>>(counts, n, eps, P);
+    colmax_kernel<<<g, 256, 0, st>>>(counts, eps, P);
     SAD_LAUNCH_CHECK();
   }
   colmap_kernel<<<1, 1024, 0, st>>>(P, eps, plan_only);
   SAD_LAUNCH_CHECK();
+  {
+    const int64_t we = P.n_sets * (int64_t)eps;
+    const int64_t nblk = (we + kScanChunk - 1) / kScanChunk;
+    list_scan_reduce_kernel<<<(unsigned)nblk, 256, 0, st>>>(P, we);
+    SAD_LAUNCH_CHECK();
+    list_scan_top_kernel<<<1, 1024, 0, st>>>(P, nblk);
+    SAD_LAUNCH_CHECK();
+    list_scan_down_kernel<<<(unsigned)nblk, 256, 0, st>>>(P, we, plan_only);
+    SAD_LAUNCH_CHECK();
+  }
   if (plan_only) return SAD_OK;
-  lensort_scan_kernel<<<1, 1024, 0, st>>>(P);
-  SAD_LAUNCH_CHECK();
-  lensort_place_kernel<<<grid_for(P.n_pad, 256), 256, 0, st>>>(lengths, n, k, P);
-  SAD_LAUNCH_CHECK();
+  if (P.n_sets == 1) {
+    lensort_scan_kernel<<<1, 1024, 0, st>>>(P);
+    SAD_LAUNCH_CHECK();
+    lensort_place_kernel<<<grid_for(P.n_pad, 256), 256, 0, st>>>(lengths, k, P);
+    SAD_LAUNCH_CHECK();
+  } else {
+    if (!g_attr_sort) {
+      if (cudaFuncSetAttribute(lensort_sets_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kSortSmem) != cudaSuccess)
+        return SAD_ERR_CUDA;
+      g_attr_sort = true;
+    }
+    lensort_sets_kernel<<<gsets, kSortThreads, kSortSmem, st>>>(lengths, k, P);
+    SAD_LAUNCH_CHECK();
+  }
   {
     const size_t smem = sizeof(uint16_t) * (size_t)eps * kPlaneRows;
     if (cudaFuncSetAttribute(planes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -781,15 +974,16 @@ int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *le
       return SAD_ERR_CUDA;
     const int64_t groups = P.n_pad / kPlaneRows;
     const int64_t cap = (int64_t)num_sms() * 8;
-    planes_kernel<<<(unsigned)(groups < cap ? groups : cap), 256, smem, st>>>(counts, n, eps, P);
+    planes_kernel<<<(unsigned)(groups < cap ? groups : cap), 256, smem, st>>>(counts, eps, P);
     SAD_LAUNCH_CHECK();
   }
-  tiles_kernel<<<1, 1024, 0, st>>>(P, n);
+  tiles_kernel<<<gsets, 1024, 0, st>>>(P);
   SAD_LAUNCH_CHECK();
   if (P.depth_cap >= 1 && P.block_cap > 0) {
     // the residual only exists when the planes are cut below the largest count
-    const int identity = P.block_cap >= host_tile_count(n) ? 1 : 0;
-    const unsigned gw = (unsigned)(eps < num_sms() * 8 ? eps : num_sms() * 8);
+    const int identity = P.block_cap >= P.tiles_total ? 1 : 0;
+    const int64_t we = P.n_sets * (int64_t)eps;
+    const unsigned gw = (unsigned)(we < num_sms() * 8 ? we : num_sms() * 8);
     if (!identity) {
       residual_mark_kernel<<<gw, 256, 0, st>>>(P, eps);
       SAD_LAUNCH_CHECK();
@@ -804,22 +998,13 @@ int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *le
   return SAD_OK;
 }
 
-int rank_finalize_launch(const RankPtrs &P, int32_t n, uint64_t *key_hi, uint64_t *key_lo,
-                         double *rank, cudaStream_t st) {
-  finalize_kernel<<<grid_for(n, 256), 256, 0, st>>>(P, n, key_hi, key_lo, rank);
+int rank_finalize_launch(const RankPtrs &P, uint64_t *key_hi, uint64_t *key_lo, double *rank,
+                         cudaStream_t st) {
+  finalize_kernel<<<grid_for(P.n_total, 256), 256, 0, st>>>(P, key_hi, key_lo, rank);
   SAD_LAUNCH_CHECK();
   return SAD_OK;
 }
 
-int64_t host_tile_count(int32_t n) {
-  const int64_t R = (n + kRowBlock - 1) / kRowBlock;
-  const int64_t C = (n + kColBlock - 1) / kColBlock;
-  int64_t total = 0;
-  for (int64_t I = 0; I < R; ++I) {
-    const int64_t j0 = I / 2;  // smallest J with I <= 2J + 1
-    if (j0 < C) total += C - j0;
-  }
-  return total;
-}
+int64_t host_tile_count(int32_t n) { return tiles_of_set(n); }
 
 }  // namespace sad

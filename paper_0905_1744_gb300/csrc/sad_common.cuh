@@ -46,67 +46,6 @@ __device__ __forceinline__ void record_error(WsHeader *h, int code, int detail =
   if (atomicCAS(&h->status, 0, code) == 0) h->detail = detail;
 }
 
-// Capacities of the data-dependent regions of a rank workspace.
-struct RankCaps {
-  int32_t depth;         // planes kept per word; 0 = all (no residual)
-  int64_t k_cap;         // plane columns
-  int64_t list_cap;      // excess entries (sequence, word) with count > depth
-  int64_t block_cap;     // residual blocks of kRowBlock x kColBlock u16
-};
-
-constexpr size_t kResidualBlockBytes = 2 * 128 * 256;  // u16 per pair of a tile
-
-// Offsets of the rank workspace regions (bytes from the workspace base).
-struct RankLayout {
-  size_t T, secend, thist, tau_sorted, mhist, perm, rec, depth, tiles, acc, cnt_gt, list_off,
-      pair_off, cursor, tile_of, block_of, colmap, lists, planes, rblocks;
-  size_t fixed_bytes;    // everything that does not depend on the capacities
-  size_t bytes;          // total
-  int64_t n_pad, max_tiles;
-  RankCaps caps;
-};
-
-inline int64_t n_pad_of(int64_t n) { return (int64_t)align_up((size_t)(n > 0 ? n : 1), kNPad); }
-
-inline int64_t max_tiles_of(int64_t n_pad) {
-  return (n_pad / kRowBlock) * (n_pad / kColBlock);
-}
-
-inline RankLayout rank_layout(int64_t n, int64_t eps, const RankCaps &caps) {
-  RankLayout L{};
-  L.n_pad = n_pad_of(n);
-  L.caps = caps;
-  L.max_tiles = max_tiles_of(L.n_pad);
-  size_t o = sizeof(WsHeader);
-  auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes, 256); return r; };
-  L.T = take(sizeof(int32_t) * eps);
-  L.secend = take(sizeof(int32_t) * (kMaxM + 2));
-  L.thist = take(sizeof(int32_t) * (kMaxM + 2));
-  L.tau_sorted = take(sizeof(int32_t) * eps);
-  L.mhist = take(sizeof(int32_t) * (kMaxM + 2));
-  L.perm = take(sizeof(int32_t) * L.n_pad);
-  L.rec = take(16 * (size_t)L.n_pad);
-  L.depth = take(sizeof(int32_t) * (L.n_pad / kRowBlock));
-  L.tiles = take(2 * sizeof(int32_t) * L.max_tiles);
-  L.acc = take(3 * sizeof(uint64_t) * (size_t)(n > 0 ? n : 1));
-  L.cnt_gt = take(sizeof(int32_t) * eps);
-  L.list_off = take(sizeof(int64_t) * (eps + 1));
-  L.pair_off = take(sizeof(int64_t) * (eps + 1));
-  L.cursor = take(sizeof(int32_t) * eps);
-  L.tile_of = take(sizeof(int32_t) * L.max_tiles);
-  L.block_of = take(sizeof(int32_t) * L.max_tiles);
-  L.fixed_bytes = o;
-  L.colmap = take(sizeof(int32_t) * (size_t)(caps.k_cap > 0 ? caps.k_cap : 1));
-  L.lists = take(2 * sizeof(int32_t) * (size_t)(caps.list_cap > 0 ? caps.list_cap : 1));
-  o = align_up(o, 1024);
-  L.planes = o;
-  o = align_up(o + (size_t)L.n_pad * (size_t)caps.k_cap, 1024);
-  L.rblocks = o;
-  o += kResidualBlockBytes * (size_t)caps.block_cap;
-  L.bytes = align_up(o, 256);
-  return L;
-}
-
 // Item of the partition: a rank key and its input index.
 struct Item {
   uint64_t hi, lo;
@@ -120,25 +59,158 @@ __host__ __device__ __forceinline__ bool item_less(const Item &a, const Item &b)
   return a.idx < b.idx;
 }
 
+// Capacities of the data-dependent regions of a rank workspace.
+struct RankCaps {
+  int32_t depth;         // planes kept per word; 0 = all (no residual)
+  int64_t k_cap;         // plane columns
+  int64_t list_cap;      // excess entries (sequence, word) with count > depth
+  int64_t block_cap;     // residual blocks of kRowBlock x kColBlock u16
+};
+
+constexpr size_t kResidualBlockBytes = 2 * 128 * 256;  // u16 per pair of a tile
+
+// One set of a (possibly batched) rank call, built on the device by rank_setup.
+// Sets are consecutive in the input order; each set's stored rows are a
+// contiguous, 256-aligned range of the global plane matrix, so every GEMM tile
+// stays inside one set (the batch is block-diagonal).
+struct RankSet {
+  int64_t seq_begin;     // first input sequence of the set
+  int64_t row_base;      // first stored row (multiple of 256)
+  int64_t tile_base;     // first entry of the set's tiles in the tile list
+  int64_t tileof_base;   // first entry of the set's (I, J) -> tile map
+  int32_t n, pad;
+};
+
+// Sizes of a rank call that the host knows before launching.
+struct RankShape {
+  int64_t n_sets, n_total, rows_total, tiles_total, tileof_total;
+};
+
+inline int64_t n_pad_of(int64_t n) { return (int64_t)align_up((size_t)(n > 0 ? n : 1), kNPad); }
+
+inline int64_t tiles_of_set(int64_t n) {
+  const int64_t R = (n + kRowBlock - 1) / kRowBlock, C = (n + kColBlock - 1) / kColBlock;
+  int64_t total = 0;
+  for (int64_t I = 0; I < R; ++I) {
+    const int64_t j0 = I / 2;  // smallest J with I <= 2J + 1
+    if (j0 < C) total += C - j0;
+  }
+  return total;
+}
+
+inline void shape_add_set(RankShape &sh, int64_t n) {
+  const int64_t np = n_pad_of(n);
+  sh.n_sets += 1;
+  sh.n_total += n;
+  sh.rows_total += np;
+  sh.tiles_total += tiles_of_set(n);
+  sh.tileof_total += (np / kRowBlock) * (np / kColBlock);
+}
+
+inline RankShape shape_single(int64_t n) {
+  RankShape sh{0, 0, 0, 0, 0};
+  shape_add_set(sh, n);
+  return sh;
+}
+
+// Offsets of the rank workspace regions (bytes from the workspace base).
+struct RankLayout {
+  size_t sets, seq_set, row_set, T, secend, thist, tau_sorted, mhist, perm, rec, depth, tiles,
+      acc, cnt_gt, list_off, pair_off, cursor, tile_of, block_of, sortbuf, scanblk, colmap, lists,
+      planes, rblocks;
+  size_t fixed_bytes;    // everything that does not depend on the capacities
+  size_t bytes;          // total
+  RankShape shape;
+  RankCaps caps;
+};
+
+inline RankLayout rank_layout(const RankShape &sh, int64_t eps, const RankCaps &caps) {
+  RankLayout L{};
+  L.shape = sh;
+  L.caps = caps;
+  size_t o = sizeof(WsHeader);
+  auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes, 256); return r; };
+  auto nz = [](int64_t x) { return (size_t)(x > 0 ? x : 1); };
+  const size_t we = (size_t)sh.n_sets * (size_t)eps;  // (set, word) entries
+  L.sets = take(sizeof(RankSet) * nz(sh.n_sets));
+  L.seq_set = take(sizeof(int32_t) * nz(sh.n_total));
+  L.row_set = take(sizeof(int32_t) * nz(sh.rows_total));
+  L.T = take(sizeof(int32_t) * eps);
+  L.secend = take(sizeof(int32_t) * (kMaxM + 2));
+  L.thist = take(sizeof(int32_t) * (kMaxM + 2));
+  L.tau_sorted = take(sizeof(int32_t) * eps);
+  L.mhist = take(sizeof(int32_t) * (kMaxM + 2));
+  L.perm = take(sizeof(int32_t) * nz(sh.rows_total));
+  L.rec = take(16 * nz(sh.rows_total));
+  L.depth = take(sizeof(int32_t) * nz(sh.rows_total / kRowBlock));
+  L.tiles = take(2 * sizeof(int32_t) * nz(sh.tiles_total));
+  L.acc = take(3 * sizeof(uint64_t) * nz(sh.n_total));
+  L.cnt_gt = take(sizeof(int32_t) * we);
+  L.list_off = take(sizeof(int64_t) * (we + 1));
+  L.pair_off = take(sizeof(int64_t) * (we + 1));
+  L.cursor = take(sizeof(int32_t) * we);
+  L.tile_of = take(sizeof(int32_t) * nz(sh.tileof_total));
+  L.block_of = take(sizeof(int32_t) * nz(sh.tiles_total));
+  L.sortbuf = take(sh.n_sets > 1 ? 2 * sizeof(Item) * nz(sh.n_total) : 256);
+  L.scanblk = take(2 * sizeof(int64_t) * (we / 4096 + 1));
+  L.fixed_bytes = o;
+  L.colmap = take(sizeof(int32_t) * (size_t)(caps.k_cap > 0 ? caps.k_cap : 1));
+  L.lists = take(2 * sizeof(int32_t) * (size_t)(caps.list_cap > 0 ? caps.list_cap : 1));
+  o = align_up(o, 1024);
+  L.planes = o;
+  o = align_up(o + (size_t)sh.rows_total * (size_t)caps.k_cap, 1024);
+  L.rblocks = o;
+  o += kResidualBlockBytes * (size_t)caps.block_cap;
+  L.bytes = align_up(o, 256);
+  return L;
+}
+
+
+// One set of a (possibly batched) partition, built on the device by part_setup.
+// Sets are consecutive in the item order.
+struct PartSet {
+  int64_t seq_begin;     // first item of the set
+  int32_t n, p;          // items, buckets
+  int64_t blk_base;      // first block / bucket segment: prefix of p
+  int64_t piv_base;      // prefix of p - 1
+  int64_t samp_base;     // prefix of p (p - 1)
+  int64_t pos_base;      // prefix of p * p
+};
+
+struct PartTotals {
+  int64_t n, p, p1, pp1, pp;  // sums over sets of n, p, p - 1, p (p - 1), p^2
+};
+
+inline PartTotals part_totals_single(int64_t n, int64_t p) {
+  return PartTotals{n, p, p - 1, p * (p - 1), p * p};
+}
+
 struct PartLayout {
-  size_t items, items2, samples, samples2, pos, dest, pivots;
+  size_t sets, segoff, gbound, items, items2, samples, samples2, pos, dest, pivots;
   size_t bytes;
 };
 
-inline PartLayout part_layout(int64_t n, int64_t p) {
+inline PartLayout part_layout_sets(int64_t n_sets, const PartTotals &t) {
   PartLayout L{};
   size_t o = sizeof(WsHeader);
   auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes, 256); return r; };
-  int64_t ns = p * (p - 1);
-  L.items = take(sizeof(Item) * (size_t)(n > 0 ? n : 1));
-  L.items2 = take(sizeof(Item) * (size_t)(n > 0 ? n : 1));
-  L.samples = take(sizeof(Item) * (size_t)(ns > 0 ? ns : 1));
-  L.samples2 = take(sizeof(Item) * (size_t)(ns > 0 ? ns : 1));
-  L.pos = take(sizeof(int32_t) * (size_t)(p * p));
-  L.dest = take(sizeof(int32_t) * (size_t)(p * p));
-  L.pivots = take(sizeof(Item) * (size_t)(p > 1 ? p - 1 : 1));
+  auto nz = [](int64_t x) { return (size_t)(x > 0 ? x : 1); };
+  L.sets = take(sizeof(PartSet) * nz(n_sets));
+  L.segoff = take(sizeof(int64_t) * (size_t)(t.p + 1));
+  L.gbound = take(sizeof(int64_t) * (size_t)(t.p + 1));
+  L.items = take(sizeof(Item) * nz(t.n));
+  L.items2 = take(sizeof(Item) * nz(t.n));
+  L.samples = take(sizeof(Item) * nz(t.pp1));
+  L.samples2 = take(sizeof(Item) * nz(t.pp1));
+  L.pos = take(sizeof(int32_t) * nz(t.pp));
+  L.dest = take(sizeof(int32_t) * nz(t.pp));
+  L.pivots = take(sizeof(Item) * nz(t.p1));
   L.bytes = o;
   return L;
+}
+
+inline PartLayout part_layout(int64_t n, int64_t p) {
+  return part_layout_sets(1, part_totals_single(n, p));
 }
 
 // ------------------------------------------------------ host bookkeeping ----

@@ -34,6 +34,16 @@ class RankPlan(ctypes.Structure):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
 
 
+class BatchPlan(ctypes.Structure):
+    """sad_batch_plan (see include/sad.h)."""
+    _fields_ = [("rank", RankPlan), ("n_sets", ctypes.c_int32), ("max_p", ctypes.c_int32),
+                ("n_total", ctypes.c_int64), ("rows_total", ctypes.c_int64),
+                ("tiles_total", ctypes.c_int64), ("tileof_total", ctypes.c_int64),
+                ("sum_p", ctypes.c_int64), ("sum_p1", ctypes.c_int64),
+                ("sum_pp1", ctypes.c_int64), ("sum_pp", ctypes.c_int64),
+                ("part_ws_bytes", ctypes.c_size_t)]
+
+
 class SadError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -73,6 +83,15 @@ def _load():
         lib.partition.restype = ctypes.c_int
         lib.sad_status_read.argtypes = [P, i32, P]
         lib.sad_status_read.restype = ctypes.c_int
+        lib.sad_batch_plan_make.argtypes = [P, P, P, P, i32, i32, i32, ctypes.POINTER(BatchPlan),
+                                            P, sz, P]
+        lib.sad_batch_plan_make.restype = ctypes.c_int
+        lib.sad_batch_rank.argtypes = [P, P, P, i32, i32, ctypes.POINTER(BatchPlan), P, P, P, P,
+                                       sz, P]
+        lib.sad_batch_rank.restype = ctypes.c_int
+        lib.sad_batch_partition.argtypes = [P, P, P, P, ctypes.POINTER(BatchPlan), P, P, P, P, sz,
+                                            P]
+        lib.sad_batch_partition.restype = ctypes.c_int
         lib.partition_noalloc.argtypes = [P, P, i32, i32, P, P, P, P]
         lib.partition_noalloc.restype = ctypes.c_int
         lib.sad_rank_info.argtypes = [P, ctypes.POINTER(i64), P]
@@ -276,3 +295,137 @@ def partition_noalloc(key_hi: torch.Tensor, key_lo: torch.Tensor, p: int, stream
                                      _ptr(piv) if p > 1 else None, _stream(stream)),
            "partition_noalloc")
     return offs, mem[:n], piv[:max(p - 1, 0)]
+
+
+class Batch:
+    """Many independent sequence sets ranked and partitioned together.
+
+    ``sets``: objects with ``codes`` (uint8), ``offsets`` (int64, N+1) and ``p``.
+    All sets share one count launch, one block-diagonal rank (one persistent
+    GEMM launch over every set's tiles) and one batched partition. ``plan()``
+    sizes everything (synchronous); ``run()`` then launches without any host
+    synchronisation, so ``capture()`` can record it in a CUDA graph and
+    ``replay()`` re-runs the whole batch with one graph launch.
+    """
+
+    def __init__(self, sets, device=None, k: int = 3, alphabet: int = 20):
+        import numpy as np
+        self.device = torch.device(device or "cuda")
+        self.k, self.alphabet = k, alphabet
+        self.n = np.array([s.offsets.shape[0] - 1 for s in sets], dtype=np.int32)
+        self.p = np.array([s.p for s in sets], dtype=np.int32)
+        lens = [np.diff(s.offsets) for s in sets]
+        codes = np.concatenate([s.codes[s.offsets[0]:s.offsets[-1]] for s in sets])
+        offsets = np.zeros(int(self.n.sum()) + 1, dtype=np.int64)
+        np.cumsum(np.concatenate(lens), out=offsets[1:])
+        self.seq_begin = np.concatenate([[0], np.cumsum(self.n)]).astype(np.int64)
+        self.boff_begin = np.concatenate([[0], np.cumsum(self.p + 1)]).astype(np.int64)
+        self.piv_begin = np.concatenate([[0], np.cumsum(self.p - 1)]).astype(np.int64)
+        self.h_codes, self.h_offsets = codes, offsets
+        dev = self.device
+        self.codes = torch.from_numpy(codes).to(dev)
+        self.offsets = torch.from_numpy(offsets).to(dev)
+        self.lengths = torch.from_numpy(np.concatenate(lens).astype(np.int32)).to(dev)
+        self.d_n = torch.from_numpy(self.n).to(dev)
+        self.d_p = torch.from_numpy(self.p).to(dev)
+        nt = int(self.n.sum())
+        self.counts = torch.empty((nt, alphabet ** k), dtype=torch.int32, device=dev)
+        self.key_hi = torch.empty(nt, dtype=torch.uint64, device=dev)
+        self.key_lo = torch.empty(nt, dtype=torch.uint64, device=dev)
+        self.rank = torch.empty(nt, dtype=torch.float64, device=dev)
+        self.bucket_offsets = torch.empty(int(self.boff_begin[-1]), dtype=torch.int32, device=dev)
+        self.members = torch.empty(nt, dtype=torch.int32, device=dev)
+        self.pivot_idx = torch.empty(max(int(self.piv_begin[-1]), 1), dtype=torch.int32,
+                                     device=dev)
+        self.ws_count = Workspace(dev, 256)
+        self.ws_rank = Workspace(dev)
+        self.ws_part = Workspace(dev)
+        self.plan_ = None
+        self.graph = None
+
+    @property
+    def n_sets(self) -> int:
+        return int(self.n.shape[0])
+
+    def count(self, stream=None):
+        kmer_count(self.codes, self.offsets, self.k, self.alphabet, ws=self.ws_count,
+                   out=self.counts, stream=stream, check=False)
+
+    def plan(self, depth: int = 0, stream=None) -> BatchPlan:
+        """Counts the batch and sizes the rank and partition workspaces (synchronous)."""
+        import numpy as np
+        self.count(stream)
+        self.ws_count.check("kmer_count (batch)", stream)
+        plan = BatchPlan()
+        plan.rank.depth = int(depth)
+        h_n = np.ascontiguousarray(self.n)
+        h_p = np.ascontiguousarray(self.p)
+        args = (_ptr(self.counts), h_n.ctypes.data_as(ctypes.c_void_p),
+                h_p.ctypes.data_as(ctypes.c_void_p), _ptr(self.d_n), self.n_sets, self.k,
+                self.alphabet, ctypes.byref(plan))
+        self.ws_rank.ensure(256)
+        rc = _load().sad_batch_plan_make(*args, _ptr(self.ws_rank.buf), self.ws_rank.nbytes,
+                                         _stream(stream))
+        if rc == ERR_WORKSPACE:
+            self.ws_rank.ensure(plan.rank.ws_bytes)
+            plan.rank.depth = int(depth)
+            rc = _load().sad_batch_plan_make(*args, _ptr(self.ws_rank.buf), self.ws_rank.nbytes,
+                                             _stream(stream))
+        _check(rc, "sad_batch_plan_make")
+        self.ws_rank.ensure(plan.rank.ws_bytes)
+        self.ws_part.ensure(plan.part_ws_bytes)
+        self.plan_ = plan
+        self.graph = None
+        return plan
+
+    def run(self, stream=None, count: bool = True):
+        """count -> rank -> partition of every set; no host synchronisation."""
+        if self.plan_ is None:
+            raise RuntimeError("Batch.plan() first")
+        lib, st = _load(), _stream(stream)
+        if count:
+            self.count(stream)
+        _check(lib.sad_batch_rank(_ptr(self.counts), _ptr(self.lengths), _ptr(self.d_n),
+                                  self.k, self.alphabet, ctypes.byref(self.plan_),
+                                  _ptr(self.key_hi), _ptr(self.key_lo), _ptr(self.rank),
+                                  _ptr(self.ws_rank.buf), self.ws_rank.nbytes, st),
+               "sad_batch_rank")
+        _check(lib.sad_batch_partition(_ptr(self.key_hi), _ptr(self.key_lo), _ptr(self.d_n),
+                                       _ptr(self.d_p), ctypes.byref(self.plan_),
+                                       _ptr(self.bucket_offsets), _ptr(self.members),
+                                       _ptr(self.pivot_idx), _ptr(self.ws_part.buf),
+                                       self.ws_part.nbytes, st), "sad_batch_partition")
+
+    def capture(self):
+        """Records run() in a CUDA graph (after one eager run)."""
+        self.run()
+        torch.cuda.synchronize(self.device)
+        self.check()
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream(self.device)
+        s.wait_stream(torch.cuda.current_stream(self.device))
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                self.run(stream=s)
+        torch.cuda.current_stream(self.device).wait_stream(s)
+        self.graph = g
+        return g
+
+    def replay(self):
+        self.graph.replay()
+
+    def check(self, stream=None):
+        self.ws_count.check("kmer_count (batch)", stream)
+        self.ws_rank.check("sad_batch_rank", stream)
+        self.ws_part.check("sad_batch_partition", stream)
+
+    def result(self, s: int) -> dict:
+        """Host copies of set s's outputs."""
+        a, b = int(self.seq_begin[s]), int(self.seq_begin[s + 1])
+        oa, ob = int(self.boff_begin[s]), int(self.boff_begin[s + 1])
+        pa, pb = int(self.piv_begin[s]), int(self.piv_begin[s + 1])
+        return dict(counts=self.counts[a:b].cpu().numpy(), key_hi=self.key_hi[a:b].cpu().numpy(),
+                    key_lo=self.key_lo[a:b].cpu().numpy(), rank=self.rank[a:b].cpu().numpy(),
+                    bucket_offsets=self.bucket_offsets[oa:ob].cpu().numpy(),
+                    members=self.members[a:b].cpu().numpy(),
+                    pivot_idx=self.pivot_idx[pa:pb].cpu().numpy())
