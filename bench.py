@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--depth", type=int, default=None,
                     help="threshold-plane depth (default: the autotuner's choice)")
+    ap.add_argument("--no-batching", action="store_true")
+    ap.add_argument("--batch-sets", type=int, default=512)
+    ap.add_argument("--batch-reps", type=int, default=10)
     return ap.parse_args()
 
 
@@ -240,6 +243,77 @@ def gemm_traffic_per_launch(n: int, k_eff: int):
     return d.get("dram_bytes_per_launch")
 
 
+def run_batching(args, dev):
+    """512 uneven sets: one plan, one captured CUDA graph per batch (count ->
+    block-diagonal rank -> batched partition), against the plain per-set path."""
+    import torch
+
+    from paper_0905_1744_gb300 import sad
+    sets = datagen.config4(args.seed, n_sets=args.batch_sets)
+    n = np.array([x.n for x in sets], dtype=np.int64)
+    pairs = float((n * (n - 1) // 2).sum())
+    b = sad.Batch(sets, device=dev)
+    # plane depth for the whole batch: timed eager runs of each candidate
+    trials = {}
+    for d in (1, 2, 3, 0):
+        b.plan(depth=d)
+        b.run()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.run()
+        e1.record()
+        e1.synchronize()
+        b.check()
+        trials[d] = e0.elapsed_time(e1)
+    depth = min(trials, key=trials.get)
+    plan = b.plan(depth=depth)
+    b.capture()
+    for _ in range(3):
+        b.replay()
+    torch.cuda.synchronize(dev)
+    times = []
+    for _ in range(args.batch_reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.replay()
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    b.check()
+    ms = statistics.median(times)
+    # plain per-set path: the public per-set call, one set after the other
+    ws = sad.Workspace(dev)
+    d_sets = [(torch.from_numpy(x.codes).to(dev), torch.from_numpy(x.offsets).to(dev), x.p)
+              for x in sets]
+    torch.cuda.synchronize(dev)
+    for c, o, p in d_sets[:4]:
+        sad.partition_set(c, o, p, ws=ws, depth=depth)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    plain = [sad.partition_set(c, o, p, ws=ws, depth=depth) for c, o, p in d_sets]
+    torch.cuda.synchronize(dev)
+    t_plain = time.perf_counter() - t0
+    exact = True
+    for i in range(0, len(sets), max(1, len(sets) // 16)):
+        got = b.result(i)
+        for key in ("key_hi", "key_lo", "bucket_offsets", "members", "pivot_idx"):
+            exact &= bool(np.array_equal(got[key], plain[i][key].cpu().numpy()))
+    return {
+        "workload": f"{len(sets)} sets, N log-uniform 50-5000, L log-uniform 50-2000, "
+                    "5-100 families per set, p = ceil(N/500)",
+        "sets": len(sets), "sequences": int(n.sum()), "pairs": pairs,
+        "ms_per_batch": ms, "sets_per_s": len(sets) / (ms / 1e3),
+        "pairs_per_s": pairs / (ms / 1e3),
+        "plain_ms_per_batch": 1e3 * t_plain, "plain_sets_per_s": len(sets) / t_plain,
+        "speedup_vs_plain": (t_plain * 1e3) / ms,
+        "depth": depth, "depth_trials_ms": {str(k): v for k, v in trials.items()},
+        "graph": "one CUDA graph replay per batch",
+        "rows": int(plan.rows_total), "tiles": int(plan.tiles_total),
+        "exact_vs_plain": exact,
+    }
+
+
 def run_sad(args):
     import torch
     import torch.distributed as dist
@@ -386,6 +460,10 @@ def run_sad(args):
                "d2h_bytes_per_step": int(4 * n + 4 * (p + 1) + 16 * n),
                "ms_per_step": 1e3 * t_e2e}
 
+    batching = None
+    if not args.no_batching:
+        batching = run_batching(args, dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, r, t, threads = oracle_sample(s, args.cpu_seconds, seed=args.seed)
@@ -411,6 +489,7 @@ def run_sad(args):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clocks,
+            "batching": batching,
             "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms),
         }
         print(json.dumps(out))

@@ -17,8 +17,9 @@ simple star-phylogeny family model instead:
   independently: each position is substituted with probability r ~ U[0.20, 0.40]
   by a background residue different from the original, then each position
   starts an indel with probability 0.02 (insertion or deletion with equal odds,
-  length uniform in 1..10, inserted residues from the background; a deletion
-  that would leave fewer than ``MIN_LEN`` residues is skipped).
+  length uniform in 1..10, inserted residues from the background; overlapping
+  deletions merge, and a member that would drop below ``MIN_LEN`` residues
+  keeps none of its deletions). All members of a family are drawn at once.
 
 A sequence set is returned in the layout the C-ABI consumes: ``codes`` (uint8,
 all sequences concatenated) and ``offsets`` (int64, N+1 entries, CSR).
@@ -75,56 +76,65 @@ def rng_for(seed: int, *stream: int) -> np.random.Generator:
     return np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, *stream])))
 
 
+# residue of each 16-bit uniform value: the background CDF quantised to 1/65536
+_TABLE = np.searchsorted(_CDF, (np.arange(65536) + 0.5) / 65536.0, side="right").clip(0, 19) \
+    .astype(np.uint8)
+
+
 def background(rng: np.random.Generator, n: int) -> np.ndarray:
     """n residues iid from the background distribution (codes 0..19)."""
-    u = rng.random(n)
-    return np.searchsorted(_CDF, u, side="right").astype(np.uint8).clip(0, 19)
+    return _TABLE[rng.integers(0, 65536, size=n, dtype=np.uint16)]
 
 
-def _substitute(rng, seq: np.ndarray, rate: float) -> np.ndarray:
-    out = seq.copy()
-    pos = np.nonzero(rng.random(seq.shape[0]) < rate)[0]
-    if pos.size:
-        new = background(rng, pos.size)
-        same = new == out[pos]
-        while same.any():                      # redraw until different
-            new[same] = background(rng, int(same.sum()))
-            same = new == out[pos]
-        out[pos] = new
-    return out
+def mutate_family(rng, ancestor: np.ndarray, m: int):
+    """m members of one family, all derived from ``ancestor`` at once.
 
-
-def _indels(rng, seq: np.ndarray) -> np.ndarray:
-    starts = np.nonzero(rng.random(seq.shape[0]) < INDEL_RATE)[0]
-    if starts.size == 0:
-        return seq
-    kinds = rng.random(starts.size) < 0.5           # True = insertion
-    lens = rng.integers(INDEL_LEN[0], INDEL_LEN[1] + 1, size=starts.size)
-    pieces = []
-    cur = 0
-    length = seq.shape[0]
-    for s, ins, ln in zip(starts.tolist(), kinds.tolist(), lens.tolist()):
-        if s < cur:                                  # inside an earlier deletion
-            continue
-        if ins:
-            pieces.append(seq[cur:s])
-            pieces.append(background(rng, ln))
-            length += ln
-            cur = s
-        else:
-            ln = min(ln, seq.shape[0] - s)
-            if length - ln < MIN_LEN:
-                continue
-            pieces.append(seq[cur:s])
-            length -= ln
-            cur = s + ln
-    pieces.append(seq[cur:])
-    return np.concatenate(pieces)
-
-
-def mutate(rng, ancestor: np.ndarray) -> np.ndarray:
-    rate = rng.uniform(*SUB_RATE)
-    return _indels(rng, _substitute(rng, ancestor, rate))
+    Member j gets its own substitution rate r_j ~ U[0.20, 0.40]: each position is
+    replaced with probability r_j by a background residue different from the
+    original. Then each position starts an indel with probability 0.02:
+    insertion or deletion with equal odds, length uniform in 1..10. A deletion at
+    i removes positions [i, i + len) (overlapping deletions merge); an insertion
+    at i puts len background residues before position i. A member that would end
+    up shorter than MIN_LEN keeps its insertions but none of its deletions.
+    Returns (codes uint8 [total], lengths int64 [m]).
+    """
+    L = ancestor.shape[0]
+    rate = rng.uniform(SUB_RATE[0], SUB_RATE[1], size=m).astype(np.float32)
+    seq = np.broadcast_to(ancestor, (m, L)).copy()
+    idx = np.nonzero(rng.random((m, L), dtype=np.float32) < rate[:, None])
+    new = background(rng, idx[0].size)
+    same = new == seq[idx]
+    while same.any():                                   # redraw until different
+        new[same] = background(rng, int(same.sum()))
+        same = new == seq[idx]
+    seq[idx] = new
+    ev = np.flatnonzero(rng.random(m * L, dtype=np.float32) < INDEL_RATE)
+    is_ins = rng.random(ev.size, dtype=np.float32) < 0.5
+    ln = rng.integers(INDEL_LEN[0], INDEL_LEN[1] + 1, size=ev.size)
+    # deleted positions: difference array of the deletion ranges
+    d, dl = ev[~is_ins], ln[~is_ins]
+    dr, dc = d // L, d % L
+    diff = np.zeros((m, L + 1), dtype=np.int8)
+    np.add.at(diff, (dr, dc), 1)
+    np.add.at(diff, (dr, np.minimum(dc + dl, L)), -1)
+    keep = np.cumsum(diff[:, :L], axis=1, dtype=np.int8) == 0
+    ins = np.zeros(m * L, dtype=np.int32)
+    ins[ev[is_ins]] = ln[is_ins]
+    ins = ins.reshape(m, L)
+    short = keep.sum(axis=1) + ins.sum(axis=1) < MIN_LEN
+    if short.any():
+        keep[short] = True
+    piece = (ins + keep).ravel()                         # output slots per position
+    lengths = (ins.sum(axis=1) + keep.sum(axis=1)).astype(np.int64)
+    total = int(lengths.sum())
+    out = np.empty(total, dtype=np.uint8)
+    kept = keep.ravel()
+    res_slot = (np.cumsum(piece) - piece + ins.ravel())[kept]  # slot of each kept residue
+    is_res = np.zeros(total, dtype=bool)
+    is_res[res_slot] = True
+    out[res_slot] = seq.ravel()[kept]
+    out[~is_res] = background(rng, total - res_slot.size)
+    return out, lengths
 
 
 def _pack(seqs, p: int, name: str) -> SeqSet:
@@ -156,12 +166,19 @@ def family_set(n_families: int, per_family, ancestor_len, p: int, seed: int,
     """
     rng = rng_for(seed, *np.atleast_1d(stream).tolist())
     sizes = np.full(n_families, per_family) if np.isscalar(per_family) else np.asarray(per_family)
-    seqs = []
+    chunks, lens = [], []
     for f in range(n_families):
         anc = background(rng, max(MIN_LEN, int(ancestor_len(rng))))
-        for _ in range(int(sizes[f])):
-            seqs.append(mutate(rng, anc))
-    return _pack(seqs, p, name)
+        if int(sizes[f]) == 0:
+            continue
+        codes, ln = mutate_family(rng, anc, int(sizes[f]))
+        chunks.append(codes)
+        lens.append(ln)
+    lens = np.concatenate(lens) if lens else np.zeros(0, np.int64)
+    offsets = np.zeros(lens.shape[0] + 1, dtype=np.int64)
+    np.cumsum(lens, out=offsets[1:])
+    codes = np.concatenate(chunks) if chunks else np.zeros(0, np.uint8)
+    return SeqSet(codes=codes, offsets=offsets, p=p, name=name)
 
 
 def _split_even(n: int, parts: int) -> np.ndarray:
@@ -207,9 +224,30 @@ def batch_set(index: int, seed: int = 0, n_lo=50, n_hi=5000, stream_id=4,
     return s
 
 
-def config4(seed: int = 0, n_sets: int = 512):
+def _batch_set_job(args):
+    kind, index, seed = args
+    return serving_set(index, seed) if kind == "serve" else batch_set(index, seed)
+
+
+def many_sets(kind: str, indices, seed: int = 0, workers: int | None = None):
+    """Sets ``indices`` of the batching ("batch") or serving ("serve") workload.
+    Independent sets are drawn in a pool of ``workers`` spawned processes (each
+    set has its own seed stream, so the result does not depend on the pool)."""
+    import os
+    indices = list(indices)
+    if workers is None:
+        workers = min(len(indices), max(1, (os.cpu_count() or 1) - 1), 32)
+    jobs = [(kind, i, seed) for i in indices]
+    if workers <= 1 or len(indices) < 8:
+        return [_batch_set_job(j) for j in jobs]
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return pool.map(_batch_set_job, jobs, chunksize=max(1, len(jobs) // (4 * workers)))
+
+
+def config4(seed: int = 0, n_sets: int = 512, workers: int | None = None):
     """512 independent sets for the batched launch."""
-    return [batch_set(i, seed) for i in range(n_sets)]
+    return many_sets("batch", range(n_sets), seed, workers)
 
 
 def serving_set(index: int, seed: int = 0) -> SeqSet:
