@@ -60,6 +60,11 @@ def parse():
     ap.add_argument("--depth", type=int, default=None,
                     help="threshold-plane depth (default: the autotuner's choice)")
     ap.add_argument("--no-batching", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-warmup", type=int, default=200)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-pool", type=int, default=64)
     ap.add_argument("--batch-sets", type=int, default=512)
     ap.add_argument("--batch-reps", type=int, default=10)
     return ap.parse_args()
@@ -314,6 +319,33 @@ def run_batching(args, dev):
     }
 
 
+def run_serving(args, dev, depth):
+    """Poisson arrivals of sets (N log-uniform 100-20000, p = 16) served with
+    continuous batching under a 150 GB HBM budget, and the same arrivals served
+    one at a time with the plain per-set calls."""
+    import torch
+
+    from paper_0905_1744_gb300 import serve
+    pool = datagen.many_sets("serve", range(args.serve_pool), args.seed)
+    total = args.serve_warmup + args.serve_requests
+    arrivals = datagen.poisson_arrivals(total, args.serve_rate, args.seed)
+    out = {"workload": f"Poisson arrivals at {args.serve_rate:g} sets/s, {args.serve_requests} "
+                       f"timed after {args.serve_warmup} warm-up, sets drawn from a pool of "
+                       f"{len(pool)} (N log-uniform 100-20000, L log-uniform 50-2000, p = 16)",
+           "budget_gb": 150, "depth": depth}
+    mixed = serve.serve(serve.make_requests(pool, arrivals), depth=depth, device=dev)
+    plain = serve.serve_plain(serve.make_requests(pool, arrivals), depth=depth, device=dev)
+    out["continuous_batching"] = serve.latency_stats(mixed, args.serve_warmup)
+    out["plain_per_set"] = serve.latency_stats(plain, args.serve_warmup)
+    pairs = np.array([r.seqset.n * (r.seqset.n - 1) / 2 for r in mixed[args.serve_warmup:]])
+    out["offered_pairs_per_s"] = float(pairs.mean() * args.serve_rate)
+    out["exact_vs_plain"] = all(
+        np.array_equal(a.result[k], b.result[k]) for a, b in zip(mixed, plain)
+        for k in ("bucket_offsets", "members", "key_hi", "key_lo"))
+    torch.cuda.synchronize(dev)
+    return out
+
+
 def run_sad(args):
     import torch
     import torch.distributed as dist
@@ -463,6 +495,9 @@ def run_sad(args):
     batching = None
     if not args.no_batching:
         batching = run_batching(args, dev)
+    serving = None
+    if not args.no_serving and world == 1:
+        serving = run_serving(args, dev, depth=batching["depth"] if batching else depth)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -490,6 +525,7 @@ def run_sad(args):
             "e2e": e2e,
             "clocks": clocks,
             "batching": batching,
+            "serving": serving,
             "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms),
         }
         print(json.dumps(out))
