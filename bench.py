@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--serve-warmup", type=int, default=200)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-pool", type=int, default=64)
+    ap.add_argument("--serve-burst", type=int, default=400)
     ap.add_argument("--batch-sets", type=int, default=512)
     ap.add_argument("--batch-reps", type=int, default=10)
     return ap.parse_args()
@@ -339,8 +340,19 @@ def run_serving(args, dev, depth):
     out["plain_per_set"] = serve.latency_stats(plain, args.serve_warmup)
     pairs = np.array([r.seqset.n * (r.seqset.n - 1) / 2 for r in mixed[args.serve_warmup:]])
     out["offered_pairs_per_s"] = float(pairs.mean() * args.serve_rate)
+    # capacity: a burst of requests all arriving at once (saturated server)
+    burst = np.zeros(args.serve_burst)
+    mixed_b = serve.serve(serve.make_requests(pool, burst), depth=depth, device=dev)
+    plain_b = serve.serve_plain(serve.make_requests(pool, burst), depth=depth, device=dev)
+    out["saturated"] = {
+        "requests": int(args.serve_burst),
+        "continuous_batching": serve.latency_stats(mixed_b),
+        "plain_per_set": serve.latency_stats(plain_b),
+    }
+    out["saturated"]["sets_per_s_ratio"] = (out["saturated"]["continuous_batching"]["sets_per_s"]
+                                            / out["saturated"]["plain_per_set"]["sets_per_s"])
     out["exact_vs_plain"] = all(
-        np.array_equal(a.result[k], b.result[k]) for a, b in zip(mixed, plain)
+        np.array_equal(a.result[k], b.result[k]) for a, b in zip(mixed + mixed_b, plain + plain_b)
         for k in ("bucket_offsets", "members", "key_hi", "key_lo"))
     torch.cuda.synchronize(dev)
     return out
