@@ -243,15 +243,23 @@ __global__ void colmax_kernel(const int32_t *__restrict__ counts, int32_t eps, R
   int32_t mx = 0, mn = 0, gt = 0;
   int32_t cur = r0 < r1 ? set_of_seq(P, r0) : 0;
   int64_t r = r0;
-  if (P.n_sets == 1) {
-    for (; r + 4 <= r1; r += 4) {
-      const int32_t a = __ldg(counts + (r + 0) * eps + tau);
-      const int32_t b = __ldg(counts + (r + 1) * eps + tau);
-      const int32_t c = __ldg(counts + (r + 2) * eps + tau);
-      const int32_t d = __ldg(counts + (r + 3) * eps + tau);
-      mx = max(mx, max(max(a, b), max(c, d)));
-      mn = min(mn, min(min(a, b), min(c, d)));
-      gt += (a > D) + (b > D) + (c > D) + (d > D);
+  for (; r + 4 <= r1; r += 4) {
+    int32_t v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = __ldg(counts + (r + u) * eps + tau);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      mx = max(mx, v[u]);
+      mn = min(mn, v[u]);
+      if (P.n_sets > 1) {
+        const int32_t s = P.seq_set[r + u];
+        if (s != cur) {
+          if (D >= 1 && gt) atomicAdd(&P.cnt_gt[(int64_t)cur * eps + tau], gt);
+          gt = 0;
+          cur = s;
+        }
+      }
+      gt += v[u] > D;
     }
   }
   for (; r < r1; ++r) {
@@ -273,8 +281,8 @@ __global__ void colmax_kernel(const int32_t *__restrict__ counts, int32_t eps, R
 }
 
 // One block of 1024 threads: histogram of T, t_max, section ends secend[t] =
-// sum_{t'<=t} #{tau : T_tau >= t'}, K_eff at the depth cap, words sorted by
-// decreasing T, and (unless plan_only) the column map colmap[col] = tau | t << 16.
+// sum_{t'<=t} #{tau : T_tau >= t'}, K_eff at the depth cap and (unless plan_only)
+// the column map colmap[col] = tau | t << 16.
 __global__ void __launch_bounds__(1024) colmap_kernel(RankPtrs P, int32_t eps, int plan_only) {
   __shared__ int32_t s_tmax;
   __shared__ int32_t s_warp[32];
@@ -333,46 +341,39 @@ __global__ void __launch_bounds__(1024) colmap_kernel(RankPtrs P, int32_t eps, i
     if (tid == 0) record_error(P.hdr, SAD_ERR_WORKSPACE, (int)k_pad);
     return;
   }
-  // Words in decreasing T order (ties by word index): position of tau =
-  // #{T > T_tau} + #{tau' < tau : T_tau' = T_tau}. Chunks of 32 words per warp,
-  // warps of a chunk in order, so the order is deterministic.
-  // thist is reused as the running cursor per T value: cursor[v] = #{T > v} first.
-  __syncthreads();
-  if (tid == 0) {
-    int32_t run = 0;
-    for (int v = tmax; v >= 1; --v) {
-      const int32_t c = P.thist[v];
-      P.thist[v] = run;
-      run += c;
-    }
-  }
-  __syncthreads();
-  for (int base = 0; base < eps; base += blockDim.x) {
-    const int tau = base + tid;
-    const int32_t v = tau < eps ? min(P.T[tau], kMaxM) : 0;
-    const unsigned same = __match_any_sync(0xffffffffu, v);
-    const int lane = tid & 31;
-    const int rank_in_warp = __popc(same & ((1u << lane) - 1u));
-    for (int w = 0; w < 32; ++w) {
-      if ((tid >> 5) == w && v >= 1) {
-        const int32_t pos = P.thist[v] + rank_in_warp;
-        P.tau_sorted[pos] = tau;
-        __syncwarp(same);
-        if (rank_in_warp == __popc(same) - 1) P.thist[v] = pos + 1;
+  // Column map, sections in ascending word order: section 1 = the words with
+  // T >= 1; section t + 1 = the words of section t with T >= t + 1 (a stable
+  // compaction of the previous section, so the work is linear in K_eff). Columns
+  // next to each other then look up nearby words when the planes are written.
+  for (int t = 1; t <= dkeep; ++t) {
+    const int32_t src_lo = t == 1 ? 0 : P.secend[t - 2];
+    const int32_t src_n = t == 1 ? eps : P.secend[t - 1] - P.secend[t - 2];
+    const int32_t dst_lo = P.secend[t - 1];
+    if (src_n <= 32) {
+      // short sections: one warp
+      if (tid < 32) {
+        const int32_t tau = tid < src_n ? (t == 1 ? tid : (P.colmap[src_lo + tid] & 0xFFFF)) : 0;
+        const bool keep = tid < src_n && P.T[tau] >= t;
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (keep) P.colmap[dst_lo + __popc(m & ((1u << tid) - 1u))] = tau | (t << 16);
       }
+    } else {
+      if (tid == 0) s_carry = 0;
       __syncthreads();
+      for (int base = 0; base < src_n; base += blockDim.x) {
+        const int i = base + tid;
+        int32_t tau = 0;
+        if (i < src_n) tau = t == 1 ? i : (P.colmap[src_lo + i] & 0xFFFF);
+        const int32_t keep = (i < src_n && P.T[tau] >= t) ? 1 : 0;
+        int32_t tot;
+        const int32_t incl = block_scan_incl<int32_t>(keep, s_warp, &tot);
+        if (keep) P.colmap[dst_lo + s_carry + incl - 1] = tau | (t << 16);
+        __syncthreads();
+        if (tid == 0) s_carry += tot;
+        __syncthreads();
+      }
     }
-  }
-  __syncthreads();
-  // colmap[col] for col < K_eff: section t is the first n_t words of tau_sorted.
-  for (int64_t col = tid; col < k_eff; col += blockDim.x) {
-    int lo = 1, hi = tmax;  // smallest t with secend[t] > col
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (P.secend[mid] > col) hi = mid; else lo = mid + 1;
-    }
-    const int32_t r = (int32_t)(col - P.secend[lo - 1]);
-    P.colmap[col] = P.tau_sorted[r] | (lo << 16);
+    __syncthreads();
   }
 }
 
@@ -664,44 +665,38 @@ __global__ void __launch_bounds__(256) planes_kernel(const int32_t *__restrict__
         }
       }
     }
-    uint4 *dst[kPlaneRows];
+    // plane bytes: thread writes 4 consecutive columns (one 32-bit store per row);
+    // neighbouring lanes look up neighbouring words of the same section
+    uint32_t *dst[kPlaneRows];
 #pragma unroll
     for (int r = 0; r < kPlaneRows; ++r)
-      dst[r] = reinterpret_cast<uint4 *>(P.planes + (g * kPlaneRows + r) * P.k_cap);
-    for (int c = threadIdx.x; c < k_pad / 16; c += blockDim.x) {
-      uint32_t w[kPlaneRows][4] = {};
-      const int32_t c0 = c * 16;
-      if (c0 + 16 <= k_eff) {
-        const int4 *cm = reinterpret_cast<const int4 *>(P.colmap + c0);
-        int4 e4[4];
+      dst[r] = reinterpret_cast<uint32_t *>(P.planes + (g * kPlaneRows + r) * P.k_cap);
+    for (int c = threadIdx.x; c < k_pad / 4; c += blockDim.x) {
+      uint32_t w[kPlaneRows] = {};
+      const int32_t c0 = c * 4;
+      if (c0 + 4 <= k_eff) {
+        const int4 e4 = __ldg(reinterpret_cast<const int4 *>(P.colmap + c0));
+        const int32_t ev[4] = {e4.x, e4.y, e4.z, e4.w};
 #pragma unroll
-        for (int q = 0; q < 4; ++q) e4[q] = __ldg(cm + q);
+        for (int b = 0; b < 4; ++b) {
+          const uint32_t tau = (uint32_t)ev[b] & 0xFFFFu, t = (uint32_t)ev[b] >> 16;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int32_t ev[4] = {e4[q].x, e4[q].y, e4[q].z, e4[q].w};
-#pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            const uint32_t tau = (uint32_t)ev[b] & 0xFFFFu, t = (uint32_t)ev[b] >> 16;
-#pragma unroll
-            for (int r = 0; r < kPlaneRows; ++r)
-              if ((uint32_t)s_cnt[r * eps + tau] >= t) w[r][q] |= 0x38u << (8 * b);
-          }
+          for (int r = 0; r < kPlaneRows; ++r)
+            if ((uint32_t)s_cnt[r * eps + tau] >= t) w[r] |= 0x38u << (8 * b);
         }
       } else {
-        for (int b = 0; b < 16; ++b) {
+        for (int b = 0; b < 4; ++b) {
           if (c0 + b < k_eff) {
             const int32_t e = __ldg(P.colmap + c0 + b);
             const uint32_t tau = (uint32_t)e & 0xFFFFu, t = (uint32_t)e >> 16;
 #pragma unroll
             for (int r = 0; r < kPlaneRows; ++r)
-              if ((uint32_t)s_cnt[r * eps + tau] >= t) w[r][b >> 2] |= 0x38u << (8 * (b & 3));
+              if ((uint32_t)s_cnt[r * eps + tau] >= t) w[r] |= 0x38u << (8 * b);
           }
         }
       }
 #pragma unroll
-      for (int r = 0; r < kPlaneRows; ++r)
-        dst[r][c] = xs[r] >= 0 ? make_uint4(w[r][0], w[r][1], w[r][2], w[r][3])
-                               : make_uint4(0, 0, 0, 0);
+      for (int r = 0; r < kPlaneRows; ++r) dst[r][c] = xs[r] >= 0 ? w[r] : 0u;
     }
     if (threadIdx.x < kPlaneRows && xs[threadIdx.x] >= 0) {
       const int64_t pos = g * kPlaneRows + threadIdx.x;
