@@ -380,10 +380,12 @@ def run_sad(args):
     lengths = torch.from_numpy(s.lengths.astype(np.int32)).to(dev)
     ws = sad.Workspace(dev)
     counts = torch.empty((n, 8000), dtype=torch.int32, device=dev)
-    sad.kmer_count(codes, offsets, ws=ws, out=counts)
+    word_max = torch.empty(8000, dtype=torch.int32, device=dev)
+    sad.kmer_count(codes, offsets, ws=ws, out=counts, word_max=word_max)
     # plane depth chosen by the autotuner (timed trials, outside the timed region)
     if args.depth is None:
-        depth, trials = autotune.choose_depth(counts, lengths, ws, use_cache=False)
+        depth, trials = autotune.choose_depth(counts, lengths, ws, use_cache=False,
+                                              word_max=word_max)
     else:
         depth, trials = args.depth, {}
     plan = sad.kmer_rank_plan(counts, depth=depth, ws=ws)
@@ -397,8 +399,9 @@ def run_sad(args):
             torch.empty(max(p - 1, 1), dtype=torch.int32, device=dev))
 
     def step():
-        sad.kmer_count(codes, offsets, ws=ws, out=counts, check=False)
-        sad.kmer_rank(counts, lengths, ws=ws, out=keys, check=False, plan=plan)
+        sad.kmer_count(codes, offsets, ws=ws, out=counts, check=False, word_max=word_max)
+        sad.kmer_rank(counts, lengths, ws=ws, out=keys, check=False, plan=plan,
+                      word_max=word_max)
         sad.partition(keys[0], keys[1], p, ws=ws_part, out=part, check=False)
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # 2x the 129 MB L2

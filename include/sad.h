@@ -90,11 +90,15 @@ size_t sad_workspace_bytes(int32_t op, int32_t n_seq, int32_t k, int32_t alphabe
  *   SAD_ERR_INVALID_ARGUMENT and no code byte outside [off[0], off[n_seq]) is read.
  *   d_counts   int32 [n_seq][eps] output; word index
  *              tau = sum_r a_r * alphabet^(k-1-r) (first letter most significant).
+ *   d_word_max (nullable) int32 [eps] output: the largest count of every word
+ *              over the n_seq sequences; passing it to kmer_rank saves that call
+ *              a pass over the counts. Needs eps <= 16384 (else
+ *              SAD_ERR_UNSUPPORTED; call without it).
  *   d_ws       workspace of sad_workspace_bytes(SAD_OP_COUNT, ...) bytes.
  */
 int kmer_count(const uint8_t *d_codes, const int64_t *d_offsets, int32_t n_seq,
-               int32_t k, int32_t alphabet, int32_t *d_counts, void *d_ws,
-               size_t ws_bytes, void *stream);
+               int32_t k, int32_t alphabet, int32_t *d_counts, int32_t *d_word_max,
+               void *d_ws, size_t ws_bytes, void *stream);
 
 /*
  * Plan of a kmer_rank call. `depth` is chosen by the caller (an autotuner, or 0);
@@ -153,6 +157,8 @@ int kmer_rank_plan(const int32_t *d_counts, int32_t n_seq, int32_t k, int32_t al
  *   d_lengths  int32 [n_seq] sequence lengths L (residues); every
  *              L - k + 1 must be in 1..65535 (SAD_ERR_UNSUPPORTED otherwise)
  *              and equal to the sum of the sequence's counts (SAD_ERR_BAD_INPUT).
+ *   d_word_max (nullable) int32 [eps], the largest count of every word, as
+ *              kmer_count returns it for these counts.
  *   plan       (nullable) a plan from kmer_rank_plan for these counts; NULL keeps
  *              all planes and takes the plane capacity from ws_bytes.
  *   d_key_hi, d_key_lo  uint64 [n_seq] outputs.
@@ -162,9 +168,10 @@ int kmer_rank_plan(const int32_t *d_counts, int32_t n_seq, int32_t k, int32_t al
  *              depth * eps >= K_eff). Data that need more than the capacities
  *              record SAD_ERR_WORKSPACE and write no keys.
  */
-int kmer_rank(const int32_t *d_counts, const int32_t *d_lengths, int32_t n_seq,
-              int32_t k, int32_t alphabet, const sad_rank_plan *plan, uint64_t *d_key_hi,
-              uint64_t *d_key_lo, double *d_rank, void *d_ws, size_t ws_bytes, void *stream);
+int kmer_rank(const int32_t *d_counts, const int32_t *d_lengths, const int32_t *d_word_max,
+              int32_t n_seq, int32_t k, int32_t alphabet, const sad_rank_plan *plan,
+              uint64_t *d_key_hi, uint64_t *d_key_lo, double *d_rank, void *d_ws,
+              size_t ws_bytes, void *stream);
 
 /*
  * partition - regular-sampling sample sort of the keys into p buckets
@@ -258,14 +265,15 @@ int sad_batch_plan_make(const int32_t *d_counts, const int32_t *h_n, const int32
 /*
  * sad_batch_rank - kmer_rank of every set of the batch (Eq. 1, Eq. 3 per set).
  *   d_counts, d_lengths  all sets' counts and lengths, set after set.
+ *   d_word_max (nullable) largest count of every word over the whole batch.
  *   d_n        device int32 [n_sets] set sizes (as given to the plan).
  *   d_key_hi, d_key_lo, d_rank  per-sequence outputs, set after set.
  *   d_ws       at least plan->rank.ws_bytes.
  */
-int sad_batch_rank(const int32_t *d_counts, const int32_t *d_lengths, const int32_t *d_n,
-                   int32_t k, int32_t alphabet, const sad_batch_plan *plan, uint64_t *d_key_hi,
-                   uint64_t *d_key_lo, double *d_rank, void *d_ws, size_t ws_bytes,
-                   void *stream);
+int sad_batch_rank(const int32_t *d_counts, const int32_t *d_lengths, const int32_t *d_word_max,
+                   const int32_t *d_n, int32_t k, int32_t alphabet, const sad_batch_plan *plan,
+                   uint64_t *d_key_hi, uint64_t *d_key_lo, double *d_rank, void *d_ws,
+                   size_t ws_bytes, void *stream);
 
 /*
  * sad_batch_partition - partition() of every set of the batch.

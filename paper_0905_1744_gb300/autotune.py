@@ -51,19 +51,21 @@ def save_cache(path: str | None):
         os.replace(tmp, path)
 
 
-def time_rank(counts, lengths, plan, ws, k=3, alphabet=20, reps=3, stream=None) -> float:
+def time_rank(counts, lengths, plan, ws, k=3, alphabet=20, reps=3, stream=None,
+              word_max=None) -> float:
     """Median milliseconds of kmer_rank with this plan (CUDA events)."""
     s = stream or torch.cuda.current_stream()
     n = counts.shape[0]
     out = (torch.empty(n, dtype=torch.uint64, device=counts.device),
            torch.empty(n, dtype=torch.uint64, device=counts.device), None)
-    sad.kmer_rank(counts, lengths, k, alphabet, ws=ws, plan=plan, out=out, stream=s)
+    sad.kmer_rank(counts, lengths, k, alphabet, ws=ws, plan=plan, out=out, stream=s,
+                  word_max=word_max)
     times = []
     for _ in range(reps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(s)
         sad.kmer_rank(counts, lengths, k, alphabet, ws=ws, plan=plan, out=out, stream=s,
-                      check=False)
+                      check=False, word_max=word_max)
         e1.record(s)
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
@@ -72,7 +74,7 @@ def time_rank(counts, lengths, plan, ws, k=3, alphabet=20, reps=3, stream=None) 
 
 
 def choose_depth(counts, lengths, ws=None, k=3, alphabet=20, candidates=CANDIDATES, reps=3,
-                 max_ws_bytes: int | None = None, use_cache=True, stream=None):
+                 max_ws_bytes: int | None = None, use_cache=True, stream=None, word_max=None):
     """Fastest plane depth for this set: (depth, {depth: ms})."""
     n = counts.shape[0]
     ws = ws or sad.Workspace(counts.device)
@@ -90,7 +92,7 @@ def choose_depth(counts, lengths, ws=None, k=3, alphabet=20, candidates=CANDIDAT
         if max_ws_bytes is not None and plan.ws_bytes > max_ws_bytes:
             continue
         ws.ensure(plan.ws_bytes)
-        trials[d] = time_rank(counts, lengths, plan, ws, k, alphabet, reps, stream)
+        trials[d] = time_rank(counts, lengths, plan, ws, k, alphabet, reps, stream, word_max)
     best = min(trials, key=trials.get)
     with _lock:
         _cache[key] = best

@@ -10,8 +10,8 @@
 namespace sad {
 
 int count_launch(const uint8_t *codes, const int64_t *offsets, int32_t n, int32_t k,
-                 int32_t alphabet, int32_t eps, int32_t *counts, WsHeader *hdr,
-                 cudaStream_t st);
+                 int32_t alphabet, int32_t eps, int32_t *counts, int32_t *word_max,
+                 WsHeader *hdr, cudaStream_t st);
 int partition_launch(const uint64_t *key_hi, const uint64_t *key_lo, int32_t n, int32_t p,
                      int32_t *bucket_offsets, int32_t *members, int32_t *pivot_idx, void *ws,
                      cudaStream_t st);
@@ -157,8 +157,8 @@ size_t sad_workspace_bytes(int32_t op, int32_t n_seq, int32_t k, int32_t alphabe
 }
 
 int kmer_count(const uint8_t *d_codes, const int64_t *d_offsets, int32_t n_seq, int32_t k,
-               int32_t alphabet, int32_t *d_counts, void *d_ws, size_t ws_bytes,
-               void *stream) {
+               int32_t alphabet, int32_t *d_counts, int32_t *d_word_max, void *d_ws,
+               size_t ws_bytes, void *stream) {
   const int64_t eps = eps_of(k, alphabet);
   if (n_seq < 0 || eps < 0) return eps < 0 && n_seq >= 0 ? SAD_ERR_UNSUPPORTED
                                                            : SAD_ERR_INVALID_ARGUMENT;
@@ -166,8 +166,10 @@ int kmer_count(const uint8_t *d_codes, const int64_t *d_offsets, int32_t n_seq, 
   if (n_seq == 0) return SAD_OK;
   if (!d_codes || !d_offsets || !d_counts || !aligned(d_counts, 16) || !aligned(d_offsets, 8))
     return SAD_ERR_INVALID_ARGUMENT;
+  if (d_word_max && eps > 16384) return SAD_ERR_UNSUPPORTED;
   return count_launch(d_codes, d_offsets, n_seq, k, alphabet, (int32_t)eps, d_counts,
-                      static_cast<WsHeader *>(d_ws), static_cast<cudaStream_t>(stream));
+                      d_word_max, static_cast<WsHeader *>(d_ws),
+                      static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"
@@ -187,7 +189,7 @@ int rank_plan_impl(const int32_t *d_counts, const RankShape &sh, const int32_t *
   if (sh.n_total > 0) {
     if (!d_counts) return SAD_ERR_INVALID_ARGUMENT;
     const RankPtrs P = rank_ptrs(d_ws, L0);
-    int rc = rank_prep_launch(P, d_counts, nullptr, d_n, k, (int32_t)eps, 1, st);
+    int rc = rank_prep_launch(P, d_counts, nullptr, d_n, nullptr, k, (int32_t)eps, 1, st);
     if (rc) return rc;
     rc = check_cuda(cudaMemcpyAsync(&h, d_ws, sizeof(h), cudaMemcpyDeviceToHost, st));
     if (rc) return rc;
@@ -211,8 +213,9 @@ int rank_plan_impl(const int32_t *d_counts, const RankShape &sh, const int32_t *
   return SAD_OK;
 }
 
-int rank_run_impl(const int32_t *d_counts, const int32_t *d_lengths, const RankShape &sh,
-                  const int32_t *d_n, int64_t eps, int32_t k, const sad_rank_plan *plan,
+int rank_run_impl(const int32_t *d_counts, const int32_t *d_lengths, const int32_t *word_max,
+                  const RankShape &sh, const int32_t *d_n, int64_t eps, int32_t k,
+                  const sad_rank_plan *plan,
                   uint64_t *d_key_hi, uint64_t *d_key_lo, double *d_rank, void *d_ws,
                   size_t ws_bytes, cudaStream_t st) {
   if (sh.rows_total / kRowBlock > 0xFFFF) return SAD_ERR_UNSUPPORTED;  // 16-bit block ids
@@ -229,7 +232,7 @@ int rank_run_impl(const int32_t *d_counts, const int32_t *d_lengths, const RankS
   }
   const RankLayout L = rank_layout(sh, eps, caps);
   const RankPtrs P = rank_ptrs(d_ws, L);
-  int rc = rank_prep_launch(P, d_counts, d_lengths, d_n, k, (int32_t)eps, 0, st);
+  int rc = rank_prep_launch(P, d_counts, d_lengths, d_n, word_max, k, (int32_t)eps, 0, st);
   if (rc) return rc;
   rc = rank_gemm_launch(P, st);
   if (rc) return rc;
@@ -275,15 +278,17 @@ int kmer_rank_plan(const int32_t *d_counts, int32_t n_seq, int32_t k, int32_t al
                         static_cast<cudaStream_t>(stream));
 }
 
-int kmer_rank(const int32_t *d_counts, const int32_t *d_lengths, int32_t n_seq, int32_t k,
-              int32_t alphabet, const sad_rank_plan *plan, uint64_t *d_key_hi,
-              uint64_t *d_key_lo, double *d_rank, void *d_ws, size_t ws_bytes, void *stream) {
+int kmer_rank(const int32_t *d_counts, const int32_t *d_lengths, const int32_t *d_word_max,
+              int32_t n_seq, int32_t k, int32_t alphabet, const sad_rank_plan *plan,
+              uint64_t *d_key_hi, uint64_t *d_key_lo, double *d_rank, void *d_ws,
+              size_t ws_bytes, void *stream) {
   const int64_t eps = eps_of(k, alphabet);
   if (eps < 0) return SAD_ERR_UNSUPPORTED;
   if (n_seq < 0 || !d_ws || !aligned(d_ws, 256)) return SAD_ERR_INVALID_ARGUMENT;
   if (n_seq == 0) return SAD_OK;
   if (!d_counts || !d_lengths || !d_key_hi || !d_key_lo) return SAD_ERR_INVALID_ARGUMENT;
-  return rank_run_impl(d_counts, d_lengths, shape_single(n_seq), nullptr, eps, k, plan,
+  return rank_run_impl(d_counts, d_lengths, d_word_max, shape_single(n_seq), nullptr, eps, k,
+                       plan,
                        d_key_hi, d_key_lo, d_rank, d_ws, ws_bytes,
                        static_cast<cudaStream_t>(stream));
 }
@@ -315,10 +320,10 @@ int sad_batch_plan_make(const int32_t *d_counts, const int32_t *h_n, const int32
                         static_cast<cudaStream_t>(stream));
 }
 
-int sad_batch_rank(const int32_t *d_counts, const int32_t *d_lengths, const int32_t *d_n,
-                   int32_t k, int32_t alphabet, const sad_batch_plan *plan, uint64_t *d_key_hi,
-                   uint64_t *d_key_lo, double *d_rank, void *d_ws, size_t ws_bytes,
-                   void *stream) {
+int sad_batch_rank(const int32_t *d_counts, const int32_t *d_lengths, const int32_t *d_word_max,
+                   const int32_t *d_n, int32_t k, int32_t alphabet, const sad_batch_plan *plan,
+                   uint64_t *d_key_hi, uint64_t *d_key_lo, double *d_rank, void *d_ws,
+                   size_t ws_bytes, void *stream) {
   const int64_t eps = eps_of(k, alphabet);
   if (eps < 0) return SAD_ERR_UNSUPPORTED;
   if (!plan || plan->n_sets < 1 || !d_n || !d_counts || !d_lengths || !d_key_hi || !d_key_lo ||
@@ -326,7 +331,8 @@ int sad_batch_rank(const int32_t *d_counts, const int32_t *d_lengths, const int3
     return SAD_ERR_INVALID_ARGUMENT;
   const RankShape sh{plan->n_sets, plan->n_total, plan->rows_total, plan->tiles_total,
                      plan->tileof_total};
-  return rank_run_impl(d_counts, d_lengths, sh, plan->n_sets > 1 ? d_n : nullptr, eps, k,
+  return rank_run_impl(d_counts, d_lengths, d_word_max, sh, plan->n_sets > 1 ? d_n : nullptr,
+                       eps, k,
                        &plan->rank, d_key_hi, d_key_lo, d_rank, d_ws, ws_bytes,
                        static_cast<cudaStream_t>(stream));
 }

@@ -6,7 +6,9 @@
 // bytes a lane's last windows run into come from the next lane by shuffle, and
 // lane 31 loads them itself. Each window's word is counted in the warp's
 // private shared-memory histogram (two 16-bit bins per 32-bit word), which is
-// then streamed out as the dense int32 row and cleared in the same pass.
+// then streamed out as the dense int32 row and cleared in the same pass. If asked,
+// the same pass keeps the block's largest count of every word (shared memory) and
+// merges it into the per-word maximum over all sequences at the end.
 #include "sad_common.cuh"
 
 namespace sad {
@@ -31,14 +33,18 @@ __global__ void __launch_bounds__(128) kmer_count_kernel(const uint8_t *__restri
                                                         const int64_t *__restrict__ offsets,
                                                         int32_t n, int32_t alphabet, int32_t eps,
                                                         int32_t *__restrict__ counts,
+                                                        int32_t *__restrict__ word_max,
                                                         WsHeader *hdr) {
   extern __shared__ uint32_t smem[];
   const int warps = blockDim.x >> 5;
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int words = (eps + 1) >> 1;
   uint32_t *hist = smem + (size_t)wid * words;
+  int32_t *smax = reinterpret_cast<int32_t *>(smem + (size_t)warps * words);  // [eps] if word_max
   for (int i = lane; i < words; i += 32) hist[i] = 0;
-  __syncwarp();
+  if (word_max)
+    for (int i = threadIdx.x; i < eps; i += blockDim.x) smax[i] = 0;
+  __syncthreads();
   const int64_t codes_end = offsets[n];
 
   for (int64_t x = (int64_t)blockIdx.x * warps + wid; x < n; x += (int64_t)gridDim.x * warps) {
@@ -86,26 +92,46 @@ __global__ void __launch_bounds__(128) kmer_count_kernel(const uint8_t *__restri
         const uint32_t a = hist[2 * q], b = hist[2 * q + 1];
         hist[2 * q] = 0;
         hist[2 * q + 1] = 0;
-        reinterpret_cast<int4 *>(row)[q] =
+        const int4 c4 =
             make_int4((int)(a & 0xFFFFu), (int)(a >> 16), (int)(b & 0xFFFFu), (int)(b >> 16));
+        reinterpret_cast<int4 *>(row)[q] = c4;
+        if (word_max && (a | b)) {
+          if (c4.x) atomicMax(&smax[4 * q + 0], c4.x);
+          if (c4.y) atomicMax(&smax[4 * q + 1], c4.y);
+          if (c4.z) atomicMax(&smax[4 * q + 2], c4.z);
+          if (c4.w) atomicMax(&smax[4 * q + 3], c4.w);
+        }
       }
     } else {
-      for (int t = lane; t < eps; t += 32)
-        row[t] = (int)((hist[t >> 1] >> (16 * (t & 1))) & 0xFFFFu);
+      for (int t = lane; t < eps; t += 32) {
+        const int c = (int)((hist[t >> 1] >> (16 * (t & 1))) & 0xFFFFu);
+        row[t] = c;
+        if (word_max && c) atomicMax(&smax[t], c);
+      }
       __syncwarp();
       for (int i = lane; i < words; i += 32) hist[i] = 0;
     }
     __syncwarp();
   }
+  if (word_max) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < eps; i += blockDim.x)
+      if (smax[i]) atomicMax(&word_max[i], smax[i]);
+  }
 }
 
 template <int K>
 int launch_count(const uint8_t *codes, const int64_t *offsets, int32_t n, int32_t alphabet,
-                 int32_t eps, int32_t *counts, WsHeader *hdr, cudaStream_t st) {
+                 int32_t eps, int32_t *counts, int32_t *word_max, WsHeader *hdr,
+                 cudaStream_t st) {
   const size_t per_warp = sizeof(uint32_t) * (size_t)((eps + 1) / 2);
+  const size_t max_bytes = word_max ? sizeof(int32_t) * (size_t)eps : 0;
   int warps = (int)((96 * 1024) / per_warp);
   warps = warps < 1 ? 1 : (warps > 4 ? 4 : warps);
-  const size_t smem = per_warp * warps;
+  const size_t smem = per_warp * warps + max_bytes;
+  if (word_max) {
+    if (cudaMemsetAsync(word_max, 0, max_bytes, st) != cudaSuccess) return SAD_ERR_CUDA;
+  }
   if (smem > 227 * 1024) return SAD_ERR_UNSUPPORTED;
   auto kern = kmer_count_kernel<K>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
@@ -119,7 +145,8 @@ int launch_count(const uint8_t *codes, const int64_t *offsets, int32_t n, int32_
   const int64_t need = (n + warps - 1) / warps;
   if (blocks > need) blocks = need;
   if (blocks < 1) blocks = 1;
-  kern<<<(unsigned)blocks, warps * 32, smem, st>>>(codes, offsets, n, alphabet, eps, counts, hdr);
+  kern<<<(unsigned)blocks, warps * 32, smem, st>>>(codes, offsets, n, alphabet, eps, counts,
+                                                   word_max, hdr);
   SAD_LAUNCH_CHECK();
   return SAD_OK;
 }
@@ -127,17 +154,14 @@ int launch_count(const uint8_t *codes, const int64_t *offsets, int32_t n, int32_
 }  // namespace
 
 int count_launch(const uint8_t *codes, const int64_t *offsets, int32_t n, int32_t k,
-                 int32_t alphabet, int32_t eps, int32_t *counts, WsHeader *hdr,
-                 cudaStream_t st) {
+                 int32_t alphabet, int32_t eps, int32_t *counts, int32_t *word_max,
+                 WsHeader *hdr, cudaStream_t st) {
   switch (k) {
-    case 1: return launch_count<1>(codes, offsets, n, alphabet, eps, counts, hdr, st);
-    case 2: return launch_count<2>(codes, offsets, n, alphabet, eps, counts, hdr, st);
-    case 3: return launch_count<3>(codes, offsets, n, alphabet, eps, counts, hdr, st);
-    case 4: return launch_count<4>(codes, offsets, n, alphabet, eps, counts, hdr, st);
-    case 5: return launch_count<5>(codes, offsets, n, alphabet, eps, counts, hdr, st);
-    case 6: return launch_count<6>(codes, offsets, n, alphabet, eps, counts, hdr, st);
-    case 7: return launch_count<7>(codes, offsets, n, alphabet, eps, counts, hdr, st);
-    case 8: return launch_count<8>(codes, offsets, n, alphabet, eps, counts, hdr, st);
+#define SAD_COUNT_CASE(KK) \
+  case KK: return launch_count<KK>(codes, offsets, n, alphabet, eps, counts, word_max, hdr, st);
+    SAD_COUNT_CASE(1) SAD_COUNT_CASE(2) SAD_COUNT_CASE(3) SAD_COUNT_CASE(4)
+    SAD_COUNT_CASE(5) SAD_COUNT_CASE(6) SAD_COUNT_CASE(7) SAD_COUNT_CASE(8)
+#undef SAD_COUNT_CASE
     default: return SAD_ERR_UNSUPPORTED;
   }
 }

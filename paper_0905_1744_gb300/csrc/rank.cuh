@@ -28,7 +28,8 @@ struct RankPtrs {
   int64_t *list_off;     // [n_sets * eps + 1] start of each excess list
   int64_t *pair_off;     // [n_sets * eps + 1] start of each list's pair range
   int32_t *cursor;       // [n_sets * eps] fill cursor of the excess lists
-  int2 *lists;           // [list_cap] (stored row, count - depth)
+  int2 *lists;           // [list_cap] (stored row, count - depth), grouped by (set, word)
+  int2 *flat;            // [list_cap] (stored row, word | (count - depth) << 16), unordered
   int32_t *tile_of;      // [tileof_total] tile index of set-local block (I, J)
   int32_t *block_of;     // [tiles_total] residual block of a tile, -1 = none
   uint32_t *rblocks;     // [block_cap][128][256] u16 residual per pair (two per word)
@@ -41,9 +42,11 @@ struct RankPtrs {
 
 RankPtrs rank_ptrs(void *ws, const RankLayout &L);
 // d_n: per-set sizes on the device (n_sets > 1), or nullptr for one set of n_total.
+// word_max (nullable): the largest count of every word, as kmer_count can return
+// it; when given, the column-maximum pass over the counts is skipped.
 int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *lengths,
-                     const int32_t *d_n, int32_t k, int32_t eps, int plan_only,
-                     cudaStream_t st);
+                     const int32_t *d_n, const int32_t *word_max, int32_t k, int32_t eps,
+                     int plan_only, cudaStream_t st);
 int rank_gemm_launch(const RankPtrs &P, cudaStream_t st);
 int rank_finalize_launch(const RankPtrs &P, uint64_t *key_hi, uint64_t *key_lo, double *rank,
                          cudaStream_t st);

@@ -66,6 +66,7 @@ RankPtrs rank_ptrs(void *ws, const RankLayout &L) {
   P.pair_off = reinterpret_cast<int64_t *>(b + L.pair_off);
   P.cursor = reinterpret_cast<int32_t *>(b + L.cursor);
   P.lists = reinterpret_cast<int2 *>(b + L.lists);
+  P.flat = reinterpret_cast<int2 *>(b + L.flat);
   P.tile_of = reinterpret_cast<int32_t *>(b + L.tile_of);
   P.block_of = reinterpret_cast<int32_t *>(b + L.block_of);
   P.rblocks = reinterpret_cast<uint32_t *>(b + L.rblocks);
@@ -212,6 +213,7 @@ __global__ void rank_init_kernel(RankPtrs P, int32_t eps, int with_keys) {
     P.hdr->pairs_total = 0;
     P.hdr->n_blocks = 0;
     P.hdr->m_max = 0;
+    P.hdr->flat_count = 0;
   }
 }
 
@@ -232,10 +234,11 @@ __global__ void lengths_kernel(const int32_t *__restrict__ lengths, int32_t k, R
 
 // T_tau = max over rows of counts[x][tau] and (D >= 1) the number of rows of each
 // set whose count exceeds D. Block (256 words) x (row slice).
-__global__ void colmax_kernel(const int32_t *__restrict__ counts, int32_t eps, RankPtrs P) {
+__global__ void colmax_kernel(const int32_t *__restrict__ counts, int32_t eps, RankPtrs P,
+                              int count_gt) {
   const int32_t tau = blockIdx.x * blockDim.x + threadIdx.x;
   if (tau >= eps) return;
-  const int32_t D = P.depth_cap;
+  const int32_t D = count_gt ? P.depth_cap : 0;
   const int64_t n = P.n_total;
   const int64_t per = (n + gridDim.y - 1) / gridDim.y;
   const int64_t r0 = (int64_t)blockIdx.y * per;
@@ -278,6 +281,17 @@ __global__ void colmax_kernel(const int32_t *__restrict__ counts, int32_t eps, R
   if (mx > kMaxM) record_error(P.hdr, SAD_ERR_UNSUPPORTED, tau);
   if (mx > 0) atomicMax(&P.T[tau], mx);
   if (D >= 1 && gt) atomicAdd(&P.cnt_gt[(int64_t)cur * eps + tau], gt);
+}
+
+// T_tau taken from a per-word maximum computed while counting.
+__global__ void copy_word_max_kernel(const int32_t *__restrict__ word_max, int32_t eps,
+                                     RankPtrs P) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < eps; i += gridDim.x * blockDim.x) {
+    const int32_t t = word_max[i];
+    if (t < 0) record_error(P.hdr, SAD_ERR_BAD_INPUT, i);
+    if (t > kMaxM) record_error(P.hdr, SAD_ERR_UNSUPPORTED, i);
+    P.T[i] = t;
+  }
 }
 
 // One block of 1024 threads: histogram of T, t_max, section ends secend[t] =
@@ -475,6 +489,20 @@ __global__ void __launch_bounds__(256) list_scan_down_kernel(RankPtrs P, int64_t
   }
 }
 
+// Excess entries from the unordered append into their (set, word) lists.
+__global__ void group_lists_kernel(RankPtrs P, int32_t eps) {
+  if (P.hdr->status != 0 || !residual_needed(P)) return;
+  const int64_t total = (int64_t)P.hdr->flat_count;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int2 e = P.flat[i];
+    const int32_t tau = e.y & 0xFFFF, ex = (int32_t)((uint32_t)e.y >> 16);
+    const int64_t w = (int64_t)set_of_row(P, e.x) * eps + tau;
+    const int32_t slot = atomicAdd(&P.cursor[w], 1);
+    P.lists[P.list_off[w] + slot] = make_int2(e.x, ex);
+  }
+}
+
 // One set: exclusive prefix over m in decreasing order, mhist[m] := #{x : m_x > m},
 // for m = m_max down to 1, 1024 consecutive values per step.
 __global__ void __launch_bounds__(1024) lensort_scan_kernel(RankPtrs P) {
@@ -650,7 +678,8 @@ __global__ void __launch_bounds__(256) planes_kernel(const int32_t *__restrict__
     }
     __syncthreads();
     if (residual) {
-      // excess entries of the rows: (stored row, count - depth) per word above depth
+      // excess entries of the rows, appended unordered: (stored row, word | excess << 16);
+      // the per-(set, word) sizes are counted for the grouping that follows
 #pragma unroll
       for (int r = 0; r < kPlaneRows; ++r) {
         if (xs[r] < 0) continue;
@@ -659,8 +688,10 @@ __global__ void __launch_bounds__(256) planes_kernel(const int32_t *__restrict__
         for (int tau = threadIdx.x; tau < eps; tau += blockDim.x) {
           const int32_t c = s_cnt[r * eps + tau];
           if (c > dkeep) {
-            const int32_t slot = atomicAdd(&P.cursor[wbase + tau], 1);
-            P.lists[P.list_off[wbase + tau] + slot] = make_int2((int32_t)pos, c - dkeep);
+            atomicAdd(&P.cnt_gt[wbase + tau], 1);
+            const unsigned long long slot = atomicAdd(&P.hdr->flat_count, 1ull);
+            if (slot < (unsigned long long)P.list_cap)
+              P.flat[slot] = make_int2((int32_t)pos, tau | ((c - dkeep) << 16));
           }
         }
       }
@@ -908,45 +939,49 @@ bool g_attr_sort = false;
 }  // namespace
 
 int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *lengths,
-                     const int32_t *d_n, int32_t k, int32_t eps, int plan_only,
-                     cudaStream_t st) {
+                     const int32_t *d_n, const int32_t *word_max, int32_t k, int32_t eps,
+                     int plan_only, cudaStream_t st) {
   const int64_t n = P.n_total;
   const unsigned gsets = (unsigned)(P.n_sets < 4096 ? P.n_sets : 4096);
-  rank_setup_kernel<<<1, 1024, 0, st>>>(d_n, (int32_t)n, P);
-  SAD_LAUNCH_CHECK();
-  if (P.n_sets > 1) {
-    rank_setmaps_kernel<<<gsets, 256, 0, st>>>(P);
-    SAD_LAUNCH_CHECK();
-  }
-  rank_init_kernel<<<grid_for(P.n_sets * (int64_t)eps + kMaxM, 256), 256, 0, st>>>(
-      P, eps, !plan_only);
-  SAD_LAUNCH_CHECK();
-  if (!plan_only) {
-    lengths_kernel<<<grid_for(n, 256), 256, 0, st>>>(lengths, k, P);
-    SAD_LAUNCH_CHECK();
-  }
-  {
-    dim3 g((eps + 255) / 256, 1);
-    int64_t slices = ((int64_t)num_sms() * 8 + g.x - 1) / g.x;
-    if (slices > (n + 63) / 64) slices = (n + 63) / 64;
-    if (slices < 1) slices = 1;
-    g.y = (unsigned)slices;
-    colmax_kernel<<<g, 256, 0, st>>>(counts, eps, P);
-    SAD_LAUNCH_CHECK();
-  }
-  colmap_kernel<<<1, 1024, 0, st>>>(P, eps, plan_only);
-  SAD_LAUNCH_CHECK();
-  {
-    const int64_t we = P.n_sets * (int64_t)eps;
-    const int64_t nblk = (we + kScanChunk - 1) / kScanChunk;
+  const int64_t we = P.n_sets * (int64_t)eps;
+  const int64_t nblk = (we + kScanChunk - 1) / kScanChunk;
+  auto list_scan = [&]() -> int {
     list_scan_reduce_kernel<<<(unsigned)nblk, 256, 0, st>>>(P, we);
     SAD_LAUNCH_CHECK();
     list_scan_top_kernel<<<1, 1024, 0, st>>>(P, nblk);
     SAD_LAUNCH_CHECK();
     list_scan_down_kernel<<<(unsigned)nblk, 256, 0, st>>>(P, we, plan_only);
     SAD_LAUNCH_CHECK();
+    return SAD_OK;
+  };
+  rank_setup_kernel<<<1, 1024, 0, st>>>(d_n, (int32_t)n, P);
+  SAD_LAUNCH_CHECK();
+  if (P.n_sets > 1) {
+    rank_setmaps_kernel<<<gsets, 256, 0, st>>>(P);
+    SAD_LAUNCH_CHECK();
   }
-  if (plan_only) return SAD_OK;
+  rank_init_kernel<<<grid_for(we + kMaxM, 256), 256, 0, st>>>(P, eps, !plan_only);
+  SAD_LAUNCH_CHECK();
+  if (!plan_only) {
+    lengths_kernel<<<grid_for(n, 256), 256, 0, st>>>(lengths, k, P);
+    SAD_LAUNCH_CHECK();
+  }
+  if (word_max && !plan_only) {
+    copy_word_max_kernel<<<grid_for(eps, 256), 256, 0, st>>>(word_max, eps, P);
+    SAD_LAUNCH_CHECK();
+  } else {
+    dim3 g((eps + 255) / 256, 1);
+    int64_t slices = ((int64_t)num_sms() * 8 + g.x - 1) / g.x;
+    if (slices > (n + 63) / 64) slices = (n + 63) / 64;
+    if (slices < 1) slices = 1;
+    g.y = (unsigned)slices;
+    // the plan counts the excess entries here; a run counts them in the plane kernel
+    colmax_kernel<<<g, 256, 0, st>>>(counts, eps, P, plan_only);
+    SAD_LAUNCH_CHECK();
+  }
+  colmap_kernel<<<1, 1024, 0, st>>>(P, eps, plan_only);
+  SAD_LAUNCH_CHECK();
+  if (plan_only) return list_scan();
   if (P.n_sets == 1) {
     lensort_scan_kernel<<<1, 1024, 0, st>>>(P);
     SAD_LAUNCH_CHECK();
@@ -972,12 +1007,17 @@ int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *le
     planes_kernel<<<(unsigned)(groups < cap ? groups : cap), 256, smem, st>>>(counts, eps, P);
     SAD_LAUNCH_CHECK();
   }
+  int rc = list_scan();
+  if (rc) return rc;
+  if (P.depth_cap >= 1 && P.list_cap > 0) {
+    group_lists_kernel<<<grid_for(P.list_cap, 256), 256, 0, st>>>(P, eps);
+    SAD_LAUNCH_CHECK();
+  }
   tiles_kernel<<<gsets, 1024, 0, st>>>(P);
   SAD_LAUNCH_CHECK();
   if (P.depth_cap >= 1 && P.block_cap > 0) {
     // the residual only exists when the planes are cut below the largest count
     const int identity = P.block_cap >= P.tiles_total ? 1 : 0;
-    const int64_t we = P.n_sets * (int64_t)eps;
     const unsigned gw = (unsigned)(we < num_sms() * 8 ? we : num_sms() * 8);
     if (!identity) {
       residual_mark_kernel<<<gw, 256, 0, st>>>(P, eps);

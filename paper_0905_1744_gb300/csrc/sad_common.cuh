@@ -38,7 +38,8 @@ struct WsHeader {
   int64_t pairs_total;   // residual pair contributions
   int32_t n_blocks;      // residual tiles (dense 128 x 256 blocks) in use
   int32_t m_max;         // largest m = L - k + 1 of the set
-  int32_t pad[48];
+  unsigned long long flat_count;  // excess entries appended by the plane kernel
+  int32_t pad[46];
 };
 static_assert(sizeof(WsHeader) == 256, "header is 256 bytes");
 
@@ -117,7 +118,7 @@ inline RankShape shape_single(int64_t n) {
 struct RankLayout {
   size_t sets, seq_set, row_set, T, secend, thist, tau_sorted, mhist, perm, rec, depth, tiles,
       acc, cnt_gt, list_off, pair_off, cursor, tile_of, block_of, sortbuf, scanblk, colmap, lists,
-      planes, rblocks;
+      flat, planes, rblocks;
   size_t fixed_bytes;    // everything that does not depend on the capacities
   size_t bytes;          // total
   RankShape shape;
@@ -156,6 +157,7 @@ inline RankLayout rank_layout(const RankShape &sh, int64_t eps, const RankCaps &
   L.fixed_bytes = o;
   L.colmap = take(sizeof(int32_t) * (size_t)(caps.k_cap > 0 ? caps.k_cap : 1));
   L.lists = take(2 * sizeof(int32_t) * (size_t)(caps.list_cap > 0 ? caps.list_cap : 1));
+  L.flat = take(2 * sizeof(int32_t) * (size_t)(caps.list_cap > 0 ? caps.list_cap : 1));
   o = align_up(o, 1024);
   L.planes = o;
   o = align_up(o + (size_t)sh.rows_total * (size_t)caps.k_cap, 1024);

@@ -72,12 +72,12 @@ def _load():
         lib.sad_launch_count.restype = ctypes.c_uint64
         lib.sad_workspace_bytes.argtypes = [i32, i32, i32, i32, i32, i32]
         lib.sad_workspace_bytes.restype = sz
-        lib.kmer_count.argtypes = [P, P, i32, i32, i32, P, P, sz, P]
+        lib.kmer_count.argtypes = [P, P, i32, i32, i32, P, P, P, sz, P]
         lib.kmer_count.restype = ctypes.c_int
         lib.kmer_rank_plan.argtypes = [P, i32, i32, i32, ctypes.POINTER(RankPlan), P, sz, P]
         lib.kmer_rank_plan.restype = ctypes.c_int
-        lib.kmer_rank.argtypes = [P, P, i32, i32, i32, ctypes.POINTER(RankPlan), P, P, P, P, sz,
-                                  P]
+        lib.kmer_rank.argtypes = [P, P, P, i32, i32, i32, ctypes.POINTER(RankPlan), P, P, P, P,
+                                  sz, P]
         lib.kmer_rank.restype = ctypes.c_int
         lib.partition.argtypes = [P, P, i32, i32, P, P, P, P, sz, P]
         lib.partition.restype = ctypes.c_int
@@ -86,8 +86,8 @@ def _load():
         lib.sad_batch_plan_make.argtypes = [P, P, P, P, i32, i32, i32, ctypes.POINTER(BatchPlan),
                                             P, sz, P]
         lib.sad_batch_plan_make.restype = ctypes.c_int
-        lib.sad_batch_rank.argtypes = [P, P, P, i32, i32, ctypes.POINTER(BatchPlan), P, P, P, P,
-                                       sz, P]
+        lib.sad_batch_rank.argtypes = [P, P, P, P, i32, i32, ctypes.POINTER(BatchPlan), P, P, P,
+                                       P, sz, P]
         lib.sad_batch_rank.restype = ctypes.c_int
         lib.sad_batch_partition.argtypes = [P, P, P, P, ctypes.POINTER(BatchPlan), P, P, P, P, sz,
                                             P]
@@ -164,15 +164,17 @@ class Workspace:
 
 def kmer_count(codes: torch.Tensor, offsets: torch.Tensor, k: int = 3, alphabet: int = 20,
                ws: Workspace | None = None, out: torch.Tensor | None = None, stream=None,
-               check: bool = True) -> torch.Tensor:
-    """int32 [N, alphabet**k] count vectors (Sec. 3, "k-mer Rank")."""
+               check: bool = True, word_max: torch.Tensor | None = None) -> torch.Tensor:
+    """int32 [N, alphabet**k] count vectors (Sec. 3, "k-mer Rank"). If ``word_max``
+    (int32 [alphabet**k]) is given it receives the largest count of every word."""
     n = offsets.numel() - 1
     ws = ws or Workspace(codes.device)
     ws.ensure(workspace_bytes(OP_COUNT, n, k, alphabet))
     if out is None:
         out = torch.empty((n, alphabet ** k), dtype=torch.int32, device=codes.device)
     _check(_load().kmer_count(_ptr(codes), _ptr(offsets), n, k, alphabet, _ptr(out),
-                              _ptr(ws.buf), ws.nbytes, _stream(stream)), "kmer_count")
+                              _ptr(word_max), _ptr(ws.buf), ws.nbytes, _stream(stream)),
+           "kmer_count")
     if check:
         ws.check("kmer_count", stream)
     return out
@@ -193,7 +195,8 @@ def kmer_rank_plan(counts: torch.Tensor, k: int = 3, alphabet: int = 20, depth: 
 
 def kmer_rank(counts: torch.Tensor, lengths: torch.Tensor, k: int = 3, alphabet: int = 20,
               ws: Workspace | None = None, with_rank: bool = True, stream=None,
-              out=None, check: bool = True, plan: RankPlan | None = None, depth: int = 0):
+              out=None, check: bool = True, plan: RankPlan | None = None, depth: int = 0,
+              word_max: torch.Tensor | None = None):
     """(key_hi uint64, key_lo uint64, rank float64 | None), Eq. 1 and Eq. 3.
 
     ``plan``: a RankPlan from kmer_rank_plan (reused as is); if None, one is made
@@ -212,7 +215,8 @@ def kmer_rank(counts: torch.Tensor, lengths: torch.Tensor, k: int = 3, alphabet:
     else:
         hi, lo, rank = out
     lengths = lengths.to(device=dev, dtype=torch.int32).contiguous()
-    _check(_load().kmer_rank(_ptr(counts), _ptr(lengths), n, k, alphabet, ctypes.byref(plan),
+    _check(_load().kmer_rank(_ptr(counts), _ptr(lengths), _ptr(word_max), n, k, alphabet,
+                             ctypes.byref(plan),
                              _ptr(hi), _ptr(lo), _ptr(rank), _ptr(ws.buf), ws.nbytes,
                              _stream(stream)), "kmer_rank")
     if check:
@@ -246,9 +250,11 @@ def partition_set(codes: torch.Tensor, offsets: torch.Tensor, p: int, k: int = 3
                   depth: int = 0):
     """count -> rank -> partition of one sequence set on the device."""
     ws = ws or Workspace(codes.device)
-    counts = kmer_count(codes, offsets, k, alphabet, ws=ws, stream=stream)
+    word_max = torch.empty(alphabet ** k, dtype=torch.int32, device=codes.device)
+    counts = kmer_count(codes, offsets, k, alphabet, ws=ws, stream=stream, word_max=word_max)
     lengths = (offsets[1:] - offsets[:-1]).to(torch.int32)
-    hi, lo, rank = kmer_rank(counts, lengths, k, alphabet, ws=ws, stream=stream, depth=depth)
+    hi, lo, rank = kmer_rank(counts, lengths, k, alphabet, ws=ws, stream=stream, depth=depth,
+                             word_max=word_max)
     offs, mem, piv = partition(hi, lo, p, ws=ws, stream=stream)
     return dict(counts=counts, key_hi=hi, key_lo=lo, rank=rank, bucket_offsets=offs,
                 members=mem, pivot_idx=piv)
@@ -330,6 +336,7 @@ class Batch:
         self.d_p = torch.from_numpy(self.p).to(dev)
         nt = int(self.n.sum())
         self.counts = torch.empty((nt, alphabet ** k), dtype=torch.int32, device=dev)
+        self.word_max = torch.empty(alphabet ** k, dtype=torch.int32, device=dev)
         self.key_hi = torch.empty(nt, dtype=torch.uint64, device=dev)
         self.key_lo = torch.empty(nt, dtype=torch.uint64, device=dev)
         self.rank = torch.empty(nt, dtype=torch.float64, device=dev)
@@ -349,7 +356,7 @@ class Batch:
 
     def count(self, stream=None):
         kmer_count(self.codes, self.offsets, self.k, self.alphabet, ws=self.ws_count,
-                   out=self.counts, stream=stream, check=False)
+                   out=self.counts, stream=stream, check=False, word_max=self.word_max)
 
     def plan(self, depth: int = 0, stream=None) -> BatchPlan:
         """Counts the batch and sizes the rank and partition workspaces (synchronous)."""
@@ -385,7 +392,8 @@ class Batch:
         lib, st = _load(), _stream(stream)
         if count:
             self.count(stream)
-        _check(lib.sad_batch_rank(_ptr(self.counts), _ptr(self.lengths), _ptr(self.d_n),
+        _check(lib.sad_batch_rank(_ptr(self.counts), _ptr(self.lengths), _ptr(self.word_max),
+                                  _ptr(self.d_n),
                                   self.k, self.alphabet, ctypes.byref(self.plan_),
                                   _ptr(self.key_hi), _ptr(self.key_lo), _ptr(self.rank),
                                   _ptr(self.ws_rank.buf), self.ws_rank.nbytes, st),

@@ -62,7 +62,7 @@ def test_argument_errors_need_no_gpu(lib):
     lib.partition.argtypes = [P, P, ctypes.c_int32, ctypes.c_int32, P, P, P, P, ctypes.c_size_t, P]
     assert lib.partition(None, None, 10, 0, None, None, None, None, 0, None) == 1
     assert lib.partition(None, None, 10, 11, None, None, None, None, 0, None) == 1
-    lib.kmer_rank.argtypes = [P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, P, P,
-                              P, ctypes.c_size_t, P]
-    assert lib.kmer_rank(None, None, 10, 9, 20, None, None, None, None, None, 0, None) == 5
-    assert lib.kmer_rank(None, None, -1, 3, 20, None, None, None, None, None, 0, None) == 1
+    lib.kmer_rank.argtypes = [P, P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, P,
+                              P, P, ctypes.c_size_t, P]
+    assert lib.kmer_rank(None, None, None, 10, 9, 20, None, None, None, None, None, 0, None) == 5
+    assert lib.kmer_rank(None, None, None, -1, 3, 20, None, None, None, None, None, 0, None) == 1

@@ -68,10 +68,13 @@ def test_count_reports_bad_input(sad):
 
 # ------------------------------------------------------------------- rank ---
 
-def check_rank(sad, oracle_mod, s, rows=None, k=3, alphabet=20, depth=0):
-    counts_g = sad.kmer_count(dev(s.codes), dev(s.offsets), k, alphabet)
+def check_rank(sad, oracle_mod, s, rows=None, k=3, alphabet=20, depth=0, word_max=False):
+    wm = torch.empty(alphabet ** k, dtype=torch.int32, device="cuda") if word_max else None
+    counts_g = sad.kmer_count(dev(s.codes), dev(s.offsets), k, alphabet, word_max=wm)
+    if wm is not None:
+        np.testing.assert_array_equal(host(wm), host(counts_g).max(axis=0))
     lengths = dev(s.lengths.astype(np.int32))
-    hi, lo, rank = sad.kmer_rank(counts_g, lengths, k, alphabet, depth=depth)
+    hi, lo, rank = sad.kmer_rank(counts_g, lengths, k, alphabet, depth=depth, word_max=wm)
     hi, lo, rank = host(hi), host(lo), host(rank)
     counts = oracle_mod.kmer_count(s.codes, s.offsets, k, alphabet)
     if rows is None:
@@ -94,18 +97,20 @@ def test_rank_sizes_and_ragged_tails(sad, oracle_mod, n):
     check_rank(sad, oracle_mod, s)
 
 
-@pytest.mark.parametrize("depth", [0, 1, 2, 3])
-def test_rank_family_set_several_tiles(sad, oracle_mod, depth):
+@pytest.mark.parametrize("depth,word_max", [(0, False), (1, False), (2, False), (3, False),
+                                            (0, True), (1, True), (2, True)])
+def test_rank_family_set_several_tiles(sad, oracle_mod, depth, word_max):
     sets = datagen.family_set(6, 230, lambda r: int(r.integers(40, 900)), p=4, seed=3, stream=9)
-    check_rank(sad, oracle_mod, sets, depth=depth)
+    check_rank(sad, oracle_mod, sets, depth=depth, word_max=word_max)
 
 
-@pytest.mark.parametrize("depth", [0, 1, 5, 40])
-def test_rank_small_alphabet_deep_planes(sad, oracle_mod, depth):
+@pytest.mark.parametrize("depth,word_max", [(0, False), (1, False), (5, False), (40, False),
+                                            (1, True), (40, True)])
+def test_rank_small_alphabet_deep_planes(sad, oracle_mod, depth, word_max):
     # 4 letters, k = 3: 64 words, counts up to hundreds -> many threshold sections,
     # and a residual of long excess lists when the planes are cut
     s = datagen.random_small(300, 3, 2500, seed=11, alphabet=4)
-    check_rank(sad, oracle_mod, s, k=3, alphabet=4, depth=depth)
+    check_rank(sad, oracle_mod, s, k=3, alphabet=4, depth=depth, word_max=word_max)
 
 
 @pytest.mark.parametrize("depth", [0, 1, 7])
