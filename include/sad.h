@@ -92,8 +92,7 @@ size_t sad_workspace_bytes(int32_t op, int32_t n_seq, int32_t k, int32_t alphabe
  *              tau = sum_r a_r * alphabet^(k-1-r) (first letter most significant).
  *   d_word_max (nullable) int32 [eps] output: the largest count of every word
  *              over the n_seq sequences; passing it to kmer_rank saves that call
- *              a pass over the counts. Needs eps <= 16384 (else
- *              SAD_ERR_UNSUPPORTED; call without it).
+ *              a pass over the counts.
  *   d_ws       workspace of sad_workspace_bytes(SAD_OP_COUNT, ...) bytes.
  */
 int kmer_count(const uint8_t *d_codes, const int64_t *d_offsets, int32_t n_seq,

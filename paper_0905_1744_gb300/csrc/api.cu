@@ -166,7 +166,6 @@ int kmer_count(const uint8_t *d_codes, const int64_t *d_offsets, int32_t n_seq, 
   if (n_seq == 0) return SAD_OK;
   if (!d_codes || !d_offsets || !d_counts || !aligned(d_counts, 16) || !aligned(d_offsets, 8))
     return SAD_ERR_INVALID_ARGUMENT;
-  if (d_word_max && eps > 16384) return SAD_ERR_UNSUPPORTED;
   return count_launch(d_codes, d_offsets, n_seq, k, alphabet, (int32_t)eps, d_counts,
                       d_word_max, static_cast<WsHeader *>(d_ws),
                       static_cast<cudaStream_t>(stream));

@@ -7,8 +7,9 @@
 // lane 31 loads them itself. Each window's word is counted in the warp's
 // private shared-memory histogram (two 16-bit bins per 32-bit word), which is
 // then streamed out as the dense int32 row and cleared in the same pass. If asked,
-// the same pass keeps the block's largest count of every word (shared memory) and
-// merges it into the per-word maximum over all sequences at the end.
+// the same pass raises the per-word maximum over all sequences (an atomic max,
+// skipped when the current value already covers the count: values only grow, so
+// a stale read can only cost a redundant atomic).
 #include "sad_common.cuh"
 
 namespace sad {
@@ -40,11 +41,8 @@ __global__ void __launch_bounds__(128) kmer_count_kernel(const uint8_t *__restri
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int words = (eps + 1) >> 1;
   uint32_t *hist = smem + (size_t)wid * words;
-  int32_t *smax = reinterpret_cast<int32_t *>(smem + (size_t)warps * words);  // [eps] if word_max
   for (int i = lane; i < words; i += 32) hist[i] = 0;
-  if (word_max)
-    for (int i = threadIdx.x; i < eps; i += blockDim.x) smax[i] = 0;
-  __syncthreads();
+  __syncwarp();
   const int64_t codes_end = offsets[n];
 
   for (int64_t x = (int64_t)blockIdx.x * warps + wid; x < n; x += (int64_t)gridDim.x * warps) {
@@ -96,27 +94,24 @@ __global__ void __launch_bounds__(128) kmer_count_kernel(const uint8_t *__restri
             make_int4((int)(a & 0xFFFFu), (int)(a >> 16), (int)(b & 0xFFFFu), (int)(b >> 16));
         reinterpret_cast<int4 *>(row)[q] = c4;
         if (word_max && (a | b)) {
-          if (c4.x) atomicMax(&smax[4 * q + 0], c4.x);
-          if (c4.y) atomicMax(&smax[4 * q + 1], c4.y);
-          if (c4.z) atomicMax(&smax[4 * q + 2], c4.z);
-          if (c4.w) atomicMax(&smax[4 * q + 3], c4.w);
+          const int32_t cv[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            volatile int32_t *wm = word_max + 4 * q + u;
+            if (cv[u] > *wm) atomicMax(word_max + 4 * q + u, cv[u]);
+          }
         }
       }
     } else {
       for (int t = lane; t < eps; t += 32) {
         const int c = (int)((hist[t >> 1] >> (16 * (t & 1))) & 0xFFFFu);
         row[t] = c;
-        if (word_max && c) atomicMax(&smax[t], c);
+        if (word_max && c > *(volatile int32_t *)(word_max + t)) atomicMax(word_max + t, c);
       }
       __syncwarp();
       for (int i = lane; i < words; i += 32) hist[i] = 0;
     }
     __syncwarp();
-  }
-  if (word_max) {
-    __syncthreads();
-    for (int i = threadIdx.x; i < eps; i += blockDim.x)
-      if (smax[i]) atomicMax(&word_max[i], smax[i]);
   }
 }
 
@@ -125,12 +120,12 @@ int launch_count(const uint8_t *codes, const int64_t *offsets, int32_t n, int32_
                  int32_t eps, int32_t *counts, int32_t *word_max, WsHeader *hdr,
                  cudaStream_t st) {
   const size_t per_warp = sizeof(uint32_t) * (size_t)((eps + 1) / 2);
-  const size_t max_bytes = word_max ? sizeof(int32_t) * (size_t)eps : 0;
   int warps = (int)((96 * 1024) / per_warp);
   warps = warps < 1 ? 1 : (warps > 4 ? 4 : warps);
-  const size_t smem = per_warp * warps + max_bytes;
+  const size_t smem = per_warp * warps;
   if (word_max) {
-    if (cudaMemsetAsync(word_max, 0, max_bytes, st) != cudaSuccess) return SAD_ERR_CUDA;
+    if (cudaMemsetAsync(word_max, 0, sizeof(int32_t) * (size_t)eps, st) != cudaSuccess)
+      return SAD_ERR_CUDA;
   }
   if (smem > 227 * 1024) return SAD_ERR_UNSUPPORTED;
   auto kern = kmer_count_kernel<K>;

@@ -685,11 +685,20 @@ __global__ void __launch_bounds__(256) planes_kernel(const int32_t *__restrict__
         if (xs[r] < 0) continue;
         const int64_t pos = g * kPlaneRows + r;
         const int64_t wbase = (int64_t)set_of_row(P, pos) * eps;
-        for (int tau = threadIdx.x; tau < eps; tau += blockDim.x) {
-          const int32_t c = s_cnt[r * eps + tau];
-          if (c > dkeep) {
+        for (int base = 0; base < eps; base += blockDim.x) {  // uniform trip count
+          const int tau = base + threadIdx.x;
+          const int32_t c = tau < eps ? s_cnt[r * eps + tau] : 0;
+          const bool ex = c > dkeep;
+          // one atomic per warp reserves the warp's slots in the flat list
+          const unsigned m = __ballot_sync(0xffffffffu, ex);
+          if (m == 0) continue;
+          const int lane = threadIdx.x & 31;
+          unsigned long long first = 0;
+          if (lane == __ffs(m) - 1) first = atomicAdd(&P.hdr->flat_count, (unsigned long long)__popc(m));
+          first = __shfl_sync(0xffffffffu, first, __ffs(m) - 1);
+          if (ex) {
             atomicAdd(&P.cnt_gt[wbase + tau], 1);
-            const unsigned long long slot = atomicAdd(&P.hdr->flat_count, 1ull);
+            const unsigned long long slot = first + __popc(m & ((1u << lane) - 1u));
             if (slot < (unsigned long long)P.list_cap)
               P.flat[slot] = make_int2((int32_t)pos, tau | ((c - dkeep) << 16));
           }
@@ -811,6 +820,28 @@ __global__ void __launch_bounds__(1024) tiles_kernel(RankPtrs P) {
 // the sequence's own pair.
 constexpr int kListChunk = 1024;
 
+// Ascending bitonic sort by .x of s[0, n), n <= kListChunk, padded with INT_MAX.
+__device__ __forceinline__ void block_sort_by_row(int2 *s, int n) {
+  int p2 = 1;
+  while (p2 < n) p2 <<= 1;
+  for (int i = n + threadIdx.x; i < p2; i += blockDim.x) s[i] = make_int2(0x7FFFFFFF, 0);
+  __syncthreads();
+  for (int size = 2; size <= p2; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < (p2 >> 1); i += blockDim.x) {
+        const int a = 2 * stride * (i / stride) + (i % stride), b = a + stride;
+        const bool asc = (a & size) == 0;
+        const int2 x = s[a], y = s[b];
+        if (asc ? (y.x < x.x) : (x.x < y.x)) {
+          s[a] = y;
+          s[b] = x;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
 template <typename Fn>
 __device__ __forceinline__ void for_each_residual_pair(const RankPtrs &P, int32_t eps, Fn fn) {
   __shared__ int2 s_u[kListChunk], s_v[kListChunk];
@@ -822,13 +853,20 @@ __device__ __forceinline__ void for_each_residual_pair(const RankPtrs &P, int32_
     const RankSet e = P.sets[w / eps];
     const int64_t cfull = dev_n_pad(e.n) / kColBlock;
     // chunk pairs (cu, cv) of the list with cu <= cv; pairs u <= v within them
+    // chunks sorted by stored row, so that neighbouring pairs land in neighbouring
+    // columns of the same tile row
     for (int64_t cv = 0; cv < len; cv += kListChunk) {
       const int nv = (int)min((int64_t)kListChunk, len - cv);
+      __syncthreads();
       for (int i = threadIdx.x; i < nv; i += blockDim.x) s_v[i] = P.lists[base + cv + i];
+      block_sort_by_row(s_v, nv);
       for (int64_t cu = 0; cu <= cv; cu += kListChunk) {
         const int nu = (int)min((int64_t)kListChunk, len - cu);
         __syncthreads();
-        for (int i = threadIdx.x; i < nu; i += blockDim.x) s_u[i] = P.lists[base + cu + i];
+        if (cu != cv) {
+          for (int i = threadIdx.x; i < nu; i += blockDim.x) s_u[i] = P.lists[base + cu + i];
+          block_sort_by_row(s_u, nu);
+        }
         __syncthreads();
         const bool same = cu == cv;
         const int npairs = nu * nv;  // <= kListChunk^2
