@@ -7,9 +7,10 @@
 // lane 31 loads them itself. Each window's word is counted in the warp's
 // private shared-memory histogram (two 16-bit bins per 32-bit word), which is
 // then streamed out as the dense int32 row and cleared in the same pass. If asked,
-// the same pass raises the per-word maximum over all sequences (an atomic max,
-// skipped when the current value already covers the count: values only grow, so
-// a stale read can only cost a redundant atomic).
+// the same pass keeps, per block, which words occurred (a bit each) and the
+// largest count of those seen twice or more (a byte each, counts above 255 going
+// straight to global memory), and merges them into the per-word maximum over all
+// sequences when the block is done.
 #include "sad_common.cuh"
 
 namespace sad {
@@ -29,6 +30,28 @@ __device__ __forceinline__ uint32_t byte_of(const uint32_t (&w)[8], int b) {
   return (w[b >> 2] >> (8 * (b & 3))) & 0xFFu;
 }
 
+// Word t has count c in one sequence: set its presence bit; counts >= 2 raise its
+// byte maximum (compare-and-swap on the containing word; rare), counts above 255
+// go to the global maximum directly.
+__device__ __forceinline__ void note_count(uint32_t *present, uint32_t *max8, int32_t *word_max,
+                                           int t, int32_t c) {
+  if (c <= 0) return;
+  atomicOr(&present[t >> 5], 1u << (t & 31));
+  if (c < 2) return;
+  if (c > 255) {
+    atomicMax(word_max + t, c);
+    return;
+  }
+  const uint32_t sh = 8u * (uint32_t)(t & 3);
+  uint32_t old = max8[t >> 2];
+  while ((int32_t)((old >> sh) & 0xFFu) < c) {
+    const uint32_t upd = (old & ~(0xFFu << sh)) | ((uint32_t)c << sh);
+    const uint32_t seen = atomicCAS(&max8[t >> 2], old, upd);
+    if (seen == old) break;
+    old = seen;
+  }
+}
+
 template <int K>
 __global__ void __launch_bounds__(128) kmer_count_kernel(const uint8_t *__restrict__ codes,
                                                         const int64_t *__restrict__ offsets,
@@ -41,8 +64,15 @@ __global__ void __launch_bounds__(128) kmer_count_kernel(const uint8_t *__restri
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int words = (eps + 1) >> 1;
   uint32_t *hist = smem + (size_t)wid * words;
+  // per-block word maxima: presence bits and byte maxima of counts >= 2
+  uint32_t *present = smem + (size_t)warps * words;             // [ceil(eps / 32)]
+  uint32_t *max8 = present + ((eps + 31) >> 5);                  // [ceil(eps / 4)]
   for (int i = lane; i < words; i += 32) hist[i] = 0;
-  __syncwarp();
+  if (word_max) {
+    for (int i = threadIdx.x; i < ((eps + 31) >> 5); i += blockDim.x) present[i] = 0;
+    for (int i = threadIdx.x; i < ((eps + 3) >> 2); i += blockDim.x) max8[i] = 0;
+  }
+  __syncthreads();
   const int64_t codes_end = offsets[n];
 
   for (int64_t x = (int64_t)blockIdx.x * warps + wid; x < n; x += (int64_t)gridDim.x * warps) {
@@ -96,22 +126,27 @@ __global__ void __launch_bounds__(128) kmer_count_kernel(const uint8_t *__restri
         if (word_max && (a | b)) {
           const int32_t cv[4] = {c4.x, c4.y, c4.z, c4.w};
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            volatile int32_t *wm = word_max + 4 * q + u;
-            if (cv[u] > *wm) atomicMax(word_max + 4 * q + u, cv[u]);
-          }
+          for (int u = 0; u < 4; ++u) note_count(present, max8, word_max, 4 * q + u, cv[u]);
         }
       }
     } else {
       for (int t = lane; t < eps; t += 32) {
         const int c = (int)((hist[t >> 1] >> (16 * (t & 1))) & 0xFFFFu);
         row[t] = c;
-        if (word_max && c > *(volatile int32_t *)(word_max + t)) atomicMax(word_max + t, c);
+        if (word_max) note_count(present, max8, word_max, t, c);
       }
       __syncwarp();
       for (int i = lane; i < words; i += 32) hist[i] = 0;
     }
     __syncwarp();
+  }
+  if (word_max) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < eps; t += blockDim.x) {
+      const int32_t m8 = (int32_t)((max8[t >> 2] >> (8 * (t & 3))) & 0xFFu);
+      const int32_t v = m8 > 0 ? m8 : (int32_t)((present[t >> 5] >> (t & 31)) & 1u);
+      if (v) atomicMax(word_max + t, v);
+    }
   }
 }
 
@@ -120,9 +155,11 @@ int launch_count(const uint8_t *codes, const int64_t *offsets, int32_t n, int32_
                  int32_t eps, int32_t *counts, int32_t *word_max, WsHeader *hdr,
                  cudaStream_t st) {
   const size_t per_warp = sizeof(uint32_t) * (size_t)((eps + 1) / 2);
+  const size_t max_bytes =
+      word_max ? sizeof(uint32_t) * (size_t)(((eps + 31) >> 5) + ((eps + 3) >> 2)) : 0;
   int warps = (int)((96 * 1024) / per_warp);
   warps = warps < 1 ? 1 : (warps > 4 ? 4 : warps);
-  const size_t smem = per_warp * warps;
+  const size_t smem = per_warp * warps + max_bytes;
   if (word_max) {
     if (cudaMemsetAsync(word_max, 0, sizeof(int32_t) * (size_t)eps, st) != cudaSuccess)
       return SAD_ERR_CUDA;

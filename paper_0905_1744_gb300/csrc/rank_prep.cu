@@ -246,23 +246,33 @@ __global__ void colmax_kernel(const int32_t *__restrict__ counts, int32_t eps, R
   int32_t mx = 0, mn = 0, gt = 0;
   int32_t cur = r0 < r1 ? set_of_seq(P, r0) : 0;
   int64_t r = r0;
-  for (; r + 4 <= r1; r += 4) {
-    int32_t v[4];
+  if (P.n_sets == 1) {
+    for (; r + 4 <= r1; r += 4) {
+      const int32_t a = __ldg(counts + (r + 0) * eps + tau);
+      const int32_t b = __ldg(counts + (r + 1) * eps + tau);
+      const int32_t c = __ldg(counts + (r + 2) * eps + tau);
+      const int32_t d = __ldg(counts + (r + 3) * eps + tau);
+      mx = max(mx, max(max(a, b), max(c, d)));
+      mn = min(mn, min(min(a, b), min(c, d)));
+      gt += (a > D) + (b > D) + (c > D) + (d > D);
+    }
+  } else {
+    for (; r + 4 <= r1; r += 4) {
+      int32_t v[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) v[u] = __ldg(counts + (r + u) * eps + tau);
+      for (int u = 0; u < 4; ++u) v[u] = __ldg(counts + (r + u) * eps + tau);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      mx = max(mx, v[u]);
-      mn = min(mn, v[u]);
-      if (P.n_sets > 1) {
+      for (int u = 0; u < 4; ++u) {
+        mx = max(mx, v[u]);
+        mn = min(mn, v[u]);
         const int32_t s = P.seq_set[r + u];
         if (s != cur) {
           if (D >= 1 && gt) atomicAdd(&P.cnt_gt[(int64_t)cur * eps + tau], gt);
           gt = 0;
           cur = s;
         }
+        gt += v[u] > D;
       }
-      gt += v[u] > D;
     }
   }
   for (; r < r1; ++r) {
