@@ -141,11 +141,15 @@ __global__ void __launch_bounds__(128) kmer_count_kernel(const uint8_t *__restri
     __syncwarp();
   }
   if (word_max) {
+    // blocks start at different words and skip words whose maximum already
+    // covers theirs, so that the atomics do not queue on the same addresses
     __syncthreads();
-    for (int t = threadIdx.x; t < eps; t += blockDim.x) {
+    const int off = (int)(((int64_t)blockIdx.x * 1024) % eps);
+    for (int i = threadIdx.x; i < eps; i += blockDim.x) {
+      const int t = i + off < eps ? i + off : i + off - eps;
       const int32_t m8 = (int32_t)((max8[t >> 2] >> (8 * (t & 3))) & 0xFFu);
       const int32_t v = m8 > 0 ? m8 : (int32_t)((present[t >> 5] >> (t & 31)) & 1u);
-      if (v) atomicMax(word_max + t, v);
+      if (v && v > *(volatile int32_t *)(word_max + t)) atomicMax(word_max + t, v);
     }
   }
 }

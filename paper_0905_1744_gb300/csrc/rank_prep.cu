@@ -617,6 +617,8 @@ __global__ void __launch_bounds__(256) planes_kernel(const int32_t *__restrict__
                                                      int32_t eps, RankPtrs P) {
   extern __shared__ uint16_t s_cnt[];  // [kPlaneRows][eps]
   __shared__ int32_t s_max[kPlaneRows], s_sum[kPlaneRows];
+  __shared__ int32_t s_scan[32];
+  __shared__ unsigned long long s_first;
   if (P.hdr->status != 0) return;
   const int32_t k_eff = (int32_t)P.hdr->k_eff;
   const int32_t k_pad = P.hdr->k_pad;
@@ -689,28 +691,32 @@ __global__ void __launch_bounds__(256) planes_kernel(const int32_t *__restrict__
     __syncthreads();
     if (residual) {
       // excess entries of the rows, appended unordered: (stored row, word | excess << 16);
-      // the per-(set, word) sizes are counted for the grouping that follows
+      // the per-(set, word) sizes are counted for the grouping that follows. The
+      // block counts its entries first and reserves their slots with one atomic.
+      int32_t mine = 0;
+#pragma unroll
+      for (int r = 0; r < kPlaneRows; ++r)
+        if (xs[r] >= 0)
+          for (int tau = threadIdx.x; tau < eps; tau += blockDim.x)
+            mine += s_cnt[r * eps + tau] > dkeep;
+      int32_t total;
+      const int32_t incl = block_scan_incl<int32_t>(mine, s_scan, &total);
+      if (threadIdx.x == 0)
+        s_first = total ? atomicAdd(&P.hdr->flat_count, (unsigned long long)total) : 0ull;
+      __syncthreads();
+      unsigned long long slot = s_first + (unsigned long long)(incl - mine);
 #pragma unroll
       for (int r = 0; r < kPlaneRows; ++r) {
-        if (xs[r] < 0) continue;
+        if (xs[r] < 0 || mine == 0) continue;
         const int64_t pos = g * kPlaneRows + r;
         const int64_t wbase = (int64_t)set_of_row(P, pos) * eps;
-        for (int base = 0; base < eps; base += blockDim.x) {  // uniform trip count
-          const int tau = base + threadIdx.x;
-          const int32_t c = tau < eps ? s_cnt[r * eps + tau] : 0;
-          const bool ex = c > dkeep;
-          // one atomic per warp reserves the warp's slots in the flat list
-          const unsigned m = __ballot_sync(0xffffffffu, ex);
-          if (m == 0) continue;
-          const int lane = threadIdx.x & 31;
-          unsigned long long first = 0;
-          if (lane == __ffs(m) - 1) first = atomicAdd(&P.hdr->flat_count, (unsigned long long)__popc(m));
-          first = __shfl_sync(0xffffffffu, first, __ffs(m) - 1);
-          if (ex) {
+        for (int tau = threadIdx.x; tau < eps; tau += blockDim.x) {
+          const int32_t c = s_cnt[r * eps + tau];
+          if (c > dkeep) {
             atomicAdd(&P.cnt_gt[wbase + tau], 1);
-            const unsigned long long slot = first + __popc(m & ((1u << lane) - 1u));
             if (slot < (unsigned long long)P.list_cap)
               P.flat[slot] = make_int2((int32_t)pos, tau | ((c - dkeep) << 16));
+            ++slot;
           }
         }
       }
