@@ -7,10 +7,11 @@
 // lane 31 loads them itself. Each window's word is counted in the warp's
 // private shared-memory histogram (two 16-bit bins per 32-bit word), which is
 // then streamed out as the dense int32 row and cleared in the same pass. If asked,
-// the same pass keeps, per block, which words occurred (a bit each) and the
-// largest count of those seen twice or more (a byte each, counts above 255 going
-// straight to global memory), and merges them into the per-word maximum over all
-// sequences when the block is done.
+// the same pass keeps which words occurred (a bit each, in a bitmap private to the
+// lane that writes the word: a lane always owns the same columns) and, per block,
+// the largest count of the words seen twice or more (a byte each, counts above
+// 255 going straight to global memory), and merges both into the per-word maximum
+// over all sequences when the block is done.
 #include "sad_common.cuh"
 
 namespace sad {
@@ -30,13 +31,9 @@ __device__ __forceinline__ uint32_t byte_of(const uint32_t (&w)[8], int b) {
   return (w[b >> 2] >> (8 * (b & 3))) & 0xFFu;
 }
 
-// Word t has count c in one sequence: set its presence bit; counts >= 2 raise its
-// byte maximum (compare-and-swap on the containing word; rare), counts above 255
-// go to the global maximum directly.
-__device__ __forceinline__ void note_count(uint32_t *present, uint32_t *max8, int32_t *word_max,
-                                           int t, int32_t c) {
-  if (c <= 0) return;
-  atomicOr(&present[t >> 5], 1u << (t & 31));
+// Word t has count c >= 2 in one sequence: raise its byte maximum (compare-and-swap
+// on the containing word), counts above 255 go to the global maximum directly.
+__device__ __forceinline__ void note_repeat(uint32_t *max8, int32_t *word_max, int t, int32_t c) {
   if (c < 2) return;
   if (c > 255) {
     atomicMax(word_max + t, c);
@@ -52,6 +49,17 @@ __device__ __forceinline__ void note_count(uint32_t *present, uint32_t *max8, in
   }
 }
 
+// Words of one warp's presence bitmap: 32 lanes x one word per 8 passes of quads
+// (eps divisible by 4) or per 32 passes of single columns.
+__host__ __device__ __forceinline__ int pres_words_of(int32_t eps) {
+  if ((eps & 3) == 0) {
+    const int passes = ((eps >> 2) + 31) / 32;
+    return 32 * ((passes + 7) / 8);
+  }
+  const int passes = (eps + 31) / 32;
+  return 32 * ((passes + 31) / 32);
+}
+
 template <int K>
 __global__ void __launch_bounds__(128) kmer_count_kernel(const uint8_t *__restrict__ codes,
                                                         const int64_t *__restrict__ offsets,
@@ -64,12 +72,14 @@ __global__ void __launch_bounds__(128) kmer_count_kernel(const uint8_t *__restri
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int words = (eps + 1) >> 1;
   uint32_t *hist = smem + (size_t)wid * words;
-  // per-block word maxima: presence bits and byte maxima of counts >= 2
-  uint32_t *present = smem + (size_t)warps * words;             // [ceil(eps / 32)]
-  uint32_t *max8 = present + ((eps + 31) >> 5);                  // [ceil(eps / 4)]
+  // word maxima: per warp a presence bitmap, [pass / 8][lane] words holding 4 bits
+  // (the 4 columns of the lane's quad) for each of 8 passes; per block byte maxima
+  const int pres_words = pres_words_of(eps);
+  uint32_t *present = smem + (size_t)warps * words + (size_t)wid * pres_words;
+  uint32_t *max8 = smem + (size_t)warps * (words + pres_words);  // [ceil(eps / 4)]
   for (int i = lane; i < words; i += 32) hist[i] = 0;
   if (word_max) {
-    for (int i = threadIdx.x; i < ((eps + 31) >> 5); i += blockDim.x) present[i] = 0;
+    for (int i = lane; i < pres_words; i += 32) present[i] = 0;
     for (int i = threadIdx.x; i < ((eps + 3) >> 2); i += blockDim.x) max8[i] = 0;
   }
   __syncthreads();
@@ -116,7 +126,8 @@ __global__ void __launch_bounds__(128) kmer_count_kernel(const uint8_t *__restri
     __syncwarp();
     int32_t *row = counts + x * (int64_t)eps;
     if ((eps & 3) == 0) {
-      for (int q = lane; q < (eps >> 2); q += 32) {
+      int pass = 0;
+      for (int q = lane; q < (eps >> 2); q += 32, ++pass) {
         const uint32_t a = hist[2 * q], b = hist[2 * q + 1];
         hist[2 * q] = 0;
         hist[2 * q + 1] = 0;
@@ -124,16 +135,25 @@ __global__ void __launch_bounds__(128) kmer_count_kernel(const uint8_t *__restri
             make_int4((int)(a & 0xFFFFu), (int)(a >> 16), (int)(b & 0xFFFFu), (int)(b >> 16));
         reinterpret_cast<int4 *>(row)[q] = c4;
         if (word_max && (a | b)) {
-          const int32_t cv[4] = {c4.x, c4.y, c4.z, c4.w};
-#pragma unroll
-          for (int u = 0; u < 4; ++u) note_count(present, max8, word_max, 4 * q + u, cv[u]);
+          const uint32_t nz = (c4.x > 0) | (c4.y > 0) << 1 | (c4.z > 0) << 2 | (c4.w > 0) << 3;
+          present[(pass >> 3) * 32 + lane] |= nz << (4 * (pass & 7));
+          if ((a | b) & 0xFFFEFFFEu) {  // some count >= 2
+            note_repeat(max8, word_max, 4 * q + 0, c4.x);
+            note_repeat(max8, word_max, 4 * q + 1, c4.y);
+            note_repeat(max8, word_max, 4 * q + 2, c4.z);
+            note_repeat(max8, word_max, 4 * q + 3, c4.w);
+          }
         }
       }
     } else {
-      for (int t = lane; t < eps; t += 32) {
+      int pass = 0;
+      for (int t = lane; t < eps; t += 32, ++pass) {
         const int c = (int)((hist[t >> 1] >> (16 * (t & 1))) & 0xFFFFu);
         row[t] = c;
-        if (word_max) note_count(present, max8, word_max, t, c);
+        if (word_max && c > 0) {
+          present[(pass >> 5) * 32 + lane] |= 1u << (pass & 31);
+          note_repeat(max8, word_max, t, c);
+        }
       }
       __syncwarp();
       for (int i = lane; i < words; i += 32) hist[i] = 0;
@@ -145,10 +165,25 @@ __global__ void __launch_bounds__(128) kmer_count_kernel(const uint8_t *__restri
     // covers theirs, so that the atomics do not queue on the same addresses
     __syncthreads();
     const int off = (int)(((int64_t)blockIdx.x * 1024) % eps);
+    const uint32_t *pres0 = smem + (size_t)warps * words;
     for (int i = threadIdx.x; i < eps; i += blockDim.x) {
       const int t = i + off < eps ? i + off : i + off - eps;
+      // the bit of word t: column quad q = t / 4 (or column t) is owned by lane q % 32
+      // in pass q / 32
+      int idx, bit;
+      if ((eps & 3) == 0) {
+        const int q = t >> 2, pass = q >> 5;
+        idx = (pass >> 3) * 32 + (q & 31);
+        bit = 4 * (pass & 7) + (t & 3);
+      } else {
+        const int pass = t >> 5;
+        idx = (pass >> 5) * 32 + (t & 31);
+        bit = pass & 31;
+      }
+      uint32_t any = 0;
+      for (int w = 0; w < warps; ++w) any |= pres0[(size_t)w * pres_words + idx];
       const int32_t m8 = (int32_t)((max8[t >> 2] >> (8 * (t & 3))) & 0xFFu);
-      const int32_t v = m8 > 0 ? m8 : (int32_t)((present[t >> 5] >> (t & 31)) & 1u);
+      const int32_t v = m8 > 0 ? m8 : (int32_t)((any >> bit) & 1u);
       if (v && v > *(volatile int32_t *)(word_max + t)) atomicMax(word_max + t, v);
     }
   }
@@ -159,10 +194,10 @@ int launch_count(const uint8_t *codes, const int64_t *offsets, int32_t n, int32_
                  int32_t eps, int32_t *counts, int32_t *word_max, WsHeader *hdr,
                  cudaStream_t st) {
   const size_t per_warp = sizeof(uint32_t) * (size_t)((eps + 1) / 2);
-  const size_t max_bytes =
-      word_max ? sizeof(uint32_t) * (size_t)(((eps + 31) >> 5) + ((eps + 3) >> 2)) : 0;
   int warps = (int)((96 * 1024) / per_warp);
   warps = warps < 1 ? 1 : (warps > 4 ? 4 : warps);
+  const size_t max_bytes =
+      word_max ? sizeof(uint32_t) * ((size_t)warps * pres_words_of(eps) + ((eps + 3) >> 2)) : 0;
   const size_t smem = per_warp * warps + max_bytes;
   if (word_max) {
     if (cudaMemsetAsync(word_max, 0, sizeof(int32_t) * (size_t)eps, st) != cudaSuccess)

@@ -26,7 +26,7 @@ struct RankPtrs {
   // residual of the counts above the plane depth, per (set, word)
   int32_t *cnt_gt;       // [n_sets * eps] sequences whose count of the word exceeds depth
   int64_t *list_off;     // [n_sets * eps + 1] start of each excess list
-  int64_t *pair_off;     // [n_sets * eps + 1] start of each list's pair range
+  int64_t *item_off;     // [n_sets * eps + 1] start of each list's work items
   int32_t *cursor;       // [n_sets * eps] fill cursor of the excess lists
   int2 *lists;           // [list_cap] (stored row, count - depth), grouped by (set, word)
   int2 *flat;            // [list_cap] (stored row, word | (count - depth) << 16), unordered

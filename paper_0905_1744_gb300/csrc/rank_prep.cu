@@ -63,7 +63,7 @@ RankPtrs rank_ptrs(void *ws, const RankLayout &L) {
   P.planes = b + L.planes;
   P.cnt_gt = reinterpret_cast<int32_t *>(b + L.cnt_gt);
   P.list_off = reinterpret_cast<int64_t *>(b + L.list_off);
-  P.pair_off = reinterpret_cast<int64_t *>(b + L.pair_off);
+  P.item_off = reinterpret_cast<int64_t *>(b + L.item_off);
   P.cursor = reinterpret_cast<int32_t *>(b + L.cursor);
   P.lists = reinterpret_cast<int2 *>(b + L.lists);
   P.flat = reinterpret_cast<int2 *>(b + L.flat);
@@ -402,10 +402,18 @@ __global__ void __launch_bounds__(1024) colmap_kernel(RankPtrs P, int32_t eps, i
 }
 
 // Offsets of the excess lists over all (set, word) entries w: list_off[w] =
-// prefix of c_w and pair_off[w] = prefix of c_w (c_w + 1) / 2, c_w = cnt_gt[w]
-// (0 when nothing is cut). Three passes: per-block totals, a scan of the block
-// totals, per-block scans with the block's carry.
+// prefix of c_w and item_off[w] = prefix of items(c_w), c_w = cnt_gt[w] (0 when
+// nothing is cut), where items(c) counts the pairs of kPairChunk-entry chunks of
+// a list of c entries (the residual's units of work). Three passes: per-block
+// totals, a scan of the block totals, per-block scans with the block's carry.
+// The number of residual pairs, sum c_w (c_w + 1) / 2, is added up on the side.
 constexpr int kScanChunk = 4096;
+constexpr int kPairChunk = 128;
+
+__host__ __device__ __forceinline__ int64_t items_of(int64_t c) {
+  const int64_t n = (c + kPairChunk - 1) / kPairChunk;
+  return n * (n + 1) / 2;
+}
 
 __device__ __forceinline__ bool residual_needed(const RankPtrs &P) {
   return P.hdr->depth < P.hdr->t_max;
@@ -415,18 +423,22 @@ __global__ void __launch_bounds__(256) list_scan_reduce_kernel(RankPtrs P, int64
   __shared__ int64_t s_warp[32];
   const bool on = residual_needed(P);
   const int64_t b0 = (int64_t)blockIdx.x * kScanChunk;
-  int64_t sl = 0, sp = 0;
+  int64_t sl = 0, sp = 0, sq = 0;
   for (int64_t w = b0 + threadIdx.x; w < b0 + kScanChunk && w < we; w += blockDim.x) {
     const int64_t c = on ? P.cnt_gt[w] : 0;
     sl += c;
-    sp += c * (c + 1) / 2;
+    sp += items_of(c);
+    sq += c * (c + 1) / 2;
   }
-  int64_t tl, tp;
+  int64_t tl, tp, tq;
   block_scan_incl<int64_t>(sl, s_warp, &tl);
   block_scan_incl<int64_t>(sp, s_warp, &tp);
+  block_scan_incl<int64_t>(sq, s_warp, &tq);
   if (threadIdx.x == 0) {
     P.scanblk[2 * blockIdx.x] = tl;
     P.scanblk[2 * blockIdx.x + 1] = tp;
+    if (tq) atomicAdd(reinterpret_cast<unsigned long long *>(&P.hdr->pairs_total),
+                      (unsigned long long)tq);
   }
 }
 
@@ -458,7 +470,7 @@ __global__ void __launch_bounds__(1024) list_scan_top_kernel(RankPtrs P, int64_t
   }
   if (threadIdx.x == 0) {
     P.hdr->list_total = s_l;
-    P.hdr->pairs_total = s_p;
+    P.hdr->items_total = s_p;
   }
 }
 
@@ -476,13 +488,13 @@ __global__ void __launch_bounds__(256) list_scan_down_kernel(RankPtrs P, int64_t
   for (int64_t base = b0; base < b0 + kScanChunk && base < we; base += blockDim.x) {
     const int64_t w = base + threadIdx.x;
     const int64_t c = (on && w < we) ? P.cnt_gt[w] : 0;
-    const int64_t pc = c * (c + 1) / 2;
+    const int64_t pc = items_of(c);
     int64_t tl, tp;
     const int64_t il = block_scan_incl<int64_t>(c, s_warp, &tl);
     const int64_t ip = block_scan_incl<int64_t>(pc, s_warp, &tp);
     if (w < we) {
       P.list_off[w] = s_l + il - c;
-      P.pair_off[w] = s_p + ip - pc;
+      P.item_off[w] = s_p + ip - pc;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -493,7 +505,7 @@ __global__ void __launch_bounds__(256) list_scan_down_kernel(RankPtrs P, int64_t
   }
   if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
     P.list_off[we] = P.hdr->list_total;
-    P.pair_off[we] = P.hdr->pairs_total;
+    P.item_off[we] = P.hdr->items_total;
     if (!plan_only && (P.hdr->list_total > P.list_cap || (on && P.block_cap <= 0)))
       record_error(P.hdr, SAD_ERR_WORKSPACE, -1);
   }
@@ -829,14 +841,17 @@ __global__ void __launch_bounds__(1024) tiles_kernel(RankPtrs P) {
 }
 
 // ------------------------------------------------------------- residual ----
-// One block per (set, word) (grid-stride): the excess list (stored row,
-// count - D) is staged in shared memory in chunks, and the block's threads walk
-// the pairs (u, v), u <= v, of the list. fn(tile, row in tile, column in tile,
-// value) is called once per pair with value = min of the two excesses; u == v is
-// the sequence's own pair.
-constexpr int kListChunk = 1024;
+// The pairs (u, v), u <= v, of each (set, word) excess list (stored row,
+// count - D) are cut into work items: pairs of kPairChunk-entry chunks (cu, cv),
+// cu <= cv, numbered cv-major within the list after the items of the lists
+// before it (item_off). Blocks take items in a grid stride, so that the pairs of
+// a long list are spread over many blocks. A block stages the two chunks in
+// shared memory sorted by row (neighbouring pairs then land in neighbouring
+// columns of the same tile row) and its threads walk the chunk pair. fn(tile,
+// row in tile, column in tile, value) is called once per pair with value = min
+// of the two excesses; u == v is the sequence's own pair.
 
-// Ascending bitonic sort by .x of s[0, n), n <= kListChunk, padded with INT_MAX.
+// Ascending bitonic sort by .x of s[0, n), n <= kPairChunk, padded with INT_MAX.
 __device__ __forceinline__ void block_sort_by_row(int2 *s, int n) {
   int p2 = 1;
   while (p2 < n) p2 <<= 1;
@@ -860,45 +875,51 @@ __device__ __forceinline__ void block_sort_by_row(int2 *s, int n) {
 
 template <typename Fn>
 __device__ __forceinline__ void for_each_residual_pair(const RankPtrs &P, int32_t eps, Fn fn) {
-  __shared__ int2 s_u[kListChunk], s_v[kListChunk];
+  __shared__ int2 s_u[kPairChunk], s_v[kPairChunk];
+  __shared__ int64_t s_w;
   const int64_t we = P.n_sets * (int64_t)eps;
-  for (int64_t w = blockIdx.x; w < we; w += gridDim.x) {
+  const int64_t total = P.hdr->items_total;
+  for (int64_t it = blockIdx.x; it < total; it += gridDim.x) {
+    __syncthreads();  // the previous item's chunks are no longer read
+    if (threadIdx.x == 0) {
+      // the list holding item it: item_off[w] <= it < item_off[w + 1]
+      int64_t lo = 0, hi = we;
+      while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (P.item_off[mid] <= it) lo = mid;
+        else hi = mid;
+      }
+      s_w = lo;
+    }
+    __syncthreads();
+    const int64_t w = s_w;
     const int64_t base = P.list_off[w];
     const int64_t len = P.list_off[w + 1] - base;
-    if (len == 0) continue;
+    const int64_t j = it - P.item_off[w];
+    int64_t cv = (int64_t)((sqrt(8.0 * (double)j + 1.0) - 1.0) * 0.5);
+    while (cv * (cv + 1) / 2 > j) --cv;
+    while ((cv + 1) * (cv + 2) / 2 <= j) ++cv;
+    const int64_t cu = j - cv * (cv + 1) / 2;
     const RankSet e = P.sets[w / eps];
     const int64_t cfull = dev_n_pad(e.n) / kColBlock;
-    // chunk pairs (cu, cv) of the list with cu <= cv; pairs u <= v within them
-    // chunks sorted by stored row, so that neighbouring pairs land in neighbouring
-    // columns of the same tile row
-    for (int64_t cv = 0; cv < len; cv += kListChunk) {
-      const int nv = (int)min((int64_t)kListChunk, len - cv);
-      __syncthreads();
-      for (int i = threadIdx.x; i < nv; i += blockDim.x) s_v[i] = P.lists[base + cv + i];
-      block_sort_by_row(s_v, nv);
-      for (int64_t cu = 0; cu <= cv; cu += kListChunk) {
-        const int nu = (int)min((int64_t)kListChunk, len - cu);
-        __syncthreads();
-        if (cu != cv) {
-          for (int i = threadIdx.x; i < nu; i += blockDim.x) s_u[i] = P.lists[base + cu + i];
-          block_sort_by_row(s_u, nu);
-        }
-        __syncthreads();
-        const bool same = cu == cv;
-        const int npairs = nu * nv;  // <= kListChunk^2
-        for (int q = threadIdx.x; q < npairs; q += blockDim.x) {
-          const int iu = q / nv, iv = q - iu * nv;
-          if (same && iu > iv) continue;
-          const int2 eu = same ? s_v[iu] : s_u[iu];
-          const int2 ev = s_v[iv];
-          const int32_t a = min(eu.x, ev.x), b = max(eu.x, ev.x);
-          const int64_t al = a - e.row_base, bl = b - e.row_base;
-          const int32_t t = P.tile_of[e.tileof_base + (al / kRowBlock) * cfull + bl / kColBlock];
-          fn(t, (int32_t)(al % kRowBlock), (int32_t)(bl % kColBlock),
-             (uint32_t)min(eu.y, ev.y));
-        }
-      }
-      __syncthreads();
+    const int nv = (int)min((int64_t)kPairChunk, len - cv * kPairChunk);
+    const int nu = (int)min((int64_t)kPairChunk, len - cu * kPairChunk);
+    const bool same = cu == cv;
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) s_v[i] = P.lists[base + cv * kPairChunk + i];
+    if (!same)
+      for (int i = threadIdx.x; i < nu; i += blockDim.x) s_u[i] = P.lists[base + cu * kPairChunk + i];
+    block_sort_by_row(s_v, nv);
+    if (!same) block_sort_by_row(s_u, nu);
+    const int npairs = nu * nv;  // <= kPairChunk^2
+    for (int q = threadIdx.x; q < npairs; q += blockDim.x) {
+      const int iu = q / nv, iv = q - iu * nv;
+      if (same && iu > iv) continue;
+      const int2 eu = same ? s_v[iu] : s_u[iu];
+      const int2 ev = s_v[iv];
+      const int32_t a = min(eu.x, ev.x), b = max(eu.x, ev.x);
+      const int64_t al = a - e.row_base, bl = b - e.row_base;
+      const int32_t t = P.tile_of[e.tileof_base + (al / kRowBlock) * cfull + bl / kColBlock];
+      fn(t, (int32_t)(al % kRowBlock), (int32_t)(bl % kColBlock), (uint32_t)min(eu.y, ev.y));
     }
   }
 }

@@ -39,7 +39,8 @@ struct WsHeader {
   int32_t n_blocks;      // residual tiles (dense 128 x 256 blocks) in use
   int32_t m_max;         // largest m = L - k + 1 of the set
   unsigned long long flat_count;  // excess entries appended by the plane kernel
-  int32_t pad[46];
+  int64_t items_total;   // residual work items (pairs of list chunks)
+  int32_t pad[44];
 };
 static_assert(sizeof(WsHeader) == 256, "header is 256 bytes");
 
@@ -117,7 +118,7 @@ inline RankShape shape_single(int64_t n) {
 // Offsets of the rank workspace regions (bytes from the workspace base).
 struct RankLayout {
   size_t sets, seq_set, row_set, T, secend, thist, tau_sorted, mhist, perm, rec, depth, tiles,
-      acc, cnt_gt, list_off, pair_off, cursor, tile_of, block_of, sortbuf, scanblk, colmap, lists,
+      acc, cnt_gt, list_off, item_off, cursor, tile_of, block_of, sortbuf, scanblk, colmap, lists,
       flat, planes, rblocks;
   size_t fixed_bytes;    // everything that does not depend on the capacities
   size_t bytes;          // total
@@ -148,7 +149,7 @@ inline RankLayout rank_layout(const RankShape &sh, int64_t eps, const RankCaps &
   L.acc = take(3 * sizeof(uint64_t) * nz(sh.n_total));
   L.cnt_gt = take(sizeof(int32_t) * we);
   L.list_off = take(sizeof(int64_t) * (we + 1));
-  L.pair_off = take(sizeof(int64_t) * (we + 1));
+  L.item_off = take(sizeof(int64_t) * (we + 1));
   L.cursor = take(sizeof(int32_t) * we);
   L.tile_of = take(sizeof(int32_t) * nz(sh.tileof_total));
   L.block_of = take(sizeof(int32_t) * nz(sh.tiles_total));
