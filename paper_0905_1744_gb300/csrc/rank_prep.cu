@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(1024) colmap_kernel(RankPtrs P, int32_t eps, i
 // a list of c entries (the residual's units of work). Three passes: per-block
 // totals, a scan of the block totals, per-block scans with the block's carry.
 // The number of residual pairs, sum c_w (c_w + 1) / 2, is added up on the side.
-constexpr int kScanChunk = 4096;
+constexpr int kScanChunk = kScanChunkWords;
 constexpr int kPairChunk = 128;
 
 __host__ __device__ __forceinline__ int64_t items_of(int64_t c) {
@@ -625,6 +625,14 @@ __global__ void __launch_bounds__(kSortThreads) lensort_sets_kernel(
 // entries (counts above the depth) to the (set, word) lists.
 constexpr int kPlaneRows = 2;
 
+// counts 4q..4q+3 of a row into its shared u16 copy (one 8-byte store), clamped to
+// [0, 65535] (larger counts do not occur: windows per sequence are at most 65535)
+__device__ __forceinline__ void stage4(uint16_t *sc, int q, int4 v) {
+  const uint32_t a = (uint32_t)min(max(v.x, 0), 0xFFFF) | (uint32_t)min(max(v.y, 0), 0xFFFF) << 16;
+  const uint32_t b = (uint32_t)min(max(v.z, 0), 0xFFFF) | (uint32_t)min(max(v.w, 0), 0xFFFF) << 16;
+  reinterpret_cast<uint2 *>(sc)[q] = make_uint2(a, b);
+}
+
 __global__ void __launch_bounds__(256) planes_kernel(const int32_t *__restrict__ counts,
                                                      int32_t eps, RankPtrs P) {
   extern __shared__ uint16_t s_cnt[];  // [kPlaneRows][eps]
@@ -662,24 +670,16 @@ __global__ void __launch_bounds__(256) planes_kernel(const int32_t *__restrict__
             for (int u = 0; u < 4; ++u) v[u] = __ldg(row4 + q + u * 256);
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-              const int32_t c[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
-#pragma unroll
-              for (int b = 0; b < 4; ++b) {
-                sc[4 * (q + u * 256) + b] = (uint16_t)min(max(c[b], 0), 0xFFFF);
-                mx = max(mx, c[b]);
-                sum += c[b];
-              }
+              stage4(sc, q + u * 256, v[u]);
+              mx = max(mx, max(max(v[u].x, v[u].y), max(v[u].z, v[u].w)));
+              sum += v[u].x + v[u].y + v[u].z + v[u].w;
             }
           }
           for (; q < q4; q += 256) {
             const int4 v = __ldg(row4 + q);
-            const int32_t c[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-              sc[4 * q + b] = (uint16_t)min(max(c[b], 0), 0xFFFF);
-              mx = max(mx, c[b]);
-              sum += c[b];
-            }
+            stage4(sc, q, v);
+            mx = max(mx, max(max(v.x, v.y), max(v.z, v.w)));
+            sum += v.x + v.y + v.z + v.w;
           }
         } else {
           for (int t = threadIdx.x; t < eps; t += blockDim.x) {
@@ -1077,8 +1077,13 @@ int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *le
     if (cudaFuncSetAttribute(planes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
       return SAD_ERR_CUDA;
+    // every block resident at once: the grid stride then splits the rows evenly
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, planes_kernel, 256, smem) !=
+        cudaSuccess)
+      return SAD_ERR_CUDA;
     const int64_t groups = P.n_pad / kPlaneRows;
-    const int64_t cap = (int64_t)num_sms() * 8;
+    const int64_t cap = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
     planes_kernel<<<(unsigned)(groups < cap ? groups : cap), 256, smem, st>>>(counts, eps, P);
     SAD_LAUNCH_CHECK();
   }

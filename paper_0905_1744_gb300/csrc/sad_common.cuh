@@ -25,6 +25,9 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // --------------------------------------------------------- workspace hdr ----
 // The first 256 bytes of every workspace.
+// entries per block of the (set, word) list scans
+constexpr int kScanChunkWords = 1024;
+
 struct WsHeader {
   int32_t status;        // first recorded sad_status (0 = none)
   int32_t detail;        // optional detail of the error (e.g. offending index)
@@ -154,7 +157,7 @@ inline RankLayout rank_layout(const RankShape &sh, int64_t eps, const RankCaps &
   L.tile_of = take(sizeof(int32_t) * nz(sh.tileof_total));
   L.block_of = take(sizeof(int32_t) * nz(sh.tiles_total));
   L.sortbuf = take(sh.n_sets > 1 ? 2 * sizeof(Item) * nz(sh.n_total) : 256);
-  L.scanblk = take(2 * sizeof(int64_t) * (we / 4096 + 1));
+  L.scanblk = take(2 * sizeof(int64_t) * (we / kScanChunkWords + 1));
   L.fixed_bytes = o;
   L.colmap = take(sizeof(int32_t) * (size_t)(caps.k_cap > 0 ? caps.k_cap : 1));
   L.lists = take(2 * sizeof(int32_t) * (size_t)(caps.list_cap > 0 ? caps.list_cap : 1));
