@@ -49,12 +49,12 @@ __device__ __forceinline__ void note_repeat(uint32_t *max8, int32_t *word_max, i
   }
 }
 
-// Words of one warp's presence bitmap: 32 lanes x one word per 8 passes of quads
-// (eps divisible by 4) or per 32 passes of single columns.
+// Words of one warp's presence bitmap: 32 lanes x one word per 4 passes of column
+// octets (eps divisible by 8) or per 32 passes of single columns.
 __host__ __device__ __forceinline__ int pres_words_of(int32_t eps) {
-  if ((eps & 3) == 0) {
-    const int passes = ((eps >> 2) + 31) / 32;
-    return 32 * ((passes + 7) / 8);
+  if ((eps & 7) == 0) {
+    const int passes = ((eps >> 3) + 31) / 32;
+    return 32 * ((passes + 3) / 4);
   }
   const int passes = (eps + 31) / 32;
   return 32 * ((passes + 31) / 32);
@@ -72,8 +72,8 @@ __global__ void __launch_bounds__(128) kmer_count_kernel(const uint8_t *__restri
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int words = (eps + 1) >> 1;
   uint32_t *hist = smem + (size_t)wid * words;
-  // word maxima: per warp a presence bitmap, [pass / 8][lane] words holding 4 bits
-  // (the 4 columns of the lane's quad) for each of 8 passes; per block byte maxima
+  // word maxima: per warp a presence bitmap ([pass / 4][lane] words holding the 8
+  // bits of the lane's column octet for 4 passes); per block byte maxima
   const int pres_words = pres_words_of(eps);
   uint32_t *present = smem + (size_t)warps * words + (size_t)wid * pres_words;
   uint32_t *max8 = smem + (size_t)warps * (words + pres_words);  // [ceil(eps / 4)]
@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(128) kmer_count_kernel(const uint8_t *__restri
   }
   __syncthreads();
   const int64_t codes_end = offsets[n];
+  const bool octets = (eps & 7) == 0 && (reinterpret_cast<uintptr_t>(counts) & 15) == 0;
 
   for (int64_t x = (int64_t)blockIdx.x * warps + wid; x < n; x += (int64_t)gridDim.x * warps) {
     const int64_t s = offsets[x], e = offsets[x + 1];
@@ -109,6 +110,22 @@ __global__ void __launch_bounds__(128) kmer_count_kernel(const uint8_t *__restri
           nx = (my + 16 < e) ? load16_guarded(codes, my + 16, codes_end) : make_uint4(0, 0, 0, 0);
         if (my >= e) continue;
         const uint32_t w[8] = {v.x, v.y, v.z, v.w, nx.x, nx.y, nx.z, nx.w};
+        if (my >= s && my + 16 + K - 1 <= e) {
+          // all 16 windows of the lane lie inside the sequence: no bounds checks
+          if (alphabet < 256) {
+            const uint32_t lim = 0x01010101u * (uint32_t)alphabet;
+            bad |= (__vcmpgeu4(v.x, lim) | __vcmpgeu4(v.y, lim) | __vcmpgeu4(v.z, lim) |
+                    __vcmpgeu4(v.w, lim)) != 0u;
+          }
+#pragma unroll
+          for (int b = 0; b < 16; ++b) {
+            uint32_t tau = 0;
+#pragma unroll
+            for (int r = 0; r < K; ++r) tau = tau * (uint32_t)alphabet + byte_of(w, b + r);
+            if (tau < (uint32_t)eps) atomicAdd(&hist[tau >> 1], 1u << (16 * (tau & 1)));
+          }
+          continue;
+        }
 #pragma unroll
         for (int b = 0; b < 16; ++b) {
           const int64_t pos = my + b;
@@ -125,23 +142,37 @@ __global__ void __launch_bounds__(128) kmer_count_kernel(const uint8_t *__restri
     }
     __syncwarp();
     int32_t *row = counts + x * (int64_t)eps;
-    if ((eps & 3) == 0) {
+    if (octets) {
+      // lane writes octets of columns o = lane + 32 pass: one 16-byte shared load
+      // (and clear) and two 16-byte stores of the row
+      uint4 *h4 = reinterpret_cast<uint4 *>(hist);
+      int4 *row4 = reinterpret_cast<int4 *>(row);
       int pass = 0;
-      for (int q = lane; q < (eps >> 2); q += 32, ++pass) {
-        const uint32_t a = hist[2 * q], b = hist[2 * q + 1];
-        hist[2 * q] = 0;
-        hist[2 * q + 1] = 0;
-        const int4 c4 =
-            make_int4((int)(a & 0xFFFFu), (int)(a >> 16), (int)(b & 0xFFFFu), (int)(b >> 16));
-        reinterpret_cast<int4 *>(row)[q] = c4;
-        if (word_max && (a | b)) {
-          const uint32_t nz = (c4.x > 0) | (c4.y > 0) << 1 | (c4.z > 0) << 2 | (c4.w > 0) << 3;
-          present[(pass >> 3) * 32 + lane] |= nz << (4 * (pass & 7));
-          if ((a | b) & 0xFFFEFFFEu) {  // some count >= 2
-            note_repeat(max8, word_max, 4 * q + 0, c4.x);
-            note_repeat(max8, word_max, 4 * q + 1, c4.y);
-            note_repeat(max8, word_max, 4 * q + 2, c4.z);
-            note_repeat(max8, word_max, 4 * q + 3, c4.w);
+      for (int o = lane; o < (eps >> 3); o += 32, ++pass) {
+        const uint4 h = h4[o];
+        h4[o] = make_uint4(0, 0, 0, 0);
+        row4[2 * o] = make_int4((int)(h.x & 0xFFFFu), (int)(h.x >> 16), (int)(h.y & 0xFFFFu),
+                                (int)(h.y >> 16));
+        row4[2 * o + 1] = make_int4((int)(h.z & 0xFFFFu), (int)(h.z >> 16),
+                                    (int)(h.w & 0xFFFFu), (int)(h.w >> 16));
+        if (word_max) {
+          const uint32_t any = h.x | h.y | h.z | h.w;
+          if (any) {
+            const uint32_t hw[4] = {h.x, h.y, h.z, h.w};
+            uint32_t nz = 0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const uint32_t m = __vcmpne2(hw[u], 0u);  // 0xFFFF per nonzero half
+              nz |= ((m & 1u) | ((m >> 15) & 2u)) << (2 * u);
+            }
+            present[(pass >> 2) * 32 + lane] |= nz << (8 * (pass & 3));
+            if (any & 0xFFFEFFFEu) {  // some count >= 2
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                note_repeat(max8, word_max, 8 * o + 2 * u, (int32_t)(hw[u] & 0xFFFFu));
+                note_repeat(max8, word_max, 8 * o + 2 * u + 1, (int32_t)(hw[u] >> 16));
+              }
+            }
           }
         }
       }
@@ -168,13 +199,13 @@ __global__ void __launch_bounds__(128) kmer_count_kernel(const uint8_t *__restri
     const uint32_t *pres0 = smem + (size_t)warps * words;
     for (int i = threadIdx.x; i < eps; i += blockDim.x) {
       const int t = i + off < eps ? i + off : i + off - eps;
-      // the bit of word t: column quad q = t / 4 (or column t) is owned by lane q % 32
-      // in pass q / 32
+      // the bit of word t: column octet o = t / 8 (or column t) is owned by lane
+      // o % 32 in pass o / 32
       int idx, bit;
-      if ((eps & 3) == 0) {
-        const int q = t >> 2, pass = q >> 5;
-        idx = (pass >> 3) * 32 + (q & 31);
-        bit = 4 * (pass & 7) + (t & 3);
+      if (octets) {
+        const int o = t >> 3, pass = o >> 5;
+        idx = (pass >> 2) * 32 + (o & 31);
+        bit = 8 * (pass & 3) + (t & 7);
       } else {
         const int pass = t >> 5;
         idx = (pass >> 5) * 32 + (t & 31);

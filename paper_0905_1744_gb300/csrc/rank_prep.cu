@@ -860,7 +860,7 @@ __device__ __forceinline__ void block_sort_by_row(int2 *s, int n) {
   for (int size = 2; size <= p2; size <<= 1) {
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
       for (int i = threadIdx.x; i < (p2 >> 1); i += blockDim.x) {
-        const int a = 2 * stride * (i / stride) + (i % stride), b = a + stride;
+        const int a = ((i & ~(stride - 1)) << 1) | (i & (stride - 1)), b = a + stride;
         const bool asc = (a & size) == 0;
         const int2 x = s[a], y = s[b];
         if (asc ? (y.x < x.x) : (x.x < y.x)) {

@@ -33,7 +33,8 @@ __device__ inline void cta_sort_small(Item *data, int cnt, Item *sm) {
   for (int size = 2; size <= p2; size <<= 1) {
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
       for (int i = threadIdx.x; i < (p2 >> 1); i += blockDim.x) {
-        const int a = 2 * stride * (i / stride) + (i % stride);
+        // pair i of the stage: i with a zero bit inserted at the stride's position
+        const int a = ((i & ~(stride - 1)) << 1) | (i & (stride - 1));
         const int b = a + stride;
         const bool asc = (a & size) == 0;
         const Item x = sm[a], y = sm[b];
