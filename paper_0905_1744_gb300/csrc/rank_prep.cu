@@ -53,7 +53,7 @@ RankPtrs rank_ptrs(void *ws, const RankLayout &L) {
   P.secend = reinterpret_cast<int32_t *>(b + L.secend);
   P.colmap = reinterpret_cast<int32_t *>(b + L.colmap);
   P.thist = reinterpret_cast<int32_t *>(b + L.thist);
-  P.tau_sorted = reinterpret_cast<int32_t *>(b + L.tau_sorted);
+  P.coltab = reinterpret_cast<int32_t *>(b + L.coltab);
   P.mhist = reinterpret_cast<int32_t *>(b + L.mhist);
   P.perm = reinterpret_cast<int32_t *>(b + L.perm);
   P.rec = reinterpret_cast<uint4 *>(b + L.rec);
@@ -398,6 +398,15 @@ __global__ void __launch_bounds__(1024) colmap_kernel(RankPtrs P, int32_t eps, i
       }
     }
     __syncthreads();
+  }
+  if (P.depth_cap >= 1 && P.depth_cap <= kTabDepth) {
+    // the inverse map for the streaming plane writer: column of (t, word)
+    for (int i = tid; i < dkeep * eps; i += blockDim.x) P.coltab[i] = -1;
+    __syncthreads();
+    for (int c = tid; c < k_eff; c += blockDim.x) {
+      const int32_t e = P.colmap[c];
+      P.coltab[(int64_t)((e >> 16) - 1) * eps + (e & 0xFFFF)] = c;
+    }
   }
 }
 
@@ -777,6 +786,134 @@ __global__ void __launch_bounds__(256) planes_kernel(const int32_t *__restrict__
   }
 }
 
+// Plane rows for depths D <= kTabDepth, streamed: one warp per stored row reads the
+// row's counts once (16 bytes per lane, four loads in flight) and writes each
+// word's bytes [c >= t], t = 1..D, at the columns the (t, word) table gives, as
+// one 4-byte store when the four words of a lane sit in four aligned consecutive
+// columns (section 1 of a set in which every word occurs). Counts above D go to a
+// per-warp buffer and are appended to the flat excess list with one atomic per
+// row; a row with more than kExCap of them is scanned again for the append.
+constexpr int kExCap = 64;
+constexpr int kStreamUnroll = 4;
+
+__device__ __forceinline__ uint32_t plane_byte(int32_t c, int32_t t) { return c >= t ? 0x38u : 0u; }
+
+__global__ void __launch_bounds__(256) planes_stream_kernel(const int32_t *__restrict__ counts,
+                                                            int32_t eps, RankPtrs P) {
+  __shared__ int2 s_ex[8][kExCap];
+  __shared__ int32_t s_exn[8];
+  if (P.hdr->status != 0) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int32_t k_eff = (int32_t)P.hdr->k_eff;
+  const int32_t k_pad = P.hdr->k_pad;
+  const int32_t dkeep = P.hdr->depth;
+  const bool residual = dkeep < P.hdr->t_max;
+  const int q4 = eps >> 2;
+  if (lane == 0) s_exn[warp] = 0;
+  __syncwarp();
+  for (int64_t pos = (int64_t)blockIdx.x * 8 + warp; pos < P.n_pad;
+       pos += (int64_t)gridDim.x * 8) {
+    const int32_t x = P.perm[pos];
+    uint8_t *prow = P.planes + pos * P.k_cap;
+    if (x < 0) {  // padding row: all zero
+      for (int c = 16 * lane; c < k_pad; c += 512)
+        *reinterpret_cast<uint4 *>(prow + c) = make_uint4(0, 0, 0, 0);
+      continue;
+    }
+    const int4 *row4 = reinterpret_cast<const int4 *>(counts + (int64_t)x * eps);
+    const int64_t wbase = (int64_t)set_of_row(P, pos) * eps;
+    int32_t mx = 0, sum = 0;
+    for (int base = 0; base < q4; base += 32 * kStreamUnroll) {
+      int4 v[kStreamUnroll];
+#pragma unroll
+      for (int u = 0; u < kStreamUnroll; ++u) {
+        const int q = base + 32 * u + lane;
+        v[u] = q < q4 ? __ldg(row4 + q) : make_int4(0, 0, 0, 0);
+      }
+#pragma unroll
+      for (int u = 0; u < kStreamUnroll; ++u) {
+        const int q = base + 32 * u + lane;
+        if (q >= q4) continue;
+        const int32_t c[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+        mx = max(mx, max(max(c[0], c[1]), max(c[2], c[3])));
+        sum += c[0] + c[1] + c[2] + c[3];
+        for (int t = 1; t <= dkeep; ++t) {
+          const int4 col = __ldg(reinterpret_cast<const int4 *>(P.coltab + (int64_t)(t - 1) * eps) + q);
+          if (col.x >= 0 && (col.x & 3) == 0 && col.y == col.x + 1 && col.z == col.x + 2 &&
+              col.w == col.x + 3) {
+            *reinterpret_cast<uint32_t *>(prow + col.x) =
+                plane_byte(c[0], t) | plane_byte(c[1], t) << 8 | plane_byte(c[2], t) << 16 |
+                plane_byte(c[3], t) << 24;
+          } else {
+            const int32_t cc[4] = {col.x, col.y, col.z, col.w};
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+              if (cc[b] >= 0) prow[cc[b]] = (uint8_t)plane_byte(c[b], t);
+          }
+        }
+        if (residual) {
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            if (c[b] > dkeep) {
+              const int slot = atomicAdd(&s_exn[warp], 1);
+              if (slot < kExCap)
+                s_ex[warp][slot] = make_int2((int32_t)pos, (4 * q + b) | ((c[b] - dkeep) << 16));
+            }
+          }
+        }
+      }
+    }
+    for (int c = k_eff + lane; c < k_pad; c += 32) prow[c] = 0;  // K padding
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    }
+    if (lane == 0) {
+      atomicMax(&P.depth[pos / kRowBlock], mx);
+      // the counts of a row must add up to its number of windows, m
+      if (sum != (int32_t)(P.rec[pos].w & 0xFFFFu)) record_error(P.hdr, SAD_ERR_BAD_INPUT, x);
+    }
+    if (residual) {
+      __syncwarp();
+      const int32_t n_ex = s_exn[warp];
+      if (n_ex > 0) {
+        unsigned long long first = 0;
+        if (lane == 0) first = atomicAdd(&P.hdr->flat_count, (unsigned long long)n_ex);
+        first = __shfl_sync(0xffffffffu, first, 0);
+        if (n_ex <= kExCap) {
+          for (int i = lane; i < n_ex; i += 32) {
+            const int2 e = s_ex[warp][i];
+            atomicAdd(&P.cnt_gt[wbase + (e.y & 0xFFFF)], 1);
+            if (first + i < (unsigned long long)P.list_cap) P.flat[first + i] = e;
+          }
+        } else {
+          // the buffer overflowed: scan the row again and append every entry
+          __syncwarp();
+          if (lane == 0) s_exn[warp] = 0;
+          __syncwarp();
+          for (int q = lane; q < q4; q += 32) {
+            const int4 v = __ldg(row4 + q);
+            const int32_t c[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+              if (c[b] > dkeep) {
+                const unsigned long long slot = first + (unsigned)atomicAdd(&s_exn[warp], 1);
+                atomicAdd(&P.cnt_gt[wbase + 4 * q + b], 1);
+                if (slot < (unsigned long long)P.list_cap)
+                  P.flat[slot] = make_int2((int32_t)pos, (4 * q + b) | ((c[b] - dkeep) << 16));
+              }
+            }
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) s_exn[warp] = 0;
+      __syncwarp();
+    }
+  }
+}
+
 // Upper-triangle tile list of every set (one block per set). Tile (I, J) of a
 // set covers its stored rows [128 I, 128 I + 128) and columns [256 J, 256 J + 256)
 // (set-local); it is needed when some pair i <= j lies in it (128 I <= 256 J + 255)
@@ -1072,7 +1209,18 @@ int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *le
     lensort_sets_kernel<<<gsets, kSortThreads, kSortSmem, st>>>(lengths, k, P);
     SAD_LAUNCH_CHECK();
   }
-  {
+  if (P.depth_cap >= 1 && P.depth_cap <= kTabDepth && (eps & 3) == 0 &&
+      (reinterpret_cast<uintptr_t>(counts) & 15) == 0 && (P.k_cap & 15) == 0) {
+    const int64_t warps = P.n_pad;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, planes_stream_kernel, 256, 0) !=
+        cudaSuccess)
+      return SAD_ERR_CUDA;
+    const int64_t cap = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
+    const int64_t want = (warps + 7) / 8;
+    planes_stream_kernel<<<(unsigned)(want < cap ? want : cap), 256, 0, st>>>(counts, eps, P);
+    SAD_LAUNCH_CHECK();
+  } else {
     const size_t smem = sizeof(uint16_t) * (size_t)eps * kPlaneRows;
     if (cudaFuncSetAttribute(planes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)

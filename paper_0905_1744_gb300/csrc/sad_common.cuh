@@ -27,6 +27,8 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 // The first 256 bytes of every workspace.
 // entries per block of the (set, word) list scans
 constexpr int kScanChunkWords = 1024;
+// plane depths up to which the planes are written from a (threshold, word) -> column table
+constexpr int kTabDepth = 8;
 
 struct WsHeader {
   int32_t status;        // first recorded sad_status (0 = none)
@@ -120,7 +122,7 @@ inline RankShape shape_single(int64_t n) {
 
 // Offsets of the rank workspace regions (bytes from the workspace base).
 struct RankLayout {
-  size_t sets, seq_set, row_set, T, secend, thist, tau_sorted, mhist, perm, rec, depth, tiles,
+  size_t sets, seq_set, row_set, T, secend, thist, coltab, mhist, perm, rec, depth, tiles,
       acc, cnt_gt, list_off, item_off, cursor, tile_of, block_of, sortbuf, scanblk, colmap, lists,
       flat, planes, rblocks;
   size_t fixed_bytes;    // everything that does not depend on the capacities
@@ -143,7 +145,7 @@ inline RankLayout rank_layout(const RankShape &sh, int64_t eps, const RankCaps &
   L.T = take(sizeof(int32_t) * eps);
   L.secend = take(sizeof(int32_t) * (kMaxM + 2));
   L.thist = take(sizeof(int32_t) * (kMaxM + 2));
-  L.tau_sorted = take(sizeof(int32_t) * eps);
+  L.coltab = take(sizeof(int32_t) * eps * kTabDepth);
   L.mhist = take(sizeof(int32_t) * (kMaxM + 2));
   L.perm = take(sizeof(int32_t) * nz(sh.rows_total));
   L.rec = take(16 * nz(sh.rows_total));
