@@ -787,12 +787,14 @@ __global__ void __launch_bounds__(256) planes_kernel(const int32_t *__restrict__
 }
 
 // Plane rows for depths D <= kTabDepth, streamed: one warp per stored row reads the
-// row's counts once (16 bytes per lane, four loads in flight) and writes each
-// word's bytes [c >= t], t = 1..D, at the columns the (t, word) table gives, as
-// one 4-byte store when the four words of a lane sit in four aligned consecutive
-// columns (section 1 of a set in which every word occurs). Counts above D go to a
-// per-warp buffer and are appended to the flat excess list with one atomic per
-// row; a row with more than kExCap of them is scanned again for the append.
+// row's counts once (16 bytes per lane, four loads in flight). Section 1 gets each
+// word's byte [c >= 1] at the column the (t, word) table gives, as one 4-byte
+// store when the four words of a lane sit in four aligned consecutive columns
+// (every word occurs somewhere). The columns past section 1 are zero-filled with
+// 16-byte stores first, and only the words counted twice or more then set their
+// bytes in sections 2..min(c, D). Counts above D go to a per-warp buffer and are
+// appended to the flat excess list with one atomic per row; a row with more than
+// kExCap of them is scanned again for the append.
 constexpr int kExCap = 64;
 constexpr int kStreamUnroll = 4;
 
@@ -804,11 +806,12 @@ __global__ void __launch_bounds__(256) planes_stream_kernel(const int32_t *__res
   __shared__ int32_t s_exn[8];
   if (P.hdr->status != 0) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int32_t k_eff = (int32_t)P.hdr->k_eff;
   const int32_t k_pad = P.hdr->k_pad;
   const int32_t dkeep = P.hdr->depth;
   const bool residual = dkeep < P.hdr->t_max;
   const int q4 = eps >> 2;
+  const int32_t s1 = P.secend[1];  // end of section 1
+  const int32_t s1_16 = min((s1 + 15) & ~15, k_pad);
   if (lane == 0) s_exn[warp] = 0;
   __syncwarp();
   for (int64_t pos = (int64_t)blockIdx.x * 8 + warp; pos < P.n_pad;
@@ -820,6 +823,11 @@ __global__ void __launch_bounds__(256) planes_stream_kernel(const int32_t *__res
         *reinterpret_cast<uint4 *>(prow + c) = make_uint4(0, 0, 0, 0);
       continue;
     }
+    // columns [s1, k_pad): zero (deeper sections and the K padding)
+    for (int c = s1 + lane; c < s1_16; c += 32) prow[c] = 0;
+    for (int c = s1_16 + 16 * lane; c < k_pad; c += 512)
+      *reinterpret_cast<uint4 *>(prow + c) = make_uint4(0, 0, 0, 0);
+    __syncwarp();
     const int4 *row4 = reinterpret_cast<const int4 *>(counts + (int64_t)x * eps);
     const int64_t wbase = (int64_t)set_of_row(P, pos) * eps;
     int32_t mx = 0, sum = 0;
@@ -837,19 +845,26 @@ __global__ void __launch_bounds__(256) planes_stream_kernel(const int32_t *__res
         const int32_t c[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
         mx = max(mx, max(max(c[0], c[1]), max(c[2], c[3])));
         sum += c[0] + c[1] + c[2] + c[3];
-        for (int t = 1; t <= dkeep; ++t) {
-          const int4 col = __ldg(reinterpret_cast<const int4 *>(P.coltab + (int64_t)(t - 1) * eps) + q);
+        {
+          const int4 col = __ldg(reinterpret_cast<const int4 *>(P.coltab) + q);
           if (col.x >= 0 && (col.x & 3) == 0 && col.y == col.x + 1 && col.z == col.x + 2 &&
               col.w == col.x + 3) {
             *reinterpret_cast<uint32_t *>(prow + col.x) =
-                plane_byte(c[0], t) | plane_byte(c[1], t) << 8 | plane_byte(c[2], t) << 16 |
-                plane_byte(c[3], t) << 24;
+                plane_byte(c[0], 1) | plane_byte(c[1], 1) << 8 | plane_byte(c[2], 1) << 16 |
+                plane_byte(c[3], 1) << 24;
           } else {
             const int32_t cc[4] = {col.x, col.y, col.z, col.w};
 #pragma unroll
             for (int b = 0; b < 4; ++b)
-              if (cc[b] >= 0) prow[cc[b]] = (uint8_t)plane_byte(c[b], t);
+              if (cc[b] >= 0) prow[cc[b]] = (uint8_t)plane_byte(c[b], 1);
           }
+        }
+        if (dkeep >= 2) {
+          // a word counted c >= 2 times is in sections 2..T >= c: its bytes there are 1
+#pragma unroll
+          for (int b = 0; b < 4; ++b)
+            for (int t = 2; t <= min(c[b], dkeep); ++t)
+              prow[P.coltab[(int64_t)(t - 1) * eps + 4 * q + b]] = 0x38;
         }
         if (residual) {
 #pragma unroll
@@ -863,7 +878,6 @@ __global__ void __launch_bounds__(256) planes_stream_kernel(const int32_t *__res
         }
       }
     }
-    for (int c = k_eff + lane; c < k_pad; c += 32) prow[c] = 0;  // K padding
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
