@@ -36,14 +36,15 @@ int64_t eps_of(int32_t k, int32_t alphabet) {
 
 bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
-// Largest K_cap (multiple of kKChunk) whose planes-only rank layout fits in ws_bytes.
+// Largest K_cap (multiple of kKCols) whose planes-only rank layout fits in ws_bytes.
 int64_t k_cap_for(const RankShape &sh, int64_t eps, size_t ws_bytes) {
   const RankLayout base = rank_layout(sh, eps, RankCaps{0, 0, 0, 0});
   if (ws_bytes <= base.fixed_bytes) return 0;
   // upper bound (the layout only grows with K_cap), then step down until it fits
-  int64_t k = (int64_t)((ws_bytes - base.fixed_bytes) / (size_t)sh.rows_total);
-  k = k / kKChunk * kKChunk;
-  while (k > 0 && rank_layout(sh, eps, RankCaps{0, k, 0, 0}).bytes > ws_bytes) k -= kKChunk;
+  // (two plane columns per byte)
+  int64_t k = (int64_t)(2 * ((ws_bytes - base.fixed_bytes) / (size_t)sh.rows_total));
+  k = k / kKCols * kKCols;
+  while (k > 0 && rank_layout(sh, eps, RankCaps{0, k, 0, 0}).bytes > ws_bytes) k -= kKCols;
   return k;
 }
 
@@ -145,7 +146,7 @@ size_t sad_workspace_bytes(int32_t op, int32_t n_seq, int32_t k, int32_t alphabe
       const RankShape sh = shape_single(n_seq);
       if (depth <= 0) return rank_layout(sh, eps, RankCaps{0, 0, 0, 0}).fixed_bytes;
       const int64_t k_cap =
-          (int64_t)align_up((size_t)eps * (size_t)depth, (size_t)kKChunk);
+          (int64_t)align_up((size_t)eps * (size_t)depth, (size_t)kKCols);
       return rank_layout(sh, eps, RankCaps{0, k_cap, 0, 0}).bytes;
     }
     case SAD_OP_PARTITION:
@@ -196,8 +197,8 @@ int rank_plan_impl(const int32_t *d_counts, const RankShape &sh, const int32_t *
     if (rc) return rc;
     if (h.status != 0) return h.status;
   }
-  int64_t k_pad = (int64_t)align_up((size_t)h.k_eff, kKChunk);
-  if (k_pad < kKChunk) k_pad = kKChunk;
+  int64_t k_pad = (int64_t)align_up((size_t)h.k_eff, kKCols);
+  if (k_pad < kKCols) k_pad = kKCols;
   const bool residual = sh.n_total > 0 && h.depth < h.t_max;
   plan->t_max = h.t_max;
   plan->k_eff = h.k_eff;
@@ -220,14 +221,14 @@ int rank_run_impl(const int32_t *d_counts, const int32_t *d_lengths, const int32
   if (sh.rows_total / kRowBlock > 0xFFFF) return SAD_ERR_UNSUPPORTED;  // 16-bit block ids
   RankCaps caps{0, 0, 0, 0};
   if (plan) {
-    if (plan->depth < 0 || plan->k_cap < kKChunk || plan->k_cap % kKChunk != 0 ||
+    if (plan->depth < 0 || plan->k_cap < kKCols || plan->k_cap % kKCols != 0 ||
         plan->list_cap < 0 || plan->block_cap < 0)
       return SAD_ERR_INVALID_ARGUMENT;
     caps = RankCaps{plan->depth, plan->k_cap, plan->list_cap, plan->block_cap};
     if (rank_layout(sh, eps, caps).bytes > ws_bytes) return SAD_ERR_WORKSPACE;
   } else {
     caps.k_cap = k_cap_for(sh, eps, ws_bytes);
-    if (caps.k_cap < kKChunk) return SAD_ERR_WORKSPACE;
+    if (caps.k_cap < kKCols) return SAD_ERR_WORKSPACE;
   }
   const RankLayout L = rank_layout(sh, eps, caps);
   const RankPtrs P = rank_ptrs(d_ws, L);

@@ -1,11 +1,12 @@
 // All-pairs shared k-mer counts on the tensor cores, streamed into the rank keys.
 //
 // S = P P^T over the threshold planes (see rank_prep.cu) is computed tile by tile
-// with tcgen05.mma (kind::f8f6f4, e4m3 operands that are exactly 0 or 1, f32
-// accumulation in TMEM): every product is 0 or 1 and every partial sum an
-// integer <= min(m_i, m_j) <= 65535 < 2^24, so the accumulators hold S exactly.
-// Only the upper triangle of the stored order is visited; each accumulator tile
-// goes straight into the Eq. 1 / Eq. 3 sums and is never written out:
+// with tcgen05.mma of kind::mxf4nvf4: the planes are packed e2m1 values that are
+// exactly 0 or 1, every block scale is 1.0, and the products are accumulated in
+// f32 in TMEM. Every product is 0 or 1 and every partial sum an integer
+// <= min(m_i, m_j) <= 65535 < 2^24, so the accumulators hold S exactly. Only the
+// upper triangle of the stored order is visited; each accumulator tile goes
+// straight into the Eq. 1 / Eq. 3 sums and is never written out:
 //
 //   term_ij = floor(S_ij 2^64 / D_ij), D_ij = m_j for stored i <= j (rows are in
 //   decreasing length), key_i += term_ij for i <= j and key_j += term_ij for i < j.
@@ -16,17 +17,19 @@
 // (red.global.add.u64), which a last kernel folds into the 128-bit key.
 //
 // When the planes are cut at a depth D, the residual sum_tau max(0, min(c_i, c_j) - D)
-// of each pair arrives as a dense 128 x 256 u16 block per tile and is added to S
+// of each pair arrives as a dense 128 x 128 u16 block per tile and is added to S
 // before the floor, so the key is the same as with all planes.
 //
 // Persistent kernel, one CTA per SM, 12 warps:
-//   warp 0      TMA producer: 128 x 128 B tile of A (rows I) and 256 x 128 B of
-//               B (rows J) per stage, 128-byte swizzle, 4-stage mbarrier ring
-//   warp 1      MMA issuer: 4 x (M=128, N=256, K=32) per stage into one of two
-//               TMEM accumulators (2 x 256 columns), commit frees the stage
+//   warp 0      TMA producer: 128 rows x 128 B (256 plane columns) of A (rows I)
+//               and of B (rows J) per stage, 128-byte swizzle, 6-stage mbarrier ring
+//   warp 1      MMA issuer: 4 x (M=128, N=128, K=64) per stage into one of two
+//               TMEM accumulators (2 x 128 columns), commit frees the stage
 //   warp 2      TMEM allocator
+//   warps 4-7   also fill the scale-factor columns of TMEM with 1.0 before the
+//               first MMA
 //   warps 4-11  epilogue: tcgen05.ld of the accumulator (lane quadrant = warp % 4,
-//               two warps per quadrant, each on half of the 256 columns)
+//               two warps per quadrant, each on half of the 128 columns)
 // The double TMEM accumulator lets the epilogue of one tile overlap the MMAs of
 // the next. Every wait is bounded (globaltimer); on a timeout the CTA records
 // SAD_ERR_TIMEOUT, drains its copies and MMAs in flight, frees TMEM and returns.
@@ -38,13 +41,19 @@ namespace sad {
 
 namespace {
 
-constexpr int kStages = 4;
+constexpr int kStages = 6;
 constexpr uint32_t kABytes = kRowBlock * kKChunk;
 constexpr uint32_t kBBytes = kColBlock * kKChunk;
 constexpr uint32_t kTxBytes = kABytes + kBBytes;
 constexpr int kThreads = 384;
 constexpr int kEpiThreads = 256;  // warps 4-11: two per TMEM lane quadrant
 constexpr uint32_t kTmemCols = 512;
+// TMEM columns: accumulators [0, 2 kColBlock), then the scale factors of A and B
+constexpr uint32_t kSfaCol = 2 * kColBlock;
+constexpr uint32_t kSfbCol = kSfaCol + 32;
+constexpr uint32_t kSfCols = 64;  // filled with 1.0
+static_assert(kSfaCol + kSfCols <= kTmemCols, "TMEM columns");
+constexpr int kHalfCols = kColBlock / 2;  // columns of one epilogue warp
 constexpr uint64_t kWaitBudgetNs = 2000000000ull;
 
 struct GemmSmem {
@@ -138,6 +147,16 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = S.tmem_base;
+  if (!skip && warp >= 4 && warp < 8) {
+    // every block scale of A and B is 1.0: fill their columns in this warp's lanes
+    const uint32_t lanes = ((warp & 3u) * 32u) << 16;
+#pragma unroll
+    for (uint32_t c = 0; c < kSfCols; c += 16) tmem_st_32x32b_x16_fill(tmem + lanes + kSfaCol + c, kScaleOne4);
+    tmem_st_wait();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
   const int32_t n_tiles = skip ? 0 : P.hdr->n_tiles;
   // counts above the plane depth come in as dense per-tile residual blocks
   const bool residual =
@@ -176,7 +195,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (!skip && warp == 1 && lane == 0) {
     // ----------------------------------------------------------------- MMA --
-    const uint32_t idesc = idesc_f8_e4m3(kRowBlock, kColBlock);
+    const uint32_t idesc = idesc_f4_e2m1(kRowBlock, kColBlock);
+    const uint32_t sfa = tmem + kSfaCol, sfb = tmem + kSfbCol;
     int stage = 0;
     uint32_t phase = 0;
     bool aborted = false;
@@ -200,9 +220,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc_fence_after();
         const uint64_t adesc = sdesc_kmajor_sw128(smem_u32(S.a[stage]));
         const uint64_t bdesc = sdesc_kmajor_sw128(smem_u32(S.b[stage]));
+        // 4 MMAs of K = 64 values = 32 bytes per row (2 in 16-byte descriptor units)
 #pragma unroll
         for (int kk = 0; kk < kKChunk / 32; ++kk)
-          mma_f8(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, idesc, (kc | kk) != 0 ? 1u : 0u);
+          mma_f4(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, idesc, sfa, sfb,
+                 (kc | kk) != 0 ? 1u : 0u);
         mma_commit(&S.empty[stage]);
         if (++stage == kStages) {
           stage = 0;
@@ -219,7 +241,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (!skip && warp >= 4 && warp < 12) {
     // ------------------------------------------------------------ epilogue --
     // warp w reads TMEM lanes 32 (w % 4).. (its quadrant) and tile columns
-    // [128 h, 128 h + 128), h = (w - 4) / 4, in sub-chunks of 16 columns.
+    // [64 h, 64 h + 64), h = (w - 4) / 4, in sub-chunks of 16 columns.
     const uint32_t q = warp & 3;
     const uint32_t half = (warp - 4) >> 2;
     const uint32_t etid = threadIdx.x - 128;
@@ -242,7 +264,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           rblk >= 0 ? reinterpret_cast<const uint4 *>(
                           P.rblocks + (int64_t)rblk * (kResidualBlockBytes / 4) +
                           (q * 32 + lane) * (kColBlock / 2)) +
-                          half * (kColBlock / 2 / 8)
+                          half * (kHalfCols / 8)
                     : nullptr;
       uint4 ra = make_uint4(0, 0, 0, 0), rb = make_uint4(0, 0, 0, 0);
       if (rrow) {
@@ -256,13 +278,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_after();
       uint32_t R0 = 0, R1 = 0, R2 = 0;
 #pragma unroll 1
-      for (int sc = 0; sc < kColBlock / 2 / 16; ++sc) {
-        const int c0 = (int)half * (kColBlock / 2) + sc * 16;
+      for (int sc = 0; sc < kHalfCols / 16; ++sc) {
+        const int c0 = (int)half * kHalfCols + sc * 16;
         uint32_t v[16];
         tmem_ld_32x32b_x16(tmem + ((q * 32u) << 16) + acc * (uint32_t)kColBlock + (uint32_t)c0,
                            v);
         const uint32_t rw[8] = {ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
-        if (rrow && sc + 1 < kColBlock / 2 / 16) {  // next sub-chunk's residual words
+        if (rrow && sc + 1 < kHalfCols / 16) {  // next sub-chunk's residual words
           ra = __ldg(rrow + 2 * (sc + 1));
           rb = __ldg(rrow + 2 * (sc + 1) + 1);
         }
@@ -348,11 +370,12 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
+// The planes as bytes: n_pad rows of K_cap / 2 bytes (two 4-bit values each).
 int make_plane_map(CUtensorMap *map, uint8_t *planes, int64_t n_pad, int64_t k_cap, int rows) {
   auto fn = encode_fn();
   if (!fn) return SAD_ERR_CUDA;
-  const cuuint64_t dims[2] = {(cuuint64_t)k_cap, (cuuint64_t)n_pad};
-  const cuuint64_t strides[1] = {(cuuint64_t)k_cap};
+  const cuuint64_t dims[2] = {(cuuint64_t)(k_cap / 2), (cuuint64_t)n_pad};
+  const cuuint64_t strides[1] = {(cuuint64_t)(k_cap / 2)};
   const cuuint32_t box[2] = {(cuuint32_t)kKChunk, (cuuint32_t)rows};
   const cuuint32_t estr[2] = {1, 1};
   const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, planes, dims, strides, box, estr,

@@ -33,7 +33,7 @@
 //   colmap         t_max, section ends, K_eff at depth D, the column map
 //   list_scan_*    offsets of the excess lists and of their pair ranges
 //   lensort_*      stored row of every sequence, per-row division records
-//   planes         P rows in fp8 e4m3 (0x38 = 1.0, 0x00 = 0.0), block depths,
+//   planes         P rows as packed e2m1 (2 = 1.0, 0 = 0.0), block depths,
 //                  excess-list entries
 //   tiles          per set, the upper-triangle tile list with per-tile K extent
 //   residual_*     give residual blocks to tiles, zero them, add every pair
@@ -124,9 +124,9 @@ __device__ __forceinline__ int64_t dev_n_pad(int64_t n) {
 
 __device__ __forceinline__ int64_t dev_tiles_of_set(int64_t n) {
   const int64_t R = (n + kRowBlock - 1) / kRowBlock, C = (n + kColBlock - 1) / kColBlock;
-  int64_t total = 0;  // sum over I < R of max(0, C - floor(I / 2))
+  int64_t total = 0;  // sum over I < R of max(0, C - floor(I / kColRatio))
   for (int64_t I = 0; I < R; ++I) {
-    const int64_t j0 = I / 2;
+    const int64_t j0 = I / kColRatio;
     if (j0 < C) total += C - j0;
   }
   return total;
@@ -352,8 +352,8 @@ __global__ void __launch_bounds__(1024) colmap_kernel(RankPtrs P, int32_t eps, i
   // planes kept: sections 1..dkeep; a residual exists when some count exceeds it
   const int32_t dkeep = P.depth_cap >= 1 ? min(P.depth_cap, tmax) : tmax;
   const int64_t k_eff = dkeep >= 1 ? (int64_t)P.secend[dkeep] : 0;
-  int64_t k_pad = (k_eff + kKChunk - 1) / kKChunk * kKChunk;
-  if (k_pad < kKChunk) k_pad = kKChunk;
+  int64_t k_pad = (k_eff + kKCols - 1) / kKCols * kKCols;
+  if (k_pad < kKCols) k_pad = kKCols;
   if (tid == 0) {
     P.hdr->t_max = tmax;
     P.hdr->depth = dkeep;
@@ -742,33 +742,35 @@ __global__ void __launch_bounds__(256) planes_kernel(const int32_t *__restrict__
         }
       }
     }
-    // plane bytes: thread writes 4 consecutive columns (one 32-bit store per row);
-    // neighbouring lanes look up neighbouring words of the same section
+    // plane values: thread writes 8 consecutive columns (one 32-bit store of eight
+    // 4-bit values per row); neighbouring lanes look up neighbouring words of the
+    // same section
     uint32_t *dst[kPlaneRows];
 #pragma unroll
     for (int r = 0; r < kPlaneRows; ++r)
-      dst[r] = reinterpret_cast<uint32_t *>(P.planes + (g * kPlaneRows + r) * P.k_cap);
-    for (int c = threadIdx.x; c < k_pad / 4; c += blockDim.x) {
+      dst[r] = reinterpret_cast<uint32_t *>(P.planes + (g * kPlaneRows + r) * (P.k_cap / 2));
+    for (int c = threadIdx.x; c < k_pad / 8; c += blockDim.x) {
       uint32_t w[kPlaneRows] = {};
-      const int32_t c0 = c * 4;
-      if (c0 + 4 <= k_eff) {
-        const int4 e4 = __ldg(reinterpret_cast<const int4 *>(P.colmap + c0));
-        const int32_t ev[4] = {e4.x, e4.y, e4.z, e4.w};
+      const int32_t c0 = c * 8;
+      if (c0 + 8 <= k_eff) {
+        const int4 e4a = __ldg(reinterpret_cast<const int4 *>(P.colmap + c0));
+        const int4 e4b = __ldg(reinterpret_cast<const int4 *>(P.colmap + c0 + 4));
+        const int32_t ev[8] = {e4a.x, e4a.y, e4a.z, e4a.w, e4b.x, e4b.y, e4b.z, e4b.w};
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
+        for (int b = 0; b < 8; ++b) {
           const uint32_t tau = (uint32_t)ev[b] & 0xFFFFu, t = (uint32_t)ev[b] >> 16;
 #pragma unroll
           for (int r = 0; r < kPlaneRows; ++r)
-            if ((uint32_t)s_cnt[r * eps + tau] >= t) w[r] |= 0x38u << (8 * b);
+            if ((uint32_t)s_cnt[r * eps + tau] >= t) w[r] |= kE2M1One << (4 * b);
         }
       } else {
-        for (int b = 0; b < 4; ++b) {
+        for (int b = 0; b < 8; ++b) {
           if (c0 + b < k_eff) {
             const int32_t e = __ldg(P.colmap + c0 + b);
             const uint32_t tau = (uint32_t)e & 0xFFFFu, t = (uint32_t)e >> 16;
 #pragma unroll
             for (int r = 0; r < kPlaneRows; ++r)
-              if ((uint32_t)s_cnt[r * eps + tau] >= t) w[r] |= 0x38u << (8 * b);
+              if ((uint32_t)s_cnt[r * eps + tau] >= t) w[r] |= kE2M1One << (4 * b);
           }
         }
       }
@@ -787,18 +789,24 @@ __global__ void __launch_bounds__(256) planes_kernel(const int32_t *__restrict__
 }
 
 // Plane rows for depths D <= kTabDepth, streamed: one warp per stored row reads the
-// row's counts once (16 bytes per lane, four loads in flight). Section 1 gets each
-// word's byte [c >= 1] at the column the (t, word) table gives, as one 4-byte
-// store when the four words of a lane sit in four aligned consecutive columns
-// (every word occurs somewhere). The columns past section 1 are zero-filled with
-// 16-byte stores first, and only the words counted twice or more then set their
-// bytes in sections 2..min(c, D). Counts above D go to a per-warp buffer and are
-// appended to the flat excess list with one atomic per row; a row with more than
-// kExCap of them is scanned again for the append.
+// row's counts once (16 bytes per lane, four loads in flight). A plane value is
+// the 4-bit e2m1 [c >= t] (1.0 or 0), two columns to a byte. When every word
+// occurs somewhere, section 1 is the identity map and a lane writes its four words
+// as one 2-byte store; the columns past section 1 are zero-filled with 16-byte
+// stores first, and only the words counted twice or more then set their values in
+// sections 2..min(c, D) (atomic OR: neighbouring columns share bytes). Otherwise
+// the whole row is zero-filled and every 1 is set that way. Counts above D go to a
+// per-warp buffer and are appended to the flat excess list with one atomic per
+// row; a row with more than kExCap of them is scanned again for the append.
 constexpr int kExCap = 64;
 constexpr int kStreamUnroll = 4;
 
-__device__ __forceinline__ uint32_t plane_byte(int32_t c, int32_t t) { return c >= t ? 0x38u : 0u; }
+__device__ __forceinline__ uint32_t plane_val(int32_t c, int32_t t) { return c >= t ? kE2M1One : 0u; }
+
+// Set plane column col of a row to 1.0 (the row bytes are zero there beforehand).
+__device__ __forceinline__ void plane_set(uint8_t *prow, int32_t col) {
+  atomicOr(reinterpret_cast<unsigned int *>(prow) + (col >> 3), kE2M1One << (4 * (col & 7)));
+}
 
 __global__ void __launch_bounds__(256) planes_stream_kernel(const int32_t *__restrict__ counts,
                                                             int32_t eps, RankPtrs P) {
@@ -811,21 +819,24 @@ __global__ void __launch_bounds__(256) planes_stream_kernel(const int32_t *__res
   const bool residual = dkeep < P.hdr->t_max;
   const int q4 = eps >> 2;
   const int32_t s1 = P.secend[1];  // end of section 1
-  const int32_t s1_16 = min((s1 + 15) & ~15, k_pad);
+  const bool ident = s1 == eps;    // section 1 = every word, in order
+  const int32_t kb = k_pad / 2;    // row bytes in use
+  // bytes zero-filled before the ones are set: past section 1, or all of the row
+  const int32_t z0 = ident ? s1 / 2 : 0;
+  const int32_t z16 = min((z0 + 15) & ~15, kb);
   if (lane == 0) s_exn[warp] = 0;
   __syncwarp();
   for (int64_t pos = (int64_t)blockIdx.x * 8 + warp; pos < P.n_pad;
        pos += (int64_t)gridDim.x * 8) {
     const int32_t x = P.perm[pos];
-    uint8_t *prow = P.planes + pos * P.k_cap;
+    uint8_t *prow = P.planes + pos * (P.k_cap / 2);
     if (x < 0) {  // padding row: all zero
-      for (int c = 16 * lane; c < k_pad; c += 512)
+      for (int c = 16 * lane; c < kb; c += 512)
         *reinterpret_cast<uint4 *>(prow + c) = make_uint4(0, 0, 0, 0);
       continue;
     }
-    // columns [s1, k_pad): zero (deeper sections and the K padding)
-    for (int c = s1 + lane; c < s1_16; c += 32) prow[c] = 0;
-    for (int c = s1_16 + 16 * lane; c < k_pad; c += 512)
+    for (int c = z0 + lane; c < z16; c += 32) prow[c] = 0;
+    for (int c = z16 + 16 * lane; c < kb; c += 512)
       *reinterpret_cast<uint4 *>(prow + c) = make_uint4(0, 0, 0, 0);
     __syncwarp();
     const int4 *row4 = reinterpret_cast<const int4 *>(counts + (int64_t)x * eps);
@@ -845,26 +856,24 @@ __global__ void __launch_bounds__(256) planes_stream_kernel(const int32_t *__res
         const int32_t c[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
         mx = max(mx, max(max(c[0], c[1]), max(c[2], c[3])));
         sum += c[0] + c[1] + c[2] + c[3];
-        {
+        if (ident) {
+          // columns 4q..4q+3 = bytes 2q, 2q+1
+          *reinterpret_cast<uint16_t *>(prow + 2 * q) =
+              (uint16_t)(plane_val(c[0], 1) | plane_val(c[1], 1) << 4 | plane_val(c[2], 1) << 8 |
+                         plane_val(c[3], 1) << 12);
+        } else {
           const int4 col = __ldg(reinterpret_cast<const int4 *>(P.coltab) + q);
-          if (col.x >= 0 && (col.x & 3) == 0 && col.y == col.x + 1 && col.z == col.x + 2 &&
-              col.w == col.x + 3) {
-            *reinterpret_cast<uint32_t *>(prow + col.x) =
-                plane_byte(c[0], 1) | plane_byte(c[1], 1) << 8 | plane_byte(c[2], 1) << 16 |
-                plane_byte(c[3], 1) << 24;
-          } else {
-            const int32_t cc[4] = {col.x, col.y, col.z, col.w};
+          const int32_t cc[4] = {col.x, col.y, col.z, col.w};
 #pragma unroll
-            for (int b = 0; b < 4; ++b)
-              if (cc[b] >= 0) prow[cc[b]] = (uint8_t)plane_byte(c[b], 1);
-          }
+          for (int b = 0; b < 4; ++b)
+            if (cc[b] >= 0 && c[b] >= 1) plane_set(prow, cc[b]);
         }
         if (dkeep >= 2) {
-          // a word counted c >= 2 times is in sections 2..T >= c: its bytes there are 1
+          // a word counted c >= 2 times is in sections 2..T >= c: its values there are 1
 #pragma unroll
           for (int b = 0; b < 4; ++b)
             for (int t = 2; t <= min(c[b], dkeep); ++t)
-              prow[P.coltab[(int64_t)(t - 1) * eps + 4 * q + b]] = 0x38;
+              plane_set(prow, P.coltab[(int64_t)(t - 1) * eps + 4 * q + b]);
         }
         if (residual) {
 #pragma unroll
@@ -929,9 +938,9 @@ __global__ void __launch_bounds__(256) planes_stream_kernel(const int32_t *__res
 }
 
 // Upper-triangle tile list of every set (one block per set). Tile (I, J) of a
-// set covers its stored rows [128 I, 128 I + 128) and columns [256 J, 256 J + 256)
-// (set-local); it is needed when some pair i <= j lies in it (128 I <= 256 J + 255)
-// and both ranges hold real rows. Tiles are grouped by kGroupCols column blocks,
+// set covers its stored rows [128 I, 128 I + 128) and columns [128 J, 128 J + 128)
+// (set-local, kColBlock = 128); it is needed when some pair i <= j lies in it
+// (I <= J) and both ranges hold real rows. Tiles are grouped by kGroupCols column blocks,
 // rows ascending inside a group, so that the tiles running at the same time share
 // their operand panels in L2. Each entry is (I | J << 16, K chunks) with global
 // block indices, the K extent being the end of section min(depth(I), depth(J), D).
@@ -961,7 +970,7 @@ __global__ void __launch_bounds__(1024) tiles_kernel(RankPtrs P) {
       if (gi < rows_total) {
         const int32_t g = (int32_t)(gi / R);
         I = (int32_t)(gi % R);
-        j0 = max(g * kGroupCols, I / 2);  // smallest J with I <= 2J + 1
+        j0 = max(g * kGroupCols, I / kColRatio);  // smallest J reaching row block I
         j1 = min((g + 1) * kGroupCols, C);
         cnt = max(0, j1 - j0);
       }
@@ -970,12 +979,13 @@ __global__ void __launch_bounds__(1024) tiles_kernel(RankPtrs P) {
       int64_t out = e.tile_base + s_carry + incl - cnt;
       const int32_t dI = P.depth[I0 + I];
       for (int32_t J = j0; J < j1; ++J) {
-        const int32_t b0 = 2 * (J0 + J), b1 = b0 + 1;
-        int32_t dJ = P.depth[b0];
-        if (b1 < nblk) dJ = max(dJ, P.depth[b1]);
+        // the column block spans row blocks kColRatio (J0 + J) .. + kColRatio - 1
+        int32_t dJ = 0;
+        for (int32_t b = kColRatio * (J0 + J); b < kColRatio * (J0 + J + 1) && b < nblk; ++b)
+          dJ = max(dJ, P.depth[b]);
         const int32_t d = min(min(dI, dJ), dkeep);
         const int32_t kend = P.secend[max(d, 0)];
-        const int32_t nk = max(1, (kend + kKChunk - 1) / kKChunk);
+        const int32_t nk = max(1, (kend + kKCols - 1) / kKCols);
         P.tile_of[e.tileof_base + (int64_t)I * cfull + J] = (int32_t)out;
         P.block_of[out] = 0;
         P.tiles[out++] = make_int2((I0 + I) | ((J0 + J) << 16), nk);
@@ -1224,7 +1234,7 @@ int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *le
     SAD_LAUNCH_CHECK();
   }
   if (P.depth_cap >= 1 && P.depth_cap <= kTabDepth && (eps & 3) == 0 &&
-      (reinterpret_cast<uintptr_t>(counts) & 15) == 0 && (P.k_cap & 15) == 0) {
+      (reinterpret_cast<uintptr_t>(counts) & 15) == 0 && (P.k_cap & 31) == 0) {
     const int64_t warps = P.n_pad;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, planes_stream_kernel, 256, 0) !=

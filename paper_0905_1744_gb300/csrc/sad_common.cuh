@@ -17,9 +17,12 @@ constexpr int kMaxEps = 65536;          // words per count vector
 constexpr int kMaxM = 65535;            // k-mers per sequence (L - k + 1)
 constexpr int kMaxP = 4096;             // buckets
 constexpr int kRowBlock = 128;          // GEMM tile rows (A operand, M)
-constexpr int kColBlock = 256;          // GEMM tile columns (B operand, N)
+constexpr int kColBlock = 128;          // GEMM tile columns (B operand, N)
+constexpr int kColRatio = kColBlock / kRowBlock;  // row blocks per column block
 constexpr int kKChunk = 128;            // K bytes per pipeline stage (one 128B swizzle row)
-constexpr int kNPad = 256;              // rows are padded to a multiple of this
+constexpr int kKCols = 2 * kKChunk;     // plane columns per stage: two 4-bit values a byte
+constexpr int kNPad = 128;              // rows are padded to a multiple of this
+static_assert(kColBlock % kRowBlock == 0 && kNPad % kColBlock == 0, "tile shapes");
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -34,7 +37,7 @@ struct WsHeader {
   int32_t status;        // first recorded sad_status (0 = none)
   int32_t detail;        // optional detail of the error (e.g. offending index)
   int64_t k_eff;         // plane columns the data needs at the chosen depth (kmer_rank)
-  int32_t k_pad;         // k_eff rounded up to kKChunk
+  int32_t k_pad;         // k_eff rounded up to kKCols
   int32_t t_max;         // largest count of any word in any sequence
   int32_t n_tiles;       // GEMM tiles scheduled
   int32_t depth;         // planes kept per word (t_max when nothing is cut)
@@ -74,7 +77,7 @@ struct RankCaps {
   int64_t block_cap;     // residual blocks of kRowBlock x kColBlock u16
 };
 
-constexpr size_t kResidualBlockBytes = 2 * 128 * 256;  // u16 per pair of a tile
+constexpr size_t kResidualBlockBytes = 2 * kRowBlock * kColBlock;  // u16 per pair of a tile
 
 // One set of a (possibly batched) rank call, built on the device by rank_setup.
 // Sets are consecutive in the input order; each set's stored rows are a
@@ -99,7 +102,7 @@ inline int64_t tiles_of_set(int64_t n) {
   const int64_t R = (n + kRowBlock - 1) / kRowBlock, C = (n + kColBlock - 1) / kColBlock;
   int64_t total = 0;
   for (int64_t I = 0; I < R; ++I) {
-    const int64_t j0 = I / 2;  // smallest J with I <= 2J + 1
+    const int64_t j0 = I / kColRatio;  // smallest J whose columns reach row block I
     if (j0 < C) total += C - j0;
   }
   return total;
@@ -165,8 +168,8 @@ inline RankLayout rank_layout(const RankShape &sh, int64_t eps, const RankCaps &
   L.lists = take(2 * sizeof(int32_t) * (size_t)(caps.list_cap > 0 ? caps.list_cap : 1));
   L.flat = take(2 * sizeof(int32_t) * (size_t)(caps.list_cap > 0 ? caps.list_cap : 1));
   o = align_up(o, 1024);
-  L.planes = o;
-  o = align_up(o + (size_t)sh.rows_total * (size_t)caps.k_cap, 1024);
+  L.planes = o;  // rows_total x K_cap 4-bit values
+  o = align_up(o + (size_t)sh.rows_total * (size_t)caps.k_cap / 2, 1024);
   L.rblocks = o;
   o += kResidualBlockBytes * (size_t)caps.block_cap;
   L.bytes = align_up(o, 256);
@@ -395,13 +398,48 @@ __device__ __forceinline__ uint64_t sdesc_kmajor_sw128(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor, kind::f8f6f4: D=f32, A=B=e4m3, both K-major, shape M x N.
-__host__ __device__ constexpr uint32_t idesc_f8_e4m3(int M, int N) {
-  return (1u << 4)                       // D format f32
-         | (0u << 7) | (0u << 10)        // A, B = E4M3
+// Block-scaled 4-bit MMA (kind::mxf4nvf4, scale_vec::4X: one UE4M3 scale per 16
+// values of K), D f32 += A x B with A, B packed e2m1 from shared memory and the
+// scales of A and B read from TMEM; K = 64 per instruction.
+__device__ __forceinline__ void mma_f4(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                       uint32_t idesc, uint32_t sfa_tmem, uint32_t sfb_tmem,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %6, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::mxf4nvf4.block_scale.scale_vec::4X "
+      "[%0], %1, %2, %3, [%4], [%5], p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(sfa_tmem), "r"(sfb_tmem), "r"(accumulate)
+      : "memory");
+}
+
+// 32 lanes (this warp's quadrant) x 16 columns of TMEM from registers, all = v.
+__device__ __forceinline__ void tmem_st_32x32b_x16_fill(uint32_t taddr, uint32_t v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+      "{%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr),
+      "r"(v)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_st_wait() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// Instruction descriptor of the block-scaled kinds: A = B = E2M1 (format 1 of
+// kind::mxf4nvf4), both K-major, scales UE4M3 (bit 23 clear), scale-factor ids 0,
+// dense K = 64, shape M x N.
+__host__ __device__ constexpr uint32_t idesc_f4_e2m1(int M, int N) {
+  return (1u << 7) | (1u << 10)          // A, B = E2M1
          | (0u << 15) | (0u << 16)       // K-major A and B
          | ((uint32_t)(N >> 3) << 17)    // N / 8
+         | (0u << 23)                    // scale type UE4M3
          | ((uint32_t)(M >> 4) << 24);   // M / 16
 }
+
+// UE4M3 encoding of 1.0 (exponent 7 = bias, mantissa 0), four to a TMEM word.
+constexpr uint32_t kScaleOne4 = 0x38383838u;
+// e2m1 encoding of 1.0 (exponent 1 = bias, mantissa 0)
+constexpr uint32_t kE2M1One = 0x2u;
 
 }  // namespace sad
