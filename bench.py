@@ -8,7 +8,8 @@ N(N-1)/2 pairs whose shared k-mer count (Eq. 1) enters the ranks, per step time.
 
 Prints one JSON line. Extra objects:
   roofline      the plane-GEMM kernel: algorithmic tensor work per launch over
-                its CUDA-event time, against the measured fp8 peak
+                its CUDA-event time, against the 4-bit (e2m1) tensor peak derived
+                from the measured bf16 peak
   cpu_baseline  the CPU oracle on a bounded sample of the same workload
   e2e           the same metric through the public API with host buffers
                 (H2D of codes + offsets and D2H of the buckets and keys timed)
@@ -445,27 +446,32 @@ def run_sad(args):
 
     # roofline of the plane GEMM (the dominant kernel)
     pk, pk_kind = peaks()
-    # e4m3 dense = 2 x bf16 (nominal 4.5 / 2.25 PFLOP/s). The burst figure: the timed loop
-    # is short (a few hundred ms) and runs at the maximum SM clock (see "clocks").
-    fp8_peak = 2.0 * pk["bf16_tflops"]
+    # e2m1 dense = 6 x bf16 (nominal 13.5 / 2.25 PFLOP/s), applied to the measured bf16
+    # peak. The burst figure: the timed loop is short (a few hundred ms) and runs at the
+    # maximum SM clock (see "clocks").
+    f4_ratio = 13.5 / 2.25
+    f4_peak = f4_ratio * pk["bf16_tflops"]
     gemm_launch_ms = gemm_ms / max(gemm_n, 1)
     alg_flops = 2.0 * info["k_eff"] * n * (n + 1) / 2           # S = P P^T, upper triangle
-    exec_flops = 2.0 * 128 * 256 * 128 * info["k_chunks"]        # MMA work actually issued
+    exec_flops = 2.0 * 128 * 128 * 256 * info["k_chunks"]        # MMA work actually issued
     useful_flops = 2.0 * 8000 * pairs                             # Eq. 1 as written: 2 eps / pair
     achieved = alg_flops / (gemm_launch_ms / 1e3) / 1e12
     roofline = {
-        "bound": "tensor", "kernel": "plane_gemm_kernel (tcgen05 kind::f8f6f4)",
-        "achieved": achieved, "peak": fp8_peak, "unit": "TFLOP/s", "frac": achieved / fp8_peak,
-        "peak_source": f"{pk_kind}: 2 x bf16_tflops burst (e4m3/bf16 nominal ratio); "
-                       f"sustained would be {2.0 * pk['bf16_tflops_sustained']:.1f}",
+        "bound": "tensor",
+        "kernel": "plane_gemm_kernel (tcgen05 kind::mxf4nvf4, e2m1 0/1 planes, unit scales)",
+        "achieved": achieved, "peak": f4_peak, "unit": "TFLOP/s", "frac": achieved / f4_peak,
+        "peak_source": f"{pk_kind}: 6 x bf16_tflops burst (e2m1/bf16 nominal ratio "
+                       f"13.5/2.25); sustained would be "
+                       f"{f4_ratio * pk['bf16_tflops_sustained']:.1f}; the e4m3 peak "
+                       f"(2 x bf16) would be {2.0 * pk['bf16_tflops']:.1f}",
         "traffic": gemm_traffic_per_launch(n, info["k_eff"]),
         "gemm_ms_per_launch": gemm_launch_ms, "gemm_share_of_step": gemm_launch_ms / ms_per_step,
         "k_eff": info["k_eff"], "k_pad": info["k_pad"], "t_max": info["t_max"],
         "tiles": info["tiles"], "depth": info["depth"],
         "residual_pairs": info["residual_pairs"], "residual_tiles": info["residual_tiles"],
         "executed_tflops": exec_flops / (gemm_launch_ms / 1e3) / 1e12,
-        "executed_frac": exec_flops / (gemm_launch_ms / 1e3) / 1e12 / fp8_peak,
-        "useful_frac": useful_flops / (gemm_launch_ms / 1e3) / 1e12 / fp8_peak,
+        "executed_frac": exec_flops / (gemm_launch_ms / 1e3) / 1e12 / f4_peak,
+        "useful_frac": useful_flops / (gemm_launch_ms / 1e3) / 1e12 / f4_peak,
     }
 
     # end to end through the public API, host buffers, H2D/D2H inside the timed region
@@ -527,7 +533,7 @@ def run_sad(args):
             "metric": "k-mer pair comparisons/s", "value": value, "unit": "pairs/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "fp8_e4m3 0/1 planes, f32 acc (exact), u128 keys",
+            "vs_baseline": None, "dtype": "e2m1 0/1 planes (fp4), f32 acc (exact), u128 keys",
             "data": "synthetic",
             "config": {"workload": WORKLOADS[args.config], "N": n, "p": p, "k": 3,
                        "alphabet": 20, "seed": args.seed,

@@ -37,14 +37,16 @@ class Request:
 
 def request_bytes(s, depth: int, k: int = 3, alphabet: int = 20) -> int:
     """HBM a request holds while it is in flight (an upper estimate): codes,
-    offsets, counts, the rank workspace (planes at depth D <= 4 of the 8000
-    word columns, padded rows), keys, partition buffers."""
+    offsets, counts, the rank workspace (4-bit planes at depth D <= 4 of the 8000
+    word columns, padded rows; 128 x 128 u16 residual blocks), keys, partition
+    buffers."""
     n = s.offsets.shape[0] - 1
     eps = alphabet ** k
-    rows = (n + 255) // 256 * 256
+    rows = (n + 127) // 128 * 128
     d = depth if depth > 0 else 4
-    planes = rows * (eps * min(d, 4) + 128)
-    residual = ((n + 127) // 128) * ((n + 255) // 256) * 65536 if depth > 0 else 0
+    planes = rows * (eps * min(d, 4) + 256) // 2
+    blocks = (rows // 128) * (rows // 128 + 1) // 2
+    residual = blocks * 2 * 128 * 128 if depth > 0 else 0
     return int(s.codes.nbytes + 8 * (n + 1) + 4 * n * eps + planes + residual + 96 * n
                + (64 << 20))
 
