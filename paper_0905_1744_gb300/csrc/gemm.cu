@@ -59,8 +59,10 @@ constexpr uint64_t kWaitBudgetNs = 2000000000ull;
 struct GemmSmem {
   uint8_t a[kStages][kABytes];
   uint8_t b[kStages][kBBytes];
-  uint4 colrec[2][kColBlock];
-  int32_t colorig[2][kColBlock];
+  uint4 colrec[2][kColBlock];     // division record of each tile column
+  uint2 colfl[2][kColBlock];      // floor(S r / d) of a column: (r | sh1 << 16 | sh2 << 24, magic)
+  int32_t colorig[2][kColBlock];  // input index of each tile column (-1 = padding)
+  uint32_t colres[2][kColBlock];  // residual column sums of off-diagonal tiles
   uint64_t full[kStages];
   uint64_t empty[kStages];
   uint64_t tfull[2];
@@ -242,17 +244,30 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ------------------------------------------------------------ epilogue --
     // warp w reads TMEM lanes 32 (w % 4).. (its quadrant) and tile columns
     // [64 h, 64 h + 64), h = (w - 4) / 4, in sub-chunks of 16 columns.
+    //
+    // Off-diagonal tiles (I < J, so i < j and D_ij = m_j for every element) add only
+    // the floor parts floor(S_ij r_j / d_j) to both keys; the linear parts S_ij Q_j
+    // of the planes come from rank_lin.cu, and those of the residual R_ij (rare) are
+    // added here: R Q_j to the row, and Q_j times the residual column sum (kept in
+    // shared memory, added to the keys one tile later) to the column. Diagonal tiles
+    // add whole terms, masked to i <= j (row) and i < j (column).
     const uint32_t q = warp & 3;
     const uint32_t half = (warp - 4) >> 2;
     const uint32_t etid = threadIdx.x - 128;
+    for (uint32_t c = etid; c < 2u * kColBlock; c += kEpiThreads) (&S.colres[0][0])[c] = 0;
     int32_t lt = 0;
+    int32_t prev_off = 0;  // the previous tile was off-diagonal: its residual column sums wait
+    bool aborted = false;
     for (int32_t t = blockIdx.x; t < n_tiles; t += gridDim.x, ++lt) {
       const int2 tl = P.tiles[t];
       const int32_t I = tl.x & 0xFFFF, J = tl.x >> 16;
       const int buf = lt & 1;
       for (uint32_t c = etid; c < (uint32_t)kColBlock; c += kEpiThreads) {
         const int64_t jpos = (int64_t)J * kColBlock + c;
-        S.colrec[buf][c] = P.rec[jpos];
+        const uint4 rec = P.rec[jpos];
+        S.colrec[buf][c] = rec;
+        const uint32_t d = rec.w & 0xFFFFu;
+        S.colfl[buf][c] = make_uint2(((0u - rec.x * d) & 0xFFFFu) | (rec.w & 0xFFFF0000u), rec.z);
         S.colorig[buf][c] = P.perm[jpos];
       }
       const int64_t row_pos = (int64_t)I * kRowBlock + q * 32 + lane;
@@ -273,68 +288,131 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       const uint32_t acc = lt & 1, aph = (lt >> 1) & 1;
       if (!mbar_wait_bounded(&S.tfull[acc], aph, abort_flag, kWaitBudgetNs)) set_abort(S, P.hdr);
-      named_bar_sync(1, kEpiThreads);  // column records staged; abort decided
-      if (*abort_flag) break;
-      tc_fence_after();
-      uint32_t R0 = 0, R1 = 0, R2 = 0;
-#pragma unroll 1
-      for (int sc = 0; sc < kHalfCols / 16; ++sc) {
-        const int c0 = (int)half * kHalfCols + sc * 16;
-        uint32_t v[16];
-        tmem_ld_32x32b_x16(tmem + ((q * 32u) << 16) + acc * (uint32_t)kColBlock + (uint32_t)c0,
-                           v);
-        const uint32_t rw[8] = {ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
-        if (rrow && sc + 1 < kHalfCols / 16) {  // next sub-chunk's residual words
-          ra = __ldg(rrow + 2 * (sc + 1));
-          rb = __ldg(rrow + 2 * (sc + 1) + 1);
-        }
-        tmem_ld_wait();
-        uint32_t cs[16], cq[16];
-#pragma unroll
-        for (int cc = 0; cc < 16; ++cc) {
-          const uint4 rec = S.colrec[buf][c0 + cc];
-          const uint32_t s = __float2uint_rn(__uint_as_float(v[cc])) +
-                             ((rw[cc >> 1] >> (16 * (cc & 1))) & 0xFFFFu);
-          const uint32_t d = rec.w & 0xFFFFu;
-          const uint32_t sh1 = (rec.w >> 16) & 0xFFu, sh2 = rec.w >> 24;
-          // floor(s * 2^64 / d) = s * Q + floor(s * r / d), r = 2^64 - Q d
-          const uint32_t r = 0u - rec.x * d;
-          const uint32_t xq = s * r;
-          const uint32_t t1 = __umulhi(rec.z, xq);
-          const uint32_t qv = (t1 + ((xq - t1) >> sh1)) >> sh2;
+      // column records staged, previous tile done; the abort decision is the same for
+      // every epilogue thread
+      aborted = named_bar_sync_or(1, kEpiThreads, *abort_flag != 0);
+      if (aborted) break;
+      if (prev_off) {
+        // residual column sums of the previous (off-diagonal) tile: Q_j times the sum
+        const int pb = buf ^ 1;
+        for (uint32_t c = etid; c < (uint32_t)kColBlock; c += kEpiThreads) {
+          const uint32_t rs = S.colres[pb][c];
+          if (rs == 0) continue;
+          S.colres[pb][c] = 0;
+          const int32_t jorig = S.colorig[pb][c];
+          if (jorig < 0) continue;
+          const uint4 rec = S.colrec[pb][c];
           const uint64_t Q = ((uint64_t)rec.y << 32) | rec.x;
-          const uint64_t lo = (uint64_t)s * Q;
-          const uint64_t lo2 = lo + qv;
-          const uint32_t hi = lo2 < lo ? 1u : 0u;
-          const uint32_t wa = (uint32_t)lo2, wb = (uint32_t)(lo2 >> 32);
-          uint32_t l0 = wa & 0xFFFFFFu;
-          uint32_t l1 = (wa >> 24) | ((wb & 0xFFFFu) << 8);
-          uint32_t l2 = (wb >> 16) | (hi << 16);
-          uint32_t scv = s, qc = qv;
-          if (diag) {
+          const uint64_t lo = Q * rs, hi = __umul64hi(Q, (uint64_t)rs);
+          unsigned long long *dst = P.acc + 3 * (int64_t)jorig;
+          red_add_u64(dst + 0, lo & 0xFFFFFFull);
+          red_add_u64(dst + 1, (lo >> 24) & 0xFFFFFFull);
+          red_add_u64(dst + 2, (lo >> 48) | (hi << 16));
+        }
+      }
+      prev_off = diag ? 0 : 1;
+      tc_fence_after();
+      uint32_t R0 = 0, R1 = 0, R2 = 0;  // row: 24-bit limb sums (R0 alone off the diagonal)
+      uint64_t L0 = 0, L1 = 0, L2 = 0;  // row: residual linear part R Q_j, off the diagonal
+      if (!diag) {
+#pragma unroll 1
+        for (int sc = 0; sc < kHalfCols / 16; ++sc) {
+          const int c0 = (int)half * kHalfCols + sc * 16;
+          uint32_t v[16];
+          tmem_ld_32x32b_x16(tmem + ((q * 32u) << 16) + acc * (uint32_t)kColBlock + (uint32_t)c0,
+                             v);
+          const uint32_t rw[8] = {ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
+          if (rrow && sc + 1 < kHalfCols / 16) {  // next sub-chunk's residual words
+            ra = __ldg(rrow + 2 * (sc + 1));
+            rb = __ldg(rrow + 2 * (sc + 1) + 1);
+          }
+          tmem_ld_wait();
+          uint32_t cq[16];
+#pragma unroll
+          for (int cc = 0; cc < 16; ++cc) {
+            const uint2 fl = S.colfl[buf][c0 + cc];
+            const uint32_t res = (rw[cc >> 1] >> (16 * (cc & 1))) & 0xFFFFu;
+            const uint32_t sv = __float2uint_rn(__uint_as_float(v[cc])) + res;
+            // floor(s r / d) by Granlund & Montgomery: s r < 2^32
+            const uint32_t xq = sv * (fl.x & 0xFFFFu);
+            const uint32_t t1 = __umulhi(fl.y, xq);
+            const uint32_t qv = (t1 + ((xq - t1) >> ((fl.x >> 16) & 0xFFu))) >> (fl.x >> 24);
+            R0 += qv;
+            cq[cc] = qv;
+            if (res) {
+              const uint4 rec = S.colrec[buf][c0 + cc];
+              const uint64_t Q = ((uint64_t)rec.y << 32) | rec.x;
+              const uint64_t lo = Q * res, hi = __umul64hi(Q, (uint64_t)res);
+              L0 += lo & 0xFFFFFFull;
+              L1 += (lo >> 24) & 0xFFFFFFull;
+              L2 += (lo >> 48) | (hi << 16);
+              atomicAdd(&S.colres[buf][c0 + cc], res);
+            }
+          }
+          transpose_reduce16(cq, lane);
+          if (lane < 16) {
+            const int32_t jorig = S.colorig[buf][c0 + (int)lane];
+            if (jorig >= 0 && cq[0] != 0) red_add_u64(P.acc + 3 * (int64_t)jorig, cq[0]);
+          }
+        }
+      } else {
+#pragma unroll 1
+        for (int sc = 0; sc < kHalfCols / 16; ++sc) {
+          const int c0 = (int)half * kHalfCols + sc * 16;
+          uint32_t v[16];
+          tmem_ld_32x32b_x16(tmem + ((q * 32u) << 16) + acc * (uint32_t)kColBlock + (uint32_t)c0,
+                             v);
+          const uint32_t rw[8] = {ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
+          if (rrow && sc + 1 < kHalfCols / 16) {  // next sub-chunk's residual words
+            ra = __ldg(rrow + 2 * (sc + 1));
+            rb = __ldg(rrow + 2 * (sc + 1) + 1);
+          }
+          tmem_ld_wait();
+          uint32_t cs[16], cq[16];
+#pragma unroll
+          for (int cc = 0; cc < 16; ++cc) {
+            const uint4 rec = S.colrec[buf][c0 + cc];
+            const uint32_t s = __float2uint_rn(__uint_as_float(v[cc])) +
+                               ((rw[cc >> 1] >> (16 * (cc & 1))) & 0xFFFFu);
+            const uint32_t d = rec.w & 0xFFFFu;
+            const uint32_t sh1 = (rec.w >> 16) & 0xFFu, sh2 = rec.w >> 24;
+            // floor(s * 2^64 / d) = s * Q + floor(s * r / d), r = 2^64 - Q d
+            const uint32_t r = 0u - rec.x * d;
+            const uint32_t xq = s * r;
+            const uint32_t t1 = __umulhi(rec.z, xq);
+            const uint32_t qv = (t1 + ((xq - t1) >> sh1)) >> sh2;
+            const uint64_t Q = ((uint64_t)rec.y << 32) | rec.x;
+            const uint64_t lo = (uint64_t)s * Q;
+            const uint64_t lo2 = lo + qv;
+            const uint32_t hi = lo2 < lo ? 1u : 0u;
+            const uint32_t wa = (uint32_t)lo2, wb = (uint32_t)(lo2 >> 32);
+            uint32_t l0 = wa & 0xFFFFFFu;
+            uint32_t l1 = (wa >> 24) | ((wb & 0xFFFFu) << 8);
+            uint32_t l2 = (wb >> 16) | (hi << 16);
+            uint32_t scv = s, qc = qv;
             const int64_t jpos = (int64_t)J * kColBlock + c0 + cc;
             if (row_pos > jpos) { l0 = 0; l1 = 0; l2 = 0; }
             if (row_pos >= jpos) { scv = 0; qc = 0; }
+            R0 += l0;
+            R1 += l1;
+            R2 += l2;
+            cs[cc] = scv;
+            cq[cc] = qc;
           }
-          R0 += l0;
-          R1 += l1;
-          R2 += l2;
-          cs[cc] = scv;
-          cq[cc] = qc;
-        }
-        transpose_reduce16(cs, lane);
-        transpose_reduce16(cq, lane);
-        if (lane < 16) {
-          const int col = c0 + (int)lane;
-          const int32_t jorig = S.colorig[buf][col];
-          if (jorig >= 0 && (cs[0] | cq[0]) != 0) {
-            const uint4 rec = S.colrec[buf][col];
-            const uint64_t Q = ((uint64_t)rec.y << 32) | rec.x;
-            const unsigned __int128 sum = (unsigned __int128)Q * cs[0] + cq[0];
-            unsigned long long *dst = P.acc + 3 * (int64_t)jorig;
-            red_add_u64(dst + 0, (unsigned long long)(sum & 0xFFFFFFu));
-            red_add_u64(dst + 1, (unsigned long long)((sum >> 24) & 0xFFFFFFu));
-            red_add_u64(dst + 2, (unsigned long long)(sum >> 48));
+          transpose_reduce16(cs, lane);
+          transpose_reduce16(cq, lane);
+          if (lane < 16) {
+            const int col = c0 + (int)lane;
+            const int32_t jorig = S.colorig[buf][col];
+            if (jorig >= 0 && (cs[0] | cq[0]) != 0) {
+              const uint4 rec = S.colrec[buf][col];
+              const uint64_t Q = ((uint64_t)rec.y << 32) | rec.x;
+              const unsigned __int128 sum = (unsigned __int128)Q * cs[0] + cq[0];
+              unsigned long long *dst = P.acc + 3 * (int64_t)jorig;
+              red_add_u64(dst + 0, (unsigned long long)(sum & 0xFFFFFFu));
+              red_add_u64(dst + 1, (unsigned long long)((sum >> 24) & 0xFFFFFFu));
+              red_add_u64(dst + 2, (unsigned long long)(sum >> 48));
+            }
           }
         }
       }
@@ -342,9 +420,26 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_arrive(&S.tempty[acc]);
       if (row_orig >= 0) {
         unsigned long long *dst = P.acc + 3 * (int64_t)row_orig;
-        red_add_u64(dst + 0, R0);
-        red_add_u64(dst + 1, R1);
-        red_add_u64(dst + 2, R2);
+        if (R0 | L0) red_add_u64(dst + 0, (unsigned long long)R0 + L0);
+        if (R1 | L1) red_add_u64(dst + 1, (unsigned long long)R1 + L1);
+        if (R2 | L2) red_add_u64(dst + 2, (unsigned long long)R2 + L2);
+      }
+    }
+    if (prev_off && !aborted) {
+      // the last tile's residual column sums
+      named_bar_sync(1, kEpiThreads);
+      const int pb = (lt - 1) & 1;
+      for (uint32_t c = etid; c < (uint32_t)kColBlock; c += kEpiThreads) {
+        const uint32_t rs = S.colres[pb][c];
+        const int32_t jorig = S.colorig[pb][c];
+        if (rs == 0 || jorig < 0) continue;
+        const uint4 rec = S.colrec[pb][c];
+        const uint64_t Q = ((uint64_t)rec.y << 32) | rec.x;
+        const uint64_t lo = Q * rs, hi = __umul64hi(Q, (uint64_t)rs);
+        unsigned long long *dst = P.acc + 3 * (int64_t)jorig;
+        red_add_u64(dst + 0, lo & 0xFFFFFFull);
+        red_add_u64(dst + 1, (lo >> 24) & 0xFFFFFFull);
+        red_add_u64(dst + 2, (lo >> 48) | (hi << 16));
       }
     }
   }

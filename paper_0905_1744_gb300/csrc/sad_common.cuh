@@ -127,7 +127,7 @@ inline RankShape shape_single(int64_t n) {
 struct RankLayout {
   size_t sets, seq_set, row_set, T, secend, thist, coltab, mhist, perm, rec, depth, tiles,
       acc, cnt_gt, list_off, item_off, cursor, tile_of, block_of, sortbuf, scanblk, colmap, lists,
-      flat, planes, rblocks;
+      flat, planes, lin_cnt, lin_q, rblocks;
   size_t fixed_bytes;    // everything that does not depend on the capacities
   size_t bytes;          // total
   RankShape shape;
@@ -170,6 +170,12 @@ inline RankLayout rank_layout(const RankShape &sh, int64_t eps, const RankCaps &
   o = align_up(o, 1024);
   L.planes = o;  // rows_total x K_cap 4-bit values
   o = align_up(o + (size_t)sh.rows_total * (size_t)caps.k_cap / 2, 1024);
+  // per 128-row block and plane column: row count and sum of Q (linear key part)
+  const size_t lin_n = (size_t)(sh.rows_total / kRowBlock) * (size_t)caps.k_cap;
+  L.lin_cnt = o;
+  o = align_up(o + sizeof(uint32_t) * lin_n, 256);
+  L.lin_q = o;
+  o = align_up(o + 2 * sizeof(uint64_t) * lin_n, 256);
   L.rblocks = o;
   o += kResidualBlockBytes * (size_t)caps.block_cap;
   L.bytes = align_up(o, 256);
@@ -258,6 +264,21 @@ __device__ __forceinline__ bool elect_lane0() { return (threadIdx.x & 31) == 0; 
 // Named barrier among `count` threads (multiple of 32).
 __device__ __forceinline__ void named_bar_sync(int id, int count) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// Named barrier that also ORs a predicate over the participating threads: every
+// thread gets the same result.
+__device__ __forceinline__ bool named_bar_sync_or(int id, int count, bool pred) {
+  uint32_t out;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, %2, %3, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}\n"
+      : "=r"(out)
+      : "r"((uint32_t)pred), "r"(id), "r"(count)
+      : "memory");
+  return out != 0;
 }
 
 // --------------------------------------------------------- PTX: mbarrier ----
