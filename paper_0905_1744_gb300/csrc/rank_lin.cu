@@ -39,18 +39,23 @@ __global__ void __launch_bounds__(256) lin_cols_kernel(RankPtrs P) {
   const uint32_t *col = reinterpret_cast<const uint32_t *>(P.planes) + b * kRowBlock * row_words + w;
   uint32_t cnt[8] = {};
   uint64_t qlo[8] = {}, qhi[8] = {};
-#pragma unroll 4
-  for (int r = 0; r < kRowBlock; ++r) {
-    const uint32_t v = __ldg(col + r * row_words);
-    if (v == 0) continue;
-    const uint4 rec = P.rec[b * kRowBlock + r];
-    const uint64_t Q = (uint64_t)rec.x | ((uint64_t)rec.y << 32);
+  constexpr int kBatch = 16;  // rows loaded before any is used
+  for (int r0 = 0; r0 < kRowBlock; r0 += kBatch) {
+    uint32_t v[kBatch];
 #pragma unroll
-    for (int n = 0; n < 8; ++n) {
-      if ((v >> (4 * n)) & 0xFu) {
-        cnt[n] += 1;
-        qlo[n] += Q;
-        qhi[n] += qlo[n] < Q ? 1u : 0u;
+    for (int r = 0; r < kBatch; ++r) v[r] = __ldg(col + (r0 + r) * row_words);
+#pragma unroll
+    for (int r = 0; r < kBatch; ++r) {
+      if (v[r] == 0) continue;
+      const uint4 rec = __ldg(P.rec + b * kRowBlock + r0 + r);
+      const uint64_t Q = (uint64_t)rec.x | ((uint64_t)rec.y << 32);
+#pragma unroll
+      for (int n = 0; n < 8; ++n) {
+        if ((v[r] >> (4 * n)) & 0xFu) {
+          cnt[n] += 1;
+          qlo[n] += Q;
+          qhi[n] += qlo[n] < Q ? 1u : 0u;
+        }
       }
     }
   }
@@ -73,18 +78,32 @@ __global__ void __launch_bounds__(256) lin_scan_kernel(RankPtrs P) {
     const int64_t b0 = e.row_base / kRowBlock;
     const int64_t nb = ((e.n > 0 ? e.n : 1) + kNPad - 1) / kNPad * kNPad / kRowBlock;
     if (nb <= 1) continue;  // one block: every pair is in its diagonal tile
+    // batches of kBatch blocks: all loads of a batch before its stores
+    constexpr int kBatch = 16;
     uint32_t run = 0;
-    for (int64_t b = b0; b < b0 + nb; ++b) {
-      const uint32_t c = P.lin_cnt[b * P.k_cap + k];
-      P.lin_cnt[b * P.k_cap + k] = run;
-      run += c;
+    for (int64_t bb = 0; bb < nb; bb += kBatch) {
+      uint32_t c[kBatch];
+#pragma unroll
+      for (int i = 0; i < kBatch; ++i)
+        c[i] = bb + i < nb ? P.lin_cnt[(b0 + bb + i) * P.k_cap + k] : 0u;
+#pragma unroll
+      for (int i = 0; i < kBatch; ++i) {
+        if (bb + i < nb) P.lin_cnt[(b0 + bb + i) * P.k_cap + k] = run;
+        run += c[i];
+      }
     }
     uint64_t vlo = 0, vhi = 0;
-    for (int64_t b = b0 + nb - 1; b >= b0; --b) {
-      const ulonglong2 q = P.lin_q[b * P.k_cap + k];
-      P.lin_q[b * P.k_cap + k] = make_ulonglong2(vlo, vhi);
-      vlo += q.x;
-      vhi += q.y + (vlo < q.x ? 1u : 0u);
+    for (int64_t bb = 0; bb < nb; bb += kBatch) {  // blocks from the last one down
+      ulonglong2 q[kBatch];
+#pragma unroll
+      for (int i = 0; i < kBatch; ++i)
+        q[i] = bb + i < nb ? P.lin_q[(b0 + nb - 1 - bb - i) * P.k_cap + k] : make_ulonglong2(0, 0);
+#pragma unroll
+      for (int i = 0; i < kBatch; ++i) {
+        if (bb + i < nb) P.lin_q[(b0 + nb - 1 - bb - i) * P.k_cap + k] = make_ulonglong2(vlo, vhi);
+        vlo += q[i].x;
+        vhi += q[i].y + (vlo < q[i].x ? 1u : 0u);
+      }
     }
   }
 }
@@ -106,17 +125,23 @@ __global__ void __launch_bounds__(256) lin_rows_kernel(RankPtrs P) {
     const uint32_t *U = P.lin_cnt + b * P.k_cap;
     const ulonglong2 *V = P.lin_q + b * P.k_cap;
     uint64_t u = 0, s0 = 0, s1 = 0, s2 = 0;
-    for (int64_t w = lane; w < words; w += 32) {
-      uint32_t v = __ldg(row + w);
-      while (v) {
-        const int n = (__ffs((int)v) - 1) >> 2;  // nibble holding the lowest set bit
-        v &= ~(0xFu << (4 * n));
-        const int64_t k = 8 * w + n;
-        u += U[k];
-        const ulonglong2 q = V[k];
-        s0 += q.x & 0xFFFFFFull;
-        s1 += (q.x >> 24) & 0xFFFFFFull;
-        s2 += (q.x >> 48) | (q.y << 16);
+    for (int64_t w0 = 4 * lane; w0 < words; w0 += 128) {
+      // four words (32 columns) per lane: 16-byte load (rows are 16-byte aligned)
+      const uint4 v4 = __ldg(reinterpret_cast<const uint4 *>(row + w0));
+      const uint32_t vw[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        uint32_t v = vw[i];
+        while (v) {
+          const int n = (__ffs((int)v) - 1) >> 2;  // nibble holding the lowest set bit
+          v &= ~(0xFu << (4 * n));
+          const int64_t k = 8 * (w0 + i) + n;
+          u += __ldg(U + k);
+          const ulonglong2 q = __ldg(V + k);
+          s0 += q.x & 0xFFFFFFull;
+          s1 += (q.x >> 24) & 0xFFFFFFull;
+          s2 += (q.x >> 48) | (q.y << 16);
+        }
       }
     }
 #pragma unroll

@@ -17,11 +17,11 @@ constexpr int kMaxEps = 65536;          // words per count vector
 constexpr int kMaxM = 65535;            // k-mers per sequence (L - k + 1)
 constexpr int kMaxP = 4096;             // buckets
 constexpr int kRowBlock = 128;          // GEMM tile rows (A operand, M)
-constexpr int kColBlock = 128;          // GEMM tile columns (B operand, N)
+constexpr int kColBlock = 256;          // GEMM tile columns (B operand): two N = 128 halves
 constexpr int kColRatio = kColBlock / kRowBlock;  // row blocks per column block
 constexpr int kKChunk = 128;            // K bytes per pipeline stage (one 128B swizzle row)
 constexpr int kKCols = 2 * kKChunk;     // plane columns per stage: two 4-bit values a byte
-constexpr int kNPad = 128;              // rows are padded to a multiple of this
+constexpr int kNPad = 256;              // rows are padded to a multiple of this
 static_assert(kColBlock % kRowBlock == 0 && kNPad % kColBlock == 0, "tile shapes");
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
