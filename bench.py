@@ -453,7 +453,7 @@ def run_sad(args):
     f4_peak = f4_ratio * pk["bf16_tflops"]
     gemm_launch_ms = gemm_ms / max(gemm_n, 1)
     alg_flops = 2.0 * info["k_eff"] * n * (n + 1) / 2           # S = P P^T, upper triangle
-    exec_flops = 2.0 * 128 * 256 * 256 * info["k_chunks"]        # MMA work actually issued
+    exec_flops = 2.0 * 128 * 128 * 256 * info["k_chunks"]        # MMA work actually issued
     useful_flops = 2.0 * 8000 * pairs                             # Eq. 1 as written: 2 eps / pair
     achieved = alg_flops / (gemm_launch_ms / 1e3) / 1e12
     roofline = {

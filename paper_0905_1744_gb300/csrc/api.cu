@@ -234,8 +234,6 @@ int rank_run_impl(const int32_t *d_counts, const int32_t *d_lengths, const int32
   const RankPtrs P = rank_ptrs(d_ws, L);
   int rc = rank_prep_launch(P, d_counts, d_lengths, d_n, word_max, k, (int32_t)eps, 0, st);
   if (rc) return rc;
-  rc = rank_linear_launch(P, st);
-  if (rc) return rc;
   rc = rank_gemm_launch(P, st);
   if (rc) return rc;
   return rank_finalize_launch(P, d_key_hi, d_key_lo, d_rank, st);

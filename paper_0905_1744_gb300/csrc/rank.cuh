@@ -22,13 +22,7 @@ struct RankPtrs {
   uint4 *rec;            // [rows_total] division record of each stored row's m
   int2 *tiles;           // [tiles_total] (I | J << 16, K chunks), global block indices
   unsigned long long *acc;  // [n_total][3] 24-bit-limb accumulators of the keys
-  uint8_t *planes;       // [rows_total][K_cap / 2] e2m1 threshold planes (sections 1..depth)
-  // linear key part, per 128-row block b and plane column k: after lin_cols the row
-  // count and the sum of Q over the block's rows with a 1 in column k; after
-  // lin_scan the count over the set's earlier blocks (U) and the Q sum over its
-  // later blocks (V)
-  uint32_t *lin_cnt;     // [rows_total / 128][K_cap]
-  ulonglong2 *lin_q;     // [rows_total / 128][K_cap] 128-bit (x = low, y = high word)
+  uint8_t *planes;       // [rows_total][K_cap] fp8 threshold planes (sections 1..depth)
   // residual of the counts above the plane depth, per (set, word)
   int32_t *cnt_gt;       // [n_sets * eps] sequences whose count of the word exceeds depth
   int64_t *list_off;     // [n_sets * eps + 1] start of each excess list
@@ -53,10 +47,6 @@ RankPtrs rank_ptrs(void *ws, const RankLayout &L);
 int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *lengths,
                      const int32_t *d_n, const int32_t *word_max, int32_t k, int32_t eps,
                      int plan_only, cudaStream_t st);
-// The linear part of the keys over pairs of rows in different 128-row blocks:
-// sum over such pairs (i < j stored) of S_ij Q_j, added to both keys, computed from
-// the planes in O(N K) (rank_lin.cu).
-int rank_linear_launch(const RankPtrs &P, cudaStream_t st);
 int rank_gemm_launch(const RankPtrs &P, cudaStream_t st);
 int rank_finalize_launch(const RankPtrs &P, uint64_t *key_hi, uint64_t *key_lo, double *rank,
                          cudaStream_t st);

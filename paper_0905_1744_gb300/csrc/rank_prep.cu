@@ -61,8 +61,6 @@ RankPtrs rank_ptrs(void *ws, const RankLayout &L) {
   P.tiles = reinterpret_cast<int2 *>(b + L.tiles);
   P.acc = reinterpret_cast<unsigned long long *>(b + L.acc);
   P.planes = b + L.planes;
-  P.lin_cnt = reinterpret_cast<uint32_t *>(b + L.lin_cnt);
-  P.lin_q = reinterpret_cast<ulonglong2 *>(b + L.lin_q);
   P.cnt_gt = reinterpret_cast<int32_t *>(b + L.cnt_gt);
   P.list_off = reinterpret_cast<int64_t *>(b + L.list_off);
   P.item_off = reinterpret_cast<int64_t *>(b + L.item_off);

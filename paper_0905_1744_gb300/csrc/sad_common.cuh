@@ -17,11 +17,11 @@ constexpr int kMaxEps = 65536;          // words per count vector
 constexpr int kMaxM = 65535;            // k-mers per sequence (L - k + 1)
 constexpr int kMaxP = 4096;             // buckets
 constexpr int kRowBlock = 128;          // GEMM tile rows (A operand, M)
-constexpr int kColBlock = 256;          // GEMM tile columns (B operand): two N = 128 halves
+constexpr int kColBlock = 128;          // GEMM tile columns (B operand, N)
 constexpr int kColRatio = kColBlock / kRowBlock;  // row blocks per column block
 constexpr int kKChunk = 128;            // K bytes per pipeline stage (one 128B swizzle row)
 constexpr int kKCols = 2 * kKChunk;     // plane columns per stage: two 4-bit values a byte
-constexpr int kNPad = 256;              // rows are padded to a multiple of this
+constexpr int kNPad = 128;              // rows are padded to a multiple of this
 static_assert(kColBlock % kRowBlock == 0 && kNPad % kColBlock == 0, "tile shapes");
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -127,7 +127,7 @@ inline RankShape shape_single(int64_t n) {
 struct RankLayout {
   size_t sets, seq_set, row_set, T, secend, thist, coltab, mhist, perm, rec, depth, tiles,
       acc, cnt_gt, list_off, item_off, cursor, tile_of, block_of, sortbuf, scanblk, colmap, lists,
-      flat, planes, lin_cnt, lin_q, rblocks;
+      flat, planes, rblocks;
   size_t fixed_bytes;    // everything that does not depend on the capacities
   size_t bytes;          // total
   RankShape shape;
@@ -170,12 +170,6 @@ inline RankLayout rank_layout(const RankShape &sh, int64_t eps, const RankCaps &
   o = align_up(o, 1024);
   L.planes = o;  // rows_total x K_cap 4-bit values
   o = align_up(o + (size_t)sh.rows_total * (size_t)caps.k_cap / 2, 1024);
-  // per 128-row block and plane column: row count and sum of Q (linear key part)
-  const size_t lin_n = (size_t)(sh.rows_total / kRowBlock) * (size_t)caps.k_cap;
-  L.lin_cnt = o;
-  o = align_up(o + sizeof(uint32_t) * lin_n, 256);
-  L.lin_q = o;
-  o = align_up(o + 2 * sizeof(uint64_t) * lin_n, 256);
   L.rblocks = o;
   o += kResidualBlockBytes * (size_t)caps.block_cap;
   L.bytes = align_up(o, 256);

@@ -42,12 +42,11 @@ def request_bytes(s, depth: int, k: int = 3, alphabet: int = 20) -> int:
     buffers."""
     n = s.offsets.shape[0] - 1
     eps = alphabet ** k
-    rows = (n + 255) // 256 * 256
+    rows = (n + 127) // 128 * 128
     d = depth if depth > 0 else 4
-    cols = eps * min(d, 4) + 256
-    planes = rows * cols // 2 + (rows // 128) * cols * 20   # + linear-part tables
-    blocks = (rows // 128) * (rows // 256 + 1)
-    residual = blocks * 2 * 128 * 256 if depth > 0 else 0
+    planes = rows * (eps * min(d, 4) + 256) // 2
+    blocks = (rows // 128) * (rows // 128 + 1) // 2
+    residual = blocks * 2 * 128 * 128 if depth > 0 else 0
     return int(s.codes.nbytes + 8 * (n + 1) + 4 * n * eps + planes + residual + 96 * n
                + (64 << 20))
 

@@ -49,8 +49,8 @@ def test_host_only_queries(lib):
     assert ws(0, 100, 3, 20, 1, 1) == 256
     rank_fixed = ws(1, 20000, 3, 20, 1, 0)
     rank_d2 = ws(1, 20000, 3, 20, 1, 2)
-    # planes at depth 2: 20224 stored rows x 16000 columns, two 4-bit values a byte
-    assert rank_fixed > 0 and rank_d2 >= rank_fixed + 20224 * 16000 // 2
+    # planes at depth 2: 20096 stored rows x 16000 columns, two 4-bit values a byte
+    assert rank_fixed > 0 and rank_d2 >= rank_fixed + 20096 * 16000 // 2
     assert ws(2, 1000, 3, 20, 16, 1) > 1000 * 48
     assert ws(2, 1000, 3, 20, 0, 1) == 0          # p < 1
     assert ws(1, 10, 9, 20, 1, 1) == 0            # k > 8 unsupported
