@@ -18,6 +18,14 @@ Parity status of each function (what pins it, in ``tests/test_oracle_pins.py``):
   partition    hand-derived regular-sampling example (N=16, p=4; N=8, p=2),
                concatenated buckets equal the sorted order, bucket intervals
                (y_{i-1}, y_i], the 2N/p load bound when p | N and N >= p^3.
+  rank_vs      exact big-integer sum over a reference multiset with shared counts
+               from substring enumeration; duplicates count twice; reference =
+               every sequence gives the centralised key.
+  local_samples  hand-derived positions (keys = index and reversed keys), block
+               bounds floor(bN/p).
+  global_rank  p = 1 with ks = N samples every sequence once (positions
+               floor(j N / (N + 1)), j = 1..N, are 0..N-1), so the globalised key
+               equals the centralised one.
 """
 from __future__ import annotations
 
@@ -65,6 +73,10 @@ def _load():
         lib.sad_oracle_kmer_rank.restype = ctypes.c_int
         lib.sad_oracle_partition.argtypes = [P, P, i32, i32, P, P, P]
         lib.sad_oracle_partition.restype = ctypes.c_int
+        lib.sad_oracle_rank_vs.argtypes = [P, P, i32, i32, i32, P, i32, P, P, P, i32]
+        lib.sad_oracle_rank_vs.restype = ctypes.c_int
+        lib.sad_oracle_local_samples.argtypes = [P, P, i32, i32, i32, P]
+        lib.sad_oracle_local_samples.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -162,3 +174,65 @@ def run_set(codes, offsets, p: int, k: int = 3, alphabet: int = 20, threads=None
     offs, mem, piv = partition(hi, lo, p)
     return dict(counts=counts, key_hi=hi, key_lo=lo, rank=rank,
                 bucket_offsets=offs, members=mem, pivot_idx=piv)
+
+
+def rank_vs(counts: np.ndarray, lengths: np.ndarray, ref, k: int = 3, alphabet: int = 20,
+            threads: int | None = None):
+    """Globalised rank (Sec. 3.1.1, Algorithm 2 step 6): every sequence against the
+    reference multiset ``ref`` (input indices). Returns (key_hi, key_lo, rank) with
+    rank = key / (len(ref) 2^64)."""
+    counts = np.ascontiguousarray(counts, dtype=np.int32)
+    lengths = np.ascontiguousarray(lengths, dtype=np.int64)
+    ref = np.ascontiguousarray(ref, dtype=np.int32)
+    n = counts.shape[0]
+    hi = np.zeros(n, np.uint64)
+    lo = np.zeros(n, np.uint64)
+    rank = np.zeros(n, np.float64)
+    _check(_load().sad_oracle_rank_vs(_ptr(counts), _ptr(lengths), n, k, alphabet, _ptr(ref),
+                                      ref.shape[0], _ptr(hi), _ptr(lo), _ptr(rank),
+                                      threads or default_threads()), "rank_vs")
+    return hi, lo, rank
+
+
+def block_bounds(n: int, p: int) -> np.ndarray:
+    """Start of each of the p contiguous blocks, floor(b N / p), and N at the end."""
+    return np.array([b * n // p for b in range(p + 1)], dtype=np.int64)
+
+
+def local_ranks(counts: np.ndarray, lengths: np.ndarray, p: int, k: int = 3,
+                alphabet: int = 20, threads: int | None = None):
+    """Algorithm 2 step 2: each block's sequences ranked against their own block
+    only (Eq. 3 over the block). Returns (key_hi, key_lo) in input order."""
+    n = counts.shape[0]
+    bnd = block_bounds(n, p)
+    hi = np.zeros(n, np.uint64)
+    lo = np.zeros(n, np.uint64)
+    for b in range(p):
+        a, e = int(bnd[b]), int(bnd[b + 1])
+        if e > a:
+            h, l, _ = kmer_rank(counts[a:e], np.asarray(lengths)[a:e], k, alphabet,
+                                threads=threads)
+            hi[a:e], lo[a:e] = h, l
+    return hi, lo
+
+
+def local_samples(key_hi: np.ndarray, key_lo: np.ndarray, p: int, ks: int) -> np.ndarray:
+    """Algorithm 2 steps 3-4: ks regular samples per block of the locally sorted
+    order (positions floor(j w_b / (ks + 1)), j = 1..ks); input indices, block-major."""
+    key_hi = np.ascontiguousarray(key_hi, dtype=np.uint64)
+    key_lo = np.ascontiguousarray(key_lo, dtype=np.uint64)
+    out = np.zeros(p * ks, np.int32)
+    _check(_load().sad_oracle_local_samples(_ptr(key_hi), _ptr(key_lo), key_hi.shape[0], p, ks,
+                                            _ptr(out)), "local_samples")
+    return out
+
+
+def global_rank(counts: np.ndarray, lengths: np.ndarray, p: int, ks: int, k: int = 3,
+                alphabet: int = 20, threads: int | None = None):
+    """Algorithm 2 steps 2-6: local ranks per block, ks samples per block of the
+    locally sorted order, every sequence re-ranked against the ks x p samples.
+    Returns (key_hi, key_lo, rank, samples)."""
+    lh, ll = local_ranks(counts, lengths, p, k, alphabet, threads)
+    samples = local_samples(lh, ll, p, ks)
+    hi, lo, rank = rank_vs(counts, lengths, samples, k, alphabet, threads)
+    return hi, lo, rank, samples

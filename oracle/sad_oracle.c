@@ -94,6 +94,8 @@ typedef struct {
   int64_t eps;
   const int32_t *rows;   /* rows to evaluate */
   int32_t n_rows;
+  const int32_t *ref;    /* reference sequences of the rank (NULL: all n) */
+  int32_t n_ref;
   uint64_t *key_hi, *key_lo;
   double *rank;
   double *rank_fp64;
@@ -102,13 +104,16 @@ typedef struct {
 } rank_job;
 
 /* Eq. 3 for one sequence i: key_i = sum_{j=1..N} floor(S_ij 2^64 / D_ij),
- * D_ij = min(n_i, n_j) - k + 1 (Eq. 1 denominator), j = i included. Also the
- * independent FP64 mean of S_ij / D_ij with Neumaier compensation. */
+ * D_ij = min(n_i, n_j) - k + 1 (Eq. 1 denominator), j = i included. With a
+ * reference list the sum runs over its entries instead (the globalised rank of
+ * Sec. 3.1.1: the k x p samples, Algorithm 2 step 6). Also the independent FP64
+ * mean of S_ij / D_ij with Neumaier compensation. */
 static void rank_row(const rank_job *J, int32_t out, int32_t i) {
   const int32_t *ci = J->counts + (int64_t)i * J->eps;
   u128 key = 0;
   double sum = 0.0, comp = 0.0;
-  for (int32_t j = 0; j < J->n; ++j) {
+  for (int32_t r = 0; r < J->n_ref; ++r) {
+    const int32_t j = J->ref ? J->ref[r] : r;
     const int32_t *cj = J->counts + (int64_t)j * J->eps;
     int64_t s = sad_oracle_shared_count(ci, cj, J->eps);
     int64_t d = J->m[i] < J->m[j] ? J->m[i] : J->m[j];
@@ -125,8 +130,8 @@ static void rank_row(const rank_job *J, int32_t out, int32_t i) {
   volatile double whole = (double)hi;
   volatile double frac = ldexp((double)lo, -64);
   volatile double total = whole + frac;
-  J->rank[out] = total / (double)J->n;
-  if (J->rank_fp64) J->rank_fp64[out] = (sum + comp) / (double)J->n;
+  J->rank[out] = total / (double)J->n_ref;
+  if (J->rank_fp64) J->rank_fp64[out] = (sum + comp) / (double)J->n_ref;
 }
 
 static void *rank_worker(void *arg) {
@@ -156,8 +161,34 @@ int sad_oracle_kmer_rank(const int32_t *counts, const int64_t *lengths, int32_t 
   }
   for (int32_t r = 0; rows && r < n_rows; ++r)
     if (rows[r] < 0 || rows[r] >= n) { free(m); return OR_INVALID; }
-  rank_job J = {counts, m, n, ipow(alphabet, k), rows, n_rows,
+  rank_job J = {counts, m, n, ipow(alphabet, k), rows, n_rows, NULL, n,
                 key_hi, key_lo, rank, rank_fp64, 0, PTHREAD_MUTEX_INITIALIZER};
+  if (threads < 1) threads = 1;
+  if (threads > 1024) threads = 1024;
+  pthread_t tid[1024];
+  for (int32_t t = 0; t < threads; ++t) pthread_create(&tid[t], NULL, rank_worker, &J);
+  for (int32_t t = 0; t < threads; ++t) pthread_join(tid[t], NULL);
+  free(m);
+  return OR_OK;
+}
+
+/* Globalised rank (Sec. 3.1.1, Algorithm 2 step 6): every sequence against the
+ * reference multiset ref[0..n_ref) (input indices; an index listed twice counts
+ * twice): key_i = sum_r floor(S_{i,ref_r} 2^64 / (min(n_i, n_ref_r) - k + 1)),
+ * rank_i = key_i / (n_ref 2^64). */
+int sad_oracle_rank_vs(const int32_t *counts, const int64_t *lengths, int32_t n, int32_t k,
+                       int32_t alphabet, const int32_t *ref, int32_t n_ref, uint64_t *key_hi,
+                       uint64_t *key_lo, double *rank, int32_t threads) {
+  if (n < 0 || k < 1 || alphabet < 1 || n_ref < 1 || !ref) return OR_INVALID;
+  for (int32_t r = 0; r < n_ref; ++r)
+    if (ref[r] < 0 || ref[r] >= n) return OR_INVALID;
+  int64_t *m = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  for (int32_t x = 0; x < n; ++x) {
+    m[x] = lengths[x] - k + 1;
+    if (m[x] < 1) { free(m); return OR_BAD_INPUT; }
+  }
+  rank_job J = {counts, m, n, ipow(alphabet, k), NULL, n, ref, n_ref,
+                key_hi, key_lo, rank, NULL, 0, PTHREAD_MUTEX_INITIALIZER};
   if (threads < 1) threads = 1;
   if (threads > 1024) threads = 1024;
   pthread_t tid[1024];
@@ -258,4 +289,29 @@ int sad_oracle_partition(const uint64_t *key_hi, const uint64_t *key_lo, int32_t
 }
 
 /* Library identity for the loader. */
+/* Algorithm 2 steps 3-4: each of the p contiguous blocks b = [floor(bN/p),
+ * floor((b+1)N/p)) of sequences (w_b of them) is sorted by its local key (ties by
+ * input index), and ks evenly spaced samples are taken at the 0-based positions
+ * floor(j w_b / (ks + 1)), j = 1..ks (the spacing of the regular sampling of
+ * Sec. 3.1.2 with ks + 1 parts). Output: input indices, block-major. Every block
+ * must hold a sequence (N >= p). */
+int sad_oracle_local_samples(const uint64_t *key_hi, const uint64_t *key_lo, int32_t n,
+                             int32_t p, int32_t ks, int32_t *sample_idx) {
+  if (p < 1 || ks < 1 || n < p) return OR_INVALID;
+  item *it = (item *)malloc(sizeof(item) * (size_t)n);
+  for (int32_t x = 0; x < n; ++x) {
+    it[x].hi = key_hi[x];
+    it[x].lo = key_lo[x];
+    it[x].idx = x;
+  }
+  for (int32_t b = 0; b < p; ++b) {
+    const int64_t lo = (int64_t)b * n / p, hi = (int64_t)(b + 1) * n / p, w = hi - lo;
+    qsort(it + lo, (size_t)w, sizeof(item), item_cmp);
+    for (int32_t j = 1; j <= ks; ++j)
+      sample_idx[(int64_t)b * ks + (j - 1)] = it[lo + (int64_t)j * w / (ks + 1)].idx;
+  }
+  free(it);
+  return OR_OK;
+}
+
 const char *sad_oracle_version(void) { return "sad-oracle-1"; }

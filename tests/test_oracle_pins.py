@@ -241,3 +241,98 @@ def test_partition_rejects_bad_p(oracle_mod):
         oracle_mod.partition(hi, lo, 0)
     offs, mem, piv = oracle_mod.partition(hi[:0], lo[:0], 3)
     assert list(offs) == [0, 0, 0, 0] and mem.size == 0
+
+
+# ----------------------------------------- globalised rank, Sec. 3.1.1 ------
+
+def exact_term(sx, sy, lx, ly, k=3):
+    """floor(|multiset intersection| 2^64 / (min(L_x, L_y) - k + 1)), from the strings."""
+    s = sum((sx & sy).values())
+    return (s << 64) // (min(lx, ly) - k + 1)
+
+
+def test_rank_vs_against_exact_floors(oracle_mod):
+    s = datagen.random_small(13, 3, 60, seed=21, alphabet=5)
+    c = oracle_mod.kmer_count(s.codes, s.offsets, 3, 5)
+    ref = np.array([4, 0, 4, 12, 7], np.int32)            # a multiset: 4 counts twice
+    hi, lo, rank = oracle_mod.rank_vs(c, s.lengths, ref, 3, 5)
+    ms = [kmer_multiset(s.seq(x), 3) for x in range(s.n)]
+    for x in range(s.n):
+        want = sum(exact_term(ms[x], ms[r], int(s.lengths[x]), int(s.lengths[r])) for r in ref)
+        assert ((int(hi[x]) << 64) | int(lo[x])) == want
+        assert abs(rank[x] - want / 2.0 ** 64 / len(ref)) <= 1e-12 * max(rank[x], 1e-300)
+
+
+def test_rank_vs_every_sequence_is_the_centralised_key(oracle_mod):
+    s = datagen.random_small(40, 3, 200, seed=22)
+    c = oracle_mod.kmer_count(s.codes, s.offsets)
+    h0, l0, r0 = oracle_mod.kmer_rank(c, s.lengths)
+    h1, l1, r1 = oracle_mod.rank_vs(c, s.lengths, np.arange(s.n)[::-1])
+    np.testing.assert_array_equal(h0, h1)
+    np.testing.assert_array_equal(l0, l1)
+    np.testing.assert_array_equal(r0, r1)
+
+
+def golden_sample_cases():
+    cases, cur = [], None
+    for tok in golden_lines("local_samples.txt"):
+        if tok[0] == "case":
+            cur = dict(name=tok[1], n=int(tok[2]), p=int(tok[3]), ks=int(tok[4]))
+            cases.append(cur)
+        else:
+            cur[tok[0]] = [int(v) for v in tok[1:]]
+    return cases
+
+
+@pytest.mark.parametrize("case", golden_sample_cases(), ids=lambda c: c["name"])
+def test_local_samples_hand_examples(oracle_mod, case):
+    lo = np.array(case["keys"], np.uint64)
+    got = oracle_mod.local_samples(np.zeros_like(lo), lo, case["p"], case["ks"])
+    assert list(got) == case["samples"]
+
+
+def test_local_ranks_see_only_their_block(oracle_mod):
+    s = datagen.random_small(30, 3, 150, seed=23)
+    c = oracle_mod.kmer_count(s.codes, s.offsets)
+    h, l = oracle_mod.local_ranks(c, s.lengths, 3)
+    # blocks [0,10) [10,20) [20,30): shuffling the rows of other blocks changes nothing
+    perm = np.concatenate([np.arange(10), 10 + np.random.default_rng(0).permutation(10),
+                           20 + np.random.default_rng(1).permutation(10)])
+    h2, l2 = oracle_mod.local_ranks(c[perm], s.lengths[perm], 3)
+    np.testing.assert_array_equal(h[:10], h2[:10])
+    np.testing.assert_array_equal(l[:10], l2[:10])
+    # and a block's keys are the centralised keys of the block alone
+    hb, lb, _ = oracle_mod.kmer_rank(c[10:20], s.lengths[10:20])
+    np.testing.assert_array_equal(h[10:20], hb)
+    np.testing.assert_array_equal(l[10:20], lb)
+
+
+def test_global_rank_with_every_sequence_sampled_is_centralised(oracle_mod):
+    s = datagen.random_small(25, 3, 120, seed=24)
+    c = oracle_mod.kmer_count(s.codes, s.offsets)
+    hi, lo, rank, samples = oracle_mod.global_rank(c, s.lengths, 1, s.n)
+    assert sorted(samples.tolist()) == list(range(s.n))     # floor(j N/(N+1)) = 0..N-1
+    h0, l0, r0 = oracle_mod.kmer_rank(c, s.lengths)
+    np.testing.assert_array_equal(hi, h0)
+    np.testing.assert_array_equal(lo, l0)
+
+
+def test_global_rank_against_exact_pipeline(oracle_mod):
+    """Steps 2-6 redone from the strings with Python integers: local keys, local
+    order, regular samples, keys against the samples."""
+    s = datagen.random_small(14, 3, 50, seed=25, alphabet=4)
+    p, ks = 3, 2
+    c = oracle_mod.kmer_count(s.codes, s.offsets, 3, 4)
+    hi, lo, _, samples = oracle_mod.global_rank(c, s.lengths, p, ks, 3, 4)
+    ms = [kmer_multiset(s.seq(x), 3) for x in range(s.n)]
+    L = [int(v) for v in s.lengths]
+    want_samples = []
+    for b in range(p):
+        blk = list(range(b * s.n // p, (b + 1) * s.n // p))
+        key = {x: sum(exact_term(ms[x], ms[y], L[x], L[y]) for y in blk) for x in blk}
+        order = sorted(blk, key=lambda x: (key[x], x))
+        want_samples += [order[j * len(blk) // (ks + 1)] for j in range(1, ks + 1)]
+    assert list(samples) == want_samples
+    for x in range(s.n):
+        want = sum(exact_term(ms[x], ms[r], L[x], L[r]) for r in want_samples)
+        assert ((int(hi[x]) << 64) | int(lo[x])) == want
