@@ -34,7 +34,7 @@
 extern "C" {
 #endif
 
-#define SAD_ABI_VERSION 2
+#define SAD_ABI_VERSION 3
 
 typedef enum sad_status {
   SAD_OK = 0,
@@ -112,7 +112,7 @@ int kmer_count(const uint8_t *d_codes, const int64_t *d_offsets, int32_t n_seq,
  *   list_entries (sequence, word) entries with a count above depth.
  *   residual_pairs  pair contributions the residual step adds.
  *   k_cap, list_cap, block_cap  capacities kmer_rank lays the workspace out
- *                with (plane columns, residual entries, residual 128 x 256
+ *                with (plane columns, residual entries, residual 128 x 128
  *                tiles); kmer_rank_plan sets them to what the data needs.
  *   ws_bytes     workspace bytes kmer_rank needs with this plan.
  */
@@ -298,6 +298,55 @@ int sad_batch_partition(const uint64_t *d_key_hi, const uint64_t *d_key_lo, cons
  */
 int sad_status_read(void *d_ws, int32_t clear, void *stream);
 
+/*
+ * Globalised k-mer rank (Sec. 3.1.1, Algorithm 2 steps 2-6). Each of p
+ * "processors" holds the contiguous block [floor(bN/p), floor((b+1)N/p)) of the
+ * sequences (input order). Step 2 ranks every block against itself: use the
+ * batched rank (sad_batch_plan_make / sad_batch_rank) with the blocks as sets.
+ * Steps 3-5 are sad_local_samples, step 6 is kmer_rank_vs with the samples as
+ * the reference set; partition on its keys then gives the buckets (steps 7-11).
+ *
+ * sad_local_samples - sorts every block by its key (ties by input index) and
+ *   takes ks evenly spaced samples of it, at the 0-based positions
+ *   floor(j w_b / (ks + 1)), j = 1..ks, of the sorted block of w_b sequences
+ *   (the spacing of the regular sampling of Sec. 3.1.2; a position may repeat
+ *   when w_b <= ks).
+ *   d_key_hi, d_key_lo  uint64 [n_seq] local keys (input order).
+ *   p          blocks, 1 <= p <= n_seq; ks >= 1, ks * p < 2^31.
+ *   d_sample_idx  int32 [p * ks] output: input indices, block-major.
+ *   d_ws       workspace of sad_local_samples_workspace_bytes(n_seq, p) bytes.
+ *   Asynchronous on `stream`; argument errors return SAD_ERR_INVALID_ARGUMENT.
+ */
+size_t sad_local_samples_workspace_bytes(int32_t n_seq, int32_t p);
+int sad_local_samples(const uint64_t *d_key_hi, const uint64_t *d_key_lo, int32_t n_seq,
+                      int32_t p, int32_t ks, int32_t *d_sample_idx, void *d_ws,
+                      size_t ws_bytes, void *stream);
+
+/*
+ * kmer_rank_vs - the k-mer rank of every sequence against a reference multiset R
+ * of sequences of the same set (Algorithm 2 step 6):
+ *     key_i = sum_{r in R} floor(S_ir * 2^64 / D_ir),   D_ir = min(L_i, L_r) - k + 1,
+ *     rank_i = (key_hi + key_lo * 2^-64) / |R|,
+ * an index listed twice in R counting twice. With R = every sequence once this is
+ * the kmer_rank key. Runs the rank preparation at full plane depth, gathers the
+ * reference rows' planes and runs the plane GEMM over (all rows) x (R).
+ *   d_counts, d_lengths, d_word_max   as for kmer_rank.
+ *   d_ref      int32 [n_ref] input indices of R (0 <= d_ref[r] < n_seq, checked on
+ *              the device: SAD_ERR_INVALID_ARGUMENT).
+ *   plan       (required) a plan from kmer_rank_plan with depth 0 for these
+ *              counts (it fixes the plane capacity k_cap).
+ *   d_ws       workspace of kmer_rank_vs_workspace_bytes(plan, n_seq, k,
+ *              alphabet, n_ref) bytes.
+ *   d_key_hi, d_key_lo  uint64 [n_seq]; d_rank (nullable) float64 [n_seq].
+ */
+size_t kmer_rank_vs_workspace_bytes(const sad_rank_plan *plan, int32_t n_seq, int32_t k,
+                                    int32_t alphabet, int32_t n_ref);
+int kmer_rank_vs(const int32_t *d_counts, const int32_t *d_lengths, const int32_t *d_word_max,
+                 int32_t n_seq, int32_t k, int32_t alphabet, const int32_t *d_ref,
+                 int32_t n_ref, const sad_rank_plan *plan, uint64_t *d_key_hi,
+                 uint64_t *d_key_lo, double *d_rank, void *d_ws, size_t ws_bytes,
+                 void *stream);
+
 /* Number of kernels this library has launched in this process. */
 uint64_t sad_launch_count(void);
 
@@ -305,7 +354,7 @@ uint64_t sad_launch_count(void);
  * Diagnostics.
  * sad_rank_info - SYNCHRONOUS: after kmer_rank on `stream`, copies the plan the
  *   device chose into info[0..8]: {status, K_eff, K_pad, t_max, tiles,
- *   executed K chunks (sum over tiles of K extent / 128), planes kept per word,
+ *   executed K chunks (sum over tiles of K extent / 256), planes kept per word,
  *   residual pair contributions, residual tiles}.
  * sad_profile - enable != 0 starts recording a CUDA event pair around every
  *   launch of the plane GEMM kernel (on its own stream); 0 stops.

@@ -293,6 +293,46 @@ int kmer_rank(const int32_t *d_counts, const int32_t *d_lengths, const int32_t *
                        static_cast<cudaStream_t>(stream));
 }
 
+size_t sad_local_samples_workspace_bytes(int32_t n_seq, int32_t p) {
+  if (n_seq < 1 || p < 1 || p > n_seq) return 0;
+  return local_samples_ws_bytes(n_seq, p);
+}
+
+int sad_local_samples(const uint64_t *d_key_hi, const uint64_t *d_key_lo, int32_t n_seq,
+                      int32_t p, int32_t ks, int32_t *d_sample_idx, void *d_ws,
+                      size_t ws_bytes, void *stream) {
+  if (n_seq < 1 || p < 1 || p > n_seq || ks < 1 || (int64_t)ks * p > 0x7FFFFFFF)
+    return SAD_ERR_INVALID_ARGUMENT;
+  if (!d_key_hi || !d_key_lo || !d_sample_idx || !d_ws || !aligned(d_ws, 256))
+    return SAD_ERR_INVALID_ARGUMENT;
+  return local_samples_launch(d_key_hi, d_key_lo, n_seq, p, ks, d_sample_idx, d_ws, ws_bytes,
+                              static_cast<cudaStream_t>(stream));
+}
+
+size_t kmer_rank_vs_workspace_bytes(const sad_rank_plan *plan, int32_t n_seq, int32_t k,
+                                    int32_t alphabet, int32_t n_ref) {
+  const int64_t eps = eps_of(k, alphabet);
+  if (eps < 0 || !plan || n_seq < 1 || n_ref < 1 || plan->k_cap < kKCols) return 0;
+  return rank_vs_ws_bytes(n_seq, eps, plan->k_cap, n_ref);
+}
+
+int kmer_rank_vs(const int32_t *d_counts, const int32_t *d_lengths, const int32_t *d_word_max,
+                 int32_t n_seq, int32_t k, int32_t alphabet, const int32_t *d_ref,
+                 int32_t n_ref, const sad_rank_plan *plan, uint64_t *d_key_hi,
+                 uint64_t *d_key_lo, double *d_rank, void *d_ws, size_t ws_bytes,
+                 void *stream) {
+  const int64_t eps = eps_of(k, alphabet);
+  if (eps < 0) return SAD_ERR_UNSUPPORTED;
+  if (n_seq < 1 || n_ref < 1 || !plan || !d_counts || !d_lengths || !d_ref || !d_key_hi ||
+      !d_key_lo || !d_ws || !aligned(d_ws, 256))
+    return SAD_ERR_INVALID_ARGUMENT;
+  if (plan->depth != 0 || plan->k_cap < kKCols || plan->k_cap % kKCols != 0)
+    return SAD_ERR_INVALID_ARGUMENT;
+  return rank_vs_launch(d_counts, d_lengths, d_word_max, n_seq, k, eps, d_ref, n_ref,
+                        plan->k_cap, d_key_hi, d_key_lo, d_rank, d_ws, ws_bytes,
+                        static_cast<cudaStream_t>(stream));
+}
+
 int sad_batch_plan_make(const int32_t *d_counts, const int32_t *h_n, const int32_t *h_p,
                         const int32_t *d_n, int32_t n_sets, int32_t k, int32_t alphabet,
                         sad_batch_plan *plan, void *d_ws, size_t ws_bytes, void *stream) {

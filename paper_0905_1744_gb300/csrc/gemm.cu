@@ -109,9 +109,26 @@ __device__ __forceinline__ void set_abort(GemmSmem &S, WsHeader *hdr) {
   record_error(hdr, SAD_ERR_TIMEOUT, (int)blockIdx.x);
 }
 
+// Tile t of a launch: (row block I, column block J, K chunks). Square mode: the
+// upper-triangle list of the rank. Rectangular mode (every stored row against the
+// reference rows, RectArgs): all R x C blocks, column block major.
+__device__ __forceinline__ void tile_at(const RankPtrs &P, const RectArgs &X, int32_t rect_nk,
+                                        int32_t t, int32_t &I, int32_t &J, int32_t &nk) {
+  if (X.rec_ref) {
+    I = t % X.row_blocks;
+    J = t / X.row_blocks;
+    nk = rect_nk;
+  } else {
+    const int2 tl = P.tiles[t];
+    I = tl.x & 0xFFFF;
+    J = tl.x >> 16;
+    nk = tl.y;
+  }
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
     plane_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
-                      const __grid_constant__ CUtensorMap tmB, RankPtrs P) {
+                      const __grid_constant__ CUtensorMap tmB, RankPtrs P, RectArgs X) {
   extern __shared__ uint8_t smem_raw[];
   GemmSmem &S = *reinterpret_cast<GemmSmem *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -157,7 +174,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const int32_t n_tiles = skip ? 0 : P.hdr->n_tiles;
+  const bool rect = X.rec_ref != nullptr;
+  const int32_t n_tiles = skip ? 0 : (rect ? X.n_tiles : P.hdr->n_tiles);
+  // rectangular mode: every tile runs all K_pad columns the rank preparation wrote
+  const int32_t rect_nk = (rect && !skip) ? max(1, P.hdr->k_pad / kKCols) : 0;
   // counts above the plane depth come in as dense per-tile residual blocks
   const bool residual =
       !skip && P.depth_cap >= 1 && P.block_cap > 0 && P.hdr->depth < P.hdr->t_max;
@@ -168,8 +188,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t phase = 0, used = 0, par = 0;
     bool aborted = false;
     for (int32_t t = blockIdx.x; t < n_tiles && !aborted; t += gridDim.x) {
-      const int2 tl = P.tiles[t];
-      const int32_t I = tl.x & 0xFFFF, J = tl.x >> 16, nk = tl.y;
+      int32_t I, J, nk;
+      tile_at(P, X, rect_nk, t, I, J, nk);
       for (int32_t kc = 0; kc < nk; ++kc) {
         if (!mbar_wait_bounded(&S.empty[stage], phase ^ 1u, abort_flag, kWaitBudgetNs)) {
           set_abort(S, P.hdr);
@@ -202,7 +222,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     bool aborted = false;
     int32_t lt = 0;
     for (int32_t t = blockIdx.x; t < n_tiles && !aborted; t += gridDim.x, ++lt) {
-      const int32_t nk = P.tiles[t].y;
+      int32_t I, J, nk;
+      tile_at(P, X, rect_nk, t, I, J, nk);
       const uint32_t acc = lt & 1, aph = (lt >> 1) & 1;
       if (!mbar_wait_bounded(&S.tempty[acc], aph ^ 1u, abort_flag, kWaitBudgetNs)) {
         set_abort(S, P.hdr);
@@ -247,13 +268,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t etid = threadIdx.x - 128;
     int32_t lt = 0;
     for (int32_t t = blockIdx.x; t < n_tiles; t += gridDim.x, ++lt) {
-      const int2 tl = P.tiles[t];
-      const int32_t I = tl.x & 0xFFFF, J = tl.x >> 16;
+      int32_t I, J, nk;
+      tile_at(P, X, rect_nk, t, I, J, nk);
       const int buf = lt & 1;
       for (uint32_t c = etid; c < (uint32_t)kColBlock; c += kEpiThreads) {
         const int64_t jpos = (int64_t)J * kColBlock + c;
-        S.colrec[buf][c] = P.rec[jpos];
-        S.colorig[buf][c] = P.perm[jpos];
+        S.colrec[buf][c] = rect ? X.rec_ref[jpos] : P.rec[jpos];
+        S.colorig[buf][c] = rect ? 0 : P.perm[jpos];
       }
       const int64_t row_pos = (int64_t)I * kRowBlock + q * 32 + lane;
       const int32_t row_orig = P.perm[row_pos];
@@ -277,6 +298,40 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (named_bar_sync_or(1, kEpiThreads, *abort_flag != 0)) break;
       tc_fence_after();
       uint32_t R0 = 0, R1 = 0, R2 = 0;
+      if (rect) {
+        // every pair counts for the row only; D = min(m_i, m_r): the record of the
+        // shorter of the two
+        const uint4 rrec = P.rec[row_pos];
+        const uint32_t dr = rrec.w & 0xFFFFu;
+#pragma unroll 1
+        for (int sc = 0; sc < kHalfCols / 16; ++sc) {
+          const int c0 = (int)half * kHalfCols + sc * 16;
+          uint32_t v[16];
+          tmem_ld_32x32b_x16(tmem + ((q * 32u) << 16) + acc * (uint32_t)kColBlock + (uint32_t)c0,
+                             v);
+          tmem_ld_wait();
+#pragma unroll
+          for (int cc = 0; cc < 16; ++cc) {
+            const uint4 crec = S.colrec[buf][c0 + cc];
+            const uint4 rec = dr <= (crec.w & 0xFFFFu) ? rrec : crec;
+            const uint32_t s = __float2uint_rn(__uint_as_float(v[cc]));
+            const uint32_t d = rec.w & 0xFFFFu;
+            const uint32_t sh1 = (rec.w >> 16) & 0xFFu, sh2 = rec.w >> 24;
+            const uint32_t r = 0u - rec.x * d;
+            const uint32_t xq = s * r;
+            const uint32_t t1 = __umulhi(rec.z, xq);
+            const uint32_t qv = (t1 + ((xq - t1) >> sh1)) >> sh2;
+            const uint64_t Q = ((uint64_t)rec.y << 32) | rec.x;
+            const uint64_t lo = (uint64_t)s * Q;
+            const uint64_t lo2 = lo + qv;
+            const uint32_t hi = lo2 < lo ? 1u : 0u;
+            const uint32_t wa = (uint32_t)lo2, wb = (uint32_t)(lo2 >> 32);
+            R0 += wa & 0xFFFFFFu;
+            R1 += (wa >> 24) | ((wb & 0xFFFFu) << 8);
+            R2 += (wb >> 16) | (hi << 16);
+          }
+        }
+      } else {
 #pragma unroll 1
       for (int sc = 0; sc < kHalfCols / 16; ++sc) {
         const int c0 = (int)half * kHalfCols + sc * 16;
@@ -338,6 +393,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       }
+      }
       tc_fence_before();
       mbar_arrive(&S.tempty[acc]);
       if (row_orig >= 0) {
@@ -357,7 +413,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+}  // namespace
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
     void *p = nullptr;
@@ -384,6 +442,17 @@ int make_plane_map(CUtensorMap *map, uint8_t *planes, int64_t n_pad, int64_t k_c
   return r == CUDA_SUCCESS ? SAD_OK : SAD_ERR_CUDA;
 }
 
+namespace {
+int gemm_attr() {
+  static bool attr_set = false;
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(plane_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kGemmSmemBytes) != cudaSuccess)
+      return SAD_ERR_CUDA;
+    attr_set = true;
+  }
+  return SAD_OK;
+}
 }  // namespace
 
 int rank_gemm_launch(const RankPtrs &P, cudaStream_t st) {
@@ -394,18 +463,33 @@ int rank_gemm_launch(const RankPtrs &P, cudaStream_t st) {
   if (rc) return rc;
   rc = make_plane_map(&mB, P.planes, P.n_pad, P.k_cap, kColBlock);
   if (rc) return rc;
-  static bool attr_set = false;
-  if (!attr_set) {
-    if (cudaFuncSetAttribute(plane_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kGemmSmemBytes) != cudaSuccess)
-      return SAD_ERR_CUDA;
-    attr_set = true;
-  }
+  if ((rc = gemm_attr())) return rc;
   const int64_t grid = tiles < num_sms() ? tiles : num_sms();
   prof_begin(st);
-  plane_gemm_kernel<<<(unsigned)grid, kThreads, kGemmSmemBytes, st>>>(mA, mB, P);
+  plane_gemm_kernel<<<(unsigned)grid, kThreads, kGemmSmemBytes, st>>>(mA, mB, P, RectArgs{});
   SAD_LAUNCH_CHECK();
   prof_end(st);
+  return SAD_OK;
+}
+
+int rank_rect_gemm_launch(const RankPtrs &P, uint8_t *ref_planes, const uint4 *rec_ref,
+                          int64_t ref_rows, cudaStream_t st) {
+  RectArgs X;
+  X.rec_ref = rec_ref;
+  X.row_blocks = (int32_t)(P.n_pad / kRowBlock);
+  const int64_t tiles = (int64_t)X.row_blocks * (ref_rows / kColBlock);
+  if (tiles == 0) return SAD_OK;
+  if (tiles > 0x7FFFFFFF) return SAD_ERR_UNSUPPORTED;
+  X.n_tiles = (int32_t)tiles;
+  CUtensorMap mA, mB;
+  int rc = make_plane_map(&mA, P.planes, P.n_pad, P.k_cap, kRowBlock);
+  if (rc) return rc;
+  rc = make_plane_map(&mB, ref_planes, ref_rows, P.k_cap, kColBlock);
+  if (rc) return rc;
+  if ((rc = gemm_attr())) return rc;
+  const int64_t grid = tiles < num_sms() ? tiles : num_sms();
+  plane_gemm_kernel<<<(unsigned)grid, kThreads, kGemmSmemBytes, st>>>(mA, mB, P, X);
+  SAD_LAUNCH_CHECK();
   return SAD_OK;
 }
 

@@ -48,6 +48,30 @@ int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *le
                      const int32_t *d_n, const int32_t *word_max, int32_t k, int32_t eps,
                      int plan_only, cudaStream_t st);
 int rank_gemm_launch(const RankPtrs &P, cudaStream_t st);
+
+// Rectangular mode of the plane GEMM: every stored row of P against ref_rows
+// reference rows (their planes in ref_planes, same K_cap, division records in
+// rec_ref), the row keys only, D = min(m_i, m_r) per pair.
+struct RectArgs {
+  const uint4 *rec_ref = nullptr;  // nullptr: square mode
+  int32_t row_blocks = 0, n_tiles = 0;
+};
+int rank_rect_gemm_launch(const RankPtrs &P, uint8_t *ref_planes, const uint4 *rec_ref,
+                          int64_t ref_rows, cudaStream_t st);
+// Globalised rank (grank.cu).
+size_t local_samples_ws_bytes(int64_t n, int64_t p);
+int local_samples_launch(const uint64_t *key_hi, const uint64_t *key_lo, int32_t n, int32_t p,
+                         int32_t ks, int32_t *sample_idx, void *ws, size_t ws_bytes,
+                         cudaStream_t st);
+size_t rank_vs_ws_bytes(int64_t n, int64_t eps, int64_t k_cap, int64_t n_ref);
+int rank_vs_launch(const int32_t *counts, const int32_t *lengths, const int32_t *word_max,
+                   int32_t n, int32_t k, int64_t eps, const int32_t *ref, int32_t n_ref,
+                   int64_t k_cap, uint64_t *key_hi, uint64_t *key_lo, double *rank, void *ws,
+                   size_t ws_bytes, cudaStream_t st);
+
+// TMA map of a plane matrix (rows x K_cap / 2 bytes, 128-byte swizzle, boxes of
+// 128 bytes x box_rows rows).
+int make_plane_map(CUtensorMap *map, uint8_t *planes, int64_t rows, int64_t k_cap, int box_rows);
 int rank_finalize_launch(const RankPtrs &P, uint64_t *key_hi, uint64_t *key_lo, double *rank,
                          cudaStream_t st);
 int64_t host_tile_count(int32_t n);

@@ -96,6 +96,15 @@ def _load():
         lib.partition_noalloc.restype = ctypes.c_int
         lib.sad_rank_info.argtypes = [P, ctypes.POINTER(i64), P]
         lib.sad_rank_info.restype = ctypes.c_int
+        lib.sad_local_samples_workspace_bytes.argtypes = [i32, i32]
+        lib.sad_local_samples_workspace_bytes.restype = sz
+        lib.sad_local_samples.argtypes = [P, P, i32, i32, i32, P, P, sz, P]
+        lib.sad_local_samples.restype = ctypes.c_int
+        lib.kmer_rank_vs_workspace_bytes.argtypes = [ctypes.POINTER(RankPlan), i32, i32, i32, i32]
+        lib.kmer_rank_vs_workspace_bytes.restype = sz
+        lib.kmer_rank_vs.argtypes = [P, P, P, i32, i32, i32, P, i32, ctypes.POINTER(RankPlan), P,
+                                     P, P, P, sz, P]
+        lib.kmer_rank_vs.restype = ctypes.c_int
         lib.sad_profile.argtypes = [i32]
         lib.sad_profile.restype = ctypes.c_int
         lib.sad_profile_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
@@ -301,6 +310,124 @@ def partition_noalloc(key_hi: torch.Tensor, key_lo: torch.Tensor, p: int, stream
                                      _ptr(piv) if p > 1 else None, _stream(stream)),
            "partition_noalloc")
     return offs, mem[:n], piv[:max(p - 1, 0)]
+
+
+def block_bounds(n: int, p: int):
+    """Starts of the p contiguous blocks, floor(b N / p), and N (Algorithm 2 step 1)."""
+    return [b * n // p for b in range(p + 1)]
+
+
+def local_ranks(counts: torch.Tensor, lengths: torch.Tensor, p: int, k: int = 3,
+                alphabet: int = 20, depth: int = 0, word_max: torch.Tensor | None = None,
+                ws: Workspace | None = None, stream=None):
+    """Algorithm 2 step 2: every block of sequences ranked against its own block,
+    as one block-diagonal batched rank (blocks as sets). Synchronous (plans).
+    Returns (key_hi, key_lo, rank) in input order; rank = key / (w_b 2^64)."""
+    import numpy as np
+    n = counts.shape[0]
+    dev = counts.device
+    if not 1 <= p <= n:
+        raise ValueError("need 1 <= p <= N")
+    h_n = np.ascontiguousarray(np.diff(block_bounds(n, p)), dtype=np.int32)
+    h_p = np.ones(p, dtype=np.int32)
+    d_n = torch.from_numpy(h_n).to(dev)
+    ws = ws or Workspace(dev)
+    ws.ensure(256)
+    plan = BatchPlan()
+    plan.rank.depth = int(depth)
+    args = (_ptr(counts), h_n.ctypes.data_as(ctypes.c_void_p), h_p.ctypes.data_as(ctypes.c_void_p),
+            _ptr(d_n), p, k, alphabet, ctypes.byref(plan))
+    rc = _load().sad_batch_plan_make(*args, _ptr(ws.buf), ws.nbytes, _stream(stream))
+    if rc == ERR_WORKSPACE:
+        ws.ensure(plan.rank.ws_bytes)
+        plan.rank.depth = int(depth)
+        rc = _load().sad_batch_plan_make(*args, _ptr(ws.buf), ws.nbytes, _stream(stream))
+    _check(rc, "sad_batch_plan_make (local ranks)")
+    ws.ensure(plan.rank.ws_bytes)
+    hi = torch.empty(n, dtype=torch.uint64, device=dev)
+    lo = torch.empty(n, dtype=torch.uint64, device=dev)
+    rank = torch.empty(n, dtype=torch.float64, device=dev)
+    lengths = lengths.to(device=dev, dtype=torch.int32).contiguous()
+    _check(_load().sad_batch_rank(_ptr(counts), _ptr(lengths), _ptr(word_max), _ptr(d_n), k,
+                                  alphabet, ctypes.byref(plan), _ptr(hi), _ptr(lo), _ptr(rank),
+                                  _ptr(ws.buf), ws.nbytes, _stream(stream)), "sad_batch_rank")
+    ws.check("local ranks", stream)
+    return hi, lo, rank
+
+
+def local_samples(key_hi: torch.Tensor, key_lo: torch.Tensor, p: int, ks: int,
+                  ws: Workspace | None = None, stream=None, out=None, check: bool = True):
+    """Algorithm 2 steps 3-5: ks evenly spaced samples of every block's sorted
+    order; int32 [p * ks] input indices, block-major."""
+    n = key_hi.numel()
+    dev = key_hi.device
+    ws = ws or Workspace(dev)
+    ws.ensure(int(_load().sad_local_samples_workspace_bytes(n, p)))
+    out = out if out is not None else torch.empty(p * ks, dtype=torch.int32, device=dev)
+    _check(_load().sad_local_samples(_ptr(key_hi), _ptr(key_lo), n, p, ks, _ptr(out),
+                                     _ptr(ws.buf), ws.nbytes, _stream(stream)),
+           "sad_local_samples")
+    if check:
+        ws.check("sad_local_samples", stream)
+    return out
+
+
+def kmer_rank_vs(counts: torch.Tensor, lengths: torch.Tensor, ref: torch.Tensor, k: int = 3,
+                 alphabet: int = 20, plan: RankPlan | None = None,
+                 word_max: torch.Tensor | None = None, ws: Workspace | None = None,
+                 stream=None, check: bool = True):
+    """Algorithm 2 step 6: every sequence ranked against the reference multiset
+    ``ref`` (input indices). ``plan``: a depth-0 RankPlan (made here if None,
+    synchronous). Returns (key_hi, key_lo, rank), rank = key / (len(ref) 2^64)."""
+    n = counts.shape[0]
+    dev = counts.device
+    ws = ws or Workspace(dev)
+    if plan is None:
+        plan = kmer_rank_plan(counts, k, alphabet, 0, ws, stream)
+    ref = ref.to(device=dev, dtype=torch.int32).contiguous()
+    n_ref = ref.numel()
+    ws.ensure(int(_load().kmer_rank_vs_workspace_bytes(ctypes.byref(plan), n, k, alphabet,
+                                                       n_ref)))
+    hi = torch.empty(n, dtype=torch.uint64, device=dev)
+    lo = torch.empty(n, dtype=torch.uint64, device=dev)
+    rank = torch.empty(n, dtype=torch.float64, device=dev)
+    lengths = lengths.to(device=dev, dtype=torch.int32).contiguous()
+    _check(_load().kmer_rank_vs(_ptr(counts), _ptr(lengths), _ptr(word_max), n, k, alphabet,
+                                _ptr(ref), n_ref, ctypes.byref(plan), _ptr(hi), _ptr(lo),
+                                _ptr(rank), _ptr(ws.buf), ws.nbytes, _stream(stream)),
+           "kmer_rank_vs")
+    if check:
+        ws.check("kmer_rank_vs", stream)
+    return hi, lo, rank
+
+
+def global_rank(counts: torch.Tensor, lengths: torch.Tensor, p: int, ks: int, k: int = 3,
+                alphabet: int = 20, word_max: torch.Tensor | None = None, local_depth: int = 0,
+                stream=None):
+    """Algorithm 2 steps 2-6 (Sec. 3.1.1): local ranks per block, ks samples per
+    block, every sequence re-ranked against the ks x p samples.
+    Returns (key_hi, key_lo, rank, samples)."""
+    lh, ll, _ = local_ranks(counts, lengths, p, k, alphabet, local_depth, word_max,
+                            stream=stream)
+    samples = local_samples(lh, ll, p, ks, stream=stream)
+    hi, lo, rank = kmer_rank_vs(counts, lengths, samples, k, alphabet, word_max=word_max,
+                                stream=stream)
+    return hi, lo, rank, samples
+
+
+def global_partition_set(codes: torch.Tensor, offsets: torch.Tensor, p: int, ks: int,
+                         k: int = 3, alphabet: int = 20, stream=None):
+    """count -> globalised rank -> partition (Algorithm 2 steps 1-11 without the
+    alignment) of one sequence set on the device."""
+    ws = Workspace(codes.device)
+    word_max = torch.empty(alphabet ** k, dtype=torch.int32, device=codes.device)
+    counts = kmer_count(codes, offsets, k, alphabet, ws=ws, stream=stream, word_max=word_max)
+    lengths = (offsets[1:] - offsets[:-1]).to(torch.int32)
+    hi, lo, rank, samples = global_rank(counts, lengths, p, ks, k, alphabet, word_max,
+                                        stream=stream)
+    offs, mem, piv = partition(hi, lo, p, ws=ws, stream=stream)
+    return dict(counts=counts, key_hi=hi, key_lo=lo, rank=rank, samples=samples,
+                bucket_offsets=offs, members=mem, pivot_idx=piv)
 
 
 class Batch:
