@@ -14,6 +14,9 @@ Prints one JSON line. Extra objects:
   e2e           the same metric through the public API with host buffers
                 (H2D of codes + offsets and D2H of the buckets and keys timed)
   clocks        SM clocks and throttle reasons sampled during the timed region
+  globalised    the globalised rank of Sec. 3.1.1 on the same set (local ranks,
+                p - 1 samples per block, rank against the samples), timed, and
+                how its buckets compare with the centralised ones
 
 --impl reference times the CPU oracle on the same workload instead (one bounded
 sample per step). Under torchrun each rank runs an independent replica of the
@@ -61,6 +64,8 @@ def parse():
     ap.add_argument("--depth", type=int, default=None,
                     help="threshold-plane depth (default: the autotuner's choice)")
     ap.add_argument("--no-batching", action="store_true")
+    ap.add_argument("--no-global", action="store_true",
+                    help="skip the globalised-rank leg (Sec. 3.1.1)")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-warmup", type=int, default=200)
@@ -321,6 +326,53 @@ def run_batching(args, dev):
     }
 
 
+def run_global(args, dev, counts, lengths, word_max, keys, p, reps: int = 10):
+    """The globalised rank of Sec. 3.1.1 (Algorithm 2 steps 2-6) on the same set:
+    local ranks of the p blocks, p - 1 regular samples per block, every sequence
+    against the p (p - 1) samples; timed per run with CUDA events (L2 flushed
+    between runs). Also how the buckets of the globalised partition compare with
+    the centralised ones of the main step."""
+    import torch
+
+    from paper_0905_1744_gb300 import sad
+    ks = max(p - 1, 1)
+    g = sad.GlobalRank(counts, lengths, p, ks, word_max=word_max)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(3):
+        g.run()
+    g.check()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(reps)]
+    for e0, e1 in evs:
+        flush.zero_()
+        e0.record(stream)
+        g.run()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    g.check()
+    ms = statistics.median([a.elapsed_time(b) for a, b in evs])
+    n = counts.shape[0]
+    offs_c, mem_c, _ = sad.partition(keys[0], keys[1], p)
+    offs_g, mem_g, _ = sad.partition(g.key_hi, g.key_lo, p)
+    bucket_c = torch.empty(n, dtype=torch.int64, device=dev)
+    bucket_g = torch.empty(n, dtype=torch.int64, device=dev)
+    for b in range(p):
+        bucket_c[mem_c[int(offs_c[b]):int(offs_c[b + 1])].long()] = b
+        bucket_g[mem_g[int(offs_g[b]):int(offs_g[b + 1])].long()] = b
+    rc, rg = keys[2], g.rank
+    return {"workload": f"same set, p = {p} blocks, {ks} samples per block "
+                        f"({p * ks} references)",
+            "ms_per_run": ms, "pairs": g.pairs(), "pairs_per_s": g.pairs() / (ms / 1e3),
+            "rank_views": {"centralised": {"min": float(rc.min()), "max": float(rc.max()),
+                                           "mean": float(rc.mean())},
+                           "globalised": {"min": float(rg.min()), "max": float(rg.max()),
+                                          "mean": float(rg.mean())},
+                           "pearson": float(torch.corrcoef(torch.stack([rc, rg]))[0, 1])},
+            "same_bucket_fraction": float((bucket_c == bucket_g).double().mean()),
+            "max_bucket": int((offs_g[1:] - offs_g[:-1]).max())}
+
+
 def run_serving(args, dev, depth):
     """Poisson arrivals of sets (N log-uniform 100-20000, p = 16) served with
     continuous batching under a 150 GB HBM budget, and the same arrivals served
@@ -513,6 +565,9 @@ def run_sad(args):
                "d2h_bytes_per_step": int(4 * n + 4 * (p + 1) + 16 * n),
                "ms_per_step": 1e3 * t_e2e}
 
+    globalised = None
+    if not args.no_global and world == 1:
+        globalised = run_global(args, dev, counts, lengths, word_max, keys, p)
     batching = None
     if not args.no_batching:
         batching = run_batching(args, dev)
@@ -545,6 +600,7 @@ def run_sad(args):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clocks,
+            "globalised": globalised,
             "batching": batching,
             "serving": serving,
             "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms),

@@ -23,6 +23,11 @@ Parity status of each function (what pins it, in ``tests/test_oracle_pins.py``):
                every sequence gives the centralised key.
   local_samples  hand-derived positions (keys = index and reversed keys), block
                bounds floor(bN/p).
+  ln_q         within 2^-30 of ln x (decimal arithmetic) over a sweep of x,
+               including powers of two and values near them.
+  rank_dist    closed forms (F = 0 gives ln b, F = 1 gives -ln(1 + 1/b)), exact
+               sums from string multisets, the FP64 mean within the
+               quantisation bound.
   global_rank  p = 1 with ks = N samples every sequence once (positions
                floor(j N / (N + 1)), j = 1..N, are 0..N-1), so the globalised key
                equals the centralised one.
@@ -77,6 +82,10 @@ def _load():
         lib.sad_oracle_rank_vs.restype = ctypes.c_int
         lib.sad_oracle_local_samples.argtypes = [P, P, i32, i32, i32, P]
         lib.sad_oracle_local_samples.restype = ctypes.c_int
+        lib.sad_oracle_ln_q.argtypes = [u64]
+        lib.sad_oracle_ln_q.restype = ctypes.c_int64
+        lib.sad_oracle_rank_dist.argtypes = [P, P, i32, i32, i32, i32, P, P, P, i32]
+        lib.sad_oracle_rank_dist.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -236,3 +245,33 @@ def global_rank(counts: np.ndarray, lengths: np.ndarray, p: int, ks: int, k: int
     samples = local_samples(lh, ll, p, ks)
     hi, lo, rank = rank_vs(counts, lengths, samples, k, alphabet, threads)
     return hi, lo, rank, samples
+
+
+def ln_q(x: int) -> int:
+    """ln(x) * 2^32 as the fixed-point value of the distance-form rank (x >= 1)."""
+    return int(_load().sad_oracle_ln_q(int(x)))
+
+
+def rank_dist(counts: np.ndarray, lengths: np.ndarray, delta_den: int, k: int = 3,
+              alphabet: int = 20, threads: int | None = None, with_fp64: bool = False):
+    """Eq. 2 / Eq. 3 literally, with Delta = 1 / delta_den: key_i = sum_j
+    (ln_q(b D) - ln_q(D + b S)) (ln times 2^32), rank_i = key_i 2^-32 / N.
+    Returns (key int64, rank float64[, rank_fp64])."""
+    counts = np.ascontiguousarray(counts, dtype=np.int32)
+    lengths = np.ascontiguousarray(lengths, dtype=np.int64)
+    n = counts.shape[0]
+    key = np.zeros(n, np.int64)
+    rank = np.zeros(n, np.float64)
+    fp = np.zeros(n, np.float64) if with_fp64 else None
+    _check(_load().sad_oracle_rank_dist(_ptr(counts), _ptr(lengths), n, k, alphabet, delta_den,
+                                        _ptr(key), _ptr(rank),
+                                        _ptr(fp) if fp is not None else None,
+                                        threads or default_threads()), "rank_dist")
+    return (key, rank, fp) if with_fp64 else (key, rank)
+
+
+def dist_sort_key(key: np.ndarray):
+    """The signed distance keys as unsigned (hi, lo) keys with the same order
+    (offset binary), for the partition."""
+    lo = (np.asarray(key, np.int64).view(np.uint64) ^ np.uint64(1 << 63))
+    return np.zeros_like(lo), lo

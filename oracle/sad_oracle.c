@@ -198,6 +198,99 @@ int sad_oracle_rank_vs(const int32_t *counts, const int64_t *lengths, int32_t n,
   return OR_OK;
 }
 
+/* ------------------------------------------------ distance-form rank ------ */
+
+/* floor(ln 2 * 2^64), from the decimal expansion ln 2 = 0.693147180559945309417... */
+#define OR_LN2_Q64 0xB17217F7D1CF79ABull
+
+/* ln(x) * 2^32 for an integer x >= 1, as a deterministic fixed-point value: the
+ * binary logarithm by repeated squaring (x = 2^e m, m in [1, 2); squaring m gives
+ * the next fraction bit of log2 m, halving it when it reaches 2), 40 fraction
+ * bits with a 64-bit mantissa, then times ln 2. */
+int64_t sad_oracle_ln_q(uint64_t x) {
+  if (x == 0) return 0;
+  int e = 63;
+  while (!((x >> e) & 1u)) --e;
+  uint64_t y = x << (63 - e);            /* m = y / 2^63 */
+  uint64_t f = 0;
+  for (int i = 1; i <= 40; ++i) {
+    u128 t = ((u128)y * (u128)y) >> 63;  /* m^2 in [1, 4) */
+    if (t >> 64) {
+      t >>= 1;
+      f |= (uint64_t)1 << (40 - i);
+    }
+    y = (uint64_t)t;
+  }
+  const u128 l2 = ((u128)(uint64_t)e << 40) | f;  /* log2 x, 40 fraction bits */
+  return (int64_t)((l2 * (u128)OR_LN2_Q64) >> 72);
+}
+
+/* Eq. 2 and Eq. 3 literally: R_i = (1/N) sum_j d(i, j), d = -ln(Delta + F(i, j)),
+ * with Delta = 1 / delta_den. With F = S / D, Delta + F = (D + b S) / (b D), so
+ * the per-pair value is q_ij = ln_q(b D) - ln_q(D + b S) (ln times 2^32) and
+ * key_i = sum_j q_ij (j = i included), rank_i = key_i 2^-32 / N (each step rounded
+ * to nearest). rank_fp64: the FP64 mean of -log(1/b + S/D) with Neumaier
+ * compensation, as an independent check. */
+typedef struct {
+  const int32_t *counts;
+  const int64_t *m;
+  int32_t n;
+  int64_t eps;
+  int64_t b;
+  int64_t *key;
+  double *rank, *rank_fp64;
+  int32_t next;
+  pthread_mutex_t lock;
+} dist_job;
+
+static void *dist_worker(void *arg) {
+  dist_job *J = (dist_job *)arg;
+  for (;;) {
+    pthread_mutex_lock(&J->lock);
+    int32_t i = J->next++;
+    pthread_mutex_unlock(&J->lock);
+    if (i >= J->n) break;
+    const int32_t *ci = J->counts + (int64_t)i * J->eps;
+    int64_t key = 0;
+    double sum = 0.0, comp = 0.0;
+    for (int32_t j = 0; j < J->n; ++j) {
+      const int64_t s = sad_oracle_shared_count(ci, J->counts + (int64_t)j * J->eps, J->eps);
+      const int64_t d = J->m[i] < J->m[j] ? J->m[i] : J->m[j];
+      key += sad_oracle_ln_q((uint64_t)(J->b * d)) - sad_oracle_ln_q((uint64_t)(d + J->b * s));
+      const double f = -log(1.0 / (double)J->b + (double)s / (double)d);
+      const double t = sum + f;
+      if (fabs(sum) >= fabs(f)) comp += (sum - t) + f; else comp += (f - t) + sum;
+      sum = t;
+    }
+    J->key[i] = key;
+    volatile double k64 = (double)key;
+    volatile double nats = k64 * ldexp(1.0, -32);
+    J->rank[i] = nats / (double)J->n;
+    if (J->rank_fp64) J->rank_fp64[i] = (sum + comp) / (double)J->n;
+  }
+  return NULL;
+}
+
+int sad_oracle_rank_dist(const int32_t *counts, const int64_t *lengths, int32_t n, int32_t k,
+                         int32_t alphabet, int32_t delta_den, int64_t *key, double *rank,
+                         double *rank_fp64, int32_t threads) {
+  if (n < 0 || k < 1 || alphabet < 1 || delta_den < 1) return OR_INVALID;
+  int64_t *m = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  for (int32_t x = 0; x < n; ++x) {
+    m[x] = lengths[x] - k + 1;
+    if (m[x] < 1) { free(m); return OR_BAD_INPUT; }
+  }
+  dist_job J = {counts, m, n, ipow(alphabet, k), delta_den, key, rank, rank_fp64, 0,
+                PTHREAD_MUTEX_INITIALIZER};
+  if (threads < 1) threads = 1;
+  if (threads > 1024) threads = 1024;
+  pthread_t tid[1024];
+  for (int32_t t = 0; t < threads; ++t) pthread_create(&tid[t], NULL, dist_worker, &J);
+  for (int32_t t = 0; t < threads; ++t) pthread_join(tid[t], NULL);
+  free(m);
+  return OR_OK;
+}
+
 /* ------------------------------------------------------------ partition --- */
 
 typedef struct { uint64_t hi, lo; int32_t idx; } item;

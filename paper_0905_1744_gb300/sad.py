@@ -401,18 +401,92 @@ def kmer_rank_vs(counts: torch.Tensor, lengths: torch.Tensor, ref: torch.Tensor,
     return hi, lo, rank
 
 
+class GlobalRank:
+    """Algorithm 2 steps 2-6 (Sec. 3.1.1) for one set of counts: local ranks per
+    block, ks samples per block, every sequence re-ranked against the ks x p
+    samples. The constructor plans (synchronous); ``run()`` then launches the
+    three steps with no host synchronisation."""
+
+    def __init__(self, counts: torch.Tensor, lengths: torch.Tensor, p: int, ks: int,
+                 k: int = 3, alphabet: int = 20, word_max: torch.Tensor | None = None,
+                 local_depth: int = 0, stream=None):
+        import numpy as np
+        n = counts.shape[0]
+        dev = counts.device
+        if not 1 <= p <= n or ks < 1:
+            raise ValueError("need 1 <= p <= N and ks >= 1")
+        self.counts, self.word_max, self.p, self.ks = counts, word_max, p, ks
+        self.k, self.alphabet, self.n = k, alphabet, n
+        self.lengths = lengths.to(device=dev, dtype=torch.int32).contiguous()
+        self.h_n = np.ascontiguousarray(np.diff(block_bounds(n, p)), dtype=np.int32)
+        h_p = np.ones(p, dtype=np.int32)
+        self.d_n = torch.from_numpy(self.h_n).to(dev)
+        self.ws_local = Workspace(dev, 256)
+        plan = BatchPlan()
+        plan.rank.depth = int(local_depth)
+        args = (_ptr(counts), self.h_n.ctypes.data_as(ctypes.c_void_p),
+                h_p.ctypes.data_as(ctypes.c_void_p), _ptr(self.d_n), p, k, alphabet,
+                ctypes.byref(plan))
+        rc = _load().sad_batch_plan_make(*args, _ptr(self.ws_local.buf), self.ws_local.nbytes,
+                                         _stream(stream))
+        if rc == ERR_WORKSPACE:
+            self.ws_local.ensure(plan.rank.ws_bytes)
+            plan.rank.depth = int(local_depth)
+            rc = _load().sad_batch_plan_make(*args, _ptr(self.ws_local.buf),
+                                             self.ws_local.nbytes, _stream(stream))
+        _check(rc, "sad_batch_plan_make (local ranks)")
+        self.ws_local.ensure(plan.rank.ws_bytes)
+        self.local_plan = plan
+        self.ws_vs = Workspace(dev)
+        self.vs_plan = kmer_rank_plan(counts, k, alphabet, 0, self.ws_vs, stream)
+        self.ws_vs.ensure(int(_load().kmer_rank_vs_workspace_bytes(
+            ctypes.byref(self.vs_plan), n, k, alphabet, p * ks)))
+        self.ws_samp = Workspace(dev, int(_load().sad_local_samples_workspace_bytes(n, p)))
+        self.local_hi = torch.empty(n, dtype=torch.uint64, device=dev)
+        self.local_lo = torch.empty(n, dtype=torch.uint64, device=dev)
+        self.local_rank = torch.empty(n, dtype=torch.float64, device=dev)
+        self.samples = torch.empty(p * ks, dtype=torch.int32, device=dev)
+        self.key_hi = torch.empty(n, dtype=torch.uint64, device=dev)
+        self.key_lo = torch.empty(n, dtype=torch.uint64, device=dev)
+        self.rank = torch.empty(n, dtype=torch.float64, device=dev)
+
+    def run(self, stream=None):
+        lib, st = _load(), _stream(stream)
+        _check(lib.sad_batch_rank(_ptr(self.counts), _ptr(self.lengths), _ptr(self.word_max),
+                                  _ptr(self.d_n), self.k, self.alphabet,
+                                  ctypes.byref(self.local_plan), _ptr(self.local_hi),
+                                  _ptr(self.local_lo), _ptr(self.local_rank),
+                                  _ptr(self.ws_local.buf), self.ws_local.nbytes, st),
+               "sad_batch_rank (local ranks)")
+        _check(lib.sad_local_samples(_ptr(self.local_hi), _ptr(self.local_lo), self.n, self.p,
+                                     self.ks, _ptr(self.samples), _ptr(self.ws_samp.buf),
+                                     self.ws_samp.nbytes, st), "sad_local_samples")
+        _check(lib.kmer_rank_vs(_ptr(self.counts), _ptr(self.lengths), _ptr(self.word_max),
+                                self.n, self.k, self.alphabet, _ptr(self.samples),
+                                self.p * self.ks, ctypes.byref(self.vs_plan), _ptr(self.key_hi),
+                                _ptr(self.key_lo), _ptr(self.rank), _ptr(self.ws_vs.buf),
+                                self.ws_vs.nbytes, st), "kmer_rank_vs")
+
+    def check(self, stream=None):
+        self.ws_local.check("local ranks", stream)
+        self.ws_samp.check("sad_local_samples", stream)
+        self.ws_vs.check("kmer_rank_vs", stream)
+
+    def pairs(self) -> int:
+        """Pairs whose shared counts enter: each block's pairs plus N x (ks p)."""
+        return int(sum(int(w) * (int(w) + 1) // 2 for w in self.h_n)) + self.n * self.p * self.ks
+
+
 def global_rank(counts: torch.Tensor, lengths: torch.Tensor, p: int, ks: int, k: int = 3,
                 alphabet: int = 20, word_max: torch.Tensor | None = None, local_depth: int = 0,
                 stream=None):
     """Algorithm 2 steps 2-6 (Sec. 3.1.1): local ranks per block, ks samples per
     block, every sequence re-ranked against the ks x p samples.
     Returns (key_hi, key_lo, rank, samples)."""
-    lh, ll, _ = local_ranks(counts, lengths, p, k, alphabet, local_depth, word_max,
-                            stream=stream)
-    samples = local_samples(lh, ll, p, ks, stream=stream)
-    hi, lo, rank = kmer_rank_vs(counts, lengths, samples, k, alphabet, word_max=word_max,
-                                stream=stream)
-    return hi, lo, rank, samples
+    g = GlobalRank(counts, lengths, p, ks, k, alphabet, word_max, local_depth, stream)
+    g.run(stream)
+    g.check(stream)
+    return g.key_hi, g.key_lo, g.rank, g.samples
 
 
 def global_partition_set(codes: torch.Tensor, offsets: torch.Tensor, p: int, ks: int,

@@ -336,3 +336,63 @@ def test_global_rank_against_exact_pipeline(oracle_mod):
     for x in range(s.n):
         want = sum(exact_term(ms[x], ms[r], L[x], L[r]) for r in want_samples)
         assert ((int(hi[x]) << 64) | int(lo[x])) == want
+
+
+# ------------------------------------- distance-form rank, Eq. 2 / Eq. 3 -----
+
+def test_ln_q_against_decimal_logarithm(oracle_mod):
+    from decimal import Decimal, getcontext
+    getcontext().prec = 50
+    xs = list(range(1, 300)) + [2 ** e + d for e in range(1, 40) for d in (-1, 0, 1)]
+    xs += [65535, 65536, 720885, 11 * 65535, 129 * 65535, 1025 * 65535]
+    prev = -1
+    for x in sorted(set(xs)):
+        got = oracle_mod.ln_q(x)
+        exact = Decimal(x).ln() * (Decimal(2) ** 32)
+        assert 0 <= exact - got < 2, x              # truncation below 2^-32 (plus < 1 ulp)
+        assert got >= prev
+        prev = got
+
+
+def test_rank_dist_closed_forms(oracle_mod):
+    # x = ACDE, y = CDEF (Eq. 1 example: S = 1, D = 2, F = 1/2); z shares nothing
+    s = datagen.from_strings(["ACDE", "CDEF", "WWWWW"])
+    c = oracle_mod.kmer_count(s.codes, s.offsets)
+    b = 10
+    key, rank = oracle_mod.rank_dist(c, s.lengths, b)
+    q = oracle_mod.ln_q
+    self_xy = q(b * 2) - q(2 + b * 2)          # F = 1: -ln(1 + 1/b)
+    half = q(b * 2) - q(2 + b * 1)             # F = 1/2: -ln(1/b + 1/2)
+    zero = lambda d: q(b * d) - q(d)           # F = 0: ln b
+    assert key[0] == self_xy + half + zero(2)
+    assert key[1] == half + self_xy + zero(2)
+    assert key[2] == zero(2) + zero(2) + (q(b * 3) - q(3 + b * 3))
+    assert abs(zero(2) / 2 ** 32 - np.log(b)) < 1e-9
+
+
+def test_rank_dist_against_exact_sums(oracle_mod):
+    s = datagen.random_small(12, 3, 45, seed=31, alphabet=4)
+    c = oracle_mod.kmer_count(s.codes, s.offsets, 3, 4)
+    for b in (1, 10, 100):
+        key, rank, fp = oracle_mod.rank_dist(c, s.lengths, b, 3, 4, with_fp64=True)
+        ms = [kmer_multiset(s.seq(x), 3) for x in range(s.n)]
+        for x in range(s.n):
+            want = 0
+            for y in range(s.n):
+                S = sum((ms[x] & ms[y]).values())
+                D = min(int(s.lengths[x]), int(s.lengths[y])) - 2
+                want += oracle_mod.ln_q(b * D) - oracle_mod.ln_q(D + b * S)
+            assert key[x] == want
+            # each term within 2^-31 of -ln(1/b + S/D): the mean too
+            assert abs(rank[x] - fp[x]) <= 2.0 ** -31 + 1e-13 * abs(fp[x])
+
+
+def test_rank_dist_orders_against_similarity(oracle_mod):
+    """d decreases in F, so for equal denominators a larger shared count gives a
+    smaller distance sum term by term: identical rows get identical keys and the
+    distance rank orders opposite to a strictly larger similarity everywhere."""
+    s = datagen.from_strings(["ACDEFGHIKLMN", "ACDEFGHIKLMN", "ACDEFGHIKLMW", "WYWYWYWYWYWY"])
+    c = oracle_mod.kmer_count(s.codes, s.offsets)
+    key, _ = oracle_mod.rank_dist(c, s.lengths, 10)
+    assert key[0] == key[1]
+    assert key[0] < key[2] < key[3]
