@@ -328,24 +328,63 @@ int sad_local_samples(const uint64_t *d_key_hi, const uint64_t *d_key_lo, int32_
  *     key_i = sum_{r in R} floor(S_ir * 2^64 / D_ir),   D_ir = min(L_i, L_r) - k + 1,
  *     rank_i = (key_hi + key_lo * 2^-64) / |R|,
  * an index listed twice in R counting twice. With R = every sequence once this is
- * the kmer_rank key. Runs the rank preparation at full plane depth, gathers the
- * reference rows' planes and runs the plane GEMM over (all rows) x (R).
+ * the kmer_rank key. With delta_den = b > 0 the rank is the distance form of
+ * kmer_rank_dist instead: key_i = sum_r (ln_q(b D_ir) - ln_q(D_ir + b S_ir)),
+ * rank_i = key_i 2^-32 / |R|, signed keys in d_key (nullable), the order-keeping
+ * unsigned view in (d_key_hi, d_key_lo). Runs the rank preparation at full plane
+ * depth, gathers the reference rows' planes and runs the plane GEMM over
+ * (all rows) x (R).
  *   d_counts, d_lengths, d_word_max   as for kmer_rank.
  *   d_ref      int32 [n_ref] input indices of R (0 <= d_ref[r] < n_seq, checked on
  *              the device: SAD_ERR_INVALID_ARGUMENT).
+ *   delta_den  0: the similarity form; b in 1..1024: the distance form, Delta = 1/b.
  *   plan       (required) a plan from kmer_rank_plan with depth 0 for these
  *              counts (it fixes the plane capacity k_cap).
  *   d_ws       workspace of kmer_rank_vs_workspace_bytes(plan, n_seq, k,
- *              alphabet, n_ref) bytes.
+ *              alphabet, n_ref, delta_den) bytes.
+ *   d_key      (nullable) int64 [n_seq], the signed keys of the distance form.
  *   d_key_hi, d_key_lo  uint64 [n_seq]; d_rank (nullable) float64 [n_seq].
  */
 size_t kmer_rank_vs_workspace_bytes(const sad_rank_plan *plan, int32_t n_seq, int32_t k,
-                                    int32_t alphabet, int32_t n_ref);
+                                    int32_t alphabet, int32_t n_ref, int32_t delta_den);
 int kmer_rank_vs(const int32_t *d_counts, const int32_t *d_lengths, const int32_t *d_word_max,
                  int32_t n_seq, int32_t k, int32_t alphabet, const int32_t *d_ref,
-                 int32_t n_ref, const sad_rank_plan *plan, uint64_t *d_key_hi,
-                 uint64_t *d_key_lo, double *d_rank, void *d_ws, size_t ws_bytes,
-                 void *stream);
+                 int32_t n_ref, int32_t delta_den, const sad_rank_plan *plan, int64_t *d_key,
+                 uint64_t *d_key_hi, uint64_t *d_key_lo, double *d_rank, void *d_ws,
+                 size_t ws_bytes, void *stream);
+
+/*
+ * kmer_rank_dist - the k-mer rank of Eq. 2 and Eq. 3 as written: the mean over
+ * the set of the distance d(i, j) = -ln(Delta + F(i, j)), Delta = 1 / delta_den.
+ * With F = S / D, d = ln(b D) - ln(D + b S) (b = delta_den), and both logarithms
+ * are the deterministic fixed-point values ln_q(x) = ln(x) * 2^32 of sad_ln_q (a
+ * repeated-squaring binary logarithm with 40 fraction bits times ln 2; within
+ * 2^-32 of ln x), so every per-pair value q_ij = ln_q(b D) - ln_q(D + b S) is an
+ * integer and the key
+ *     key_i = sum_j q_ij   (signed, j = i included)
+ * is exact. rank_i = key_i * 2^-32 / N (each step rounded to nearest), in nats;
+ * a smaller rank is a more similar sequence. d_key_hi = 0 and d_key_lo = key_i xor
+ * 2^63 order the keys as unsigned values, for partition.
+ *   delta_den  b, 1..1024.
+ *   plan       (required) a plan from kmer_rank_plan for these counts (any depth).
+ *   d_key      (nullable) int64 [n_seq]: the signed keys.
+ *   d_ws       workspace of kmer_rank_dist_workspace_bytes(plan, n_seq, k, alphabet,
+ *              delta_den) bytes (the rank workspace plus the ln_q table).
+ * Other arguments as for kmer_rank.
+ */
+size_t kmer_rank_dist_workspace_bytes(const sad_rank_plan *plan, int32_t n_seq, int32_t k,
+                                      int32_t alphabet, int32_t delta_den);
+int kmer_rank_dist(const int32_t *d_counts, const int32_t *d_lengths, const int32_t *d_word_max,
+                   int32_t n_seq, int32_t k, int32_t alphabet, int32_t delta_den,
+                   const sad_rank_plan *plan, int64_t *d_key, uint64_t *d_key_hi,
+                   uint64_t *d_key_lo, double *d_rank, void *d_ws, size_t ws_bytes,
+                   void *stream);
+
+/*
+ * sad_ln_q - ln_q(x) = ln(x) * 2^32 as the fixed-point value the distance-form
+ * rank uses (0 for x = 0), for n values d_x on the device into d_out (int64).
+ */
+int sad_ln_q(const uint64_t *d_x, int64_t n, int64_t *d_out, void *stream);
 
 /* Number of kernels this library has launched in this process. */
 uint64_t sad_launch_count(void);

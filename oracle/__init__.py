@@ -86,6 +86,8 @@ def _load():
         lib.sad_oracle_ln_q.restype = ctypes.c_int64
         lib.sad_oracle_rank_dist.argtypes = [P, P, i32, i32, i32, i32, P, P, P, i32]
         lib.sad_oracle_rank_dist.restype = ctypes.c_int
+        lib.sad_oracle_rank_vs_dist.argtypes = [P, P, i32, i32, i32, i32, P, i32, P, P, i32]
+        lib.sad_oracle_rank_vs_dist.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -275,3 +277,20 @@ def dist_sort_key(key: np.ndarray):
     (offset binary), for the partition."""
     lo = (np.asarray(key, np.int64).view(np.uint64) ^ np.uint64(1 << 63))
     return np.zeros_like(lo), lo
+
+
+def rank_vs_dist(counts: np.ndarray, lengths: np.ndarray, delta_den: int, ref, k: int = 3,
+                 alphabet: int = 20, threads: int | None = None):
+    """The distance form against a reference multiset (input indices):
+    key_i = sum_r (ln_q(b D) - ln_q(D + b S)), rank_i = key_i 2^-32 / len(ref).
+    Returns (key int64, rank float64)."""
+    counts = np.ascontiguousarray(counts, dtype=np.int32)
+    lengths = np.ascontiguousarray(lengths, dtype=np.int64)
+    ref = np.ascontiguousarray(ref, dtype=np.int32)
+    n = counts.shape[0]
+    key = np.zeros(n, np.int64)
+    rank = np.zeros(n, np.float64)
+    _check(_load().sad_oracle_rank_vs_dist(_ptr(counts), _ptr(lengths), n, k, alphabet, delta_den,
+                                           _ptr(ref), ref.shape[0], _ptr(key), _ptr(rank),
+                                           threads or default_threads()), "rank_vs_dist")
+    return key, rank

@@ -237,6 +237,8 @@ typedef struct {
   int32_t n;
   int64_t eps;
   int64_t b;
+  const int32_t *ref;    /* reference multiset (NULL: all n) */
+  int32_t n_ref;
   int64_t *key;
   double *rank, *rank_fp64;
   int32_t next;
@@ -253,7 +255,8 @@ static void *dist_worker(void *arg) {
     const int32_t *ci = J->counts + (int64_t)i * J->eps;
     int64_t key = 0;
     double sum = 0.0, comp = 0.0;
-    for (int32_t j = 0; j < J->n; ++j) {
+    for (int32_t r = 0; r < J->n_ref; ++r) {
+      const int32_t j = J->ref ? J->ref[r] : r;
       const int64_t s = sad_oracle_shared_count(ci, J->counts + (int64_t)j * J->eps, J->eps);
       const int64_t d = J->m[i] < J->m[j] ? J->m[i] : J->m[j];
       key += sad_oracle_ln_q((uint64_t)(J->b * d)) - sad_oracle_ln_q((uint64_t)(d + J->b * s));
@@ -265,8 +268,8 @@ static void *dist_worker(void *arg) {
     J->key[i] = key;
     volatile double k64 = (double)key;
     volatile double nats = k64 * ldexp(1.0, -32);
-    J->rank[i] = nats / (double)J->n;
-    if (J->rank_fp64) J->rank_fp64[i] = (sum + comp) / (double)J->n;
+    J->rank[i] = nats / (double)J->n_ref;
+    if (J->rank_fp64) J->rank_fp64[i] = (sum + comp) / (double)J->n_ref;
   }
   return NULL;
 }
@@ -280,7 +283,31 @@ int sad_oracle_rank_dist(const int32_t *counts, const int64_t *lengths, int32_t 
     m[x] = lengths[x] - k + 1;
     if (m[x] < 1) { free(m); return OR_BAD_INPUT; }
   }
-  dist_job J = {counts, m, n, ipow(alphabet, k), delta_den, key, rank, rank_fp64, 0,
+  dist_job J = {counts, m, n, ipow(alphabet, k), delta_den, NULL, n, key, rank, rank_fp64, 0,
+                PTHREAD_MUTEX_INITIALIZER};
+  if (threads < 1) threads = 1;
+  if (threads > 1024) threads = 1024;
+  pthread_t tid[1024];
+  for (int32_t t = 0; t < threads; ++t) pthread_create(&tid[t], NULL, dist_worker, &J);
+  for (int32_t t = 0; t < threads; ++t) pthread_join(tid[t], NULL);
+  free(m);
+  return OR_OK;
+}
+
+/* The distance form against a reference multiset ref[0..n_ref) (the globalised
+ * rank of Sec. 3.1.1 on Eq. 2): key_i = sum_r q_{i, ref_r}, rank_i = key_i 2^-32 / n_ref. */
+int sad_oracle_rank_vs_dist(const int32_t *counts, const int64_t *lengths, int32_t n, int32_t k,
+                            int32_t alphabet, int32_t delta_den, const int32_t *ref,
+                            int32_t n_ref, int64_t *key, double *rank, int32_t threads) {
+  if (n < 0 || k < 1 || alphabet < 1 || delta_den < 1 || n_ref < 1 || !ref) return OR_INVALID;
+  for (int32_t r = 0; r < n_ref; ++r)
+    if (ref[r] < 0 || ref[r] >= n) return OR_INVALID;
+  int64_t *m = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  for (int32_t x = 0; x < n; ++x) {
+    m[x] = lengths[x] - k + 1;
+    if (m[x] < 1) { free(m); return OR_BAD_INPUT; }
+  }
+  dist_job J = {counts, m, n, ipow(alphabet, k), delta_den, ref, n_ref, key, rank, NULL, 0,
                 PTHREAD_MUTEX_INITIALIZER};
   if (threads < 1) threads = 1;
   if (threads > 1024) threads = 1024;

@@ -310,27 +310,75 @@ int sad_local_samples(const uint64_t *d_key_hi, const uint64_t *d_key_lo, int32_
 }
 
 size_t kmer_rank_vs_workspace_bytes(const sad_rank_plan *plan, int32_t n_seq, int32_t k,
-                                    int32_t alphabet, int32_t n_ref) {
+                                    int32_t alphabet, int32_t n_ref, int32_t delta_den) {
   const int64_t eps = eps_of(k, alphabet);
-  if (eps < 0 || !plan || n_seq < 1 || n_ref < 1 || plan->k_cap < kKCols) return 0;
-  return rank_vs_ws_bytes(n_seq, eps, plan->k_cap, n_ref);
+  if (eps < 0 || !plan || n_seq < 1 || n_ref < 1 || plan->k_cap < kKCols || delta_den < 0 ||
+      delta_den > 1024)
+    return 0;
+  return rank_vs_ws_bytes(n_seq, eps, plan->k_cap, n_ref, delta_den);
 }
 
 int kmer_rank_vs(const int32_t *d_counts, const int32_t *d_lengths, const int32_t *d_word_max,
                  int32_t n_seq, int32_t k, int32_t alphabet, const int32_t *d_ref,
-                 int32_t n_ref, const sad_rank_plan *plan, uint64_t *d_key_hi,
-                 uint64_t *d_key_lo, double *d_rank, void *d_ws, size_t ws_bytes,
-                 void *stream) {
+                 int32_t n_ref, int32_t delta_den, const sad_rank_plan *plan, int64_t *d_key,
+                 uint64_t *d_key_hi, uint64_t *d_key_lo, double *d_rank, void *d_ws,
+                 size_t ws_bytes, void *stream) {
   const int64_t eps = eps_of(k, alphabet);
   if (eps < 0) return SAD_ERR_UNSUPPORTED;
   if (n_seq < 1 || n_ref < 1 || !plan || !d_counts || !d_lengths || !d_ref || !d_key_hi ||
-      !d_key_lo || !d_ws || !aligned(d_ws, 256))
+      !d_key_lo || !d_ws || !aligned(d_ws, 256) || delta_den < 0 || delta_den > 1024)
     return SAD_ERR_INVALID_ARGUMENT;
   if (plan->depth != 0 || plan->k_cap < kKCols || plan->k_cap % kKCols != 0)
     return SAD_ERR_INVALID_ARGUMENT;
   return rank_vs_launch(d_counts, d_lengths, d_word_max, n_seq, k, eps, d_ref, n_ref,
-                        plan->k_cap, d_key_hi, d_key_lo, d_rank, d_ws, ws_bytes,
-                        static_cast<cudaStream_t>(stream));
+                        plan->k_cap, delta_den, d_key, d_key_hi, d_key_lo, d_rank, d_ws,
+                        ws_bytes, static_cast<cudaStream_t>(stream));
+}
+
+size_t kmer_rank_dist_workspace_bytes(const sad_rank_plan *plan, int32_t n_seq, int32_t k,
+                                      int32_t alphabet, int32_t delta_den) {
+  const int64_t eps = eps_of(k, alphabet);
+  if (eps < 0 || !plan || n_seq < 1 || delta_den < 1 || delta_den > 1024) return 0;
+  const RankCaps caps{plan->depth, plan->k_cap, plan->list_cap, plan->block_cap};
+  const size_t base = rank_layout(shape_single(n_seq), eps, caps).bytes;
+  return align_up(base, 256) + sizeof(int64_t) * ln_table_entries(delta_den);
+}
+
+int kmer_rank_dist(const int32_t *d_counts, const int32_t *d_lengths, const int32_t *d_word_max,
+                   int32_t n_seq, int32_t k, int32_t alphabet, int32_t delta_den,
+                   const sad_rank_plan *plan, int64_t *d_key, uint64_t *d_key_hi,
+                   uint64_t *d_key_lo, double *d_rank, void *d_ws, size_t ws_bytes,
+                   void *stream) {
+  const int64_t eps = eps_of(k, alphabet);
+  if (eps < 0) return SAD_ERR_UNSUPPORTED;
+  if (n_seq < 1 || !plan || !d_counts || !d_lengths || !d_key_hi || !d_key_lo || !d_ws ||
+      !aligned(d_ws, 256) || delta_den < 1 || delta_den > 1024)
+    return SAD_ERR_INVALID_ARGUMENT;
+  if (plan->depth < 0 || plan->k_cap < kKCols || plan->k_cap % kKCols != 0 ||
+      plan->list_cap < 0 || plan->block_cap < 0)
+    return SAD_ERR_INVALID_ARGUMENT;
+  const RankShape sh = shape_single(n_seq);
+  if (sh.rows_total / kRowBlock > 0xFFFF) return SAD_ERR_UNSUPPORTED;
+  const RankCaps caps{plan->depth, plan->k_cap, plan->list_cap, plan->block_cap};
+  const RankLayout L = rank_layout(sh, eps, caps);
+  const size_t table_off = align_up(L.bytes, 256);
+  if (table_off + sizeof(int64_t) * ln_table_entries(delta_den) > ws_bytes)
+    return SAD_ERR_WORKSPACE;
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int64_t *table = reinterpret_cast<int64_t *>(static_cast<uint8_t *>(d_ws) + table_off);
+  const RankPtrs P = rank_ptrs(d_ws, L);
+  int rc = ln_table_launch(table, delta_den, st);
+  if (rc) return rc;
+  rc = rank_prep_launch(P, d_counts, d_lengths, nullptr, d_word_max, k, (int32_t)eps, 0, st);
+  if (rc) return rc;
+  rc = rank_dist_gemm_launch(P, table, delta_den, st);
+  if (rc) return rc;
+  return rank_dist_finalize_launch(P, d_key, d_key_hi, d_key_lo, d_rank, 0, st);
+}
+
+int sad_ln_q(const uint64_t *d_x, int64_t n, int64_t *d_out, void *stream) {
+  if (n < 0 || (n > 0 && (!d_x || !d_out))) return SAD_ERR_INVALID_ARGUMENT;
+  return ln_q_launch(d_x, n, d_out, static_cast<cudaStream_t>(stream));
 }
 
 int sad_batch_plan_make(const int32_t *d_counts, const int32_t *h_n, const int32_t *h_p,

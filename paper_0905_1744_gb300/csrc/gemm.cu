@@ -61,6 +61,7 @@ struct GemmSmem {
   uint8_t b[kStages][kBBytes];
   uint4 colrec[2][kColBlock];
   int32_t colorig[2][kColBlock];
+  int64_t collb[2][kColBlock];  // distance mode: ln_q(b d) of each tile column
   uint64_t full[kStages];
   uint64_t empty[kStages];
   uint64_t tfull[2];
@@ -126,9 +127,11 @@ __device__ __forceinline__ void tile_at(const RankPtrs &P, const RectArgs &X, in
   }
 }
 
+template <bool kDist>
 __global__ void __launch_bounds__(kThreads, 1)
     plane_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
-                      const __grid_constant__ CUtensorMap tmB, RankPtrs P, RectArgs X) {
+                      const __grid_constant__ CUtensorMap tmB, RankPtrs P, RectArgs X,
+                      DistArgs Z) {
   extern __shared__ uint8_t smem_raw[];
   GemmSmem &S = *reinterpret_cast<GemmSmem *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -275,6 +278,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int64_t jpos = (int64_t)J * kColBlock + c;
         S.colrec[buf][c] = rect ? X.rec_ref[jpos] : P.rec[jpos];
         S.colorig[buf][c] = rect ? 0 : P.perm[jpos];
+        if constexpr (kDist)
+          S.collb[buf][c] = Z.ln_table[(int64_t)Z.b * (int64_t)(P.rec[jpos].w & 0xFFFFu)];
       }
       const int64_t row_pos = (int64_t)I * kRowBlock + q * 32 + lane;
       const int32_t row_orig = P.perm[row_pos];
@@ -298,7 +303,81 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (named_bar_sync_or(1, kEpiThreads, *abort_flag != 0)) break;
       tc_fence_after();
       uint32_t R0 = 0, R1 = 0, R2 = 0;
-      if (rect) {
+      int64_t Rd = 0;  // distance mode: the row's sum of q
+      if (kDist && rect) {
+        // distance mode against reference rows: D = min(m_i, m_r) per pair, row sums only,
+        // reference columns past n_ref (padding) left out
+        const uint32_t dr = P.rec[row_pos].w & 0xFFFFu;
+#pragma unroll 1
+        for (int sc = 0; sc < kHalfCols / 16; ++sc) {
+          const int c0 = (int)half * kHalfCols + sc * 16;
+          uint32_t v[16];
+          tmem_ld_32x32b_x16(tmem + ((q * 32u) << 16) + acc * (uint32_t)kColBlock + (uint32_t)c0,
+                             v);
+          tmem_ld_wait();
+          int64_t ta[16], tb[16];
+#pragma unroll
+          for (int cc = 0; cc < 16; ++cc) {
+            const uint32_t s = __float2uint_rn(__uint_as_float(v[cc]));
+            const uint32_t dc = S.colrec[buf][c0 + cc].w & 0xFFFFu;
+            const uint32_t d = dr < dc ? dr : dc;
+            ta[cc] = __ldg(Z.ln_table + (uint32_t)Z.b * d);
+            tb[cc] = __ldg(Z.ln_table + (d + (uint32_t)Z.b * s));
+          }
+#pragma unroll
+          for (int cc = 0; cc < 16; ++cc) {
+            const int64_t jpos = (int64_t)J * kColBlock + c0 + cc;
+            Rd += jpos < X.n_ref ? ta[cc] - tb[cc] : 0;
+          }
+        }
+      } else if constexpr (kDist) {
+        // Eq. 2 / Eq. 3 with Delta = 1/b: q_ij = ln_q(b m_j) - ln_q(m_j + b S_ij), i <= j
+        // (D_ij = m_j in the stored order); signed 64-bit sums, the column sums
+        // reduced as a low 24-bit part and a signed high part
+#pragma unroll 1
+        for (int sc = 0; sc < kHalfCols / 16; ++sc) {
+          const int c0 = (int)half * kHalfCols + sc * 16;
+          uint32_t v[16];
+          tmem_ld_32x32b_x16(tmem + ((q * 32u) << 16) + acc * (uint32_t)kColBlock + (uint32_t)c0,
+                             v);
+          const uint32_t rw[8] = {ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
+          if (rrow && sc + 1 < kHalfCols / 16) {
+            ra = __ldg(rrow + 2 * (sc + 1));
+            rb = __ldg(rrow + 2 * (sc + 1) + 1);
+          }
+          tmem_ld_wait();
+          int64_t tv[16];
+#pragma unroll
+          for (int cc = 0; cc < 16; ++cc) {
+            const uint32_t s = __float2uint_rn(__uint_as_float(v[cc])) +
+                               ((rw[cc >> 1] >> (16 * (cc & 1))) & 0xFFFFu);
+            const uint32_t d = S.colrec[buf][c0 + cc].w & 0xFFFFu;
+            tv[cc] = __ldg(Z.ln_table + (d + (uint32_t)Z.b * s));
+          }
+          uint32_t cl[16], ch[16];
+#pragma unroll
+          for (int cc = 0; cc < 16; ++cc) {
+            const int64_t qd = S.collb[buf][c0 + cc] - tv[cc];
+            const int64_t jpos = (int64_t)J * kColBlock + c0 + cc;
+            // padding columns (no sequence) count nowhere: unlike F, d is not 0 at S = 0
+            const bool real = S.colorig[buf][c0 + cc] >= 0;
+            const bool in_row = real && (!diag || row_pos <= jpos);
+            const bool in_col = !diag || row_pos < jpos;
+            Rd += in_row ? qd : 0;
+            const int64_t cv = in_col ? qd : 0;
+            cl[cc] = (uint32_t)(cv & 0xFFFFFF);
+            ch[cc] = (uint32_t)(int32_t)(cv >> 24);
+          }
+          transpose_reduce16(cl, lane);
+          transpose_reduce16(ch, lane);
+          if (lane < 16) {
+            const int32_t jorig = S.colorig[buf][c0 + (int)lane];
+            const int64_t tot = (int64_t)(int32_t)ch[0] * (int64_t)(1 << 24) + (int64_t)cl[0];
+            if (jorig >= 0 && tot != 0)
+              red_add_u64(P.acc + 3 * (int64_t)jorig, (unsigned long long)tot);
+          }
+        }
+      } else if (rect) {
         // every pair counts for the row only; D = min(m_i, m_r): the record of the
         // shorter of the two
         const uint4 rrec = P.rec[row_pos];
@@ -398,9 +477,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_arrive(&S.tempty[acc]);
       if (row_orig >= 0) {
         unsigned long long *dst = P.acc + 3 * (int64_t)row_orig;
-        red_add_u64(dst + 0, R0);
-        red_add_u64(dst + 1, R1);
-        red_add_u64(dst + 2, R2);
+        if constexpr (kDist) {
+          red_add_u64(dst, (unsigned long long)Rd);
+        } else {
+          red_add_u64(dst + 0, R0);
+          red_add_u64(dst + 1, R1);
+          red_add_u64(dst + 2, R2);
+        }
       }
     }
   }
@@ -446,7 +529,11 @@ namespace {
 int gemm_attr() {
   static bool attr_set = false;
   if (!attr_set) {
-    if (cudaFuncSetAttribute(plane_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(plane_gemm_kernel<false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kGemmSmemBytes) != cudaSuccess ||
+        cudaFuncSetAttribute(plane_gemm_kernel<true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kGemmSmemBytes) != cudaSuccess)
       return SAD_ERR_CUDA;
     attr_set = true;
@@ -466,16 +553,39 @@ int rank_gemm_launch(const RankPtrs &P, cudaStream_t st) {
   if ((rc = gemm_attr())) return rc;
   const int64_t grid = tiles < num_sms() ? tiles : num_sms();
   prof_begin(st);
-  plane_gemm_kernel<<<(unsigned)grid, kThreads, kGemmSmemBytes, st>>>(mA, mB, P, RectArgs{});
+  plane_gemm_kernel<false>
+      <<<(unsigned)grid, kThreads, kGemmSmemBytes, st>>>(mA, mB, P, RectArgs{}, DistArgs{});
   SAD_LAUNCH_CHECK();
   prof_end(st);
   return SAD_OK;
 }
 
+int rank_dist_gemm_launch(const RankPtrs &P, const int64_t *ln_table, int32_t b,
+                          cudaStream_t st) {
+  const int64_t tiles = P.tiles_total;
+  if (tiles == 0) return SAD_OK;
+  CUtensorMap mA, mB;
+  int rc = make_plane_map(&mA, P.planes, P.n_pad, P.k_cap, kRowBlock);
+  if (rc) return rc;
+  rc = make_plane_map(&mB, P.planes, P.n_pad, P.k_cap, kColBlock);
+  if (rc) return rc;
+  if ((rc = gemm_attr())) return rc;
+  DistArgs Z;
+  Z.ln_table = ln_table;
+  Z.b = b;
+  const int64_t grid = tiles < num_sms() ? tiles : num_sms();
+  plane_gemm_kernel<true>
+      <<<(unsigned)grid, kThreads, kGemmSmemBytes, st>>>(mA, mB, P, RectArgs{}, Z);
+  SAD_LAUNCH_CHECK();
+  return SAD_OK;
+}
+
 int rank_rect_gemm_launch(const RankPtrs &P, uint8_t *ref_planes, const uint4 *rec_ref,
-                          int64_t ref_rows, cudaStream_t st) {
+                          int64_t ref_rows, int32_t n_ref, const int64_t *ln_table, int32_t b,
+                          cudaStream_t st) {
   RectArgs X;
   X.rec_ref = rec_ref;
+  X.n_ref = n_ref;
   X.row_blocks = (int32_t)(P.n_pad / kRowBlock);
   const int64_t tiles = (int64_t)X.row_blocks * (ref_rows / kColBlock);
   if (tiles == 0) return SAD_OK;
@@ -488,7 +598,15 @@ int rank_rect_gemm_launch(const RankPtrs &P, uint8_t *ref_planes, const uint4 *r
   if (rc) return rc;
   if ((rc = gemm_attr())) return rc;
   const int64_t grid = tiles < num_sms() ? tiles : num_sms();
-  plane_gemm_kernel<<<(unsigned)grid, kThreads, kGemmSmemBytes, st>>>(mA, mB, P, X);
+  if (ln_table) {
+    DistArgs Z;
+    Z.ln_table = ln_table;
+    Z.b = b;
+    plane_gemm_kernel<true><<<(unsigned)grid, kThreads, kGemmSmemBytes, st>>>(mA, mB, P, X, Z);
+  } else {
+    plane_gemm_kernel<false>
+        <<<(unsigned)grid, kThreads, kGemmSmemBytes, st>>>(mA, mB, P, X, DistArgs{});
+  }
   SAD_LAUNCH_CHECK();
   return SAD_OK;
 }

@@ -8,7 +8,8 @@
 //              (local_samples_launch);
 //   steps 5-6  the ks x p samples are the reference set; every sequence is ranked
 //              against it: key_i = sum_r floor(S_{i,r} 2^64 / D_{i,r}),
-//              D = min(L_i, L_r) - k + 1, rank_i = key_i / (|R| 2^64)
+//              D = min(L_i, L_r) - k + 1, rank_i = key_i / (|R| 2^64), or in the
+//              distance form of Eq. 2 key_i = sum_r q_{i,r} (see dist.cu)
 //              (rank_vs_launch: the rank preparation at full plane depth, the
 //              reference rows' planes gathered, then the plane GEMM in its
 //              rectangular mode).
@@ -74,11 +75,11 @@ __global__ void pick_samples_kernel(const Item *items, const int64_t *segoff, in
 // ------------------------------------------------------------- rank vs R ---
 
 struct RefLayout {
-  size_t inv, planes, rec, bytes;  // offsets after the rank layout
+  size_t inv, planes, rec, table, bytes;  // offsets after the rank layout
   int64_t ref_rows;
 };
 
-RefLayout ref_layout(size_t base, int64_t n_pad, int64_t n_ref, int64_t k_cap) {
+RefLayout ref_layout(size_t base, int64_t n_pad, int64_t n_ref, int64_t k_cap, int32_t delta_den) {
   RefLayout R{};
   R.ref_rows = (n_ref + kColBlock - 1) / kColBlock * kColBlock;
   size_t o = align_up(base, 256);
@@ -88,6 +89,8 @@ RefLayout ref_layout(size_t base, int64_t n_pad, int64_t n_ref, int64_t k_cap) {
   o = align_up(o + (size_t)R.ref_rows * (size_t)k_cap / 2, 256);
   R.rec = o;
   o = align_up(o + 16 * (size_t)R.ref_rows, 256);
+  R.table = o;  // distance form: the ln_q table
+  if (delta_den > 0) o = align_up(o + sizeof(int64_t) * ln_table_entries(delta_den), 256);
   R.bytes = o;
   return R;
 }
@@ -189,17 +192,17 @@ int local_samples_launch(const uint64_t *key_hi, const uint64_t *key_lo, int32_t
   return SAD_OK;
 }
 
-size_t rank_vs_ws_bytes(int64_t n, int64_t eps, int64_t k_cap, int64_t n_ref) {
+size_t rank_vs_ws_bytes(int64_t n, int64_t eps, int64_t k_cap, int64_t n_ref, int32_t delta_den) {
   const RankLayout L = rank_layout(shape_single(n), eps, RankCaps{0, k_cap, 0, 0});
-  return ref_layout(L.bytes, L.shape.rows_total, n_ref, k_cap).bytes;
+  return ref_layout(L.bytes, L.shape.rows_total, n_ref, k_cap, delta_den).bytes;
 }
 
 int rank_vs_launch(const int32_t *counts, const int32_t *lengths, const int32_t *word_max,
                    int32_t n, int32_t k, int64_t eps, const int32_t *ref, int32_t n_ref,
-                   int64_t k_cap, uint64_t *key_hi, uint64_t *key_lo, double *rank, void *ws,
-                   size_t ws_bytes, cudaStream_t st) {
+                   int64_t k_cap, int32_t delta_den, int64_t *key, uint64_t *key_hi,
+                   uint64_t *key_lo, double *rank, void *ws, size_t ws_bytes, cudaStream_t st) {
   const RankLayout L = rank_layout(shape_single(n), eps, RankCaps{0, k_cap, 0, 0});
-  const RefLayout R = ref_layout(L.bytes, L.shape.rows_total, n_ref, k_cap);
+  const RefLayout R = ref_layout(L.bytes, L.shape.rows_total, n_ref, k_cap, delta_den);
   if (ws_bytes < R.bytes) return SAD_ERR_WORKSPACE;
   if (L.shape.rows_total / kRowBlock > 0xFFFF) return SAD_ERR_UNSUPPORTED;
   const RankPtrs P = rank_ptrs(ws, L);
@@ -208,15 +211,19 @@ int rank_vs_launch(const int32_t *counts, const int32_t *lengths, const int32_t 
   uint8_t *ref_planes = b + R.planes;
   uint4 *rec_ref = reinterpret_cast<uint4 *>(b + R.rec);
   // all planes (depth 0): no residual; the square tile list is built but not run
-  int rc = rank_prep_launch(P, counts, lengths, nullptr, word_max, k, (int32_t)eps, 0, st);
+  int64_t *table = delta_den > 0 ? reinterpret_cast<int64_t *>(b + R.table) : nullptr;
+  int rc = SAD_OK;
+  if (table && (rc = ln_table_launch(table, delta_den, st))) return rc;
+  rc = rank_prep_launch(P, counts, lengths, nullptr, word_max, k, (int32_t)eps, 0, st);
   if (rc) return rc;
   inv_perm_kernel<<<grid_of(P.n_pad, 256), 256, 0, st>>>(P, inv);
   SAD_LAUNCH_CHECK();
   gather_ref_kernel<<<(unsigned)(R.ref_rows < 65535 ? R.ref_rows : 65535), 256, 0, st>>>(
       P, inv, ref, n_ref, R.ref_rows, ref_planes, rec_ref);
   SAD_LAUNCH_CHECK();
-  rc = rank_rect_gemm_launch(P, ref_planes, rec_ref, R.ref_rows, st);
+  rc = rank_rect_gemm_launch(P, ref_planes, rec_ref, R.ref_rows, n_ref, table, delta_den, st);
   if (rc) return rc;
+  if (table) return rank_dist_finalize_launch(P, key, key_hi, key_lo, rank, n_ref, st);
   finalize_vs_kernel<<<grid_of(n, 256), 256, 0, st>>>(P, n_ref, key_hi, key_lo, rank);
   SAD_LAUNCH_CHECK();
   return SAD_OK;

@@ -54,20 +54,39 @@ int rank_gemm_launch(const RankPtrs &P, cudaStream_t st);
 // rec_ref), the row keys only, D = min(m_i, m_r) per pair.
 struct RectArgs {
   const uint4 *rec_ref = nullptr;  // nullptr: square mode
-  int32_t row_blocks = 0, n_tiles = 0;
+  int32_t row_blocks = 0, n_tiles = 0, n_ref = 0;
 };
+// ln_table != nullptr: the distance form (see DistArgs) with D = min(m_i, m_r).
 int rank_rect_gemm_launch(const RankPtrs &P, uint8_t *ref_planes, const uint4 *rec_ref,
-                          int64_t ref_rows, cudaStream_t st);
+                          int64_t ref_rows, int32_t n_ref, const int64_t *ln_table, int32_t b,
+                          cudaStream_t st);
+
+// Distance mode of the plane GEMM (Eq. 2 / Eq. 3 literally, Delta = 1 / b): for
+// stored i <= j, q_ij = ln_table[b m_j] - ln_table[m_j + b S_ij] (ln x times 2^32),
+// the signed sums added to acc[3 x] of both sequences (the pair once).
+struct DistArgs {
+  const int64_t *ln_table = nullptr;  // [(b + 1) * 65535 + 1]
+  int32_t b = 0;
+};
+int rank_dist_gemm_launch(const RankPtrs &P, const int64_t *ln_table, int32_t b,
+                          cudaStream_t st);
+// Distance-form rank (dist.cu).
+size_t ln_table_entries(int32_t b);
+int ln_table_launch(int64_t *table, int32_t b, cudaStream_t st);
+int ln_q_launch(const uint64_t *x, int64_t n, int64_t *out, cudaStream_t st);
+// n_div > 0: rank = key 2^-32 / n_div (a reference set); 0: the set's size.
+int rank_dist_finalize_launch(const RankPtrs &P, int64_t *key, uint64_t *key_hi,
+                              uint64_t *key_lo, double *rank, int64_t n_div, cudaStream_t st);
 // Globalised rank (grank.cu).
 size_t local_samples_ws_bytes(int64_t n, int64_t p);
 int local_samples_launch(const uint64_t *key_hi, const uint64_t *key_lo, int32_t n, int32_t p,
                          int32_t ks, int32_t *sample_idx, void *ws, size_t ws_bytes,
                          cudaStream_t st);
-size_t rank_vs_ws_bytes(int64_t n, int64_t eps, int64_t k_cap, int64_t n_ref);
+size_t rank_vs_ws_bytes(int64_t n, int64_t eps, int64_t k_cap, int64_t n_ref, int32_t delta_den);
 int rank_vs_launch(const int32_t *counts, const int32_t *lengths, const int32_t *word_max,
                    int32_t n, int32_t k, int64_t eps, const int32_t *ref, int32_t n_ref,
-                   int64_t k_cap, uint64_t *key_hi, uint64_t *key_lo, double *rank, void *ws,
-                   size_t ws_bytes, cudaStream_t st);
+                   int64_t k_cap, int32_t delta_den, int64_t *key, uint64_t *key_hi,
+                   uint64_t *key_lo, double *rank, void *ws, size_t ws_bytes, cudaStream_t st);
 
 // TMA map of a plane matrix (rows x K_cap / 2 bytes, 128-byte swizzle, boxes of
 // 128 bytes x box_rows rows).

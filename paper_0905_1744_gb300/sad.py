@@ -100,11 +100,20 @@ def _load():
         lib.sad_local_samples_workspace_bytes.restype = sz
         lib.sad_local_samples.argtypes = [P, P, i32, i32, i32, P, P, sz, P]
         lib.sad_local_samples.restype = ctypes.c_int
-        lib.kmer_rank_vs_workspace_bytes.argtypes = [ctypes.POINTER(RankPlan), i32, i32, i32, i32]
+        lib.kmer_rank_vs_workspace_bytes.argtypes = [ctypes.POINTER(RankPlan), i32, i32, i32, i32,
+                                                     i32]
         lib.kmer_rank_vs_workspace_bytes.restype = sz
-        lib.kmer_rank_vs.argtypes = [P, P, P, i32, i32, i32, P, i32, ctypes.POINTER(RankPlan), P,
-                                     P, P, P, sz, P]
+        lib.kmer_rank_vs.argtypes = [P, P, P, i32, i32, i32, P, i32, i32,
+                                     ctypes.POINTER(RankPlan), P, P, P, P, P, sz, P]
         lib.kmer_rank_vs.restype = ctypes.c_int
+        lib.kmer_rank_dist_workspace_bytes.argtypes = [ctypes.POINTER(RankPlan), i32, i32, i32,
+                                                       i32]
+        lib.kmer_rank_dist_workspace_bytes.restype = sz
+        lib.kmer_rank_dist.argtypes = [P, P, P, i32, i32, i32, i32, ctypes.POINTER(RankPlan), P,
+                                       P, P, P, P, sz, P]
+        lib.kmer_rank_dist.restype = ctypes.c_int
+        lib.sad_ln_q.argtypes = [P, i64, P, P]
+        lib.sad_ln_q.restype = ctypes.c_int
         lib.sad_profile.argtypes = [i32]
         lib.sad_profile.restype = ctypes.c_int
         lib.sad_profile_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
@@ -375,10 +384,12 @@ def local_samples(key_hi: torch.Tensor, key_lo: torch.Tensor, p: int, ks: int,
 def kmer_rank_vs(counts: torch.Tensor, lengths: torch.Tensor, ref: torch.Tensor, k: int = 3,
                  alphabet: int = 20, plan: RankPlan | None = None,
                  word_max: torch.Tensor | None = None, ws: Workspace | None = None,
-                 stream=None, check: bool = True):
+                 stream=None, check: bool = True, delta_den: int = 0):
     """Algorithm 2 step 6: every sequence ranked against the reference multiset
     ``ref`` (input indices). ``plan``: a depth-0 RankPlan (made here if None,
-    synchronous). Returns (key_hi, key_lo, rank), rank = key / (len(ref) 2^64)."""
+    synchronous). Returns (key_hi, key_lo, rank), rank = key / (len(ref) 2^64);
+    with ``delta_den`` = b > 0 the distance form (Eq. 2, Delta = 1/b): returns
+    (key int64, key_hi, key_lo, rank), rank = key 2^-32 / len(ref)."""
     n = counts.shape[0]
     dev = counts.device
     ws = ws or Workspace(dev)
@@ -387,18 +398,55 @@ def kmer_rank_vs(counts: torch.Tensor, lengths: torch.Tensor, ref: torch.Tensor,
     ref = ref.to(device=dev, dtype=torch.int32).contiguous()
     n_ref = ref.numel()
     ws.ensure(int(_load().kmer_rank_vs_workspace_bytes(ctypes.byref(plan), n, k, alphabet,
-                                                       n_ref)))
+                                                       n_ref, delta_den)))
+    key = torch.empty(n, dtype=torch.int64, device=dev) if delta_den else None
     hi = torch.empty(n, dtype=torch.uint64, device=dev)
     lo = torch.empty(n, dtype=torch.uint64, device=dev)
     rank = torch.empty(n, dtype=torch.float64, device=dev)
     lengths = lengths.to(device=dev, dtype=torch.int32).contiguous()
     _check(_load().kmer_rank_vs(_ptr(counts), _ptr(lengths), _ptr(word_max), n, k, alphabet,
-                                _ptr(ref), n_ref, ctypes.byref(plan), _ptr(hi), _ptr(lo),
-                                _ptr(rank), _ptr(ws.buf), ws.nbytes, _stream(stream)),
-           "kmer_rank_vs")
+                                _ptr(ref), n_ref, delta_den, ctypes.byref(plan), _ptr(key),
+                                _ptr(hi), _ptr(lo), _ptr(rank), _ptr(ws.buf), ws.nbytes,
+                                _stream(stream)), "kmer_rank_vs")
     if check:
         ws.check("kmer_rank_vs", stream)
-    return hi, lo, rank
+    return (key, hi, lo, rank) if delta_den else (hi, lo, rank)
+
+
+def ln_q(x: torch.Tensor, stream=None) -> torch.Tensor:
+    """ln(x) * 2^32 as the deterministic fixed-point value of the distance-form rank."""
+    x = x.to(dtype=torch.uint64).contiguous()
+    out = torch.empty(x.shape, dtype=torch.int64, device=x.device)
+    _check(_load().sad_ln_q(_ptr(x), x.numel(), _ptr(out), _stream(stream)), "sad_ln_q")
+    return out
+
+
+def kmer_rank_dist(counts: torch.Tensor, lengths: torch.Tensor, delta_den: int = 10, k: int = 3,
+                   alphabet: int = 20, plan: RankPlan | None = None, depth: int = 0,
+                   word_max: torch.Tensor | None = None, ws: Workspace | None = None,
+                   stream=None, check: bool = True):
+    """Eq. 2 / Eq. 3 literally: the mean of d = -ln(1/delta_den + F) over the set.
+    Returns (key int64, key_hi, key_lo, rank float64); (key_hi, key_lo) order as
+    the signed key, for partition."""
+    n = counts.shape[0]
+    dev = counts.device
+    ws = ws or Workspace(dev)
+    if plan is None:
+        plan = kmer_rank_plan(counts, k, alphabet, depth, ws, stream)
+    ws.ensure(int(_load().kmer_rank_dist_workspace_bytes(ctypes.byref(plan), n, k, alphabet,
+                                                         delta_den)))
+    key = torch.empty(n, dtype=torch.int64, device=dev)
+    hi = torch.empty(n, dtype=torch.uint64, device=dev)
+    lo = torch.empty(n, dtype=torch.uint64, device=dev)
+    rank = torch.empty(n, dtype=torch.float64, device=dev)
+    lengths = lengths.to(device=dev, dtype=torch.int32).contiguous()
+    _check(_load().kmer_rank_dist(_ptr(counts), _ptr(lengths), _ptr(word_max), n, k, alphabet,
+                                  delta_den, ctypes.byref(plan), _ptr(key), _ptr(hi), _ptr(lo),
+                                  _ptr(rank), _ptr(ws.buf), ws.nbytes, _stream(stream)),
+           "kmer_rank_dist")
+    if check:
+        ws.check("kmer_rank_dist", stream)
+    return key, hi, lo, rank
 
 
 class GlobalRank:
@@ -409,13 +457,14 @@ class GlobalRank:
 
     def __init__(self, counts: torch.Tensor, lengths: torch.Tensor, p: int, ks: int,
                  k: int = 3, alphabet: int = 20, word_max: torch.Tensor | None = None,
-                 local_depth: int = 0, stream=None):
+                 local_depth: int = 0, stream=None, delta_den: int = 0):
         import numpy as np
         n = counts.shape[0]
         dev = counts.device
         if not 1 <= p <= n or ks < 1:
             raise ValueError("need 1 <= p <= N and ks >= 1")
         self.counts, self.word_max, self.p, self.ks = counts, word_max, p, ks
+        self.delta_den = int(delta_den)
         self.k, self.alphabet, self.n = k, alphabet, n
         self.lengths = lengths.to(device=dev, dtype=torch.int32).contiguous()
         self.h_n = np.ascontiguousarray(np.diff(block_bounds(n, p)), dtype=np.int32)
@@ -440,7 +489,8 @@ class GlobalRank:
         self.ws_vs = Workspace(dev)
         self.vs_plan = kmer_rank_plan(counts, k, alphabet, 0, self.ws_vs, stream)
         self.ws_vs.ensure(int(_load().kmer_rank_vs_workspace_bytes(
-            ctypes.byref(self.vs_plan), n, k, alphabet, p * ks)))
+            ctypes.byref(self.vs_plan), n, k, alphabet, p * ks, self.delta_den)))
+        self.key = torch.empty(n, dtype=torch.int64, device=dev) if self.delta_den else None
         self.ws_samp = Workspace(dev, int(_load().sad_local_samples_workspace_bytes(n, p)))
         self.local_hi = torch.empty(n, dtype=torch.uint64, device=dev)
         self.local_lo = torch.empty(n, dtype=torch.uint64, device=dev)
@@ -463,9 +513,10 @@ class GlobalRank:
                                      self.ws_samp.nbytes, st), "sad_local_samples")
         _check(lib.kmer_rank_vs(_ptr(self.counts), _ptr(self.lengths), _ptr(self.word_max),
                                 self.n, self.k, self.alphabet, _ptr(self.samples),
-                                self.p * self.ks, ctypes.byref(self.vs_plan), _ptr(self.key_hi),
-                                _ptr(self.key_lo), _ptr(self.rank), _ptr(self.ws_vs.buf),
-                                self.ws_vs.nbytes, st), "kmer_rank_vs")
+                                self.p * self.ks, self.delta_den, ctypes.byref(self.vs_plan),
+                                _ptr(self.key), _ptr(self.key_hi), _ptr(self.key_lo),
+                                _ptr(self.rank), _ptr(self.ws_vs.buf), self.ws_vs.nbytes, st),
+               "kmer_rank_vs")
 
     def check(self, stream=None):
         self.ws_local.check("local ranks", stream)

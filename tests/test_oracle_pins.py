@@ -396,3 +396,16 @@ def test_rank_dist_orders_against_similarity(oracle_mod):
     key, _ = oracle_mod.rank_dist(c, s.lengths, 10)
     assert key[0] == key[1]
     assert key[0] < key[2] < key[3]
+
+
+def test_rank_vs_dist_every_sequence_is_rank_dist(oracle_mod):
+    s = datagen.random_small(30, 3, 150, seed=32)
+    c = oracle_mod.kmer_count(s.codes, s.offsets)
+    k0, r0 = oracle_mod.rank_dist(c, s.lengths, 10)
+    k1, r1 = oracle_mod.rank_vs_dist(c, s.lengths, 10, np.arange(s.n)[::-1])
+    np.testing.assert_array_equal(k0, k1)
+    np.testing.assert_array_equal(r0, r1)
+    # a reference listed twice counts twice
+    k2, _ = oracle_mod.rank_vs_dist(c, s.lengths, 10, [4, 4])
+    k3, _ = oracle_mod.rank_vs_dist(c, s.lengths, 10, [4])
+    np.testing.assert_array_equal(k2, 2 * k3)
