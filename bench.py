@@ -17,6 +17,9 @@ Prints one JSON line. Extra objects:
   globalised    the globalised rank of Sec. 3.1.1 on the same set (local ranks,
                 p - 1 samples per block, rank against the samples), timed, and
                 how its buckets compare with the centralised ones
+  distance_form the rank of Eq. 2 / Eq. 3 as written (mean -ln(1/10 + F)), timed
+  table1_synthetic  the statistics of Table 1 (centralised vs globalised ranks in
+                the distance form) on a synthetic 500-sequence family set
 
 --impl reference times the CPU oracle on the same workload instead (one bounded
 sample per step). Under torchrun each rank runs an independent replica of the
@@ -65,7 +68,7 @@ def parse():
                     help="threshold-plane depth (default: the autotuner's choice)")
     ap.add_argument("--no-batching", action="store_true")
     ap.add_argument("--no-global", action="store_true",
-                    help="skip the globalised-rank leg (Sec. 3.1.1)")
+                    help="skip the globalised-rank, distance-form and Table 1 legs")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-warmup", type=int, default=200)
@@ -373,6 +376,73 @@ def run_global(args, dev, counts, lengths, word_max, keys, p, reps: int = 10):
             "max_bucket": int((offs_g[1:] - offs_g[:-1]).max())}
 
 
+def run_distance(args, dev, counts, lengths, word_max, depth, reps: int = 5):
+    """Eq. 2 / Eq. 3 as written (mean of -ln(1/b + F), b = 10) on the same set and
+    plane depth: one plan, then timed kmer_rank_dist calls (CUDA events, L2
+    flushed between runs)."""
+    import torch
+
+    from paper_0905_1744_gb300 import sad
+    b = 10
+    ws = sad.Workspace(dev)
+    plan = sad.kmer_rank_plan(counts, depth=depth, ws=ws)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(2):
+        out = sad.kmer_rank_dist(counts, lengths, b, plan=plan, word_max=word_max, ws=ws)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(reps)]
+    for e0, e1 in evs:
+        flush.zero_()
+        e0.record(stream)
+        out = sad.kmer_rank_dist(counts, lengths, b, plan=plan, word_max=word_max, ws=ws,
+                                 check=False)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ws.check("kmer_rank_dist")
+    ms = statistics.median([a.elapsed_time(c) for a, c in evs])
+    n = counts.shape[0]
+    rank = out[3]
+    return {"delta": f"1/{b}", "depth": depth, "ms_per_rank": ms,
+            "pairs_per_s": n * (n - 1) / 2 / (ms / 1e3),
+            "rank_nats": {"min": float(rank.min()), "max": float(rank.max()),
+                          "mean": float(rank.mean())}}
+
+
+def run_table1(args, dev, seed: int = 0):
+    """A synthetic re-run of the comparison of Table 1 (Sec. 3.1.1): 500 sequences
+    in 10 families, distance-form ranks (Delta = 1/10) against all sequences
+    (centralised) and against 8 samples from each of 4 blocks (globalised)."""
+    import torch
+
+    from paper_0905_1744_gb300 import sad
+    s = datagen.family_set(10, 50, lambda r: int(np.clip(r.normal(300, 100), 50, 1000)), p=4,
+                           seed=seed, stream=41, name="table1")
+    codes = torch.from_numpy(s.codes).to(dev)
+    offsets = torch.from_numpy(s.offsets).to(dev)
+    lengths = torch.from_numpy(s.lengths.astype(np.int32)).to(dev)
+    word_max = torch.empty(8000, dtype=torch.int32, device=dev)
+    counts = sad.kmer_count(codes, offsets, word_max=word_max)
+    _, _, _, central = sad.kmer_rank_dist(counts, lengths, 10, word_max=word_max)
+    g = sad.GlobalRank(counts, lengths, 4, 8, word_max=word_max, delta_den=10)
+    g.run()
+    g.check()
+    c, gl = central.cpu().numpy(), g.rank.cpu().numpy()
+    diff = gl - c
+    return {"workload": "500 sequences in 10 families (ancestor L ~ N(300,100) clipped to "
+                        "50-1000, 20-40% substitutions, 2% indels), k = 3, Delta = 1/10; "
+                        "globalised: p = 4 blocks, 8 samples each",
+            "central_max_min": [float(c.max()), float(c.min())],
+            "central_mean": float(c.mean()),
+            "global_max_min": [float(gl.max()), float(gl.min())],
+            "global_mean": float(gl.mean()),
+            "variance_wrt_central": float(np.mean(diff ** 2)),
+            "std_wrt_central": float(np.sqrt(np.mean(diff ** 2))),
+            "pearson": float(np.corrcoef(c, gl)[0, 1]),
+            "spearman": float(np.corrcoef(np.argsort(np.argsort(c)),
+                                          np.argsort(np.argsort(gl)))[0, 1])}
+
+
 def run_serving(args, dev, depth):
     """Poisson arrivals of sets (N log-uniform 100-20000, p = 16) served with
     continuous batching under a 150 GB HBM budget, and the same arrivals served
@@ -565,9 +635,11 @@ def run_sad(args):
                "d2h_bytes_per_step": int(4 * n + 4 * (p + 1) + 16 * n),
                "ms_per_step": 1e3 * t_e2e}
 
-    globalised = None
+    globalised = distance = table1 = None
     if not args.no_global and world == 1:
         globalised = run_global(args, dev, counts, lengths, word_max, keys, p)
+        distance = run_distance(args, dev, counts, lengths, word_max, depth)
+        table1 = run_table1(args, dev, args.seed)
     batching = None
     if not args.no_batching:
         batching = run_batching(args, dev)
@@ -601,6 +673,8 @@ def run_sad(args):
             "e2e": e2e,
             "clocks": clocks,
             "globalised": globalised,
+            "distance_form": distance,
+            "table1_synthetic": table1,
             "batching": batching,
             "serving": serving,
             "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms),

@@ -111,3 +111,20 @@ def test_rank_vs_distance_every_sequence_is_rank_dist(sad):
                                     delta_den=10)
     np.testing.assert_array_equal(host(k0), host(k1))
     np.testing.assert_array_equal(host(r0), host(r1))
+
+
+def test_global_rank_distance_form_matches_oracle(sad, oracle_mod):
+    """Steps 2-6 with the re-rank in the distance form: local ranks (similarity
+    form) pick the samples, then every sequence against them in Eq. 2's form."""
+    s = family(500, 14)
+    c = oracle_mod.kmer_count(s.codes, s.offsets)
+    counts = sad.kmer_count(dev(s.codes), dev(s.offsets))
+    g = sad.GlobalRank(counts, dev(s.lengths.astype(np.int32)), 4, 8, delta_den=10)
+    g.run()
+    g.check()
+    lh, ll = oracle_mod.local_ranks(c, s.lengths, 4)
+    samples = oracle_mod.local_samples(lh, ll, 4, 8)
+    np.testing.assert_array_equal(host(g.samples), samples)
+    okey, orank = oracle_mod.rank_vs_dist(c, s.lengths, 10, samples)
+    np.testing.assert_array_equal(host(g.key), okey)
+    np.testing.assert_array_equal(host(g.rank), orank)
