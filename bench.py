@@ -20,6 +20,8 @@ Prints one JSON line. Extra objects:
   distance_form the rank of Eq. 2 / Eq. 3 as written (mean -ln(1/10 + F)), timed
   table1_synthetic  the statistics of Table 1 (centralised vs globalised ranks in
                 the distance form) on a synthetic 500-sequence family set
+  sparse_ablation  the same keys by sparse intersection on the CUDA cores (the
+                per-pair cost of Table 2), against the plane-GEMM rank time
 
 --impl reference times the CPU oracle on the same workload instead (one bounded
 sample per step). Under torchrun each rank runs an independent replica of the
@@ -409,6 +411,33 @@ def run_distance(args, dev, counts, lengths, word_max, depth, reps: int = 5):
                           "mean": float(rank.mean())}}
 
 
+def run_sparse(args, dev, counts, lengths, rank_ms, reps: int = 2):
+    """The ablation of Table 2's per-pair cost: the same keys by sparse
+    intersection on the CUDA cores (O(L) per pair, every ordered pair), timed
+    with CUDA events on the same set, beside the plane-GEMM rank time."""
+    import torch
+
+    from paper_0905_1744_gb300 import sad
+    ws = sad.Workspace(dev)
+    entries = sad.sparse_entries(counts, lengths, ws=ws)
+    sad.kmer_rank_sparse(counts, lengths, ws=ws, entries=entries)
+    stream = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(reps)]
+    for e0, e1 in evs:
+        e0.record(stream)
+        sad.kmer_rank_sparse(counts, lengths, ws=ws, entries=entries, check=False)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ws.check("kmer_rank_sparse")
+    ms = statistics.median([a.elapsed_time(b) for a, b in evs])
+    n = counts.shape[0]
+    return {"kind": "sparse intersection on CUDA cores (every ordered pair)",
+            "list_entries": int(entries), "ms_per_rank": ms,
+            "pairs_per_s": n * (n - 1) / 2 / (ms / 1e3),
+            "plane_gemm_rank_ms": rank_ms, "plane_gemm_speedup": ms / rank_ms}
+
+
 def run_table1(args, dev, seed: int = 0):
     """A synthetic re-run of the comparison of Table 1 (Sec. 3.1.1): 500 sequences
     in 10 families, distance-form ranks (Delta = 1/10) against all sequences
@@ -635,10 +664,11 @@ def run_sad(args):
                "d2h_bytes_per_step": int(4 * n + 4 * (p + 1) + 16 * n),
                "ms_per_step": 1e3 * t_e2e}
 
-    globalised = distance = table1 = None
+    globalised = distance = table1 = sparse = None
     if not args.no_global and world == 1:
         globalised = run_global(args, dev, counts, lengths, word_max, keys, p)
         distance = run_distance(args, dev, counts, lengths, word_max, depth)
+        sparse = run_sparse(args, dev, counts, lengths, trials.get(depth))
         table1 = run_table1(args, dev, args.seed)
     batching = None
     if not args.no_batching:
@@ -675,6 +705,7 @@ def run_sad(args):
             "globalised": globalised,
             "distance_form": distance,
             "table1_synthetic": table1,
+            "sparse_ablation": sparse,
             "batching": batching,
             "serving": serving,
             "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms),

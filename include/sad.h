@@ -386,6 +386,29 @@ int kmer_rank_dist(const int32_t *d_counts, const int32_t *d_lengths, const int3
  */
 int sad_ln_q(const uint64_t *d_x, int64_t n, int64_t *d_out, void *stream);
 
+/*
+ * kmer_rank_sparse - the kmer_rank keys (same definition, bit for bit) computed by
+ * sparse intersection on the CUDA cores instead of the threshold-plane GEMM: the
+ * per-pair cost of Table 2, O(L) per pair (one sequence's list of occurring words
+ * against the other's counts), every ordered pair evaluated. A comparison point
+ * for the tensor-core path, not a faster one.
+ * kmer_rank_sparse_entries - SYNCHRONOUS: the total number of (sequence, word)
+ *   entries with a nonzero count, the capacity kmer_rank_sparse needs; its
+ *   workspace must hold kmer_rank_sparse_workspace_bytes(n_seq, 0) bytes.
+ *   entries_cap  at least that total (SAD_ERR_WORKSPACE recorded otherwise).
+ *   d_ws       kmer_rank_sparse_workspace_bytes(n_seq, entries_cap) bytes.
+ *   eps = alphabet^k up to 65536 (a 16-bit shared histogram of eps bins per CTA).
+ * Other arguments as for kmer_rank.
+ */
+size_t kmer_rank_sparse_workspace_bytes(int32_t n_seq, int64_t entries_cap);
+int kmer_rank_sparse_entries(const int32_t *d_counts, const int32_t *d_lengths, int32_t n_seq,
+                             int32_t k, int32_t alphabet, int64_t *entries, void *d_ws,
+                             size_t ws_bytes, void *stream);
+int kmer_rank_sparse(const int32_t *d_counts, const int32_t *d_lengths, int32_t n_seq,
+                     int32_t k, int32_t alphabet, int64_t entries_cap, uint64_t *d_key_hi,
+                     uint64_t *d_key_lo, double *d_rank, void *d_ws, size_t ws_bytes,
+                     void *stream);
+
 /* Number of kernels this library has launched in this process. */
 uint64_t sad_launch_count(void);
 

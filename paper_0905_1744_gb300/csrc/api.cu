@@ -376,6 +376,44 @@ int kmer_rank_dist(const int32_t *d_counts, const int32_t *d_lengths, const int3
   return rank_dist_finalize_launch(P, d_key, d_key_hi, d_key_lo, d_rank, 0, st);
 }
 
+size_t kmer_rank_sparse_workspace_bytes(int32_t n_seq, int64_t entries_cap) {
+  if (n_seq < 1 || entries_cap < 0) return 0;
+  return sparse_ws_bytes(n_seq, entries_cap);
+}
+
+int kmer_rank_sparse_entries(const int32_t *d_counts, const int32_t *d_lengths, int32_t n_seq,
+                             int32_t k, int32_t alphabet, int64_t *entries, void *d_ws,
+                             size_t ws_bytes, void *stream) {
+  const int64_t eps = eps_of(k, alphabet);
+  if (eps < 0) return SAD_ERR_UNSUPPORTED;
+  if (n_seq < 1 || !d_counts || !d_lengths || !entries || !d_ws || !aligned(d_ws, 256))
+    return SAD_ERR_INVALID_ARGUMENT;
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc = sparse_count_launch(d_counts, d_lengths, n_seq, k, (int32_t)eps, d_ws, ws_bytes, st);
+  if (rc) return rc;
+  WsHeader h;
+  rc = check_cuda(cudaMemcpyAsync(&h, d_ws, sizeof(h), cudaMemcpyDeviceToHost, st));
+  if (rc) return rc;
+  rc = check_cuda(cudaStreamSynchronize(st));
+  if (rc) return rc;
+  if (h.status != 0) return h.status;
+  *entries = h.list_total;
+  return SAD_OK;
+}
+
+int kmer_rank_sparse(const int32_t *d_counts, const int32_t *d_lengths, int32_t n_seq,
+                     int32_t k, int32_t alphabet, int64_t entries_cap, uint64_t *d_key_hi,
+                     uint64_t *d_key_lo, double *d_rank, void *d_ws, size_t ws_bytes,
+                     void *stream) {
+  const int64_t eps = eps_of(k, alphabet);
+  if (eps < 0) return SAD_ERR_UNSUPPORTED;
+  if (n_seq < 1 || entries_cap < 0 || !d_counts || !d_lengths || !d_key_hi || !d_key_lo ||
+      !d_ws || !aligned(d_ws, 256))
+    return SAD_ERR_INVALID_ARGUMENT;
+  return sparse_rank_launch(d_counts, d_lengths, n_seq, k, (int32_t)eps, entries_cap, d_key_hi,
+                            d_key_lo, d_rank, d_ws, ws_bytes, static_cast<cudaStream_t>(stream));
+}
+
 int sad_ln_q(const uint64_t *d_x, int64_t n, int64_t *d_out, void *stream) {
   if (n < 0 || (n > 0 && (!d_x || !d_out))) return SAD_ERR_INVALID_ARGUMENT;
   return ln_q_launch(d_x, n, d_out, static_cast<cudaStream_t>(stream));

@@ -6,6 +6,24 @@
 
 namespace sad {
 
+// Division record for denominator d (1..65535), used by the GEMM epilogue (and the
+// sparse ablation) to
+// form floor(S * 2^64 / d) = S * Q + floor(S * r / d) exactly, with
+// Q = floor((2^64 - 1) / d), r = 2^64 - Q d in [1, d], and floor(x / d) for
+// x < 2^32 by Granlund & Montgomery (1994), "Division by invariant integers
+// using multiplication", Fig. 4.1: l = ceil(log2 d),
+// m' = floor(2^32 (2^l - d) / d) + 1, t1 = umulhi(m', x),
+// q = (t1 + ((x - t1) >> min(l,1))) >> max(l-1, 0).
+__device__ __forceinline__ uint4 division_record(uint32_t d) {
+  const uint64_t Q = 0xFFFFFFFFFFFFFFFFull / d;
+  const uint32_t l = 32u - (uint32_t)__clz((int)(d - 1u));
+  const uint64_t magic = (((uint64_t)1 << 32) * (((uint64_t)1 << l) - d)) / d + 1u;
+  const uint32_t sh1 = l < 1u ? l : 1u;
+  const uint32_t sh2 = l > 0u ? l - 1u : 0u;
+  return make_uint4((uint32_t)Q, (uint32_t)(Q >> 32), (uint32_t)magic,
+                    d | (sh1 << 16) | (sh2 << 24));
+}
+
 struct RankPtrs {
   WsHeader *hdr;
   RankSet *sets;         // [n_sets]
@@ -87,6 +105,14 @@ int rank_vs_launch(const int32_t *counts, const int32_t *lengths, const int32_t 
                    int32_t n, int32_t k, int64_t eps, const int32_t *ref, int32_t n_ref,
                    int64_t k_cap, int32_t delta_den, int64_t *key, uint64_t *key_hi,
                    uint64_t *key_lo, double *rank, void *ws, size_t ws_bytes, cudaStream_t st);
+
+// Sparse-intersection rank on the CUDA cores (sparse.cu).
+size_t sparse_ws_bytes(int64_t n, int64_t entries_cap);
+int sparse_count_launch(const int32_t *counts, const int32_t *lengths, int32_t n, int32_t k,
+                        int32_t eps, void *ws, size_t ws_bytes, cudaStream_t st);
+int sparse_rank_launch(const int32_t *counts, const int32_t *lengths, int32_t n, int32_t k,
+                       int32_t eps, int64_t entries_cap, uint64_t *key_hi, uint64_t *key_lo,
+                       double *rank, void *ws, size_t ws_bytes, cudaStream_t st);
 
 // TMA map of a plane matrix (rows x K_cap / 2 bytes, 128-byte swizzle, boxes of
 // 128 bytes x box_rows rows).

@@ -555,23 +555,6 @@ __global__ void __launch_bounds__(1024) lensort_scan_kernel(RankPtrs P) {
   }
 }
 
-// Division record for denominator d (1..65535), used by the GEMM epilogue to
-// form floor(S * 2^64 / d) = S * Q + floor(S * r / d) exactly, with
-// Q = floor((2^64 - 1) / d), r = 2^64 - Q d in [1, d], and floor(x / d) for
-// x < 2^32 by Granlund & Montgomery (1994), "Division by invariant integers
-// using multiplication", Fig. 4.1: l = ceil(log2 d),
-// m' = floor(2^32 (2^l - d) / d) + 1, t1 = umulhi(m', x),
-// q = (t1 + ((x - t1) >> min(l,1))) >> max(l-1, 0).
-__device__ __forceinline__ uint4 division_record(uint32_t d) {
-  const uint64_t Q = 0xFFFFFFFFFFFFFFFFull / d;
-  const uint32_t l = 32u - (uint32_t)__clz((int)(d - 1u));
-  const uint64_t magic = (((uint64_t)1 << 32) * (((uint64_t)1 << l) - d)) / d + 1u;
-  const uint32_t sh1 = l < 1u ? l : 1u;
-  const uint32_t sh2 = l > 0u ? l - 1u : 0u;
-  return make_uint4((uint32_t)Q, (uint32_t)(Q >> 32), (uint32_t)magic,
-                    d | (sh1 << 16) | (sh2 << 24));
-}
-
 // One set: stored row of every sequence from the counting sort over m.
 __global__ void lensort_place_kernel(const int32_t *__restrict__ lengths, int32_t k,
                                      RankPtrs P) {

@@ -114,6 +114,13 @@ def _load():
         lib.kmer_rank_dist.restype = ctypes.c_int
         lib.sad_ln_q.argtypes = [P, i64, P, P]
         lib.sad_ln_q.restype = ctypes.c_int
+        lib.kmer_rank_sparse_workspace_bytes.argtypes = [i32, i64]
+        lib.kmer_rank_sparse_workspace_bytes.restype = sz
+        lib.kmer_rank_sparse_entries.argtypes = [P, P, i32, i32, i32, ctypes.POINTER(i64), P, sz,
+                                                 P]
+        lib.kmer_rank_sparse_entries.restype = ctypes.c_int
+        lib.kmer_rank_sparse.argtypes = [P, P, i32, i32, i32, i64, P, P, P, P, sz, P]
+        lib.kmer_rank_sparse.restype = ctypes.c_int
         lib.sad_profile.argtypes = [i32]
         lib.sad_profile.restype = ctypes.c_int
         lib.sad_profile_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
@@ -447,6 +454,45 @@ def kmer_rank_dist(counts: torch.Tensor, lengths: torch.Tensor, delta_den: int =
     if check:
         ws.check("kmer_rank_dist", stream)
     return key, hi, lo, rank
+
+
+def sparse_entries(counts: torch.Tensor, lengths: torch.Tensor, k: int = 3, alphabet: int = 20,
+                   ws: Workspace | None = None, stream=None) -> int:
+    """(sequence, word) entries with a nonzero count: the list capacity of
+    kmer_rank_sparse. Synchronous."""
+    n = counts.shape[0]
+    ws = ws or Workspace(counts.device)
+    ws.ensure(int(_load().kmer_rank_sparse_workspace_bytes(n, 0)))
+    lengths = lengths.to(device=counts.device, dtype=torch.int32).contiguous()
+    e = ctypes.c_int64()
+    _check(_load().kmer_rank_sparse_entries(_ptr(counts), _ptr(lengths), n, k, alphabet,
+                                            ctypes.byref(e), _ptr(ws.buf), ws.nbytes,
+                                            _stream(stream)), "kmer_rank_sparse_entries")
+    return int(e.value)
+
+
+def kmer_rank_sparse(counts: torch.Tensor, lengths: torch.Tensor, k: int = 3,
+                     alphabet: int = 20, ws: Workspace | None = None, stream=None,
+                     entries: int | None = None, check: bool = True):
+    """The kmer_rank keys by sparse intersection on the CUDA cores (the O(L)-per-pair
+    comparison point of Table 2). ``entries``: the list capacity (sized here,
+    synchronously, if None). Returns (key_hi, key_lo, rank)."""
+    n = counts.shape[0]
+    dev = counts.device
+    ws = ws or Workspace(dev)
+    lengths = lengths.to(device=dev, dtype=torch.int32).contiguous()
+    if entries is None:
+        entries = sparse_entries(counts, lengths, k, alphabet, ws, stream)
+    ws.ensure(int(_load().kmer_rank_sparse_workspace_bytes(n, entries)))
+    hi = torch.empty(n, dtype=torch.uint64, device=dev)
+    lo = torch.empty(n, dtype=torch.uint64, device=dev)
+    rank = torch.empty(n, dtype=torch.float64, device=dev)
+    _check(_load().kmer_rank_sparse(_ptr(counts), _ptr(lengths), n, k, alphabet, entries,
+                                    _ptr(hi), _ptr(lo), _ptr(rank), _ptr(ws.buf), ws.nbytes,
+                                    _stream(stream)), "kmer_rank_sparse")
+    if check:
+        ws.check("kmer_rank_sparse", stream)
+    return hi, lo, rank
 
 
 class GlobalRank:
