@@ -13,6 +13,8 @@
 //   scatter        step 11: move every item to its bucket
 //   seg_sort       each bucket sorted by (key, index)
 //   members        output input indices
+// One set with few buckets takes a faster route (chunk sorts and rank merges,
+// below) to the same result.
 //
 // Sorting inside one CTA: a bitonic network in shared memory for up to 4096
 // items; longer ranges sort 4096-item chunks that way and then merge runs of
@@ -247,6 +249,79 @@ __global__ void scatter_kernel(const Item *items, Item *out, const int32_t *pos_
   }
 }
 
+// ---------------------------------------------------------------------------
+// One set with p <= kFastP and blocks of at most kFastChunks chunks: more CTAs and
+// no second sort. Each block's chunks of kChunk items are sorted by one CTA each,
+// and an item's place in its sorted block is its place in its chunk plus the
+// number of smaller items in each other chunk (binary searches; all items differ).
+// After the pivots, the items of bucket i arrive as p sorted runs (its sub-block
+// of every block), so an item's place in its bucket is, the same way, its place
+// in its run plus the smaller items of the other runs; members are written there.
+constexpr int kChunk = 256;
+constexpr int kFastChunks = 64;
+constexpr int kFastP = 64;
+
+// (blockIdx.y = block b, blockIdx.x = chunk of the block): sort it in place.
+__global__ void __launch_bounds__(128) chunk_sort_kernel(Item *items, const int64_t *segoff) {
+  __shared__ Item sm[kChunk];
+  const int64_t a = segoff[blockIdx.y], e = segoff[blockIdx.y + 1];
+  const int64_t lo = a + (int64_t)blockIdx.x * kChunk;
+  if (lo >= e) return;
+  cta_sort_small(items + lo, (int)min((int64_t)kChunk, e - lo), sm);
+}
+
+__device__ __forceinline__ int64_t block_of_item(int64_t x, int64_t n, int64_t p) {
+  int64_t b = x * p / n;
+  while (b + 1 < p && block_lo(b + 1, n, p) <= x) ++b;
+  while (b > 0 && block_lo(b, n, p) > x) --b;
+  return b;
+}
+
+__global__ void chunk_merge_kernel(const Item *__restrict__ in, Item *__restrict__ out,
+                                   int64_t n, int64_t p) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = block_of_item(x, n, p);
+    const int64_t lo = block_lo(b, n, p), e = block_lo(b + 1, n, p);
+    const int64_t c = (x - lo) / kChunk;
+    const Item it = in[x];
+    int64_t rank = x - (lo + c * kChunk);
+    for (int64_t c2 = 0; lo + c2 * kChunk < e; ++c2) {
+      if (c2 == c) continue;
+      const int64_t a = lo + c2 * kChunk;
+      rank += count_less(in + a, min((int64_t)kChunk, e - a), it);
+    }
+    out[lo + rank] = it;
+  }
+}
+
+// Items of the sorted blocks -> members in bucket order (offsets of the set in boff).
+__global__ void bucket_place_kernel(const Item *__restrict__ sorted, const int32_t *pos,
+                                    const int32_t *boff, int32_t *members, int64_t n,
+                                    int64_t p) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = block_of_item(x, n, p);
+    const int64_t e = x - block_lo(b, n, p);
+    const int32_t *pb = pos + b * p;
+    int lo = 0, hi = (int)p - 1;  // bucket: first i with e < pos[b][i]
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (e < pb[mid]) hi = mid; else lo = mid + 1;
+    }
+    const int i = lo;
+    const Item it = sorted[x];
+    int64_t rank = e - (i > 0 ? pb[i - 1] : 0);
+    for (int64_t b2 = 0; b2 < p; ++b2) {
+      if (b2 == b) continue;
+      const int32_t *q = pos + b2 * p;
+      const int64_t a = block_lo(b2, n, p) + (i > 0 ? q[i - 1] : 0);
+      rank += count_less(sorted + a, q[i] - (i > 0 ? q[i - 1] : 0), it);
+    }
+    members[boff[i] + rank] = it.idx;
+  }
+}
+
 __global__ void members_kernel(const Item *items, int32_t *members, int64_t n) {
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
        x += (int64_t)gridDim.x * blockDim.x)
@@ -301,6 +376,32 @@ int partition_sets_launch(const uint64_t *key_hi, const uint64_t *key_lo, int32_
   SAD_LAUNCH_CHECK();
   part_init_kernel<<<grid_for(n, 256), 256, 0, st>>>(key_hi, key_lo, n, sets, n_sets, items);
   SAD_LAUNCH_CHECK();
+  // one set of small blocks and few buckets: chunk sorts and rank merges
+  const int64_t w_max = d_n || p_single < 1 ? 0 : ((int64_t)n_single + p_single - 1) / p_single;
+  if (!d_n && n_single > 0 && p_single <= kFastP && w_max <= (int64_t)kFastChunks * kChunk) {
+    dim3 gc((unsigned)((w_max + kChunk - 1) / kChunk), (unsigned)p_single);
+    chunk_sort_kernel<<<gc, 128, 0, st>>>(items, segoff);
+    SAD_LAUNCH_CHECK();
+    chunk_merge_kernel<<<grid_for(n, 256), 256, 0, st>>>(items, items2, n, p_single);
+    SAD_LAUNCH_CHECK();
+    if (max_p > 1) {
+      samples_kernel<<<gsets, kSortThreads, kSortSmem, st>>>(items2, Y, Y2, piv, pivot_idx, sets,
+                                                             n_sets);
+      SAD_LAUNCH_CHECK();
+    }
+    {
+      const int64_t pp = (int64_t)max_p * max_p;
+      dim3 g((unsigned)((pp + 255) / 256 < 1024 ? (pp + 255) / 256 : 1024), (unsigned)n_sets);
+      subblocks_kernel<<<g, 256, 0, st>>>(items2, piv, pos, sets);
+      SAD_LAUNCH_CHECK();
+    }
+    bucket_scan_kernel<<<gsets, 1024, 0, st>>>(pos, dest, bucket_offsets, gbound, sets, n_sets);
+    SAD_LAUNCH_CHECK();
+    bucket_place_kernel<<<grid_for(n, 256), 256, 0, st>>>(items2, pos, bucket_offsets, members,
+                                                          n, p_single);
+    SAD_LAUNCH_CHECK();
+    return SAD_OK;
+  }
   seg_sort_kernel<<<gseg, kSortThreads, kSortSmem, st>>>(items, items2, tot.p, segoff);
   SAD_LAUNCH_CHECK();
   if (max_p > 1) {

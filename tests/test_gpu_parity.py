@@ -166,7 +166,11 @@ def test_rank_rejects_inconsistent_lengths(sad):
                                           (20000, 16, None), (100000, 64, None),
                                           (100000, 64, 50), (4097 * 3, 3, None),
                                           (30000, 2, 1000), (57, 57, None), (77, 1, None),
-                                          (5000, 100, None), (1, 1, None)])
+                                          (5000, 100, None), (1, 1, None),
+                                          # the bounds of the chunk-merge route (p <= 64,
+                                          # blocks of at most 64 x 256 items)
+                                          (6500, 65, None), (6400, 64, 3), (16384, 1, None),
+                                          (16385, 1, None), (40000, 2, 7), (300, 64, None)])
 def test_partition_matches_oracle(sad, oracle_mod, n, p, distinct):
     hi, lo = datagen.random_keys(n, seed=n * 7 + p, distinct=distinct)
     offs, mem, piv = sad.partition(dev(hi), dev(lo), p)
