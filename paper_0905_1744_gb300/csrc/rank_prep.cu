@@ -920,7 +920,7 @@ __global__ void __launch_bounds__(256) planes_stream_kernel(const int32_t *__res
   }
 }
 
-// Upper-triangle tile list of every set (one block per set). Tile (I, J) of a
+// Upper-triangle tile list of every set (blocks per set and column group). Tile (I, J) of a
 // set covers its stored rows [128 I, 128 I + 128) and columns [128 J, 128 J + 128)
 // (set-local, kColBlock = 128); it is needed when some pair i <= j lies in it
 // (I <= J) and both ranges hold real rows. Tiles are grouped by kGroupCols column blocks,
@@ -929,13 +929,21 @@ __global__ void __launch_bounds__(256) planes_stream_kernel(const int32_t *__res
 // block indices, the K extent being the end of section min(depth(I), depth(J), D).
 constexpr int kGroupCols = 8;
 
-__global__ void __launch_bounds__(1024) tiles_kernel(RankPtrs P) {
+// Tiles of column group g of a set: rows I with J in [8g, 8g + 8) and J >= I / kColRatio.
+__device__ __forceinline__ int32_t group_row_tiles(int32_t g, int32_t I, int32_t C) {
+  const int32_t j0 = max(g * kGroupCols, I / kColRatio);
+  const int32_t j1 = min((g + 1) * kGroupCols, C);
+  return max(0, j1 - j0);
+}
+
+// (blockIdx.y: sets in a grid stride; blockIdx.x: column groups in a grid stride)
+__global__ void __launch_bounds__(256) tiles_kernel(RankPtrs P) {
   __shared__ int32_t s_warp[32];
   __shared__ int32_t s_carry;
   const int tid = threadIdx.x;
   const int32_t nblk = (int32_t)(P.n_pad / kRowBlock);
   const int32_t dkeep = P.hdr->depth;
-  for (int32_t si = blockIdx.x; si < (int32_t)P.n_sets; si += gridDim.x) {
+  for (int32_t si = blockIdx.y; si < (int32_t)P.n_sets; si += gridDim.y) {
     const RankSet e = P.sets[si];
     const int32_t n = e.n;
     const int32_t R = (n + kRowBlock - 1) / kRowBlock;
@@ -943,44 +951,48 @@ __global__ void __launch_bounds__(1024) tiles_kernel(RankPtrs P) {
     const int64_t cfull = dev_n_pad(n) / kColBlock;
     const int32_t I0 = (int32_t)(e.row_base / kRowBlock), J0 = (int32_t)(e.row_base / kColBlock);
     const int32_t groups = (C + kGroupCols - 1) / kGroupCols;
-    if (tid == 0) s_carry = 0;
-    __syncthreads();
-    const int64_t rows_total = (int64_t)groups * R;
-    unsigned long long chunks = 0;
-    for (int64_t base = 0; base < rows_total; base += blockDim.x) {
-      const int64_t gi = base + tid;
-      int32_t I = 0, j0 = 0, j1 = 0, cnt = 0;
-      if (gi < rows_total) {
-        const int32_t g = (int32_t)(gi / R);
-        I = (int32_t)(gi % R);
-        j0 = max(g * kGroupCols, I / kColRatio);  // smallest J reaching row block I
-        j1 = min((g + 1) * kGroupCols, C);
-        cnt = max(0, j1 - j0);
-      }
+    for (int32_t g = blockIdx.x; g < groups; g += gridDim.x) {
+      // tiles of the groups before g come first
+      int32_t before = 0;
+      for (int64_t gi = tid; gi < (int64_t)g * R; gi += blockDim.x)
+        before += group_row_tiles((int32_t)(gi / R), (int32_t)(gi % R), C);
       int32_t tot;
-      const int32_t incl = block_scan_incl<int32_t>(cnt, s_warp, &tot);
-      int64_t out = e.tile_base + s_carry + incl - cnt;
-      const int32_t dI = P.depth[I0 + I];
-      for (int32_t J = j0; J < j1; ++J) {
-        // the column block spans row blocks kColRatio (J0 + J) .. + kColRatio - 1
-        int32_t dJ = 0;
-        for (int32_t b = kColRatio * (J0 + J); b < kColRatio * (J0 + J + 1) && b < nblk; ++b)
-          dJ = max(dJ, P.depth[b]);
-        const int32_t d = min(min(dI, dJ), dkeep);
-        const int32_t kend = P.secend[max(d, 0)];
-        const int32_t nk = max(1, (kend + kKCols - 1) / kKCols);
-        P.tile_of[e.tileof_base + (int64_t)I * cfull + J] = (int32_t)out;
-        P.block_of[out] = 0;
-        P.tiles[out++] = make_int2((I0 + I) | ((J0 + J) << 16), nk);
-        chunks += (unsigned long long)nk;
-      }
+      block_scan_incl<int32_t>(before, s_warp, &tot);
+      if (tid == 0) s_carry = tot;
       __syncthreads();
-      if (tid == 0) s_carry += tot;
+      unsigned long long chunks = 0;
+      int32_t group_tiles = 0;
+      for (int32_t base = 0; base < R; base += blockDim.x) {
+        const int32_t I = base + tid;
+        const int32_t cnt = I < R ? group_row_tiles(g, I, C) : 0;
+        const int32_t incl = block_scan_incl<int32_t>(cnt, s_warp, &tot);
+        int64_t out = e.tile_base + s_carry + incl - cnt;
+        if (cnt > 0) {
+          const int32_t dI = P.depth[I0 + I];
+          const int32_t j0 = max(g * kGroupCols, I / kColRatio);
+          for (int32_t J = j0; J < j0 + cnt; ++J) {
+            // the column block spans row blocks kColRatio (J0 + J) .. + kColRatio - 1
+            int32_t dJ = 0;
+            for (int32_t b = kColRatio * (J0 + J); b < kColRatio * (J0 + J + 1) && b < nblk; ++b)
+              dJ = max(dJ, P.depth[b]);
+            const int32_t d = min(min(dI, dJ), dkeep);
+            const int32_t kend = P.secend[max(d, 0)];
+            const int32_t nk = max(1, (kend + kKCols - 1) / kKCols);
+            P.tile_of[e.tileof_base + (int64_t)I * cfull + J] = (int32_t)out;
+            P.block_of[out] = 0;
+            P.tiles[out++] = make_int2((I0 + I) | ((J0 + J) << 16), nk);
+            chunks += (unsigned long long)nk;
+          }
+        }
+        __syncthreads();
+        if (tid == 0) s_carry += tot;
+        group_tiles += tot;
+        __syncthreads();
+      }
+      if (chunks) atomicAdd(&P.hdr->k_chunks, chunks);
+      if (tid == 0) atomicAdd(&P.hdr->n_tiles, group_tiles);
       __syncthreads();
     }
-    if (chunks) atomicAdd(&P.hdr->k_chunks, chunks);
-    if (tid == 0) atomicAdd(&P.hdr->n_tiles, s_carry);
-    __syncthreads();
   }
 }
 
@@ -1248,7 +1260,12 @@ int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *le
     group_lists_kernel<<<grid_for(P.list_cap, 256), 256, 0, st>>>(P, eps);
     SAD_LAUNCH_CHECK();
   }
-  tiles_kernel<<<gsets, 1024, 0, st>>>(P);
+  {
+    // one set: a CTA per column group; batches: a few per set
+    const int64_t groups1 = ((n + kColBlock - 1) / kColBlock + kGroupCols - 1) / kGroupCols;
+    dim3 g((unsigned)(P.n_sets == 1 ? (groups1 > 0 ? groups1 : 1) : 4), gsets);
+    tiles_kernel<<<g, 256, 0, st>>>(P);
+  }
   SAD_LAUNCH_CHECK();
   if (P.depth_cap >= 1 && P.block_cap > 0) {
     // the residual only exists when the planes are cut below the largest count
