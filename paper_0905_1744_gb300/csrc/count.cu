@@ -221,9 +221,9 @@ __global__ void __launch_bounds__(128) kmer_count_kernel(const uint8_t *__restri
 }
 
 template <int K>
-int launch_count(const uint8_t *codes, const int64_t *offsets, int32_t n, int32_t alphabet,
-                 int32_t eps, int32_t *counts, int32_t *word_max, WsHeader *hdr,
-                 cudaStream_t st) {
+int launch_count_warp(const uint8_t *codes, const int64_t *offsets, int32_t n, int32_t alphabet,
+                      int32_t eps, int32_t *counts, int32_t *word_max, WsHeader *hdr,
+                      cudaStream_t st) {
   const size_t per_warp = sizeof(uint32_t) * (size_t)((eps + 1) / 2);
   int warps = (int)((96 * 1024) / per_warp);
   warps = warps < 1 ? 1 : (warps > 4 ? 4 : warps);
@@ -251,6 +251,153 @@ int launch_count(const uint8_t *codes, const int64_t *offsets, int32_t n, int32_
                                                    word_max, hdr);
   SAD_LAUNCH_CHECK();
   return SAD_OK;
+}
+
+// CTA per sequence (eps divisible by 8, eps <= 8 * kCtaThreads * 4, 16-byte aligned
+// rows): the 8 warps share one shared histogram, so an SM holds several times the
+// sequences of the warp-per-sequence kernel and keeps more row stores in flight.
+// Thread t always writes the column octets o = t + kCtaThreads * pass, so the words
+// it has seen occur fit one 32-bit register (8 bits per pass); counts >= 2 go to
+// per-CTA byte maxima as in the warp kernel.
+constexpr int kCtaThreads = 256;
+
+template <int K>
+__global__ void __launch_bounds__(kCtaThreads) kmer_count_cta_kernel(
+    const uint8_t *__restrict__ codes, const int64_t *__restrict__ offsets, int32_t n,
+    int32_t alphabet, int32_t eps, int32_t *__restrict__ counts, int32_t *__restrict__ word_max,
+    WsHeader *hdr) {
+  extern __shared__ uint32_t smem[];
+  uint32_t *hist = smem;                    // [eps / 2]
+  uint32_t *max8 = smem + (eps >> 1);       // [eps / 4]
+  const int tid = threadIdx.x;
+  for (int i = tid; i < (eps >> 1); i += kCtaThreads) hist[i] = 0;
+  if (word_max)
+    for (int i = tid; i < (eps >> 2); i += kCtaThreads) max8[i] = 0;
+  uint32_t present = 0;
+  __syncthreads();
+  const int64_t codes_end = offsets[n];
+  const int octets = eps >> 3;
+  for (int64_t x = blockIdx.x; x < n; x += gridDim.x) {
+    const int64_t s = offsets[x], e = offsets[x + 1];
+    int err = 0;
+    if (s < 0 || e > codes_end || e < s) err = SAD_ERR_INVALID_ARGUMENT;
+    else if (e - s < K) err = SAD_ERR_BAD_INPUT;
+    else if (e - s - K + 1 > kMaxM) err = SAD_ERR_UNSUPPORTED;
+    bool bad = false;
+    if (err) {
+      if (tid == 0) record_error(hdr, err, (int)x);
+    } else {
+      // 16 bytes per thread per step; the k - 1 bytes past them come from the next
+      // 16-byte load (L1)
+      for (int64_t c = (s & ~(int64_t)15) + 16 * tid; c < e; c += 16 * kCtaThreads) {
+        const uint4 v = load16_guarded(codes, c, codes_end);
+        const uint4 nx = (K > 1 && c + 16 < e) ? load16_guarded(codes, c + 16, codes_end)
+                                               : make_uint4(0, 0, 0, 0);
+        const uint32_t w[8] = {v.x, v.y, v.z, v.w, nx.x, nx.y, nx.z, nx.w};
+        if (c >= s && c + 16 + K - 1 <= e) {
+          if (alphabet < 256) {
+            const uint32_t lim = 0x01010101u * (uint32_t)alphabet;
+            bad |= (__vcmpgeu4(v.x, lim) | __vcmpgeu4(v.y, lim) | __vcmpgeu4(v.z, lim) |
+                    __vcmpgeu4(v.w, lim)) != 0u;
+          }
+#pragma unroll
+          for (int b = 0; b < 16; ++b) {
+            uint32_t tau = 0;
+#pragma unroll
+            for (int r = 0; r < K; ++r) tau = tau * (uint32_t)alphabet + byte_of(w, b + r);
+            if (tau < (uint32_t)eps) atomicAdd(&hist[tau >> 1], 1u << (16 * (tau & 1)));
+          }
+        } else {
+#pragma unroll
+          for (int b = 0; b < 16; ++b) {
+            const int64_t pos = c + b;
+            if (pos >= s && pos < e && byte_of(w, b) >= (uint32_t)alphabet) bad = true;
+            if (pos >= s && pos + K <= e) {
+              uint32_t tau = 0;
+#pragma unroll
+              for (int r = 0; r < K; ++r) tau = tau * (uint32_t)alphabet + byte_of(w, b + r);
+              if (tau < (uint32_t)eps) atomicAdd(&hist[tau >> 1], 1u << (16 * (tau & 1)));
+            }
+          }
+        }
+      }
+    }
+    if (__syncthreads_or(bad) && tid == 0) record_error(hdr, SAD_ERR_BAD_INPUT, (int)x);
+    // the row: octet o = tid + kCtaThreads pass, one 16-byte shared load (and clear)
+    // and two 16-byte stores
+    uint4 *h4 = reinterpret_cast<uint4 *>(hist);
+    int4 *row4 = reinterpret_cast<int4 *>(counts + x * (int64_t)eps);
+    int pass = 0;
+    for (int o = tid; o < octets; o += kCtaThreads, ++pass) {
+      const uint4 h = h4[o];
+      h4[o] = make_uint4(0, 0, 0, 0);
+      row4[2 * o] = make_int4((int)(h.x & 0xFFFFu), (int)(h.x >> 16), (int)(h.y & 0xFFFFu),
+                              (int)(h.y >> 16));
+      row4[2 * o + 1] = make_int4((int)(h.z & 0xFFFFu), (int)(h.z >> 16), (int)(h.w & 0xFFFFu),
+                                  (int)(h.w >> 16));
+      if (word_max) {
+        const uint32_t any = h.x | h.y | h.z | h.w;
+        if (any) {
+          const uint32_t hw[4] = {h.x, h.y, h.z, h.w};
+          uint32_t nz = 0;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const uint32_t m = __vcmpne2(hw[u], 0u);
+            nz |= ((m & 1u) | ((m >> 15) & 2u)) << (2 * u);
+          }
+          present |= nz << (8 * pass);
+          if (any & 0xFFFEFFFEu) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              note_repeat(max8, word_max, 8 * o + 2 * u, (int32_t)(hw[u] & 0xFFFFu));
+              note_repeat(max8, word_max, 8 * o + 2 * u + 1, (int32_t)(hw[u] >> 16));
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (word_max) {
+    __syncthreads();
+    int pass = 0;
+    for (int o = tid; o < octets; o += kCtaThreads, ++pass) {
+      for (int u = 0; u < 8; ++u) {
+        const int t = 8 * o + u;
+        const int32_t m8 = (int32_t)((max8[t >> 2] >> (8 * (t & 3))) & 0xFFu);
+        const int32_t v = m8 > 0 ? m8 : (int32_t)((present >> (8 * pass + u)) & 1u);
+        if (v && v > *(volatile int32_t *)(word_max + t)) atomicMax(word_max + t, v);
+      }
+    }
+  }
+}
+
+template <int K>
+int launch_count(const uint8_t *codes, const int64_t *offsets, int32_t n, int32_t alphabet,
+                 int32_t eps, int32_t *counts, int32_t *word_max, WsHeader *hdr,
+                 cudaStream_t st) {
+  if ((eps & 7) == 0 && eps <= 8 * kCtaThreads * 4 &&
+      (reinterpret_cast<uintptr_t>(counts) & 15) == 0) {
+    const size_t smem = sizeof(uint32_t) * (size_t)((eps >> 1) + (word_max ? (eps >> 2) : 0));
+    if (word_max && cudaMemsetAsync(word_max, 0, sizeof(int32_t) * (size_t)eps, st) != cudaSuccess)
+      return SAD_ERR_CUDA;
+    auto kern = kmer_count_cta_kernel<K>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return SAD_ERR_CUDA;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCtaThreads, smem) !=
+        cudaSuccess)
+      return SAD_ERR_CUDA;
+    int64_t blocks = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
+    if (blocks > n) blocks = n;
+    if (blocks < 1) blocks = 1;
+    kern<<<(unsigned)blocks, kCtaThreads, smem, st>>>(codes, offsets, n, alphabet, eps, counts,
+                                                     word_max, hdr);
+    SAD_LAUNCH_CHECK();
+    return SAD_OK;
+  }
+  return launch_count_warp<K>(codes, offsets, n, alphabet, eps, counts, word_max, hdr, st);
 }
 
 }  // namespace

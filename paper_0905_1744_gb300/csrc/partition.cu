@@ -277,25 +277,23 @@ __device__ __forceinline__ int64_t block_of_item(int64_t x, int64_t n, int64_t p
   return b;
 }
 
-// Warp per item: the lanes count the smaller items of the other chunks of its block
-// (binary searches side by side), the sum is its place.
+// Thread per item: its place in its chunk plus the smaller items of the block's
+// other chunks (a few binary searches).
 __global__ void chunk_merge_kernel(const Item *__restrict__ in, Item *__restrict__ out,
                                    int64_t n, int64_t p) {
-  const int lane = threadIdx.x & 31;
-  for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n;
-       x += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+       x += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b = block_of_item(x, n, p);
     const int64_t lo = block_lo(b, n, p), e = block_lo(b + 1, n, p);
     const int64_t c = (x - lo) / kChunk;
     const Item it = in[x];
-    int64_t rank = 0;
-    for (int64_t c2 = lane; lo + c2 * kChunk < e; c2 += 32) {
+    int64_t rank = x - (lo + c * kChunk);
+    for (int64_t c2 = 0; lo + c2 * kChunk < e; ++c2) {
       if (c2 == c) continue;
       const int64_t a = lo + c2 * kChunk;
       rank += count_less(in + a, min((int64_t)kChunk, e - a), it);
     }
-    for (int o = 16; o > 0; o >>= 1) rank += __shfl_xor_sync(0xffffffffu, rank, o);
-    if (lane == 0) out[lo + rank + (x - (lo + c * kChunk))] = it;
+    out[lo + rank] = it;
   }
 }
 
@@ -389,7 +387,7 @@ int partition_sets_launch(const uint64_t *key_hi, const uint64_t *key_lo, int32_
     dim3 gc((unsigned)((w_max + kChunk - 1) / kChunk), (unsigned)p_single);
     chunk_sort_kernel<<<gc, 128, 0, st>>>(items, segoff);
     SAD_LAUNCH_CHECK();
-    chunk_merge_kernel<<<grid_for(n * 32, 256), 256, 0, st>>>(items, items2, n, p_single);
+    chunk_merge_kernel<<<grid_for(n, 128), 128, 0, st>>>(items, items2, n, p_single);
     SAD_LAUNCH_CHECK();
     if (max_p > 1) {
       samples_kernel<<<gsets, kSortThreads, kSortSmem, st>>>(items2, Y, Y2, piv, pivot_idx, sets,
@@ -404,8 +402,10 @@ int partition_sets_launch(const uint64_t *key_hi, const uint64_t *key_lo, int32_
     }
     bucket_scan_kernel<<<gsets, 1024, 0, st>>>(pos, dest, bucket_offsets, gbound, sets, n_sets);
     SAD_LAUNCH_CHECK();
-    bucket_place_kernel<<<grid_for(n * 32, 256), 256, 0, st>>>(items2, pos, bucket_offsets,
-                                                               members, n, p_single);
+    // a warp per item, all resident at once
+    bucket_place_kernel<<<(unsigned)((n * 32 + 255) / 256 < 65535 * 16 ? (n * 32 + 255) / 256
+                                                                      : 65535 * 16),
+                          256, 0, st>>>(items2, pos, bucket_offsets, members, n, p_single);
     SAD_LAUNCH_CHECK();
     return SAD_OK;
   }
