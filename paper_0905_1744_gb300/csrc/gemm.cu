@@ -79,6 +79,11 @@ __device__ __forceinline__ void red_add_u64(unsigned long long *p, unsigned long
   asm volatile("red.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+// acc += v as a 64-bit sum with its carries counted in c.
+__device__ __forceinline__ void add_carry(uint64_t &acc, uint32_t &c, uint64_t v) {
+  asm("add.cc.u64 %0, %0, %2;\n\taddc.u32 %1, %1, 0;" : "+l"(acc), "+r"(c) : "l"(v));
+}
+
 // Column sums of a 32 x 16 block held one row per lane (v[i] = column i): after
 // the call v[0] of lane L is the sum over all 32 lanes of column L & 15.
 __device__ __forceinline__ void transpose_reduce16(uint32_t (&v)[16], uint32_t lane) {
@@ -302,7 +307,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       // column records staged; the abort decision is the same for every epilogue thread
       if (named_bar_sync_or(1, kEpiThreads, *abort_flag != 0)) break;
       tc_fence_after();
-      uint32_t R0 = 0, R1 = 0, R2 = 0;
+      // similarity modes: the row's sum of terms = Rc 2^64 + Rlo (every term is below
+      // 2^64 but for F = 1, where it is exactly 2^64: s = d)
+      uint64_t Rlo = 0;
+      uint32_t Rc = 0;
       int64_t Rd = 0;  // distance mode: the row's sum of q
       if (kDist && rect) {
         // distance mode against reference rows: D = min(m_i, m_r) per pair, row sums only,
@@ -403,11 +411,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint64_t Q = ((uint64_t)rec.y << 32) | rec.x;
             const uint64_t lo = (uint64_t)s * Q;
             const uint64_t lo2 = lo + qv;
-            const uint32_t hi = lo2 < lo ? 1u : 0u;
-            const uint32_t wa = (uint32_t)lo2, wb = (uint32_t)(lo2 >> 32);
-            R0 += wa & 0xFFFFFFu;
-            R1 += (wa >> 24) | ((wb & 0xFFFFu) << 8);
-            R2 += (wb >> 16) | (hi << 16);
+            add_carry(Rlo, Rc, lo2);
+            Rc += lo2 < lo ? 1u : 0u;
           }
         }
       } else {
@@ -438,21 +443,16 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t qv = (t1 + ((xq - t1) >> sh1)) >> sh2;
           const uint64_t Q = ((uint64_t)rec.y << 32) | rec.x;
           const uint64_t lo = (uint64_t)s * Q;
-          const uint64_t lo2 = lo + qv;
-          const uint32_t hi = lo2 < lo ? 1u : 0u;
-          const uint32_t wa = (uint32_t)lo2, wb = (uint32_t)(lo2 >> 32);
-          uint32_t l0 = wa & 0xFFFFFFu;
-          uint32_t l1 = (wa >> 24) | ((wb & 0xFFFFu) << 8);
-          uint32_t l2 = (wb >> 16) | (hi << 16);
+          uint64_t lo2 = lo + qv;
+          uint32_t hi = lo2 < lo ? 1u : 0u;
           uint32_t scv = s, qc = qv;
           if (diag) {
             const int64_t jpos = (int64_t)J * kColBlock + c0 + cc;
-            if (row_pos > jpos) { l0 = 0; l1 = 0; l2 = 0; }
+            if (row_pos > jpos) { lo2 = 0; hi = 0; }
             if (row_pos >= jpos) { scv = 0; qc = 0; }
           }
-          R0 += l0;
-          R1 += l1;
-          R2 += l2;
+          add_carry(Rlo, Rc, lo2);
+          Rc += hi;
           cs[cc] = scv;
           cq[cc] = qc;
         }
@@ -480,9 +480,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         if constexpr (kDist) {
           red_add_u64(dst, (unsigned long long)Rd);
         } else {
-          red_add_u64(dst + 0, R0);
-          red_add_u64(dst + 1, R1);
-          red_add_u64(dst + 2, R2);
+          // Rc 2^64 + Rlo as 24-bit limbs: bits 0-23, 24-47, and the rest (Rc above bit 16)
+          red_add_u64(dst + 0, Rlo & 0xFFFFFFull);
+          red_add_u64(dst + 1, (Rlo >> 24) & 0xFFFFFFull);
+          red_add_u64(dst + 2, (Rlo >> 48) | ((unsigned long long)Rc << 16));
         }
       }
     }
