@@ -254,12 +254,74 @@ int launch_count_warp(const uint8_t *codes, const int64_t *offsets, int32_t n, i
 }
 
 // CTA per sequence (eps divisible by 8, eps <= 8 * kCtaThreads * 4, 16-byte aligned
-// rows): the 8 warps share one shared histogram, so an SM holds several times the
-// sequences of the warp-per-sequence kernel and keeps more row stores in flight.
-// Thread t always writes the column octets o = t + kCtaThreads * pass, so the words
-// it has seen occur fit one 32-bit register (8 bits per pass); counts >= 2 go to
-// per-CTA byte maxima as in the warp kernel.
+// rows): the 8 warps share a shared histogram, double-buffered: while the CTA writes
+// one sequence's row out of one buffer, the threads holding the next sequence's
+// bytes count it into the other, so a sequence costs one barrier and its counting
+// hides behind the previous row's stores. Thread t always writes the column octets
+// o = t + kCtaThreads * pass, so the words it has seen occur fit one 32-bit register
+// (8 bits per pass); counts >= 2 go to per-CTA byte maxima as in the warp kernel.
 constexpr int kCtaThreads = 256;
+
+template <int K>
+__device__ __forceinline__ bool cta_count_sequence(const uint8_t *__restrict__ codes,
+                                                   int64_t codes_end, int64_t s, int64_t e,
+                                                   int32_t alphabet, int32_t eps,
+                                                   uint32_t *hist) {
+  bool bad = false;
+  // 16 bytes per thread per step; the k - 1 bytes past them come from the next
+  // 16-byte load (L1)
+  for (int64_t c = (s & ~(int64_t)15) + 16 * threadIdx.x; c < e; c += 16 * kCtaThreads) {
+    const uint4 v = load16_guarded(codes, c, codes_end);
+    const uint4 nx = (K > 1 && c + 16 < e) ? load16_guarded(codes, c + 16, codes_end)
+                                           : make_uint4(0, 0, 0, 0);
+    const uint32_t w[8] = {v.x, v.y, v.z, v.w, nx.x, nx.y, nx.z, nx.w};
+    if (c >= s && c + 16 + K - 1 <= e) {
+      if (alphabet < 256) {
+        const uint32_t lim = 0x01010101u * (uint32_t)alphabet;
+        bad |= (__vcmpgeu4(v.x, lim) | __vcmpgeu4(v.y, lim) | __vcmpgeu4(v.z, lim) |
+                __vcmpgeu4(v.w, lim)) != 0u;
+      }
+#pragma unroll
+      for (int b = 0; b < 16; ++b) {
+        uint32_t tau = 0;
+#pragma unroll
+        for (int r = 0; r < K; ++r) tau = tau * (uint32_t)alphabet + byte_of(w, b + r);
+        if (tau < (uint32_t)eps) atomicAdd(&hist[tau >> 1], 1u << (16 * (tau & 1)));
+      }
+    } else {
+#pragma unroll
+      for (int b = 0; b < 16; ++b) {
+        const int64_t pos = c + b;
+        if (pos >= s && pos < e && byte_of(w, b) >= (uint32_t)alphabet) bad = true;
+        if (pos >= s && pos + K <= e) {
+          uint32_t tau = 0;
+#pragma unroll
+          for (int r = 0; r < K; ++r) tau = tau * (uint32_t)alphabet + byte_of(w, b + r);
+          if (tau < (uint32_t)eps) atomicAdd(&hist[tau >> 1], 1u << (16 * (tau & 1)));
+        }
+      }
+    }
+  }
+  return bad;
+}
+
+// Validates sequence x and counts it into hist; returns the thread's bad-code flag.
+template <int K>
+__device__ __forceinline__ bool cta_take_sequence(const uint8_t *__restrict__ codes,
+                                                  const int64_t *__restrict__ offsets,
+                                                  int64_t codes_end, int64_t x, int32_t alphabet,
+                                                  int32_t eps, uint32_t *hist, WsHeader *hdr) {
+  const int64_t s = offsets[x], e = offsets[x + 1];
+  int err = 0;
+  if (s < 0 || e > codes_end || e < s) err = SAD_ERR_INVALID_ARGUMENT;
+  else if (e - s < K) err = SAD_ERR_BAD_INPUT;
+  else if (e - s - K + 1 > kMaxM) err = SAD_ERR_UNSUPPORTED;
+  if (err) {
+    if (threadIdx.x == 0) record_error(hdr, err, (int)x);
+    return false;
+  }
+  return cta_count_sequence<K>(codes, codes_end, s, e, alphabet, eps, hist);
+}
 
 template <int K>
 __global__ void __launch_bounds__(kCtaThreads) kmer_count_cta_kernel(
@@ -267,65 +329,30 @@ __global__ void __launch_bounds__(kCtaThreads) kmer_count_cta_kernel(
     int32_t alphabet, int32_t eps, int32_t *__restrict__ counts, int32_t *__restrict__ word_max,
     WsHeader *hdr) {
   extern __shared__ uint32_t smem[];
-  uint32_t *hist = smem;                    // [eps / 2]
-  uint32_t *max8 = smem + (eps >> 1);       // [eps / 4]
+  uint32_t *histbuf = smem;                   // 2 x [eps / 2]
+  uint32_t *max8 = smem + eps;                // [eps / 4]
   const int tid = threadIdx.x;
-  for (int i = tid; i < (eps >> 1); i += kCtaThreads) hist[i] = 0;
+  for (int i = tid; i < eps; i += kCtaThreads) histbuf[i] = 0;
   if (word_max)
     for (int i = tid; i < (eps >> 2); i += kCtaThreads) max8[i] = 0;
   uint32_t present = 0;
   __syncthreads();
   const int64_t codes_end = offsets[n];
   const int octets = eps >> 3;
-  for (int64_t x = blockIdx.x; x < n; x += gridDim.x) {
-    const int64_t s = offsets[x], e = offsets[x + 1];
-    int err = 0;
-    if (s < 0 || e > codes_end || e < s) err = SAD_ERR_INVALID_ARGUMENT;
-    else if (e - s < K) err = SAD_ERR_BAD_INPUT;
-    else if (e - s - K + 1 > kMaxM) err = SAD_ERR_UNSUPPORTED;
-    bool bad = false;
-    if (err) {
-      if (tid == 0) record_error(hdr, err, (int)x);
-    } else {
-      // 16 bytes per thread per step; the k - 1 bytes past them come from the next
-      // 16-byte load (L1)
-      for (int64_t c = (s & ~(int64_t)15) + 16 * tid; c < e; c += 16 * kCtaThreads) {
-        const uint4 v = load16_guarded(codes, c, codes_end);
-        const uint4 nx = (K > 1 && c + 16 < e) ? load16_guarded(codes, c + 16, codes_end)
-                                               : make_uint4(0, 0, 0, 0);
-        const uint32_t w[8] = {v.x, v.y, v.z, v.w, nx.x, nx.y, nx.z, nx.w};
-        if (c >= s && c + 16 + K - 1 <= e) {
-          if (alphabet < 256) {
-            const uint32_t lim = 0x01010101u * (uint32_t)alphabet;
-            bad |= (__vcmpgeu4(v.x, lim) | __vcmpgeu4(v.y, lim) | __vcmpgeu4(v.z, lim) |
-                    __vcmpgeu4(v.w, lim)) != 0u;
-          }
-#pragma unroll
-          for (int b = 0; b < 16; ++b) {
-            uint32_t tau = 0;
-#pragma unroll
-            for (int r = 0; r < K; ++r) tau = tau * (uint32_t)alphabet + byte_of(w, b + r);
-            if (tau < (uint32_t)eps) atomicAdd(&hist[tau >> 1], 1u << (16 * (tau & 1)));
-          }
-        } else {
-#pragma unroll
-          for (int b = 0; b < 16; ++b) {
-            const int64_t pos = c + b;
-            if (pos >= s && pos < e && byte_of(w, b) >= (uint32_t)alphabet) bad = true;
-            if (pos >= s && pos + K <= e) {
-              uint32_t tau = 0;
-#pragma unroll
-              for (int r = 0; r < K; ++r) tau = tau * (uint32_t)alphabet + byte_of(w, b + r);
-              if (tau < (uint32_t)eps) atomicAdd(&hist[tau >> 1], 1u << (16 * (tau & 1)));
-            }
-          }
-        }
-      }
-    }
+  int64_t x = blockIdx.x;
+  if (x < n) {
+    const bool bad = cta_take_sequence<K>(codes, offsets, codes_end, x, alphabet, eps, histbuf, hdr);
     if (__syncthreads_or(bad) && tid == 0) record_error(hdr, SAD_ERR_BAD_INPUT, (int)x);
-    // the row: octet o = tid + kCtaThreads pass, one 16-byte shared load (and clear)
-    // and two 16-byte stores
-    uint4 *h4 = reinterpret_cast<uint4 *>(hist);
+  }
+  for (int it = 0; x < n; ++it, x += gridDim.x) {
+    uint32_t *cur = histbuf + (it & 1) * (eps >> 1);
+    uint32_t *nxt = histbuf + ((it + 1) & 1) * (eps >> 1);
+    const int64_t xn = x + gridDim.x;
+    bool badn = false;
+    if (xn < n) badn = cta_take_sequence<K>(codes, offsets, codes_end, xn, alphabet, eps, nxt, hdr);
+    // the row of x: octet o = tid + kCtaThreads pass, one 16-byte shared load (and
+    // clear) and two 16-byte stores
+    uint4 *h4 = reinterpret_cast<uint4 *>(cur);
     int4 *row4 = reinterpret_cast<int4 *>(counts + x * (int64_t)eps);
     int pass = 0;
     for (int o = tid; o < octets; o += kCtaThreads, ++pass) {
@@ -356,7 +383,8 @@ __global__ void __launch_bounds__(kCtaThreads) kmer_count_cta_kernel(
         }
       }
     }
-    __syncthreads();
+    // the next sequence is counted and this row's buffer is clear for the one after
+    if (__syncthreads_or(badn) && tid == 0) record_error(hdr, SAD_ERR_BAD_INPUT, (int)xn);
   }
   if (word_max) {
     __syncthreads();
@@ -378,7 +406,7 @@ int launch_count(const uint8_t *codes, const int64_t *offsets, int32_t n, int32_
                  cudaStream_t st) {
   if ((eps & 7) == 0 && eps <= 8 * kCtaThreads * 4 &&
       (reinterpret_cast<uintptr_t>(counts) & 15) == 0) {
-    const size_t smem = sizeof(uint32_t) * (size_t)((eps >> 1) + (word_max ? (eps >> 2) : 0));
+    const size_t smem = sizeof(uint32_t) * (size_t)(eps + (word_max ? (eps >> 2) : 0));
     if (word_max && cudaMemsetAsync(word_max, 0, sizeof(int32_t) * (size_t)eps, st) != cudaSuccess)
       return SAD_ERR_CUDA;
     auto kern = kmer_count_cta_kernel<K>;
