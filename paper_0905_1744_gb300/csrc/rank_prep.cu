@@ -772,7 +772,7 @@ __global__ void __launch_bounds__(256) planes_kernel(const int32_t *__restrict__
 }
 
 // Plane rows for depths D <= kTabDepth, streamed: one warp per stored row reads the
-// row's counts once (16 bytes per lane, eight loads in flight). A plane value is
+// row's counts once (16 bytes per lane, four loads in flight). A plane value is
 // the 4-bit e2m1 [c >= t] (1.0 or 0), two columns to a byte. When every word
 // occurs somewhere, section 1 is the identity map and a lane writes its four words
 // as one 2-byte store; the columns past section 1 are zero-filled with 16-byte
@@ -782,7 +782,7 @@ __global__ void __launch_bounds__(256) planes_kernel(const int32_t *__restrict__
 // per-warp buffer and are appended to the flat excess list with one atomic per
 // row; a row with more than kExCap of them is scanned again for the append.
 constexpr int kExCap = 64;
-constexpr int kStreamUnroll = 8;
+constexpr int kStreamUnroll = 4;
 
 __device__ __forceinline__ uint32_t plane_val(int32_t c, int32_t t) { return c >= t ? kE2M1One : 0u; }
 
