@@ -34,6 +34,8 @@ struct RankPtrs {
   int32_t *colmap;       // [K_cap] column -> word | threshold << 16
   int32_t *thist;        // [65537] histogram / cursor over T values
   int32_t *coltab;       // [kTabDepth][eps] column of (threshold t, word), -1 = none
+  int32_t *promcol;      // [eps] plane column of a word's threshold depth + 1, -1 = none
+  int64_t *weight;       // [eps] residual weight of a word: sum over sets of cnt_gt^2
   int32_t *mhist;        // [65537] histogram / cursor over m = L - k + 1 (one set)
   int32_t *perm;         // [rows_total] stored row -> input index (-1 = padding)
   int32_t *depth;        // [rows_total / 128] largest count in each 128-row block

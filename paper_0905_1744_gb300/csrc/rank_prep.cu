@@ -54,6 +54,8 @@ RankPtrs rank_ptrs(void *ws, const RankLayout &L) {
   P.colmap = reinterpret_cast<int32_t *>(b + L.colmap);
   P.thist = reinterpret_cast<int32_t *>(b + L.thist);
   P.coltab = reinterpret_cast<int32_t *>(b + L.coltab);
+  P.promcol = reinterpret_cast<int32_t *>(b + L.promcol);
+  P.weight = reinterpret_cast<int64_t *>(b + L.weight);
   P.mhist = reinterpret_cast<int32_t *>(b + L.mhist);
   P.perm = reinterpret_cast<int32_t *>(b + L.perm);
   P.rec = reinterpret_cast<uint4 *>(b + L.rec);
@@ -213,6 +215,8 @@ __global__ void rank_init_kernel(RankPtrs P, int32_t eps, int with_keys) {
     P.hdr->pairs_total = 0;
     P.hdr->n_blocks = 0;
     P.hdr->m_max = 0;
+    P.hdr->n_promoted = 0;
+    P.hdr->k_ext = 0;
     P.hdr->flat_count = 0;
   }
 }
@@ -520,6 +524,104 @@ __global__ void __launch_bounds__(256) list_scan_down_kernel(RankPtrs P, int64_t
   }
 }
 
+// Planes in the K padding. K_eff is padded to a whole number of K chunks, so the
+// GEMM multiplies K_pad - K_eff zero columns anyway; they are given the plane of
+// threshold depth + 1 of the words with the most residual pairs (weight = sum over
+// sets of cnt_gt^2, ties by word), at no cost in the GEMM. Their excess entries
+// lose one (the new plane holds it) and leave the residual when nothing remains.
+__global__ void promote_weight_kernel(RankPtrs P, int32_t eps) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < eps;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t w = 0;
+    if (P.hdr->status == 0 && residual_needed(P))
+      for (int64_t s = 0; s < P.n_sets; ++s) {
+        const int64_t c = P.cnt_gt[s * eps + t];
+        w += c * c;
+      }
+    P.weight[t] = w;
+    P.promcol[t] = -1;
+  }
+}
+
+// One block: the words with weight >= w*, w* the smallest threshold that selects at
+// most K_pad - K_eff words (and only words with two or more excess sequences),
+// numbered in word order after K_eff.
+__global__ void __launch_bounds__(1024) promote_select_kernel(RankPtrs P, int32_t eps) {
+  __shared__ int32_t s_warp[32];
+  __shared__ int32_t s_carry;
+  if (P.hdr->status != 0 || !residual_needed(P)) return;
+  const int32_t k_eff = (int32_t)P.hdr->k_eff, n_free = P.hdr->k_pad - k_eff;
+  if (n_free <= 0) return;
+  const int tid = threadIdx.x;
+  // binary search of w* in [4, max weight + 1]: count(w) = #{t : weight[t] >= w}
+  int64_t lo = 4, hi = 4;
+  {
+    int64_t mx = 0;
+    for (int t = tid; t < eps; t += blockDim.x) mx = max(mx, P.weight[t]);
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    __shared__ int64_t s_mx[32];
+    if ((tid & 31) == 0) s_mx[tid >> 5] = mx;
+    __syncthreads();
+    if (tid == 0) {
+      int64_t m = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = max(m, s_mx[w]);
+      s_mx[0] = m;
+    }
+    __syncthreads();
+    hi = max((int64_t)4, s_mx[0] + 1);
+  }
+  // invariant: count(hi) <= n_free (count(max + 1) = 0); find the smallest such w
+  while (lo < hi) {
+    const int64_t mid = lo + (hi - lo) / 2;
+    int32_t c = 0;
+    for (int t = tid; t < eps; t += blockDim.x) c += P.weight[t] >= mid ? 1 : 0;
+    int32_t tot;
+    block_scan_incl<int32_t>(c, s_warp, &tot);
+    if (tot <= n_free) hi = mid; else lo = mid + 1;
+  }
+  const int64_t wstar = hi;
+  if (tid == 0) s_carry = 0;
+  __syncthreads();
+  for (int base = 0; base < eps; base += blockDim.x) {
+    const int t = base + tid;
+    const int32_t sel = (t < eps && P.weight[t] >= wstar) ? 1 : 0;
+    int32_t tot;
+    const int32_t incl = block_scan_incl<int32_t>(sel, s_warp, &tot);
+    if (sel) P.promcol[t] = k_eff + s_carry + incl - 1;
+    __syncthreads();
+    if (tid == 0) s_carry += tot;
+    __syncthreads();
+  }
+  if (tid == 0) {
+    P.hdr->n_promoted = s_carry;
+    P.hdr->k_ext = k_eff + s_carry;
+    P.hdr->k_eff = k_eff + s_carry;
+  }
+}
+
+// Excess entries of promoted words: the plane value at the word's new column, one
+// less excess; entries left with none are dropped (row -1) and uncounted.
+__global__ void promote_apply_kernel(RankPtrs P, int32_t eps) {
+  if (P.hdr->status != 0 || !residual_needed(P) || P.hdr->n_promoted == 0) return;
+  const int64_t total = min((int64_t)P.hdr->flat_count, P.list_cap);
+  const int64_t row_words = P.k_cap / 8;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int2 e = P.flat[i];
+    const int32_t tau = e.y & 0xFFFF, ex = (int32_t)((uint32_t)e.y >> 16);
+    const int32_t col = P.promcol[tau];
+    if (col < 0) continue;
+    atomicOr(reinterpret_cast<unsigned int *>(P.planes) + (int64_t)e.x * row_words + (col >> 3),
+             kE2M1One << (4 * (col & 7)));
+    if (ex > 1) {
+      P.flat[i] = make_int2(e.x, tau | ((ex - 1) << 16));
+    } else {
+      atomicSub(&P.cnt_gt[(int64_t)set_of_row(P, e.x) * eps + tau], 1);
+      P.flat[i] = make_int2(-1, e.y);
+    }
+  }
+}
+
 // Excess entries from the unordered append into their (set, word) lists.
 __global__ void group_lists_kernel(RankPtrs P, int32_t eps) {
   if (P.hdr->status != 0 || !residual_needed(P)) return;
@@ -527,6 +629,7 @@ __global__ void group_lists_kernel(RankPtrs P, int32_t eps) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int2 e = P.flat[i];
+    if (e.x < 0) continue;  // all of its excess went into a promoted plane
     const int32_t tau = e.y & 0xFFFF, ex = (int32_t)((uint32_t)e.y >> 16);
     const int64_t w = (int64_t)set_of_row(P, e.x) * eps + tau;
     const int32_t slot = atomicAdd(&P.cursor[w], 1);
@@ -976,7 +1079,9 @@ __global__ void __launch_bounds__(256) tiles_kernel(RankPtrs P) {
             for (int32_t b = kColRatio * (J0 + J); b < kColRatio * (J0 + J + 1) && b < nblk; ++b)
               dJ = max(dJ, P.depth[b]);
             const int32_t d = min(min(dI, dJ), dkeep);
-            const int32_t kend = P.secend[max(d, 0)];
+            // the promoted planes of depth + 1 sit right after K_eff of the sections
+            const int32_t kend =
+                (P.hdr->n_promoted > 0 && min(dI, dJ) > dkeep) ? P.hdr->k_ext : P.secend[max(d, 0)];
             const int32_t nk = max(1, (kend + kKCols - 1) / kKCols);
             P.tile_of[e.tileof_base + (int64_t)I * cfull + J] = (int32_t)out;
             P.block_of[out] = 0;
@@ -1252,6 +1357,14 @@ int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *le
     const int64_t groups = P.n_pad / kPlaneRows;
     const int64_t cap = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
     planes_kernel<<<(unsigned)(groups < cap ? groups : cap), 256, smem, st>>>(counts, eps, P);
+    SAD_LAUNCH_CHECK();
+  }
+  if (P.depth_cap >= 1 && P.list_cap > 0) {
+    promote_weight_kernel<<<grid_for(eps, 256), 256, 0, st>>>(P, eps);
+    SAD_LAUNCH_CHECK();
+    promote_select_kernel<<<1, 1024, 0, st>>>(P, eps);
+    SAD_LAUNCH_CHECK();
+    promote_apply_kernel<<<grid_for(P.list_cap, 256), 256, 0, st>>>(P, eps);
     SAD_LAUNCH_CHECK();
   }
   int rc = list_scan();

@@ -48,7 +48,9 @@ struct WsHeader {
   int32_t m_max;         // largest m = L - k + 1 of the set
   unsigned long long flat_count;  // excess entries appended by the plane kernel
   int64_t items_total;   // residual work items (pairs of list chunks)
-  int32_t pad[44];
+  int32_t n_promoted;    // words given a plane of threshold depth + 1 in the K padding
+  int32_t k_ext;         // K extent of tiles whose two row blocks both reach depth + 1
+  int32_t pad[42];
 };
 static_assert(sizeof(WsHeader) == 256, "header is 256 bytes");
 
@@ -125,7 +127,8 @@ inline RankShape shape_single(int64_t n) {
 
 // Offsets of the rank workspace regions (bytes from the workspace base).
 struct RankLayout {
-  size_t sets, seq_set, row_set, T, secend, thist, coltab, mhist, perm, rec, depth, tiles,
+  size_t sets, seq_set, row_set, T, secend, thist, coltab, promcol, weight, mhist, perm, rec,
+      depth, tiles,
       acc, cnt_gt, list_off, item_off, cursor, tile_of, block_of, sortbuf, scanblk, colmap, lists,
       flat, planes, rblocks;
   size_t fixed_bytes;    // everything that does not depend on the capacities
@@ -149,6 +152,8 @@ inline RankLayout rank_layout(const RankShape &sh, int64_t eps, const RankCaps &
   L.secend = take(sizeof(int32_t) * (kMaxM + 2));
   L.thist = take(sizeof(int32_t) * (kMaxM + 2));
   L.coltab = take(sizeof(int32_t) * eps * kTabDepth);
+  L.promcol = take(sizeof(int32_t) * eps);
+  L.weight = take(sizeof(int64_t) * eps);
   L.mhist = take(sizeof(int32_t) * (kMaxM + 2));
   L.perm = take(sizeof(int32_t) * nz(sh.rows_total));
   L.rec = take(16 * nz(sh.rows_total));
