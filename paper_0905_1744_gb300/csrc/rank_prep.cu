@@ -545,46 +545,51 @@ __global__ void promote_weight_kernel(RankPtrs P, int32_t eps) {
 
 // One block: the words with weight >= w*, w* the smallest threshold that selects at
 // most K_pad - K_eff words (and only words with two or more excess sequences),
-// numbered in word order after K_eff.
-__global__ void __launch_bounds__(1024) promote_select_kernel(RankPtrs P, int32_t eps) {
+// numbered in word order after K_eff. The weights are staged in shared memory when
+// they fit; each step of the binary search counts with warp reductions and one
+// shared counter.
+__global__ void __launch_bounds__(1024) promote_select_kernel(RankPtrs P, int32_t eps,
+                                                              int staged) {
+  extern __shared__ int64_t s_w[];  // [eps] when staged
   __shared__ int32_t s_warp[32];
   __shared__ int32_t s_carry;
+  __shared__ unsigned long long s_max;
+  __shared__ int32_t s_cnt;
   if (P.hdr->status != 0 || !residual_needed(P)) return;
   const int32_t k_eff = (int32_t)P.hdr->k_eff, n_free = P.hdr->k_pad - k_eff;
   if (n_free <= 0) return;
   const int tid = threadIdx.x;
-  // binary search of w* in [4, max weight + 1]: count(w) = #{t : weight[t] >= w}
-  int64_t lo = 4, hi = 4;
+  const int64_t *w = staged ? s_w : P.weight;
+  if (tid == 0) s_max = 0;
+  if (staged)
+    for (int t = tid; t < eps; t += blockDim.x) s_w[t] = P.weight[t];
+  __syncthreads();
   {
     int64_t mx = 0;
-    for (int t = tid; t < eps; t += blockDim.x) mx = max(mx, P.weight[t]);
-    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    __shared__ int64_t s_mx[32];
-    if ((tid & 31) == 0) s_mx[tid >> 5] = mx;
-    __syncthreads();
-    if (tid == 0) {
-      int64_t m = 0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = max(m, s_mx[w]);
-      s_mx[0] = m;
-    }
-    __syncthreads();
-    hi = max((int64_t)4, s_mx[0] + 1);
+    for (int t = tid; t < eps; t += blockDim.x) mx = max(mx, w[t]);
+    atomicMax(&s_max, (unsigned long long)mx);
   }
+  __syncthreads();
   // invariant: count(hi) <= n_free (count(max + 1) = 0); find the smallest such w
+  int64_t lo = 4, hi = max((int64_t)4, (int64_t)s_max + 1);
   while (lo < hi) {
     const int64_t mid = lo + (hi - lo) / 2;
     int32_t c = 0;
-    for (int t = tid; t < eps; t += blockDim.x) c += P.weight[t] >= mid ? 1 : 0;
-    int32_t tot;
-    block_scan_incl<int32_t>(c, s_warp, &tot);
-    if (tot <= n_free) hi = mid; else lo = mid + 1;
+    for (int t = tid; t < eps; t += blockDim.x) c += w[t] >= mid ? 1 : 0;
+    c = __reduce_add_sync(0xffffffffu, c);
+    if (tid == 0) s_cnt = 0;
+    __syncthreads();
+    if ((tid & 31) == 0 && c) atomicAdd(&s_cnt, c);
+    __syncthreads();
+    if (s_cnt <= n_free) hi = mid; else lo = mid + 1;
+    __syncthreads();
   }
   const int64_t wstar = hi;
   if (tid == 0) s_carry = 0;
   __syncthreads();
   for (int base = 0; base < eps; base += blockDim.x) {
     const int t = base + tid;
-    const int32_t sel = (t < eps && P.weight[t] >= wstar) ? 1 : 0;
+    const int32_t sel = (t < eps && w[t] >= wstar) ? 1 : 0;
     int32_t tot;
     const int32_t incl = block_scan_incl<int32_t>(sel, s_warp, &tot);
     if (sel) P.promcol[t] = k_eff + s_carry + incl - 1;
@@ -1362,7 +1367,13 @@ int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *le
   if (P.depth_cap >= 1 && P.list_cap > 0) {
     promote_weight_kernel<<<grid_for(eps, 256), 256, 0, st>>>(P, eps);
     SAD_LAUNCH_CHECK();
-    promote_select_kernel<<<1, 1024, 0, st>>>(P, eps);
+    const int staged = eps <= 16384 ? 1 : 0;
+    const size_t smem = staged ? sizeof(int64_t) * (size_t)eps : 0;
+    if (staged && cudaFuncSetAttribute(promote_select_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem) != cudaSuccess)
+      return SAD_ERR_CUDA;
+    promote_select_kernel<<<1, 1024, smem, st>>>(P, eps, staged);
     SAD_LAUNCH_CHECK();
     promote_apply_kernel<<<grid_for(P.list_cap, 256), 256, 0, st>>>(P, eps);
     SAD_LAUNCH_CHECK();
