@@ -545,62 +545,79 @@ __global__ void promote_weight_kernel(RankPtrs P, int32_t eps) {
 
 // One block: the words with weight >= w*, w* the smallest threshold that selects at
 // most K_pad - K_eff words (and only words with two or more excess sequences),
-// numbered in word order after K_eff. The weights are staged in shared memory when
-// they fit; each step of the binary search counts with warp reductions and one
-// shared counter.
+// numbered in word order after K_eff. w* is one above the (n_free + 1)-th largest
+// weight, found by a radix select (8-bit digits from the top: a histogram of the
+// candidates' digit, then the digit where the count from the top reaches the rank).
 __global__ void __launch_bounds__(1024) promote_select_kernel(RankPtrs P, int32_t eps,
                                                               int staged) {
   extern __shared__ int64_t s_w[];  // [eps] when staged
   __shared__ int32_t s_warp[32];
-  __shared__ int32_t s_carry;
-  __shared__ unsigned long long s_max;
-  __shared__ int32_t s_cnt;
+  __shared__ int32_t s_hist[256];
+  __shared__ unsigned long long s_max, s_prefix;
+  __shared__ int32_t s_rank, s_found;
   if (P.hdr->status != 0 || !residual_needed(P)) return;
   const int32_t k_eff = (int32_t)P.hdr->k_eff, n_free = P.hdr->k_pad - k_eff;
   if (n_free <= 0) return;
   const int tid = threadIdx.x;
-  const int64_t *w = staged ? s_w : P.weight;
-  if (tid == 0) s_max = 0;
+  const uint64_t *w = reinterpret_cast<const uint64_t *>(staged ? s_w : P.weight);
+  if (tid == 0) {
+    s_max = 0;
+    s_prefix = 0;
+    s_rank = n_free + 1;
+    s_found = 1;
+  }
   if (staged)
     for (int t = tid; t < eps; t += blockDim.x) s_w[t] = P.weight[t];
   __syncthreads();
   {
-    int64_t mx = 0;
+    uint64_t mx = 0;
     for (int t = tid; t < eps; t += blockDim.x) mx = max(mx, w[t]);
     atomicMax(&s_max, (unsigned long long)mx);
   }
   __syncthreads();
-  // invariant: count(hi) <= n_free (count(max + 1) = 0); find the smallest such w
-  int64_t lo = 4, hi = max((int64_t)4, (int64_t)s_max + 1);
-  while (lo < hi) {
-    const int64_t mid = lo + (hi - lo) / 2;
-    int32_t c = 0;
-    for (int t = tid; t < eps; t += blockDim.x) c += w[t] >= mid ? 1 : 0;
-    c = __reduce_add_sync(0xffffffffu, c);
-    if (tid == 0) s_cnt = 0;
+  int top = 0;
+  while (top < 64 && (s_max >> top) > 255) top += 8;
+  uint64_t mask = 0;
+  for (int shift = top; shift >= 0; shift -= 8) {
+    if (tid < 256) s_hist[tid] = 0;
     __syncthreads();
-    if ((tid & 31) == 0 && c) atomicAdd(&s_cnt, c);
+    const uint64_t prefix = s_prefix;
+    for (int t = tid; t < eps; t += blockDim.x)
+      if ((w[t] & mask) == prefix) atomicAdd(&s_hist[(w[t] >> shift) & 255], 1);
     __syncthreads();
-    if (s_cnt <= n_free) hi = mid; else lo = mid + 1;
+    if (tid == 0) {
+      int32_t need = s_rank, cum = 0, d = 255;
+      for (; d >= 0; --d) {
+        if (cum + s_hist[d] >= need) break;
+        cum += s_hist[d];
+      }
+      if (d < 0) {  // fewer candidates than the rank: every weight is selectable
+        s_found = 0;
+        d = 0;
+      }
+      s_rank = need - cum;
+      s_prefix = prefix | ((unsigned long long)d << shift);
+    }
+    mask |= (uint64_t)255 << shift;
     __syncthreads();
+    if (!s_found) break;
   }
-  const int64_t wstar = hi;
-  if (tid == 0) s_carry = 0;
-  __syncthreads();
-  for (int base = 0; base < eps; base += blockDim.x) {
-    const int t = base + tid;
-    const int32_t sel = (t < eps && w[t] >= wstar) ? 1 : 0;
-    int32_t tot;
-    const int32_t incl = block_scan_incl<int32_t>(sel, s_warp, &tot);
-    if (sel) P.promcol[t] = k_eff + s_carry + incl - 1;
-    __syncthreads();
-    if (tid == 0) s_carry += tot;
-    __syncthreads();
-  }
+  // the (n_free + 1)-th largest weight is s_prefix (when there are that many words)
+  const uint64_t wstar = max((uint64_t)4, s_found ? (uint64_t)s_prefix + 1 : (uint64_t)0);
+  // number the selected words in word order: each thread takes consecutive words
+  const int per = (eps + blockDim.x - 1) / blockDim.x;
+  const int t0 = tid * per;
+  int32_t mine = 0;
+  for (int t = t0; t < t0 + per && t < eps; ++t) mine += w[t] >= wstar ? 1 : 0;
+  int32_t tot;
+  const int32_t incl = block_scan_incl<int32_t>(mine, s_warp, &tot);
+  int32_t next = k_eff + incl - mine;
+  for (int t = t0; t < t0 + per && t < eps; ++t)
+    if (w[t] >= wstar) P.promcol[t] = next++;
   if (tid == 0) {
-    P.hdr->n_promoted = s_carry;
-    P.hdr->k_ext = k_eff + s_carry;
-    P.hdr->k_eff = k_eff + s_carry;
+    P.hdr->n_promoted = tot;
+    P.hdr->k_ext = k_eff + tot;
+    P.hdr->k_eff = k_eff + tot;
   }
 }
 
