@@ -552,7 +552,7 @@ __global__ void __launch_bounds__(1024) promote_select_kernel(RankPtrs P, int32_
                                                               int staged) {
   extern __shared__ int64_t s_w[];  // [eps] when staged
   __shared__ int32_t s_warp[32];
-  __shared__ int32_t s_hist[256];
+  __shared__ int32_t s_hist[257];  // + a bin for words that are not candidates
   __shared__ unsigned long long s_max, s_prefix;
   __shared__ int32_t s_rank, s_found;
   if (P.hdr->status != 0 || !residual_needed(P)) return;
@@ -579,11 +579,17 @@ __global__ void __launch_bounds__(1024) promote_select_kernel(RankPtrs P, int32_
   while (top < 64 && (s_max >> top) > 255) top += 8;
   uint64_t mask = 0;
   for (int shift = top; shift >= 0; shift -= 8) {
-    if (tid < 256) s_hist[tid] = 0;
+    if (tid < 257) s_hist[tid] = 0;
     __syncthreads();
     const uint64_t prefix = s_prefix;
-    for (int t = tid; t < eps; t += blockDim.x)
-      if ((w[t] & mask) == prefix) atomicAdd(&s_hist[(w[t] >> shift) & 255], 1);
+    // lanes with the same digit add together (most weights share the low digits)
+    for (int base = 0; base < eps; base += blockDim.x) {
+      const int t = base + tid;
+      const bool cand = t < eps && (w[t] & mask) == prefix;
+      const int d = cand ? (int)((w[t] >> shift) & 255) : 256;
+      const unsigned same = __match_any_sync(0xffffffffu, d);
+      if (cand && (tid & 31) == __ffs(same) - 1) atomicAdd(&s_hist[d], __popc(same));
+    }
     __syncthreads();
     if (tid == 0) {
       int32_t need = s_rank, cum = 0, d = 255;
