@@ -591,18 +591,30 @@ __global__ void __launch_bounds__(1024) promote_select_kernel(RankPtrs P, int32_
       if (cand && (tid & 31) == __ffs(same) - 1) atomicAdd(&s_hist[d], __popc(same));
     }
     __syncthreads();
-    if (tid == 0) {
-      int32_t need = s_rank, cum = 0, d = 255;
-      for (; d >= 0; --d) {
-        if (cum + s_hist[d] >= need) break;
-        cum += s_hist[d];
+    if (tid < 32) {
+      // warp 0 walks the bins from the top: lane l holds bins 255-8l .. 248-8l
+      const int32_t need = s_rank;
+      int32_t mine = 0;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) mine += s_hist[255 - 8 * tid - j];
+      int32_t incl = mine;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (tid >= o) incl += v;
       }
-      if (d < 0) {  // fewer candidates than the rank: every weight is selectable
-        s_found = 0;
-        d = 0;
+      const unsigned hit = __ballot_sync(0xffffffffu, incl >= need);
+      if (hit == 0) {  // fewer candidates than the rank: every weight is selectable
+        if (tid == 0) {
+          s_found = 0;
+          s_prefix = prefix;
+        }
+      } else if (tid == __ffs(hit) - 1) {
+        int32_t cum = incl - mine, d = 255 - 8 * tid;
+        while (cum + s_hist[d] < need) cum += s_hist[d--];
+        s_rank = need - cum;
+        s_prefix = prefix | ((unsigned long long)d << shift);
       }
-      s_rank = need - cum;
-      s_prefix = prefix | ((unsigned long long)d << shift);
     }
     mask |= (uint64_t)255 << shift;
     __syncthreads();
