@@ -572,7 +572,9 @@ __global__ void __launch_bounds__(1024) promote_select_kernel(RankPtrs P, int32_
   {
     uint64_t mx = 0;
     for (int t = tid; t < eps; t += blockDim.x) mx = max(mx, w[t]);
-    atomicMax(&s_max, (unsigned long long)mx);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((tid & 31) == 0) atomicMax(&s_max, (unsigned long long)mx);
   }
   __syncthreads();
   int top = 0;
