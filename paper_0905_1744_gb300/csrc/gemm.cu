@@ -33,7 +33,7 @@
 // The double TMEM accumulator lets the epilogue of one tile overlap the MMAs of
 // the next.
 //
-// Pair mode (one set, square): clusters of two CTAs run the M = 256 form of the
+// Pair mode (one set, square; opt-in): clusters of two CTAs run the M = 256 form of the
 // MMA (cta_group::2). The pair takes row blocks 2u and 2u + 1 against one column
 // block J >= 2u: each CTA loads its own 128 rows of A and one 64-row half of B,
 // so a CTA takes in 24 KB per K chunk instead of 32 for the same 128 x 128 tile
@@ -145,6 +145,38 @@ __device__ __forceinline__ void tile_at(const RankPtrs &P, const RectArgs &X, in
     I = tl.x & 0xFFFF;
     J = tl.x >> 16;
     nk = tl.y;
+  }
+}
+
+// Square similarity epilogue over 16 columns of this lane's accumulator row.
+// colrec holds (Qlo, Qhi, Wlo, Whi) per column: Q = floor((2^64 - 1) / d) and the
+// floor weight W of d = m_j, so term = s Q + floor(s W / 2^63) with s = S + the
+// residual. The row keeps sum s Qlo, sum s Qhi (each below 2^54 over 64 columns)
+// and the sum of the floors; cs, cq get what the columns add (s and the floor).
+// On a diagonal tile the row takes j >= i only and the columns j > i only.
+template <bool kDiag>
+__device__ __forceinline__ void f_block16(const uint32_t (&v)[16], const uint32_t (&rw)[8],
+                                          const uint4 *colrec, int64_t row_pos, int64_t jpos0,
+                                          uint64_t &sql, uint64_t &sqh, uint32_t &qsum,
+                                          uint32_t (&cs)[16], uint32_t (&cq)[16]) {
+#pragma unroll
+  for (int cc = 0; cc < 16; ++cc) {
+    const uint4 rec = colrec[cc];
+    // the accumulator is an integer below 2^24: + 2^23 puts it in the low mantissa bits
+    const uint32_t sv = __float_as_uint(__fadd_rn(__uint_as_float(v[cc]), 8388608.0f)) - 0x4B000000u;
+    const uint32_t s = sv + ((cc & 1) ? (rw[cc >> 1] >> 16) : (rw[cc >> 1] & 0xFFFFu));
+    const uint32_t q = (uint32_t)(((uint64_t)s * rec.w + __umulhi(s, rec.z)) >> 31);
+    uint32_t sr = s, qr = q, sc = s, qc = q;
+    if constexpr (kDiag) {
+      const int64_t jpos = jpos0 + cc;
+      if (row_pos > jpos) { sr = 0; qr = 0; }
+      if (row_pos >= jpos) { sc = 0; qc = 0; }
+    }
+    sql += (uint64_t)sr * rec.x;
+    sqh += (uint64_t)sr * rec.y;
+    qsum += qr;
+    cs[cc] = sc;
+    cq[cc] = qc;
   }
 }
 
@@ -430,7 +462,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int buf = lt & 1;
       for (uint32_t c = etid; c < (uint32_t)kColBlock; c += kEpiThreads) {
         const int64_t jpos = (int64_t)J * kColBlock + c;
-        S.colrec[buf][c] = rect ? X.rec_ref[jpos] : P.rec[jpos];
+        if (!kDist && !rect) {
+          const uint4 rc = P.rec[jpos];
+          const uint2 w = P.recw[jpos];
+          S.colrec[buf][c] = make_uint4(rc.x, rc.y, w.x, w.y);
+        } else {
+          S.colrec[buf][c] = rect ? X.rec_ref[jpos] : P.rec[jpos];
+        }
         S.colorig[buf][c] = rect ? 0 : P.perm[jpos];
         if constexpr (kDist)
           S.collb[buf][c] = Z.ln_table[(int64_t)Z.b * (int64_t)(P.rec[jpos].w & 0xFFFFu)];
@@ -569,6 +607,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       } else {
+      uint64_t sql = 0, sqh = 0;  // sum s Qlo, sum s Qhi
+      uint32_t qsum = 0;          // sum floor(s W / 2^63)
 #pragma unroll 1
       for (int sc = 0; sc < kHalfCols / 16; ++sc) {
         const int c0 = (int)half * kHalfCols + sc * 16;
@@ -582,33 +622,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         tmem_ld_wait();
         uint32_t cs[16], cq[16];
-#pragma unroll
-        for (int cc = 0; cc < 16; ++cc) {
-          const uint4 rec = S.colrec[buf][c0 + cc];
-          const uint32_t s = __float2uint_rn(__uint_as_float(v[cc])) +
-                             ((rw[cc >> 1] >> (16 * (cc & 1))) & 0xFFFFu);
-          const uint32_t d = rec.w & 0xFFFFu;
-          const uint32_t sh1 = (rec.w >> 16) & 0xFFu, sh2 = rec.w >> 24;
-          // floor(s * 2^64 / d) = s * Q + floor(s * r / d), r = 2^64 - Q d
-          const uint32_t r = 0u - rec.x * d;
-          const uint32_t xq = s * r;
-          const uint32_t t1 = __umulhi(rec.z, xq);
-          const uint32_t qv = (t1 + ((xq - t1) >> sh1)) >> sh2;
-          const uint64_t Q = ((uint64_t)rec.y << 32) | rec.x;
-          const uint64_t lo = (uint64_t)s * Q;
-          uint64_t lo2 = lo + qv;
-          uint32_t hi = lo2 < lo ? 1u : 0u;
-          uint32_t scv = s, qc = qv;
-          if (diag) {
-            const int64_t jpos = (int64_t)J * kColBlock + c0 + cc;
-            if (row_pos > jpos) { lo2 = 0; hi = 0; }
-            if (row_pos >= jpos) { scv = 0; qc = 0; }
-          }
-          add_carry(Rlo, Rc, lo2);
-          Rc += hi;
-          cs[cc] = scv;
-          cq[cc] = qc;
-        }
+        if (diag)
+          f_block16<true>(v, rw, &S.colrec[buf][c0], row_pos, (int64_t)J * kColBlock + c0, sql,
+                          sqh, qsum, cs, cq);
+        else
+          f_block16<false>(v, rw, &S.colrec[buf][c0], row_pos, 0, sql, sqh, qsum, cs, cq);
         transpose_reduce16(cs, lane);
         transpose_reduce16(cq, lane);
         if (lane < 16) {
@@ -624,6 +642,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             red_add_u64(dst + 2, (unsigned long long)(sum >> 48));
           }
         }
+      }
+      {
+        // the row's sum of terms sql + sqh 2^32 + qsum as Rc 2^64 + Rlo
+        const uint64_t a = sql + (sqh << 32);
+        const uint64_t b = a + qsum;
+        Rlo = b;
+        Rc = (uint32_t)(sqh >> 32) + (a < sql ? 1u : 0u) + (b < a ? 1u : 0u);
       }
       }
       tc_fence_before();
@@ -718,10 +743,12 @@ int gemm_attr() {
   return SAD_OK;
 }
 
-// Pair mode is the default for one set; SAD_GEMM_PAIR=0 selects one CTA per tile.
+// Pair mode is opt-in (SAD_GEMM_PAIR=1): on the paper-scale set its TMA + MMA
+// mainloop measured slower than one CTA per tile (0.84 against 0.72 ms) although
+// each CTA loads a quarter fewer bytes.
 bool pair_mode_enabled() {
   const char *e = getenv("SAD_GEMM_PAIR");
-  return !(e && e[0] == '0');
+  return e && e[0] == '1';
 }
 
 // Largest number of co-resident clusters of two for the pair kernel (0: none).

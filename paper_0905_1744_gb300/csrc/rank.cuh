@@ -24,6 +24,22 @@ __device__ __forceinline__ uint4 division_record(uint32_t d) {
                     d | (sh1 << 16) | (sh2 << 24));
 }
 
+// The small part of a term, floor(s r / d) with r = 2^64 - Q d in [1, d], as one
+// fixed-point product: floor(s W / 2^63) with W = ceil(2^63 r / d) <= 2^63. For
+// every s < 2^16 the excess s (W - 2^63 r / d) / 2^63 < 2^-47 stays below the gap
+// 1/d between the fraction of s r / d and the next integer, so the floor is exact.
+// W by long division in two steps (r 2^47 < 2^64, then the remainder times 2^16).
+__device__ __forceinline__ uint2 floor_weight(uint32_t d) {
+  const uint64_t Q = 0xFFFFFFFFFFFFFFFFull / d;
+  const uint64_t r = 0ull - Q * d;
+  const uint64_t n1 = r << 47;
+  const uint64_t q1 = n1 / d, r1 = n1 - q1 * d;
+  const uint64_t n2 = r1 << 16;
+  const uint64_t q2 = n2 / d, r2 = n2 - q2 * d;
+  const uint64_t W = (q1 << 16) + q2 + (r2 != 0 ? 1u : 0u);
+  return make_uint2((uint32_t)W, (uint32_t)(W >> 32));
+}
+
 struct RankPtrs {
   WsHeader *hdr;
   RankSet *sets;         // [n_sets]
@@ -40,6 +56,7 @@ struct RankPtrs {
   int32_t *perm;         // [rows_total] stored row -> input index (-1 = padding)
   int32_t *depth;        // [rows_total / 128] largest count in each 128-row block
   uint4 *rec;            // [rows_total] division record of each stored row's m
+  uint2 *recw;           // [rows_total] floor_weight of each stored row's m
   int2 *tiles;           // [tiles_total] (I | J << 16, K chunks), global block indices
   unsigned long long *acc;  // [n_total][3] 24-bit-limb accumulators of the keys
   uint8_t *planes;       // [rows_total][K_cap] fp8 threshold planes (sections 1..depth)

@@ -59,6 +59,7 @@ RankPtrs rank_ptrs(void *ws, const RankLayout &L) {
   P.mhist = reinterpret_cast<int32_t *>(b + L.mhist);
   P.perm = reinterpret_cast<int32_t *>(b + L.perm);
   P.rec = reinterpret_cast<uint4 *>(b + L.rec);
+  P.recw = reinterpret_cast<uint2 *>(b + L.recw);
   P.depth = reinterpret_cast<int32_t *>(b + L.depth);
   P.tiles = reinterpret_cast<int2 *>(b + L.tiles);
   P.acc = reinterpret_cast<unsigned long long *>(b + L.acc);
@@ -711,9 +712,11 @@ __global__ void lensort_place_kernel(const int32_t *__restrict__ lengths, int32_
       const int32_t pos = atomicAdd(&P.mhist[m], 1);
       P.perm[pos] = (int32_t)x;
       P.rec[pos] = division_record((uint32_t)m);
+      P.recw[pos] = floor_weight((uint32_t)m);
     } else {
       P.perm[x] = -1;
       P.rec[x] = division_record(1u);  // padding rows: S = 0, term = 0
+      P.recw[x] = floor_weight(1u);
     }
   }
 }
@@ -745,9 +748,11 @@ __global__ void __launch_bounds__(kSortThreads) lensort_sets_kernel(
         const int32_t m = lengths[e.seq_begin + x] - k + 1;
         P.perm[row] = (int32_t)(e.seq_begin + x);
         P.rec[row] = division_record((uint32_t)min(max(m, 1), kMaxM));
+        P.recw[row] = floor_weight((uint32_t)min(max(m, 1), kMaxM));
       } else {
         P.perm[row] = -1;
         P.rec[row] = division_record(1u);
+        P.recw[row] = floor_weight(1u);
       }
     }
     __syncthreads();

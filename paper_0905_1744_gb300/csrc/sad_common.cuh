@@ -128,7 +128,7 @@ inline RankShape shape_single(int64_t n) {
 // Offsets of the rank workspace regions (bytes from the workspace base).
 struct RankLayout {
   size_t sets, seq_set, row_set, T, secend, thist, coltab, promcol, weight, mhist, perm, rec,
-      depth, tiles,
+      recw, depth, tiles,
       acc, cnt_gt, list_off, item_off, cursor, tile_of, block_of, sortbuf, scanblk, colmap, lists,
       flat, planes, rblocks;
   size_t fixed_bytes;    // everything that does not depend on the capacities
@@ -157,6 +157,7 @@ inline RankLayout rank_layout(const RankShape &sh, int64_t eps, const RankCaps &
   L.mhist = take(sizeof(int32_t) * (kMaxM + 2));
   L.perm = take(sizeof(int32_t) * nz(sh.rows_total));
   L.rec = take(16 * nz(sh.rows_total));
+  L.recw = take(8 * nz(sh.rows_total));
   L.depth = take(sizeof(int32_t) * nz(sh.rows_total / kRowBlock));
   L.tiles = take(2 * sizeof(int32_t) * nz(sh.tiles_total));
   L.acc = take(3 * sizeof(uint64_t) * nz(sh.n_total));

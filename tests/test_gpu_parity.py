@@ -131,13 +131,13 @@ def test_rank_depth_cap_ragged(sad, oracle_mod, n, depth):
 
 
 @pytest.mark.parametrize("n,depth", [(1, 0), (129, 0), (383, 1), (700, 2)])
-def test_rank_one_cta_per_tile_kernel(sad, oracle_mod, monkeypatch, n, depth):
-    """One set runs on CTA pairs (M = 256 MMAs) by default; the one-CTA-per-tile
-    kernel (batches, and SAD_GEMM_PAIR=0) gives the same keys, including odd
+def test_rank_cta_pair_kernel(sad, oracle_mod, monkeypatch, n, depth):
+    """SAD_GEMM_PAIR=1 runs one set on CTA pairs (M = 256 MMAs, each CTA loading
+    half of B): the same keys as one CTA per tile and the oracle, including odd
     numbers of row blocks where the last pair's second tile is empty."""
     s = datagen.random_small(n, 3, 700, seed=n + 5, alphabet=20)
     hi0, lo0, r0 = check_rank(sad, oracle_mod, s, depth=depth)
-    monkeypatch.setenv("SAD_GEMM_PAIR", "0")
+    monkeypatch.setenv("SAD_GEMM_PAIR", "1")
     hi1, lo1, r1 = check_rank(sad, oracle_mod, s, depth=depth)
     np.testing.assert_array_equal(hi0, hi1)
     np.testing.assert_array_equal(lo0, lo1)
