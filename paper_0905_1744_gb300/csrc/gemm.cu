@@ -11,9 +11,11 @@
 //   term_ij = floor(S_ij 2^64 / D_ij), D_ij = m_j for stored i <= j (rows are in
 //   decreasing length), key_i += term_ij for i <= j and key_j += term_ij for i < j.
 //
-// Terms are split into 24-bit limbs; the row sums of a tile stay in registers,
-// the column sums are reduced across the 32 lanes of a warp with a transposing
-// shuffle tree, and both are added to per-sequence 64-bit limb accumulators
+// The row sums of a tile stay in registers, the column sums are reduced across
+// the 32 lanes of a warp with a transposing shuffle tree; the square mode then
+// meets the two column halves' row sums and the four lane quadrants' column sums
+// in shared memory, so a tile adds one 128-bit sum per row and per column, split
+// as T mod 2^32 and T >> 32 into two 64-bit accumulators per sequence
 // (red.global.add.u64), which a last kernel folds into the 128-bit key.
 //
 // When the planes are cut at a depth D, the residual sum_tau max(0, min(c_i, c_j) - D)
@@ -78,6 +80,10 @@ struct GemmSmem {
   uint4 colrec[2][kColBlock];
   int32_t colorig[2][kColBlock];
   int64_t collb[2][kColBlock];  // distance mode: ln_q(b d) of each tile column
+  // square similarity mode: the four lane quadrants' column sums (s, floor) and the
+  // second column half's row sums (Rlo, Rc), added once per tile
+  uint2 colpart[2][4][kColBlock];
+  uint4 rowpart[2][kRowBlock];
   uint64_t full[kStages];
   uint64_t empty[kStages];
   uint64_t tfull[2];
@@ -93,6 +99,17 @@ constexpr size_t kGemmSmemBytes = sizeof(GemmSmem) + 1024;
 
 __device__ __forceinline__ void red_add_u64(unsigned long long *p, unsigned long long v) {
   asm volatile("red.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// T = hi 2^64 + lo (T < 2^72) into a key's limbs: acc0 += T mod 2^32, acc1 += T >> 32.
+// A key takes fewer than 2^17 such adds, so acc1 < 2^57 and acc0 < 2^49.
+__device__ __forceinline__ void red_key(unsigned long long *dst, uint64_t lo, uint64_t hi) {
+  red_add_u64(dst, lo & 0xFFFFFFFFull);
+  red_add_u64(dst + 1, (lo >> 32) | (hi << 32));
+}
+
+__device__ __forceinline__ void named_bar_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
 // acc += v as a 64-bit sum with its carries counted in c.
@@ -162,7 +179,7 @@ __device__ __forceinline__ void f_block16(const uint32_t (&v)[16], const uint32_
 #pragma unroll
   for (int cc = 0; cc < 16; ++cc) {
     const uint4 rec = colrec[cc];
-    // the accumulator is an integer below 2^24: + 2^23 puts it in the low mantissa bits
+    // the accumulator is an integer below 2^16: + 2^23 puts it in the low mantissa bits
     const uint32_t sv = __float_as_uint(__fadd_rn(__uint_as_float(v[cc]), 8388608.0f)) - 0x4B000000u;
     const uint32_t s = sv + ((cc & 1) ? (rw[cc >> 1] >> 16) : (rw[cc >> 1] & 0xFFFFu));
     const uint32_t q = (uint32_t)(((uint64_t)s * rec.w + __umulhi(s, rec.z)) >> 31);
@@ -629,19 +646,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           f_block16<false>(v, rw, &S.colrec[buf][c0], row_pos, 0, sql, sqh, qsum, cs, cq);
         transpose_reduce16(cs, lane);
         transpose_reduce16(cq, lane);
-        if (lane < 16) {
-          const int col = c0 + (int)lane;
-          const int32_t jorig = S.colorig[buf][col];
-          if (jorig >= 0 && (cs[0] | cq[0]) != 0) {
-            const uint4 rec = S.colrec[buf][col];
-            const uint64_t Q = ((uint64_t)rec.y << 32) | rec.x;
-            const unsigned __int128 sum = (unsigned __int128)Q * cs[0] + cq[0];
-            unsigned long long *dst = P.acc + 3 * (int64_t)jorig;
-            red_add_u64(dst + 0, (unsigned long long)(sum & 0xFFFFFFu));
-            red_add_u64(dst + 1, (unsigned long long)((sum >> 24) & 0xFFFFFFu));
-            red_add_u64(dst + 2, (unsigned long long)(sum >> 48));
-          }
-        }
+        if (lane < 16) S.colpart[buf][q][c0 + (int)lane] = make_uint2(cs[0], cq[0]);
       }
       {
         // the row's sum of terms sql + sqh 2^32 + qsum as Rc 2^64 + Rlo
@@ -663,16 +668,43 @@ __global__ void __launch_bounds__(kThreads, 1)
       } else {
         mbar_arrive(&S.tempty[acc]);
       }
-      if (row_orig >= 0) {
-        unsigned long long *dst = P.acc + 3 * (int64_t)row_orig;
-        if constexpr (kDist) {
-          red_add_u64(dst, (unsigned long long)Rd);
-        } else {
-          // Rc 2^64 + Rlo as 24-bit limbs: bits 0-23, 24-47, and the rest (Rc above bit 16)
-          red_add_u64(dst + 0, Rlo & 0xFFFFFFull);
-          red_add_u64(dst + 1, (Rlo >> 24) & 0xFFFFFFull);
-          red_add_u64(dst + 2, (Rlo >> 48) | ((unsigned long long)Rc << 16));
+      if (!kDist && !rect) {
+        // square similarity: the row sums of the two column halves and the column
+        // sums of the four lane quadrants meet in shared memory; then half 0 adds
+        // one row each and half 1 one column each to the keys
+        if (tile_ok && half == 1)
+          S.rowpart[buf][q * 32 + lane] = make_uint4((uint32_t)Rlo, (uint32_t)(Rlo >> 32), Rc, 0u);
+        named_bar_sync(2, kEpiThreads);
+        if (tile_ok && half == 0) {
+          if (row_orig >= 0) {
+            const uint4 o = S.rowpart[buf][q * 32 + lane];
+            const uint64_t lo = Rlo + (((uint64_t)o.y << 32) | o.x);
+            const uint64_t hi = (uint64_t)Rc + o.z + (lo < Rlo ? 1u : 0u);
+            red_key(P.acc + 3 * (int64_t)row_orig, lo, hi);
+          }
+        } else if (tile_ok) {
+          const int c = (int)etid - kRowBlock;  // half 1: one column each
+          const int32_t jorig = S.colorig[buf][c];
+          uint32_t cs = 0, cq = 0;
+#pragma unroll
+          for (int qq = 0; qq < 4; ++qq) {
+            const uint2 v2 = S.colpart[buf][qq][c];
+            cs += v2.x;
+            cq += v2.y;
+          }
+          if (jorig >= 0 && (cs | cq) != 0) {
+            const uint4 rec = S.colrec[buf][c];
+            const uint64_t Q = ((uint64_t)rec.y << 32) | rec.x;
+            const unsigned __int128 sum = (unsigned __int128)Q * cs + cq;
+            red_key(P.acc + 3 * (int64_t)jorig, (uint64_t)sum, (uint64_t)(sum >> 64));
+          }
         }
+      } else if (row_orig >= 0) {
+        unsigned long long *dst = P.acc + 3 * (int64_t)row_orig;
+        if constexpr (kDist)
+          red_add_u64(dst, (unsigned long long)Rd);
+        else
+          red_key(dst, Rlo, Rc);
       }
     }
   }

@@ -135,14 +135,14 @@ __global__ void gather_ref_kernel(RankPtrs P, const int32_t *__restrict__ inv,
   }
 }
 
-// key = acc0 + acc1 2^24 + acc2 2^48; rank = (hi + lo 2^-64) / |R|.
+// key = acc0 + acc1 2^32; rank = (hi + lo 2^-64) / |R|.
 __global__ void finalize_vs_kernel(RankPtrs P, int32_t n_ref, uint64_t *__restrict__ key_hi,
                                    uint64_t *__restrict__ key_lo, double *__restrict__ rank) {
   if (P.hdr->status != 0) return;
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < P.n_total;
        x += (int64_t)gridDim.x * blockDim.x) {
-    const unsigned __int128 a0 = P.acc[3 * x + 0], a1 = P.acc[3 * x + 1], a2 = P.acc[3 * x + 2];
-    const unsigned __int128 key = a0 + (a1 << 24) + (a2 << 48);
+    const unsigned __int128 a0 = P.acc[3 * x + 0], a1 = P.acc[3 * x + 1];
+    const unsigned __int128 key = a0 + (a1 << 32);
     const uint64_t hi = (uint64_t)(key >> 64), lo = (uint64_t)key;
     key_hi[x] = hi;
     key_lo[x] = lo;

@@ -58,7 +58,7 @@ struct RankPtrs {
   uint4 *rec;            // [rows_total] division record of each stored row's m
   uint2 *recw;           // [rows_total] floor_weight of each stored row's m
   int2 *tiles;           // [tiles_total] (I | J << 16, K chunks), global block indices
-  unsigned long long *acc;  // [n_total][3] 24-bit-limb accumulators of the keys
+  unsigned long long *acc;  // [n_total][3] key = acc0 + acc1 2^32 (distance mode: acc0)
   uint8_t *planes;       // [rows_total][K_cap] fp8 threshold planes (sections 1..depth)
   // residual of the counts above the plane depth, per (set, word)
   int32_t *cnt_gt;       // [n_sets * eps] sequences whose count of the word exceeds depth
