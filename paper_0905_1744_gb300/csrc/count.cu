@@ -257,9 +257,10 @@ int launch_count_warp(const uint8_t *codes, const int64_t *offsets, int32_t n, i
 // rows): the 8 warps share a shared histogram, double-buffered: while the CTA writes
 // one sequence's row out of one buffer, the threads holding the next sequence's
 // bytes count it into the other, so a sequence costs one barrier and its counting
-// hides behind the previous row's stores. Thread t always writes the column octets
-// o = t + kCtaThreads * pass, so the words it has seen occur fit one 32-bit register
-// (8 bits per pass); counts >= 2 go to per-CTA byte maxima as in the warp kernel.
+// hides behind the previous row's stores. Thread t always writes the column quads
+// o = t + kCtaThreads * pass (16 bytes each, so a warp store covers 512 contiguous
+// bytes), and the words it has seen occur fit one 32-bit register (4 bits per
+// pass); counts >= 2 go to per-CTA byte maxima as in the warp kernel.
 constexpr int kCtaThreads = 256;
 
 template <int K>
@@ -338,7 +339,7 @@ __global__ void __launch_bounds__(kCtaThreads) kmer_count_cta_kernel(
   uint32_t present = 0;
   __syncthreads();
   const int64_t codes_end = offsets[n];
-  const int octets = eps >> 3;
+  const int quads = eps >> 2;  // at most 8 kCtaThreads: 4 presence bits a pass fit `present`
   int64_t x = blockIdx.x;
   if (x < n) {
     const bool bad = cta_take_sequence<K>(codes, offsets, codes_end, x, alphabet, eps, histbuf, hdr);
@@ -350,35 +351,27 @@ __global__ void __launch_bounds__(kCtaThreads) kmer_count_cta_kernel(
     const int64_t xn = x + gridDim.x;
     bool badn = false;
     if (xn < n) badn = cta_take_sequence<K>(codes, offsets, codes_end, xn, alphabet, eps, nxt, hdr);
-    // the row of x: octet o = tid + kCtaThreads pass, one 16-byte shared load (and
-    // clear) and two 16-byte stores
-    uint4 *h4 = reinterpret_cast<uint4 *>(cur);
+    // the row of x: quad o = tid + kCtaThreads pass (4 counts), one 8-byte shared
+    // load (and clear) and one 16-byte store, so a warp writes 512 contiguous bytes
+    uint2 *h2 = reinterpret_cast<uint2 *>(cur);
     int4 *row4 = reinterpret_cast<int4 *>(counts + x * (int64_t)eps);
     int pass = 0;
-    for (int o = tid; o < octets; o += kCtaThreads, ++pass) {
-      const uint4 h = h4[o];
-      h4[o] = make_uint4(0, 0, 0, 0);
-      row4[2 * o] = make_int4((int)(h.x & 0xFFFFu), (int)(h.x >> 16), (int)(h.y & 0xFFFFu),
-                              (int)(h.y >> 16));
-      row4[2 * o + 1] = make_int4((int)(h.z & 0xFFFFu), (int)(h.z >> 16), (int)(h.w & 0xFFFFu),
-                                  (int)(h.w >> 16));
+    for (int o = tid; o < quads; o += kCtaThreads, ++pass) {
+      const uint2 h = h2[o];
+      h2[o] = make_uint2(0, 0);
+      row4[o] = make_int4((int)(h.x & 0xFFFFu), (int)(h.x >> 16), (int)(h.y & 0xFFFFu),
+                          (int)(h.y >> 16));
       if (word_max) {
-        const uint32_t any = h.x | h.y | h.z | h.w;
+        const uint32_t any = h.x | h.y;
         if (any) {
-          const uint32_t hw[4] = {h.x, h.y, h.z, h.w};
-          uint32_t nz = 0;
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const uint32_t m = __vcmpne2(hw[u], 0u);
-            nz |= ((m & 1u) | ((m >> 15) & 2u)) << (2 * u);
-          }
-          present |= nz << (8 * pass);
+          const uint32_t m0 = __vcmpne2(h.x, 0u), m1 = __vcmpne2(h.y, 0u);
+          const uint32_t nz = (m0 & 1u) | ((m0 >> 15) & 2u) | ((m1 & 1u) << 2) | ((m1 >> 13) & 8u);
+          present |= nz << (4 * pass);
           if (any & 0xFFFEFFFEu) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              note_repeat(max8, word_max, 8 * o + 2 * u, (int32_t)(hw[u] & 0xFFFFu));
-              note_repeat(max8, word_max, 8 * o + 2 * u + 1, (int32_t)(hw[u] >> 16));
-            }
+            note_repeat(max8, word_max, 4 * o + 0, (int32_t)(h.x & 0xFFFFu));
+            note_repeat(max8, word_max, 4 * o + 1, (int32_t)(h.x >> 16));
+            note_repeat(max8, word_max, 4 * o + 2, (int32_t)(h.y & 0xFFFFu));
+            note_repeat(max8, word_max, 4 * o + 3, (int32_t)(h.y >> 16));
           }
         }
       }
@@ -389,11 +382,11 @@ __global__ void __launch_bounds__(kCtaThreads) kmer_count_cta_kernel(
   if (word_max) {
     __syncthreads();
     int pass = 0;
-    for (int o = tid; o < octets; o += kCtaThreads, ++pass) {
-      for (int u = 0; u < 8; ++u) {
-        const int t = 8 * o + u;
-        const int32_t m8 = (int32_t)((max8[t >> 2] >> (8 * (t & 3))) & 0xFFu);
-        const int32_t v = m8 > 0 ? m8 : (int32_t)((present >> (8 * pass + u)) & 1u);
+    for (int o = tid; o < quads; o += kCtaThreads, ++pass) {
+      for (int u = 0; u < 4; ++u) {
+        const int t = 4 * o + u;
+        const int32_t m8 = (int32_t)((max8[o] >> (8 * u)) & 0xFFu);
+        const int32_t v = m8 > 0 ? m8 : (int32_t)((present >> (4 * pass + u)) & 1u);
         if (v && v > *(volatile int32_t *)(word_max + t)) atomicMax(word_max + t, v);
       }
     }
