@@ -31,6 +31,10 @@ __device__ __forceinline__ uint32_t byte_of(const uint32_t (&w)[8], int b) {
   return (w[b >> 2] >> (8 * (b & 3))) & 0xFFu;
 }
 
+__device__ __forceinline__ uint32_t byte_of3(const uint32_t (&w)[3], int b) {
+  return (w[b >> 2] >> (8 * (b & 3))) & 0xFFu;
+}
+
 // Word t has count c >= 2 in one sequence: raise its byte maximum (compare-and-swap
 // on the containing word), counts above 255 go to the global maximum directly.
 __device__ __forceinline__ void note_repeat(uint32_t *max8, int32_t *word_max, int t, int32_t c) {
@@ -269,35 +273,45 @@ __device__ __forceinline__ bool cta_count_sequence(const uint8_t *__restrict__ c
                                                    int32_t alphabet, int32_t eps,
                                                    uint32_t *hist) {
   bool bad = false;
-  // 16 bytes per thread per step; the k - 1 bytes past them come from the next
-  // 16-byte load (L1)
-  for (int64_t c = (s & ~(int64_t)15) + 16 * threadIdx.x; c < e; c += 16 * kCtaThreads) {
+  // eight threads per 16-byte chunk, two windows each (a sequence of a few hundred
+  // codes spreads over half of the CTA); the chunk and the k - 1 bytes past it come
+  // from two 16-byte loads, shared through L1
+  const int part = (int)(threadIdx.x & 7u);
+  for (int64_t c = (s & ~(int64_t)15) + 16 * (threadIdx.x >> 3); c < e;
+       c += 16 * (kCtaThreads / 8)) {
     const uint4 v = load16_guarded(codes, c, codes_end);
     const uint4 nx = (K > 1 && c + 16 < e) ? load16_guarded(codes, c + 16, codes_end)
                                            : make_uint4(0, 0, 0, 0);
-    const uint32_t w[8] = {v.x, v.y, v.z, v.w, nx.x, nx.y, nx.z, nx.w};
-    if (c >= s && c + 16 + K - 1 <= e) {
-      if (alphabet < 256) {
-        const uint32_t lim = 0x01010101u * (uint32_t)alphabet;
-        bad |= (__vcmpgeu4(v.x, lim) | __vcmpgeu4(v.y, lim) | __vcmpgeu4(v.z, lim) |
-                __vcmpgeu4(v.w, lim)) != 0u;
-      }
+    // bytes 2 part .. 2 part + 9 of the two loads: the words from 4 (part / 2) on,
+    // shifted right by 2 (part & 1) bytes
+    const int q = part >> 1;
+    const uint32_t a0 = q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w;
+    const uint32_t a1 = q == 0 ? v.y : q == 1 ? v.z : q == 2 ? v.w : nx.x;
+    const uint32_t a2 = q == 0 ? v.z : q == 1 ? v.w : q == 2 ? nx.x : nx.y;
+    const uint32_t a3 = q == 0 ? v.w : q == 1 ? nx.x : q == 2 ? nx.y : nx.z;
+    const uint32_t sh = 16u * (uint32_t)(part & 1);
+    const uint32_t w[3] = {__funnelshift_r(a0, a1, sh), __funnelshift_r(a1, a2, sh),
+                           __funnelshift_r(a2, a3, sh)};
+    const int64_t c2 = c + 2 * part;
+    if (c2 >= s && c2 + 2 + K - 1 <= e) {
+      if (alphabet < 256)
+        bad |= (__vcmpgeu4(w[0], 0x01010101u * (uint32_t)alphabet) & 0xFFFFu) != 0u;
 #pragma unroll
-      for (int b = 0; b < 16; ++b) {
+      for (int b = 0; b < 2; ++b) {
         uint32_t tau = 0;
 #pragma unroll
-        for (int r = 0; r < K; ++r) tau = tau * (uint32_t)alphabet + byte_of(w, b + r);
+        for (int r = 0; r < K; ++r) tau = tau * (uint32_t)alphabet + byte_of3(w, b + r);
         if (tau < (uint32_t)eps) atomicAdd(&hist[tau >> 1], 1u << (16 * (tau & 1)));
       }
     } else {
 #pragma unroll
-      for (int b = 0; b < 16; ++b) {
-        const int64_t pos = c + b;
-        if (pos >= s && pos < e && byte_of(w, b) >= (uint32_t)alphabet) bad = true;
+      for (int b = 0; b < 2; ++b) {
+        const int64_t pos = c2 + b;
+        if (pos >= s && pos < e && byte_of3(w, b) >= (uint32_t)alphabet) bad = true;
         if (pos >= s && pos + K <= e) {
           uint32_t tau = 0;
 #pragma unroll
-          for (int r = 0; r < K; ++r) tau = tau * (uint32_t)alphabet + byte_of(w, b + r);
+          for (int r = 0; r < K; ++r) tau = tau * (uint32_t)alphabet + byte_of3(w, b + r);
           if (tau < (uint32_t)eps) atomicAdd(&hist[tau >> 1], 1u << (16 * (tau & 1)));
         }
       }
