@@ -71,6 +71,7 @@ __global__ void __launch_bounds__(128) kmer_count_kernel(const uint8_t *__restri
                                                         int32_t *__restrict__ counts,
                                                         int32_t *__restrict__ word_max,
                                                         WsHeader *hdr) {
+  pdl_enter();
   extern __shared__ uint32_t smem[];
   const int warps = blockDim.x >> 5;
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -251,8 +252,8 @@ int launch_count_warp(const uint8_t *codes, const int64_t *offsets, int32_t n, i
   const int64_t need = (n + warps - 1) / warps;
   if (blocks > need) blocks = need;
   if (blocks < 1) blocks = 1;
-  kern<<<(unsigned)blocks, warps * 32, smem, st>>>(codes, offsets, n, alphabet, eps, counts,
-                                                   word_max, hdr);
+  pdl_launch(kern, (unsigned)blocks, warps * 32, smem, st, codes, offsets, n, alphabet, eps, counts,
+             word_max, hdr);
   SAD_LAUNCH_CHECK();
   return SAD_OK;
 }
@@ -343,6 +344,7 @@ __global__ void __launch_bounds__(kCtaThreads) kmer_count_cta_kernel(
     const uint8_t *__restrict__ codes, const int64_t *__restrict__ offsets, int32_t n,
     int32_t alphabet, int32_t eps, int32_t *__restrict__ counts, int32_t *__restrict__ word_max,
     WsHeader *hdr) {
+  pdl_enter();
   extern __shared__ uint32_t smem[];
   uint32_t *histbuf = smem;                   // 2 x [eps / 2]
   uint32_t *max8 = smem + eps;                // [eps / 4]
@@ -427,8 +429,8 @@ int launch_count(const uint8_t *codes, const int64_t *offsets, int32_t n, int32_
     int64_t blocks = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
     if (blocks > n) blocks = n;
     if (blocks < 1) blocks = 1;
-    kern<<<(unsigned)blocks, kCtaThreads, smem, st>>>(codes, offsets, n, alphabet, eps, counts,
-                                                     word_max, hdr);
+    pdl_launch(kern, (unsigned)blocks, kCtaThreads, smem, st, codes, offsets, n, alphabet, eps,
+               counts, word_max, hdr);
     SAD_LAUNCH_CHECK();
     return SAD_OK;
   }

@@ -42,12 +42,14 @@ __device__ __forceinline__ int64_t ln_q_dev(uint64_t x) {
 }
 
 __global__ void ln_table_kernel(int64_t *table, int64_t n) {
+  pdl_enter();
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
        x += (int64_t)gridDim.x * blockDim.x)
     table[x] = ln_q_dev((uint64_t)x);
 }
 
 __global__ void ln_q_kernel(const uint64_t *x, int64_t n, int64_t *out) {
+  pdl_enter();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     out[i] = ln_q_dev(x[i]);
@@ -58,6 +60,7 @@ __global__ void ln_q_kernel(const uint64_t *x, int64_t n, int64_t *out) {
 __global__ void dist_finalize_kernel(RankPtrs P, int64_t *key, uint64_t *__restrict__ key_hi,
                                      uint64_t *__restrict__ key_lo, double *__restrict__ rank,
                                      int64_t n_div) {
+  pdl_enter();
   if (P.hdr->status != 0) return;
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < P.n_total;
        x += (int64_t)gridDim.x * blockDim.x) {
@@ -84,22 +87,22 @@ size_t ln_table_entries(int32_t b) { return (size_t)(b + 1) * (size_t)kMaxM + 1;
 
 int ln_table_launch(int64_t *table, int32_t b, cudaStream_t st) {
   const int64_t n = (int64_t)ln_table_entries(b);
-  ln_table_kernel<<<grid_of(n, 256), 256, 0, st>>>(table, n);
+  pdl_launch(ln_table_kernel, grid_of(n, 256), 256, 0, st, table, n);
   SAD_LAUNCH_CHECK();
   return SAD_OK;
 }
 
 int ln_q_launch(const uint64_t *x, int64_t n, int64_t *out, cudaStream_t st) {
   if (n <= 0) return SAD_OK;
-  ln_q_kernel<<<grid_of(n, 256), 256, 0, st>>>(x, n, out);
+  pdl_launch(ln_q_kernel, grid_of(n, 256), 256, 0, st, x, n, out);
   SAD_LAUNCH_CHECK();
   return SAD_OK;
 }
 
 int rank_dist_finalize_launch(const RankPtrs &P, int64_t *key, uint64_t *key_hi,
                               uint64_t *key_lo, double *rank, int64_t n_div, cudaStream_t st) {
-  dist_finalize_kernel<<<grid_of(P.n_total, 256), 256, 0, st>>>(P, key, key_hi, key_lo, rank,
-                                                                  n_div);
+  pdl_launch(dist_finalize_kernel, grid_of(P.n_total, 256), 256, 0, st, P, key, key_hi, key_lo,
+             rank, n_div);
   SAD_LAUNCH_CHECK();
   return SAD_OK;
 }

@@ -221,6 +221,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     plane_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                       const __grid_constant__ CUtensorMap tmB, RankPtrs P, RectArgs X,
                       DistArgs Z) {
+  pdl_enter();
   extern __shared__ uint8_t smem_raw[];
   GemmSmem &S = *reinterpret_cast<GemmSmem *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -863,8 +864,8 @@ int rank_gemm_launch(const RankPtrs &P, cudaStream_t st) {
   bool done = false;
   if ((rc = launch_pair<false>(P, mA, DistArgs{}, st, &done))) return rc;
   if (!done)
-    plane_gemm_kernel<false, false>
-        <<<(unsigned)grid, kThreads, kGemmSmemBytes, st>>>(mA, mB, P, RectArgs{}, DistArgs{});
+    pdl_launch(plane_gemm_kernel<false, false>, (unsigned)grid, kThreads, kGemmSmemBytes, st, mA,
+               mB, P, RectArgs{}, DistArgs{});
   SAD_LAUNCH_CHECK();
   prof_end(st);
   return SAD_OK;
@@ -887,8 +888,8 @@ int rank_dist_gemm_launch(const RankPtrs &P, const int64_t *ln_table, int32_t b,
   bool done = false;
   if ((rc = launch_pair<true>(P, mA, Z, st, &done))) return rc;
   if (!done)
-    plane_gemm_kernel<true, false>
-        <<<(unsigned)grid, kThreads, kGemmSmemBytes, st>>>(mA, mB, P, RectArgs{}, Z);
+    pdl_launch(plane_gemm_kernel<true, false>, (unsigned)grid, kThreads, kGemmSmemBytes, st, mA, mB,
+               P, RectArgs{}, Z);
   SAD_LAUNCH_CHECK();
   return SAD_OK;
 }
@@ -915,11 +916,11 @@ int rank_rect_gemm_launch(const RankPtrs &P, uint8_t *ref_planes, const uint4 *r
     DistArgs Z;
     Z.ln_table = ln_table;
     Z.b = b;
-    plane_gemm_kernel<true, false>
-        <<<(unsigned)grid, kThreads, kGemmSmemBytes, st>>>(mA, mB, P, X, Z);
+    pdl_launch(plane_gemm_kernel<true, false>, (unsigned)grid, kThreads, kGemmSmemBytes, st, mA, mB,
+               P, X, Z);
   } else {
-    plane_gemm_kernel<false, false>
-        <<<(unsigned)grid, kThreads, kGemmSmemBytes, st>>>(mA, mB, P, X, DistArgs{});
+    pdl_launch(plane_gemm_kernel<false, false>, (unsigned)grid, kThreads, kGemmSmemBytes, st, mA,
+               mB, P, X, DistArgs{});
   }
   SAD_LAUNCH_CHECK();
   return SAD_OK;

@@ -39,6 +39,7 @@ SamplesLayout samples_layout(int64_t n, int64_t p) {
 
 __global__ void samples_setup_kernel(const uint64_t *__restrict__ hi, const uint64_t *__restrict__ lo,
                                      int32_t n, int32_t p, int64_t *segoff, Item *items) {
+  pdl_enter();
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nt = (int64_t)gridDim.x * blockDim.x;
   for (int64_t b = tid; b <= p; b += nt) segoff[b] = b * (int64_t)n / p;
@@ -55,6 +56,7 @@ __global__ void samples_setup_kernel(const uint64_t *__restrict__ hi, const uint
 __global__ void __launch_bounds__(kSortThreads) block_sort_kernel(Item *items, Item *scratch,
                                                                    int32_t p,
                                                                    const int64_t *segoff) {
+  pdl_enter();
   extern __shared__ Item sm[];
   for (int32_t b = blockIdx.x; b < p; b += gridDim.x) {
     const int64_t a = segoff[b], e = segoff[b + 1];
@@ -64,6 +66,7 @@ __global__ void __launch_bounds__(kSortThreads) block_sort_kernel(Item *items, I
 
 __global__ void pick_samples_kernel(const Item *items, const int64_t *segoff, int32_t p,
                                     int32_t ks, int32_t *sample_idx) {
+  pdl_enter();
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)p * ks;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b = t / ks, j = t % ks + 1;
@@ -96,6 +99,7 @@ RefLayout ref_layout(size_t base, int64_t n_pad, int64_t n_ref, int64_t k_cap, i
 }
 
 __global__ void inv_perm_kernel(RankPtrs P, int32_t *inv) {
+  pdl_enter();
   if (P.hdr->status != 0) return;
   for (int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pos < P.n_pad;
        pos += (int64_t)gridDim.x * blockDim.x) {
@@ -109,6 +113,7 @@ __global__ void inv_perm_kernel(RankPtrs P, int32_t *inv) {
 __global__ void gather_ref_kernel(RankPtrs P, const int32_t *__restrict__ inv,
                                   const int32_t *__restrict__ ref, int32_t n_ref,
                                   int64_t ref_rows, uint8_t *ref_planes, uint4 *rec_ref) {
+  pdl_enter();
   if (P.hdr->status != 0) return;
   const int64_t row_bytes = P.k_cap / 2;
   const int64_t used = P.hdr->k_pad / 2;  // multiple of 128
@@ -138,6 +143,7 @@ __global__ void gather_ref_kernel(RankPtrs P, const int32_t *__restrict__ inv,
 // key = acc0 + acc1 2^32; rank = (hi + lo 2^-64) / |R|.
 __global__ void finalize_vs_kernel(RankPtrs P, int32_t n_ref, uint64_t *__restrict__ key_hi,
                                    uint64_t *__restrict__ key_lo, double *__restrict__ rank) {
+  pdl_enter();
   if (P.hdr->status != 0) return;
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < P.n_total;
        x += (int64_t)gridDim.x * blockDim.x) {
@@ -180,14 +186,14 @@ int local_samples_launch(const uint64_t *key_hi, const uint64_t *key_lo, int32_t
       return SAD_ERR_CUDA;
     attr = true;
   }
-  samples_setup_kernel<<<grid_of((int64_t)n + p + 1, 256), 256, 0, st>>>(key_hi, key_lo, n, p,
-                                                                         segoff, items);
+  pdl_launch(samples_setup_kernel, grid_of((int64_t)n + p + 1, 256), 256, 0, st, key_hi, key_lo, n,
+             p, segoff, items);
   SAD_LAUNCH_CHECK();
-  block_sort_kernel<<<(unsigned)(p < 65535 ? p : 65535), kSortThreads, kSortSmem, st>>>(
-      items, scratch, p, segoff);
+  pdl_launch(block_sort_kernel, (unsigned)(p < 65535 ? p : 65535), kSortThreads, kSortSmem, st,
+             items, scratch, p, segoff);
   SAD_LAUNCH_CHECK();
-  pick_samples_kernel<<<grid_of((int64_t)p * ks, 256), 256, 0, st>>>(items, segoff, p, ks,
-                                                                     sample_idx);
+  pdl_launch(pick_samples_kernel, grid_of((int64_t)p * ks, 256), 256, 0, st, items, segoff, p, ks,
+             sample_idx);
   SAD_LAUNCH_CHECK();
   return SAD_OK;
 }
@@ -216,15 +222,15 @@ int rank_vs_launch(const int32_t *counts, const int32_t *lengths, const int32_t 
   if (table && (rc = ln_table_launch(table, delta_den, st))) return rc;
   rc = rank_prep_launch(P, counts, lengths, nullptr, word_max, k, (int32_t)eps, 0, st);
   if (rc) return rc;
-  inv_perm_kernel<<<grid_of(P.n_pad, 256), 256, 0, st>>>(P, inv);
+  pdl_launch(inv_perm_kernel, grid_of(P.n_pad, 256), 256, 0, st, P, inv);
   SAD_LAUNCH_CHECK();
-  gather_ref_kernel<<<(unsigned)(R.ref_rows < 65535 ? R.ref_rows : 65535), 256, 0, st>>>(
-      P, inv, ref, n_ref, R.ref_rows, ref_planes, rec_ref);
+  pdl_launch(gather_ref_kernel, (unsigned)(R.ref_rows < 65535 ? R.ref_rows : 65535), 256, 0, st, P,
+             inv, ref, n_ref, R.ref_rows, ref_planes, rec_ref);
   SAD_LAUNCH_CHECK();
   rc = rank_rect_gemm_launch(P, ref_planes, rec_ref, R.ref_rows, n_ref, table, delta_den, st);
   if (rc) return rc;
   if (table) return rank_dist_finalize_launch(P, key, key_hi, key_lo, rank, n_ref, st);
-  finalize_vs_kernel<<<grid_of(n, 256), 256, 0, st>>>(P, n_ref, key_hi, key_lo, rank);
+  pdl_launch(finalize_vs_kernel, grid_of(n, 256), 256, 0, st, P, n_ref, key_hi, key_lo, rank);
   SAD_LAUNCH_CHECK();
   return SAD_OK;
 }

@@ -43,6 +43,7 @@ __device__ __forceinline__ int32_t set_of(const PartSet *sets, int32_t n_sets, i
 __global__ void __launch_bounds__(1024) part_setup_kernel(const int32_t *d_n, const int32_t *d_p,
                                                           int32_t n_sets, int32_t n1, int32_t p1,
                                                           PartSet *sets, int64_t *segoff) {
+  pdl_enter();
   __shared__ int64_t s_warp[32];
   __shared__ int64_t s_c[5];
   const int tid = threadIdx.x;
@@ -95,6 +96,7 @@ __global__ void __launch_bounds__(1024) part_setup_kernel(const int32_t *d_n, co
 
 __global__ void part_init_kernel(const uint64_t *__restrict__ hi, const uint64_t *__restrict__ lo,
                                  int64_t n, const PartSet *sets, int32_t n_sets, Item *items) {
+  pdl_enter();
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
        x += (int64_t)gridDim.x * blockDim.x) {
     Item it;
@@ -110,6 +112,7 @@ __global__ void part_init_kernel(const uint64_t *__restrict__ hi, const uint64_t
 __global__ void __launch_bounds__(kSortThreads) seg_sort_kernel(Item *items, Item *scratch,
                                                                  int64_t n_seg,
                                                                  const int64_t *offs) {
+  pdl_enter();
   extern __shared__ Item sm[];
   for (int64_t s = blockIdx.x; s < n_seg; s += gridDim.x) {
     const int64_t lo = offs[s], hi = offs[s + 1];
@@ -123,6 +126,7 @@ __global__ void __launch_bounds__(kSortThreads) samples_kernel(const Item *items
                                                                 int32_t *pivot_idx,
                                                                 const PartSet *sets,
                                                                 int32_t n_sets) {
+  pdl_enter();
   extern __shared__ Item sm[];
   for (int32_t si = blockIdx.x; si < n_sets; si += gridDim.x) {
     const PartSet S = sets[si];
@@ -151,6 +155,7 @@ __global__ void __launch_bounds__(kSortThreads) samples_kernel(const Item *items
 // blockIdx.y = set.
 __global__ void subblocks_kernel(const Item *items, const Item *piv_all, int32_t *pos_all,
                                  const PartSet *sets) {
+  pdl_enter();
   const PartSet S = sets[blockIdx.y];
   const int64_t n = S.n, p = S.p, total = p * p;
   const Item *it = items + S.seq_begin;
@@ -172,6 +177,7 @@ __global__ void __launch_bounds__(1024) bucket_scan_kernel(const int32_t *pos_al
                                                            int64_t *gbound,
                                                            const PartSet *sets,
                                                            int32_t n_sets) {
+  pdl_enter();
   __shared__ int32_t s_warp[32];
   __shared__ int32_t s_carry;
   const int tid = threadIdx.x;
@@ -230,6 +236,7 @@ __global__ void __launch_bounds__(1024) bucket_scan_kernel(const int32_t *pos_al
 __global__ void scatter_kernel(const Item *items, Item *out, const int32_t *pos_all,
                                const int32_t *dest_all, int64_t n_total, const PartSet *sets,
                                int32_t n_sets) {
+  pdl_enter();
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n_total;
        x += (int64_t)gridDim.x * blockDim.x) {
     const PartSet S = sets[set_of(sets, n_sets, x)];
@@ -263,6 +270,7 @@ constexpr int kFastP = 64;
 
 // (blockIdx.y = block b, blockIdx.x = chunk of the block): sort it in place.
 __global__ void __launch_bounds__(128) chunk_sort_kernel(Item *items, const int64_t *segoff) {
+  pdl_enter();
   __shared__ Item sm[kChunk];
   const int64_t a = segoff[blockIdx.y], e = segoff[blockIdx.y + 1];
   const int64_t lo = a + (int64_t)blockIdx.x * kChunk;
@@ -281,6 +289,7 @@ __device__ __forceinline__ int64_t block_of_item(int64_t x, int64_t n, int64_t p
 // other chunks (a few binary searches).
 __global__ void chunk_merge_kernel(const Item *__restrict__ in, Item *__restrict__ out,
                                    int64_t n, int64_t p) {
+  pdl_enter();
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
        x += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b = block_of_item(x, n, p);
@@ -302,6 +311,7 @@ __global__ void chunk_merge_kernel(const Item *__restrict__ in, Item *__restrict
 __global__ void bucket_place_kernel(const Item *__restrict__ sorted, const int32_t *pos,
                                     const int32_t *boff, int32_t *members, int64_t n,
                                     int64_t p) {
+  pdl_enter();
   const int lane = threadIdx.x & 31;
   for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n;
        x += ((int64_t)gridDim.x * blockDim.x) >> 5) {
@@ -328,6 +338,7 @@ __global__ void bucket_place_kernel(const Item *__restrict__ sorted, const int32
 }
 
 __global__ void members_kernel(const Item *items, int32_t *members, int64_t n) {
+  pdl_enter();
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
        x += (int64_t)gridDim.x * blockDim.x)
     members[x] = items[x].idx;
@@ -377,58 +388,62 @@ int partition_sets_launch(const uint64_t *key_hi, const uint64_t *key_lo, int32_
   const int64_t n = tot.n;
   const unsigned gsets = (unsigned)(n_sets < 65535 ? n_sets : 65535);
   const unsigned gseg = (unsigned)(tot.p < 65535 * 4 ? tot.p : 65535 * 4);
-  part_setup_kernel<<<1, 1024, 0, st>>>(d_n, d_p, n_sets, n_single, p_single, sets, segoff);
+  pdl_launch(part_setup_kernel, 1, 1024, 0, st, d_n, d_p, n_sets, n_single, p_single, sets, segoff);
   SAD_LAUNCH_CHECK();
-  part_init_kernel<<<grid_for(n, 256), 256, 0, st>>>(key_hi, key_lo, n, sets, n_sets, items);
+  pdl_launch(part_init_kernel, grid_for(n, 256), 256, 0, st, key_hi, key_lo, n, sets, n_sets,
+             items);
   SAD_LAUNCH_CHECK();
   // one set of small blocks and few buckets: chunk sorts and rank merges
   const int64_t w_max = d_n || p_single < 1 ? 0 : ((int64_t)n_single + p_single - 1) / p_single;
   if (!d_n && n_single > 0 && p_single <= kFastP && w_max <= (int64_t)kFastChunks * kChunk) {
     dim3 gc((unsigned)((w_max + kChunk - 1) / kChunk), (unsigned)p_single);
-    chunk_sort_kernel<<<gc, 128, 0, st>>>(items, segoff);
+    pdl_launch(chunk_sort_kernel, gc, 128, 0, st, items, segoff);
     SAD_LAUNCH_CHECK();
-    chunk_merge_kernel<<<grid_for(n, 128), 128, 0, st>>>(items, items2, n, p_single);
+    pdl_launch(chunk_merge_kernel, grid_for(n, 128), 128, 0, st, items, items2, n, p_single);
     SAD_LAUNCH_CHECK();
     if (max_p > 1) {
-      samples_kernel<<<gsets, kSortThreads, kSortSmem, st>>>(items2, Y, Y2, piv, pivot_idx, sets,
-                                                             n_sets);
+      pdl_launch(samples_kernel, gsets, kSortThreads, kSortSmem, st, items2, Y, Y2, piv, pivot_idx,
+                 sets, n_sets);
       SAD_LAUNCH_CHECK();
     }
     {
       const int64_t pp = (int64_t)max_p * max_p;
       dim3 g((unsigned)((pp + 255) / 256 < 1024 ? (pp + 255) / 256 : 1024), (unsigned)n_sets);
-      subblocks_kernel<<<g, 256, 0, st>>>(items2, piv, pos, sets);
+      pdl_launch(subblocks_kernel, g, 256, 0, st, items2, piv, pos, sets);
       SAD_LAUNCH_CHECK();
     }
-    bucket_scan_kernel<<<gsets, 1024, 0, st>>>(pos, dest, bucket_offsets, gbound, sets, n_sets);
+    pdl_launch(bucket_scan_kernel, gsets, 1024, 0, st, pos, dest, bucket_offsets, gbound, sets,
+               n_sets);
     SAD_LAUNCH_CHECK();
     // a warp per item, all resident at once
-    bucket_place_kernel<<<(unsigned)((n * 32 + 255) / 256 < 65535 * 16 ? (n * 32 + 255) / 256
-                                                                      : 65535 * 16),
-                          256, 0, st>>>(items2, pos, bucket_offsets, members, n, p_single);
+    pdl_launch(bucket_place_kernel,
+               (unsigned)((n * 32 + 255) / 256 < 65535 * 16 ? (n * 32 + 255) / 256 : 65535 * 16),
+               256, 0, st, items2, pos, bucket_offsets, members, n, p_single);
     SAD_LAUNCH_CHECK();
     return SAD_OK;
   }
-  seg_sort_kernel<<<gseg, kSortThreads, kSortSmem, st>>>(items, items2, tot.p, segoff);
+  pdl_launch(seg_sort_kernel, gseg, kSortThreads, kSortSmem, st, items, items2, tot.p, segoff);
   SAD_LAUNCH_CHECK();
   if (max_p > 1) {
-    samples_kernel<<<gsets, kSortThreads, kSortSmem, st>>>(items, Y, Y2, piv, pivot_idx, sets,
-                                                           n_sets);
+    pdl_launch(samples_kernel, gsets, kSortThreads, kSortSmem, st, items, Y, Y2, piv, pivot_idx,
+               sets, n_sets);
     SAD_LAUNCH_CHECK();
   }
   {
     const int64_t pp = (int64_t)max_p * max_p;
     dim3 g((unsigned)((pp + 255) / 256 < 1024 ? (pp + 255) / 256 : 1024), (unsigned)n_sets);
-    subblocks_kernel<<<g, 256, 0, st>>>(items, piv, pos, sets);
+    pdl_launch(subblocks_kernel, g, 256, 0, st, items, piv, pos, sets);
     SAD_LAUNCH_CHECK();
   }
-  bucket_scan_kernel<<<gsets, 1024, 0, st>>>(pos, dest, bucket_offsets, gbound, sets, n_sets);
+  pdl_launch(bucket_scan_kernel, gsets, 1024, 0, st, pos, dest, bucket_offsets, gbound, sets,
+             n_sets);
   SAD_LAUNCH_CHECK();
-  scatter_kernel<<<grid_for(n, 256), 256, 0, st>>>(items, items2, pos, dest, n, sets, n_sets);
+  pdl_launch(scatter_kernel, grid_for(n, 256), 256, 0, st, items, items2, pos, dest, n, sets,
+             n_sets);
   SAD_LAUNCH_CHECK();
-  seg_sort_kernel<<<gseg, kSortThreads, kSortSmem, st>>>(items2, items, tot.p, gbound);
+  pdl_launch(seg_sort_kernel, gseg, kSortThreads, kSortSmem, st, items2, items, tot.p, gbound);
   SAD_LAUNCH_CHECK();
-  members_kernel<<<grid_for(n, 256), 256, 0, st>>>(items2, members, n);
+  pdl_launch(members_kernel, grid_for(n, 256), 256, 0, st, items2, members, n);
   SAD_LAUNCH_CHECK();
   return SAD_OK;
 }

@@ -146,6 +146,7 @@ __device__ __forceinline__ int32_t set_of_row(const RankPtrs &P, int64_t r) {
 // One block: the set table (prefix sums of n, padded rows, tiles, tile-map size).
 __global__ void __launch_bounds__(1024) rank_setup_kernel(const int32_t *d_n, int32_t n1,
                                                           RankPtrs P) {
+  pdl_enter();
   __shared__ int64_t s_warp[32];
   __shared__ int64_t s_c[4];
   const int tid = threadIdx.x;
@@ -183,6 +184,7 @@ __global__ void __launch_bounds__(1024) rank_setup_kernel(const int32_t *d_n, in
 
 // Set index of every input sequence and every stored row (batches only).
 __global__ void rank_setmaps_kernel(RankPtrs P) {
+  pdl_enter();
   for (int32_t s = blockIdx.x; s < (int32_t)P.n_sets; s += gridDim.x) {
     const RankSet e = P.sets[s];
     for (int64_t i = threadIdx.x; i < e.n; i += blockDim.x) P.seq_set[e.seq_begin + i] = s;
@@ -192,6 +194,7 @@ __global__ void rank_setmaps_kernel(RankPtrs P) {
 }
 
 __global__ void rank_init_kernel(RankPtrs P, int32_t eps, int with_keys) {
+  pdl_enter();
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nt = (int64_t)gridDim.x * blockDim.x;
   const int64_t we = P.n_sets * (int64_t)eps;
@@ -223,6 +226,7 @@ __global__ void rank_init_kernel(RankPtrs P, int32_t eps, int with_keys) {
 }
 
 __global__ void lengths_kernel(const int32_t *__restrict__ lengths, int32_t k, RankPtrs P) {
+  pdl_enter();
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < P.n_total;
        x += (int64_t)gridDim.x * blockDim.x) {
     const int32_t m = lengths[x] - k + 1;
@@ -241,6 +245,7 @@ __global__ void lengths_kernel(const int32_t *__restrict__ lengths, int32_t k, R
 // set whose count exceeds D. Block (256 words) x (row slice).
 __global__ void colmax_kernel(const int32_t *__restrict__ counts, int32_t eps, RankPtrs P,
                               int count_gt) {
+  pdl_enter();
   const int32_t tau = blockIdx.x * blockDim.x + threadIdx.x;
   if (tau >= eps) return;
   const int32_t D = count_gt ? P.depth_cap : 0;
@@ -301,6 +306,7 @@ __global__ void colmax_kernel(const int32_t *__restrict__ counts, int32_t eps, R
 // T_tau taken from a per-word maximum computed while counting.
 __global__ void copy_word_max_kernel(const int32_t *__restrict__ word_max, int32_t eps,
                                      RankPtrs P) {
+  pdl_enter();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < eps; i += gridDim.x * blockDim.x) {
     const int32_t t = word_max[i];
     if (t < 0) record_error(P.hdr, SAD_ERR_BAD_INPUT, i);
@@ -313,6 +319,7 @@ __global__ void copy_word_max_kernel(const int32_t *__restrict__ word_max, int32
 // sum_{t'<=t} #{tau : T_tau >= t'}, K_eff at the depth cap and (unless plan_only)
 // the column map colmap[col] = tau | t << 16.
 __global__ void __launch_bounds__(1024) colmap_kernel(RankPtrs P, int32_t eps, int plan_only) {
+  pdl_enter();
   __shared__ int32_t s_tmax;
   __shared__ int32_t s_warp[32];
   __shared__ int32_t s_carry;
@@ -434,6 +441,7 @@ __device__ __forceinline__ bool residual_needed(const RankPtrs &P) {
 }
 
 __global__ void __launch_bounds__(256) list_scan_reduce_kernel(RankPtrs P, int64_t we) {
+  pdl_enter();
   __shared__ int64_t s_warp[32];
   const bool on = residual_needed(P);
   const int64_t b0 = (int64_t)blockIdx.x * kScanChunk;
@@ -457,6 +465,7 @@ __global__ void __launch_bounds__(256) list_scan_reduce_kernel(RankPtrs P, int64
 }
 
 __global__ void __launch_bounds__(1024) list_scan_top_kernel(RankPtrs P, int64_t nblk) {
+  pdl_enter();
   __shared__ int64_t s_warp[32];
   __shared__ int64_t s_l, s_p;
   if (threadIdx.x == 0) {
@@ -490,6 +499,7 @@ __global__ void __launch_bounds__(1024) list_scan_top_kernel(RankPtrs P, int64_t
 
 __global__ void __launch_bounds__(256) list_scan_down_kernel(RankPtrs P, int64_t we,
                                                              int plan_only) {
+  pdl_enter();
   __shared__ int64_t s_warp[32];
   __shared__ int64_t s_l, s_p;
   const bool on = residual_needed(P);
@@ -531,6 +541,7 @@ __global__ void __launch_bounds__(256) list_scan_down_kernel(RankPtrs P, int64_t
 // sets of cnt_gt^2, ties by word), at no cost in the GEMM. Their excess entries
 // lose one (the new plane holds it) and leave the residual when nothing remains.
 __global__ void promote_weight_kernel(RankPtrs P, int32_t eps) {
+  pdl_enter();
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < eps;
        t += (int64_t)gridDim.x * blockDim.x) {
     int64_t w = 0;
@@ -551,6 +562,7 @@ __global__ void promote_weight_kernel(RankPtrs P, int32_t eps) {
 // candidates' digit, then the digit where the count from the top reaches the rank).
 __global__ void __launch_bounds__(1024) promote_select_kernel(RankPtrs P, int32_t eps,
                                                               int staged) {
+  pdl_enter();
   extern __shared__ int64_t s_w[];  // [eps] when staged
   __shared__ int32_t s_warp[32];
   __shared__ int32_t s_hist[257];  // + a bin for words that are not candidates
@@ -645,6 +657,7 @@ __global__ void __launch_bounds__(1024) promote_select_kernel(RankPtrs P, int32_
 // Excess entries of promoted words: the plane value at the word's new column, one
 // less excess; entries left with none are dropped (row -1) and uncounted.
 __global__ void promote_apply_kernel(RankPtrs P, int32_t eps) {
+  pdl_enter();
   if (P.hdr->status != 0 || !residual_needed(P) || P.hdr->n_promoted == 0) return;
   const int64_t total = min((int64_t)P.hdr->flat_count, P.list_cap);
   const int64_t row_words = P.k_cap / 8;
@@ -667,6 +680,7 @@ __global__ void promote_apply_kernel(RankPtrs P, int32_t eps) {
 
 // Excess entries from the unordered append into their (set, word) lists.
 __global__ void group_lists_kernel(RankPtrs P, int32_t eps) {
+  pdl_enter();
   if (P.hdr->status != 0 || !residual_needed(P)) return;
   const int64_t total = (int64_t)P.hdr->flat_count;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
@@ -683,6 +697,7 @@ __global__ void group_lists_kernel(RankPtrs P, int32_t eps) {
 // One set: exclusive prefix over m in decreasing order, mhist[m] := #{x : m_x > m},
 // for m = m_max down to 1, 1024 consecutive values per step.
 __global__ void __launch_bounds__(1024) lensort_scan_kernel(RankPtrs P) {
+  pdl_enter();
   __shared__ int32_t s_warp[32];
   __shared__ int32_t s_carry;
   const int tid = threadIdx.x;
@@ -704,6 +719,7 @@ __global__ void __launch_bounds__(1024) lensort_scan_kernel(RankPtrs P) {
 // One set: stored row of every sequence from the counting sort over m.
 __global__ void lensort_place_kernel(const int32_t *__restrict__ lengths, int32_t k,
                                      RankPtrs P) {
+  pdl_enter();
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < P.n_pad;
        x += (int64_t)gridDim.x * blockDim.x) {
     if (x < P.n_total) {
@@ -725,6 +741,7 @@ __global__ void lensort_place_kernel(const int32_t *__restrict__ lengths, int32_
 // and places them (and the set's padding rows) at the set's rows.
 __global__ void __launch_bounds__(kSortThreads) lensort_sets_kernel(
     const int32_t *__restrict__ lengths, int32_t k, RankPtrs P) {
+  pdl_enter();
   extern __shared__ Item sm[];
   Item *buf = P.sortbuf, *scratch = P.sortbuf + P.n_total;
   for (int32_t s = blockIdx.x; s < (int32_t)P.n_sets; s += gridDim.x) {
@@ -777,6 +794,7 @@ __device__ __forceinline__ void stage4(uint16_t *sc, int q, int4 v) {
 
 __global__ void __launch_bounds__(256) planes_kernel(const int32_t *__restrict__ counts,
                                                      int32_t eps, RankPtrs P) {
+  pdl_enter();
   extern __shared__ uint16_t s_cnt[];  // [kPlaneRows][eps]
   __shared__ int32_t s_max[kPlaneRows], s_sum[kPlaneRows];
   __shared__ int32_t s_scan[32];
@@ -943,6 +961,7 @@ __device__ __forceinline__ void plane_set(uint8_t *prow, int32_t col) {
 
 __global__ void __launch_bounds__(256) planes_stream_kernel(const int32_t *__restrict__ counts,
                                                             int32_t eps, RankPtrs P) {
+  pdl_enter();
   __shared__ int2 s_ex[8][kExCap];
   __shared__ int32_t s_exn[8];
   if (P.hdr->status != 0) return;
@@ -1088,6 +1107,7 @@ __device__ __forceinline__ int32_t group_row_tiles(int32_t g, int32_t I, int32_t
 
 // (blockIdx.y: sets in a grid stride; blockIdx.x: column groups in a grid stride)
 __global__ void __launch_bounds__(256) tiles_kernel(RankPtrs P) {
+  pdl_enter();
   __shared__ int32_t s_warp[32];
   __shared__ int32_t s_carry;
   const int tid = threadIdx.x;
@@ -1239,6 +1259,7 @@ __device__ __forceinline__ bool residual_on(const RankPtrs &P) {
 // Only needed when fewer residual blocks than tiles are reserved: mark the
 // tiles that some pair touches.
 __global__ void __launch_bounds__(256) residual_mark_kernel(RankPtrs P, int32_t eps) {
+  pdl_enter();
   if (!residual_on(P)) return;
   for_each_residual_pair(P, eps, [&](int32_t t, int32_t, int32_t, uint32_t) {
     if (P.block_of[t] != 1) P.block_of[t] = 1;
@@ -1248,6 +1269,7 @@ __global__ void __launch_bounds__(256) residual_mark_kernel(RankPtrs P, int32_t 
 // block_of[t] := index of tile t's residual block, -1 if none. With a block for
 // every tile (identity) nothing needs marking.
 __global__ void __launch_bounds__(1024) residual_scan_kernel(RankPtrs P, int identity) {
+  pdl_enter();
   __shared__ int32_t s_warp[32];
   __shared__ int32_t s_carry;
   const int32_t nt = P.hdr->n_tiles;
@@ -1271,6 +1293,7 @@ __global__ void __launch_bounds__(1024) residual_scan_kernel(RankPtrs P, int ide
 }
 
 __global__ void residual_zero_kernel(RankPtrs P) {
+  pdl_enter();
   if (P.hdr->status != 0) return;
   const int64_t words4 = (int64_t)P.hdr->n_blocks * (int64_t)(kResidualBlockBytes / 16);
   uint4 *p = reinterpret_cast<uint4 *>(P.rblocks);
@@ -1280,6 +1303,7 @@ __global__ void residual_zero_kernel(RankPtrs P) {
 }
 
 __global__ void __launch_bounds__(256) residual_add_kernel(RankPtrs P, int32_t eps) {
+  pdl_enter();
   if (!residual_on(P)) return;
   for_each_residual_pair(P, eps, [&](int32_t t, int32_t row, int32_t col, uint32_t val) {
     const int64_t blk = P.block_of[t];
@@ -1292,6 +1316,7 @@ __global__ void __launch_bounds__(256) residual_add_kernel(RankPtrs P, int32_t e
 // key = acc0 + acc1 2^32 (128-bit); rank = (hi + lo 2^-64) / N of the set.
 __global__ void finalize_kernel(RankPtrs P, uint64_t *__restrict__ key_hi,
                                 uint64_t *__restrict__ key_lo, double *__restrict__ rank) {
+  pdl_enter();
   if (P.hdr->status != 0) return;
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < P.n_total;
        x += (int64_t)gridDim.x * blockDim.x) {
@@ -1329,28 +1354,28 @@ int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *le
   const int64_t we = P.n_sets * (int64_t)eps;
   const int64_t nblk = (we + kScanChunk - 1) / kScanChunk;
   auto list_scan = [&]() -> int {
-    list_scan_reduce_kernel<<<(unsigned)nblk, 256, 0, st>>>(P, we);
+    pdl_launch(list_scan_reduce_kernel, (unsigned)nblk, 256, 0, st, P, we);
     SAD_LAUNCH_CHECK();
-    list_scan_top_kernel<<<1, 1024, 0, st>>>(P, nblk);
+    pdl_launch(list_scan_top_kernel, 1, 1024, 0, st, P, nblk);
     SAD_LAUNCH_CHECK();
-    list_scan_down_kernel<<<(unsigned)nblk, 256, 0, st>>>(P, we, plan_only);
+    pdl_launch(list_scan_down_kernel, (unsigned)nblk, 256, 0, st, P, we, plan_only);
     SAD_LAUNCH_CHECK();
     return SAD_OK;
   };
-  rank_setup_kernel<<<1, 1024, 0, st>>>(d_n, (int32_t)n, P);
+  pdl_launch(rank_setup_kernel, 1, 1024, 0, st, d_n, (int32_t)n, P);
   SAD_LAUNCH_CHECK();
   if (P.n_sets > 1) {
-    rank_setmaps_kernel<<<gsets, 256, 0, st>>>(P);
+    pdl_launch(rank_setmaps_kernel, gsets, 256, 0, st, P);
     SAD_LAUNCH_CHECK();
   }
-  rank_init_kernel<<<grid_for(we + kMaxM, 256), 256, 0, st>>>(P, eps, !plan_only);
+  pdl_launch(rank_init_kernel, grid_for(we + kMaxM, 256), 256, 0, st, P, eps, !plan_only);
   SAD_LAUNCH_CHECK();
   if (!plan_only) {
-    lengths_kernel<<<grid_for(n, 256), 256, 0, st>>>(lengths, k, P);
+    pdl_launch(lengths_kernel, grid_for(n, 256), 256, 0, st, lengths, k, P);
     SAD_LAUNCH_CHECK();
   }
   if (word_max && !plan_only) {
-    copy_word_max_kernel<<<grid_for(eps, 256), 256, 0, st>>>(word_max, eps, P);
+    pdl_launch(copy_word_max_kernel, grid_for(eps, 256), 256, 0, st, word_max, eps, P);
     SAD_LAUNCH_CHECK();
   } else {
     dim3 g((eps + 255) / 256, 1);
@@ -1359,16 +1384,16 @@ int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *le
     if (slices < 1) slices = 1;
     g.y = (unsigned)slices;
     // the plan counts the excess entries here; a run counts them in the plane kernel
-    colmax_kernel<<<g, 256, 0, st>>>(counts, eps, P, plan_only);
+    pdl_launch(colmax_kernel, g, 256, 0, st, counts, eps, P, plan_only);
     SAD_LAUNCH_CHECK();
   }
-  colmap_kernel<<<1, 1024, 0, st>>>(P, eps, plan_only);
+  pdl_launch(colmap_kernel, 1, 1024, 0, st, P, eps, plan_only);
   SAD_LAUNCH_CHECK();
   if (plan_only) return list_scan();
   if (P.n_sets == 1) {
-    lensort_scan_kernel<<<1, 1024, 0, st>>>(P);
+    pdl_launch(lensort_scan_kernel, 1, 1024, 0, st, P);
     SAD_LAUNCH_CHECK();
-    lensort_place_kernel<<<grid_for(P.n_pad, 256), 256, 0, st>>>(lengths, k, P);
+    pdl_launch(lensort_place_kernel, grid_for(P.n_pad, 256), 256, 0, st, lengths, k, P);
     SAD_LAUNCH_CHECK();
   } else {
     if (!g_attr_sort) {
@@ -1377,7 +1402,7 @@ int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *le
         return SAD_ERR_CUDA;
       g_attr_sort = true;
     }
-    lensort_sets_kernel<<<gsets, kSortThreads, kSortSmem, st>>>(lengths, k, P);
+    pdl_launch(lensort_sets_kernel, gsets, kSortThreads, kSortSmem, st, lengths, k, P);
     SAD_LAUNCH_CHECK();
   }
   if (P.depth_cap >= 1 && P.depth_cap <= kTabDepth && (eps & 3) == 0 &&
@@ -1389,7 +1414,8 @@ int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *le
       return SAD_ERR_CUDA;
     const int64_t cap = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
     const int64_t want = (warps + 7) / 8;
-    planes_stream_kernel<<<(unsigned)(want < cap ? want : cap), 256, 0, st>>>(counts, eps, P);
+    pdl_launch(planes_stream_kernel, (unsigned)(want < cap ? want : cap), 256, 0, st, counts, eps,
+               P);
     SAD_LAUNCH_CHECK();
   } else {
     const size_t smem = sizeof(uint16_t) * (size_t)eps * kPlaneRows;
@@ -1403,11 +1429,12 @@ int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *le
       return SAD_ERR_CUDA;
     const int64_t groups = P.n_pad / kPlaneRows;
     const int64_t cap = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
-    planes_kernel<<<(unsigned)(groups < cap ? groups : cap), 256, smem, st>>>(counts, eps, P);
+    pdl_launch(planes_kernel, (unsigned)(groups < cap ? groups : cap), 256, smem, st, counts, eps,
+               P);
     SAD_LAUNCH_CHECK();
   }
   if (P.depth_cap >= 1 && P.list_cap > 0) {
-    promote_weight_kernel<<<grid_for(eps, 256), 256, 0, st>>>(P, eps);
+    pdl_launch(promote_weight_kernel, grid_for(eps, 256), 256, 0, st, P, eps);
     SAD_LAUNCH_CHECK();
     const int staged = eps <= 16384 ? 1 : 0;
     const size_t smem = staged ? sizeof(int64_t) * (size_t)eps : 0;
@@ -1415,22 +1442,22 @@ int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *le
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem) != cudaSuccess)
       return SAD_ERR_CUDA;
-    promote_select_kernel<<<1, 1024, smem, st>>>(P, eps, staged);
+    pdl_launch(promote_select_kernel, 1, 1024, smem, st, P, eps, staged);
     SAD_LAUNCH_CHECK();
-    promote_apply_kernel<<<grid_for(P.list_cap, 256), 256, 0, st>>>(P, eps);
+    pdl_launch(promote_apply_kernel, grid_for(P.list_cap, 256), 256, 0, st, P, eps);
     SAD_LAUNCH_CHECK();
   }
   int rc = list_scan();
   if (rc) return rc;
   if (P.depth_cap >= 1 && P.list_cap > 0) {
-    group_lists_kernel<<<grid_for(P.list_cap, 256), 256, 0, st>>>(P, eps);
+    pdl_launch(group_lists_kernel, grid_for(P.list_cap, 256), 256, 0, st, P, eps);
     SAD_LAUNCH_CHECK();
   }
   {
     // one set: a CTA per column group; batches: a few per set
     const int64_t groups1 = ((n + kColBlock - 1) / kColBlock + kGroupCols - 1) / kGroupCols;
     dim3 g((unsigned)(P.n_sets == 1 ? (groups1 > 0 ? groups1 : 1) : 4), gsets);
-    tiles_kernel<<<g, 256, 0, st>>>(P);
+    pdl_launch(tiles_kernel, g, 256, 0, st, P);
   }
   SAD_LAUNCH_CHECK();
   if (P.depth_cap >= 1 && P.block_cap > 0) {
@@ -1438,14 +1465,14 @@ int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *le
     const int identity = P.block_cap >= P.tiles_total ? 1 : 0;
     const unsigned gw = (unsigned)(we < num_sms() * 8 ? we : num_sms() * 8);
     if (!identity) {
-      residual_mark_kernel<<<gw, 256, 0, st>>>(P, eps);
+      pdl_launch(residual_mark_kernel, gw, 256, 0, st, P, eps);
       SAD_LAUNCH_CHECK();
     }
-    residual_scan_kernel<<<1, 1024, 0, st>>>(P, identity);
+    pdl_launch(residual_scan_kernel, 1, 1024, 0, st, P, identity);
     SAD_LAUNCH_CHECK();
-    residual_zero_kernel<<<(unsigned)num_sms() * 8, 256, 0, st>>>(P);
+    pdl_launch(residual_zero_kernel, (unsigned)num_sms() * 8, 256, 0, st, P);
     SAD_LAUNCH_CHECK();
-    residual_add_kernel<<<gw, 256, 0, st>>>(P, eps);
+    pdl_launch(residual_add_kernel, gw, 256, 0, st, P, eps);
     SAD_LAUNCH_CHECK();
   }
   return SAD_OK;
@@ -1453,7 +1480,7 @@ int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *le
 
 int rank_finalize_launch(const RankPtrs &P, uint64_t *key_hi, uint64_t *key_lo, double *rank,
                          cudaStream_t st) {
-  finalize_kernel<<<grid_for(P.n_total, 256), 256, 0, st>>>(P, key_hi, key_lo, rank);
+  pdl_launch(finalize_kernel, grid_for(P.n_total, 256), 256, 0, st, P, key_hi, key_lo, rank);
   SAD_LAUNCH_CHECK();
   return SAD_OK;
 }

@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "../../include/sad.h"
 
 namespace sad {
@@ -245,6 +247,32 @@ void prof_end(cudaStream_t st);
       return SAD_ERR_CUDA;                                   \
     }                                                        \
   } while (0)
+
+// Kernels are launched with programmatic stream serialization: a kernel's CTAs may
+// be scheduled while the previous kernel on the stream is finishing, and every
+// kernel's first statement, pdl_enter(), waits until that kernel has completed and
+// its memory is visible (griddepcontrol.wait) before touching memory, then lets
+// the next kernel be scheduled once all of this kernel's CTAs have started.
+template <typename... KArgs, typename... Args>
+inline void pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t st, Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  (void)cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);  // error: SAD_LAUNCH_CHECK
+}
+
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 
 // ------------------------------------------------------------- PTX: misc ----
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {

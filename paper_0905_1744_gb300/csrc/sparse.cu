@@ -38,6 +38,7 @@ SparseLayout sparse_layout(int64_t n, int64_t entries_cap) {
 __global__ void sparse_nnz_kernel(const int32_t *__restrict__ counts, const int32_t *lengths,
                                   int32_t n, int32_t eps, int32_t k, int32_t *nnz, uint4 *rec,
                                   WsHeader *hdr) {
+  pdl_enter();
   const int lane = threadIdx.x & 31;
   for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n;
        x += ((int64_t)gridDim.x * blockDim.x) >> 5) {
@@ -61,6 +62,7 @@ __global__ void sparse_nnz_kernel(const int32_t *__restrict__ counts, const int3
 __global__ void __launch_bounds__(1024) sparse_scan_kernel(const int32_t *nnz, int32_t n,
                                                            int64_t *off, int64_t cap,
                                                            WsHeader *hdr) {
+  pdl_enter();
   __shared__ int64_t s_warp[32];
   __shared__ int64_t s_carry;
   if (threadIdx.x == 0) s_carry = 0;
@@ -99,6 +101,7 @@ __global__ void __launch_bounds__(1024) sparse_scan_kernel(const int32_t *nnz, i
 // Warp per sequence: the list in ascending word order (ballot compaction).
 __global__ void sparse_fill_kernel(const int32_t *__restrict__ counts, int32_t n, int32_t eps,
                                    const int64_t *off, uint32_t *entries, WsHeader *hdr) {
+  pdl_enter();
   if (hdr->status != 0) return;
   const int lane = threadIdx.x & 31;
   for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n;
@@ -145,6 +148,7 @@ __global__ void __launch_bounds__(kSparseWarps * 32)
                        const int64_t *__restrict__ off, const uint32_t *__restrict__ entries,
                        const uint4 *__restrict__ rec, uint64_t *key_hi, uint64_t *key_lo,
                        double *rank, WsHeader *hdr) {
+  pdl_enter();
   extern __shared__ uint16_t s_hist[];  // [eps]
   __shared__ uint64_t s_hi[kSparseWarps], s_lo[kSparseWarps];
   if (hdr->status != 0) return;
@@ -211,9 +215,8 @@ int sparse_count_launch(const int32_t *counts, const int32_t *lengths, int32_t n
   uint8_t *b = static_cast<uint8_t *>(ws);
   WsHeader *hdr = reinterpret_cast<WsHeader *>(b);
   if (cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st) != cudaSuccess) return SAD_ERR_CUDA;
-  sparse_nnz_kernel<<<grid_of((int64_t)n * 32, 256), 256, 0, st>>>(
-      counts, lengths, n, eps, k, reinterpret_cast<int32_t *>(b + L.nnz),
-      reinterpret_cast<uint4 *>(b + L.rec), hdr);
+  pdl_launch(sparse_nnz_kernel, grid_of((int64_t)n * 32, 256), 256, 0, st, counts, lengths, n, eps,
+             k, reinterpret_cast<int32_t *>(b + L.nnz), reinterpret_cast<uint4 *>(b + L.rec), hdr);
   SAD_LAUNCH_CHECK();
   return SAD_OK;
 }
@@ -232,11 +235,11 @@ int sparse_rank_launch(const int32_t *counts, const int32_t *lengths, int32_t n,
   int64_t *off = reinterpret_cast<int64_t *>(b + L.off);
   uint32_t *entries = reinterpret_cast<uint32_t *>(b + L.entries);
   const uint4 *rec = reinterpret_cast<const uint4 *>(b + L.rec);
-  sparse_scan_kernel<<<1, 1024, 0, st>>>(reinterpret_cast<const int32_t *>(b + L.nnz), n, off,
-                                         entries_cap, hdr);
+  pdl_launch(sparse_scan_kernel, 1, 1024, 0, st, reinterpret_cast<const int32_t *>(b + L.nnz), n,
+             off, entries_cap, hdr);
   SAD_LAUNCH_CHECK();
-  sparse_fill_kernel<<<grid_of((int64_t)n * 32, 256), 256, 0, st>>>(counts, n, eps, off, entries,
-                                                                    hdr);
+  pdl_launch(sparse_fill_kernel, grid_of((int64_t)n * 32, 256), 256, 0, st, counts, n, eps, off,
+             entries, hdr);
   SAD_LAUNCH_CHECK();
   static bool attr = false;
   if (!attr) {
@@ -246,8 +249,8 @@ int sparse_rank_launch(const int32_t *counts, const int32_t *lengths, int32_t n,
     attr = true;
   }
   const int64_t grid = n < (int64_t)num_sms() * 4 ? n : (int64_t)num_sms() * 4;
-  sparse_rank_kernel<<<(unsigned)(grid > 0 ? grid : 1), kSparseWarps * 32, smem, st>>>(
-      counts, n, eps, off, entries, rec, key_hi, key_lo, rank, hdr);
+  pdl_launch(sparse_rank_kernel, (unsigned)(grid > 0 ? grid : 1), kSparseWarps * 32, smem, st,
+             counts, n, eps, off, entries, rec, key_hi, key_lo, rank, hdr);
   SAD_LAUNCH_CHECK();
   return SAD_OK;
 }
