@@ -135,6 +135,33 @@ __global__ void __launch_bounds__(kSortThreads) samples_kernel(const Item *items
     Item *Y = Y_all + S.samp_base, *Y2 = Y2_all + S.samp_base, *piv = piv_all + S.piv_base;
     const Item *it = items + S.seq_begin;
     const int64_t ns = p * (p - 1);
+    if (ns <= (int64_t)blockDim.x) {
+      // few samples: each thread ranks one against all of them in shared memory
+      // (a sample taken twice, w_b < p, is ordered by its sample number) and the
+      // samples at the pivot ranks are the pivots
+      for (int64_t e = threadIdx.x; e < ns; e += blockDim.x) {
+        const int64_t b = e / (p - 1), j = e % (p - 1) + 1;
+        const int64_t lo = block_lo(b, n, p), w = block_lo(b + 1, n, p) - lo;
+        sm[e] = it[lo + j * w / p];
+      }
+      __syncthreads();
+      const int64_t e = threadIdx.x;
+      if (e < ns) {
+        const Item y = sm[e];
+        int64_t r = 0;
+        for (int64_t f = 0; f < ns; ++f) {
+          const Item z = sm[f];
+          r += (item_less(z, y) || (f < e && !item_less(y, z))) ? 1 : 0;
+        }
+        const int64_t off = r - (p / 2 - 1);  // rank (i)p + floor(p/2) - 1, 0-based
+        if (off >= 0 && off % p == 0 && off / p < p - 1) {
+          piv[off / p] = y;
+          if (pivot_idx) pivot_idx[S.piv_base + off / p] = y.idx;
+        }
+      }
+      __syncthreads();
+      continue;
+    }
     for (int64_t e = threadIdx.x; e < ns; e += blockDim.x) {
       const int64_t b = e / (p - 1), j = e % (p - 1) + 1;
       const int64_t lo = block_lo(b, n, p), w = block_lo(b + 1, n, p) - lo;

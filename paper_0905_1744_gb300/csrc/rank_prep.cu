@@ -330,7 +330,9 @@ __global__ void __launch_bounds__(1024) colmap_kernel(RankPtrs P, int32_t eps, i
   for (int tau = tid; tau < eps; tau += blockDim.x) {
     const int32_t t = min(P.T[tau], kMaxM);
     local_max = max(local_max, t);
-    atomicAdd(&P.thist[t], 1);
+    // most words share a few values of T: one atomic per value per warp
+    const unsigned same = __match_any_sync(__activemask(), t);
+    if ((tid & 31) == __ffs(same) - 1) atomicAdd(&P.thist[t], __popc(same));
   }
   atomicMax(&s_tmax, local_max);
   __syncthreads();
@@ -382,6 +384,12 @@ __global__ void __launch_bounds__(1024) colmap_kernel(RankPtrs P, int32_t eps, i
   // compaction of the previous section, so the work is linear in K_eff). Columns
   // next to each other then look up nearby words when the planes are written.
   for (int t = 1; t <= dkeep; ++t) {
+    if (t == 1 && P.secend[1] == eps) {
+      // every word occurs somewhere: section 1 is the identity
+      for (int c = tid; c < eps; c += blockDim.x) P.colmap[c] = c | (1 << 16);
+      __syncthreads();
+      continue;
+    }
     const int32_t src_lo = t == 1 ? 0 : P.secend[t - 2];
     const int32_t src_n = t == 1 ? eps : P.secend[t - 1] - P.secend[t - 2];
     const int32_t dst_lo = P.secend[t - 1];
@@ -1274,6 +1282,15 @@ __global__ void __launch_bounds__(1024) residual_scan_kernel(RankPtrs P, int ide
   __shared__ int32_t s_carry;
   const int32_t nt = P.hdr->n_tiles;
   const bool on = residual_on(P);
+  if (identity) {
+    // a block per tile: no scan
+    for (int32_t t = threadIdx.x; t < nt; t += blockDim.x) P.block_of[t] = on ? t : -1;
+    if (threadIdx.x == 0) {
+      P.hdr->n_blocks = on ? nt : 0;
+      if (on && nt > P.block_cap) record_error(P.hdr, SAD_ERR_WORKSPACE, nt);
+    }
+    return;
+  }
   if (threadIdx.x == 0) s_carry = 0;
   __syncthreads();
   for (int32_t base = 0; base < nt; base += blockDim.x) {

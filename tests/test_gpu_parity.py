@@ -184,7 +184,11 @@ def test_rank_rejects_inconsistent_lengths(sad):
                                           # the bounds of the chunk-merge route (p <= 64,
                                           # blocks of at most 64 x 256 items)
                                           (6500, 65, None), (6400, 64, 3), (16384, 1, None),
-                                          (16385, 1, None), (40000, 2, 7), (300, 64, None)])
+                                          (16385, 1, None), (40000, 2, 7), (300, 64, None),
+                                          # pivots by ranking p (p - 1) <= 1024 samples,
+                                          # blocks shorter than p (samples taken twice)
+                                          (40, 16, None), (20, 8, 2), (33, 32, None),
+                                          (992, 32, 4), (3, 2, None)])
 def test_partition_matches_oracle(sad, oracle_mod, n, p, distinct):
     hi, lo = datagen.random_keys(n, seed=n * 7 + p, distinct=distinct)
     offs, mem, piv = sad.partition(dev(hi), dev(lo), p)
