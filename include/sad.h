@@ -34,7 +34,7 @@
 extern "C" {
 #endif
 
-#define SAD_ABI_VERSION 3
+#define SAD_ABI_VERSION 4
 
 typedef enum sad_status {
   SAD_OK = 0,
@@ -138,6 +138,25 @@ typedef struct sad_rank_plan {
  */
 int kmer_rank_plan(const int32_t *d_counts, int32_t n_seq, int32_t k, int32_t alphabet,
                    sad_rank_plan *plan, void *d_ws, size_t ws_bytes, void *stream);
+
+/*
+ * kmer_rank_plan_bound - host only (no device access, no synchronisation): fills
+ * `plan` (plan->depth >= 1 is the input) with capacities that hold for ANY counts
+ * of n_seq sequences of total length total_len residues, so kmer_rank can run
+ * right after kmer_count without the synchronous kmer_rank_plan. The bounds (the
+ * threshold identity min(a, b) = sum_t [a >= t][b >= t], Sec. 3 Eq. 1):
+ *   k_cap      = eps * depth rounded up to 256 (K_eff = sum_tau min(T_tau, depth)),
+ *   list_cap   = (total_len - n_seq (k - 1)) / (depth + 1) (a sequence of m
+ *                windows has at most m / (depth + 1) words counted more than
+ *                depth times),
+ *   block_cap  = every tile of the upper triangle (a residual block per tile).
+ * t_max, k_eff, list_entries and residual_pairs are set to -1 (not known).
+ * Returns SAD_ERR_INVALID_ARGUMENT for depth < 1 (all planes need the word
+ * maxima) or negative sizes, SAD_ERR_UNSUPPORTED for unsupported k / alphabet
+ * or more than 65535 row blocks.
+ */
+int kmer_rank_plan_bound(int32_t n_seq, int64_t total_len, int32_t k, int32_t alphabet,
+                         sad_rank_plan *plan);
 
 /*
  * kmer_rank - the k-mer rank of every sequence against the whole set.

@@ -278,6 +278,32 @@ int kmer_rank_plan(const int32_t *d_counts, int32_t n_seq, int32_t k, int32_t al
                         static_cast<cudaStream_t>(stream));
 }
 
+int kmer_rank_plan_bound(int32_t n_seq, int64_t total_len, int32_t k, int32_t alphabet,
+                         sad_rank_plan *plan) {
+  const int64_t eps = eps_of(k, alphabet);
+  if (eps < 0) return SAD_ERR_UNSUPPORTED;
+  if (n_seq < 0 || total_len < 0 || !plan || plan->depth < 1) return SAD_ERR_INVALID_ARGUMENT;
+  const RankShape sh = shape_single(n_seq);
+  if (sh.rows_total / kRowBlock > 0xFFFF) return SAD_ERR_UNSUPPORTED;
+  const int64_t d = plan->depth;
+  // K_eff = sum over words of min(T, d) <= eps d; a sequence has at most m / (d + 1)
+  // words counted more than d times, and sum m = total_len - n (k - 1)
+  int64_t k_cap = (int64_t)align_up((size_t)(eps * d), kKCols);
+  if (k_cap < kKCols) k_cap = kKCols;
+  const int64_t windows = total_len - (int64_t)n_seq * (k - 1);
+  plan->t_max = -1;
+  plan->k_eff = -1;
+  plan->list_entries = -1;
+  plan->residual_pairs = -1;
+  plan->k_cap = k_cap;
+  plan->list_cap = windows > 0 ? windows / (d + 1) : 0;
+  plan->block_cap = sh.tiles_total;  // a block per tile: the identity block map
+  plan->ws_bytes =
+      rank_layout(sh, eps, RankCaps{plan->depth, plan->k_cap, plan->list_cap, plan->block_cap})
+          .bytes;
+  return SAD_OK;
+}
+
 int kmer_rank(const int32_t *d_counts, const int32_t *d_lengths, const int32_t *d_word_max,
               int32_t n_seq, int32_t k, int32_t alphabet, const sad_rank_plan *plan,
               uint64_t *d_key_hi, uint64_t *d_key_lo, double *d_rank, void *d_ws,

@@ -76,6 +76,8 @@ def _load():
         lib.kmer_count.restype = ctypes.c_int
         lib.kmer_rank_plan.argtypes = [P, i32, i32, i32, ctypes.POINTER(RankPlan), P, sz, P]
         lib.kmer_rank_plan.restype = ctypes.c_int
+        lib.kmer_rank_plan_bound.argtypes = [i32, i64, i32, i32, ctypes.POINTER(RankPlan)]
+        lib.kmer_rank_plan_bound.restype = ctypes.c_int
         lib.kmer_rank.argtypes = [P, P, P, i32, i32, i32, ctypes.POINTER(RankPlan), P, P, P, P,
                                   sz, P]
         lib.kmer_rank.restype = ctypes.c_int
@@ -218,6 +220,18 @@ def kmer_rank_plan(counts: torch.Tensor, k: int = 3, alphabet: int = 20, depth: 
     return plan
 
 
+def kmer_rank_plan_bound(n: int, total_len: int, k: int = 3, alphabet: int = 20,
+                         depth: int = 1) -> RankPlan:
+    """Capacities for kmer_rank at plane depth ``depth`` >= 1 that hold for any
+    counts of ``n`` sequences of ``total_len`` residues in all: no device work and
+    no synchronisation (K_cap = eps depth, excess entries <= windows / (depth + 1),
+    a residual block per tile)."""
+    plan = RankPlan(depth=int(depth))
+    _check(_load().kmer_rank_plan_bound(int(n), int(total_len), k, alphabet, ctypes.byref(plan)),
+           "kmer_rank_plan_bound")
+    return plan
+
+
 def kmer_rank(counts: torch.Tensor, lengths: torch.Tensor, k: int = 3, alphabet: int = 20,
               ws: Workspace | None = None, with_rank: bool = True, stream=None,
               out=None, check: bool = True, plan: RankPlan | None = None, depth: int = 0,
@@ -273,14 +287,26 @@ def partition(key_hi: torch.Tensor, key_lo: torch.Tensor, p: int, ws: Workspace 
 def partition_set(codes: torch.Tensor, offsets: torch.Tensor, p: int, k: int = 3,
                   alphabet: int = 20, ws: Workspace | None = None, stream=None,
                   depth: int = 0):
-    """count -> rank -> partition of one sequence set on the device."""
+    """count -> rank -> partition of one sequence set on the device. With
+    ``depth`` >= 1 the rank runs on the host-side capacity bounds
+    (kmer_rank_plan_bound), so the three calls queue without a synchronisation;
+    the workspace status (the first error any of them recorded) is read once at
+    the end."""
     ws = ws or Workspace(codes.device)
+    n = offsets.numel() - 1
+    plan = kmer_rank_plan_bound(n, codes.numel(), k, alphabet, depth) if depth >= 1 else None
+    if plan is not None:
+        # one size for the three calls: a later growth would drop an earlier status
+        ws.ensure(max(plan.ws_bytes, workspace_bytes(OP_COUNT, n, k, alphabet),
+                      workspace_bytes(OP_PARTITION, n, p=p)))
     word_max = torch.empty(alphabet ** k, dtype=torch.int32, device=codes.device)
-    counts = kmer_count(codes, offsets, k, alphabet, ws=ws, stream=stream, word_max=word_max)
+    counts = kmer_count(codes, offsets, k, alphabet, ws=ws, stream=stream, word_max=word_max,
+                        check=plan is None)
     lengths = (offsets[1:] - offsets[:-1]).to(torch.int32)
     hi, lo, rank = kmer_rank(counts, lengths, k, alphabet, ws=ws, stream=stream, depth=depth,
-                             word_max=word_max)
-    offs, mem, piv = partition(hi, lo, p, ws=ws, stream=stream)
+                             word_max=word_max, plan=plan, check=plan is None)
+    offs, mem, piv = partition(hi, lo, p, ws=ws, stream=stream, check=False)
+    ws.check("partition_set", stream)
     return dict(counts=counts, key_hi=hi, key_lo=lo, rank=rank, bucket_offsets=offs,
                 members=mem, pivot_idx=piv)
 

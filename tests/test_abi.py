@@ -26,7 +26,8 @@ def lib():
 
 def test_header_declares_the_three_calls():
     names = declared_functions()
-    for f in ("kmer_count", "kmer_rank", "partition", "kmer_rank_plan", "sad_workspace_bytes",
+    for f in ("kmer_count", "kmer_rank", "partition", "kmer_rank_plan", "kmer_rank_plan_bound",
+              "sad_workspace_bytes",
               "sad_status_read", "sad_status_string", "sad_abi_version", "sad_launch_count"):
         assert f in names
 
@@ -38,7 +39,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_host_only_queries(lib):
     lib.sad_abi_version.restype = ctypes.c_int
-    assert lib.sad_abi_version() == 3
+    assert lib.sad_abi_version() == 4
     lib.sad_status_string.restype = ctypes.c_char_p
     lib.sad_status_string.argtypes = [ctypes.c_int]
     assert lib.sad_status_string(0) == b"ok"
@@ -67,3 +68,55 @@ def test_argument_errors_need_no_gpu(lib):
                               P, P, ctypes.c_size_t, P]
     assert lib.kmer_rank(None, None, None, 10, 9, 20, None, None, None, None, None, 0, None) == 5
     assert lib.kmer_rank(None, None, None, -1, 3, 20, None, None, None, None, None, 0, None) == 1
+
+
+class _Plan(ctypes.Structure):
+    _fields_ = [("depth", ctypes.c_int32), ("t_max", ctypes.c_int32),
+                ("k_eff", ctypes.c_int64), ("list_entries", ctypes.c_int64),
+                ("residual_pairs", ctypes.c_int64), ("k_cap", ctypes.c_int64),
+                ("list_cap", ctypes.c_int64), ("block_cap", ctypes.c_int64),
+                ("ws_bytes", ctypes.c_size_t)]
+
+
+def _bound(lib, n, total_len, depth, k=3, alphabet=20):
+    f = lib.kmer_rank_plan_bound
+    f.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                  ctypes.POINTER(_Plan)]
+    f.restype = ctypes.c_int
+    plan = _Plan(depth=depth)
+    return f(n, total_len, k, alphabet, ctypes.byref(plan)), plan
+
+
+def test_rank_plan_bound_is_host_only(lib):
+    rc, plan = _bound(lib, 20000, 6_000_000, 1)
+    assert rc == 0
+    assert plan.k_cap == 8192                            # eps * 1 rounded up to 256
+    assert plan.list_cap == (6_000_000 - 2 * 20000) // 2
+    assert plan.block_cap == 157 * 158 // 2              # every upper-triangle tile
+    assert plan.ws_bytes > 20096 * 8192 // 2 + 32768 * plan.block_cap
+    assert plan.k_eff == -1 and plan.t_max == -1
+    assert _bound(lib, 20000, 6_000_000, 2)[1].k_cap == 16128       # 16000 rounded up
+    assert _bound(lib, 10, 100, 0)[0] == 1               # all planes need the word maxima
+    assert _bound(lib, -1, 100, 1)[0] == 1
+    assert _bound(lib, 10, 100, 1, k=9)[0] == 5
+
+
+@pytest.mark.parametrize("depth", [1, 2, 3])
+def test_rank_plan_bound_holds_for_the_data(lib, oracle_mod, depth):
+    """The capacities bound what the data need: K_eff = sum_tau min(T_tau, D) and
+    the excess entries #{(x, tau): c_x(tau) > D} (counted here from the oracle's
+    counts), on sets with long repeats and on a family set."""
+    import numpy as np
+    from paper_0905_1744_gb300 import datagen
+    sets = [datagen.from_strings(["A" * 3000, "AC" * 900, "ACD" * 400, "W" * 5, "ACDEFGHIK"]),
+            datagen.random_small(300, 3, 2500, seed=11, alphabet=4),
+            datagen.family_set(6, 40, lambda r: int(r.integers(40, 900)), p=4, seed=3,
+                               stream=9)]
+    for s in sets:
+        alphabet = int(s.codes.max()) + 1 if s.codes.size else 20
+        alphabet = 4 if alphabet <= 4 else 20
+        c = oracle_mod.kmer_count(s.codes, s.offsets, 3, alphabet)
+        rc, plan = _bound(lib, s.n, int(s.codes.size), depth, 3, alphabet)
+        assert rc == 0
+        assert np.minimum(c.max(axis=0), depth).sum() <= plan.k_cap
+        assert int((c > depth).sum()) <= plan.list_cap

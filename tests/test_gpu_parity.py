@@ -214,6 +214,38 @@ def test_config1_end_to_end(sad, oracle_mod):
         np.testing.assert_array_equal(host(res[key]), ref[key], err_msg=key)
 
 
+@pytest.mark.parametrize("depth", [1, 2])
+def test_config1_end_to_end_on_bound_plan(sad, oracle_mod, depth):
+    """partition_set with depth >= 1 queues count -> rank -> partition on the
+    host-side capacity bounds, without a synchronisation in between."""
+    s = datagen.config1()
+    res = sad.partition_set(dev(s.codes), dev(s.offsets), s.p, depth=depth)
+    ref = oracle_mod.run_set(s.codes, s.offsets, s.p)
+    for key in ("counts", "key_hi", "key_lo", "rank", "bucket_offsets", "members", "pivot_idx"):
+        np.testing.assert_array_equal(host(res[key]), ref[key], err_msg=key)
+
+
+@pytest.mark.parametrize("depth", [1, 2, 5])
+def test_rank_on_bound_plan(sad, oracle_mod, depth):
+    """kmer_rank_plan_bound's capacities hold for long repeats (a large residual)
+    and for a family set; the keys are the oracle's."""
+    sets = [datagen.from_strings(["A" * 3000, "A" * 2000, "AC" * 900, "ACD" * 400, "W" * 5,
+                                  "ACDEFGHIKLMNPQRSTVWY" * 30]),
+            datagen.family_set(6, 230, lambda r: int(r.integers(40, 900)), p=4, seed=3,
+                               stream=9)]
+    for s in sets:
+        wm = torch.empty(8000, dtype=torch.int32, device="cuda")
+        counts = sad.kmer_count(dev(s.codes), dev(s.offsets), word_max=wm)
+        plan = sad.kmer_rank_plan_bound(s.n, s.codes.size, depth=depth)
+        hi, lo, rank = sad.kmer_rank(counts, dev(s.lengths.astype(np.int32)), plan=plan,
+                                     word_max=wm)
+        c = oracle_mod.kmer_count(s.codes, s.offsets)
+        ohi, olo, orank, _ = oracle_mod.kmer_rank(c, s.lengths, 3, 20, with_fp64=True)
+        np.testing.assert_array_equal(host(hi), ohi)
+        np.testing.assert_array_equal(host(lo), olo)
+        np.testing.assert_array_equal(host(rank), orank)
+
+
 def csr_invariants(hi, lo, p, offs, mem, piv):
     n = hi.shape[0]
     order = np.lexsort((np.arange(n), lo, hi))
