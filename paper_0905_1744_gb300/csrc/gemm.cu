@@ -23,9 +23,12 @@
 // before the floor, so the key is the same as with all planes.
 //
 // Persistent kernel, one CTA per SM, 12 warps:
-//   warp 0      TMA producer: 128 rows x 128 B (256 plane columns) of A (rows I)
-//               and of B (rows J) per stage, 128-byte swizzle, 6-stage mbarrier ring
-//   warp 1      MMA issuer: 4 x (M=128, N=128, K=64) per stage into one of two
+//   warp 0      TMA producer: per stage two K chunks of 256 plane columns (128 B)
+//               of A (rows I) and of B (rows J), each operand one 3-D TMA request
+//               that lands as two 128-row tiles with the 128-byte swizzle; a
+//               3-stage mbarrier ring (64 KB a stage: the cost of a stage is
+//               mostly fixed, so fewer, larger stages run faster)
+//   warp 1      MMA issuer: 8 x (M=128, N=128, K=64) per stage into one of two
 //               TMEM accumulators (2 x 128 columns), commit frees the stage
 //   warp 2      TMEM allocator
 //   warps 4-7   also fill the scale-factor columns of TMEM with 1.0 before the
@@ -56,9 +59,13 @@ namespace sad {
 
 namespace {
 
-constexpr int kStages = 6;
-constexpr uint32_t kABytes = kRowBlock * kKChunk;
-constexpr uint32_t kBBytes = kColBlock * kKChunk;
+// A stage holds two 256-column K chunks (two 128-byte-swizzled tiles per operand,
+// one 3-D TMA request each).
+constexpr int kStages = 3;
+constexpr int32_t kCps = 2;  // K chunks per stage
+constexpr uint32_t kSubA = kRowBlock * kKChunk, kSubB = kColBlock * kKChunk;
+constexpr uint32_t kABytes = kSubA * kCps;
+constexpr uint32_t kBBytes = kSubB * kCps;
 constexpr uint32_t kTxBytes = kABytes + kBBytes;
 constexpr int kThreads = 384;
 constexpr int kEpiThreads = 256;  // warps 4-11: two per TMEM lane quadrant
@@ -303,7 +310,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       int32_t u, J, nk;
       pair_at(P, pair_R, p, u, J, nk);
       const int32_t I = 2 * u + (int32_t)crank;
-      for (int32_t kc = 0; kc < nk; ++kc) {
+      for (int32_t kc = 0; kc < (nk + kCps - 1) / kCps; ++kc) {
         if (!mbar_wait_bounded_cluster(&S.empty[stage], phase ^ 1u, abort_flag, kWaitBudgetNs)) {
           set_abort(S, P.hdr);
           aborted = true;
@@ -311,9 +318,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (leader) mbar_arrive_expect_tx(&S.full[stage], 2 * kPairTxBytes);
         const uint32_t fb = mapa_shared(&S.full[stage], 0);
-        tma_load_2d_pair(S.a[stage], &tmA, fb, kc * kKChunk, I * kRowBlock);
-        tma_load_2d_pair(S.b[stage], &tmB, fb, kc * kKChunk,
-                         J * kColBlock + (int32_t)crank * (kColBlock / 2));
+        tma_load_3d_pair(S.a[stage], &tmA, fb, 0, I * kRowBlock, kc * kCps);
+        tma_load_3d_pair(S.b[stage], &tmB, fb, 0, J * kColBlock + (int32_t)crank * (kColBlock / 2),
+                         kc * kCps);
         used |= 1u << stage;
         par = (par & ~(1u << stage)) | (phase << stage);
         if (++stage == kStages) {
@@ -343,15 +350,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int32_t t = blockIdx.x; t < n_tiles && !aborted; t += gridDim.x) {
       int32_t I, J, nk;
       tile_at(P, X, rect_nk, t, I, J, nk);
-      for (int32_t kc = 0; kc < nk; ++kc) {
+      for (int32_t kc = 0; kc < (nk + kCps - 1) / kCps; ++kc) {
         if (!mbar_wait_bounded(&S.empty[stage], phase ^ 1u, abort_flag, kWaitBudgetNs)) {
           set_abort(S, P.hdr);
           aborted = true;
           break;
         }
         mbar_arrive_expect_tx(&S.full[stage], kTxBytes);
-        tma_load_2d(S.a[stage], &tmA, &S.full[stage], kc * kKChunk, I * kRowBlock);
-        tma_load_2d(S.b[stage], &tmB, &S.full[stage], kc * kKChunk, J * kColBlock);
+        tma_load_3d(S.a[stage], &tmA, &S.full[stage], 0, I * kRowBlock, kc * kCps);
+        tma_load_3d(S.b[stage], &tmB, &S.full[stage], 0, J * kColBlock, kc * kCps);
         used |= 1u << stage;
         par = (par & ~(1u << stage)) | (phase << stage);
         if (++stage == kStages) {
@@ -385,19 +392,23 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       tc_fence_after();
       const uint32_t d_tmem = tmem + acc * (uint32_t)kColBlock;
-      for (int32_t kc = 0; kc < nk; ++kc) {
+      for (int32_t kc = 0; kc < (nk + kCps - 1) / kCps; ++kc) {
         if (!mbar_wait_bounded_cluster(&S.full[stage], phase, abort_flag, kWaitBudgetNs)) {
           set_abort(S, P.hdr);
           aborted = true;
           break;
         }
         tc_fence_after();
-        const uint64_t adesc = sdesc_kmajor_sw128(smem_u32(S.a[stage]));
-        const uint64_t bdesc = sdesc_kmajor_sw128(smem_u32(S.b[stage]));
+        // each CTA holds 64 rows of B: its K chunks are kSubB / 2 apart
+        const int nsub = min(kCps, nk - kc * kCps);
+        for (int sub = 0; sub < nsub; ++sub) {
+          const uint64_t adesc = sdesc_kmajor_sw128(smem_u32(S.a[stage] + sub * kSubA));
+          const uint64_t bdesc = sdesc_kmajor_sw128(smem_u32(S.b[stage] + sub * (kSubB / 2)));
 #pragma unroll
-        for (int kk = 0; kk < kKChunk / 32; ++kk)
-          mma_f4_pair(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, idesc, sfa, sfb,
-                      (kc | kk) != 0 ? 1u : 0u);
+          for (int kk = 0; kk < kKChunk / 32; ++kk)
+            mma_f4_pair(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, idesc, sfa, sfb,
+                        (kc | sub | kk) != 0 ? 1u : 0u);
+        }
         mma_commit_pair(&S.empty[stage], 0x3);
         if (++stage == kStages) {
           stage = 0;
@@ -430,20 +441,24 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       tc_fence_after();
       const uint32_t d_tmem = tmem + acc * (uint32_t)kColBlock;
-      for (int32_t kc = 0; kc < nk; ++kc) {
+      for (int32_t kc = 0; kc < (nk + kCps - 1) / kCps; ++kc) {
         if (!mbar_wait_bounded(&S.full[stage], phase, abort_flag, kWaitBudgetNs)) {
           set_abort(S, P.hdr);
           aborted = true;
           break;
         }
         tc_fence_after();
-        const uint64_t adesc = sdesc_kmajor_sw128(smem_u32(S.a[stage]));
-        const uint64_t bdesc = sdesc_kmajor_sw128(smem_u32(S.b[stage]));
-        // 4 MMAs of K = 64 values = 32 bytes per row (2 in 16-byte descriptor units)
+        // per K chunk 4 MMAs of K = 64 values = 32 bytes per row (2 in 16-byte
+        // descriptor units); a last chunk past the tile's extent is not used
+        const int nsub = min(kCps, nk - kc * kCps);
+        for (int sub = 0; sub < nsub; ++sub) {
+          const uint64_t adesc = sdesc_kmajor_sw128(smem_u32(S.a[stage] + sub * kSubA));
+          const uint64_t bdesc = sdesc_kmajor_sw128(smem_u32(S.b[stage] + sub * kSubB));
 #pragma unroll
-        for (int kk = 0; kk < kKChunk / 32; ++kk)
-          mma_f4(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, idesc, sfa, sfb,
-                 (kc | kk) != 0 ? 1u : 0u);
+          for (int kk = 0; kk < kKChunk / 32; ++kk)
+            mma_f4(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, idesc, sfa, sfb,
+                   (kc | sub | kk) != 0 ? 1u : 0u);
+        }
         mma_commit(&S.empty[stage]);
         if (++stage == kStages) {
           stage = 0;
@@ -744,11 +759,13 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 int make_plane_map(CUtensorMap *map, uint8_t *planes, int64_t n_pad, int64_t k_cap, int rows) {
   auto fn = encode_fn();
   if (!fn) return SAD_ERR_CUDA;
-  const cuuint64_t dims[2] = {(cuuint64_t)(k_cap / 2), (cuuint64_t)n_pad};
-  const cuuint64_t strides[1] = {(cuuint64_t)(k_cap / 2)};
-  const cuuint32_t box[2] = {(cuuint32_t)kKChunk, (cuuint32_t)rows};
-  const cuuint32_t estr[2] = {1, 1};
-  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, planes, dims, strides, box, estr,
+  // (byte in chunk, row, chunk): a box of kCps chunks lands as kCps row-major tiles
+  const cuuint64_t dims[3] = {(cuuint64_t)kKChunk, (cuuint64_t)n_pad,
+                              (cuuint64_t)(k_cap / 2 / kKChunk)};
+  const cuuint64_t strides[2] = {(cuuint64_t)(k_cap / 2), (cuuint64_t)kKChunk};
+  const cuuint32_t box[3] = {(cuuint32_t)kKChunk, (cuuint32_t)rows, (cuuint32_t)kCps};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, planes, dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? SAD_OK : SAD_ERR_CUDA;
