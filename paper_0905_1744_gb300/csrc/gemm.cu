@@ -660,9 +660,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                           sqh, qsum, cs, cq);
         else
           f_block16<false>(v, rw, &S.colrec[buf][c0], row_pos, 0, sql, sqh, qsum, cs, cq);
-        transpose_reduce16(cs, lane);
-        transpose_reduce16(cq, lane);
-        if (lane < 16) S.colpart[buf][q][c0 + (int)lane] = make_uint2(cs[0], cq[0]);
+        // column sums over the warp's 32 rows: one warp-wide reduction per column
+        uint32_t mcs = 0, mcq = 0;
+#pragma unroll
+        for (int cc = 0; cc < 16; ++cc) {
+          const uint32_t a = __reduce_add_sync(0xffffffffu, cs[cc]);
+          const uint32_t b = __reduce_add_sync(0xffffffffu, cq[cc]);
+          if (lane == (uint32_t)cc) {
+            mcs = a;
+            mcq = b;
+          }
+        }
+        if (lane < 16) S.colpart[buf][q][c0 + (int)lane] = make_uint2(mcs, mcq);
       }
       {
         // the row's sum of terms sql + sqh 2^32 + qsum as Rc 2^64 + Rlo
