@@ -435,7 +435,9 @@ def run_sparse(args, dev, counts, lengths, rank_ms, reps: int = 2):
     return {"kind": "sparse intersection on CUDA cores (every ordered pair)",
             "list_entries": int(entries), "ms_per_rank": ms,
             "pairs_per_s": n * (n - 1) / 2 / (ms / 1e3),
-            "plane_gemm_rank_ms": rank_ms, "plane_gemm_speedup": ms / rank_ms}
+            "plane_gemm_rank_ms": rank_ms,
+            # the rank time comes from the depth trials (absent when --depth is given)
+            "plane_gemm_speedup": ms / rank_ms if rank_ms else None}
 
 
 def run_table1(args, dev, seed: int = 0):

@@ -12,11 +12,12 @@
 //   decreasing length), key_i += term_ij for i <= j and key_j += term_ij for i < j.
 //
 // The row sums of a tile stay in registers, the column sums are reduced across
-// the 32 lanes of a warp with a transposing shuffle tree; the square mode then
-// meets the two column halves' row sums and the four lane quadrants' column sums
-// in shared memory, so a tile adds one 128-bit sum per row and per column, split
-// as T mod 2^32 and T >> 32 into two 64-bit accumulators per sequence
-// (red.global.add.u64), which a last kernel folds into the 128-bit key.
+// the 32 lanes of a warp (redux.sync, one per column); the square modes then meet
+// the two column halves' row sums and the four lane quadrants' column sums in
+// shared memory, so a tile adds one sum per row and per column: 128-bit, split as
+// T mod 2^32 and T >> 32 into two 64-bit accumulators per sequence (similarity),
+// or one signed 64-bit value (distance form), by red.global.add.u64; a last
+// kernel folds them into the key.
 //
 // When the planes are cut at a depth D, the residual sum_tau max(0, min(c_i, c_j) - D)
 // of each pair arrives as a dense 128 x 128 u16 block per tile and is added to S
@@ -122,22 +123,6 @@ __device__ __forceinline__ void named_bar_sync(int id, int count) {
 // acc += v as a 64-bit sum with its carries counted in c.
 __device__ __forceinline__ void add_carry(uint64_t &acc, uint32_t &c, uint64_t v) {
   asm("add.cc.u64 %0, %0, %2;\n\taddc.u32 %1, %1, 0;" : "+l"(acc), "+r"(c) : "l"(v));
-}
-
-// Column sums of a 32 x 16 block held one row per lane (v[i] = column i): after
-// the call v[0] of lane L is the sum over all 32 lanes of column L & 15.
-__device__ __forceinline__ void transpose_reduce16(uint32_t (&v)[16], uint32_t lane) {
-#pragma unroll
-  for (int w = 8; w >= 1; w >>= 1) {
-    const bool upper = (lane & (uint32_t)w) != 0;
-#pragma unroll
-    for (int i = 0; i < w; ++i) {
-      const uint32_t send = upper ? v[i] : v[i + w];
-      const uint32_t keep = upper ? v[i + w] : v[i];
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, w);
-    }
-  }
-  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 16);
 }
 
 __device__ __forceinline__ void tmem_ld_32x32b_x16(uint32_t taddr, uint32_t (&v)[16]) {
@@ -600,14 +585,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             cl[cc] = (uint32_t)(cv & 0xFFFFFF);
             ch[cc] = (uint32_t)(int32_t)(cv >> 24);
           }
-          transpose_reduce16(cl, lane);
-          transpose_reduce16(ch, lane);
-          if (lane < 16) {
-            const int32_t jorig = S.colorig[buf][c0 + (int)lane];
-            const int64_t tot = (int64_t)(int32_t)ch[0] * (int64_t)(1 << 24) + (int64_t)cl[0];
-            if (jorig >= 0 && tot != 0)
-              red_add_u64(P.acc + 3 * (int64_t)jorig, (unsigned long long)tot);
+          // column sums over the warp's 32 rows (low parts below 2^29, signed high
+          // parts), one warp-wide reduction per column, met in shared memory
+          uint32_t mcl = 0, mch = 0;
+#pragma unroll
+          for (int cc = 0; cc < 16; ++cc) {
+            const uint32_t a = __reduce_add_sync(0xffffffffu, cl[cc]);
+            const uint32_t b = (uint32_t)__reduce_add_sync(0xffffffffu, (int32_t)ch[cc]);
+            if (lane == (uint32_t)cc) {
+              mcl = a;
+              mch = b;
+            }
           }
+          if (lane < 16) S.colpart[buf][q][c0 + (int)lane] = make_uint2(mcl, mch);
         }
       } else if (rect) {
         // every pair counts for the row only; D = min(m_i, m_r): the record of the
@@ -693,7 +683,31 @@ __global__ void __launch_bounds__(kThreads, 1)
       } else {
         mbar_arrive(&S.tempty[acc]);
       }
-      if (!kDist && !rect) {
+      if (kDist && !rect) {
+        // square distance form: as below, with one signed 64-bit sum per row and column
+        if (tile_ok && half == 1)
+          S.rowpart[buf][q * 32 + lane] =
+              make_uint4((uint32_t)(uint64_t)Rd, (uint32_t)((uint64_t)Rd >> 32), 0u, 0u);
+        named_bar_sync(2, kEpiThreads);
+        if (tile_ok && half == 0) {
+          if (row_orig >= 0) {
+            const uint4 o = S.rowpart[buf][q * 32 + lane];
+            const int64_t tot = Rd + (int64_t)(((uint64_t)o.y << 32) | o.x);
+            red_add_u64(P.acc + 3 * (int64_t)row_orig, (unsigned long long)tot);
+          }
+        } else if (tile_ok) {
+          const int c = (int)etid - kRowBlock;  // half 1: one column each
+          const int32_t jorig = S.colorig[buf][c];
+          int64_t tot = 0;
+#pragma unroll
+          for (int qq = 0; qq < 4; ++qq) {
+            const uint2 v2 = S.colpart[buf][qq][c];
+            tot += (int64_t)(int32_t)v2.y * (int64_t)(1 << 24) + (int64_t)v2.x;
+          }
+          if (jorig >= 0 && tot != 0)
+            red_add_u64(P.acc + 3 * (int64_t)jorig, (unsigned long long)tot);
+        }
+      } else if (!kDist && !rect) {
         // square similarity: the row sums of the two column halves and the column
         // sums of the four lane quadrants meet in shared memory; then half 0 adds
         // one row each and half 1 one column each to the keys
