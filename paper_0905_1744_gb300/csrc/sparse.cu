@@ -249,8 +249,11 @@ int sparse_rank_launch(const int32_t *counts, const int32_t *lengths, int32_t n,
     attr = true;
   }
   const int64_t grid = n < (int64_t)num_sms() * 4 ? n : (int64_t)num_sms() * 4;
-  pdl_launch(sparse_rank_kernel, (unsigned)(grid > 0 ? grid : 1), kSparseWarps * 32, smem, st,
-             counts, n, eps, off, entries, rec, key_hi, key_lo, rank, hdr);
+  // plain stream order: launched early, its CTAs (4 a SM, rows in a static stride)
+  // would be placed unevenly while the previous kernel still holds SMs (measured 2x
+  // slower); its pdl_enter() is then a no-op
+  sparse_rank_kernel<<<(unsigned)(grid > 0 ? grid : 1), kSparseWarps * 32, smem, st>>>(
+      counts, n, eps, off, entries, rec, key_hi, key_lo, rank, hdr);
   SAD_LAUNCH_CHECK();
   return SAD_OK;
 }
