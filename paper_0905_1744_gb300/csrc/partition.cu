@@ -145,14 +145,22 @@ __global__ void __launch_bounds__(kSortThreads) samples_kernel(const Item *items
         sm[e] = it[lo + j * w / p];
       }
       __syncthreads();
-      const int64_t e = threadIdx.x;
+      // a group of g threads (a power of two, within a warp) ranks one sample
+      int g = 1;
+      while (g < 32 && (int64_t)(2 * g) * ns <= (int64_t)blockDim.x) g *= 2;
+      const int64_t e = threadIdx.x / g;
+      const int u = (int)(threadIdx.x % g);
+      int32_t r = 0;
+      Item y{};
       if (e < ns) {
-        const Item y = sm[e];
-        int64_t r = 0;
-        for (int64_t f = 0; f < ns; ++f) {
+        y = sm[e];
+        for (int64_t f = u; f < ns; f += g) {
           const Item z = sm[f];
           r += (item_less(z, y) || (f < e && !item_less(y, z))) ? 1 : 0;
         }
+      }
+      for (int o = 1; o < g; o <<= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+      if (e < ns && u == 0) {
         const int64_t off = r - (p / 2 - 1);  // rank (i)p + floor(p/2) - 1, 0-based
         if (off >= 0 && off % p == 0 && off / p < p - 1) {
           piv[off / p] = y;
