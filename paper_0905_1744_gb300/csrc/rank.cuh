@@ -69,14 +69,7 @@ struct RankPtrs {
   int2 *flat;            // [list_cap] (stored row, word | (count - depth) << 16), unordered
   int32_t *tile_of;      // [tileof_total] tile index of set-local block (I, J)
   int32_t *block_of;     // [tiles_total] residual block of a tile, -1 = none
-  // one set, a residual block per tile: excess entries grouped by (row block, word)
-  int32_t *wb_cnt;       // [blocks][eps] entries of each (block, word); scatter cursor
-  int32_t *wb_off;       // [blocks][eps] start of each word's run within its block
-  uint32_t *wb_bits;     // [blocks][eps / 32] words with an entry in the block
-  int64_t *wb_base;      // [blocks + 1] start of each block's entries
-  uint32_t *wb_list;     // [list_cap] row within the block << 16 | excess
-  int32_t wb;            // the tables above are in use
-  uint32_t *rblocks;     // [block_cap][128][128] u16 residual per pair (two per word)
+  uint32_t *rblocks;     // [block_cap][128][256] u16 residual per pair (two per word)
   Item *sortbuf;         // [2 n_total] per-set length sort (n_sets > 1 only)
   int64_t *scanblk;      // [2 x blocks] block totals of the excess-list scan
   int64_t n_pad;         // rows_total: stored rows over all sets

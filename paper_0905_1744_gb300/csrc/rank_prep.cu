@@ -74,12 +74,6 @@ RankPtrs rank_ptrs(void *ws, const RankLayout &L) {
   P.block_of = reinterpret_cast<int32_t *>(b + L.block_of);
   P.rblocks = reinterpret_cast<uint32_t *>(b + L.rblocks);
   P.sortbuf = reinterpret_cast<Item *>(b + L.sortbuf);
-  P.wb_cnt = reinterpret_cast<int32_t *>(b + L.wb_cnt);
-  P.wb_off = reinterpret_cast<int32_t *>(b + L.wb_off);
-  P.wb_bits = reinterpret_cast<uint32_t *>(b + L.wb_bits);
-  P.wb_base = reinterpret_cast<int64_t *>(b + L.wb_base);
-  P.wb_list = reinterpret_cast<uint32_t *>(b + L.wb_list);
-  P.wb = L.wb ? 1 : 0;
   P.scanblk = reinterpret_cast<int64_t *>(b + L.scanblk);
   P.n_pad = L.shape.rows_total;
   P.n_total = L.shape.n_total;
@@ -213,7 +207,6 @@ __global__ void rank_init_kernel(RankPtrs P, int32_t eps, int with_keys) {
   if (with_keys) {
     zero_range(P.depth, P.n_pad / kRowBlock, tid, nt);
     zero_range(P.acc, 3 * P.n_total, tid, nt);
-    if (P.wb) zero_range(P.wb_cnt, (P.n_pad / kRowBlock) * (int64_t)eps, tid, nt);
   }
   if (tid == 0) {
     P.hdr->k_eff = 0;
@@ -1337,180 +1330,6 @@ __global__ void __launch_bounds__(256) residual_add_kernel(RankPtrs P, int32_t e
   });
 }
 
-// ---- residual blocks per tile (one set, a block per tile) --------------------
-// The residual of pair (i, j), sum over words of min(e_i, e_j) with e the excess
-// of a count over the plane depth (after promotion), needs for a tile (I, J) the
-// excess entries of row blocks I and J of every word that occurs in both. The
-// flat entries are grouped by (row block, word): counts, per-block scans (which
-// also give a bitmap of the block's words), a scan of the block totals, and a
-// scatter that counts the same cells down again. Each tile's block is then summed
-// in shared memory and written out whole, which also clears it.
-
-__global__ void wb_count_kernel(RankPtrs P, int32_t eps) {
-  pdl_enter();
-  if (!residual_on(P)) return;
-  if (blockIdx.x == 0 && threadIdx.x == 0 && (int64_t)P.hdr->flat_count > P.list_cap)
-    record_error(P.hdr, SAD_ERR_WORKSPACE, (int)min((int64_t)P.hdr->flat_count, (int64_t)INT32_MAX));
-  const int64_t total = min((int64_t)P.hdr->flat_count, P.list_cap);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int2 e = P.flat[i];
-    if (e.x < 0) continue;
-    atomicAdd(&P.wb_cnt[(int64_t)(e.x / kRowBlock) * eps + (e.y & 0xFFFF)], 1);
-  }
-}
-
-// One block per row block b: local offsets of its word runs, the bitmap of its
-// words, and its total (into wb_base[b], scanned next).
-__global__ void __launch_bounds__(1024) wb_scan_kernel(RankPtrs P, int32_t eps) {
-  pdl_enter();
-  __shared__ int32_t s_warp[32];
-  __shared__ int32_t s_carry;
-  if (!residual_on(P)) return;
-  const int64_t b = blockIdx.x;
-  const int32_t nbw = (eps + 31) / 32;
-  if (threadIdx.x == 0) s_carry = 0;
-  __syncthreads();
-  for (int base = 0; base < eps; base += blockDim.x) {
-    const int tau = base + threadIdx.x;
-    const int32_t c = tau < eps ? P.wb_cnt[b * eps + tau] : 0;
-    int32_t tot;
-    const int32_t incl = block_scan_incl<int32_t>(c, s_warp, &tot);
-    if (tau < eps) P.wb_off[b * eps + tau] = s_carry + incl - c;
-    const unsigned m = __ballot_sync(0xffffffffu, c > 0);
-    if ((threadIdx.x & 31) == 0 && (tau >> 5) < nbw) P.wb_bits[b * nbw + (tau >> 5)] = m;
-    __syncthreads();
-    if (threadIdx.x == 0) s_carry += tot;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) P.wb_base[b] = s_carry;
-}
-
-// wb_base := exclusive prefix of the block totals, wb_base[blocks] = all entries.
-__global__ void __launch_bounds__(1024) wb_base_kernel(RankPtrs P) {
-  pdl_enter();
-  __shared__ int64_t s_warp[32];
-  __shared__ int64_t s_carry;
-  if (!residual_on(P)) return;
-  const int64_t nrb = P.n_pad / kRowBlock;
-  if (threadIdx.x == 0) s_carry = 0;
-  __syncthreads();
-  for (int64_t base = 0; base < nrb; base += blockDim.x) {
-    const int64_t b = base + threadIdx.x;
-    const int64_t c = b < nrb ? P.wb_base[b] : 0;
-    int64_t tot;
-    const int64_t incl = block_scan_incl<int64_t>(c, s_warp, &tot);
-    __syncthreads();  // every block total is read before any is overwritten
-    if (b < nrb) P.wb_base[b] = s_carry + incl - c;
-    __syncthreads();
-    if (threadIdx.x == 0) s_carry += tot;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) P.wb_base[nrb] = s_carry;
-}
-
-__global__ void wb_scatter_kernel(RankPtrs P, int32_t eps) {
-  pdl_enter();
-  if (!residual_on(P)) return;
-  const int64_t total = min((int64_t)P.hdr->flat_count, P.list_cap);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int2 e = P.flat[i];
-    if (e.x < 0) continue;
-    const int64_t b = e.x / kRowBlock, cell = b * eps + (e.y & 0xFFFF);
-    const int64_t pos = P.wb_base[b] + P.wb_off[cell] + (atomicSub(&P.wb_cnt[cell], 1) - 1);
-    const uint32_t ex = (uint32_t)e.y >> 16;  // 1 .. 65535
-    P.wb_list[pos] = ((uint32_t)(e.x % kRowBlock) << 16) | ex;
-  }
-}
-
-constexpr int kWbThreads = 256;
-constexpr int kWbHeavy = 64;    // pairs of a word above which the whole block shares it
-constexpr int kWbQueue = 256;
-
-// Adds the pairs of word tau's entries in rows [i0, i1) of block I and [j0, j1) of
-// block J, pair q = t, t + stride, ...; returns the unordered pairs counted (i <= j
-// on the diagonal tile).
-__device__ __forceinline__ uint32_t wb_word_pairs(const uint32_t *li, const uint32_t *lj,
-                                                  int32_t ni, int32_t nj, bool diag,
-                                                  uint32_t *sblk, int32_t t, int32_t stride) {
-  uint32_t np = 0;
-  const int32_t total = ni * nj;
-  for (int32_t q = t; q < total; q += stride) {
-    const int32_t a = q / nj, c = q - a * nj;
-    const uint32_t ea = li[a], ec = lj[c];
-    const uint32_t ra = ea >> 16, rc = ec >> 16;
-    const uint32_t x = min(ea & 0xFFFFu, ec & 0xFFFFu);
-    atomicAdd(&sblk[ra * (kColBlock / 2) + (rc >> 1)], x << (16 * (rc & 1)));
-    np += (!diag || ra <= rc) ? 1u : 0u;
-  }
-  return np;
-}
-
-// One tile at a time per block: the tile's 128 x 128 u16 residual summed in shared
-// memory and written to its block (block t of tile t).
-__global__ void __launch_bounds__(kWbThreads) wb_tiles_kernel(RankPtrs P, int32_t eps) {
-  pdl_enter();
-  extern __shared__ uint32_t s_wb[];  // block, then the bitmap of J's words
-  __shared__ int32_t s_heavy[kWbQueue];
-  __shared__ int32_t s_nheavy;
-  uint32_t *sblk = s_wb;
-  uint32_t *sbits = s_wb + kRowBlock * (kColBlock / 2);
-  if (!residual_on(P)) return;
-  const int32_t nt = P.hdr->n_tiles;
-  const int32_t nbw = (eps + 31) / 32;
-  uint32_t npairs = 0;
-  for (int32_t t = blockIdx.x; t < nt; t += gridDim.x) {
-    const int2 tl = P.tiles[t];
-    const int32_t I = tl.x & 0xFFFF, J = tl.x >> 16;
-    __syncthreads();  // the previous tile's block is written out
-    for (int i = threadIdx.x; i < kRowBlock * (kColBlock / 2); i += blockDim.x) sblk[i] = 0;
-    for (int i = threadIdx.x; i < nbw; i += blockDim.x) sbits[i] = P.wb_bits[(int64_t)J * nbw + i];
-    if (threadIdx.x == 0) s_nheavy = 0;
-    __syncthreads();
-    const int64_t bi = P.wb_base[I], bj = P.wb_base[J];
-    const int32_t endi = (int32_t)(P.wb_base[I + 1] - bi), endj = (int32_t)(P.wb_base[J + 1] - bj);
-    const int32_t *offi = P.wb_off + (int64_t)I * eps, *offj = P.wb_off + (int64_t)J * eps;
-    const bool diag = I == J;
-    for (int w = threadIdx.x; w < nbw; w += blockDim.x) {
-      uint32_t m = P.wb_bits[(int64_t)I * nbw + w] & sbits[w];
-      while (m) {
-        const int32_t tau = w * 32 + __ffs(m) - 1;
-        m &= m - 1;
-        const int32_t i0 = offi[tau], i1 = tau + 1 < eps ? offi[tau + 1] : endi;
-        const int32_t j0 = offj[tau], j1 = tau + 1 < eps ? offj[tau + 1] : endj;
-        if ((i1 - i0) * (j1 - j0) > kWbHeavy) {
-          const int32_t slot = atomicAdd(&s_nheavy, 1);
-          if (slot < kWbQueue) {
-            s_heavy[slot] = tau;
-            continue;
-          }
-        }
-        npairs += wb_word_pairs(P.wb_list + bi + i0, P.wb_list + bj + j0, i1 - i0, j1 - j0,
-                                diag, sblk, 0, 1);
-      }
-    }
-    __syncthreads();
-    // words with many pairs: the whole block on each
-    const int32_t nh = min(s_nheavy, kWbQueue);
-    for (int32_t h = 0; h < nh; ++h) {
-      const int32_t tau = s_heavy[h];
-      const int32_t i0 = offi[tau], i1 = tau + 1 < eps ? offi[tau + 1] : endi;
-      const int32_t j0 = offj[tau], j1 = tau + 1 < eps ? offj[tau + 1] : endj;
-      npairs += wb_word_pairs(P.wb_list + bi + i0, P.wb_list + bj + j0, i1 - i0, j1 - j0, diag,
-                              sblk, (int32_t)threadIdx.x, (int32_t)blockDim.x);
-    }
-    __syncthreads();
-    uint4 *dst = reinterpret_cast<uint4 *>(P.rblocks + (int64_t)t * (kResidualBlockBytes / 4));
-    const uint4 *src = reinterpret_cast<const uint4 *>(sblk);
-    for (int i = threadIdx.x; i < (int)(kResidualBlockBytes / 16); i += blockDim.x) dst[i] = src[i];
-  }
-  for (int o = 16; o > 0; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
-  if ((threadIdx.x & 31) == 0 && npairs)
-    atomicAdd(reinterpret_cast<unsigned long long *>(&P.hdr->pairs_total),
-              (unsigned long long)npairs);
-}
-
 // key = acc0 + acc1 2^32 (128-bit); rank = (hi + lo 2^-64) / N of the set.
 __global__ void finalize_kernel(RankPtrs P, uint64_t *__restrict__ key_hi,
                                 uint64_t *__restrict__ key_lo, double *__restrict__ rank) {
@@ -1645,13 +1464,11 @@ int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *le
     pdl_launch(promote_apply_kernel, grid_for(P.list_cap, 256), 256, 0, st, P, eps);
     SAD_LAUNCH_CHECK();
   }
-  if (!P.wb) {
-    int rc = list_scan();
-    if (rc) return rc;
-    if (P.depth_cap >= 1 && P.list_cap > 0) {
-      pdl_launch(group_lists_kernel, grid_for(P.list_cap, 256), 256, 0, st, P, eps);
-      SAD_LAUNCH_CHECK();
-    }
+  int rc = list_scan();
+  if (rc) return rc;
+  if (P.depth_cap >= 1 && P.list_cap > 0) {
+    pdl_launch(group_lists_kernel, grid_for(P.list_cap, 256), 256, 0, st, P, eps);
+    SAD_LAUNCH_CHECK();
   }
   {
     // one set: a CTA per column group; batches: a few per set
@@ -1670,37 +1487,10 @@ int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *le
     }
     pdl_launch(residual_scan_kernel, 1, 1024, 0, st, P, identity);
     SAD_LAUNCH_CHECK();
-    if (P.wb) {
-      // one set, a block per tile: group the excess entries by (row block, word),
-      // then build each tile's block in shared memory
-      const unsigned ge = grid_for(P.list_cap, 256);
-      const int64_t nrb = P.n_pad / kRowBlock;
-      pdl_launch(wb_count_kernel, ge, 256, 0, st, P, eps);
-      SAD_LAUNCH_CHECK();
-      pdl_launch(wb_scan_kernel, (unsigned)nrb, 1024, 0, st, P, eps);
-      SAD_LAUNCH_CHECK();
-      pdl_launch(wb_base_kernel, 1, 1024, 0, st, P);
-      SAD_LAUNCH_CHECK();
-      pdl_launch(wb_scatter_kernel, ge, 256, 0, st, P, eps);
-      SAD_LAUNCH_CHECK();
-      const size_t smem = kResidualBlockBytes + sizeof(uint32_t) * (size_t)((eps + 31) / 32);
-      if (cudaFuncSetAttribute(wb_tiles_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem) != cudaSuccess)
-        return SAD_ERR_CUDA;
-      int per_sm = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wb_tiles_kernel, kWbThreads,
-                                                        smem) != cudaSuccess)
-        return SAD_ERR_CUDA;
-      const int64_t cap = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
-      const int64_t gt = P.tiles_total < cap ? P.tiles_total : cap;
-      pdl_launch(wb_tiles_kernel, (unsigned)(gt > 0 ? gt : 1), kWbThreads, smem, st, P, eps);
-      SAD_LAUNCH_CHECK();
-    } else {
-      pdl_launch(residual_zero_kernel, (unsigned)num_sms() * 8, 256, 0, st, P);
-      SAD_LAUNCH_CHECK();
-      pdl_launch(residual_add_kernel, gw, 256, 0, st, P, eps);
-      SAD_LAUNCH_CHECK();
-    }
+    pdl_launch(residual_zero_kernel, (unsigned)num_sms() * 8, 256, 0, st, P);
+    SAD_LAUNCH_CHECK();
+    pdl_launch(residual_add_kernel, gw, 256, 0, st, P, eps);
+    SAD_LAUNCH_CHECK();
   }
   return SAD_OK;
 }

@@ -82,7 +82,6 @@ struct RankCaps {
 };
 
 constexpr size_t kResidualBlockBytes = 2 * kRowBlock * kColBlock;  // u16 per pair of a tile
-constexpr int64_t kWbMaxBlocks = 2048;  // row blocks for the per-(block, word) residual tables
 
 // One set of a (possibly batched) rank call, built on the device by rank_setup.
 // Sets are consecutive in the input order; each set's stored rows are a
@@ -133,8 +132,7 @@ struct RankLayout {
   size_t sets, seq_set, row_set, T, secend, thist, coltab, promcol, weight, mhist, perm, rec,
       recw, depth, tiles,
       acc, cnt_gt, list_off, item_off, cursor, tile_of, block_of, sortbuf, scanblk, colmap, lists,
-      flat, wb_cnt, wb_off, wb_bits, wb_base, wb_list, planes, rblocks;
-  bool wb;               // residual blocks built per tile from per-(row block, word) lists
+      flat, planes, rblocks;
   size_t fixed_bytes;    // everything that does not depend on the capacities
   size_t bytes;          // total
   RankShape shape;
@@ -177,17 +175,6 @@ inline RankLayout rank_layout(const RankShape &sh, int64_t eps, const RankCaps &
   L.colmap = take(sizeof(int32_t) * (size_t)(caps.k_cap > 0 ? caps.k_cap : 1));
   L.lists = take(2 * sizeof(int32_t) * (size_t)(caps.list_cap > 0 ? caps.list_cap : 1));
   L.flat = take(2 * sizeof(int32_t) * (size_t)(caps.list_cap > 0 ? caps.list_cap : 1));
-  // one set with a residual block per tile: the excess entries grouped by (row
-  // block, word), and each tile's block built in shared memory
-  const int64_t nrb = sh.rows_total / kRowBlock;
-  L.wb = sh.n_sets == 1 && caps.depth >= 1 && caps.list_cap > 0 && caps.block_cap > 0 &&
-         caps.block_cap >= sh.tiles_total && nrb >= 1 && nrb <= kWbMaxBlocks;
-  const size_t cells = L.wb ? (size_t)nrb * (size_t)eps : 0;
-  L.wb_cnt = take(sizeof(int32_t) * cells);
-  L.wb_off = take(sizeof(int32_t) * cells);
-  L.wb_bits = take(L.wb ? sizeof(uint32_t) * (size_t)nrb * (size_t)((eps + 31) / 32) : 0);
-  L.wb_base = take(L.wb ? sizeof(int64_t) * (size_t)(nrb + 1) : 0);
-  L.wb_list = take(L.wb ? sizeof(uint32_t) * (size_t)caps.list_cap : 0);
   o = align_up(o, 1024);
   L.planes = o;  // rows_total x K_cap 4-bit values
   o = align_up(o + (size_t)sh.rows_total * (size_t)caps.k_cap / 2, 1024);
