@@ -69,7 +69,7 @@ struct RankPtrs {
   int2 *flat;            // [list_cap] (stored row, word | (count - depth) << 16), unordered
   int32_t *tile_of;      // [tileof_total] tile index of set-local block (I, J)
   int32_t *block_of;     // [tiles_total] residual block of a tile, -1 = none
-  uint32_t *rblocks;     // [block_cap][128][256] u16 residual per pair (two per word)
+  uint32_t *rblocks;     // [block_cap][128][128] u16 residual per pair (two per word)
   Item *sortbuf;         // [2 n_total] per-set length sort (n_sets > 1 only)
   int64_t *scanblk;      // [2 x blocks] block totals of the excess-list scan
   int64_t n_pad;         // rows_total: stored rows over all sets
