@@ -120,3 +120,35 @@ def test_rank_plan_bound_holds_for_the_data(lib, oracle_mod, depth):
         assert rc == 0
         assert np.minimum(c.max(axis=0), depth).sum() <= plan.k_cap
         assert int((c > depth).sum()) <= plan.list_cap
+
+
+def test_every_kernel_waits_for_its_predecessor_first():
+    """Kernels are launched with programmatic stream serialization: each must wait
+    (pdl_enter, griddepcontrol.wait) before it touches memory, so its first
+    statement is pdl_enter()."""
+    src_dir = os.path.join(ROOT, "paper_0905_1744_gb300", "csrc")
+    found = 0
+    for name in sorted(os.listdir(src_dir)):
+        if not name.endswith(".cu"):
+            continue
+        text = open(os.path.join(src_dir, name)).read()
+        for m in re.finditer(r"__global__", text):
+            # the kernel's parameter list, then its body
+            i = text.index("(", text.index("(", m.end()) + 1) if "__launch_bounds__" in \
+                text[m.end():text.index("(", m.end()) + 1] else text.index("(", m.end())
+            depth, j = 0, i
+            while True:
+                if text[j] == "(":
+                    depth += 1
+                elif text[j] == ")":
+                    depth -= 1
+                    if depth == 0:
+                        break
+                j += 1
+            k = text.index("{", j)
+            if ";" in text[j:k]:
+                continue  # a declaration
+            body = text[k + 1:k + 400].lstrip()
+            assert body.startswith("pdl_enter();"), (name, text[m.start():k][:120])
+            found += 1
+    assert found >= 40
