@@ -94,6 +94,36 @@ __global__ void __launch_bounds__(1024) part_setup_kernel(const int32_t *d_n, co
   }
 }
 
+// One set with its size on the host: the set table (every base 0), the block
+// offsets floor(b n / p) and the items, in one launch.
+__global__ void part_init_single_kernel(const uint64_t *__restrict__ hi,
+                                        const uint64_t *__restrict__ lo, int64_t n, int64_t p,
+                                        PartSet *sets, int64_t *segoff, Item *items) {
+  pdl_enter();
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nt = (int64_t)gridDim.x * blockDim.x;
+  if (tid == 0) {
+    PartSet e;
+    e.seq_begin = 0;
+    e.n = (int32_t)n;
+    e.p = (int32_t)p;
+    e.blk_base = 0;
+    e.piv_base = 0;
+    e.samp_base = 0;
+    e.pos_base = 0;
+    sets[0] = e;
+  }
+  for (int64_t b = tid; b <= p; b += nt) segoff[b] = block_lo(b, n, p);
+  for (int64_t x = tid; x < n; x += nt) {
+    Item it;
+    it.hi = hi[x];
+    it.lo = lo[x];
+    it.idx = (int32_t)x;
+    it.pad = 0;
+    items[x] = it;
+  }
+}
+
 __global__ void part_init_kernel(const uint64_t *__restrict__ hi, const uint64_t *__restrict__ lo,
                                  int64_t n, const PartSet *sets, int32_t n_sets, Item *items) {
   pdl_enter();
@@ -423,11 +453,18 @@ int partition_sets_launch(const uint64_t *key_hi, const uint64_t *key_lo, int32_
   const int64_t n = tot.n;
   const unsigned gsets = (unsigned)(n_sets < 65535 ? n_sets : 65535);
   const unsigned gseg = (unsigned)(tot.p < 65535 * 4 ? tot.p : 65535 * 4);
-  pdl_launch(part_setup_kernel, 1, 1024, 0, st, d_n, d_p, n_sets, n_single, p_single, sets, segoff);
-  SAD_LAUNCH_CHECK();
-  pdl_launch(part_init_kernel, grid_for(n, 256), 256, 0, st, key_hi, key_lo, n, sets, n_sets,
-             items);
-  SAD_LAUNCH_CHECK();
+  if (n_sets == 1 && !d_n && !d_p) {
+    pdl_launch(part_init_single_kernel, grid_for(n, 256), 256, 0, st, key_hi, key_lo, n,
+               (int64_t)p_single, sets, segoff, items);
+    SAD_LAUNCH_CHECK();
+  } else {
+    pdl_launch(part_setup_kernel, 1, 1024, 0, st, d_n, d_p, n_sets, n_single, p_single, sets,
+               segoff);
+    SAD_LAUNCH_CHECK();
+    pdl_launch(part_init_kernel, grid_for(n, 256), 256, 0, st, key_hi, key_lo, n, sets, n_sets,
+               items);
+    SAD_LAUNCH_CHECK();
+  }
   // one set of small blocks and few buckets: chunk sorts and rank merges
   const int64_t w_max = d_n || p_single < 1 ? 0 : ((int64_t)n_single + p_single - 1) / p_single;
   if (!d_n && n_single > 0 && p_single <= kFastP && w_max <= (int64_t)kFastChunks * kChunk) {
