@@ -59,7 +59,7 @@ struct RankPtrs {
   uint2 *recw;           // [rows_total] floor_weight of each stored row's m
   int2 *tiles;           // [tiles_total] (I | J << 16, K chunks), global block indices
   unsigned long long *acc;  // [n_total][3] key = acc0 + acc1 2^32 (distance mode: acc0)
-  uint8_t *planes;       // [rows_total][K_cap] fp8 threshold planes (sections 1..depth)
+  uint8_t *planes;       // [rows_total][K_cap / 2] packed e2m1 threshold planes (sections 1..depth)
   // residual of the counts above the plane depth, per (set, word)
   int32_t *cnt_gt;       // [n_sets * eps] sequences whose count of the word exceeds depth
   int64_t *list_off;     // [n_sets * eps + 1] start of each excess list

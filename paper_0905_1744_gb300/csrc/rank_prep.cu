@@ -14,11 +14,11 @@
 // and the second term is nonzero only for words both sequences hold more than
 // D times. Each such (set, word) gets a list of (stored row, count - D); every
 // pair in a list adds min of the two excesses to that pair's residual, which is
-// summed into a dense 128 x 256 u16 block of its GEMM tile and added to the
+// summed into a dense 128 x 128 u16 block of its GEMM tile and added to the
 // tile's accumulator in the epilogue, before the floor.
 //
 // Sets. A call ranks one or more independent sets (a batch). Each set's rows are
-// stored contiguously (256-aligned) and its tiles only pair rows of that set, so
+// stored contiguously (128-aligned) and its tiles only pair rows of that set, so
 // the GEMM is block-diagonal; the column layout is shared (T over all sets).
 // Within a set, rows are stored in order of decreasing length (the order of
 // equal lengths is free: it changes no result), so that for every stored pair

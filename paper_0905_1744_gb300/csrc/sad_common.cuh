@@ -21,8 +21,8 @@ constexpr int kMaxP = 4096;             // buckets
 constexpr int kRowBlock = 128;          // GEMM tile rows (A operand, M)
 constexpr int kColBlock = 128;          // GEMM tile columns (B operand, N)
 constexpr int kColRatio = kColBlock / kRowBlock;  // row blocks per column block
-constexpr int kKChunk = 128;            // K bytes per pipeline stage (one 128B swizzle row)
-constexpr int kKCols = 2 * kKChunk;     // plane columns per stage: two 4-bit values a byte
+constexpr int kKChunk = 128;            // K bytes of a chunk (one 128B swizzle row)
+constexpr int kKCols = 2 * kKChunk;     // plane columns per K chunk: two 4-bit values a byte
 constexpr int kNPad = 128;              // rows are padded to a multiple of this
 static_assert(kColBlock % kRowBlock == 0 && kNPad % kColBlock == 0, "tile shapes");
 
@@ -46,7 +46,7 @@ struct WsHeader {
   unsigned long long k_chunks;  // sum over tiles of their K chunks (executed MMA work)
   int64_t list_total;    // (sequence, word) entries with a count above depth
   int64_t pairs_total;   // residual pair contributions
-  int32_t n_blocks;      // residual tiles (dense 128 x 256 blocks) in use
+  int32_t n_blocks;      // residual tiles (dense 128 x 128 blocks) in use
   int32_t m_max;         // largest m = L - k + 1 of the set
   unsigned long long flat_count;  // excess entries appended by the plane kernel
   int64_t items_total;   // residual work items (pairs of list chunks)
@@ -85,11 +85,11 @@ constexpr size_t kResidualBlockBytes = 2 * kRowBlock * kColBlock;  // u16 per pa
 
 // One set of a (possibly batched) rank call, built on the device by rank_setup.
 // Sets are consecutive in the input order; each set's stored rows are a
-// contiguous, 256-aligned range of the global plane matrix, so every GEMM tile
+// contiguous, 128-aligned range of the global plane matrix, so every GEMM tile
 // stays inside one set (the batch is block-diagonal).
 struct RankSet {
   int64_t seq_begin;     // first input sequence of the set
-  int64_t row_base;      // first stored row (multiple of 256)
+  int64_t row_base;      // first stored row (multiple of 128)
   int64_t tile_base;     // first entry of the set's tiles in the tile list
   int64_t tileof_base;   // first entry of the set's (I, J) -> tile map
   int32_t n, pad;
