@@ -54,7 +54,26 @@ WORKLOADS = {
 }
 
 
-def parse():
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest of every rank's x (all ranks call it), then a barrier: the
+    timed region of a replica job ends when its slowest replica does."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def job_value(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput of `world` replicas, each processing units_per_rank in
+    the job's time (the slowest replica's)."""
+    return world * units_per_rank / seconds
+
+
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=60)
@@ -79,7 +98,7 @@ def parse():
     ap.add_argument("--serve-burst", type=int, default=400)
     ap.add_argument("--batch-sets", type=int, default=512)
     ap.add_argument("--batch-reps", type=int, default=10)
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def dist_env():
@@ -588,14 +607,9 @@ def run_sad(args):
     ws.check("timed rank")
     ws_part.check("timed partition")
     step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        dist.barrier()
+    total_ms = max_over_ranks(float(sum(step_ms)), world, dev)
     ms_per_step = total_ms / args.steps
-    value = world * pairs / (ms_per_step / 1e3)
+    value = job_value(pairs, world, ms_per_step / 1e3)
 
     # roofline of the plane GEMM (the dominant kernel)
     pk, pk_kind = peaks()
@@ -656,12 +670,8 @@ def run_sad(args):
         t0 = time.perf_counter()
         for _ in range(reps):
             e2e_step()
-        t_e2e = (time.perf_counter() - t0) / reps
-        if world > 1:
-            t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t.item())
-        e2e = {"value": world * pairs / t_e2e, "unit": "pairs/s",
+        t_e2e = max_over_ranks((time.perf_counter() - t0) / reps, world, dev)
+        e2e = {"value": job_value(pairs, world, t_e2e), "unit": "pairs/s",
                "h2d_bytes_per_step": int(s.codes.nbytes + s.offsets.nbytes),
                "d2h_bytes_per_step": int(4 * n + 4 * (p + 1) + 16 * n),
                "ms_per_step": 1e3 * t_e2e}
