@@ -36,10 +36,11 @@ class Request:
 
 
 def request_bytes(s, depth: int, k: int = 3, alphabet: int = 20) -> int:
-    """HBM a request holds while it is in flight (an upper estimate): codes,
-    offsets, counts, the rank workspace (4-bit planes at depth D <= 4 of the 8000
-    word columns, padded rows; 128 x 128 u16 residual blocks), keys, partition
-    buffers."""
+    """HBM a request holds while it is in flight, estimated for admission: codes,
+    offsets, counts, the rank workspace (4-bit planes of min(D, 4) full sections of
+    the word columns, which covers protein sets, where few words repeat more than
+    once in a sequence; padded rows; every 128 x 128 u16 residual block of the
+    upper triangle), keys, partition buffers, 64 MB of slack."""
     n = s.offsets.shape[0] - 1
     eps = alphabet ** k
     rows = (n + 127) // 128 * 128
@@ -49,6 +50,21 @@ def request_bytes(s, depth: int, k: int = 3, alphabet: int = 20) -> int:
     residual = blocks * 2 * 128 * 128 if depth > 0 else 0
     return int(s.codes.nbytes + 8 * (n + 1) + 4 * n * eps + planes + residual + 96 * n
                + (64 << 20))
+
+
+def select_batch(queue, used: int, budget_bytes: int, max_batch: int, depth: int):
+    """The next batch to admit: the longest prefix of the arrival-ordered queue
+    (at most max_batch requests) whose bytes fit beside the ``used`` bytes of the
+    batches in flight. Returns (requests, bytes); empty when the head of the queue
+    does not fit yet (it is never overtaken, so admission stays in arrival order)."""
+    take, nbytes = [], 0
+    for r in queue:
+        rb = request_bytes(r.seqset, depth)
+        if len(take) >= max_batch or used + nbytes + rb > budget_bytes:
+            break
+        take.append(r)
+        nbytes += rb
+    return take, nbytes
 
 
 class _InFlight:
@@ -91,6 +107,14 @@ def serve(requests, depth: int = 2, budget_bytes: int = 150 * GB, slots: int = 3
           max_batch: int = 64, device=None, t0: float | None = None):
     """Continuous batching over ``requests`` (sorted by arrival). Returns them with
     ``done`` and ``result`` filled in. Arrival times are honoured in real time."""
+    if slots < 1 or max_batch < 1:
+        raise ValueError("serve: slots and max_batch must be at least 1")
+    for r in requests:
+        if request_bytes(r.seqset, depth) > budget_bytes:
+            # it could never be admitted, and the loop below would wait for it forever
+            raise ValueError(f"serve: request {r.rid} needs "
+                             f"{request_bytes(r.seqset, depth)} bytes, above the "
+                             f"{budget_bytes}-byte budget")
     device = torch.device(device or "cuda")
     streams = [torch.cuda.Stream(device) for _ in range(slots)]
     free_streams = list(streams)
@@ -112,13 +136,7 @@ def serve(requests, depth: int = 2, budget_bytes: int = 150 * GB, slots: int = 3
                 used -= f.nbytes
         # admissions: everything queued that fits, one batch per free slot
         while queue and free_streams:
-            take, nbytes = [], 0
-            for r in queue:
-                rb = request_bytes(r.seqset, depth)
-                if len(take) >= max_batch or used + nbytes + rb > budget_bytes:
-                    break
-                take.append(r)
-                nbytes += rb
+            take, nbytes = select_batch(queue, used, budget_bytes, max_batch, depth)
             if not take:
                 break
             queue = queue[len(take):]

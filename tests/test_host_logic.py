@@ -1,0 +1,145 @@
+"""Host-side logic that needs no GPU: serving admission and the depth autotuner's
+choice and cache (the device calls they make are replaced by fakes here; the same
+paths run on the GPU in test_gpu_serve.py and test_gpu_configs.py)."""
+import json
+import types
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_0905_1744_gb300 import autotune, datagen, serve  # noqa: E402
+
+
+def _set(n, length=50, seed=0):
+    return datagen.random_small(n, 3, length, seed=seed)
+
+
+# ------------------------------------------------------------------ serving ---
+
+def test_request_bytes_grows_with_set_size_and_depth():
+    small, big = _set(10), _set(300)
+    for d in (1, 2, 4):
+        assert serve.request_bytes(small, d) < serve.request_bytes(big, d)
+    b = [serve.request_bytes(big, d) for d in (1, 2, 3, 4)]
+    assert b == sorted(b) and len(set(b)) == 4
+    # depth 0 keeps every plane: sized as four sections, with no residual blocks
+    assert serve.request_bytes(big, 0) < serve.request_bytes(big, 4)
+    # the counts alone (4 bytes x 8000 words a sequence) are inside the estimate
+    assert serve.request_bytes(big, 1) > 4 * 300 * 8000
+
+
+def test_select_batch_takes_the_fitting_prefix_in_arrival_order():
+    sets = [_set(20 + 10 * i, seed=i) for i in range(5)]
+    reqs = serve.make_requests(sets, np.zeros(5))
+    rb = [serve.request_bytes(s, 1) for s in sets]
+    # everything fits
+    take, nb = serve.select_batch(reqs, 0, sum(rb), 64, 1)
+    assert [r.rid for r in take] == [0, 1, 2, 3, 4] and nb == sum(rb)
+    # max_batch caps the batch
+    take, nb = serve.select_batch(reqs, 0, sum(rb), 2, 1)
+    assert [r.rid for r in take] == [0, 1] and nb == rb[0] + rb[1]
+    # the bytes in flight count against the budget
+    take, _ = serve.select_batch(reqs, sum(rb) - rb[0] - rb[1], sum(rb), 64, 1)
+    assert [r.rid for r in take] == [0, 1]
+    # a later, smaller request never overtakes a head that does not fit
+    take, nb = serve.select_batch(reqs[1:], 0, rb[1] - 1, 64, 1)
+    assert take == [] and nb == 0
+    take, _ = serve.select_batch(reqs, 0, rb[0], 64, 1)
+    assert [r.rid for r in take] == [0]
+
+
+def test_serve_rejects_a_request_above_the_budget_before_any_device_call():
+    reqs = serve.make_requests([_set(50)], [0.0])
+    need = serve.request_bytes(reqs[0].seqset, 2)
+    with pytest.raises(ValueError, match="budget"):
+        serve.serve(reqs, depth=2, budget_bytes=need - 1, device="cpu")
+    with pytest.raises(ValueError):
+        serve.serve(reqs, depth=2, slots=0, device="cpu")
+
+
+def test_latency_stats():
+    reqs = serve.make_requests([_set(5)], [0.0, 0.5, 1.0, 1.5])
+    for r, d in zip(reqs, (0.1, 0.7, 1.3, 2.0)):
+        r.done = d
+    st = serve.latency_stats(reqs)
+    lat = np.array([0.1, 0.2, 0.3, 0.5])
+    assert st["mean_ms"] == pytest.approx(1e3 * lat.mean())
+    assert st["p50_ms"] == pytest.approx(1e3 * np.percentile(lat, 50))
+    assert st["sets_per_s"] == pytest.approx(4 / 2.0)
+    assert serve.latency_stats(reqs, skip=2)["sets_per_s"] == pytest.approx(2 / 1.0)
+
+
+# ---------------------------------------------------------------- autotuner ---
+
+def _fake_plans(monkeypatch, t_max, ws_bytes, residual_pairs=1000):
+    calls = []
+
+    def plan(counts, k=3, alphabet=20, depth=0, ws=None, stream=None):
+        calls.append(depth)
+        return types.SimpleNamespace(depth=depth, t_max=t_max, residual_pairs=residual_pairs,
+                                     ws_bytes=ws_bytes(depth))
+    monkeypatch.setattr(autotune.sad, "kmer_rank_plan", plan)
+    return calls
+
+
+class _FakeWs:
+    def __init__(self):
+        self.ensured = []
+
+    def ensure(self, nbytes):
+        self.ensured.append(nbytes)
+
+
+def test_choose_depth_times_each_distinct_depth_and_keeps_the_fastest(monkeypatch):
+    autotune._cache.clear()
+    _fake_plans(monkeypatch, t_max=4, ws_bytes=lambda d: 100 * (d + 1))
+    ms = {0: 3.0, 1: 1.5, 2: 1.2, 3: 2.0}
+    timed = []
+
+    def time_rank(counts, lengths, plan, ws, *a, **kw):
+        timed.append(plan.depth)
+        return ms[plan.depth]
+    monkeypatch.setattr(autotune, "time_rank", time_rank)
+    ws = _FakeWs()
+    counts = torch.zeros(300, 8000, dtype=torch.int32)
+    best, trials = autotune.choose_depth(counts, None, ws, use_cache=False)
+    # depths at or above t_max keep every plane, the same work as depth 0: not timed
+    assert timed == [0, 1, 2, 3] and trials == ms and best == 2
+    assert ws.ensured == [100, 200, 300, 400]
+    # a workspace limit drops the depths that need more
+    timed.clear()
+    best, trials = autotune.choose_depth(counts, None, ws, use_cache=False, max_ws_bytes=250)
+    assert timed == [0, 1] and best == 1
+
+
+def test_choose_depth_cache_by_size_class(monkeypatch, tmp_path):
+    autotune._cache.clear()
+    _fake_plans(monkeypatch, t_max=3, ws_bytes=lambda d: 1)
+    monkeypatch.setattr(autotune, "time_rank",
+                        lambda counts, lengths, plan, ws, *a, **kw: {0: 2.0, 1: 1.0, 2: 3.0}[plan.depth])
+    counts = torch.zeros(1000, 1, dtype=torch.int32)
+    best, trials = autotune.choose_depth(counts, None, _FakeWs())
+    assert best == 1 and trials
+    # same size class (log2 N, t_max, log2 residual pairs): answered from the cache
+    best2, trials2 = autotune.choose_depth(torch.zeros(1023, 1, dtype=torch.int32), None,
+                                           _FakeWs())
+    assert best2 == 1 and trials2 == {}
+    path = str(tmp_path / "tune.json")
+    autotune.save_cache(path)
+    with open(path) as f:
+        saved = json.load(f)
+    plan1 = types.SimpleNamespace(t_max=3, residual_pairs=1000)
+    assert saved == {autotune.signature(1000, plan1): 1}
+    autotune._cache.clear()
+    autotune.load_cache(path)
+    assert autotune._cache == saved
+    autotune._cache.clear()
+
+
+def test_signature_buckets():
+    p = types.SimpleNamespace(t_max=5, residual_pairs=0)
+    assert autotune.signature(1024, p) == autotune.signature(2047, p) == "n10_t5_r0"
+    assert autotune.signature(2048, p) == "n11_t5_r0"
+    assert autotune.signature(0, types.SimpleNamespace(t_max=1, residual_pairs=3)) == "n0_t1_r1"
