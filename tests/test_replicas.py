@@ -1,6 +1,7 @@
 """The N > 1 path of bench.py on CPU: independent replicas over a world_size-2
 gloo process group (no collective touches the data path; the timing takes the
 slowest replica, the value counts every replica's work)."""
+import json
 import os
 import socket
 
@@ -24,19 +25,20 @@ def _replica(rank, world, port, out):
     import bench
     # each replica times a different amount; the job takes the slowest
     t = bench.max_over_ranks(1.0 + rank, world, torch.device("cpu"))
-    out[rank] = (t, bench.job_value(100.0, world, t), bench.dist_env())
+    with open(os.path.join(out, f"{rank}.json"), "w") as f:
+        json.dump([t, bench.job_value(100.0, world, t), list(bench.dist_env())], f)
     dist.destroy_process_group()
 
 
-def test_max_over_ranks_and_job_value_on_two_gloo_ranks():
+def test_max_over_ranks_and_job_value_on_two_gloo_ranks(tmp_path):
     port = _free_port()
-    out = mp.Manager().dict()
-    mp.spawn(_replica, args=(2, port, out), nprocs=2, join=True)
+    mp.spawn(_replica, args=(2, port, str(tmp_path)), nprocs=2, join=True)
     for rank in (0, 1):
-        t, value, env = out[rank]
+        with open(tmp_path / f"{rank}.json") as f:
+            t, value, env = json.load(f)
         assert t == 2.0                  # the slowest replica's time, on every rank
         assert value == 2 * 100.0 / 2.0  # both replicas' work over that time
-        assert env == (rank, 2, rank)
+        assert env == [rank, 2, rank]
 
 
 def test_single_process_needs_no_group():
@@ -50,12 +52,14 @@ def _reference_rank(rank, world, port, out):
                       WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
     import bench
     args = bench.parse(["--impl", "reference", "--steps", "1", "--warmup", "0"])
-    out[rank] = bench.run_reference(args) if rank != 0 else "skipped"
+    res = bench.run_reference(args) if rank != 0 else "skipped"
+    with open(os.path.join(out, f"{rank}.json"), "w") as f:
+        json.dump(res, f)
 
 
-def test_reference_arm_runs_on_rank_zero_only():
+def test_reference_arm_runs_on_rank_zero_only(tmp_path):
     """Under torchrun the reference arm's other ranks exit without work."""
     port = _free_port()
-    out = mp.Manager().dict()
-    mp.spawn(_reference_rank, args=(2, port, out), nprocs=2, join=True)
-    assert out[1] is None
+    mp.spawn(_reference_rank, args=(2, port, str(tmp_path)), nprocs=2, join=True)
+    with open(tmp_path / "1.json") as f:
+        assert json.load(f) is None
