@@ -233,6 +233,19 @@ def test_partition_load_bound(oracle_mod, p):
             assert np.diff(offs).max() <= 2 * n // p
 
 
+def test_partition_load_bound_on_ranked_workloads(oracle_mod):
+    """Sec. 3.3.2 on real keys: the 200-sequence set (p = 4) and set 7 of the
+    batching workload (N = 1631, p = 4), both with N >= p^3, rank then partition; no
+    bucket exceeds 2N/p and the buckets tile the (key, index) order."""
+    for s in (datagen.config1(), datagen.batch_set(7)):
+        assert s.p >= 4
+        assert s.n >= s.p ** 3
+        r = oracle_mod.run_set(s.codes, s.offsets, s.p)
+        assert np.diff(r["bucket_offsets"]).max() <= 2 * s.n // s.p
+        check_partition_properties(r["key_hi"], r["key_lo"], s.p, r["bucket_offsets"],
+                                   r["members"], r["pivot_idx"])
+
+
 def test_partition_rejects_bad_p(oracle_mod):
     hi, lo = datagen.random_keys(5, seed=1)
     with pytest.raises(oracle_mod.OracleError):
