@@ -73,6 +73,24 @@ def job_value(units_per_rank: float, world: int, seconds: float) -> float:
     return world * units_per_rank / seconds
 
 
+def time_calls(calls: dict, reps: int, flush, stream, event_cls) -> dict:
+    """Median device milliseconds of each call run alone: L2 flushed before every
+    repetition, events recorded on the launching stream around the call."""
+    out = {}
+    for name, fn in calls.items():
+        times = []
+        for _ in range(reps):
+            flush()
+            e0, e1 = event_cls(enable_timing=True), event_cls(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        out[name] = statistics.median(times)
+    return out
+
+
 def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -641,6 +659,30 @@ def run_sad(args):
         "useful_frac": useful_flops / (gemm_launch_ms / 1e3) / 1e12 / f4_peak,
     }
 
+    # each call of the step alone (a2 count: HBM-bound; a7-a10 partition: latency-bound)
+    call_ms = time_calls(
+        {"kmer_count": lambda: sad.kmer_count(codes, offsets, ws=ws, out=counts, check=False,
+                                              word_max=word_max),
+         "kmer_rank": lambda: sad.kmer_rank(counts, lengths, ws=ws, out=keys, check=False,
+                                            plan=plan, word_max=word_max),
+         "partition": lambda: sad.partition(keys[0], keys[1], p, ws=ws_part, out=part,
+                                            check=False)},
+        reps=max(3, min(args.steps, 10)), flush=flush.zero_, stream=stream,
+        event_cls=torch.cuda.Event)
+    ws.check("per-call timing")
+    ws_part.check("per-call timing")
+    # codes and offsets read, counts [N][8000] and the per-word maxima written
+    count_bytes = int(s.codes.nbytes + s.offsets.nbytes + 4 * 8000 * n + 4 * 8000)
+    count_gbs = count_bytes / (call_ms["kmer_count"] / 1e3) / 1e9
+    calls = {
+        "kmer_count": {"ms": call_ms["kmer_count"], "algorithmic_bytes": count_bytes,
+                       "gbs": count_gbs, "hbm_peak_gbs": pk["hbm_gbs"],
+                       "frac": count_gbs / pk["hbm_gbs"], "peak_source": pk_kind},
+        "kmer_rank": {"ms": call_ms["kmer_rank"], "depth": info["depth"]},
+        "partition": {"ms": call_ms["partition"], "p": p},
+        "timing": "median of alone-runs, L2 flushed before each, CUDA events on the stream",
+    }
+
     # end to end through the public API, host buffers, H2D/D2H inside the timed region
     e2e = None
     if not args.no_e2e:
@@ -711,6 +753,7 @@ def run_sad(args):
             "gpu_launches": int(launches),
             "autotune": {"depth": depth, "trial_ms": {str(d): t for d, t in trials.items()}},
             "roofline": roofline,
+            "calls": calls,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clocks,

@@ -1,6 +1,7 @@
-"""Host-side logic that needs no GPU: serving admission and the depth autotuner's
-choice and cache (the device calls they make are replaced by fakes here; the same
-paths run on the GPU in test_gpu_serve.py and test_gpu_configs.py)."""
+"""Host-side logic that needs no GPU: serving admission, the depth autotuner's
+choice and cache, and the bench's per-call timing helper (the device calls and
+events they use are replaced by fakes here; the same paths run on the GPU in
+test_gpu_serve.py, test_gpu_configs.py and bench.py)."""
 import json
 import types
 
@@ -143,3 +144,38 @@ def test_signature_buckets():
     assert autotune.signature(1024, p) == autotune.signature(2047, p) == "n10_t5_r0"
     assert autotune.signature(2048, p) == "n11_t5_r0"
     assert autotune.signature(0, types.SimpleNamespace(t_max=1, residual_pairs=3)) == "n0_t1_r1"
+
+
+# ------------------------------------------------------------ bench helpers ---
+
+def test_time_calls_brackets_each_call_after_a_flush():
+    import bench
+    log = []
+    clock = [0.0]
+
+    class Ev:
+        def __init__(self, enable_timing=False):
+            assert enable_timing
+            self.t = None
+
+        def record(self, stream):
+            assert stream == "s"
+            self.t = clock[0]
+            log.append("record")
+
+        def synchronize(self):
+            pass
+
+        def elapsed_time(self, other):
+            return other.t - self.t
+
+    def work(ms):
+        def fn():
+            log.append("call")
+            clock[0] += ms
+        return fn
+
+    out = bench.time_calls({"a": work(2.0), "b": work(5.0)}, reps=3,
+                           flush=lambda: log.append("flush"), stream="s", event_cls=Ev)
+    assert out == {"a": 2.0, "b": 5.0}
+    assert log == ["flush", "record", "call", "record"] * 6
