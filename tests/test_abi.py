@@ -152,3 +152,108 @@ def test_every_kernel_waits_for_its_predecessor_first():
             assert body.startswith("pdl_enter();"), (name, text[m.start():k][:120])
             found += 1
     assert found >= 40
+
+
+def test_every_entry_point_checks_its_arguments_on_the_host():
+    """Each compute entry point rejects bad sizes, missing buffers, unsupported
+    k/alphabet and undersized workspaces before it touches the device (through the
+    binding's own prototypes). A fake, 256-aligned, never-dereferenced address
+    stands in for device buffers where a call needs one to reach its next check."""
+    from paper_0905_1744_gb300 import sad
+    L = sad.lib()
+    OK, INV, WS, UNS = sad.OK, sad.ERR_INVALID_ARGUMENT, sad.ERR_WORKSPACE, sad.ERR_UNSUPPORTED
+    d = 1 << 20                              # fake device address, aligned, never used
+    byref = ctypes.byref
+    # kmer_count
+    assert L.kmer_count(None, None, -1, 3, 20, None, None, d, 4096, None) == INV
+    assert L.kmer_count(None, None, 5, 9, 20, None, None, d, 4096, None) == UNS
+    assert L.kmer_count(None, None, 5, 3, 20, None, None, None, 4096, None) == INV
+    assert L.kmer_count(None, None, 5, 3, 20, None, None, d + 8, 4096, None) == INV  # unaligned
+    assert L.kmer_count(None, None, 5, 3, 20, None, None, d, 0, None) == INV
+    assert L.kmer_count(None, None, 5, 3, 20, None, None, d, 4096, None) == INV      # no codes
+    assert L.kmer_count(d, d + 4, 5, 3, 20, d, None, d, 4096, None) == INV           # offsets
+    assert L.kmer_count(None, None, 0, 3, 20, None, None, d, 4096, None) == OK       # empty set
+    # kmer_rank_plan: the fixed part of the workspace is reported when it is too small
+    plan = sad.RankPlan(depth=1)
+    assert L.kmer_rank_plan(None, 10, 9, 20, byref(plan), d, 0, None) == UNS
+    assert L.kmer_rank_plan(None, 10, 3, 20, None, d, 0, None) == INV
+    assert L.kmer_rank_plan(None, -1, 3, 20, byref(plan), d, 0, None) == INV
+    assert L.kmer_rank_plan(None, 10, 3, 20, byref(sad.RankPlan(depth=-1)), d, 0, None) == INV
+    assert L.kmer_rank_plan(None, 10, 3, 20, byref(plan), d, 0, None) == WS
+    assert plan.ws_bytes > 0
+    # kmer_rank: a plan's capacities are checked, then the workspace against them
+    good = sad.RankPlan(depth=1, k_cap=8192, list_cap=0, block_cap=0)
+    args = (d, d, None, 300, 3, 20)
+    outs = (d, d, None)
+    assert L.kmer_rank(*args, byref(good), *outs, d, 0, None) == WS
+    assert L.kmer_rank(*args, None, *outs, d, 0, None) == WS
+    assert L.kmer_rank(*args, byref(sad.RankPlan(depth=1, k_cap=100)), *outs, d, 1 << 30,
+                       None) == INV
+    assert L.kmer_rank(*args, byref(sad.RankPlan(depth=1, k_cap=8192, list_cap=-1)), *outs, d,
+                       1 << 30, None) == INV
+    assert L.kmer_rank(None, d, None, 300, 3, 20, byref(good), *outs, d, 1 << 30, None) == INV
+    assert L.kmer_rank(d, d, None, 300, 3, 20, byref(good), None, d, None, d, 1 << 30,
+                       None) == INV
+    assert L.kmer_rank(None, None, None, 0, 3, 20, None, None, None, None, d, 0, None) == OK
+    # partition and the allocation-free partition
+    assert L.partition(d, d, 10, 65, d, d, None, d, 1 << 20, None) == INV   # p above 64
+    assert L.partition(d, d, 10, 4, None, d, None, d, 1 << 20, None) == INV
+    assert L.partition(d, d, 10, 4, d, d, None, d, 0, None) == WS
+    assert L.partition_noalloc(d, d, 10, 0, d, d, None, None) == INV
+    assert L.partition_noalloc(d, d, 10, 11, d, d, None, None) == INV
+    assert L.partition_noalloc(d, d, 40000, 4, d, d, None, None) == UNS
+    assert L.partition_noalloc(d, d, 10, 4, None, d, None, None) == INV
+    # globalised rank: local samples, then every sequence against the references
+    assert L.sad_local_samples_workspace_bytes(10, 11) == 0
+    assert L.sad_local_samples(d, d, 10, 11, 2, d, d, 1 << 20, None) == INV
+    assert L.sad_local_samples(d, d, 10, 2, 0, d, d, 1 << 20, None) == INV
+    assert L.sad_local_samples(d, d, 10, 2, 2, None, d, 1 << 20, None) == INV
+    full = sad.RankPlan(depth=0, k_cap=8192)
+    assert L.kmer_rank_vs_workspace_bytes(byref(sad.RankPlan(depth=0, k_cap=0)), 10, 3, 20, 4,
+                                          0) == 0
+    assert L.kmer_rank_vs_workspace_bytes(byref(full), 10, 3, 20, 4, 0) > 0
+    vs = lambda plan, n_ref=4, delta=0: L.kmer_rank_vs(  # noqa: E731
+        d, d, None, 10, 3, 20, d, n_ref, delta, plan, None, d, d, None, d, 1 << 30, None)
+    assert vs(byref(sad.RankPlan(depth=1, k_cap=8192))) == INV      # needs every plane
+    assert vs(byref(sad.RankPlan(depth=0, k_cap=8000))) == INV      # k_cap not 256-aligned
+    assert vs(byref(full), n_ref=0) == INV
+    assert vs(byref(full), delta=1025) == INV
+    assert vs(None) == INV
+    # distance form
+    assert L.kmer_rank_dist_workspace_bytes(byref(good), 10, 3, 20, 0) == 0
+    assert L.kmer_rank_dist_workspace_bytes(byref(good), 10, 3, 20, 10) > 0
+    dist = lambda plan, delta=10, ws=1 << 30: L.kmer_rank_dist(  # noqa: E731
+        d, d, None, 10, 3, 20, delta, plan, None, d, d, None, d, ws, None)
+    assert dist(byref(good), delta=0) == INV
+    assert dist(byref(sad.RankPlan(depth=1, k_cap=8192, block_cap=-1))) == INV
+    assert dist(byref(good), ws=0) == WS
+    assert L.sad_ln_q(None, -1, None, None) == INV
+    assert L.sad_ln_q(None, 5, None, None) == INV
+    # sparse ablation
+    n_entries = ctypes.c_int64(0)
+    assert L.kmer_rank_sparse_workspace_bytes(0, 5) == 0
+    assert L.kmer_rank_sparse_workspace_bytes(10, -1) == 0
+    assert L.kmer_rank_sparse_entries(d, d, 0, 3, 20, byref(n_entries), d, 1 << 20, None) == INV
+    assert L.kmer_rank_sparse_entries(d, d, 10, 3, 20, None, d, 1 << 20, None) == INV
+    assert L.kmer_rank_sparse_entries(d, d, 10, 9, 20, byref(n_entries), d, 1 << 20,
+                                      None) == UNS
+    assert L.kmer_rank_sparse(d, d, 10, 3, 20, -1, d, d, None, d, 1 << 20, None) == INV
+    assert L.kmer_rank_sparse(d, d, 10, 3, 20, 5, d, None, None, d, 1 << 20, None) == INV
+    # batched forms
+    bp = sad.BatchPlan()
+    n_arr = (ctypes.c_int32 * 2)(10, 20)
+    p_arr = (ctypes.c_int32 * 2)(2, 25)                  # the second set has p > N
+    assert L.sad_batch_plan_make(d, n_arr, p_arr, d, 0, 3, 20, byref(bp), d, 1 << 20,
+                                 None) == INV
+    assert L.sad_batch_plan_make(d, n_arr, p_arr, d, 2, 3, 20, byref(bp), d, 1 << 20,
+                                 None) == INV
+    assert L.sad_batch_plan_make(d, n_arr, p_arr, d, 2, 3, 20, None, d, 1 << 20, None) == INV
+    assert L.sad_batch_rank(d, d, None, d, 3, 20, byref(bp), d, d, None, d, 1 << 20,
+                            None) == INV                   # n_sets = 0
+    bp.n_sets, bp.part_ws_bytes = 2, 1 << 20
+    assert L.sad_batch_partition(d, d, d, d, byref(bp), d, d, None, d, 1024, None) == WS
+    assert L.sad_batch_partition(d, d, d, None, byref(bp), d, d, None, d, 1 << 20, None) == INV
+    # status and info reads
+    info = (ctypes.c_int64 * 9)()
+    assert L.sad_rank_info(None, info, None) == INV
+    assert L.sad_status_read(None, 0, None) == INV
