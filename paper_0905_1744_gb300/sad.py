@@ -20,6 +20,7 @@ OP_COUNT, OP_RANK, OP_PARTITION = 0, 1, 2
 
 _lib = None
 _lock = threading.Lock()
+_DEVICE_TYPE = "cuda"       # where every tensor handed to the library must live
 
 
 class RankPlan(ctypes.Structure):
@@ -139,6 +140,37 @@ def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
 
+def _need(t, elem_bytes: int, name: str, where: str):
+    """A tensor whose data pointer goes to the library: on a CUDA device, dense,
+    with the element size the C-ABI declares for it (None passes: optional)."""
+    if t is None:
+        return
+    if not isinstance(t, torch.Tensor) or t.device.type != _DEVICE_TYPE:
+        raise TypeError(f"{where}: {name} must be a CUDA tensor")
+    if t.element_size() != elem_bytes:
+        raise TypeError(f"{where}: {name} must have {elem_bytes}-byte elements, not {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{where}: {name} must be contiguous")
+
+
+def _need_counts(counts, k: int, alphabet: int, where: str, word_max=None):
+    """int32 [N][alphabet^k] count vectors (and the optional per-word maxima)."""
+    _need(counts, 4, "counts", where)
+    if counts.dim() != 2 or counts.shape[1] != alphabet ** k:
+        raise ValueError(f"{where}: counts must be [N, {alphabet ** k}], not "
+                         f"{list(counts.shape)}")
+    _need(word_max, 4, "word_max", where)
+    if word_max is not None and word_max.numel() < alphabet ** k:
+        raise ValueError(f"{where}: word_max needs {alphabet ** k} entries")
+
+
+def _need_keys(key_hi, key_lo, where: str):
+    _need(key_hi, 8, "key_hi", where)
+    _need(key_lo, 8, "key_lo", where)
+    if key_hi.numel() != key_lo.numel():
+        raise ValueError(f"{where}: key_hi and key_lo differ in length")
+
+
 def _stream(stream):
     s = stream if stream is not None else torch.cuda.current_stream()
     return ctypes.c_void_p(s.cuda_stream)
@@ -194,7 +226,16 @@ def kmer_count(codes: torch.Tensor, offsets: torch.Tensor, k: int = 3, alphabet:
                check: bool = True, word_max: torch.Tensor | None = None) -> torch.Tensor:
     """int32 [N, alphabet**k] count vectors (Sec. 3, "k-mer Rank"). If ``word_max``
     (int32 [alphabet**k]) is given it receives the largest count of every word."""
+    _need(codes, 1, "codes", "kmer_count")
+    _need(offsets, 8, "offsets", "kmer_count")
+    _need(word_max, 4, "word_max", "kmer_count")
     n = offsets.numel() - 1
+    if out is not None:
+        _need(out, 4, "out", "kmer_count")
+        if out.dim() != 2 or tuple(out.shape) != (n, alphabet ** k):
+            raise ValueError(f"kmer_count: out must be [{n}, {alphabet ** k}]")
+    if word_max is not None and word_max.numel() < alphabet ** k:
+        raise ValueError(f"kmer_count: word_max needs {alphabet ** k} entries")
     ws = ws or Workspace(codes.device)
     ws.ensure(workspace_bytes(OP_COUNT, n, k, alphabet))
     if out is None:
@@ -211,6 +252,7 @@ def kmer_rank_plan(counts: torch.Tensor, k: int = 3, alphabet: int = 20, depth: 
                    ws: Workspace | None = None, stream=None) -> RankPlan:
     """Sizes and capacities for kmer_rank at plane depth ``depth`` (0 = all
     planes). Synchronous."""
+    _need_counts(counts, k, alphabet, "kmer_rank_plan")
     n = counts.shape[0]
     ws = ws or Workspace(counts.device)
     ws.ensure(workspace_bytes(OP_RANK, n, k, alphabet, depth=0))
@@ -241,8 +283,15 @@ def kmer_rank(counts: torch.Tensor, lengths: torch.Tensor, k: int = 3, alphabet:
     ``plan``: a RankPlan from kmer_rank_plan (reused as is); if None, one is made
     here for ``depth`` (0 = all planes), which synchronises the stream.
     """
+    _need_counts(counts, k, alphabet, "kmer_rank", word_max)
     n = counts.shape[0]
     dev = counts.device
+    if out is not None:
+        hi, lo, rank = out
+        _need_keys(hi, lo, "kmer_rank")
+        _need(rank, 8, "rank", "kmer_rank")
+        if hi.numel() != n or (rank is not None and rank.numel() != n):
+            raise ValueError(f"kmer_rank: outputs must hold {n} entries")
     ws = ws or Workspace(dev)
     if plan is None:
         plan = kmer_rank_plan(counts, k, alphabet, depth, ws, stream)
@@ -251,8 +300,6 @@ def kmer_rank(counts: torch.Tensor, lengths: torch.Tensor, k: int = 3, alphabet:
         hi = torch.empty(n, dtype=torch.uint64, device=dev)
         lo = torch.empty(n, dtype=torch.uint64, device=dev)
         rank = torch.empty(n, dtype=torch.float64, device=dev) if with_rank else None
-    else:
-        hi, lo, rank = out
     lengths = lengths.to(device=dev, dtype=torch.int32).contiguous()
     _check(_load().kmer_rank(_ptr(counts), _ptr(lengths), _ptr(word_max), n, k, alphabet,
                              ctypes.byref(plan),
@@ -263,11 +310,22 @@ def kmer_rank(counts: torch.Tensor, lengths: torch.Tensor, k: int = 3, alphabet:
     return hi, lo, rank
 
 
+def _need_partition_out(offs, mem, piv, n: int, p: int, where: str):
+    _need(offs, 4, "bucket_offsets", where)
+    _need(mem, 4, "members", where)
+    _need(piv, 4, "pivot_idx", where)
+    if offs.numel() < p + 1 or mem.numel() < n or (p > 1 and piv.numel() < p - 1):
+        raise ValueError(f"{where}: outputs need p + 1, N and p - 1 entries")
+
+
 def partition(key_hi: torch.Tensor, key_lo: torch.Tensor, p: int, ws: Workspace | None = None,
               stream=None, out=None, check: bool = True):
     """(bucket_offsets int32 [p+1], members int32 [N], pivot_idx int32 [p-1])."""
+    _need_keys(key_hi, key_lo, "partition")
     n = key_hi.numel()
     dev = key_hi.device
+    if out is not None:
+        _need_partition_out(*out, n, p, "partition")
     ws = ws or Workspace(dev)
     ws.ensure(workspace_bytes(OP_PARTITION, n, p=p))
     if out is None:
@@ -340,6 +398,7 @@ def partition_noalloc(key_hi: torch.Tensor, key_lo: torch.Tensor, p: int, stream
     memory: the library keeps a fixed 2 MiB scratch array per device, so the call
     allocates nothing beyond the outputs (which the caller may pass in ``out``).
     Limits: N <= 32768, p <= 64. Calls sharing a device must not overlap."""
+    _need_keys(key_hi, key_lo, "partition_noalloc")
     n = key_hi.numel()
     dev = key_hi.device
     if out is None:
@@ -348,6 +407,7 @@ def partition_noalloc(key_hi: torch.Tensor, key_lo: torch.Tensor, p: int, stream
         piv = torch.empty(max(p - 1, 1), dtype=torch.int32, device=dev)
     else:
         offs, mem, piv = out
+        _need_partition_out(offs, mem, piv, n, p, "partition_noalloc")
     _check(_load().partition_noalloc(_ptr(key_hi), _ptr(key_lo), n, p, _ptr(offs), _ptr(mem),
                                      _ptr(piv) if p > 1 else None, _stream(stream)),
            "partition_noalloc")
@@ -366,6 +426,7 @@ def local_ranks(counts: torch.Tensor, lengths: torch.Tensor, p: int, k: int = 3,
     as one block-diagonal batched rank (blocks as sets). Synchronous (plans).
     Returns (key_hi, key_lo, rank) in input order; rank = key / (w_b 2^64)."""
     import numpy as np
+    _need_counts(counts, k, alphabet, "local_ranks", word_max)
     n = counts.shape[0]
     dev = counts.device
     if not 1 <= p <= n:
@@ -401,8 +462,13 @@ def local_samples(key_hi: torch.Tensor, key_lo: torch.Tensor, p: int, ks: int,
                   ws: Workspace | None = None, stream=None, out=None, check: bool = True):
     """Algorithm 2 steps 3-5: ks evenly spaced samples of every block's sorted
     order; int32 [p * ks] input indices, block-major."""
+    _need_keys(key_hi, key_lo, "local_samples")
     n = key_hi.numel()
     dev = key_hi.device
+    if out is not None:
+        _need(out, 4, "out", "local_samples")
+        if out.numel() < p * ks:
+            raise ValueError(f"local_samples: out needs {p * ks} entries")
     ws = ws or Workspace(dev)
     ws.ensure(int(_load().sad_local_samples_workspace_bytes(n, p)))
     out = out if out is not None else torch.empty(p * ks, dtype=torch.int32, device=dev)
@@ -423,6 +489,7 @@ def kmer_rank_vs(counts: torch.Tensor, lengths: torch.Tensor, ref: torch.Tensor,
     synchronous). Returns (key_hi, key_lo, rank), rank = key / (len(ref) 2^64);
     with ``delta_den`` = b > 0 the distance form (Eq. 2, Delta = 1/b): returns
     (key int64, key_hi, key_lo, rank), rank = key 2^-32 / len(ref)."""
+    _need_counts(counts, k, alphabet, "kmer_rank_vs", word_max)
     n = counts.shape[0]
     dev = counts.device
     ws = ws or Workspace(dev)
@@ -448,6 +515,8 @@ def kmer_rank_vs(counts: torch.Tensor, lengths: torch.Tensor, ref: torch.Tensor,
 
 def ln_q(x: torch.Tensor, stream=None) -> torch.Tensor:
     """ln(x) * 2^32 as the deterministic fixed-point value of the distance-form rank."""
+    if not isinstance(x, torch.Tensor) or x.device.type != _DEVICE_TYPE:
+        raise TypeError("ln_q: x must be a CUDA tensor")
     x = x.to(dtype=torch.uint64).contiguous()
     out = torch.empty(x.shape, dtype=torch.int64, device=x.device)
     _check(_load().sad_ln_q(_ptr(x), x.numel(), _ptr(out), _stream(stream)), "sad_ln_q")
@@ -461,6 +530,7 @@ def kmer_rank_dist(counts: torch.Tensor, lengths: torch.Tensor, delta_den: int =
     """Eq. 2 / Eq. 3 literally: the mean of d = -ln(1/delta_den + F) over the set.
     Returns (key int64, key_hi, key_lo, rank float64); (key_hi, key_lo) order as
     the signed key, for partition."""
+    _need_counts(counts, k, alphabet, "kmer_rank_dist", word_max)
     n = counts.shape[0]
     dev = counts.device
     ws = ws or Workspace(dev)
@@ -486,6 +556,7 @@ def sparse_entries(counts: torch.Tensor, lengths: torch.Tensor, k: int = 3, alph
                    ws: Workspace | None = None, stream=None) -> int:
     """(sequence, word) entries with a nonzero count: the list capacity of
     kmer_rank_sparse. Synchronous."""
+    _need_counts(counts, k, alphabet, "sparse_entries")
     n = counts.shape[0]
     ws = ws or Workspace(counts.device)
     ws.ensure(int(_load().kmer_rank_sparse_workspace_bytes(n, 0)))
@@ -503,6 +574,7 @@ def kmer_rank_sparse(counts: torch.Tensor, lengths: torch.Tensor, k: int = 3,
     """The kmer_rank keys by sparse intersection on the CUDA cores (the O(L)-per-pair
     comparison point of Table 2). ``entries``: the list capacity (sized here,
     synchronously, if None). Returns (key_hi, key_lo, rank)."""
+    _need_counts(counts, k, alphabet, "kmer_rank_sparse")
     n = counts.shape[0]
     dev = counts.device
     ws = ws or Workspace(dev)
@@ -531,6 +603,7 @@ class GlobalRank:
                  k: int = 3, alphabet: int = 20, word_max: torch.Tensor | None = None,
                  local_depth: int = 0, stream=None, delta_den: int = 0):
         import numpy as np
+        _need_counts(counts, k, alphabet, "GlobalRank", word_max)
         n = counts.shape[0]
         dev = counts.device
         if not 1 <= p <= n or ks < 1:

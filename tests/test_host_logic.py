@@ -179,3 +179,78 @@ def test_time_calls_brackets_each_call_after_a_flush():
                            flush=lambda: log.append("flush"), stream="s", event_cls=Ev)
     assert out == {"a": 2.0, "b": 5.0}
     assert log == ["flush", "record", "call", "record"] * 6
+
+
+# ------------------------------------------------- binding argument checks ---
+
+@pytest.fixture
+def sad_no_lib(monkeypatch):
+    """The binding with its library replaced by a tripwire: every check below must
+    raise before any library call."""
+    from paper_0905_1744_gb300 import sad
+
+    def tripwire():
+        raise AssertionError("the library was reached")
+    monkeypatch.setattr(sad, "_load", tripwire)
+    return sad
+
+
+def test_binding_refuses_host_tensors(sad_no_lib):
+    sad = sad_no_lib
+    u8, i64 = torch.zeros(10, dtype=torch.uint8), torch.tensor([0, 5, 10])
+    counts = torch.zeros((2, 8000), dtype=torch.int32)
+    keys = torch.zeros(4, dtype=torch.uint64)
+    lengths = torch.tensor([5, 5], dtype=torch.int32)
+    calls = [lambda: sad.kmer_count(u8, i64),
+             lambda: sad.kmer_rank_plan(counts),
+             lambda: sad.kmer_rank(counts, lengths),
+             lambda: sad.partition(keys, keys, 2),
+             lambda: sad.partition_noalloc(keys, keys, 2),
+             lambda: sad.local_samples(keys, keys, 2, 1),
+             lambda: sad.local_ranks(counts, lengths, 1),
+             lambda: sad.kmer_rank_vs(counts, lengths, torch.tensor([0, 1])),
+             lambda: sad.kmer_rank_dist(counts, lengths),
+             lambda: sad.sparse_entries(counts, lengths),
+             lambda: sad.kmer_rank_sparse(counts, lengths),
+             lambda: sad.ln_q(keys),
+             lambda: sad.GlobalRank(counts, lengths, 1, 1)]
+    for f in calls:
+        with pytest.raises(TypeError, match="CUDA tensor"):
+            f()
+
+
+def test_binding_checks_element_size_layout_and_shape(sad_no_lib, monkeypatch):
+    sad = sad_no_lib
+    monkeypatch.setattr(sad, "_DEVICE_TYPE", "cpu")   # host tensors stand in for device ones
+    u8, i64 = torch.zeros(10, dtype=torch.uint8), torch.tensor([0, 5, 10])
+    with pytest.raises(TypeError, match="8-byte"):
+        sad.kmer_count(u8, i64.to(torch.int32))      # offsets are int64 in the C-ABI
+    with pytest.raises(TypeError, match="1-byte"):
+        sad.kmer_count(u8.to(torch.int32), i64)
+    with pytest.raises(ValueError, match="out must be"):
+        sad.kmer_count(u8, i64, out=torch.zeros((3, 8000), dtype=torch.int32))
+    with pytest.raises(ValueError, match="word_max"):
+        sad.kmer_count(u8, i64, word_max=torch.zeros(10, dtype=torch.int32))
+    counts = torch.zeros((2, 8000), dtype=torch.int32)
+    lengths = torch.tensor([5, 5], dtype=torch.int32)
+    with pytest.raises(ValueError, match="contiguous"):
+        sad.kmer_rank(torch.zeros((8000, 2), dtype=torch.int32).t(), lengths)
+    with pytest.raises(ValueError, match=r"\[N, 64\]"):
+        sad.kmer_rank(counts, lengths, 3, 4)          # counts of another alphabet
+    with pytest.raises(TypeError, match="4-byte"):
+        sad.kmer_rank(counts.to(torch.int64), lengths)
+    with pytest.raises(ValueError, match="outputs"):
+        sad.kmer_rank(counts, lengths,
+                      out=(torch.zeros(3, dtype=torch.uint64), torch.zeros(3, dtype=torch.uint64),
+                           None))
+    keys = torch.zeros(4, dtype=torch.uint64)
+    with pytest.raises(ValueError, match="differ"):
+        sad.partition(keys, keys[:3], 2)
+    with pytest.raises(TypeError, match="8-byte"):
+        sad.partition(keys.to(torch.int32), keys, 2)
+    with pytest.raises(ValueError, match="outputs need"):
+        sad.partition(keys, keys, 2, out=(torch.zeros(3, dtype=torch.int32),
+                                          torch.zeros(2, dtype=torch.int32),
+                                          torch.zeros(1, dtype=torch.int32)))
+    with pytest.raises(ValueError, match="out needs"):
+        sad.local_samples(keys, keys, 2, 3, out=torch.zeros(5, dtype=torch.int32))
