@@ -153,7 +153,7 @@ int kmer_rank_plan(const int32_t *d_counts, int32_t n_seq, int32_t k, int32_t al
  * t_max, k_eff, list_entries and residual_pairs are set to -1 (not known).
  * Returns SAD_ERR_INVALID_ARGUMENT for depth < 1 (all planes need the word
  * maxima) or negative sizes, SAD_ERR_UNSUPPORTED for unsupported k / alphabet
- * or more than 65535 row blocks.
+ * or more than 32767 row blocks of 128 (n_seq > 4194176).
  */
 int kmer_rank_plan_bound(int32_t n_seq, int64_t total_len, int32_t k, int32_t alphabet,
                          sad_rank_plan *plan);
@@ -171,7 +171,9 @@ int kmer_rank_plan_bound(int32_t n_seq, int64_t total_len, int32_t k, int32_t al
  * Internally min(a, b) = sum_t [a >= t][b >= t] turns all pairs into one
  * threshold-plane GEMM on the tensor cores; the N x N matrix is never stored.
  *   d_counts   int32 [n_seq][eps] from kmer_count (16-byte aligned for the
- *              vector path).
+ *              vector path); n_seq (or, batched, the rows of all sets, each set
+ *              padded to a multiple of 128) at most 32767 x 128 = 4194176
+ *              (SAD_ERR_UNSUPPORTED otherwise).
  *   d_lengths  int32 [n_seq] sequence lengths L (residues); every
  *              L - k + 1 must be in 1..65535 (SAD_ERR_UNSUPPORTED otherwise)
  *              and equal to the sum of the sequence's counts (SAD_ERR_BAD_INPUT).

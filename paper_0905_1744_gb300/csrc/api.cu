@@ -218,7 +218,7 @@ int rank_run_impl(const int32_t *d_counts, const int32_t *d_lengths, const int32
                   const sad_rank_plan *plan,
                   uint64_t *d_key_hi, uint64_t *d_key_lo, double *d_rank, void *d_ws,
                   size_t ws_bytes, cudaStream_t st) {
-  if (sh.rows_total / kRowBlock > 0xFFFF) return SAD_ERR_UNSUPPORTED;  // 16-bit block ids
+  if (sh.rows_total / kRowBlock > kMaxRowBlocks) return SAD_ERR_UNSUPPORTED;  // packed tile ids
   RankCaps caps{0, 0, 0, 0};
   if (plan) {
     if (plan->depth < 0 || plan->k_cap < kKCols || plan->k_cap % kKCols != 0 ||
@@ -284,7 +284,7 @@ int kmer_rank_plan_bound(int32_t n_seq, int64_t total_len, int32_t k, int32_t al
   if (eps < 0) return SAD_ERR_UNSUPPORTED;
   if (n_seq < 0 || total_len < 0 || !plan || plan->depth < 1) return SAD_ERR_INVALID_ARGUMENT;
   const RankShape sh = shape_single(n_seq);
-  if (sh.rows_total / kRowBlock > 0xFFFF) return SAD_ERR_UNSUPPORTED;
+  if (sh.rows_total / kRowBlock > kMaxRowBlocks) return SAD_ERR_UNSUPPORTED;
   const int64_t d = plan->depth;
   // K_eff = sum over words of min(T, d) <= eps d; a sequence has at most m / (d + 1)
   // words counted more than d times, and sum m = total_len - n (k - 1)
@@ -384,7 +384,7 @@ int kmer_rank_dist(const int32_t *d_counts, const int32_t *d_lengths, const int3
       plan->list_cap < 0 || plan->block_cap < 0)
     return SAD_ERR_INVALID_ARGUMENT;
   const RankShape sh = shape_single(n_seq);
-  if (sh.rows_total / kRowBlock > 0xFFFF) return SAD_ERR_UNSUPPORTED;
+  if (sh.rows_total / kRowBlock > kMaxRowBlocks) return SAD_ERR_UNSUPPORTED;
   const RankCaps caps{plan->depth, plan->k_cap, plan->list_cap, plan->block_cap};
   const RankLayout L = rank_layout(sh, eps, caps);
   const size_t table_off = align_up(L.bytes, 256);

@@ -210,7 +210,7 @@ int rank_vs_launch(const int32_t *counts, const int32_t *lengths, const int32_t 
   const RankLayout L = rank_layout(shape_single(n), eps, RankCaps{0, k_cap, 0, 0});
   const RefLayout R = ref_layout(L.bytes, L.shape.rows_total, n_ref, k_cap, delta_den);
   if (ws_bytes < R.bytes) return SAD_ERR_WORKSPACE;
-  if (L.shape.rows_total / kRowBlock > 0xFFFF) return SAD_ERR_UNSUPPORTED;
+  if (L.shape.rows_total / kRowBlock > kMaxRowBlocks) return SAD_ERR_UNSUPPORTED;
   const RankPtrs P = rank_ptrs(ws, L);
   uint8_t *b = static_cast<uint8_t *>(ws);
   int32_t *inv = reinterpret_cast<int32_t *>(b + R.inv);

@@ -24,6 +24,9 @@ constexpr int kColRatio = kColBlock / kRowBlock;  // row blocks per column block
 constexpr int kKChunk = 128;            // K bytes of a chunk (one 128B swizzle row)
 constexpr int kKCols = 2 * kKChunk;     // plane columns per K chunk: two 4-bit values a byte
 constexpr int kNPad = 128;              // rows are padded to a multiple of this
+// row blocks of one plane matrix: the tile list packs a tile's blocks as I | J << 16
+// in an int32 and reads J back with a signed shift, so J stays below 2^15
+constexpr int64_t kMaxRowBlocks = 0x7FFF;
 static_assert(kColBlock % kRowBlock == 0 && kNPad % kColBlock == 0, "tile shapes");
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }

@@ -99,6 +99,9 @@ def test_rank_plan_bound_is_host_only(lib):
     assert _bound(lib, 10, 100, 0)[0] == 1               # all planes need the word maxima
     assert _bound(lib, -1, 100, 1)[0] == 1
     assert _bound(lib, 10, 100, 1, k=9)[0] == 5
+    # the tile list packs row-block ids in 15 bits: at most 32767 blocks of 128 rows
+    assert _bound(lib, 32767 * 128, 300 * 32767 * 128, 1)[0] == 0
+    assert _bound(lib, 32767 * 128 + 1, 300 * (32767 * 128 + 1), 1)[0] == 5
 
 
 @pytest.mark.parametrize("depth", [1, 2, 3])
