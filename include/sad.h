@@ -42,7 +42,7 @@ typedef enum sad_status {
   SAD_ERR_WORKSPACE = 2,        /* workspace smaller than the data requires    */
   SAD_ERR_CUDA = 3,             /* a CUDA runtime call failed                  */
   SAD_ERR_TIMEOUT = 4,          /* a bounded device-side wait gave up          */
-  SAD_ERR_UNSUPPORTED = 5,      /* parameters outside what this build handles  */
+  SAD_ERR_UNSUPPORTED = 5,      /* parameters outside what the library handles */
   SAD_ERR_BAD_INPUT = 6         /* code >= alphabet, length < k, counts that do
                                    not add up to L - k + 1                     */
 } sad_status;

@@ -16,7 +16,8 @@
  *              (The printed subscript c^Y_j is read as c^Y_i.)
  *   rank       Eq. 3: R_i = (1/N) sum_{j=1..N} F(i,j): the mean of F over the
  *              whole set, j = i included. The paper averages the distance form
- *              of Eq. 2; this build ranks on F itself (see the design notes).
+ *              of Eq. 2; the rank here is the mean of F itself, and the
+ *              distance form is sad_oracle_rank_dist below.
  *              The key carried for each sequence is the 128-bit fixed-point sum
  *              key_i = sum_j floor(S_ij * 2^64 / D_ij), S_ij the Eq. 1 numerator
  *              and D_ij its denominator; the float view is

@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(128) kmer_count_kernel(const uint8_t *__restri
     } else if (e - s < K) {
       if (lane == 0) record_error(hdr, SAD_ERR_BAD_INPUT, (int)x);
     } else if (e - s - K + 1 > kMaxM) {
-      // 16-bit bins: longer sequences are outside what this build handles.
+      // 16-bit bins: longer sequences are outside what the library handles.
       if (lane == 0) record_error(hdr, SAD_ERR_UNSUPPORTED, (int)x);
     } else {
       bool bad = false;
