@@ -264,10 +264,12 @@ def run_reference(args):
     pairs = s.n * (s.n - 1) / 2
     out = {
         "impl": "reference", "metric": "k-mer pair comparisons/s", "value": value,
-        "unit": "pairs/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+        "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * pairs / value, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64/uint128 (CPU)", "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.config], "N": s.n, "p": s.p, "k": 3},
+        "device": "host CPU cores (the oracle; no GPU work)",
+        "config": {"workload": WORKLOADS[args.config], "N": s.n, "p": s.p, "k": 3,
+                   "alphabet": 20, "seed": args.seed, "parallelism": f"{threads} host threads"},
         "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": threads, "kind": "oracle",
                          "sample": f"rank of {rows_used} random rows against all {s.n} "
                                    f"sequences per step, extrapolated to the full set",
