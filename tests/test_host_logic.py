@@ -254,3 +254,44 @@ def test_binding_checks_element_size_layout_and_shape(sad_no_lib, monkeypatch):
                                           torch.zeros(1, dtype=torch.int32)))
     with pytest.raises(ValueError, match="out needs"):
         sad.local_samples(keys, keys, 2, 3, out=torch.zeros(5, dtype=torch.int32))
+
+
+# ------------------------------------------------------------ batch layout ---
+
+def test_batch_layout_and_per_set_results_on_the_host():
+    """The batch concatenates every set's sequences (offsets rebased), and its
+    per-set views cut the shared outputs at the right places: sequences, p + 1
+    bucket offsets and p - 1 pivots per set."""
+    from paper_0905_1744_gb300 import sad
+    sets = [datagen.random_small(n, 3, 40, seed=n) for n in (5, 1, 12)]
+    sets[0].p, sets[1].p, sets[2].p = 2, 1, 4
+    # a set whose offsets start past 0 (a view into a larger code buffer)
+    big = datagen.random_small(9, 3, 30, seed=99)
+    view = types.SimpleNamespace(codes=big.codes, offsets=big.offsets[3:], p=3)
+    sets.append(view)
+    b = sad.Batch(sets, device="cpu")
+    n = [5, 1, 12, 6]
+    assert b.n.tolist() == n and b.p.tolist() == [2, 1, 4, 3] and b.n_sets == 4
+    assert b.seq_begin.tolist() == [0, 5, 6, 18, 24]
+    assert b.boff_begin.tolist() == [0, 3, 5, 10, 14]
+    assert b.piv_begin.tolist() == [0, 1, 1, 4, 6]
+    codes = np.concatenate([s.codes[s.offsets[0]:s.offsets[-1]] for s in sets])
+    np.testing.assert_array_equal(b.codes.numpy(), codes)
+    lens = np.concatenate([np.diff(s.offsets) for s in sets])
+    np.testing.assert_array_equal(np.diff(b.offsets.numpy()), lens)
+    assert b.offsets[0] == 0 and b.lengths.dtype == torch.int32
+    np.testing.assert_array_equal(b.lengths.numpy(), lens)
+    assert tuple(b.counts.shape) == (24, 8000)
+    # per-set results are slices of the shared outputs
+    b.key_hi.copy_(torch.arange(24, dtype=torch.int64).to(torch.uint64))
+    b.members.copy_(torch.arange(24, dtype=torch.int32))
+    b.bucket_offsets.copy_(torch.arange(14, dtype=torch.int32))
+    b.pivot_idx.copy_(torch.arange(6, dtype=torch.int32))
+    r = b.result(2)
+    assert r["key_hi"].tolist() == list(range(6, 18))
+    assert r["members"].tolist() == list(range(6, 18))
+    assert r["bucket_offsets"].tolist() == [5, 6, 7, 8, 9]
+    assert r["pivot_idx"].tolist() == [1, 2, 3]
+    assert b.result(1)["pivot_idx"].tolist() == []
+    with pytest.raises(RuntimeError, match="plan"):
+        b.run()
