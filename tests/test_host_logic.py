@@ -295,3 +295,24 @@ def test_batch_layout_and_per_set_results_on_the_host():
     assert b.result(1)["pivot_idx"].tolist() == []
     with pytest.raises(RuntimeError, match="plan"):
         b.run()
+
+
+def test_gemm_traffic_is_reported_only_for_the_captured_source(tmp_path, monkeypatch):
+    """The DRAM traffic in the roofline comes from a committed ncu capture and is
+    reported only while the GEMM source is byte-identical to the captured one and
+    the set size matches; otherwise it is null."""
+    import hashlib
+
+    import bench
+    src = tmp_path / "paper_0905_1744_gb300" / "csrc"
+    src.mkdir(parents=True)
+    (src / "gemm.cu").write_bytes(b"// kernel v1\n")
+    (tmp_path / "profiles").mkdir()
+    sha = hashlib.sha256(b"// kernel v1\n").hexdigest()
+    (tmp_path / "profiles" / "plane_gemm_traffic.json").write_text(json.dumps(
+        {"N": 20000, "gemm_cu_sha256": sha, "dram_bytes_per_launch": 123}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.gemm_traffic_per_launch(20000, 8189) == 123
+    assert bench.gemm_traffic_per_launch(200, 8189) is None
+    (src / "gemm.cu").write_bytes(b"// kernel v2\n")
+    assert bench.gemm_traffic_per_launch(20000, 8189) is None
