@@ -10,6 +10,9 @@ Prints one JSON line. Extra objects:
   roofline      the plane-GEMM kernel: algorithmic tensor work per launch over
                 its CUDA-event time, against the 4-bit (e2m1) tensor peak derived
                 from the measured bf16 peak
+  calls         each call of the step run alone (L2 flushed before each run):
+                kmer_count with its algorithmic bytes and HBM fraction,
+                kmer_rank and partition as times
   cpu_baseline  the CPU oracle on a bounded sample of the same workload
   e2e           the same metric through the public API with host buffers
                 (H2D of codes + offsets and D2H of the buckets and keys timed)
@@ -22,6 +25,9 @@ Prints one JSON line. Extra objects:
                 the distance form) on a synthetic 500-sequence family set
   sparse_ablation  the same keys by sparse intersection on the CUDA cores (the
                 per-pair cost of Table 2), against the plane-GEMM rank time
+  batching      512 uneven sets in one captured CUDA graph against plain per-set calls
+  serving       continuous batching of Poisson arrivals (and a saturated burst)
+                against one-at-a-time service, latency percentiles and sets/s
 
 --impl reference times the CPU oracle on the same workload instead (one bounded
 sample per step). Under torchrun each rank runs an independent replica of the
