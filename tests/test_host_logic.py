@@ -316,3 +316,31 @@ def test_gemm_traffic_is_reported_only_for_the_captured_source(tmp_path, monkeyp
     assert bench.gemm_traffic_per_launch(200, 8189) is None
     (src / "gemm.cu").write_bytes(b"// kernel v2\n")
     assert bench.gemm_traffic_per_launch(20000, 8189) is None
+
+
+def test_reference_arm_prints_the_contract_line(monkeypatch, capsys):
+    """One JSON line with the main line's keys plus impl, cpu_baseline and e2e (the
+    oracle's timing replaced by a stub here; its real run takes minutes)."""
+    import bench
+    monkeypatch.setattr(bench, "oracle_counts", lambda s: None)
+    monkeypatch.setattr(bench, "oracle_sample",
+                        lambda s, sec, seed=0, counts=None: (2.0e6, 40, sec, 4))
+    for var in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        monkeypatch.delenv(var, raising=False)
+    bench.run_reference(bench.parse(["--impl", "reference", "--config", "1", "--steps", "4",
+                                     "--warmup", "3"]))
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["steps"] == 4 and d["warmup"] == 3
+    assert d["value"] == 2.0e6 and d["higher_is_better"] is True
+    assert d["ms_per_step"] == pytest.approx(1e3 * (200 * 199 / 2) / 2.0e6)
+    assert d["config"]["workload"] == bench.WORKLOADS[1] and d["config"]["N"] == 200
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 4 and cb["value"] == d["value"]
+    assert "sample" in cb
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
