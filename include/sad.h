@@ -66,7 +66,7 @@ int sad_abi_version(void);
  *   k, alphabet  word length and alphabet size (eps = alphabet^k words).
  *   p         number of buckets (SAD_OP_PARTITION only).
  *   depth     SAD_OP_RANK only: the threshold-plane columns to reserve, as a
- *             multiple of eps (K_cap = eps * depth rounded up to 128), with no
+ *             multiple of eps (K_cap = eps * depth rounded up to 256), with no
  *             residual capacity: enough for kmer_rank without a plan when
  *             K_eff = sum over words of the largest count <= K_cap.
  *             kmer_rank_plan() gives exact sizes for any depth. depth <= 0 gives
@@ -134,7 +134,8 @@ typedef struct sad_rank_plan {
  * until `stream` is idle.
  *   d_counts   int32 [n_seq][eps], as written by kmer_count.
  *   d_ws       a workspace of at least sad_workspace_bytes(SAD_OP_RANK, n_seq,
- *              k, alphabet, 0, 0) bytes (the fixed part).
+ *              k, alphabet, 0, 0) bytes (the fixed part). A smaller one returns
+ *              SAD_ERR_WORKSPACE at once with plan->ws_bytes set to that size.
  */
 int kmer_rank_plan(const int32_t *d_counts, int32_t n_seq, int32_t k, int32_t alphabet,
                    sad_rank_plan *plan, void *d_ws, size_t ws_bytes, void *stream);
