@@ -252,7 +252,7 @@ int partition_noalloc(const uint64_t *d_key_hi, const uint64_t *d_key_lo, int32_
  *                   workspace).
  *   n_sets, max_p   sets and the largest p_s.
  *   n_total, rows_total, tiles_total, tileof_total  sums over sets of n_s,
- *                   stored rows (n_s rounded up to 256), GEMM tiles and
+ *                   stored rows (n_s rounded up to 128), GEMM tiles and
  *                   tile-map entries.
  *   sum_p, sum_p1, sum_pp1, sum_pp  sums of p_s, p_s - 1, p_s (p_s - 1), p_s^2.
  *   part_ws_bytes   workspace bytes of sad_batch_partition.
