@@ -30,7 +30,11 @@ Parity status of each function (what pins it, in ``tests/test_oracle_pins.py``):
                quantisation bound.
   global_rank  p = 1 with ks = N samples every sequence once (positions
                floor(j N / (N + 1)), j = 1..N, are 0..N-1), so the globalised key
-               equals the centralised one.
+               equals the centralised one; the whole pipeline against exact
+               big-integer sums built from the sampled indices.
+  local_ranks  each block's keys equal the centralised keys of that block taken
+               as a set of its own (nothing outside the block enters).
+  rank_vs_dist every sequence as the reference set gives rank_dist.
 """
 from __future__ import annotations
 
