@@ -2,14 +2,16 @@
 """Throughput of the Sample-Align-D decomposition hot path on GB300.
 
 One step = kmer_count -> kmer_rank -> partition of one synthetic sequence set
-(default: N = 20000 protein sequences in 50 families, k = 3, p = 16) with the
-inputs already in HBM. The metric is k-mer pair comparisons per second: the
-N(N-1)/2 pairs whose shared k-mer count (Eq. 1) enters the ranks, per step time.
+(default: the largest workload, N = 100000 protein sequences in 500 families,
+k = 3, p = 64) with the inputs already in HBM. The metric is k-mer pair
+comparisons per second: the N(N-1)/2 pairs whose shared k-mer count (Eq. 1)
+enters the ranks, per step time.
 
 Prints one JSON line. Extra objects:
-  roofline      the plane-GEMM kernel: algorithmic tensor work per launch over
-                its CUDA-event time, against the 4-bit (e2m1) tensor peak derived
-                from the measured bf16 peak
+  roofline      the plane-GEMM kernel: the work of Eq. 1 as written (2 x 8000
+                ops per unordered pair) per launch over its CUDA-event time,
+                against the 4-bit (e2m1) tensor peak derived from the measured
+                bf16 peak; the MMA work actually issued beside it
   calls         each call of the step run alone (L2 flushed before each run):
                 kmer_count with its algorithmic bytes and HBM fraction,
                 kmer_rank and partition as times
@@ -17,9 +19,11 @@ Prints one JSON line. Extra objects:
   e2e           the same metric through the public API with host buffers
                 (H2D of codes + offsets and D2H of the buckets and keys timed)
   clocks        SM clocks and throttle reasons sampled during the timed region
-  globalised    the globalised rank of Sec. 3.1.1 on the same set (local ranks,
-                p - 1 samples per block, rank against the samples), timed, and
-                how its buckets compare with the centralised ones
+  configs       the other two workloads (N = 200 and N = 20000), each with the
+                same roofline, calls, e2e and oracle figures
+  globalised    the globalised rank of Sec. 3.1.1 on the N = 20000 set (local
+                ranks, p - 1 samples per block, rank against the samples), timed,
+                and how its buckets compare with the centralised ones
   distance_form the rank of Eq. 2 / Eq. 3 as written (mean -ln(1/10 + F)), timed
   table1_synthetic  the statistics of Table 1 (centralised vs globalised ranks in
                 the distance form) on a synthetic 500-sequence family set
@@ -56,7 +60,8 @@ WORKLOADS = {
     1: "N=200 iid protein sequences, L uniform 100-400, k=3 (8000 words), p=4",
     2: "N=20000 sequences in 50 families (ancestor L ~ N(300,100) clipped to 50-1000, "
        "20-40% substitutions, 2% indels of length 1-10), k=3, p=16",
-    3: "N=100000 sequences in 500 families (ancestor L log-uniform 50-2000), k=3, p=64",
+    3: "N=100000 sequences in 500 families (ancestor L log-uniform 50-2000, 20-40% "
+       "substitutions, 2% indels of length 1-10), k=3, p=64",
 }
 
 
@@ -103,7 +108,10 @@ def parse(argv=None):
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="sad", choices=["sad", "reference"])
-    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3])
+    ap.add_argument("--config", type=int, default=3, choices=[1, 2, 3],
+                    help="the main line's workload (default: the largest, N = 100000)")
+    ap.add_argument("--no-extra-configs", action="store_true",
+                    help="skip the c1/c2 lines (and the legs that run on the paper-scale set)")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
@@ -230,8 +238,9 @@ def oracle_sample(s, seconds: float, seed: int = 0, counts=None):
     """Time the oracle's rank on a row sample sized to ~`seconds` of CPU work.
 
     Returns (pairs_per_s, rows, elapsed, threads). The oracle computes each
-    row's shared counts with all N sequences, so R rows stand for R/N of the
-    full rank; the full set's pair count N(N-1)/2 then takes t * N / R.
+    sampled row's shared counts with all N sequences, so R rows are R (N - 1)
+    ordered comparisons, R (N - 1) / 2 unordered pair-equivalents; the rate is
+    that over the sample's own time (the full set would take N / R times as long).
     """
     import oracle
     oracle.build()
@@ -249,36 +258,45 @@ def oracle_sample(s, seconds: float, seed: int = 0, counts=None):
     t0 = time.perf_counter()
     oracle.kmer_rank(counts, s.lengths, rows=rows, threads=threads)
     t = time.perf_counter() - t0
-    pairs_full = s.n * (s.n - 1) / 2
-    return pairs_full / (t * s.n / r), r, t, threads
+    return r * (s.n - 1) / 2 / t, r, t, threads
+
+
+def bench_config(cfg: int, s, seed: int) -> dict:
+    """The workload description both arms print (identical dicts)."""
+    return {"workload": WORKLOADS[cfg], "N": s.n, "p": s.p, "k": 3, "alphabet": 20,
+            "seed": seed,
+            "l2": "inputs larger than L2 (int32 counts 4 x 8000 x N bytes) and a 256 MB "
+                  "write between timed GPU steps"}
 
 
 def run_reference(args):
+    """The oracle on the host cores: each step ranks a bounded random row sample
+    against all N sequences; ms_per_step is that sample's own time."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     s = datagen.config(args.config, args.seed)
     per_step = max(0.5, 120.0 / max(1, args.steps + args.warmup))
     counts = oracle_counts(s)
-    vals, rows_used, threads = [], 0, 1
+    vals, secs, rows_used, threads = [], [], 0, 1
     for i in range(args.warmup + args.steps):
         v, r, t, threads = oracle_sample(s, per_step, seed=args.seed + i, counts=counts)
         if i >= args.warmup:
             vals.append(v)
+            secs.append(t)
             rows_used = r
     value = statistics.mean(vals)
-    pairs = s.n * (s.n - 1) / 2
     out = {
         "impl": "reference", "metric": "k-mer pair comparisons/s", "value": value,
         "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * pairs / value, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": 1e3 * statistics.mean(secs), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64/uint128 (CPU)", "data": "synthetic",
-        "device": "host CPU cores (the oracle; no GPU work)",
-        "config": {"workload": WORKLOADS[args.config], "N": s.n, "p": s.p, "k": 3,
-                   "alphabet": 20, "seed": args.seed, "parallelism": f"{threads} host threads"},
+        "device": f"host CPU cores (the oracle, {threads} threads; no GPU work)",
+        "config": bench_config(args.config, s, args.seed),
         "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": threads, "kind": "oracle",
-                         "sample": f"rank of {rows_used} random rows against all {s.n} "
-                                   f"sequences per step, extrapolated to the full set",
+                         "sample": f"each step: {rows_used} random rows against all {s.n} "
+                                   f"sequences ({rows_used} x {s.n - 1} / 2 pair-equivalents), "
+                                   "timed alone",
                          "cpu": cpu_model()},
         "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
@@ -557,19 +575,18 @@ def run_serving(args, dev, depth):
     return out
 
 
-def run_sad(args):
+def measure_config(cfg: int, args, dev, world: int, steps: int, warmup: int,
+                   with_e2e: bool, with_cpu: bool, cpu_seconds: float) -> dict:
+    """One config's step (kmer_count -> kmer_rank -> partition, inputs in HBM):
+    autotuned plan, CUDA-event timing of `steps` steps after `warmup`, the plane
+    GEMM's roofline, each call alone, the public API with host buffers (e2e) and
+    the oracle on a bounded sample."""
     import torch
     import torch.distributed as dist
 
     from paper_0905_1744_gb300 import autotune, sad
 
-    rank, world, local = dist_env()
-    if world > 1:
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    dev = torch.device("cuda", local if world > 1 else 0)
-    torch.cuda.set_device(dev)
-    s = datagen.config(args.config, args.seed)
+    s = datagen.config(cfg, args.seed)
     n, p = s.n, s.p
     pairs = n * (n - 1) / 2
     stream = torch.cuda.current_stream()
@@ -604,14 +621,14 @@ def run_sad(args):
         sad.partition(keys[0], keys[1], p, ws=ws_part, out=part, check=False)
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # 2x the 129 MB L2
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     ws.check("warmup rank")
     ws_part.check("warmup partition")
     info = sad.rank_info(ws)
 
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
+           for _ in range(steps)]
     sampler = ClockSampler(dev.index)
     sampler.start()
     time.sleep(0.3)
@@ -634,37 +651,35 @@ def run_sad(args):
     ws_part.check("timed partition")
     step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
     total_ms = max_over_ranks(float(sum(step_ms)), world, dev)
-    ms_per_step = total_ms / args.steps
+    ms_per_step = total_ms / steps
     value = job_value(pairs, world, ms_per_step / 1e3)
 
     # roofline of the plane GEMM (the dominant kernel)
     pk, pk_kind = peaks()
     # e2m1 dense = 6 x bf16 (nominal 13.5 / 2.25 PFLOP/s), applied to the measured bf16
-    # peak. The burst figure: the timed loop is short (a few hundred ms) and runs at the
-    # maximum SM clock (see "clocks").
+    # peak. The burst figure: the timed loop is short and runs at the maximum SM clock
+    # (see "clocks").
     f4_ratio = 13.5 / 2.25
     f4_peak = f4_ratio * pk["bf16_tflops"]
     gemm_launch_ms = gemm_ms / max(gemm_n, 1)
-    alg_flops = 2.0 * info["k_eff"] * n * (n + 1) / 2           # S = P P^T, upper triangle
-    exec_flops = 2.0 * 128 * 128 * 256 * info["k_chunks"]        # MMA work actually issued
-    useful_flops = 2.0 * 8000 * pairs                             # Eq. 1 as written: 2 eps / pair
-    achieved = alg_flops / (gemm_launch_ms / 1e3) / 1e12
+    useful_flops = 2.0 * 8000 * pairs                    # Eq. 1 as written: 2 eps per pair
+    exec_flops = 2.0 * 128 * 128 * 256 * info["k_chunks"]  # MMA work actually issued
+    achieved = useful_flops / (gemm_launch_ms / 1e3) / 1e12
     roofline = {
         "bound": "tensor",
         "kernel": "plane_gemm_kernel (tcgen05 kind::mxf4nvf4, e2m1 0/1 planes, unit scales)",
         "achieved": achieved, "peak": f4_peak, "unit": "TFLOP/s", "frac": achieved / f4_peak,
+        "work": "Eq. 1 as written: 2 x 8000 ops (min and add over the 8000 words) per "
+                "unordered pair, N(N-1)/2 pairs per launch",
         "peak_source": f"{pk_kind}: 6 x bf16_tflops burst (e2m1/bf16 nominal ratio "
                        f"13.5/2.25); sustained would be "
-                       f"{f4_ratio * pk['bf16_tflops_sustained']:.1f}; the e4m3 peak "
-                       f"(2 x bf16) would be {2.0 * pk['bf16_tflops']:.1f}",
+                       f"{f4_ratio * pk['bf16_tflops_sustained']:.1f}",
         "traffic": gemm_traffic_per_launch(n, info["k_eff"]),
         "gemm_ms_per_launch": gemm_launch_ms, "gemm_share_of_step": gemm_launch_ms / ms_per_step,
-        "k_eff": info["k_eff"], "k_pad": info["k_pad"], "t_max": info["t_max"],
-        "tiles": info["tiles"], "depth": info["depth"],
-        "residual_pairs": info["residual_pairs"], "residual_tiles": info["residual_tiles"],
         "executed_tflops": exec_flops / (gemm_launch_ms / 1e3) / 1e12,
         "executed_frac": exec_flops / (gemm_launch_ms / 1e3) / 1e12 / f4_peak,
-        "useful_frac": useful_flops / (gemm_launch_ms / 1e3) / 1e12 / f4_peak,
+        "plan": {k: info[k] for k in ("k_eff", "k_pad", "t_max", "tiles", "k_chunks", "depth",
+                                      "residual_pairs", "residual_tiles")},
     }
 
     # each call of the step alone (a2 count: HBM-bound; a7-a10 partition: latency-bound)
@@ -675,7 +690,7 @@ def run_sad(args):
                                             plan=plan, word_max=word_max),
          "partition": lambda: sad.partition(keys[0], keys[1], p, ws=ws_part, out=part,
                                             check=False)},
-        reps=max(3, min(args.steps, 10)), flush=flush.zero_, stream=stream,
+        reps=max(3, min(steps, 10)), flush=flush.zero_, stream=stream,
         event_cls=torch.cuda.Event)
     ws.check("per-call timing")
     ws_part.check("per-call timing")
@@ -693,7 +708,7 @@ def run_sad(args):
 
     # end to end through the public API, host buffers, H2D/D2H inside the timed region
     e2e = None
-    if not args.no_e2e:
+    if with_e2e:
         h_codes = torch.from_numpy(s.codes).pin_memory()
         h_offs = torch.from_numpy(s.offsets).pin_memory()
         h_mem = torch.empty(n, dtype=torch.int32).pin_memory()
@@ -714,7 +729,7 @@ def run_sad(args):
 
         for _ in range(2):
             e2e_step()
-        reps = max(3, min(args.steps, 20))
+        reps = max(3, min(steps, 20))
         if world > 1:
             dist.barrier()
         t0 = time.perf_counter()
@@ -726,52 +741,101 @@ def run_sad(args):
                "d2h_bytes_per_step": int(4 * n + 4 * (p + 1) + 16 * n),
                "ms_per_step": 1e3 * t_e2e}
 
+    cpu = None
+    if with_cpu:
+        v, r, t, threads = oracle_sample(s, cpu_seconds, seed=args.seed)
+        cpu = {"value": v, "unit": "pairs/s", "cores": threads, "kind": "oracle",
+               "sample": f"{r} random rows against all {n} sequences "
+                         f"({r} x {n - 1} / 2 pair-equivalents) in {t:.1f} s",
+               "cpu": cpu_model()}
+
+    return {"s": s, "value": value, "ms_per_step": ms_per_step, "steps": steps,
+            "warmup": warmup, "launches": int(launches), "clocks": clocks,
+            "autotune": {"depth": depth, "trial_ms": {str(d): t for d, t in trials.items()}},
+            "roofline": roofline, "calls": calls, "e2e": e2e, "cpu_baseline": cpu,
+            "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms),
+            "tensors": (counts, lengths, word_max, keys, depth, trials)}
+
+
+def extra_line(m: dict) -> dict:
+    """A secondary config's figures, in the main line's vocabulary."""
+    return {"N": m["s"].n, "p": m["s"].p, "value": m["value"], "unit": "pairs/s",
+            "ms_per_step": m["ms_per_step"], "steps": m["steps"], "warmup": m["warmup"],
+            "autotune": m["autotune"], "roofline": m["roofline"], "calls": m["calls"],
+            "e2e": m["e2e"], "cpu_baseline": m["cpu_baseline"], "clocks": m["clocks"]}
+
+
+def run_sad(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    cpu_ok = rank == 0 and world == 1 and not args.no_cpu_baseline
+
+    main = measure_config(args.config, args, dev, world, args.steps, args.warmup,
+                          with_e2e=not args.no_e2e, with_cpu=cpu_ok,
+                          cpu_seconds=args.cpu_seconds)
+    extras = {}
+    side = None
+    if not args.no_extra_configs and world == 1:
+        for c in (1, 2, 3):
+            if c == args.config:
+                continue
+            m = measure_config(c, args, dev, world, min(args.steps, 20), 3, with_e2e=True,
+                               with_cpu=cpu_ok, cpu_seconds=min(args.cpu_seconds, 8.0))
+            extras[f"c{c}"] = {"workload": WORKLOADS[c], **extra_line(m)}
+            if c == 2:
+                side = m
+    if side is None and args.config == 2:
+        side = main
+
     globalised = distance = table1 = sparse = None
-    if not args.no_global and world == 1:
-        globalised = run_global(args, dev, counts, lengths, word_max, keys, p)
-        distance = run_distance(args, dev, counts, lengths, word_max, depth)
-        sparse = run_sparse(args, dev, counts, lengths, trials.get(depth))
+    if not args.no_global and world == 1 and side is not None:
+        counts, lengths, word_max, keys, depth2, trials2 = side["tensors"]
+        p2 = side["s"].p
+        globalised = run_global(args, dev, counts, lengths, word_max, keys, p2)
+        distance = run_distance(args, dev, counts, lengths, word_max, depth2)
+        sparse = run_sparse(args, dev, counts, lengths, trials2.get(depth2))
         table1 = run_table1(args, dev, args.seed)
+        for leg in (globalised, distance, sparse):
+            leg["on"] = "the paper-scale set: " + WORKLOADS[2]
     batching = None
     if not args.no_batching:
         batching = run_batching(args, dev)
     serving = None
     if not args.no_serving and world == 1:
-        serving = run_serving(args, dev, depth=batching["depth"] if batching else depth)
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, r, t, threads = oracle_sample(s, args.cpu_seconds, seed=args.seed)
-        cpu = {"value": v, "unit": "pairs/s", "cores": threads, "kind": "oracle",
-               "sample": f"rank of {r} random rows against all {n} sequences "
-                         f"({t:.1f} s), extrapolated to the full set",
-               "cpu": cpu_model()}
+        serving = run_serving(args, dev, depth=batching["depth"] if batching else 0)
 
     if rank == 0:
+        s = main["s"]
         out = {
-            "metric": "k-mer pair comparisons/s", "value": value, "unit": "pairs/s",
+            "metric": "k-mer pair comparisons/s", "value": main["value"], "unit": "pairs/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": main["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "e2m1 0/1 planes (fp4), f32 acc (exact), u128 keys",
             "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.config], "N": n, "p": p, "k": 3,
-                       "alphabet": 20, "seed": args.seed,
-                       "l2": "flushed between steps (256 MB write)",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
-            "gpu_launches": int(launches),
-            "autotune": {"depth": depth, "trial_ms": {str(d): t for d, t in trials.items()}},
-            "roofline": roofline,
-            "calls": calls,
-            "cpu_baseline": cpu,
-            "e2e": e2e,
-            "clocks": clocks,
+            "config": bench_config(args.config, s, args.seed),
+            "parallelism": "replicas" if world > 1 else "single GPU",
+            "gpu_launches": main["launches"],
+            "autotune": main["autotune"],
+            "roofline": main["roofline"],
+            "calls": main["calls"],
+            "cpu_baseline": main["cpu_baseline"],
+            "e2e": main["e2e"],
+            "clocks": main["clocks"],
+            "configs": extras,
             "globalised": globalised,
             "distance_form": distance,
             "table1_synthetic": table1,
             "sparse_ablation": sparse,
             "batching": batching,
             "serving": serving,
-            "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms),
+            "step_ms_min": main["step_ms_min"], "step_ms_median": main["step_ms_median"],
         }
         print(json.dumps(out))
     if world > 1:

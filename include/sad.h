@@ -221,15 +221,17 @@ int partition(const uint64_t *d_key_hi, const uint64_t *d_key_lo, int32_t n_seq,
  * a host application that forbids allocation after start-up, a hot path that
  * must not touch the allocator). The paper has no counterpart: this is an
  * interface convenience of this library.
- *   Its scratch is a fixed 2 MiB array inside the library's device image, held
- *   by every GPU that loads the library until the process exits. Limits:
- *   n_seq <= 32768 and p <= 64; larger calls return SAD_ERR_UNSUPPORTED and
- *   launch nothing. Other arguments and outputs are those of partition().
+ *   Its scratch is a fixed array inside the library's device image, sized for
+ *   the largest accepted call (about 2.1 MiB), held by every GPU that loads the
+ *   library until the process exits. Limits: n_seq <= 32768 and p <= 64, in
+ *   any combination; larger calls return SAD_ERR_UNSUPPORTED and launch
+ *   nothing. Other arguments and outputs are those of partition().
  *   The first call on a device looks up the array's device address (with that
  *   device current); make that first call before any stream capture.
- *   All calls share the one array and it keeps the last call's contents; the
- *   call clears what must start at zero. Calls whose GPU work overlaps race on
- *   the array: keep them ordered on one stream.
+ *   All calls share the one array and it keeps the last call's contents;
+ *   nothing in it needs clearing, since each call writes every region before
+ *   reading it. Calls whose GPU work overlaps race on the array: keep them
+ *   ordered on one stream.
  */
 int partition_noalloc(const uint64_t *d_key_hi, const uint64_t *d_key_lo, int32_t n_seq,
                       int32_t p, int32_t *d_bucket_offsets, int32_t *d_members,
@@ -448,6 +450,21 @@ uint64_t sad_launch_count(void);
 int sad_rank_info(void *d_ws, int64_t *info, void *stream);
 int sad_profile(int32_t enable);
 int sad_profile_read(double *gemm_ms, int64_t *gemm_launches);
+
+/*
+ * sad_debug_wait_budget_ns - failure detection test hook (the paper has no
+ *   counterpart). Every wait of the plane GEMM (a TMA copy landing, an MMA
+ *   freeing a pipeline stage, an accumulator filling or draining) is a bounded
+ *   spin on %globaltimer; on running out the CTA records SAD_ERR_TIMEOUT in the
+ *   workspace status, waits for its own copies and MMAs in flight (with a fixed
+ *   2 s budget), frees its tensor memory and returns, so the context stays
+ *   usable. This sets the budget of those main-loop waits for every later launch
+ *   in the process: ns = 0 restores the default of 2 s. A budget of a few
+ *   nanoseconds makes the first wait that does not succeed at once give up,
+ *   which is how the tests drive the timeout path without a hang.
+ *   Returns SAD_OK.
+ */
+int sad_debug_wait_budget_ns(uint64_t ns);
 
 #ifdef __cplusplus
 }

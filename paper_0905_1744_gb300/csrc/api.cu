@@ -58,6 +58,13 @@ int check_cuda(cudaError_t e) {
 void note_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
 
 namespace {
+constexpr uint64_t kDefaultWaitNs = 2000000000ull;
+std::atomic<uint64_t> g_wait_ns{kDefaultWaitNs};
+}  // namespace
+
+uint64_t gemm_wait_ns() { return g_wait_ns.load(std::memory_order_relaxed); }
+
+namespace {
 std::mutex g_prof_mu;
 bool g_prof_on = false;
 std::vector<cudaEvent_t> g_prof_pool;                       // reusable events
@@ -115,6 +122,11 @@ int num_sms() {
 using namespace sad;
 
 extern "C" {
+
+int sad_debug_wait_budget_ns(uint64_t ns) {
+  g_wait_ns.store(ns == 0 ? kDefaultWaitNs : ns, std::memory_order_relaxed);
+  return SAD_OK;
+}
 
 const char *sad_status_string(int status) {
   switch (status) {

@@ -39,22 +39,13 @@
 // The double TMEM accumulator lets the epilogue of one tile overlap the MMAs of
 // the next.
 //
-// Pair mode (one set, square; opt-in): clusters of two CTAs run the M = 256 form of the
-// MMA (cta_group::2). The pair takes row blocks 2u and 2u + 1 against one column
-// block J >= 2u: each CTA loads its own 128 rows of A and one 64-row half of B,
-// so a CTA takes in 24 KB per K chunk instead of 32 for the same 128 x 128 tile
-// of results; the even CTA waits for both CTAs' copies, issues the MMAs and
-// multicasts its commits to both. Each CTA's epilogue is the one above on its
-// own tile (2u + rank, J); a tile below the diagonal or past the last row block
-// is computed and left out.
-//
-// Every wait is bounded (globaltimer); on a timeout the CTA records
-// SAD_ERR_TIMEOUT, drains its copies and MMAs in flight, frees TMEM and returns.
+// Every wait is bounded (globaltimer; the budget of the main-loop waits is
+// P.wait_ns, 2 s unless a test shortens it); on a timeout the CTA records
+// SAD_ERR_TIMEOUT, drains its copies and MMAs in flight (waits with the full 2 s
+// budget), frees TMEM and returns.
 #include "rank.cuh"
 
 #include <cudaTypedefs.h>
-
-#include <cstdlib>
 
 namespace sad {
 
@@ -77,10 +68,9 @@ constexpr uint32_t kSfbCol = kSfaCol + 32;
 constexpr uint32_t kSfCols = 64;  // filled with 1.0
 static_assert(kSfaCol + kSfCols <= kTmemCols, "TMEM columns");
 constexpr int kHalfCols = kColBlock / 2;  // columns of one epilogue warp
-constexpr uint64_t kWaitBudgetNs = 2000000000ull;
-// pair mode: bytes one CTA loads per stage (A rows + half of B's rows)
-constexpr uint32_t kPairTxBytes = kABytes + kBBytes / 2;
-constexpr int kEpiWarps = kEpiThreads / 32;
+// budget of the drain waits after an abort (the copies and MMAs in flight finish
+// in microseconds)
+constexpr uint64_t kDrainBudgetNs = 2000000000ull;
 
 struct GemmSmem {
   uint8_t a[kStages][kABytes];
@@ -189,26 +179,7 @@ __device__ __forceinline__ void f_block16(const uint32_t (&v)[16], const uint32_
   }
 }
 
-// Pair p of a pair-mode launch over R row blocks (R column blocks): row blocks
-// 2u, 2u + 1 against column block J, u-major with J = 2u .. R - 1; nk is the
-// larger K extent of the pair's tiles (columns past a tile's own extent are zero
-// in one of its two row blocks). tile_of: the (I, J) -> tile map of the set.
-__device__ __forceinline__ void pair_at(const RankPtrs &P, int32_t R, int32_t p, int32_t &u,
-                                        int32_t &J, int32_t &nk) {
-  // pairs before row pair u: u (R - u + 1)
-  int32_t lo = 0, hi = (R + 1) / 2;  // largest u with u (R - u + 1) <= p
-  while (hi - lo > 1) {
-    const int32_t mid = (lo + hi) >> 1;
-    if ((int64_t)mid * (R - mid + 1) <= p) lo = mid; else hi = mid;
-  }
-  u = lo;
-  J = 2 * u + (p - u * (R - u + 1));
-  const int64_t base = P.sets[0].tileof_base;
-  nk = P.tiles[P.tile_of[base + (int64_t)(2 * u) * R + J]].y;
-  if (2 * u + 1 <= J) nk = max(nk, P.tiles[P.tile_of[base + (int64_t)(2 * u + 1) * R + J]].y);
-}
-
-template <bool kDist, bool kPair>
+template <bool kDist>
 __global__ void __launch_bounds__(kThreads, 1)
     plane_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                       const __grid_constant__ CUtensorMap tmB, RankPtrs P, RectArgs X,
@@ -219,11 +190,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   volatile int32_t *abort_flag = &S.abort;
-  const uint32_t crank = kPair ? cluster_ctarank() : 0u;
-  const bool leader = crank == 0;
-  // persistent loop: work units (tiles, or pairs in pair mode) unit0, unit0 + ustride, ...
-  const int32_t unit0 = kPair ? (int32_t)cluster_id_x() : (int32_t)blockIdx.x;
-  const int32_t ustride = kPair ? (int32_t)cluster_count_x() : (int32_t)gridDim.x;
+  const uint64_t wait_ns = P.wait_ns;  // budget of the main-loop waits
 
   if (threadIdx.x == 0) {
     S.abort = 0;
@@ -235,8 +202,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&S.tfull[a], 1);
-      // pair mode: one arrival per epilogue warp of both CTAs, on the even CTA's barrier
-      mbar_init(&S.tempty[a], kPair ? 2 * kEpiWarps : kEpiThreads);
+      mbar_init(&S.tempty[a], kEpiThreads);
     }
     mbar_init(&S.drain, 1);
     fence_mbar_init();
@@ -247,22 +213,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   __syncthreads();
   const bool skip = S.skip != 0;
-  // pair mode: the allocation is a collective of both CTAs, whatever either decides
-  const bool has_tmem = kPair || !skip;
-  if (has_tmem && warp == 2) {
-    if constexpr (kPair) {
-      tmem_alloc_pair(&S.tmem_base, kTmemCols);
-      tmem_relinquish_pair();
-    } else {
-      tmem_alloc(&S.tmem_base, kTmemCols);
-      tmem_relinquish();
-    }
+  if (!skip && warp == 2) {
+    tmem_alloc(&S.tmem_base, kTmemCols);
+    tmem_relinquish();
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = S.tmem_base;
-  if (has_tmem && warp >= 4 && warp < 8) {
+  if (!skip && warp >= 4 && warp < 8) {
     // every block scale of A and B is 1.0: fill their columns in this warp's lanes
     const uint32_t lanes = ((warp & 3u) * 32u) << 16;
 #pragma unroll
@@ -271,63 +230,17 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   tc_fence_before();
   __syncthreads();
-  // pair mode: both CTAs' barriers and TMEM are ready before either uses the other's
-  if constexpr (kPair) cluster_sync_all();
   tc_fence_after();
   const bool rect = X.rec_ref != nullptr;
-  // work units: pairs (pair mode, X.n_tiles), reference tiles (rectangular), or tiles
-  const int32_t n_tiles = skip ? 0 : ((rect || kPair) ? X.n_tiles : P.hdr->n_tiles);
-  const int32_t pair_R = X.row_blocks;  // pair mode: row (= column) blocks of the set
+  // work units: reference tiles (rectangular mode) or the rank's tiles
+  const int32_t n_tiles = skip ? 0 : (rect ? X.n_tiles : P.hdr->n_tiles);
   // rectangular mode: every tile runs all K_pad columns the rank preparation wrote
   const int32_t rect_nk = (rect && !skip) ? max(1, P.hdr->k_pad / kKCols) : 0;
   // counts above the plane depth come in as dense per-tile residual blocks
   const bool residual =
       !skip && P.depth_cap >= 1 && P.block_cap > 0 && P.hdr->depth < P.hdr->t_max;
 
-  if (kPair && !skip && warp == 0 && lane == 0) {
-    // ------------------------------------------------- producer, pair mode --
-    // both CTAs count their copies on the even CTA's full barrier, which expects
-    // the bytes of both
-    int stage = 0;
-    uint32_t phase = 0, used = 0, par = 0;
-    bool aborted = false;
-    for (int32_t p = unit0; p < n_tiles && !aborted; p += ustride) {
-      int32_t u, J, nk;
-      pair_at(P, pair_R, p, u, J, nk);
-      const int32_t I = 2 * u + (int32_t)crank;
-      for (int32_t kc = 0; kc < (nk + kCps - 1) / kCps; ++kc) {
-        if (!mbar_wait_bounded_cluster(&S.empty[stage], phase ^ 1u, abort_flag, kWaitBudgetNs)) {
-          set_abort(S, P.hdr);
-          aborted = true;
-          break;
-        }
-        if (leader) mbar_arrive_expect_tx(&S.full[stage], 2 * kPairTxBytes);
-        const uint32_t fb = mapa_shared(&S.full[stage], 0);
-        tma_load_3d_pair(S.a[stage], &tmA, fb, 0, I * kRowBlock, kc * kCps);
-        tma_load_3d_pair(S.b[stage], &tmB, fb, 0, J * kColBlock + (int32_t)crank * (kColBlock / 2),
-                         kc * kCps);
-        used |= 1u << stage;
-        par = (par & ~(1u << stage)) | (phase << stage);
-        if (++stage == kStages) {
-          stage = 0;
-          phase ^= 1u;
-        }
-      }
-    }
-    if (aborted || *abort_flag) {
-      if (leader) {
-        // the even CTA's full barriers count the copies of both CTAs
-        for (int s = 0; s < kStages; ++s)
-          if (used & (1u << s))
-            mbar_wait_bounded(&S.full[s], (par >> s) & 1u, &S.never, kWaitBudgetNs);
-      } else {
-        // this CTA cannot see its copies land: give them time (they take microseconds)
-        const uint64_t t0 = globaltimer_ns();
-        while (globaltimer_ns() - t0 < 200000ull) {
-        }
-      }
-    }
-  } else if (!kPair && !skip && warp == 0 && lane == 0) {
+  if (!skip && warp == 0 && lane == 0) {
     // ------------------------------------------------------------ producer --
     int stage = 0;
     uint32_t phase = 0, used = 0, par = 0;
@@ -336,7 +249,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       int32_t I, J, nk;
       tile_at(P, X, rect_nk, t, I, J, nk);
       for (int32_t kc = 0; kc < (nk + kCps - 1) / kCps; ++kc) {
-        if (!mbar_wait_bounded(&S.empty[stage], phase ^ 1u, abort_flag, kWaitBudgetNs)) {
+        if (!mbar_wait_bounded(&S.empty[stage], phase ^ 1u, abort_flag, wait_ns)) {
           set_abort(S, P.hdr);
           aborted = true;
           break;
@@ -352,62 +265,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
     }
-    if (aborted || *abort_flag) {
-      // let every copy this thread started land before the CTA exits
-      for (int s = 0; s < kStages; ++s)
-        if (used & (1u << s))
-          mbar_wait_bounded(&S.full[s], (par >> s) & 1u, &S.never, kWaitBudgetNs);
-    }
-  } else if (kPair && !skip && warp == 1 && lane == 0 && leader) {
-    // ------------------------------------------------------ MMA, pair mode --
-    const uint32_t idesc = idesc_f4_e2m1(2 * kRowBlock, kColBlock);
-    const uint32_t sfa = tmem + kSfaCol, sfb = tmem + kSfbCol;
-    int stage = 0;
-    uint32_t phase = 0;
-    bool aborted = false;
-    int32_t lt = 0;
-    for (int32_t p = unit0; p < n_tiles && !aborted; p += ustride, ++lt) {
-      int32_t u, J, nk;
-      pair_at(P, pair_R, p, u, J, nk);
-      const uint32_t acc = lt & 1, aph = (lt >> 1) & 1;
-      if (!mbar_wait_bounded_cluster(&S.tempty[acc], aph ^ 1u, abort_flag, kWaitBudgetNs)) {
-        set_abort(S, P.hdr);
-        aborted = true;
-        break;
-      }
-      tc_fence_after();
-      const uint32_t d_tmem = tmem + acc * (uint32_t)kColBlock;
-      for (int32_t kc = 0; kc < (nk + kCps - 1) / kCps; ++kc) {
-        if (!mbar_wait_bounded_cluster(&S.full[stage], phase, abort_flag, kWaitBudgetNs)) {
-          set_abort(S, P.hdr);
-          aborted = true;
-          break;
-        }
-        tc_fence_after();
-        // each CTA holds 64 rows of B: its K chunks are kSubB / 2 apart
-        const int nsub = min(kCps, nk - kc * kCps);
-        for (int sub = 0; sub < nsub; ++sub) {
-          const uint64_t adesc = sdesc_kmajor_sw128(smem_u32(S.a[stage] + sub * kSubA));
-          const uint64_t bdesc = sdesc_kmajor_sw128(smem_u32(S.b[stage] + sub * (kSubB / 2)));
-#pragma unroll
-          for (int kk = 0; kk < kKChunk / 32; ++kk)
-            mma_f4_pair(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, idesc, sfa, sfb,
-                        (kc | sub | kk) != 0 ? 1u : 0u);
-        }
-        mma_commit_pair(&S.empty[stage], 0x3);
-        if (++stage == kStages) {
-          stage = 0;
-          phase ^= 1u;
-        }
-      }
-      if (aborted) break;
-      mma_commit_pair(&S.tfull[acc], 0x3);
-    }
-    if (aborted || *abort_flag) {
-      mma_commit_pair(&S.drain, 0x1);
-      mbar_wait_bounded(&S.drain, 0, &S.never, kWaitBudgetNs);
-    }
-  } else if (!kPair && !skip && warp == 1 && lane == 0) {
+    // let every copy this thread started land before the CTA exits (after a normal
+    // run the MMAs have consumed them all and these waits return at once)
+    for (int s = 0; s < kStages; ++s)
+      if (used & (1u << s)) mbar_wait_bounded(&S.full[s], (par >> s) & 1u, &S.never, kDrainBudgetNs);
+  } else if (!skip && warp == 1 && lane == 0) {
     // ----------------------------------------------------------------- MMA --
     const uint32_t idesc = idesc_f4_e2m1(kRowBlock, kColBlock);
     const uint32_t sfa = tmem + kSfaCol, sfb = tmem + kSfbCol;
@@ -419,7 +281,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       int32_t I, J, nk;
       tile_at(P, X, rect_nk, t, I, J, nk);
       const uint32_t acc = lt & 1, aph = (lt >> 1) & 1;
-      if (!mbar_wait_bounded(&S.tempty[acc], aph ^ 1u, abort_flag, kWaitBudgetNs)) {
+      if (!mbar_wait_bounded(&S.tempty[acc], aph ^ 1u, abort_flag, wait_ns)) {
         set_abort(S, P.hdr);
         aborted = true;
         break;
@@ -427,7 +289,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_after();
       const uint32_t d_tmem = tmem + acc * (uint32_t)kColBlock;
       for (int32_t kc = 0; kc < (nk + kCps - 1) / kCps; ++kc) {
-        if (!mbar_wait_bounded(&S.full[stage], phase, abort_flag, kWaitBudgetNs)) {
+        if (!mbar_wait_bounded(&S.full[stage], phase, abort_flag, wait_ns)) {
           set_abort(S, P.hdr);
           aborted = true;
           break;
@@ -453,10 +315,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (aborted) break;
       mma_commit(&S.tfull[acc]);
     }
-    if (aborted || *abort_flag) {
-      mma_commit(&S.drain);
-      mbar_wait_bounded(&S.drain, 0, &S.never, kWaitBudgetNs);
-    }
+    // every MMA this thread issued has completed before TMEM is freed (after an
+    // abort, and also when an epilogue gave up after this loop ended normally)
+    mma_commit(&S.drain);
+    mbar_wait_bounded(&S.drain, 0, &S.never, kDrainBudgetNs);
   } else if (!skip && warp >= 4 && warp < 12) {
     // ------------------------------------------------------------ epilogue --
     // warp w reads TMEM lanes 32 (w % 4).. (its quadrant) and tile columns
@@ -465,18 +327,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t half = (warp - 4) >> 2;
     const uint32_t etid = threadIdx.x - 128;
     int32_t lt = 0;
-    for (int32_t t = unit0; t < n_tiles; t += ustride, ++lt) {
+    for (int32_t t = blockIdx.x; t < n_tiles; t += gridDim.x, ++lt) {
       int32_t I, J, nk;
-      int32_t tile = t;  // pair mode: this CTA's tile of the pair, -1 below the diagonal
-      if constexpr (kPair) {
-        int32_t u;
-        pair_at(P, pair_R, t, u, J, nk);
-        I = 2 * u + (int32_t)crank;
-        tile = I <= J ? P.tile_of[P.sets[0].tileof_base + (int64_t)I * pair_R + J] : -1;
-      } else {
-        tile_at(P, X, rect_nk, t, I, J, nk);
-      }
-      const bool tile_ok = tile >= 0;
+      tile_at(P, X, rect_nk, t, I, J, nk);
+      const int32_t tile = t;
+      const bool tile_ok = true;
       const int buf = lt & 1;
       for (uint32_t c = etid; c < (uint32_t)kColBlock; c += kEpiThreads) {
         const int64_t jpos = (int64_t)J * kColBlock + c;
@@ -508,8 +363,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         rb = __ldg(rrow + 1);
       }
       const uint32_t acc = lt & 1, aph = (lt >> 1) & 1;
-      const bool got = kPair ? mbar_wait_bounded_cluster(&S.tfull[acc], aph, abort_flag, kWaitBudgetNs)
-                             : mbar_wait_bounded(&S.tfull[acc], aph, abort_flag, kWaitBudgetNs);
+      const bool got = mbar_wait_bounded(&S.tfull[acc], aph, abort_flag, wait_ns);
       if (!got) set_abort(S, P.hdr);
       // column records staged; the abort decision is the same for every epilogue thread
       if (named_bar_sync_or(1, kEpiThreads, *abort_flag != 0)) break;
@@ -672,17 +526,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       }
       tc_fence_before();
-      if constexpr (kPair) {
-        __syncwarp();
-        if (lane == 0) {
-          if (leader)
-            mbar_arrive(&S.tempty[acc]);
-          else
-            mbar_arrive_cluster(mapa_shared(&S.tempty[acc], 0));
-        }
-      } else {
-        mbar_arrive(&S.tempty[acc]);
-      }
+      mbar_arrive(&S.tempty[acc]);
       if (kDist && !rect) {
         // square distance form: as below, with one signed 64-bit sum per row and column
         if (tile_ok && half == 1)
@@ -750,14 +594,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   tc_fence_before();
   __syncthreads();
-  if constexpr (kPair) {
-    // every MMA into either CTA's TMEM, reading either CTA's shared memory, is done
-    cluster_sync_all();
-    if (warp == 2) {
-      tc_fence_after();
-      tmem_dealloc_pair(tmem, kTmemCols);
-    }
-  } else if (!skip && warp == 2) {
+  if (!skip && warp == 2) {
     tc_fence_after();
     tmem_dealloc(tmem, kTmemCols);
   }
@@ -798,16 +635,10 @@ namespace {
 int gemm_attr() {
   static bool attr_set = false;
   if (!attr_set) {
-    if (cudaFuncSetAttribute(plane_gemm_kernel<false, false>,
+    if (cudaFuncSetAttribute(plane_gemm_kernel<false>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kGemmSmemBytes) != cudaSuccess ||
-        cudaFuncSetAttribute(plane_gemm_kernel<true, false>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kGemmSmemBytes) != cudaSuccess ||
-        cudaFuncSetAttribute(plane_gemm_kernel<false, true>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kGemmSmemBytes) != cudaSuccess ||
-        cudaFuncSetAttribute(plane_gemm_kernel<true, true>,
+        cudaFuncSetAttribute(plane_gemm_kernel<true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kGemmSmemBytes) != cudaSuccess)
       return SAD_ERR_CUDA;
@@ -816,78 +647,6 @@ int gemm_attr() {
   return SAD_OK;
 }
 
-// Pair mode is opt-in (SAD_GEMM_PAIR=1): on the paper-scale set its TMA + MMA
-// mainloop measured slower than one CTA per tile (0.84 against 0.72 ms) although
-// each CTA loads a quarter fewer bytes.
-bool pair_mode_enabled() {
-  const char *e = getenv("SAD_GEMM_PAIR");
-  return e && e[0] == '1';
-}
-
-// Largest number of co-resident clusters of two for the pair kernel (0: none).
-template <bool kDist>
-int pair_clusters() {
-  static int cached = -1;
-  if (cached < 0) {
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3((unsigned)(2 * num_sms()), 1, 1);
-    cfg.blockDim = dim3(kThreads, 1, 1);
-    cfg.dynamicSmemBytes = kGemmSmemBytes;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, plane_gemm_kernel<kDist, true>, &cfg) != cudaSuccess) {
-      (void)cudaGetLastError();
-      n = 0;
-    }
-    cached = n;
-  }
-  return cached;
-}
-
-// One set, square: the CTA-pair kernel over the u-major pairs of row blocks.
-// Returns SAD_OK and sets *done when it launched; leaves *done false when the
-// device cannot hold a cluster of two (the caller then runs one CTA per tile).
-template <bool kDist>
-int launch_pair(const RankPtrs &P, const CUtensorMap &mA, const DistArgs &Z, cudaStream_t st,
-                bool *done) {
-  *done = false;
-  if (P.n_sets != 1 || !pair_mode_enabled()) return SAD_OK;
-  const int ncl = pair_clusters<kDist>();
-  if (ncl < 1) return SAD_OK;
-  const int64_t R = (P.n_total + kRowBlock - 1) / kRowBlock;
-  int64_t pairs = 0;
-  for (int64_t u = 0; 2 * u < R; ++u) pairs += R - 2 * u;
-  if (pairs <= 0 || pairs > 0x7FFFFFFF) return SAD_OK;
-  CUtensorMap mBh;  // B in halves of 64 rows, one per CTA of the pair
-  int rc = make_plane_map(&mBh, P.planes, P.n_pad, P.k_cap, kColBlock / 2);
-  if (rc) return rc;
-  RectArgs X;
-  X.n_tiles = (int32_t)pairs;
-  X.row_blocks = (int32_t)R;
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = 2;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  const int64_t clusters = pairs < ncl ? pairs : ncl;
-  cfg.gridDim = dim3((unsigned)(2 * clusters), 1, 1);
-  cfg.blockDim = dim3(kThreads, 1, 1);
-  cfg.dynamicSmemBytes = kGemmSmemBytes;
-  cfg.stream = st;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  if (cudaLaunchKernelEx(&cfg, plane_gemm_kernel<kDist, true>, mA, mBh, P, X, Z) != cudaSuccess)
-    return SAD_ERR_CUDA;
-  *done = true;
-  return SAD_OK;
-}
 }  // namespace
 
 int rank_gemm_launch(const RankPtrs &P, cudaStream_t st) {
@@ -901,11 +660,8 @@ int rank_gemm_launch(const RankPtrs &P, cudaStream_t st) {
   if ((rc = gemm_attr())) return rc;
   const int64_t grid = tiles < num_sms() ? tiles : num_sms();
   prof_begin(st);
-  bool done = false;
-  if ((rc = launch_pair<false>(P, mA, DistArgs{}, st, &done))) return rc;
-  if (!done)
-    pdl_launch(plane_gemm_kernel<false, false>, (unsigned)grid, kThreads, kGemmSmemBytes, st, mA,
-               mB, P, RectArgs{}, DistArgs{});
+  pdl_launch(plane_gemm_kernel<false>, (unsigned)grid, kThreads, kGemmSmemBytes, st, mA, mB, P,
+             RectArgs{}, DistArgs{});
   SAD_LAUNCH_CHECK();
   prof_end(st);
   return SAD_OK;
@@ -925,11 +681,8 @@ int rank_dist_gemm_launch(const RankPtrs &P, const int64_t *ln_table, int32_t b,
   Z.ln_table = ln_table;
   Z.b = b;
   const int64_t grid = tiles < num_sms() ? tiles : num_sms();
-  bool done = false;
-  if ((rc = launch_pair<true>(P, mA, Z, st, &done))) return rc;
-  if (!done)
-    pdl_launch(plane_gemm_kernel<true, false>, (unsigned)grid, kThreads, kGemmSmemBytes, st, mA, mB,
-               P, RectArgs{}, Z);
+  pdl_launch(plane_gemm_kernel<true>, (unsigned)grid, kThreads, kGemmSmemBytes, st, mA, mB, P,
+             RectArgs{}, Z);
   SAD_LAUNCH_CHECK();
   return SAD_OK;
 }
@@ -956,11 +709,11 @@ int rank_rect_gemm_launch(const RankPtrs &P, uint8_t *ref_planes, const uint4 *r
     DistArgs Z;
     Z.ln_table = ln_table;
     Z.b = b;
-    pdl_launch(plane_gemm_kernel<true, false>, (unsigned)grid, kThreads, kGemmSmemBytes, st, mA, mB,
-               P, X, Z);
+    pdl_launch(plane_gemm_kernel<true>, (unsigned)grid, kThreads, kGemmSmemBytes, st, mA, mB, P,
+               X, Z);
   } else {
-    pdl_launch(plane_gemm_kernel<false, false>, (unsigned)grid, kThreads, kGemmSmemBytes, st, mA,
-               mB, P, X, DistArgs{});
+    pdl_launch(plane_gemm_kernel<false>, (unsigned)grid, kThreads, kGemmSmemBytes, st, mA, mB, P,
+               X, DistArgs{});
   }
   SAD_LAUNCH_CHECK();
   return SAD_OK;

@@ -19,8 +19,9 @@
 // with cudaGetSymbolAddress while that device is current and caches it. That
 // first call should therefore come before any stream capture.
 //
-// Every call shares the one array and leaves its contents behind; the call
-// clears what must start at zero (the status header). Calls whose GPU work
+// Every call shares the one array and leaves its contents behind; nothing in it
+// has to start at zero, because each call's kernels write every region before
+// they read it (the partition records no status in the header). Calls whose GPU work
 // overlaps (on different streams, or from different threads without ordering)
 // race on the array: serialise them on one stream.
 #include <mutex>
@@ -37,7 +38,10 @@ namespace {
 
 constexpr int32_t kNoAllocMaxN = 32768;
 constexpr int32_t kNoAllocMaxP = 64;
-constexpr size_t kNoAllocScratchBytes = (size_t)2 << 20;  // 2 MiB
+// The partition's workspace at the largest accepted (N, p): every region of the
+// layout grows with N and p, so this holds every accepted call (about 2.1 MiB).
+constexpr size_t kNoAllocScratchBytes = part_layout(kNoAllocMaxN, kNoAllocMaxP).bytes;
+static_assert(kNoAllocScratchBytes <= ((size_t)3 << 20), "scratch stays modest");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
@@ -77,7 +81,6 @@ extern "C" int partition_noalloc(const uint64_t *d_key_hi, const uint64_t *d_key
   if (n_seq < 0 || p < 1) return SAD_ERR_INVALID_ARGUMENT;
   if (n_seq > 0 && p > n_seq) return SAD_ERR_INVALID_ARGUMENT;
   if (n_seq > kNoAllocMaxN || p > kNoAllocMaxP) return SAD_ERR_UNSUPPORTED;
-  if (part_layout(n_seq, p).bytes > kNoAllocScratchBytes) return SAD_ERR_UNSUPPORTED;
   if (!d_bucket_offsets) return SAD_ERR_INVALID_ARGUMENT;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (n_seq == 0) {
@@ -92,11 +95,8 @@ extern "C" int partition_noalloc(const uint64_t *d_key_hi, const uint64_t *d_key
   void *scratch = nullptr;
   int rc = noalloc_scratch(&scratch);
   if (rc) return rc;
-  // the header (status word) must start at zero; the rest is written before it is read
-  if (cudaMemsetAsync(scratch, 0, sizeof(WsHeader), st) != cudaSuccess) {
-    cudaGetLastError();
-    return SAD_ERR_CUDA;
-  }
+  // every region the partition kernels read is written by an earlier kernel of the
+  // same call, so nothing needs clearing between calls
   return partition_launch(d_key_hi, d_key_lo, n_seq, p, d_bucket_offsets, d_members,
                           d_pivot_idx, scratch, st);
 }

@@ -75,6 +75,7 @@ struct RankPtrs {
   int64_t n_pad;         // rows_total: stored rows over all sets
   int64_t n_total, n_sets, tiles_total, k_cap, list_cap, block_cap;
   int32_t depth_cap;     // 0 = all planes
+  uint64_t wait_ns;      // budget of the GEMM's main-loop waits
 };
 
 RankPtrs rank_ptrs(void *ws, const RankLayout &L);

@@ -83,6 +83,7 @@ RankPtrs rank_ptrs(void *ws, const RankLayout &L) {
   P.list_cap = L.caps.list_cap;
   P.block_cap = L.caps.block_cap;
   P.depth_cap = L.caps.depth;
+  P.wait_ns = gemm_wait_ns();
   return P;
 }
 

@@ -29,7 +29,7 @@ constexpr int kNPad = 128;              // rows are padded to a multiple of this
 constexpr int64_t kMaxRowBlocks = 0x7FFF;
 static_assert(kColBlock % kRowBlock == 0 && kNPad % kColBlock == 0, "tile shapes");
 
-inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // --------------------------------------------------------- workspace hdr ----
 // The first 256 bytes of every workspace.
@@ -203,7 +203,7 @@ struct PartTotals {
   int64_t n, p, p1, pp1, pp;  // sums over sets of n, p, p - 1, p (p - 1), p^2
 };
 
-inline PartTotals part_totals_single(int64_t n, int64_t p) {
+constexpr PartTotals part_totals_single(int64_t n, int64_t p) {
   return PartTotals{n, p, p - 1, p * (p - 1), p * p};
 }
 
@@ -212,7 +212,8 @@ struct PartLayout {
   size_t bytes;
 };
 
-inline PartLayout part_layout_sets(int64_t n_sets, const PartTotals &t) {
+// Every region grows with n and p, so the layout at the largest (n, p) bounds all smaller ones.
+constexpr PartLayout part_layout_sets(int64_t n_sets, const PartTotals &t) {
   PartLayout L{};
   size_t o = sizeof(WsHeader);
   auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes, 256); return r; };
@@ -231,13 +232,15 @@ inline PartLayout part_layout_sets(int64_t n_sets, const PartTotals &t) {
   return L;
 }
 
-inline PartLayout part_layout(int64_t n, int64_t p) {
+constexpr PartLayout part_layout(int64_t n, int64_t p) {
   return part_layout_sets(1, part_totals_single(n, p));
 }
 
 // ------------------------------------------------------ host bookkeeping ----
 void note_launch(int n = 1);
 int num_sms();
+// Budget of the plane GEMM's main-loop waits (sad_debug_wait_budget_ns; 2 s by default).
+uint64_t gemm_wait_ns();
 // GEMM timing hooks (no-ops unless sad_profile(1) was called)
 void prof_begin(cudaStream_t st);
 void prof_end(cudaStream_t st);

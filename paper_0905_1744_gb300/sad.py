@@ -128,6 +128,8 @@ def _load():
         lib.sad_profile.restype = ctypes.c_int
         lib.sad_profile_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
         lib.sad_profile_read.restype = ctypes.c_int
+        lib.sad_debug_wait_budget_ns.argtypes = [ctypes.c_uint64]
+        lib.sad_debug_wait_budget_ns.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -389,15 +391,22 @@ def profile_read():
     return float(ms.value), int(n.value)
 
 
+def debug_wait_budget_ns(ns: int):
+    """Budget of the plane GEMM's main-loop waits for later launches (0 = the
+    default 2 s). A test hook: a few nanoseconds drives the timeout path."""
+    _check(_load().sad_debug_wait_budget_ns(int(ns)), "sad_debug_wait_budget_ns")
+
+
 NOALLOC_MAX_N, NOALLOC_MAX_P = 32768, 64
 
 
 def partition_noalloc(key_hi: torch.Tensor, key_lo: torch.Tensor, p: int, stream=None,
                       out=None):
     """partition() without a workspace, for callers that cannot allocate device
-    memory: the library keeps a fixed 2 MiB scratch array per device, so the call
-    allocates nothing beyond the outputs (which the caller may pass in ``out``).
-    Limits: N <= 32768, p <= 64. Calls sharing a device must not overlap."""
+    memory: the library keeps a fixed scratch array per device (about 2.1 MiB,
+    sized for the largest accepted call), so the call allocates nothing beyond
+    the outputs (which the caller may pass in ``out``). Limits: N <= 32768 and
+    p <= 64 in any combination. Calls sharing a device must not overlap."""
     _need_keys(key_hi, key_lo, "partition_noalloc")
     n = key_hi.numel()
     dev = key_hi.device

@@ -130,20 +130,6 @@ def test_rank_depth_cap_ragged(sad, oracle_mod, n, depth):
     check_rank(sad, oracle_mod, s, k=3, alphabet=8, depth=depth)
 
 
-@pytest.mark.parametrize("n,depth", [(1, 0), (129, 0), (383, 1), (700, 2)])
-def test_rank_cta_pair_kernel(sad, oracle_mod, monkeypatch, n, depth):
-    """SAD_GEMM_PAIR=1 runs one set on CTA pairs (M = 256 MMAs, each CTA loading
-    half of B): the same keys as one CTA per tile and the oracle, including odd
-    numbers of row blocks where the last pair's second tile is empty."""
-    s = datagen.random_small(n, 3, 700, seed=n + 5, alphabet=20)
-    hi0, lo0, r0 = check_rank(sad, oracle_mod, s, depth=depth)
-    monkeypatch.setenv("SAD_GEMM_PAIR", "1")
-    hi1, lo1, r1 = check_rank(sad, oracle_mod, s, depth=depth)
-    np.testing.assert_array_equal(hi0, hi1)
-    np.testing.assert_array_equal(lo0, lo1)
-    np.testing.assert_array_equal(r0, r1)
-
-
 def test_rank_identical_sequences_tie(sad, oracle_mod):
     s = datagen.from_strings(["ACDEFGHIKLMNPQ"] * 300 + ["WYWYWYWY"] * 10)
     hi, lo, _ = check_rank(sad, oracle_mod, s)

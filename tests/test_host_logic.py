@@ -337,8 +337,13 @@ def test_reference_arm_prints_the_contract_line(monkeypatch, capsys):
         assert key in d, key
     assert d["impl"] == "reference" and d["steps"] == 4 and d["warmup"] == 3
     assert d["value"] == 2.0e6 and d["higher_is_better"] is True
-    assert d["ms_per_step"] == pytest.approx(1e3 * (200 * 199 / 2) / 2.0e6)
+    # a step is the timed sample itself (here the stub's 120 s / 7 samples), not an
+    # extrapolation to the full set, so K steps fit in the run's wall time
+    assert d["ms_per_step"] == pytest.approx(1e3 * 120.0 / 7)
     assert d["config"]["workload"] == bench.WORKLOADS[1] and d["config"]["N"] == 200
+    # the GPU arm prints the same config dict for the same workload
+    from paper_0905_1744_gb300 import datagen
+    assert d["config"] == bench.bench_config(1, datagen.config(1, 0), 0)
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] == 4 and cb["value"] == d["value"]
     assert "sample" in cb

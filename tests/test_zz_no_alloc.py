@@ -26,7 +26,10 @@ def sad():
 
 
 def test_noalloc_matches_partition_twice(sad):
-    cases = [(20000, 16, None), (5000, 64, 40)]      # second call: smaller N, more buckets, ties
+    # second call: smaller N, more buckets, ties; then the documented maximum with
+    # few and with the most buckets (the scratch is sized for the largest accepted call)
+    cases = [(20000, 16, None), (5000, 64, 40), (sad.NOALLOC_MAX_N, 16, None),
+             (sad.NOALLOC_MAX_N, sad.NOALLOC_MAX_P, None), (sad.NOALLOC_MAX_N, 1, 100)]
     for n, p, distinct in cases:
         hi, lo = datagen.random_keys(n, seed=1000 + n, distinct=distinct)
         d_hi, d_lo = torch.from_numpy(hi).cuda(), torch.from_numpy(lo).cuda()
