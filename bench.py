@@ -679,7 +679,7 @@ def measure_config(cfg: int, args, dev, world: int, steps: int, warmup: int,
         "executed_tflops": exec_flops / (gemm_launch_ms / 1e3) / 1e12,
         "executed_frac": exec_flops / (gemm_launch_ms / 1e3) / 1e12 / f4_peak,
         "plan": {k: info[k] for k in ("k_eff", "k_pad", "t_max", "tiles", "k_chunks", "depth",
-                                      "residual_pairs", "residual_tiles")},
+                                      "rem_entries", "rem_blocks", "heavy_entries", "bm_cols")},
     }
 
     # each call of the step alone (a2 count: HBM-bound; a7-a10 partition: latency-bound)

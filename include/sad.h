@@ -34,7 +34,7 @@
 extern "C" {
 #endif
 
-#define SAD_ABI_VERSION 4
+#define SAD_ABI_VERSION 5
 
 typedef enum sad_status {
   SAD_OK = 0,
@@ -100,31 +100,45 @@ int kmer_count(const uint8_t *d_codes, const int64_t *d_offsets, int32_t n_seq,
                void *d_ws, size_t ws_bytes, void *stream);
 
 /*
- * Plan of a kmer_rank call. `depth` is chosen by the caller (an autotuner, or 0);
- * kmer_rank_plan fills in the rest from the counts.
- *   depth        threshold planes kept per word on the tensor cores; 0 keeps
- *                them all. With depth D >= 1 the pairs that share a word more
- *                than D times each get the exact remainder
- *                sum_word max(0, min(c_x, c_y) - D) from a sparse residual step,
- *                so the keys are identical for every depth.
+ * Plan of a kmer_rank call. `depth` and `budget` are chosen by the caller (an
+ * autotuner, or 0); kmer_rank_plan fills in the rest from the counts.
+ *   depth        threshold sections kept as planes on the tensor cores: 0 keeps
+ *                them all (no remainder); D >= 1 keeps min(D, 8). Each column
+ *                block of 128 stored rows then runs its tiles over its own first
+ *                d_J <= D sections (d_J: the smallest depth whose remainder fits
+ *                the budget), and every threshold of min(a, b) = sum_t [a >= t]
+ *                [b >= t] that those columns leave out is added back exactly in
+ *                the epilogue from per-row remainder lists, so the keys are
+ *                identical for every depth and budget.
+ *   budget       remainder entries per column block (0 = the default, 768).
  *   t_max        largest count of any word in any sequence.
- *   k_eff        threshold-plane columns at this depth.
- *   list_entries (sequence, word) entries with a count above depth.
- *   residual_pairs  pair contributions the residual step adds.
- *   k_cap, list_cap, block_cap  capacities kmer_rank lays the workspace out
- *                with (plane columns, residual entries, residual 128 x 128
- *                tiles); kmer_rank_plan sets them to what the data needs.
+ *   t_bits       largest threshold of the remainder bitmap, min(D + 4, 16);
+ *                counts above it are heavy entries, read from the counts.
+ *   k_eff        plane columns of the kept sections.
+ *   list_entries (sequence, word) entries counted twice or more.
+ *   rem_bound    remainder entries there can be: sum over those entries of
+ *                min(count, t_bits) - 1.
+ *   heavy_entries entries counted more than t_bits times.
+ *   k_cap, list_cap, rem_cap, heavy_cap, bm_cols  capacities kmer_rank lays
+ *                the workspace out with (plane columns, entries counted twice or
+ *                more, remainder entries, heavy entries, bitmap columns of
+ *                rows_total bits); kmer_rank_plan sets them to what the data needs.
  *   ws_bytes     workspace bytes kmer_rank needs with this plan.
  */
 typedef struct sad_rank_plan {
   int32_t depth;
+  int32_t budget;
   int32_t t_max;
+  int32_t t_bits;
   int64_t k_eff;
   int64_t list_entries;
-  int64_t residual_pairs;
+  int64_t rem_bound;
+  int64_t heavy_entries;
   int64_t k_cap;
   int64_t list_cap;
-  int64_t block_cap;
+  int64_t rem_cap;
+  int64_t heavy_cap;
+  int64_t bm_cols;
   size_t ws_bytes;
 } sad_rank_plan;
 
@@ -142,16 +156,21 @@ int kmer_rank_plan(const int32_t *d_counts, int32_t n_seq, int32_t k, int32_t al
 
 /*
  * kmer_rank_plan_bound - host only (no device access, no synchronisation): fills
- * `plan` (plan->depth >= 1 is the input) with capacities that hold for ANY counts
- * of n_seq sequences of total length total_len residues, so kmer_rank can run
- * right after kmer_count without the synchronous kmer_rank_plan. The bounds (the
- * threshold identity min(a, b) = sum_t [a >= t][b >= t], Sec. 3 Eq. 1):
- *   k_cap      = eps * depth rounded up to 256 (K_eff = sum_tau min(T_tau, depth)),
- *   list_cap   = (total_len - n_seq (k - 1)) / (depth + 1) (a sequence of m
- *                windows has at most m / (depth + 1) words counted more than
- *                depth times),
- *   block_cap  = every tile of the upper triangle (a residual block per tile).
- * t_max, k_eff, list_entries and residual_pairs are set to -1 (not known).
+ * `plan` (plan->depth >= 1 and plan->budget are the input) with capacities that
+ * hold for ANY counts of n_seq sequences of total length total_len residues, so
+ * kmer_rank can run right after kmer_count without the synchronous
+ * kmer_rank_plan. With W = total_len - n_seq (k - 1) windows, D = min(depth, 8)
+ * and T_b = min(D + 4, 16) (the threshold identity of Sec. 3 Eq. 1):
+ *   k_cap      = eps * D rounded up to 256 (K_eff = sum_tau min(T_tau, D)),
+ *   list_cap   = W / 2 (a sequence of m windows has at most m / 2 words counted
+ *                twice or more),
+ *   rem_cap    = W - n_seq (a sequence's counts c >= 2 add at most m - 1
+ *                thresholds above the first),
+ *   heavy_cap  = W / (T_b + 1),
+ *   bm_cols    = sum over t = 2..T_b of min(eps, W / t) (section t holds the
+ *                words some sequence counts t times).
+ * t_max, t_bits, k_eff, list_entries, rem_bound and heavy_entries are set to -1
+ * (not known).
  * Returns SAD_ERR_INVALID_ARGUMENT for depth < 1 (all planes need the word
  * maxima) or negative sizes, SAD_ERR_UNSUPPORTED for unsupported k / alphabet
  * or more than 32767 row blocks of 128 (n_seq > 4194176).

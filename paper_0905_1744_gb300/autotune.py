@@ -6,7 +6,7 @@ exactly by the sparse residual step, whose cost grows with the number of pairs
 of sequences that share a word more than D times. Which D is fastest depends on
 the set (its size, its repeat structure), so each candidate is timed on the
 device with CUDA events and the fastest kept. Results are cached per size class
-(log2 N, t_max, log2 of the residual pairs at depth 1) in memory and, if a path
+(log2 N, t_max, log2 of the remainder bound at depth 1) in memory and, if a path
 is given, in a JSON file.
 """
 from __future__ import annotations
@@ -31,7 +31,7 @@ def _bucket(x: int) -> int:
 
 
 def signature(n: int, plan1: "sad.RankPlan") -> str:
-    return f"n{_bucket(n)}_t{plan1.t_max}_r{_bucket(plan1.residual_pairs)}"
+    return f"n{_bucket(n)}_t{plan1.t_max}_r{_bucket(plan1.rem_bound)}"
 
 
 def load_cache(path: str | None):

@@ -36,15 +36,22 @@ int64_t eps_of(int32_t k, int32_t alphabet) {
 
 bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
+RankCaps planes_only(int64_t k_cap) { return RankCaps{0, 0, k_cap, 0, 0, 0, 0}; }
+
+RankCaps caps_of(const sad_rank_plan *plan) {
+  return RankCaps{plan->depth, plan->budget, plan->k_cap, plan->list_cap, plan->rem_cap,
+                  plan->heavy_cap, plan->bm_cols};
+}
+
 // Largest K_cap (multiple of kKCols) whose planes-only rank layout fits in ws_bytes.
 int64_t k_cap_for(const RankShape &sh, int64_t eps, size_t ws_bytes) {
-  const RankLayout base = rank_layout(sh, eps, RankCaps{0, 0, 0, 0});
+  const RankLayout base = rank_layout(sh, eps, planes_only(0));
   if (ws_bytes <= base.fixed_bytes) return 0;
   // upper bound (the layout only grows with K_cap), then step down until it fits
   // (two plane columns per byte)
   int64_t k = (int64_t)(2 * ((ws_bytes - base.fixed_bytes) / (size_t)sh.rows_total));
   k = k / kKCols * kKCols;
-  while (k > 0 && rank_layout(sh, eps, RankCaps{0, k, 0, 0}).bytes > ws_bytes) k -= kKCols;
+  while (k > 0 && rank_layout(sh, eps, planes_only(k)).bytes > ws_bytes) k -= kKCols;
   return k;
 }
 
@@ -156,10 +163,10 @@ size_t sad_workspace_bytes(int32_t op, int32_t n_seq, int32_t k, int32_t alphabe
     case SAD_OP_RANK: {
       if (eps < 0) return 0;
       const RankShape sh = shape_single(n_seq);
-      if (depth <= 0) return rank_layout(sh, eps, RankCaps{0, 0, 0, 0}).fixed_bytes;
+      if (depth <= 0) return rank_layout(sh, eps, planes_only(0)).fixed_bytes;
       const int64_t k_cap =
           (int64_t)align_up((size_t)eps * (size_t)depth, (size_t)kKCols);
-      return rank_layout(sh, eps, RankCaps{0, k_cap, 0, 0}).bytes;
+      return rank_layout(sh, eps, planes_only(k_cap)).bytes;
     }
     case SAD_OP_PARTITION:
       if (p < 1 || p > kMaxP) return 0;
@@ -192,7 +199,9 @@ namespace {
 int rank_plan_impl(const int32_t *d_counts, const RankShape &sh, const int32_t *d_n,
                    int64_t eps, int32_t k, sad_rank_plan *plan, void *d_ws, size_t ws_bytes,
                    cudaStream_t st) {
-  const RankLayout L0 = rank_layout(sh, eps, RankCaps{plan->depth, 0, 0, 0});
+  RankCaps c0 = planes_only(0);
+  c0.depth = plan->depth;
+  const RankLayout L0 = rank_layout(sh, eps, c0);
   if (ws_bytes < L0.fixed_bytes) {
     plan->ws_bytes = L0.fixed_bytes;
     return SAD_ERR_WORKSPACE;
@@ -211,18 +220,26 @@ int rank_plan_impl(const int32_t *d_counts, const RankShape &sh, const int32_t *
   }
   int64_t k_pad = (int64_t)align_up((size_t)h.k_eff, kKCols);
   if (k_pad < kKCols) k_pad = kKCols;
-  const bool residual = sh.n_total > 0 && h.depth < h.t_max;
+  const bool rem = plan->depth >= 1 && sh.n_total > 0;
   plan->t_max = h.t_max;
+  plan->t_bits = h.t_bits;
   plan->k_eff = h.k_eff;
   plan->list_entries = h.list_total;
-  plan->residual_pairs = h.pairs_total;
+  plan->rem_bound = h.rem_bound;
+  plan->heavy_entries = h.heavy_total;
   plan->k_cap = k_pad;
-  plan->list_cap = residual ? h.list_total : 0;
-  plan->block_cap =
-      residual ? (h.pairs_total < sh.tiles_total ? h.pairs_total : sh.tiles_total) : 0;
-  const RankCaps caps{plan->depth, plan->k_cap, plan->list_cap, plan->block_cap};
-  plan->ws_bytes = rank_layout(sh, eps, caps).bytes;
+  plan->list_cap = rem ? h.list_total : 0;
+  plan->rem_cap = rem ? h.rem_bound : 0;
+  plan->heavy_cap = rem ? h.heavy_total : 0;
+  plan->bm_cols = rem ? h.bm_cols : 0;
+  plan->ws_bytes = rank_layout(sh, eps, caps_of(plan)).bytes;
   return SAD_OK;
+}
+
+bool plan_valid(const sad_rank_plan *plan) {
+  return plan->depth >= 0 && plan->budget >= 0 && plan->k_cap >= kKCols &&
+         plan->k_cap % kKCols == 0 && plan->list_cap >= 0 && plan->rem_cap >= 0 &&
+         plan->heavy_cap >= 0 && plan->bm_cols >= 0;
 }
 
 int rank_run_impl(const int32_t *d_counts, const int32_t *d_lengths, const int32_t *word_max,
@@ -231,19 +248,19 @@ int rank_run_impl(const int32_t *d_counts, const int32_t *d_lengths, const int32
                   uint64_t *d_key_hi, uint64_t *d_key_lo, double *d_rank, void *d_ws,
                   size_t ws_bytes, cudaStream_t st) {
   if (sh.rows_total / kRowBlock > kMaxRowBlocks) return SAD_ERR_UNSUPPORTED;  // packed tile ids
-  RankCaps caps{0, 0, 0, 0};
+  RankCaps caps = planes_only(0);
   if (plan) {
-    if (plan->depth < 0 || plan->k_cap < kKCols || plan->k_cap % kKCols != 0 ||
-        plan->list_cap < 0 || plan->block_cap < 0)
-      return SAD_ERR_INVALID_ARGUMENT;
-    caps = RankCaps{plan->depth, plan->k_cap, plan->list_cap, plan->block_cap};
+    if (!plan_valid(plan)) return SAD_ERR_INVALID_ARGUMENT;
+    caps = caps_of(plan);
     if (rank_layout(sh, eps, caps).bytes > ws_bytes) return SAD_ERR_WORKSPACE;
   } else {
     caps.k_cap = k_cap_for(sh, eps, ws_bytes);
     if (caps.k_cap < kKCols) return SAD_ERR_WORKSPACE;
   }
   const RankLayout L = rank_layout(sh, eps, caps);
-  const RankPtrs P = rank_ptrs(d_ws, L);
+  RankPtrs P = rank_ptrs(d_ws, L);
+  P.eps = (int32_t)eps;
+  P.counts = d_counts;
   int rc = rank_prep_launch(P, d_counts, d_lengths, d_n, word_max, k, (int32_t)eps, 0, st);
   if (rc) return rc;
   rc = rank_gemm_launch(P, st);
@@ -297,22 +314,26 @@ int kmer_rank_plan_bound(int32_t n_seq, int64_t total_len, int32_t k, int32_t al
   if (n_seq < 0 || total_len < 0 || !plan || plan->depth < 1) return SAD_ERR_INVALID_ARGUMENT;
   const RankShape sh = shape_single(n_seq);
   if (sh.rows_total / kRowBlock > kMaxRowBlocks) return SAD_ERR_UNSUPPORTED;
-  const int64_t d = plan->depth;
-  // K_eff = sum over words of min(T, d) <= eps d; a sequence has at most m / (d + 1)
-  // words counted more than d times, and sum m = total_len - n (k - 1)
+  const int64_t d = plan->depth < kMaxPlaneDepth ? plan->depth : kMaxPlaneDepth;
+  const int64_t tb = t_bits_of((int32_t)d);
+  // K_eff = sum over words of min(T, d) <= eps d
   int64_t k_cap = (int64_t)align_up((size_t)(eps * d), kKCols);
   if (k_cap < kKCols) k_cap = kKCols;
   const int64_t windows = total_len - (int64_t)n_seq * (k - 1);
+  int64_t bm = 0;
+  for (int64_t t = 2; t <= tb && windows > 0; ++t) bm += windows / t < eps ? windows / t : eps;
   plan->t_max = -1;
+  plan->t_bits = -1;
   plan->k_eff = -1;
   plan->list_entries = -1;
-  plan->residual_pairs = -1;
+  plan->rem_bound = -1;
+  plan->heavy_entries = -1;
   plan->k_cap = k_cap;
-  plan->list_cap = windows > 0 ? windows / (d + 1) : 0;
-  plan->block_cap = sh.tiles_total;  // a block per tile: the identity block map
-  plan->ws_bytes =
-      rank_layout(sh, eps, RankCaps{plan->depth, plan->k_cap, plan->list_cap, plan->block_cap})
-          .bytes;
+  plan->list_cap = windows > 0 ? windows / 2 : 0;
+  plan->rem_cap = windows > n_seq ? windows - n_seq : 0;
+  plan->heavy_cap = windows > 0 ? windows / (tb + 1) : 0;
+  plan->bm_cols = bm;
+  plan->ws_bytes = rank_layout(sh, eps, caps_of(plan)).bytes;
   return SAD_OK;
 }
 
@@ -377,8 +398,7 @@ size_t kmer_rank_dist_workspace_bytes(const sad_rank_plan *plan, int32_t n_seq, 
                                       int32_t alphabet, int32_t delta_den) {
   const int64_t eps = eps_of(k, alphabet);
   if (eps < 0 || !plan || n_seq < 1 || delta_den < 1 || delta_den > 1024) return 0;
-  const RankCaps caps{plan->depth, plan->k_cap, plan->list_cap, plan->block_cap};
-  const size_t base = rank_layout(shape_single(n_seq), eps, caps).bytes;
+  const size_t base = rank_layout(shape_single(n_seq), eps, caps_of(plan)).bytes;
   return align_up(base, 256) + sizeof(int64_t) * ln_table_entries(delta_den);
 }
 
@@ -392,19 +412,18 @@ int kmer_rank_dist(const int32_t *d_counts, const int32_t *d_lengths, const int3
   if (n_seq < 1 || !plan || !d_counts || !d_lengths || !d_key_hi || !d_key_lo || !d_ws ||
       !aligned(d_ws, 256) || delta_den < 1 || delta_den > 1024)
     return SAD_ERR_INVALID_ARGUMENT;
-  if (plan->depth < 0 || plan->k_cap < kKCols || plan->k_cap % kKCols != 0 ||
-      plan->list_cap < 0 || plan->block_cap < 0)
-    return SAD_ERR_INVALID_ARGUMENT;
+  if (!plan_valid(plan)) return SAD_ERR_INVALID_ARGUMENT;
   const RankShape sh = shape_single(n_seq);
   if (sh.rows_total / kRowBlock > kMaxRowBlocks) return SAD_ERR_UNSUPPORTED;
-  const RankCaps caps{plan->depth, plan->k_cap, plan->list_cap, plan->block_cap};
-  const RankLayout L = rank_layout(sh, eps, caps);
+  const RankLayout L = rank_layout(sh, eps, caps_of(plan));
   const size_t table_off = align_up(L.bytes, 256);
   if (table_off + sizeof(int64_t) * ln_table_entries(delta_den) > ws_bytes)
     return SAD_ERR_WORKSPACE;
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   int64_t *table = reinterpret_cast<int64_t *>(static_cast<uint8_t *>(d_ws) + table_off);
-  const RankPtrs P = rank_ptrs(d_ws, L);
+  RankPtrs P = rank_ptrs(d_ws, L);
+  P.eps = (int32_t)eps;
+  P.counts = d_counts;
   int rc = ln_table_launch(table, delta_den, st);
   if (rc) return rc;
   rc = rank_prep_launch(P, d_counts, d_lengths, nullptr, d_word_max, k, (int32_t)eps, 0, st);
@@ -547,8 +566,10 @@ int sad_rank_info(void *d_ws, int64_t *info, void *stream) {
   info[4] = h.n_tiles;
   info[5] = (int64_t)h.k_chunks;
   info[6] = h.depth;
-  info[7] = h.pairs_total;
-  info[8] = h.n_blocks;
+  info[7] = h.rem_entries;
+  info[8] = h.rem_blocks;
+  info[9] = h.heavy_entries;
+  info[10] = h.bm_cols;
   return SAD_OK;
 }
 

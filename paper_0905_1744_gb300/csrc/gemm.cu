@@ -19,9 +19,17 @@
 // or one signed 64-bit value (distance form), by red.global.add.u64; a last
 // kernel folds them into the key.
 //
-// When the planes are cut at a depth D, the residual sum_tau max(0, min(c_i, c_j) - D)
-// of each pair arrives as a dense 128 x 128 u16 block per tile and is added to S
-// before the floor, so the key is the same as with all planes.
+// When the planes are cut (plans of depth >= 1), the tile's column block J lists
+// per column v the threshold columns (tau, t) that v counts but that the tile's K
+// chunks do not cover (its remainder entries, see rank_prep.cu). They are added on
+// the tensor cores as extra K chunks of the tile: entry e becomes K column e of
+// a chunk whose A row u holds [c_u(tau_e) >= t_e] (the remainder bitmap's bit of
+// row u) and whose B row v holds [e is an entry of column v], so the MMA adds
+// sum over v's entries of [c_u(tau) >= t] to S_uv. Two builder warps write these
+// chunks into the operand ring (the 128-byte-swizzled K-major layout TMA writes)
+// in place of a TMA copy. Counts above the bitmap's thresholds (heavy entries,
+// rare) add min(c_u, c) - T_b in the epilogue from the counts. The key is the same
+// as with all planes.
 //
 // Persistent kernel, one CTA per SM, 12 warps:
 //   warp 0      TMA producer: per stage two K chunks of 256 plane columns (128 B)
@@ -31,7 +39,7 @@
 //               mostly fixed, so fewer, larger stages run faster)
 //   warp 1      MMA issuer: 8 x (M=128, N=128, K=64) per stage into one of two
 //               TMEM accumulators (2 x 128 columns), commit frees the stage
-//   warp 2      TMEM allocator
+//   warp 2      TMEM allocator, then with warp 3 the remainder builder
 //   warps 4-7   also fill the scale-factor columns of TMEM with 1.0 before the
 //               first MMA
 //   warps 4-11  epilogue: tcgen05.ld of the accumulator (lane quadrant = warp % 4,
@@ -68,6 +76,12 @@ constexpr uint32_t kSfbCol = kSfaCol + 32;
 constexpr uint32_t kSfCols = 64;  // filled with 1.0
 static_assert(kSfaCol + kSfCols <= kTmemCols, "TMEM columns");
 constexpr int kHalfCols = kColBlock / 2;  // columns of one epilogue warp
+// remainder entries of a column block staged in shared memory by the builder
+// (larger lists are read from global memory)
+constexpr int kRemStage = 832;
+static_assert(kRemBudgetDefault <= kRemStage, "the default budget fits the staging");
+constexpr int kRemChunk = 2 * kKChunk;  // remainder entries per extra K chunk (one per column)
+constexpr int kBuildThreads = 64;       // warps 2-3
 // budget of the drain waits after an abort (the copies and MMAs in flight finish
 // in microseconds)
 constexpr uint64_t kDrainBudgetNs = 2000000000ull;
@@ -82,8 +96,15 @@ struct GemmSmem {
   // second column half's row sums (Rlo, Rc), added once per tile
   uint2 colpart[2][4][kColBlock];
   uint4 rowpart[2][kRowBlock];
+  // the builder's tile: first remainder entry of each column (relative to its
+  // column block) and, when the block's list fits, the bitmap slice (4 words: bits
+  // of the tile's 128 rows) of each entry
+  int32_t remoff[kColBlock + 1];
+  uint4 remsl[kRemStage];
+  uint32_t nib[256];  // byte b -> eight 4-bit values, 1.0 (e2m1) where b has a 1 bit
   uint64_t full[kStages];
   uint64_t empty[kStages];
+  uint64_t bfree[kStages];  // the producer hands a free slot to the builder
   uint64_t tfull[2];
   uint64_t tempty[2];
   uint64_t drain;
@@ -94,6 +115,7 @@ struct GemmSmem {
 };
 
 constexpr size_t kGemmSmemBytes = sizeof(GemmSmem) + 1024;
+static_assert(kGemmSmemBytes <= 232448, "227 KB of shared memory per CTA");
 
 __device__ __forceinline__ void red_add_u64(unsigned long long *p, unsigned long long v) {
   asm volatile("red.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
@@ -130,31 +152,134 @@ __device__ __forceinline__ void set_abort(GemmSmem &S, WsHeader *hdr) {
   record_error(hdr, SAD_ERR_TIMEOUT, (int)blockIdx.x);
 }
 
-// Tile t of a launch: (row block I, column block J, K chunks). Square mode: the
-// upper-triangle list of the rank. Rectangular mode (every stored row against the
-// reference rows, RectArgs): all R x C blocks, column block major.
+// Tile t of a launch: (row block I, column block J, plane K chunks nk, remainder
+// K chunks nx). Square mode: the upper-triangle list of the rank. Rectangular mode
+// (every stored row against the reference rows, RectArgs): all R x C blocks,
+// column block major, no remainder.
 __device__ __forceinline__ void tile_at(const RankPtrs &P, const RectArgs &X, int32_t rect_nk,
-                                        int32_t t, int32_t &I, int32_t &J, int32_t &nk) {
+                                        int32_t t, int32_t &I, int32_t &J, int32_t &nk,
+                                        int32_t &nx) {
   if (X.rec_ref) {
     I = t % X.row_blocks;
     J = t / X.row_blocks;
     nk = rect_nk;
+    nx = 0;
   } else {
     const int2 tl = P.tiles[t];
     I = tl.x & 0xFFFF;
     J = tl.x >> 16;
-    nk = tl.y;
+    nk = tl.y & 0xFFFF;
+    nx = (int32_t)((uint32_t)tl.y >> 16);
   }
+}
+
+// Stages of a tile: its plane chunks, then its remainder chunks, kCps to a stage.
+__device__ __forceinline__ int32_t stages_of(int32_t nk, int32_t nx) {
+  return (nk + kCps - 1) / kCps + (nx + kCps - 1) / kCps;
+}
+
+// 32 x 32 bit transpose across a warp: lane l holds row l (bit b = column b); on
+// return lane u holds column u (bit l = row l). Recursive swap of the off-diagonal
+// blocks of 16, 8, 4, 2 and 1.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, uint32_t lane) {
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const uint32_t m = s == 16 ? 0x0000FFFFu
+                     : s == 8  ? 0x00FF00FFu
+                     : s == 4  ? 0x0F0F0F0Fu
+                     : s == 2  ? 0x33333333u
+                               : 0x55555555u;
+    const uint32_t y = __shfl_xor_sync(0xffffffffu, x, s);
+    x = (lane & (uint32_t)s) ? ((x & ~m) | ((y >> s) & m)) : ((x & m) | ((y << s) & ~m));
+  }
+  return x;
+}
+
+// Bits [a, b) of a 32-bit word (clipped to [0, 32)).
+__device__ __forceinline__ uint32_t bit_range(int32_t a, int32_t b) {
+  a = max(a, 0);
+  b = min(b, 32);
+  if (a >= b) return 0u;
+  const uint32_t hi = b >= 32 ? 0xFFFFFFFFu : ((1u << b) - 1u);
+  const uint32_t lo = a <= 0 ? 0u : ((1u << a) - 1u);
+  return hi & ~lo;
+}
+
+// One remainder K chunk x (entries [256 x, 256 x + 256) of the column block's list,
+// rn entries in all) into the operand tiles a (128 rows u of the tile) and b (128
+// rows v = tile columns), 128 bytes a row, 16-byte unit j of row r at unit j ^ (r & 7)
+// (the 128-byte swizzle). A unit holds 32 entries of one row as 4-bit values. Row u
+// of a: the bitmap bits of the tile's rows, transposed 32 x 32 at a time per warp;
+// row v of b: 1.0 for the entries of column v (a contiguous range).
+__device__ __forceinline__ void build_chunk(const RankPtrs &P, const GemmSmem &S, uint8_t *a,
+                                            uint8_t *b, int32_t x, int32_t rn, bool staged,
+                                            int64_t rbase, int64_t bm_stride, int32_t I,
+                                            uint32_t bt, uint32_t lane) {
+  const uint32_t bw = bt >> 5;
+  // a: 4 lane quadrants q x 8 units j; builder warp bw takes the units j = 2 i + bw
+  // of every quadrant (16 items), all of whose words are loaded before any is used
+  uint32_t w[16];
+  if (staged) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int32_t e = x * kRemChunk + (int32_t)((2 * i + bw) * 32 + lane);
+        w[4 * i + q] = e < rn ? (&S.remsl[e].x)[q] : 0u;
+      }
+  } else {
+    uint32_t col[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int32_t e = x * kRemChunk + (int32_t)((2 * i + bw) * 32 + lane);
+      col[i] = e < rn ? __ldg(P.rem + rbase + e) : 0xFFFFFFFFu;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        w[4 * i + q] = col[i] != 0xFFFFFFFFu
+                           ? __ldg(P.bitmap + (int64_t)col[i] * bm_stride + (int64_t)I * 4 + q)
+                           : 0u;
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const uint32_t j = 2 * i + bw;
+#pragma unroll
+    for (uint32_t q = 0; q < 4; ++q) {
+      const uint32_t m = warp_transpose32(w[4 * i + q], lane);  // bit l: entry 32 j + l
+      const uint32_t r = q * 32 + lane;                         // of row 32 q + lane
+      *reinterpret_cast<uint4 *>(a + r * 128 + ((j ^ (r & 7)) * 16)) =
+          make_uint4(S.nib[m & 0xFF], S.nib[(m >> 8) & 0xFF], S.nib[(m >> 16) & 0xFF],
+                     S.nib[m >> 24]);
+    }
+  }
+  // b: rows v, two per builder thread
+#pragma unroll 1
+  for (uint32_t v = bt; v < (uint32_t)kColBlock; v += kBuildThreads) {
+    const int32_t lo = S.remoff[v] - x * kRemChunk, hi = S.remoff[v + 1] - x * kRemChunk;
+#pragma unroll
+    for (uint32_t j = 0; j < 8; ++j) {
+      const uint32_t m = bit_range(lo - (int32_t)(32 * j), hi - (int32_t)(32 * j));
+      *reinterpret_cast<uint4 *>(b + v * 128 + ((j ^ (v & 7)) * 16)) =
+          make_uint4(S.nib[m & 0xFF], S.nib[(m >> 8) & 0xFF], S.nib[(m >> 16) & 0xFF],
+                     S.nib[m >> 24]);
+    }
+  }
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 // Square similarity epilogue over 16 columns of this lane's accumulator row.
 // colrec holds (Qlo, Qhi, Wlo, Whi) per column: Q = floor((2^64 - 1) / d) and the
 // floor weight W of d = m_j, so term = s Q + floor(s W / 2^63) with s = S + the
-// residual. The row keeps sum s Qlo, sum s Qhi (each below 2^54 over 64 columns)
+// remainder r of the column. The row keeps sum s Qlo, sum s Qhi (each below 2^54 over 64 columns)
 // and the sum of the floors; cs, cq get what the columns add (s and the floor).
 // On a diagonal tile the row takes j >= i only and the columns j > i only.
 template <bool kDiag>
-__device__ __forceinline__ void f_block16(const uint32_t (&v)[16], const uint32_t (&rw)[8],
+__device__ __forceinline__ void f_block16(const uint32_t (&v)[16], const uint32_t (&rr)[16],
                                           const uint4 *colrec, int64_t row_pos, int64_t jpos0,
                                           uint64_t &sql, uint64_t &sqh, uint32_t &qsum,
                                           uint32_t (&cs)[16], uint32_t (&cq)[16]) {
@@ -163,7 +288,7 @@ __device__ __forceinline__ void f_block16(const uint32_t (&v)[16], const uint32_
     const uint4 rec = colrec[cc];
     // the accumulator is an integer below 2^16: + 2^23 puts it in the low mantissa bits
     const uint32_t sv = __float_as_uint(__fadd_rn(__uint_as_float(v[cc]), 8388608.0f)) - 0x4B000000u;
-    const uint32_t s = sv + ((cc & 1) ? (rw[cc >> 1] >> 16) : (rw[cc >> 1] & 0xFFFFu));
+    const uint32_t s = sv + rr[cc];
     const uint32_t q = (uint32_t)(((uint64_t)s * rec.w + __umulhi(s, rec.z)) >> 31);
     uint32_t sr = s, qr = q, sc = s, qc = q;
     if constexpr (kDiag) {
@@ -176,6 +301,30 @@ __device__ __forceinline__ void f_block16(const uint32_t (&v)[16], const uint32_
     qsum += qr;
     cs[cc] = sc;
     cq[cc] = qc;
+  }
+}
+
+// Heavy remainder of S for this lane's row and the 16 tile columns c0..c0 + 15:
+// for each heavy entry (tau, c) of column v, max(0, min(c_u(tau), c) - T_b) from
+// the counts (the thresholds up to T_b come through the remainder chunks).
+__device__ __forceinline__ void tile_heavy(const RankPtrs &P, int32_t hn, int64_t hbase,
+                                           int32_t row_x, int32_t tbits, int32_t J, int c0,
+                                           uint32_t (&rr)[16]) {
+#pragma unroll
+  for (int cc = 0; cc < 16; ++cc) rr[cc] = 0;
+  if (hn > 0) {
+    const int64_t v0 = (int64_t)J * kColBlock + c0;
+#pragma unroll
+    for (int cc = 0; cc < 16; ++cc) {
+      const int32_t h0 = P.rowrem[2 * (v0 + cc) + 1];
+      const int32_t h1 = (c0 + cc + 1 < kColBlock) ? P.rowrem[2 * (v0 + cc + 1) + 1] : hn;
+      for (int32_t h = h0; h < h1; ++h) {
+        const int2 e = __ldg(P.heavy + hbase + h);
+        const int32_t cu = row_x >= 0 ? __ldg(P.counts + (int64_t)row_x * P.eps + e.x) : 0;
+        const int32_t x = min(cu, e.y) - tbits;
+        rr[cc] += x > 0 ? (uint32_t)x : 0u;
+      }
+    }
   }
 }
 
@@ -199,6 +348,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&S.full[s], 1);
       mbar_init(&S.empty[s], 1);
+      mbar_init(&S.bfree[s], 1);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&S.tfull[a], 1);
@@ -236,9 +386,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int32_t n_tiles = skip ? 0 : (rect ? X.n_tiles : P.hdr->n_tiles);
   // rectangular mode: every tile runs all K_pad columns the rank preparation wrote
   const int32_t rect_nk = (rect && !skip) ? max(1, P.hdr->k_pad / kKCols) : 0;
-  // counts above the plane depth come in as dense per-tile residual blocks
-  const bool residual =
-      !skip && P.depth_cap >= 1 && P.block_cap > 0 && P.hdr->depth < P.hdr->t_max;
+  // counts the planes of a tile do not cover come from the remainder lists
+  const bool residual = !skip && !rect && P.depth_cap >= 1;
+  const int64_t bm_stride = P.n_pad / 32;
+  const int32_t tbits = t_bits_of(min(P.depth_cap, kMaxPlaneDepth));
 
   if (!skip && warp == 0 && lane == 0) {
     // ------------------------------------------------------------ producer --
@@ -246,13 +397,24 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t phase = 0, used = 0, par = 0;
     bool aborted = false;
     for (int32_t t = blockIdx.x; t < n_tiles && !aborted; t += gridDim.x) {
-      int32_t I, J, nk;
-      tile_at(P, X, rect_nk, t, I, J, nk);
-      for (int32_t kc = 0; kc < (nk + kCps - 1) / kCps; ++kc) {
+      int32_t I, J, nk, nx;
+      tile_at(P, X, rect_nk, t, I, J, nk, nx);
+      const int32_t sk = (nk + kCps - 1) / kCps;
+      for (int32_t kc = 0; kc < sk + (nx + kCps - 1) / kCps; ++kc) {
         if (!mbar_wait_bounded(&S.empty[stage], phase ^ 1u, abort_flag, wait_ns)) {
           set_abort(S, P.hdr);
           aborted = true;
           break;
+        }
+        if (kc >= sk) {
+          // a remainder stage: the slot is free; the builder fills it and arrives on
+          // its full barrier (slots are handed over in order, one round at a time)
+          mbar_arrive(&S.bfree[stage]);
+          if (++stage == kStages) {
+            stage = 0;
+            phase ^= 1u;
+          }
+          continue;
         }
         mbar_arrive_expect_tx(&S.full[stage], kTxBytes);
         tma_load_3d(S.a[stage], &tmA, &S.full[stage], 0, I * kRowBlock, kc * kCps);
@@ -278,8 +440,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     bool aborted = false;
     int32_t lt = 0;
     for (int32_t t = blockIdx.x; t < n_tiles && !aborted; t += gridDim.x, ++lt) {
-      int32_t I, J, nk;
-      tile_at(P, X, rect_nk, t, I, J, nk);
+      int32_t I, J, nk, nx;
+      tile_at(P, X, rect_nk, t, I, J, nk, nx);
+      const int32_t sk = (nk + kCps - 1) / kCps;
       const uint32_t acc = lt & 1, aph = (lt >> 1) & 1;
       if (!mbar_wait_bounded(&S.tempty[acc], aph ^ 1u, abort_flag, wait_ns)) {
         set_abort(S, P.hdr);
@@ -288,7 +451,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       tc_fence_after();
       const uint32_t d_tmem = tmem + acc * (uint32_t)kColBlock;
-      for (int32_t kc = 0; kc < (nk + kCps - 1) / kCps; ++kc) {
+      for (int32_t kc = 0; kc < stages_of(nk, nx); ++kc) {
         if (!mbar_wait_bounded(&S.full[stage], phase, abort_flag, wait_ns)) {
           set_abort(S, P.hdr);
           aborted = true;
@@ -296,8 +459,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         tc_fence_after();
         // per K chunk 4 MMAs of K = 64 values = 32 bytes per row (2 in 16-byte
-        // descriptor units); a last chunk past the tile's extent is not used
-        const int nsub = min(kCps, nk - kc * kCps);
+        // descriptor units); a last chunk past the tile's extent (plane or
+        // remainder) is not used
+        const int nsub = kc < sk ? min(kCps, nk - kc * kCps) : min(kCps, nx - (kc - sk) * kCps);
         for (int sub = 0; sub < nsub; ++sub) {
           const uint64_t adesc = sdesc_kmajor_sw128(smem_u32(S.a[stage] + sub * kSubA));
           const uint64_t bdesc = sdesc_kmajor_sw128(smem_u32(S.b[stage] + sub * kSubB));
@@ -319,6 +483,64 @@ __global__ void __launch_bounds__(kThreads, 1)
     // abort, and also when an epilogue gave up after this loop ended normally)
     mma_commit(&S.drain);
     mbar_wait_bounded(&S.drain, 0, &S.never, kDrainBudgetNs);
+  } else if (!skip && (warp == 2 || warp == 3)) {
+    // -------------------------------------------------------- remainder builder --
+    // Walks the same stage sequence as the producer; each remainder stage of a tile
+    // is handed over by the producer (bfree, after the slot's previous contents were
+    // consumed), written here and released to the MMA on the slot's full barrier.
+    // The hand-overs of one slot complete in order, so their parity is tracked per
+    // slot (bpar); no copy in flight ever leaves this role.
+    const uint32_t bt = threadIdx.x - 64;
+    for (uint32_t i = bt; i < 256; i += kBuildThreads) {
+      uint32_t v = 0;
+      for (int k = 0; k < 8; ++k) v |= ((i >> k) & 1u) * (kE2M1One << (4 * k));
+      S.nib[i] = v;
+    }
+    named_bar_sync(3, kBuildThreads);
+    int stage = 0;
+    uint32_t bpar = 0;
+    bool aborted = false;
+    for (int32_t t = blockIdx.x; t < n_tiles && !aborted; t += gridDim.x) {
+      int32_t I, J, nk, nx;
+      tile_at(P, X, rect_nk, t, I, J, nk, nx);
+      const int32_t sk = (nk + kCps - 1) / kCps;
+      stage = (stage + sk) % kStages;
+      if (nx == 0) continue;
+      const int64_t rbase = P.blkrem[2 * J];
+      const int32_t rn = (int32_t)(P.blkrem[2 * J + 2] - rbase);
+      const bool staged = rn <= kRemStage;
+      // the column offsets and (when they fit) the entries' bitmap slices of row block I
+      for (int c = (int)bt; c <= kColBlock; c += kBuildThreads)
+        S.remoff[c] = c < kColBlock ? P.rowrem[2 * ((int64_t)J * kColBlock + c)] : rn;
+      if (staged)
+        for (int e = (int)bt; e < rn; e += kBuildThreads)
+          S.remsl[e] = __ldg(reinterpret_cast<const uint4 *>(
+              P.bitmap + (int64_t)__ldg(P.rem + rbase + e) * bm_stride + (int64_t)I * 4));
+      named_bar_sync(3, kBuildThreads);
+      for (int32_t xs = 0; xs < (nx + kCps - 1) / kCps; ++xs) {
+        bool ok = true;
+        if (bt == 0) {
+          ok = mbar_wait_bounded(&S.bfree[stage], (bpar >> stage) & 1u, abort_flag, wait_ns);
+          if (!ok) set_abort(S, P.hdr);
+        }
+        bpar ^= 1u << stage;
+        if (named_bar_sync_or(3, kBuildThreads, !ok || *abort_flag != 0)) {
+          aborted = true;
+          break;
+        }
+        const int nsub = min(kCps, nx - xs * kCps);
+        for (int sub = 0; sub < nsub; ++sub)
+          build_chunk(P, S, S.a[stage] + sub * kSubA, S.b[stage] + sub * kSubB, xs * kCps + sub,
+                      rn, staged, rbase, bm_stride, I, bt, lane);
+        // the tensor cores read the stage through the async proxy
+        fence_proxy_async_smem();
+        named_bar_sync(3, kBuildThreads);
+        if (bt == 0) mbar_arrive(&S.full[stage]);
+        if (++stage == kStages) stage = 0;
+      }
+      // the next tile's staging overwrites remoff and remsl
+      named_bar_sync(3, kBuildThreads);
+    }
   } else if (!skip && warp >= 4 && warp < 12) {
     // ------------------------------------------------------------ epilogue --
     // warp w reads TMEM lanes 32 (w % 4).. (its quadrant) and tile columns
@@ -328,9 +550,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t etid = threadIdx.x - 128;
     int32_t lt = 0;
     for (int32_t t = blockIdx.x; t < n_tiles; t += gridDim.x, ++lt) {
-      int32_t I, J, nk;
-      tile_at(P, X, rect_nk, t, I, J, nk);
-      const int32_t tile = t;
+      int32_t I, J, nk, nx;
+      tile_at(P, X, rect_nk, t, I, J, nk, nx);
       const bool tile_ok = true;
       const int buf = lt & 1;
       for (uint32_t c = etid; c < (uint32_t)kColBlock; c += kEpiThreads) {
@@ -349,19 +570,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t row_pos = (int64_t)I * kRowBlock + q * 32 + lane;
       const int32_t row_orig = tile_ok ? P.perm[row_pos] : -1;
       const bool diag = (int64_t)I * kRowBlock + kRowBlock - 1 >= (int64_t)J * kColBlock;
-      const int32_t rblk = (residual && tile_ok) ? P.block_of[tile] : -1;
-      // this row's residual words (two u16 per word), 16 columns = 2 uint4 per sub-chunk
-      const uint4 *rrow =
-          rblk >= 0 ? reinterpret_cast<const uint4 *>(
-                          P.rblocks + (int64_t)rblk * (kResidualBlockBytes / 4) +
-                          (q * 32 + lane) * (kColBlock / 2)) +
-                          half * (kHalfCols / 8)
-                    : nullptr;
-      uint4 ra = make_uint4(0, 0, 0, 0), rb = make_uint4(0, 0, 0, 0);
-      if (rrow) {
-        ra = __ldg(rrow + 0);
-        rb = __ldg(rrow + 1);
+      // heavy remainder entries [hbase, hbase + hn) of the column block, grouped by
+      // column; they read this row's count of their word
+      int64_t hbase = 0;
+      int32_t hn = 0;
+      if (residual) {
+        hbase = P.blkrem[2 * J + 1];
+        hn = (int32_t)(P.blkrem[2 * J + 3] - hbase);
       }
+      const int32_t row_x = hn > 0 ? P.perm[row_pos] : -1;
       const uint32_t acc = lt & 1, aph = (lt >> 1) & 1;
       const bool got = mbar_wait_bounded(&S.tfull[acc], aph, abort_flag, wait_ns);
       if (!got) set_abort(S, P.hdr);
@@ -411,17 +628,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           uint32_t v[16];
           tmem_ld_32x32b_x16(tmem + ((q * 32u) << 16) + acc * (uint32_t)kColBlock + (uint32_t)c0,
                              v);
-          const uint32_t rw[8] = {ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
-          if (rrow && sc + 1 < kHalfCols / 16) {
-            ra = __ldg(rrow + 2 * (sc + 1));
-            rb = __ldg(rrow + 2 * (sc + 1) + 1);
-          }
+          uint32_t rr[16];
+          tile_heavy(P, hn, hbase, row_x, tbits, J, c0, rr);
           tmem_ld_wait();
           int64_t tv[16];
 #pragma unroll
           for (int cc = 0; cc < 16; ++cc) {
-            const uint32_t s = __float2uint_rn(__uint_as_float(v[cc])) +
-                               ((rw[cc >> 1] >> (16 * (cc & 1))) & 0xFFFFu);
+            const uint32_t s = __float2uint_rn(__uint_as_float(v[cc])) + rr[cc];
             const uint32_t d = S.colrec[buf][c0 + cc].w & 0xFFFFu;
             tv[cc] = __ldg(Z.ln_table + (d + (uint32_t)Z.b * s));
           }
@@ -492,18 +705,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint32_t v[16];
         tmem_ld_32x32b_x16(tmem + ((q * 32u) << 16) + acc * (uint32_t)kColBlock + (uint32_t)c0,
                            v);
-        const uint32_t rw[8] = {ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
-        if (rrow && sc + 1 < kHalfCols / 16) {  // next sub-chunk's residual words
-          ra = __ldg(rrow + 2 * (sc + 1));
-          rb = __ldg(rrow + 2 * (sc + 1) + 1);
-        }
+        uint32_t rr[16];
+        tile_heavy(P, hn, hbase, row_x, tbits, J, c0, rr);
         tmem_ld_wait();
         uint32_t cs[16], cq[16];
         if (diag)
-          f_block16<true>(v, rw, &S.colrec[buf][c0], row_pos, (int64_t)J * kColBlock + c0, sql,
+          f_block16<true>(v, rr, &S.colrec[buf][c0], row_pos, (int64_t)J * kColBlock + c0, sql,
                           sqh, qsum, cs, cq);
         else
-          f_block16<false>(v, rw, &S.colrec[buf][c0], row_pos, 0, sql, sqh, qsum, cs, cq);
+          f_block16<false>(v, rr, &S.colrec[buf][c0], row_pos, 0, sql, sqh, qsum, cs, cq);
         // column sums over the warp's 32 rows: one warp-wide reduction per column
         uint32_t mcs = 0, mcq = 0;
 #pragma unroll

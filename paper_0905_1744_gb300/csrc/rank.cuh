@@ -48,33 +48,35 @@ struct RankPtrs {
   int32_t *T;            // [eps] largest count of each word over all sets
   int32_t *secend;       // [t_max + 1] end column of threshold section t
   int32_t *colmap;       // [K_cap] column -> word | threshold << 16
+  int8_t *dstar;         // [K_cap] smallest plane depth d whose tiles cover the column
   int32_t *thist;        // [65537] histogram / cursor over T values
   int32_t *coltab;       // [kTabDepth][eps] column of (threshold t, word), -1 = none
-  int32_t *promcol;      // [eps] plane column of a word's threshold depth + 1, -1 = none
-  int64_t *weight;       // [eps] residual weight of a word: sum over sets of cnt_gt^2
   int32_t *mhist;        // [65537] histogram / cursor over m = L - k + 1 (one set)
   int32_t *perm;         // [rows_total] stored row -> input index (-1 = padding)
   int32_t *depth;        // [rows_total / 128] largest count in each 128-row block
+  int32_t *bdepth;       // [rows_total / 128] plane depth of each column block (remainder)
   uint4 *rec;            // [rows_total] division record of each stored row's m
   uint2 *recw;           // [rows_total] floor_weight of each stored row's m
   int2 *tiles;           // [tiles_total] (I | J << 16, K chunks), global block indices
   unsigned long long *acc;  // [n_total][3] key = acc0 + acc1 2^32 (distance mode: acc0)
-  uint8_t *planes;       // [rows_total][K_cap / 2] packed e2m1 threshold planes (sections 1..depth)
-  // residual of the counts above the plane depth, per (set, word)
-  int32_t *cnt_gt;       // [n_sets * eps] sequences whose count of the word exceeds depth
-  int64_t *list_off;     // [n_sets * eps + 1] start of each excess list
-  int64_t *item_off;     // [n_sets * eps + 1] start of each list's work items
-  int32_t *cursor;       // [n_sets * eps] fill cursor of the excess lists
-  int2 *lists;           // [list_cap] (stored row, count - depth), grouped by (set, word)
-  int2 *flat;            // [list_cap] (stored row, word | (count - depth) << 16), unordered
-  int32_t *tile_of;      // [tileof_total] tile index of set-local block (I, J)
-  int32_t *block_of;     // [tiles_total] residual block of a tile, -1 = none
-  uint32_t *rblocks;     // [block_cap][128][128] u16 residual per pair (two per word)
+  uint8_t *planes;       // [rows_total][K_cap / 2] packed e2m1 threshold planes
+  // remainder of the counts the planes of a tile do not cover (depth >= 1)
+  uint32_t *prof;        // [rows_total][kProf] per-row remainder profile
+  int32_t *rowrem;       // [rows_total][2] first remainder / heavy entry of the row in its block
+  int64_t *blkrem;       // [blocks + 1][2] first remainder / heavy entry of each block
+  int32_t *cursor;       // [rows_total][2] fill cursors
+  int2 *flat;            // [list_cap] (stored row, word | count << 16), count >= 2, unordered
+  uint32_t *rem;         // [rem_cap] bitmap column of each remainder entry, grouped by row
+  int2 *heavy;           // [heavy_cap] (word, count) of counts above T_b, grouped by row
+  uint32_t *bitmap;      // [bm_cols][rows_total / 32] bit r of column (t, word): count >= t
   Item *sortbuf;         // [2 n_total] per-set length sort (n_sets > 1 only)
-  int64_t *scanblk;      // [2 x blocks] block totals of the excess-list scan
+  int64_t *scanblk;      // block totals of the remainder scans
+  const int32_t *counts; // the rank's input counts (heavy remainder entries read them)
   int64_t n_pad;         // rows_total: stored rows over all sets
-  int64_t n_total, n_sets, tiles_total, k_cap, list_cap, block_cap;
+  int64_t n_total, n_sets, tiles_total, k_cap, list_cap, rem_cap, heavy_cap, bm_cols;
   int32_t depth_cap;     // 0 = all planes
+  int32_t budget;        // remainder entries per column block
+  int32_t eps;
   uint64_t wait_ns;      // budget of the GEMM's main-loop waits
 };
 

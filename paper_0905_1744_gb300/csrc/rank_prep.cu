@@ -4,18 +4,28 @@
 // exact identity min(a, b) = sum_{t>=1} [a >= t][b >= t]: with one 0/1 column
 // per (word tau, threshold t), t = 1..T_tau, T_tau = max_x c^x_tau, the matrix
 // P[x][(tau,t)] = [c^x_tau >= t] satisfies S = P P^T. The columns are laid out
-// threshold-major: section t holds the words with T_tau >= t, so the first
-// sections are the dense ones and a tile whose rows never count any word more
-// than d times only needs the first d sections (its K extent).
+// threshold-major: section t holds the words with T_tau >= t (in word order), so
+// the first sections are the dense ones and a tile whose rows never count any
+// word more than d times only needs the columns up to the end of section d.
 //
-// Depth cap. Only the sections t = 1..D may be kept as planes (D = the plan's
-// depth; 0 keeps all). What the planes miss is exact too:
-//   min(a, b) = sum_{t=1..D} [a >= t][b >= t] + max(0, min(a, b) - D),
-// and the second term is nonzero only for words both sequences hold more than
-// D times. Each such (set, word) gets a list of (stored row, count - D); every
-// pair in a list adds min of the two excesses to that pair's residual, which is
-// summed into a dense 128 x 128 u16 block of its GEMM tile and added to the
-// tile's accumulator in the epilogue, before the floor.
+// Plane depth and remainder (plans of depth D >= 1). Only the sections 1..D'
+// (D' = min(D, t_max, 8)) are kept as planes. Each column block J of 128 stored
+// rows gets its own plane depth d_J <= D': the tiles of column J run the GEMM over
+// the plane columns [0, K_end(d_J)), K_end(d) = the end of section d rounded up
+// to the 256-column K chunk, and every threshold column (tau, t) that a row v of
+// block J counts (c_v(tau) >= t, t >= 2) but that lies at or past K_end(d_J) -- or
+// above the planes -- is a remainder entry of row v. For a pair (u, v) of such a
+// tile the planes give the identity's sum over the covered columns, and
+//   S_uv = (plane columns < K_end) + sum over v's remainder entries (tau, t) of
+//          [c_u(tau) >= t],
+// which the GEMM epilogue evaluates from a bitmap of the columns (bit u of
+// column (tau, t) = [c_u(tau) >= t]) before the floor, so every key is exact for
+// every choice of depths. (When a tile's extent is cut lower by its row blocks'
+// largest counts, the columns between are zero for the block that cuts it.)
+// d_J is the smallest depth whose remainder entries fit the plan's budget per
+// block. Thresholds above T_b = min(D' + 4, 16) are not in the bitmap: a count
+// c > T_b of row v adds a heavy entry (tau, c), worth max(0, min(c_u, c) - T_b)
+// for row u, which the epilogue reads from the counts.
 //
 // Sets. A call ranks one or more independent sets (a batch). Each set's rows are
 // stored contiguously (128-aligned) and its tiles only pair rows of that set, so
@@ -25,18 +35,23 @@
 // i <= j the Eq. 1 denominator is min(L_i, L_j) - k + 1 = m_j, the column's own.
 //
 // Kernels, in launch order:
-//   rank_setup     the set table (row, tile and tile-map bases per set)
+//   rank_setup     the set table (row and tile bases per set)
 //   rank_setmaps   set index of every sequence and stored row (batches only)
 //   rank_init      zero the scratch regions of the workspace
 //   lengths        m = L - k + 1, validation, histogram of m (one set)
-//   colmax         T_tau = max_x c^x_tau, count validation, #{x : c^x_tau > D}
-//   colmap         t_max, section ends, K_eff at depth D, the column map
-//   list_scan_*    offsets of the excess lists and of their pair ranges
+//   colmax         T_tau = max_x c^x_tau, count validation (and, for a plan, the
+//                  sizes of the remainder lists)
+//   colmap         t_max, section ends, K_eff, the column maps, the covering depth
+//                  of every plane column
 //   lensort_*      stored row of every sequence, per-row division records
-//   planes         P rows as packed e2m1 (2 = 1.0, 0 = 0.0), block depths,
-//                  excess-list entries
+//   bitmap_zero    clear the remainder bitmap
+//   planes         P rows as packed e2m1 (2 = 1.0, 0 = 0.0), block largest counts;
+//                  depth >= 1: bitmap bits, per-row remainder profile, the
+//                  (row, word, count >= 2) entries
+//   rem_depth      per column block: plane depth d_J, per-row entry offsets
+//   rem_scan       block offsets of the remainder lists
+//   rem_scatter    the remainder lists, grouped by row
 //   tiles          per set, the upper-triangle tile list with per-tile K extent
-//   residual_*     give residual blocks to tiles, zero them, add every pair
 #include "rank.cuh"
 #include "sort.cuh"
 
@@ -52,37 +67,41 @@ RankPtrs rank_ptrs(void *ws, const RankLayout &L) {
   P.T = reinterpret_cast<int32_t *>(b + L.T);
   P.secend = reinterpret_cast<int32_t *>(b + L.secend);
   P.colmap = reinterpret_cast<int32_t *>(b + L.colmap);
+  P.dstar = reinterpret_cast<int8_t *>(b + L.dstar);
   P.thist = reinterpret_cast<int32_t *>(b + L.thist);
   P.coltab = reinterpret_cast<int32_t *>(b + L.coltab);
-  P.promcol = reinterpret_cast<int32_t *>(b + L.promcol);
-  P.weight = reinterpret_cast<int64_t *>(b + L.weight);
   P.mhist = reinterpret_cast<int32_t *>(b + L.mhist);
   P.perm = reinterpret_cast<int32_t *>(b + L.perm);
   P.rec = reinterpret_cast<uint4 *>(b + L.rec);
   P.recw = reinterpret_cast<uint2 *>(b + L.recw);
   P.depth = reinterpret_cast<int32_t *>(b + L.depth);
+  P.bdepth = reinterpret_cast<int32_t *>(b + L.bdepth);
   P.tiles = reinterpret_cast<int2 *>(b + L.tiles);
   P.acc = reinterpret_cast<unsigned long long *>(b + L.acc);
   P.planes = b + L.planes;
-  P.cnt_gt = reinterpret_cast<int32_t *>(b + L.cnt_gt);
-  P.list_off = reinterpret_cast<int64_t *>(b + L.list_off);
-  P.item_off = reinterpret_cast<int64_t *>(b + L.item_off);
+  P.prof = reinterpret_cast<uint32_t *>(b + L.prof);
+  P.rowrem = reinterpret_cast<int32_t *>(b + L.rowrem);
+  P.blkrem = reinterpret_cast<int64_t *>(b + L.blkrem);
   P.cursor = reinterpret_cast<int32_t *>(b + L.cursor);
-  P.lists = reinterpret_cast<int2 *>(b + L.lists);
   P.flat = reinterpret_cast<int2 *>(b + L.flat);
-  P.tile_of = reinterpret_cast<int32_t *>(b + L.tile_of);
-  P.block_of = reinterpret_cast<int32_t *>(b + L.block_of);
-  P.rblocks = reinterpret_cast<uint32_t *>(b + L.rblocks);
+  P.rem = reinterpret_cast<uint32_t *>(b + L.rem);
+  P.heavy = reinterpret_cast<int2 *>(b + L.heavy);
+  P.bitmap = reinterpret_cast<uint32_t *>(b + L.bitmap);
   P.sortbuf = reinterpret_cast<Item *>(b + L.sortbuf);
   P.scanblk = reinterpret_cast<int64_t *>(b + L.scanblk);
+  P.counts = nullptr;
   P.n_pad = L.shape.rows_total;
   P.n_total = L.shape.n_total;
   P.n_sets = L.shape.n_sets;
   P.tiles_total = L.shape.tiles_total;
   P.k_cap = L.caps.k_cap;
   P.list_cap = L.caps.list_cap;
-  P.block_cap = L.caps.block_cap;
+  P.rem_cap = L.caps.rem_cap;
+  P.heavy_cap = L.caps.heavy_cap;
+  P.bm_cols = L.caps.bm_cols;
   P.depth_cap = L.caps.depth;
+  P.budget = L.caps.budget > 0 ? L.caps.budget : kRemBudgetDefault;
+  P.eps = 0;
   P.wait_ns = gemm_wait_ns();
   return P;
 }
@@ -140,9 +159,18 @@ __device__ __forceinline__ int32_t set_of_seq(const RankPtrs &P, int64_t x) {
   return P.n_sets > 1 ? P.seq_set[x] : 0;
 }
 
-__device__ __forceinline__ int32_t set_of_row(const RankPtrs &P, int64_t r) {
-  return P.n_sets > 1 ? P.row_set[r] : 0;
+
+// Plane depth kept by a plan (0 = every section).
+__device__ __forceinline__ int32_t kept_depth(const RankPtrs &P, int32_t tmax) {
+  return P.depth_cap >= 1 ? min(min(P.depth_cap, kMaxPlaneDepth), tmax) : tmax;
 }
+
+// Largest threshold of the remainder bitmap (counts above it are heavy entries).
+__device__ __forceinline__ int32_t bit_depth(const RankPtrs &P) {
+  return t_bits_of(min(P.depth_cap, kMaxPlaneDepth));
+}
+
+__device__ __forceinline__ bool remainder_mode(const RankPtrs &P) { return P.depth_cap >= 1; }
 
 // One block: the set table (prefix sums of n, padded rows, tiles, tile-map size).
 __global__ void __launch_bounds__(1024) rank_setup_kernel(const int32_t *d_n, int32_t n1,
@@ -198,16 +226,14 @@ __global__ void rank_init_kernel(RankPtrs P, int32_t eps, int with_keys) {
   pdl_enter();
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nt = (int64_t)gridDim.x * blockDim.x;
-  const int64_t we = P.n_sets * (int64_t)eps;
   zero_range(P.T, eps, tid, nt);
   zero_range(P.thist, kMaxM + 2, tid, nt);
   zero_range(P.mhist, kMaxM + 2, tid, nt);
   zero_range(P.secend, kMaxM + 2, tid, nt);
-  zero_range(P.cnt_gt, we, tid, nt);
-  zero_range(P.cursor, we, tid, nt);
   if (with_keys) {
     zero_range(P.depth, P.n_pad / kRowBlock, tid, nt);
     zero_range(P.acc, 3 * P.n_total, tid, nt);
+    if (remainder_mode(P)) zero_range(P.cursor, 2 * P.n_pad, tid, nt);
   }
   if (tid == 0) {
     P.hdr->k_eff = 0;
@@ -217,12 +243,15 @@ __global__ void rank_init_kernel(RankPtrs P, int32_t eps, int with_keys) {
     P.hdr->k_chunks = 0;
     P.hdr->depth = 0;
     P.hdr->list_total = 0;
-    P.hdr->pairs_total = 0;
-    P.hdr->n_blocks = 0;
+    P.hdr->rem_bound = 0;
+    P.hdr->heavy_total = 0;
+    P.hdr->bm_cols = 0;
     P.hdr->m_max = 0;
-    P.hdr->n_promoted = 0;
-    P.hdr->k_ext = 0;
     P.hdr->flat_count = 0;
+    P.hdr->rem_entries = 0;
+    P.hdr->heavy_entries = 0;
+    P.hdr->t_bits = 0;
+    P.hdr->rem_blocks = 0;
   }
 }
 
@@ -242,66 +271,45 @@ __global__ void lengths_kernel(const int32_t *__restrict__ lengths, int32_t k, R
   }
 }
 
-// T_tau = max over rows of counts[x][tau] and (D >= 1) the number of rows of each
-// set whose count exceeds D. Block (256 words) x (row slice).
+// T_tau = max over rows of counts[x][tau]. For a plan of depth >= 1 also the sizes of
+// the remainder: entries (x, tau) with a count c >= 2, the sum of min(c, T_b) - 1
+// over them (the remainder entries there can be) and the entries with c > T_b.
+// Block (256 words) x (row slice).
 __global__ void colmax_kernel(const int32_t *__restrict__ counts, int32_t eps, RankPtrs P,
-                              int count_gt) {
+                              int count_lists) {
   pdl_enter();
   const int32_t tau = blockIdx.x * blockDim.x + threadIdx.x;
   if (tau >= eps) return;
-  const int32_t D = count_gt ? P.depth_cap : 0;
+  const bool lists = count_lists && remainder_mode(P);
+  const int32_t tb = bit_depth(P);
   const int64_t n = P.n_total;
   const int64_t per = (n + gridDim.y - 1) / gridDim.y;
   const int64_t r0 = (int64_t)blockIdx.y * per;
   const int64_t r1 = r0 + per < n ? r0 + per : n;
-  int32_t mx = 0, mn = 0, gt = 0;
-  int32_t cur = r0 < r1 ? set_of_seq(P, r0) : 0;
-  int64_t r = r0;
-  if (P.n_sets == 1) {
-    for (; r + 4 <= r1; r += 4) {
-      const int32_t a = __ldg(counts + (r + 0) * eps + tau);
-      const int32_t b = __ldg(counts + (r + 1) * eps + tau);
-      const int32_t c = __ldg(counts + (r + 2) * eps + tau);
-      const int32_t d = __ldg(counts + (r + 3) * eps + tau);
-      mx = max(mx, max(max(a, b), max(c, d)));
-      mn = min(mn, min(min(a, b), min(c, d)));
-      gt += (a > D) + (b > D) + (c > D) + (d > D);
-    }
-  } else {
-    for (; r + 4 <= r1; r += 4) {
-      int32_t v[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) v[u] = __ldg(counts + (r + u) * eps + tau);
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        mx = max(mx, v[u]);
-        mn = min(mn, v[u]);
-        const int32_t s = P.seq_set[r + u];
-        if (s != cur) {
-          if (D >= 1 && gt) atomicAdd(&P.cnt_gt[(int64_t)cur * eps + tau], gt);
-          gt = 0;
-          cur = s;
-        }
-        gt += v[u] > D;
-      }
-    }
-  }
-  for (; r < r1; ++r) {
+  int32_t mx = 0, mn = 0;
+  long long nl = 0, nr = 0, nh = 0;
+  for (int64_t r = r0; r < r1; ++r) {
     const int32_t a = __ldg(counts + r * eps + tau);
     mx = max(mx, a);
     mn = min(mn, a);
-    const int32_t s = set_of_seq(P, r);
-    if (s != cur) {
-      if (D >= 1 && gt) atomicAdd(&P.cnt_gt[(int64_t)cur * eps + tau], gt);
-      gt = 0;
-      cur = s;
+    if (lists && a >= 2) {
+      nl += 1;
+      nr += min(a, tb) - 1;
+      nh += a > tb ? 1 : 0;
     }
-    gt += a > D;
   }
   if (mn < 0) record_error(P.hdr, SAD_ERR_BAD_INPUT, tau);
   if (mx > kMaxM) record_error(P.hdr, SAD_ERR_UNSUPPORTED, tau);
   if (mx > 0) atomicMax(&P.T[tau], mx);
-  if (D >= 1 && gt) atomicAdd(&P.cnt_gt[(int64_t)cur * eps + tau], gt);
+  if (nl) {
+    atomicAdd(reinterpret_cast<unsigned long long *>(&P.hdr->list_total),
+              (unsigned long long)nl);
+    atomicAdd(reinterpret_cast<unsigned long long *>(&P.hdr->rem_bound),
+              (unsigned long long)nr);
+    if (nh)
+      atomicAdd(reinterpret_cast<unsigned long long *>(&P.hdr->heavy_total),
+                (unsigned long long)nh);
+  }
 }
 
 // T_tau taken from a per-word maximum computed while counting.
@@ -317,8 +325,11 @@ __global__ void copy_word_max_kernel(const int32_t *__restrict__ word_max, int32
 }
 
 // One block of 1024 threads: histogram of T, t_max, section ends secend[t] =
-// sum_{t'<=t} #{tau : T_tau >= t'}, K_eff at the depth cap and (unless plan_only)
-// the column map colmap[col] = tau | t << 16.
+// sum_{t'<=t} #{tau : T_tau >= t'}, K_eff at the kept depth, the bitmap columns
+// and (unless plan_only) the column map colmap[col] = tau | t << 16, the column
+// table coltab[t - 1][tau] (thresholds up to the bitmap's, depth >= 1) and the
+// covering depth dstar[col] of every plane column: the smallest d whose K extent,
+// the end of section d rounded up to a K chunk, lies past the column.
 __global__ void __launch_bounds__(1024) colmap_kernel(RankPtrs P, int32_t eps, int plan_only) {
   pdl_enter();
   __shared__ int32_t s_tmax;
@@ -364,19 +375,24 @@ __global__ void __launch_bounds__(1024) colmap_kernel(RankPtrs P, int32_t eps, i
   }
   if (tid == 0) P.secend[0] = 0;
   __syncthreads();
-  // planes kept: sections 1..dkeep; a residual exists when some count exceeds it
-  const int32_t dkeep = P.depth_cap >= 1 ? min(P.depth_cap, tmax) : tmax;
+  // planes kept: sections 1..dkeep; the bitmap holds thresholds 2..tb
+  const int32_t dkeep = kept_depth(P, tmax);
   const int64_t k_eff = dkeep >= 1 ? (int64_t)P.secend[dkeep] : 0;
   int64_t k_pad = (k_eff + kKCols - 1) / kKCols * kKCols;
   if (k_pad < kKCols) k_pad = kKCols;
+  const bool rem = remainder_mode(P);
+  const int32_t tb = rem ? min(bit_depth(P), tmax) : 0;
+  const int32_t bm_cols = tb >= 2 ? P.secend[tb] - P.secend[1] : 0;
   if (tid == 0) {
     P.hdr->t_max = tmax;
     P.hdr->depth = dkeep;
     P.hdr->k_eff = k_eff;
     P.hdr->k_pad = (int32_t)k_pad;
+    P.hdr->t_bits = tb;
+    P.hdr->bm_cols = bm_cols;
   }
   if (plan_only) return;
-  if (k_pad > P.k_cap) {
+  if (k_pad > P.k_cap || (int64_t)bm_cols > P.bm_cols) {
     if (tid == 0) record_error(P.hdr, SAD_ERR_WORKSPACE, (int)k_pad);
     return;
   }
@@ -420,287 +436,41 @@ __global__ void __launch_bounds__(1024) colmap_kernel(RankPtrs P, int32_t eps, i
     }
     __syncthreads();
   }
-  if (P.depth_cap >= 1 && P.depth_cap <= kTabDepth) {
-    // the inverse map for the streaming plane writer: column of (t, word)
-    for (int i = tid; i < dkeep * eps; i += blockDim.x) P.coltab[i] = -1;
+  if (rem) {
+    // the inverse map: column of (t, word) for t <= max(dkeep, tb) (-1 = none); the
+    // kept sections from the column map, the bitmap's further sections by a scan
+    const int32_t ttab = max(dkeep, tb);
+    for (int i = tid; i < ttab * eps; i += blockDim.x) P.coltab[i] = -1;
     __syncthreads();
     for (int c = tid; c < k_eff; c += blockDim.x) {
       const int32_t e = P.colmap[c];
       P.coltab[(int64_t)((e >> 16) - 1) * eps + (e & 0xFFFF)] = c;
     }
-  }
-}
-
-// Offsets of the excess lists over all (set, word) entries w: list_off[w] =
-// prefix of c_w and item_off[w] = prefix of items(c_w), c_w = cnt_gt[w] (0 when
-// nothing is cut), where items(c) counts the pairs of kPairChunk-entry chunks of
-// a list of c entries (the residual's units of work). Three passes: per-block
-// totals, a scan of the block totals, per-block scans with the block's carry.
-// The number of residual pairs, sum c_w (c_w + 1) / 2, is added up on the side.
-constexpr int kScanChunk = kScanChunkWords;
-constexpr int kPairChunk = 128;
-
-__host__ __device__ __forceinline__ int64_t items_of(int64_t c) {
-  const int64_t n = (c + kPairChunk - 1) / kPairChunk;
-  return n * (n + 1) / 2;
-}
-
-__device__ __forceinline__ bool residual_needed(const RankPtrs &P) {
-  return P.hdr->depth < P.hdr->t_max;
-}
-
-__global__ void __launch_bounds__(256) list_scan_reduce_kernel(RankPtrs P, int64_t we) {
-  pdl_enter();
-  __shared__ int64_t s_warp[32];
-  const bool on = residual_needed(P);
-  const int64_t b0 = (int64_t)blockIdx.x * kScanChunk;
-  int64_t sl = 0, sp = 0, sq = 0;
-  for (int64_t w = b0 + threadIdx.x; w < b0 + kScanChunk && w < we; w += blockDim.x) {
-    const int64_t c = on ? P.cnt_gt[w] : 0;
-    sl += c;
-    sp += items_of(c);
-    sq += c * (c + 1) / 2;
-  }
-  int64_t tl, tp, tq;
-  block_scan_incl<int64_t>(sl, s_warp, &tl);
-  block_scan_incl<int64_t>(sp, s_warp, &tp);
-  block_scan_incl<int64_t>(sq, s_warp, &tq);
-  if (threadIdx.x == 0) {
-    P.scanblk[2 * blockIdx.x] = tl;
-    P.scanblk[2 * blockIdx.x + 1] = tp;
-    if (tq) atomicAdd(reinterpret_cast<unsigned long long *>(&P.hdr->pairs_total),
-                      (unsigned long long)tq);
-  }
-}
-
-__global__ void __launch_bounds__(1024) list_scan_top_kernel(RankPtrs P, int64_t nblk) {
-  pdl_enter();
-  __shared__ int64_t s_warp[32];
-  __shared__ int64_t s_l, s_p;
-  if (threadIdx.x == 0) {
-    s_l = 0;
-    s_p = 0;
-  }
-  __syncthreads();
-  for (int64_t base = 0; base < nblk; base += blockDim.x) {
-    const int64_t b = base + threadIdx.x;
-    const int64_t vl = b < nblk ? P.scanblk[2 * b] : 0;
-    const int64_t vp = b < nblk ? P.scanblk[2 * b + 1] : 0;
-    int64_t tl, tp;
-    const int64_t il = block_scan_incl<int64_t>(vl, s_warp, &tl);
-    const int64_t ip = block_scan_incl<int64_t>(vp, s_warp, &tp);
-    if (b < nblk) {
-      P.scanblk[2 * b] = s_l + il - vl;  // exclusive carry of block b
-      P.scanblk[2 * b + 1] = s_p + ip - vp;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      s_l += tl;
-      s_p += tp;
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    P.hdr->list_total = s_l;
-    P.hdr->items_total = s_p;
-  }
-}
-
-__global__ void __launch_bounds__(256) list_scan_down_kernel(RankPtrs P, int64_t we,
-                                                             int plan_only) {
-  pdl_enter();
-  __shared__ int64_t s_warp[32];
-  __shared__ int64_t s_l, s_p;
-  const bool on = residual_needed(P);
-  const int64_t b0 = (int64_t)blockIdx.x * kScanChunk;
-  if (threadIdx.x == 0) {
-    s_l = P.scanblk[2 * blockIdx.x];
-    s_p = P.scanblk[2 * blockIdx.x + 1];
-  }
-  __syncthreads();
-  for (int64_t base = b0; base < b0 + kScanChunk && base < we; base += blockDim.x) {
-    const int64_t w = base + threadIdx.x;
-    const int64_t c = (on && w < we) ? P.cnt_gt[w] : 0;
-    const int64_t pc = items_of(c);
-    int64_t tl, tp;
-    const int64_t il = block_scan_incl<int64_t>(c, s_warp, &tl);
-    const int64_t ip = block_scan_incl<int64_t>(pc, s_warp, &tp);
-    if (w < we) {
-      P.list_off[w] = s_l + il - c;
-      P.item_off[w] = s_p + ip - pc;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      s_l += tl;
-      s_p += tp;
-    }
-    __syncthreads();
-  }
-  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
-    P.list_off[we] = P.hdr->list_total;
-    P.item_off[we] = P.hdr->items_total;
-    if (!plan_only && (P.hdr->list_total > P.list_cap || (on && P.block_cap <= 0)))
-      record_error(P.hdr, SAD_ERR_WORKSPACE, -1);
-  }
-}
-
-// Planes in the K padding. K_eff is padded to a whole number of K chunks, so the
-// GEMM multiplies K_pad - K_eff zero columns anyway; they are given the plane of
-// threshold depth + 1 of the words with the most residual pairs (weight = sum over
-// sets of cnt_gt^2, ties by word), at no cost in the GEMM. Their excess entries
-// lose one (the new plane holds it) and leave the residual when nothing remains.
-__global__ void promote_weight_kernel(RankPtrs P, int32_t eps) {
-  pdl_enter();
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < eps;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    int64_t w = 0;
-    if (P.hdr->status == 0 && residual_needed(P))
-      for (int64_t s = 0; s < P.n_sets; ++s) {
-        const int64_t c = P.cnt_gt[s * eps + t];
-        w += c * c;
-      }
-    P.weight[t] = w;
-    P.promcol[t] = -1;
-  }
-}
-
-// One block: the words with weight >= w*, w* the smallest threshold that selects at
-// most K_pad - K_eff words (and only words with two or more excess sequences),
-// numbered in word order after K_eff. w* is one above the (n_free + 1)-th largest
-// weight, found by a radix select (8-bit digits from the top: a histogram of the
-// candidates' digit, then the digit where the count from the top reaches the rank).
-__global__ void __launch_bounds__(1024) promote_select_kernel(RankPtrs P, int32_t eps,
-                                                              int staged) {
-  pdl_enter();
-  extern __shared__ int64_t s_w[];  // [eps] when staged
-  __shared__ int32_t s_warp[32];
-  __shared__ int32_t s_hist[257];  // + a bin for words that are not candidates
-  __shared__ unsigned long long s_max, s_prefix;
-  __shared__ int32_t s_rank, s_found;
-  if (P.hdr->status != 0 || !residual_needed(P)) return;
-  const int32_t k_eff = (int32_t)P.hdr->k_eff, n_free = P.hdr->k_pad - k_eff;
-  if (n_free <= 0) return;
-  const int tid = threadIdx.x;
-  const uint64_t *w = reinterpret_cast<const uint64_t *>(staged ? s_w : P.weight);
-  if (tid == 0) {
-    s_max = 0;
-    s_prefix = 0;
-    s_rank = n_free + 1;
-    s_found = 1;
-  }
-  if (staged)
-    for (int t = tid; t < eps; t += blockDim.x) s_w[t] = P.weight[t];
-  __syncthreads();
-  {
-    uint64_t mx = 0;
-    for (int t = tid; t < eps; t += blockDim.x) mx = max(mx, w[t]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((tid & 31) == 0) atomicMax(&s_max, (unsigned long long)mx);
-  }
-  __syncthreads();
-  int top = 0;
-  while (top < 64 && (s_max >> top) > 255) top += 8;
-  uint64_t mask = 0;
-  for (int shift = top; shift >= 0; shift -= 8) {
-    if (tid < 257) s_hist[tid] = 0;
-    __syncthreads();
-    const uint64_t prefix = s_prefix;
-    // lanes with the same digit add together (most weights share the low digits)
-    for (int base = 0; base < eps; base += blockDim.x) {
-      const int t = base + tid;
-      const bool cand = t < eps && (w[t] & mask) == prefix;
-      const int d = cand ? (int)((w[t] >> shift) & 255) : 256;
-      const unsigned same = __match_any_sync(0xffffffffu, d);
-      if (cand && (tid & 31) == __ffs(same) - 1) atomicAdd(&s_hist[d], __popc(same));
-    }
-    __syncthreads();
-    if (tid < 32) {
-      // warp 0 walks the bins from the top: lane l holds bins 255-8l .. 248-8l
-      const int32_t need = s_rank;
-      int32_t mine = 0;
-#pragma unroll
-      for (int j = 0; j < 8; ++j) mine += s_hist[255 - 8 * tid - j];
-      int32_t incl = mine;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (tid >= o) incl += v;
-      }
-      const unsigned hit = __ballot_sync(0xffffffffu, incl >= need);
-      if (hit == 0) {  // fewer candidates than the rank: every weight is selectable
-        if (tid == 0) {
-          s_found = 0;
-          s_prefix = prefix;
-        }
-      } else if (tid == __ffs(hit) - 1) {
-        int32_t cum = incl - mine, d = 255 - 8 * tid;
-        while (cum + s_hist[d] < need) cum += s_hist[d--];
-        s_rank = need - cum;
-        s_prefix = prefix | ((unsigned long long)d << shift);
+    for (int t = dkeep + 1; t <= tb; ++t) {
+      if (tid == 0) s_carry = 0;
+      __syncthreads();
+      for (int base = 0; base < eps; base += blockDim.x) {
+        const int tau = base + tid;
+        const int32_t keep = (tau < eps && P.T[tau] >= t) ? 1 : 0;
+        int32_t tot;
+        const int32_t incl = block_scan_incl<int32_t>(keep, s_warp, &tot);
+        if (keep) P.coltab[(int64_t)(t - 1) * eps + tau] = P.secend[t - 1] + s_carry + incl - 1;
+        __syncthreads();
+        if (tid == 0) s_carry += tot;
+        __syncthreads();
       }
     }
-    mask |= (uint64_t)255 << shift;
-    __syncthreads();
-    if (!s_found) break;
-  }
-  // the (n_free + 1)-th largest weight is s_prefix (when there are that many words)
-  const uint64_t wstar = max((uint64_t)4, s_found ? (uint64_t)s_prefix + 1 : (uint64_t)0);
-  // number the selected words in word order: each thread takes consecutive words
-  const int per = (eps + blockDim.x - 1) / blockDim.x;
-  const int t0 = tid * per;
-  int32_t mine = 0;
-  for (int t = t0; t < t0 + per && t < eps; ++t) mine += w[t] >= wstar ? 1 : 0;
-  int32_t tot;
-  const int32_t incl = block_scan_incl<int32_t>(mine, s_warp, &tot);
-  int32_t next = k_eff + incl - mine;
-  for (int t = t0; t < t0 + per && t < eps; ++t)
-    if (w[t] >= wstar) P.promcol[t] = next++;
-  if (tid == 0) {
-    P.hdr->n_promoted = tot;
-    P.hdr->k_ext = k_eff + tot;
-    P.hdr->k_eff = k_eff + tot;
-  }
-}
-
-// Excess entries of promoted words: the plane value at the word's new column, one
-// less excess; entries left with none are dropped (row -1) and uncounted.
-__global__ void promote_apply_kernel(RankPtrs P, int32_t eps) {
-  pdl_enter();
-  if (P.hdr->status != 0 || !residual_needed(P) || P.hdr->n_promoted == 0) return;
-  const int64_t total = min((int64_t)P.hdr->flat_count, P.list_cap);
-  const int64_t row_words = P.k_cap / 8;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int2 e = P.flat[i];
-    const int32_t tau = e.y & 0xFFFF, ex = (int32_t)((uint32_t)e.y >> 16);
-    const int32_t col = P.promcol[tau];
-    if (col < 0) continue;
-    atomicOr(reinterpret_cast<unsigned int *>(P.planes) + (int64_t)e.x * row_words + (col >> 3),
-             kE2M1One << (4 * (col & 7)));
-    if (ex > 1) {
-      P.flat[i] = make_int2(e.x, tau | ((ex - 1) << 16));
-    } else {
-      atomicSub(&P.cnt_gt[(int64_t)set_of_row(P, e.x) * eps + tau], 1);
-      P.flat[i] = make_int2(-1, e.y);
+    // covering depth of each plane column (columns past K_eff: padding, never a
+    // remainder entry)
+    for (int64_t c = tid; c < k_pad; c += blockDim.x) {
+      int32_t d = 1;
+      while (d < dkeep &&
+             min((int64_t)(P.secend[d] + kKCols - 1) / kKCols * kKCols, k_pad) <= c)
+        ++d;
+      P.dstar[c] = (int8_t)d;
     }
   }
-}
 
-// Excess entries from the unordered append into their (set, word) lists.
-__global__ void group_lists_kernel(RankPtrs P, int32_t eps) {
-  pdl_enter();
-  if (P.hdr->status != 0 || !residual_needed(P)) return;
-  const int64_t total = (int64_t)P.hdr->flat_count;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int2 e = P.flat[i];
-    if (e.x < 0) continue;  // all of its excess went into a promoted plane
-    const int32_t tau = e.y & 0xFFFF, ex = (int32_t)((uint32_t)e.y >> 16);
-    const int64_t w = (int64_t)set_of_row(P, e.x) * eps + tau;
-    const int32_t slot = atomicAdd(&P.cursor[w], 1);
-    P.lists[P.list_off[w] + slot] = make_int2(e.x, ex);
-  }
 }
 
 // One set: exclusive prefix over m in decreasing order, mhist[m] := #{x : m_x > m},
@@ -785,12 +555,39 @@ __global__ void __launch_bounds__(kSortThreads) lensort_sets_kernel(
   }
 }
 
+// Remainder bookkeeping of a count c >= 2 of word tau in stored row pos (plans of
+// depth >= 1): the bitmap bits of thresholds 2..min(c, tb), the row's profile (each
+// threshold counted under the first plane depth that covers its column, dkeep + 1
+// when it is above the planes) and the row's heavy count (c > tb).
+__device__ __noinline__ void note_count(const RankPtrs &P, int64_t pos, int32_t tau, int32_t c,
+                                           int32_t dkeep, int32_t tb, int32_t n1,
+                                           int64_t bm_stride, uint32_t *s_prof) {
+  const int32_t top = min(c, tb);
+  for (int32_t t = 2; t <= top; ++t) {
+    const int32_t col = P.coltab[(int64_t)(t - 1) * P.eps + tau];
+    atomicOr(&P.bitmap[(int64_t)(col - n1) * bm_stride + (pos >> 5)], 1u << (pos & 31));
+    const int32_t ds = t <= dkeep ? (int32_t)P.dstar[col] : dkeep + 1;
+    atomicAdd(&s_prof[ds - 1], 1u);
+  }
+  if (c > tb) atomicAdd(&s_prof[kProf - 1], 1u);
+}
+
+__global__ void bitmap_zero_kernel(RankPtrs P) {
+  pdl_enter();
+  if (P.hdr->status != 0) return;
+  const int64_t words4 = (int64_t)P.hdr->bm_cols * (P.n_pad / 128);
+  uint4 *p = reinterpret_cast<uint4 *>(P.bitmap);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words4;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = make_uint4(0, 0, 0, 0);
+}
+
 // Plane rows, kPlaneRows stored rows per block iteration: stage the rows' counts
 // (as 16-bit) in shared memory with 16-byte loads, write their K_pad plane bytes
 // 16 at a time (the column map of a chunk is read once for all the rows), raise
-// the depth of each row's 128-row block to the row's largest count, check that
-// the row's counts add up to its number of windows m, and append its excess
-// entries (counts above the depth) to the (set, word) lists.
+// the largest count of each row's 128-row block, check that the row's counts add
+// up to its number of windows m, and (depth >= 1) note its counts >= 2 for the
+// remainder and append them to the flat entry list.
 constexpr int kPlaneRows = 2;
 
 // counts 4q..4q+3 of a row into its shared u16 copy (one 8-byte store), clamped to
@@ -808,11 +605,15 @@ __global__ void __launch_bounds__(256) planes_kernel(const int32_t *__restrict__
   __shared__ int32_t s_max[kPlaneRows], s_sum[kPlaneRows];
   __shared__ int32_t s_scan[32];
   __shared__ unsigned long long s_first;
+  __shared__ uint32_t s_prof[kPlaneRows][kProf];
   if (P.hdr->status != 0) return;
   const int32_t k_eff = (int32_t)P.hdr->k_eff;
   const int32_t k_pad = P.hdr->k_pad;
   const int32_t dkeep = P.hdr->depth;
-  const bool residual = dkeep < P.hdr->t_max;
+  const bool residual = remainder_mode(P);
+  const int32_t tb = bit_depth(P);
+  const int32_t n1 = P.secend[1];
+  const int64_t bm_stride = P.n_pad / 32;
   const bool vec = (eps & 3) == 0 && (reinterpret_cast<uintptr_t>(counts) & 15) == 0;
   const int64_t groups = P.n_pad / kPlaneRows;
   for (int64_t g = blockIdx.x; g < groups; g += gridDim.x) {
@@ -823,6 +624,7 @@ __global__ void __launch_bounds__(256) planes_kernel(const int32_t *__restrict__
       s_max[threadIdx.x] = 0;
       s_sum[threadIdx.x] = 0;
     }
+    if (threadIdx.x < kPlaneRows * kProf) (&s_prof[0][0])[threadIdx.x] = 0u;
 #pragma unroll
     for (int r = 0; r < kPlaneRows; ++r) {
       uint16_t *sc = s_cnt + r * eps;
@@ -871,15 +673,14 @@ __global__ void __launch_bounds__(256) planes_kernel(const int32_t *__restrict__
     }
     __syncthreads();
     if (residual) {
-      // excess entries of the rows, appended unordered: (stored row, word | excess << 16);
-      // the per-(set, word) sizes are counted for the grouping that follows. The
-      // block counts its entries first and reserves their slots with one atomic.
+      // counts >= 2 of the rows, appended unordered: (stored row, word | count << 16).
+      // The block counts its entries first and reserves their slots with one atomic.
       int32_t mine = 0;
 #pragma unroll
       for (int r = 0; r < kPlaneRows; ++r)
         if (xs[r] >= 0)
           for (int tau = threadIdx.x; tau < eps; tau += blockDim.x)
-            mine += s_cnt[r * eps + tau] > dkeep;
+            mine += s_cnt[r * eps + tau] >= 2;
       int32_t total;
       const int32_t incl = block_scan_incl<int32_t>(mine, s_scan, &total);
       if (threadIdx.x == 0)
@@ -890,13 +691,12 @@ __global__ void __launch_bounds__(256) planes_kernel(const int32_t *__restrict__
       for (int r = 0; r < kPlaneRows; ++r) {
         if (xs[r] < 0 || mine == 0) continue;
         const int64_t pos = g * kPlaneRows + r;
-        const int64_t wbase = (int64_t)set_of_row(P, pos) * eps;
         for (int tau = threadIdx.x; tau < eps; tau += blockDim.x) {
           const int32_t c = s_cnt[r * eps + tau];
-          if (c > dkeep) {
-            atomicAdd(&P.cnt_gt[wbase + tau], 1);
+          if (c >= 2) {
+            note_count(P, pos, tau, c, dkeep, tb, n1, bm_stride, s_prof[r]);
             if (slot < (unsigned long long)P.list_cap)
-              P.flat[slot] = make_int2((int32_t)pos, tau | ((c - dkeep) << 16));
+              P.flat[slot] = make_int2((int32_t)pos, tau | (c << 16));
             ++slot;
           }
         }
@@ -937,6 +737,7 @@ __global__ void __launch_bounds__(256) planes_kernel(const int32_t *__restrict__
 #pragma unroll
       for (int r = 0; r < kPlaneRows; ++r) dst[r][c] = xs[r] >= 0 ? w[r] : 0u;
     }
+    __syncthreads();  // the rows' profiles are complete
     if (threadIdx.x < kPlaneRows && xs[threadIdx.x] >= 0) {
       const int64_t pos = g * kPlaneRows + threadIdx.x;
       atomicMax(&P.depth[pos / kRowBlock], s_max[threadIdx.x]);
@@ -944,20 +745,25 @@ __global__ void __launch_bounds__(256) planes_kernel(const int32_t *__restrict__
       if (s_sum[threadIdx.x] != (int32_t)(P.rec[pos].w & 0xFFFFu))
         record_error(P.hdr, SAD_ERR_BAD_INPUT, xs[threadIdx.x]);
     }
+    if (residual && threadIdx.x < kPlaneRows * kProf) {
+      const int r = threadIdx.x / kProf, j = threadIdx.x % kProf;
+      P.prof[(g * kPlaneRows + r) * kProf + j] = s_prof[r][j];
+    }
     __syncthreads();
   }
 }
 
-// Plane rows for depths D <= kTabDepth, streamed: one warp per stored row reads the
+// Plane rows for plans of depth >= 1, streamed: one warp per stored row reads the
 // row's counts once (16 bytes per lane, four loads in flight). A plane value is
 // the 4-bit e2m1 [c >= t] (1.0 or 0), two columns to a byte. When every word
 // occurs somewhere, section 1 is the identity map and a lane writes its four words
 // as one 2-byte store; the columns past section 1 are zero-filled with 16-byte
 // stores first, and only the words counted twice or more then set their values in
 // sections 2..min(c, D) (atomic OR: neighbouring columns share bytes). Otherwise
-// the whole row is zero-filled and every 1 is set that way. Counts above D go to a
-// per-warp buffer and are appended to the flat excess list with one atomic per
-// row; a row with more than kExCap of them is scanned again for the append.
+// the whole row is zero-filled and every 1 is set that way. Counts >= 2 also set
+// their remainder bitmap bits and the row's profile, and go to a per-warp buffer
+// that is appended to the flat entry list with one atomic per row; a row with more
+// than kExCap of them is scanned again for the append.
 constexpr int kExCap = 64;
 constexpr int kStreamUnroll = 4;
 
@@ -973,11 +779,14 @@ __global__ void __launch_bounds__(256) planes_stream_kernel(const int32_t *__res
   pdl_enter();
   __shared__ int2 s_ex[8][kExCap];
   __shared__ int32_t s_exn[8];
+  __shared__ uint32_t s_prof[8][kProf];
   if (P.hdr->status != 0) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int32_t k_pad = P.hdr->k_pad;
   const int32_t dkeep = P.hdr->depth;
-  const bool residual = dkeep < P.hdr->t_max;
+  const bool residual = remainder_mode(P);
+  const int32_t tb = bit_depth(P);
+  const int64_t bm_stride = P.n_pad / 32;
   const int q4 = eps >> 2;
   const int32_t s1 = P.secend[1];  // end of section 1
   const bool ident = s1 == eps;    // section 1 = every word, in order
@@ -986,6 +795,7 @@ __global__ void __launch_bounds__(256) planes_stream_kernel(const int32_t *__res
   const int32_t z0 = ident ? s1 / 2 : 0;
   const int32_t z16 = min((z0 + 15) & ~15, kb);
   if (lane == 0) s_exn[warp] = 0;
+  if (lane < kProf) s_prof[warp][lane] = 0u;
   __syncwarp();
   for (int64_t pos = (int64_t)blockIdx.x * 8 + warp; pos < P.n_pad;
        pos += (int64_t)gridDim.x * 8) {
@@ -994,6 +804,7 @@ __global__ void __launch_bounds__(256) planes_stream_kernel(const int32_t *__res
     if (x < 0) {  // padding row: all zero
       for (int c = 16 * lane; c < kb; c += 512)
         *reinterpret_cast<uint4 *>(prow + c) = make_uint4(0, 0, 0, 0);
+      if (residual && lane < kProf) P.prof[pos * kProf + lane] = 0u;
       continue;
     }
     for (int c = z0 + lane; c < z16; c += 32) prow[c] = 0;
@@ -1001,7 +812,6 @@ __global__ void __launch_bounds__(256) planes_stream_kernel(const int32_t *__res
       *reinterpret_cast<uint4 *>(prow + c) = make_uint4(0, 0, 0, 0);
     __syncwarp();
     const int4 *row4 = reinterpret_cast<const int4 *>(counts + (int64_t)x * eps);
-    const int64_t wbase = (int64_t)set_of_row(P, pos) * eps;
     int32_t mx = 0, sum = 0;
     for (int base = 0; base < q4; base += 32 * kStreamUnroll) {
       int4 v[kStreamUnroll];
@@ -1039,10 +849,10 @@ __global__ void __launch_bounds__(256) planes_stream_kernel(const int32_t *__res
         if (residual) {
 #pragma unroll
           for (int b = 0; b < 4; ++b) {
-            if (c[b] > dkeep) {
+            if (c[b] >= 2) {
+              note_count(P, pos, 4 * q + b, c[b], dkeep, tb, s1, bm_stride, s_prof[warp]);
               const int slot = atomicAdd(&s_exn[warp], 1);
-              if (slot < kExCap)
-                s_ex[warp][slot] = make_int2((int32_t)pos, (4 * q + b) | ((c[b] - dkeep) << 16));
+              if (slot < kExCap) s_ex[warp][slot] = make_int2((int32_t)pos, (4 * q + b) | (c[b] << 16));
             }
           }
         }
@@ -1060,6 +870,10 @@ __global__ void __launch_bounds__(256) planes_stream_kernel(const int32_t *__res
     }
     if (residual) {
       __syncwarp();
+      if (lane < kProf) {
+        P.prof[pos * kProf + lane] = s_prof[warp][lane];
+        s_prof[warp][lane] = 0u;
+      }
       const int32_t n_ex = s_exn[warp];
       if (n_ex > 0) {
         unsigned long long first = 0;
@@ -1067,9 +881,7 @@ __global__ void __launch_bounds__(256) planes_stream_kernel(const int32_t *__res
         first = __shfl_sync(0xffffffffu, first, 0);
         if (n_ex <= kExCap) {
           for (int i = lane; i < n_ex; i += 32) {
-            const int2 e = s_ex[warp][i];
-            atomicAdd(&P.cnt_gt[wbase + (e.y & 0xFFFF)], 1);
-            if (first + i < (unsigned long long)P.list_cap) P.flat[first + i] = e;
+            if (first + i < (unsigned long long)P.list_cap) P.flat[first + i] = s_ex[warp][i];
           }
         } else {
           // the buffer overflowed: scan the row again and append every entry
@@ -1081,11 +893,10 @@ __global__ void __launch_bounds__(256) planes_stream_kernel(const int32_t *__res
             const int32_t c[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-              if (c[b] > dkeep) {
+              if (c[b] >= 2) {
                 const unsigned long long slot = first + (unsigned)atomicAdd(&s_exn[warp], 1);
-                atomicAdd(&P.cnt_gt[wbase + 4 * q + b], 1);
                 if (slot < (unsigned long long)P.list_cap)
-                  P.flat[slot] = make_int2((int32_t)pos, (4 * q + b) | ((c[b] - dkeep) << 16));
+                  P.flat[slot] = make_int2((int32_t)pos, (4 * q + b) | (c[b] << 16));
               }
             }
           }
@@ -1098,14 +909,160 @@ __global__ void __launch_bounds__(256) planes_stream_kernel(const int32_t *__res
   }
 }
 
+// ------------------------------------------------------------ remainder ----
+// Per column block b (128 stored rows, one thread each): N_b(d) = the block's
+// remainder entries at plane depth d (its rows' thresholds whose covering depth is
+// above d), for d = 1..min(dkeep, largest count); the block's depth d_b is the
+// smallest d with N_b(d) <= budget (else the largest). Each row's entries at d_b
+// (and its heavy entries) get offsets inside the block; the block totals go to
+// blkrem for the scan. Profile slot j of a row counts the thresholds whose
+// covering depth is j + 1 (slot dkeep: above the planes); at depth d the slots
+// j >= d are uncovered.
+constexpr int kRemThreads = kColBlock;
+
+__global__ void __launch_bounds__(kRemThreads) rem_depth_kernel(RankPtrs P) {
+  pdl_enter();
+  __shared__ uint32_t s_n[kMaxPlaneDepth + 1];
+  __shared__ int32_t s_d;
+  __shared__ int32_t s_warp[32];
+  if (P.hdr->status != 0) return;
+  const int32_t dkeep = P.hdr->depth;
+  const int64_t nblk = P.n_pad / kColBlock;
+  for (int64_t b = blockIdx.x; b < nblk; b += gridDim.x) {
+    const int64_t v = b * kColBlock + threadIdx.x;
+    uint32_t pr[kProf];
+#pragma unroll
+    for (int j = 0; j < kProf; ++j) pr[j] = P.prof[v * kProf + j];
+    if (threadIdx.x <= kMaxPlaneDepth) s_n[threadIdx.x] = 0u;
+    __syncthreads();
+    uint32_t tail = 0;
+#pragma unroll
+    for (int d = kMaxPlaneDepth; d >= 1; --d) {
+      if (d <= dkeep) {
+        tail += pr[d];
+        uint32_t w = tail;
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(&s_n[d], w);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int32_t bmax = P.depth[b];
+      const int32_t dcap = max(1, min(dkeep, bmax));
+      int32_t d = dcap;
+      for (int32_t dd = 1; dd < dcap; ++dd)
+        if (s_n[dd] <= (uint32_t)P.budget) {
+          d = dd;
+          break;
+        }
+      s_d = d;
+      P.bdepth[b] = d;
+      if (d < bmax) atomicAdd(&P.hdr->rem_blocks, 1);
+    }
+    __syncthreads();
+    const int32_t d = s_d;
+    uint32_t e = 0;
+#pragma unroll
+    for (int j = 1; j <= kMaxPlaneDepth; ++j)
+      if (j >= d && j <= dkeep) e += pr[j];
+    const uint32_t h = pr[kProf - 1];
+    int32_t tot_e, tot_h;
+    const int32_t incl_e = block_scan_incl<int32_t>((int32_t)e, s_warp, &tot_e);
+    const int32_t incl_h = block_scan_incl<int32_t>((int32_t)h, s_warp, &tot_h);
+    P.rowrem[2 * v] = incl_e - (int32_t)e;
+    P.rowrem[2 * v + 1] = incl_h - (int32_t)h;
+    if (threadIdx.x == 0) {
+      P.blkrem[2 * b] = tot_e;
+      P.blkrem[2 * b + 1] = tot_h;
+    }
+    __syncthreads();
+  }
+}
+
+// One block: exclusive scan of the block totals (in place), the grand totals at
+// index nblk, and the capacity checks.
+__global__ void __launch_bounds__(1024) rem_scan_kernel(RankPtrs P) {
+  pdl_enter();
+  __shared__ int64_t s_warp[32];
+  __shared__ int64_t s_carry[2];
+  if (P.hdr->status != 0) return;
+  const int64_t nblk = P.n_pad / kColBlock;
+  if (threadIdx.x < 2) s_carry[threadIdx.x] = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < nblk; base += blockDim.x) {
+    const int64_t b = base + threadIdx.x;
+#pragma unroll
+    for (int f = 0; f < 2; ++f) {
+      const int64_t x = b < nblk ? P.blkrem[2 * b + f] : 0;
+      int64_t tot;
+      const int64_t incl = block_scan_incl<int64_t>(x, s_warp, &tot);
+      if (b < nblk) P.blkrem[2 * b + f] = s_carry[f] + incl - x;
+      __syncthreads();
+      if (threadIdx.x == 0) s_carry[f] += tot;
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x == 0) {
+    P.blkrem[2 * nblk] = s_carry[0];
+    P.blkrem[2 * nblk + 1] = s_carry[1];
+    P.hdr->rem_entries = s_carry[0];
+    P.hdr->heavy_entries = s_carry[1];
+    if (P.hdr->flat_count > (unsigned long long)P.list_cap)
+      record_error(P.hdr, SAD_ERR_WORKSPACE, 1);
+    else if (s_carry[0] > P.rem_cap)
+      record_error(P.hdr, SAD_ERR_WORKSPACE, 2);
+    else if (s_carry[1] > P.heavy_cap)
+      record_error(P.hdr, SAD_ERR_WORKSPACE, 3);
+  }
+}
+
+// Every flat entry (row, word, count): the thresholds that the plane depth of the
+// row's block does not cover become remainder entries of the row (their bitmap
+// columns), and a count above T_b one heavy entry. The order inside a row is free.
+__global__ void __launch_bounds__(256) rem_scatter_kernel(RankPtrs P) {
+  pdl_enter();
+  if (P.hdr->status != 0) return;
+  const int32_t dkeep = P.hdr->depth;
+  const int32_t tb = bit_depth(P);
+  const int32_t n1 = P.secend[1];
+  const int64_t nf = (int64_t)min(P.hdr->flat_count, (unsigned long long)P.list_cap);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int2 f = P.flat[i];
+    const int64_t pos = f.x;
+    const int32_t tau = f.y & 0xFFFF;
+    const int32_t c = (int32_t)((uint32_t)f.y >> 16);
+    const int64_t b = pos / kColBlock;
+    const int32_t d = P.bdepth[b];
+    const int64_t base = P.blkrem[2 * b] + P.rowrem[2 * pos];
+    const int32_t top = min(c, tb);
+    for (int32_t t = 2; t <= top; ++t) {
+      const int32_t col = P.coltab[(int64_t)(t - 1) * P.eps + tau];
+      const bool covered = t <= dkeep && (int32_t)P.dstar[col] <= d;
+      if (!covered) {
+        const int32_t slot = atomicAdd(&P.cursor[2 * pos], 1);
+        P.rem[base + slot] = (uint32_t)(col - n1);
+      }
+    }
+    if (c > tb) {
+      const int32_t slot = atomicAdd(&P.cursor[2 * pos + 1], 1);
+      P.heavy[P.blkrem[2 * b + 1] + P.rowrem[2 * pos + 1] + slot] = make_int2(tau, c);
+    }
+  }
+}
+
 // Upper-triangle tile list of every set (blocks per set and column group). Tile (I, J) of a
 // set covers its stored rows [128 I, 128 I + 128) and columns [128 J, 128 J + 128)
 // (set-local, kColBlock = 128); it is needed when some pair i <= j lies in it
 // (I <= J) and both ranges hold real rows. Tiles are grouped by kGroupCols column blocks,
 // rows ascending inside a group, so that the tiles running at the same time share
-// their operand panels in L2. Each entry is (I | J << 16, K chunks) with global
-// block indices, the K extent being the end of section min(depth(I), depth(J), D).
+// their operand panels in L2. Each entry is (I | J << 16, nk | nx << 16) with global
+// block indices: nk plane K chunks, up to the end of section e = min(largest count
+// of I, largest count of J, plane depth of J) (the kept depth when nothing is cut),
+// and nx remainder K chunks of 256 entries of column block J.
 constexpr int kGroupCols = 8;
+// remainder entries per extra K chunk of a tile: one K column each
+constexpr int kRemChunkCols = kKCols;
 
 // Tiles of column group g of a set: rows I with J in [8g, 8g + 8) and J >= I / kColRatio.
 __device__ __forceinline__ int32_t group_row_tiles(int32_t g, int32_t I, int32_t C) {
@@ -1122,12 +1079,12 @@ __global__ void __launch_bounds__(256) tiles_kernel(RankPtrs P) {
   const int tid = threadIdx.x;
   const int32_t nblk = (int32_t)(P.n_pad / kRowBlock);
   const int32_t dkeep = P.hdr->depth;
+  const bool rem = remainder_mode(P);
   for (int32_t si = blockIdx.y; si < (int32_t)P.n_sets; si += gridDim.y) {
     const RankSet e = P.sets[si];
     const int32_t n = e.n;
     const int32_t R = (n + kRowBlock - 1) / kRowBlock;
     const int32_t C = (n + kColBlock - 1) / kColBlock;
-    const int64_t cfull = dev_n_pad(n) / kColBlock;
     const int32_t I0 = (int32_t)(e.row_base / kRowBlock), J0 = (int32_t)(e.row_base / kColBlock);
     const int32_t groups = (C + kGroupCols - 1) / kGroupCols;
     for (int32_t g = blockIdx.x; g < groups; g += gridDim.x) {
@@ -1154,15 +1111,20 @@ __global__ void __launch_bounds__(256) tiles_kernel(RankPtrs P) {
             int32_t dJ = 0;
             for (int32_t b = kColRatio * (J0 + J); b < kColRatio * (J0 + J + 1) && b < nblk; ++b)
               dJ = max(dJ, P.depth[b]);
-            const int32_t d = min(min(dI, dJ), dkeep);
-            // the promoted planes of depth + 1 sit right after K_eff of the sections
-            const int32_t kend =
-                (P.hdr->n_promoted > 0 && min(dI, dJ) > dkeep) ? P.hdr->k_ext : P.secend[max(d, 0)];
+            const int32_t cut = rem ? P.bdepth[J0 + J] : dkeep;
+            const int32_t d = min(min(dI, dJ), cut);
+            const int32_t kend = P.secend[max(d, 0)];
             const int32_t nk = max(1, (kend + kKCols - 1) / kKCols);
-            P.tile_of[e.tileof_base + (int64_t)I * cfull + J] = (int32_t)out;
-            P.block_of[out] = 0;
-            P.tiles[out++] = make_int2((I0 + I) | ((J0 + J) << 16), nk);
-            chunks += (unsigned long long)nk;
+            // remainder chunks of the column block (one K column per entry)
+            int32_t nx = 0;
+            if (rem) {
+              const int64_t ne = P.blkrem[2 * (J0 + J) + 2] - P.blkrem[2 * (J0 + J)];
+              const int64_t x = (ne + kRemChunkCols - 1) / kRemChunkCols;
+              if (x > 0x7FFF) record_error(P.hdr, SAD_ERR_UNSUPPORTED, J0 + J);
+              nx = (int32_t)min(x, (int64_t)0x7FFF);
+            }
+            P.tiles[out++] = make_int2((I0 + I) | ((J0 + J) << 16), nk | (nx << 16));
+            chunks += (unsigned long long)(nk + nx);
           }
         }
         __syncthreads();
@@ -1175,160 +1137,6 @@ __global__ void __launch_bounds__(256) tiles_kernel(RankPtrs P) {
       __syncthreads();
     }
   }
-}
-
-// ------------------------------------------------------------- residual ----
-// The pairs (u, v), u <= v, of each (set, word) excess list (stored row,
-// count - D) are cut into work items: pairs of kPairChunk-entry chunks (cu, cv),
-// cu <= cv, numbered cv-major within the list after the items of the lists
-// before it (item_off). Blocks take items in a grid stride, so that the pairs of
-// a long list are spread over many blocks. A block stages the two chunks in
-// shared memory sorted by row (neighbouring pairs then land in neighbouring
-// columns of the same tile row) and its threads walk the chunk pair. fn(tile,
-// row in tile, column in tile, value) is called once per pair with value = min
-// of the two excesses; u == v is the sequence's own pair.
-
-// Ascending bitonic sort by .x of s[0, n), n <= kPairChunk, padded with INT_MAX.
-__device__ __forceinline__ void block_sort_by_row(int2 *s, int n) {
-  int p2 = 1;
-  while (p2 < n) p2 <<= 1;
-  for (int i = n + threadIdx.x; i < p2; i += blockDim.x) s[i] = make_int2(0x7FFFFFFF, 0);
-  __syncthreads();
-  for (int size = 2; size <= p2; size <<= 1) {
-    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int i = threadIdx.x; i < (p2 >> 1); i += blockDim.x) {
-        const int a = ((i & ~(stride - 1)) << 1) | (i & (stride - 1)), b = a + stride;
-        const bool asc = (a & size) == 0;
-        const int2 x = s[a], y = s[b];
-        if (asc ? (y.x < x.x) : (x.x < y.x)) {
-          s[a] = y;
-          s[b] = x;
-        }
-      }
-      __syncthreads();
-    }
-  }
-}
-
-template <typename Fn>
-__device__ __forceinline__ void for_each_residual_pair(const RankPtrs &P, int32_t eps, Fn fn) {
-  __shared__ int2 s_u[kPairChunk], s_v[kPairChunk];
-  __shared__ int64_t s_w;
-  const int64_t we = P.n_sets * (int64_t)eps;
-  const int64_t total = P.hdr->items_total;
-  for (int64_t it = blockIdx.x; it < total; it += gridDim.x) {
-    __syncthreads();  // the previous item's chunks are no longer read
-    if (threadIdx.x == 0) {
-      // the list holding item it: item_off[w] <= it < item_off[w + 1]
-      int64_t lo = 0, hi = we;
-      while (hi - lo > 1) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (P.item_off[mid] <= it) lo = mid;
-        else hi = mid;
-      }
-      s_w = lo;
-    }
-    __syncthreads();
-    const int64_t w = s_w;
-    const int64_t base = P.list_off[w];
-    const int64_t len = P.list_off[w + 1] - base;
-    const int64_t j = it - P.item_off[w];
-    int64_t cv = (int64_t)((sqrt(8.0 * (double)j + 1.0) - 1.0) * 0.5);
-    while (cv * (cv + 1) / 2 > j) --cv;
-    while ((cv + 1) * (cv + 2) / 2 <= j) ++cv;
-    const int64_t cu = j - cv * (cv + 1) / 2;
-    const RankSet e = P.sets[w / eps];
-    const int64_t cfull = dev_n_pad(e.n) / kColBlock;
-    const int nv = (int)min((int64_t)kPairChunk, len - cv * kPairChunk);
-    const int nu = (int)min((int64_t)kPairChunk, len - cu * kPairChunk);
-    const bool same = cu == cv;
-    for (int i = threadIdx.x; i < nv; i += blockDim.x) s_v[i] = P.lists[base + cv * kPairChunk + i];
-    if (!same)
-      for (int i = threadIdx.x; i < nu; i += blockDim.x) s_u[i] = P.lists[base + cu * kPairChunk + i];
-    block_sort_by_row(s_v, nv);
-    if (!same) block_sort_by_row(s_u, nu);
-    const int npairs = nu * nv;  // <= kPairChunk^2
-    for (int q = threadIdx.x; q < npairs; q += blockDim.x) {
-      const int iu = q / nv, iv = q - iu * nv;
-      if (same && iu > iv) continue;
-      const int2 eu = same ? s_v[iu] : s_u[iu];
-      const int2 ev = s_v[iv];
-      const int32_t a = min(eu.x, ev.x), b = max(eu.x, ev.x);
-      const int64_t al = a - e.row_base, bl = b - e.row_base;
-      const int32_t t = P.tile_of[e.tileof_base + (al / kRowBlock) * cfull + bl / kColBlock];
-      fn(t, (int32_t)(al % kRowBlock), (int32_t)(bl % kColBlock), (uint32_t)min(eu.y, ev.y));
-    }
-  }
-}
-
-__device__ __forceinline__ bool residual_on(const RankPtrs &P) {
-  return P.hdr->status == 0 && P.hdr->depth < P.hdr->t_max;
-}
-
-// Only needed when fewer residual blocks than tiles are reserved: mark the
-// tiles that some pair touches.
-__global__ void __launch_bounds__(256) residual_mark_kernel(RankPtrs P, int32_t eps) {
-  pdl_enter();
-  if (!residual_on(P)) return;
-  for_each_residual_pair(P, eps, [&](int32_t t, int32_t, int32_t, uint32_t) {
-    if (P.block_of[t] != 1) P.block_of[t] = 1;
-  });
-}
-
-// block_of[t] := index of tile t's residual block, -1 if none. With a block for
-// every tile (identity) nothing needs marking.
-__global__ void __launch_bounds__(1024) residual_scan_kernel(RankPtrs P, int identity) {
-  pdl_enter();
-  __shared__ int32_t s_warp[32];
-  __shared__ int32_t s_carry;
-  const int32_t nt = P.hdr->n_tiles;
-  const bool on = residual_on(P);
-  if (identity) {
-    // a block per tile: no scan
-    for (int32_t t = threadIdx.x; t < nt; t += blockDim.x) P.block_of[t] = on ? t : -1;
-    if (threadIdx.x == 0) {
-      P.hdr->n_blocks = on ? nt : 0;
-      if (on && nt > P.block_cap) record_error(P.hdr, SAD_ERR_WORKSPACE, nt);
-    }
-    return;
-  }
-  if (threadIdx.x == 0) s_carry = 0;
-  __syncthreads();
-  for (int32_t base = 0; base < nt; base += blockDim.x) {
-    const int32_t t = base + threadIdx.x;
-    const int32_t f = (on && t < nt && (identity || P.block_of[t] == 1)) ? 1 : 0;
-    int32_t tot;
-    const int32_t incl = block_scan_incl<int32_t>(f, s_warp, &tot);
-    if (t < nt) P.block_of[t] = f ? s_carry + incl - 1 : -1;
-    __syncthreads();
-    if (threadIdx.x == 0) s_carry += tot;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    P.hdr->n_blocks = s_carry;
-    if (s_carry > P.block_cap) record_error(P.hdr, SAD_ERR_WORKSPACE, s_carry);
-  }
-}
-
-__global__ void residual_zero_kernel(RankPtrs P) {
-  pdl_enter();
-  if (P.hdr->status != 0) return;
-  const int64_t words4 = (int64_t)P.hdr->n_blocks * (int64_t)(kResidualBlockBytes / 16);
-  uint4 *p = reinterpret_cast<uint4 *>(P.rblocks);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words4;
-       i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = make_uint4(0, 0, 0, 0);
-}
-
-__global__ void __launch_bounds__(256) residual_add_kernel(RankPtrs P, int32_t eps) {
-  pdl_enter();
-  if (!residual_on(P)) return;
-  for_each_residual_pair(P, eps, [&](int32_t t, int32_t row, int32_t col, uint32_t val) {
-    const int64_t blk = P.block_of[t];
-    // two u16 per word; a pair's residual never exceeds 65535, so no carry crosses
-    atomicAdd(&P.rblocks[blk * (kResidualBlockBytes / 4) + row * (kColBlock / 2) + (col >> 1)],
-              val << (16 * (col & 1)));
-  });
 }
 
 // key = acc0 + acc1 2^32 (128-bit); rank = (hi + lo 2^-64) / N of the set.
@@ -1369,31 +1177,25 @@ int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *le
                      int plan_only, cudaStream_t st) {
   const int64_t n = P.n_total;
   const unsigned gsets = (unsigned)(P.n_sets < 4096 ? P.n_sets : 4096);
-  const int64_t we = P.n_sets * (int64_t)eps;
-  const int64_t nblk = (we + kScanChunk - 1) / kScanChunk;
-  auto list_scan = [&]() -> int {
-    pdl_launch(list_scan_reduce_kernel, (unsigned)nblk, 256, 0, st, P, we);
-    SAD_LAUNCH_CHECK();
-    pdl_launch(list_scan_top_kernel, 1, 1024, 0, st, P, nblk);
-    SAD_LAUNCH_CHECK();
-    pdl_launch(list_scan_down_kernel, (unsigned)nblk, 256, 0, st, P, we, plan_only);
-    SAD_LAUNCH_CHECK();
-    return SAD_OK;
-  };
-  pdl_launch(rank_setup_kernel, 1, 1024, 0, st, d_n, (int32_t)n, P);
+  const bool rem = P.depth_cap >= 1;
+  RankPtrs Q = P;
+  Q.eps = eps;
+  Q.counts = counts;
+  pdl_launch(rank_setup_kernel, 1, 1024, 0, st, d_n, (int32_t)n, Q);
   SAD_LAUNCH_CHECK();
-  if (P.n_sets > 1) {
-    pdl_launch(rank_setmaps_kernel, gsets, 256, 0, st, P);
+  if (Q.n_sets > 1) {
+    pdl_launch(rank_setmaps_kernel, gsets, 256, 0, st, Q);
     SAD_LAUNCH_CHECK();
   }
-  pdl_launch(rank_init_kernel, grid_for(we + kMaxM, 256), 256, 0, st, P, eps, !plan_only);
+  pdl_launch(rank_init_kernel, grid_for(2 * Q.n_pad + kMaxM, 256), 256, 0, st, Q, eps,
+             !plan_only);
   SAD_LAUNCH_CHECK();
   if (!plan_only) {
-    pdl_launch(lengths_kernel, grid_for(n, 256), 256, 0, st, lengths, k, P);
+    pdl_launch(lengths_kernel, grid_for(n, 256), 256, 0, st, lengths, k, Q);
     SAD_LAUNCH_CHECK();
   }
   if (word_max && !plan_only) {
-    pdl_launch(copy_word_max_kernel, grid_for(eps, 256), 256, 0, st, word_max, eps, P);
+    pdl_launch(copy_word_max_kernel, grid_for(eps, 256), 256, 0, st, word_max, eps, Q);
     SAD_LAUNCH_CHECK();
   } else {
     dim3 g((eps + 255) / 256, 1);
@@ -1401,17 +1203,17 @@ int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *le
     if (slices > (n + 63) / 64) slices = (n + 63) / 64;
     if (slices < 1) slices = 1;
     g.y = (unsigned)slices;
-    // the plan counts the excess entries here; a run counts them in the plane kernel
-    pdl_launch(colmax_kernel, g, 256, 0, st, counts, eps, P, plan_only);
+    // the plan counts the remainder's sizes here; a run counts its entries in the plane kernel
+    pdl_launch(colmax_kernel, g, 256, 0, st, counts, eps, Q, plan_only);
     SAD_LAUNCH_CHECK();
   }
-  pdl_launch(colmap_kernel, 1, 1024, 0, st, P, eps, plan_only);
+  pdl_launch(colmap_kernel, 1, 1024, 0, st, Q, eps, plan_only);
   SAD_LAUNCH_CHECK();
-  if (plan_only) return list_scan();
-  if (P.n_sets == 1) {
-    pdl_launch(lensort_scan_kernel, 1, 1024, 0, st, P);
+  if (plan_only) return SAD_OK;
+  if (Q.n_sets == 1) {
+    pdl_launch(lensort_scan_kernel, 1, 1024, 0, st, Q);
     SAD_LAUNCH_CHECK();
-    pdl_launch(lensort_place_kernel, grid_for(P.n_pad, 256), 256, 0, st, lengths, k, P);
+    pdl_launch(lensort_place_kernel, grid_for(Q.n_pad, 256), 256, 0, st, lengths, k, Q);
     SAD_LAUNCH_CHECK();
   } else {
     if (!g_attr_sort) {
@@ -1420,12 +1222,16 @@ int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *le
         return SAD_ERR_CUDA;
       g_attr_sort = true;
     }
-    pdl_launch(lensort_sets_kernel, gsets, kSortThreads, kSortSmem, st, lengths, k, P);
+    pdl_launch(lensort_sets_kernel, gsets, kSortThreads, kSortSmem, st, lengths, k, Q);
     SAD_LAUNCH_CHECK();
   }
-  if (P.depth_cap >= 1 && P.depth_cap <= kTabDepth && (eps & 3) == 0 &&
-      (reinterpret_cast<uintptr_t>(counts) & 15) == 0 && (P.k_cap & 31) == 0) {
-    const int64_t warps = P.n_pad;
+  if (rem && Q.bm_cols > 0) {
+    pdl_launch(bitmap_zero_kernel, (unsigned)num_sms() * 8, 256, 0, st, Q);
+    SAD_LAUNCH_CHECK();
+  }
+  if (rem && (eps & 3) == 0 && (reinterpret_cast<uintptr_t>(counts) & 15) == 0 &&
+      (Q.k_cap & 31) == 0) {
+    const int64_t warps = Q.n_pad;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, planes_stream_kernel, 256, 0) !=
         cudaSuccess)
@@ -1433,7 +1239,7 @@ int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *le
     const int64_t cap = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
     const int64_t want = (warps + 7) / 8;
     pdl_launch(planes_stream_kernel, (unsigned)(want < cap ? want : cap), 256, 0, st, counts, eps,
-               P);
+               Q);
     SAD_LAUNCH_CHECK();
   } else {
     const size_t smem = sizeof(uint16_t) * (size_t)eps * kPlaneRows;
@@ -1445,54 +1251,28 @@ int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *le
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, planes_kernel, 256, smem) !=
         cudaSuccess)
       return SAD_ERR_CUDA;
-    const int64_t groups = P.n_pad / kPlaneRows;
+    const int64_t groups = Q.n_pad / kPlaneRows;
     const int64_t cap = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
     pdl_launch(planes_kernel, (unsigned)(groups < cap ? groups : cap), 256, smem, st, counts, eps,
-               P);
+               Q);
     SAD_LAUNCH_CHECK();
   }
-  if (P.depth_cap >= 1 && P.list_cap > 0) {
-    pdl_launch(promote_weight_kernel, grid_for(eps, 256), 256, 0, st, P, eps);
+  if (rem) {
+    const int64_t nblk = Q.n_pad / kColBlock;
+    pdl_launch(rem_depth_kernel, (unsigned)(nblk < 65535 ? nblk : 65535), kRemThreads, 0, st, Q);
     SAD_LAUNCH_CHECK();
-    const int staged = eps <= 16384 ? 1 : 0;
-    const size_t smem = staged ? sizeof(int64_t) * (size_t)eps : 0;
-    if (staged && cudaFuncSetAttribute(promote_select_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem) != cudaSuccess)
-      return SAD_ERR_CUDA;
-    pdl_launch(promote_select_kernel, 1, 1024, smem, st, P, eps, staged);
+    pdl_launch(rem_scan_kernel, 1, 1024, 0, st, Q);
     SAD_LAUNCH_CHECK();
-    pdl_launch(promote_apply_kernel, grid_for(P.list_cap, 256), 256, 0, st, P, eps);
-    SAD_LAUNCH_CHECK();
-  }
-  int rc = list_scan();
-  if (rc) return rc;
-  if (P.depth_cap >= 1 && P.list_cap > 0) {
-    pdl_launch(group_lists_kernel, grid_for(P.list_cap, 256), 256, 0, st, P, eps);
+    pdl_launch(rem_scatter_kernel, grid_for(Q.list_cap, 256), 256, 0, st, Q);
     SAD_LAUNCH_CHECK();
   }
   {
     // one set: a CTA per column group; batches: a few per set
     const int64_t groups1 = ((n + kColBlock - 1) / kColBlock + kGroupCols - 1) / kGroupCols;
-    dim3 g((unsigned)(P.n_sets == 1 ? (groups1 > 0 ? groups1 : 1) : 4), gsets);
-    pdl_launch(tiles_kernel, g, 256, 0, st, P);
+    dim3 g((unsigned)(Q.n_sets == 1 ? (groups1 > 0 ? groups1 : 1) : 4), gsets);
+    pdl_launch(tiles_kernel, g, 256, 0, st, Q);
   }
   SAD_LAUNCH_CHECK();
-  if (P.depth_cap >= 1 && P.block_cap > 0) {
-    // the residual only exists when the planes are cut below the largest count
-    const int identity = P.block_cap >= P.tiles_total ? 1 : 0;
-    const unsigned gw = (unsigned)(we < num_sms() * 8 ? we : num_sms() * 8);
-    if (!identity) {
-      pdl_launch(residual_mark_kernel, gw, 256, 0, st, P, eps);
-      SAD_LAUNCH_CHECK();
-    }
-    pdl_launch(residual_scan_kernel, 1, 1024, 0, st, P, identity);
-    SAD_LAUNCH_CHECK();
-    pdl_launch(residual_zero_kernel, (unsigned)num_sms() * 8, 256, 0, st, P);
-    SAD_LAUNCH_CHECK();
-    pdl_launch(residual_add_kernel, gw, 256, 0, st, P, eps);
-    SAD_LAUNCH_CHECK();
-  }
   return SAD_OK;
 }
 

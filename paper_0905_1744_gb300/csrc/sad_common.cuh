@@ -33,29 +33,41 @@ constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // --------------------------------------------------------- workspace hdr ----
 // The first 256 bytes of every workspace.
-// entries per block of the (set, word) list scans
-constexpr int kScanChunkWords = 1024;
-// plane depths up to which the planes are written from a (threshold, word) -> column table
-constexpr int kTabDepth = 8;
+// Plane depth. A rank plan of depth D >= 1 keeps the threshold sections
+// 1..min(D, t_max) (at most kMaxPlaneDepth) as planes; what the planes of a tile
+// do not cover comes from the remainder lists (see rank_prep.cu).
+constexpr int kMaxPlaneDepth = 8;
+// thresholds above the plane depth that the remainder's bitmap still holds; counts
+// beyond (kTabDepth at most) are remainder entries of their own kind (heavy)
+constexpr int kBitExtra = 4;
+// (threshold, word) -> column table rows
+constexpr int kTabDepth = 16;
+// per-row remainder profile: entries by the first depth d* that covers them
+// (1..D, D + 1 = none), then the heavy entries
+constexpr int kProf = kMaxPlaneDepth + 2;
+// default remainder budget: entries per column block the GEMM epilogue stages
+constexpr int kRemBudgetDefault = 768;
 
 struct WsHeader {
   int32_t status;        // first recorded sad_status (0 = none)
   int32_t detail;        // optional detail of the error (e.g. offending index)
-  int64_t k_eff;         // plane columns the data needs at the chosen depth (kmer_rank)
+  int64_t k_eff;         // plane columns of the kept sections (kmer_rank)
   int32_t k_pad;         // k_eff rounded up to kKCols
   int32_t t_max;         // largest count of any word in any sequence
   int32_t n_tiles;       // GEMM tiles scheduled
-  int32_t depth;         // planes kept per word (t_max when nothing is cut)
+  int32_t depth;         // threshold sections kept as planes (t_max when nothing is cut)
   unsigned long long k_chunks;  // sum over tiles of their K chunks (executed MMA work)
-  int64_t list_total;    // (sequence, word) entries with a count above depth
-  int64_t pairs_total;   // residual pair contributions
-  int32_t n_blocks;      // residual tiles (dense 128 x 128 blocks) in use
+  int64_t list_total;    // (sequence, word) entries counted twice or more
+  int64_t rem_bound;     // plan: sum over those of min(c, T_b) - 1 (remainder entries bound)
+  int64_t heavy_total;   // plan: entries counted more than T_b times
+  int32_t bm_cols;       // bitmap columns: (word, threshold) with 2 <= t <= T_b
   int32_t m_max;         // largest m = L - k + 1 of the set
-  unsigned long long flat_count;  // excess entries appended by the plane kernel
-  int64_t items_total;   // residual work items (pairs of list chunks)
-  int32_t n_promoted;    // words given a plane of threshold depth + 1 in the K padding
-  int32_t k_ext;         // K extent of tiles whose two row blocks both reach depth + 1
-  int32_t pad[42];
+  unsigned long long flat_count;  // entries appended by the plane kernel
+  int64_t rem_entries;   // remainder entries in use (bitmap columns listed per row)
+  int64_t heavy_entries; // heavy remainder entries in use
+  int32_t t_bits;        // T_b: largest threshold held in the bitmap
+  int32_t rem_blocks;    // column blocks whose plane depth is below their largest count
+  int32_t pad[38];
 };
 static_assert(sizeof(WsHeader) == 256, "header is 256 bytes");
 
@@ -78,13 +90,19 @@ __host__ __device__ __forceinline__ bool item_less(const Item &a, const Item &b)
 
 // Capacities of the data-dependent regions of a rank workspace.
 struct RankCaps {
-  int32_t depth;         // planes kept per word; 0 = all (no residual)
+  int32_t depth;         // plane depth D; 0 = all sections, no remainder
+  int32_t budget;        // remainder entries per column block (0 = kRemBudgetDefault)
   int64_t k_cap;         // plane columns
-  int64_t list_cap;      // excess entries (sequence, word) with count > depth
-  int64_t block_cap;     // residual blocks of kRowBlock x kColBlock u16
+  int64_t list_cap;      // entries (sequence, word) counted twice or more
+  int64_t rem_cap;       // remainder entries (bitmap columns)
+  int64_t heavy_cap;     // heavy remainder entries
+  int64_t bm_cols;       // bitmap columns
 };
 
-constexpr size_t kResidualBlockBytes = 2 * kRowBlock * kColBlock;  // u16 per pair of a tile
+// Largest threshold the remainder bitmap holds for a plan of depth D >= 1.
+__host__ __device__ constexpr int32_t t_bits_of(int32_t depth) {
+  return depth + kBitExtra < kTabDepth ? depth + kBitExtra : kTabDepth;
+}
 
 // One set of a (possibly batched) rank call, built on the device by rank_setup.
 // Sets are consecutive in the input order; each set's stored rows are a
@@ -132,10 +150,9 @@ inline RankShape shape_single(int64_t n) {
 
 // Offsets of the rank workspace regions (bytes from the workspace base).
 struct RankLayout {
-  size_t sets, seq_set, row_set, T, secend, thist, coltab, promcol, weight, mhist, perm, rec,
-      recw, depth, tiles,
-      acc, cnt_gt, list_off, item_off, cursor, tile_of, block_of, sortbuf, scanblk, colmap, lists,
-      flat, planes, rblocks;
+  size_t sets, seq_set, row_set, T, secend, thist, coltab, dstar, mhist, perm, rec, recw,
+      depth, bdepth, tiles, acc, prof, rowrem, blkrem, cursor, sortbuf, scanblk, colmap, flat,
+      rem, heavy, planes, bitmap;
   size_t fixed_bytes;    // everything that does not depend on the capacities
   size_t bytes;          // total
   RankShape shape;
@@ -149,7 +166,7 @@ inline RankLayout rank_layout(const RankShape &sh, int64_t eps, const RankCaps &
   size_t o = sizeof(WsHeader);
   auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes, 256); return r; };
   auto nz = [](int64_t x) { return (size_t)(x > 0 ? x : 1); };
-  const size_t we = (size_t)sh.n_sets * (size_t)eps;  // (set, word) entries
+  const size_t blocks = nz(sh.rows_total / kRowBlock);
   L.sets = take(sizeof(RankSet) * nz(sh.n_sets));
   L.seq_set = take(sizeof(int32_t) * nz(sh.n_total));
   L.row_set = take(sizeof(int32_t) * nz(sh.rows_total));
@@ -157,36 +174,34 @@ inline RankLayout rank_layout(const RankShape &sh, int64_t eps, const RankCaps &
   L.secend = take(sizeof(int32_t) * (kMaxM + 2));
   L.thist = take(sizeof(int32_t) * (kMaxM + 2));
   L.coltab = take(sizeof(int32_t) * eps * kTabDepth);
-  L.promcol = take(sizeof(int32_t) * eps);
-  L.weight = take(sizeof(int64_t) * eps);
   L.mhist = take(sizeof(int32_t) * (kMaxM + 2));
   L.perm = take(sizeof(int32_t) * nz(sh.rows_total));
   L.rec = take(16 * nz(sh.rows_total));
   L.recw = take(8 * nz(sh.rows_total));
-  L.depth = take(sizeof(int32_t) * nz(sh.rows_total / kRowBlock));
+  L.depth = take(sizeof(int32_t) * blocks);
+  L.bdepth = take(sizeof(int32_t) * blocks);
   L.tiles = take(2 * sizeof(int32_t) * nz(sh.tiles_total));
   L.acc = take(3 * sizeof(uint64_t) * nz(sh.n_total));
-  L.cnt_gt = take(sizeof(int32_t) * we);
-  L.list_off = take(sizeof(int64_t) * (we + 1));
-  L.item_off = take(sizeof(int64_t) * (we + 1));
-  L.cursor = take(sizeof(int32_t) * we);
-  L.tile_of = take(sizeof(int32_t) * nz(sh.tileof_total));
-  L.block_of = take(sizeof(int32_t) * nz(sh.tiles_total));
+  L.prof = take(sizeof(uint32_t) * kProf * nz(sh.rows_total));
+  L.rowrem = take(2 * sizeof(int32_t) * nz(sh.rows_total));
+  L.blkrem = take(2 * sizeof(int64_t) * (blocks + 1));
+  L.cursor = take(2 * sizeof(int32_t) * nz(sh.rows_total));
   L.sortbuf = take(sh.n_sets > 1 ? 2 * sizeof(Item) * nz(sh.n_total) : 256);
-  L.scanblk = take(2 * sizeof(int64_t) * (we / kScanChunkWords + 1));
+  L.scanblk = take(2 * sizeof(int64_t) * (blocks / 1024 + 2));
   L.fixed_bytes = o;
-  L.colmap = take(sizeof(int32_t) * (size_t)(caps.k_cap > 0 ? caps.k_cap : 1));
-  L.lists = take(2 * sizeof(int32_t) * (size_t)(caps.list_cap > 0 ? caps.list_cap : 1));
-  L.flat = take(2 * sizeof(int32_t) * (size_t)(caps.list_cap > 0 ? caps.list_cap : 1));
+  L.colmap = take(sizeof(int32_t) * nz(caps.k_cap));
+  L.dstar = take(nz(caps.k_cap));
+  L.flat = take(2 * sizeof(int32_t) * nz(caps.list_cap));
+  L.rem = take(sizeof(uint32_t) * nz(caps.rem_cap));
+  L.heavy = take(2 * sizeof(int32_t) * nz(caps.heavy_cap));
   o = align_up(o, 1024);
   L.planes = o;  // rows_total x K_cap 4-bit values
   o = align_up(o + (size_t)sh.rows_total * (size_t)caps.k_cap / 2, 1024);
-  L.rblocks = o;
-  o += kResidualBlockBytes * (size_t)caps.block_cap;
+  L.bitmap = o;  // bm_cols x rows_total bits
+  o += (size_t)(caps.bm_cols > 0 ? caps.bm_cols : 0) * (size_t)(sh.rows_total / 8);
   L.bytes = align_up(o, 256);
   return L;
 }
-
 
 // One set of a (possibly batched) partition, built on the device by part_setup.
 // Sets are consecutive in the item order.
@@ -348,10 +363,36 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   return ok != 0;
 }
 
+// Non-blocking test of the phase with the given parity.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Budgets below this are a test's: every check of the barrier is non-blocking
+// and the clock is read after each, so the budget runs out even where a blocking
+// try_wait would have outlasted it.
+constexpr uint64_t kShortWaitNs = 1000000ull;
+
 // Bounded wait for the phase with the given parity to complete. Gives up when
 // *abort becomes non-zero or after `budget_ns` of wall time; returns false then.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
                                                   volatile int *abort, uint64_t budget_ns) {
+  if (budget_ns < kShortWaitNs) {
+    const uint64_t t0 = globaltimer_ns();
+    while (!mbar_test_wait(bar, parity)) {
+      if (*abort) return false;
+      if (globaltimer_ns() - t0 > budget_ns) return false;
+    }
+    return true;
+  }
   if (mbar_try_wait(bar, parity)) return true;
   uint64_t t0 = globaltimer_ns();
   for (uint32_t it = 1;; ++it) {

@@ -24,12 +24,14 @@ _DEVICE_TYPE = "cuda"       # where every tensor handed to the library must live
 
 
 class RankPlan(ctypes.Structure):
-    """sad_rank_plan: depth in; sizes and capacities out (see include/sad.h)."""
-    _fields_ = [("depth", ctypes.c_int32), ("t_max", ctypes.c_int32),
+    """sad_rank_plan: depth and budget in; sizes and capacities out (see include/sad.h)."""
+    _fields_ = [("depth", ctypes.c_int32), ("budget", ctypes.c_int32),
+                ("t_max", ctypes.c_int32), ("t_bits", ctypes.c_int32),
                 ("k_eff", ctypes.c_int64), ("list_entries", ctypes.c_int64),
-                ("residual_pairs", ctypes.c_int64), ("k_cap", ctypes.c_int64),
-                ("list_cap", ctypes.c_int64), ("block_cap", ctypes.c_int64),
-                ("ws_bytes", ctypes.c_size_t)]
+                ("rem_bound", ctypes.c_int64), ("heavy_entries", ctypes.c_int64),
+                ("k_cap", ctypes.c_int64), ("list_cap", ctypes.c_int64),
+                ("rem_cap", ctypes.c_int64), ("heavy_cap", ctypes.c_int64),
+                ("bm_cols", ctypes.c_int64), ("ws_bytes", ctypes.c_size_t)]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
@@ -251,26 +253,26 @@ def kmer_count(codes: torch.Tensor, offsets: torch.Tensor, k: int = 3, alphabet:
 
 
 def kmer_rank_plan(counts: torch.Tensor, k: int = 3, alphabet: int = 20, depth: int = 0,
-                   ws: Workspace | None = None, stream=None) -> RankPlan:
+                   ws: Workspace | None = None, stream=None, budget: int = 0) -> RankPlan:
     """Sizes and capacities for kmer_rank at plane depth ``depth`` (0 = all
-    planes). Synchronous."""
+    planes) with ``budget`` remainder entries per column block (0 = default).
+    Synchronous."""
     _need_counts(counts, k, alphabet, "kmer_rank_plan")
     n = counts.shape[0]
     ws = ws or Workspace(counts.device)
     ws.ensure(workspace_bytes(OP_RANK, n, k, alphabet, depth=0))
-    plan = RankPlan(depth=int(depth))
+    plan = RankPlan(depth=int(depth), budget=int(budget))
     _check(_load().kmer_rank_plan(_ptr(counts), n, k, alphabet, ctypes.byref(plan),
                                   _ptr(ws.buf), ws.nbytes, _stream(stream)), "kmer_rank_plan")
     return plan
 
 
 def kmer_rank_plan_bound(n: int, total_len: int, k: int = 3, alphabet: int = 20,
-                         depth: int = 1) -> RankPlan:
+                         depth: int = 1, budget: int = 0) -> RankPlan:
     """Capacities for kmer_rank at plane depth ``depth`` >= 1 that hold for any
     counts of ``n`` sequences of ``total_len`` residues in all: no device work and
-    no synchronisation (K_cap = eps depth, excess entries <= windows / (depth + 1),
-    a residual block per tile)."""
-    plan = RankPlan(depth=int(depth))
+    no synchronisation (bounds from the number of windows; see include/sad.h)."""
+    plan = RankPlan(depth=int(depth), budget=int(budget))
     _check(_load().kmer_rank_plan_bound(int(n), int(total_len), k, alphabet, ctypes.byref(plan)),
            "kmer_rank_plan_bound")
     return plan
@@ -376,7 +378,7 @@ def rank_info(ws: Workspace, stream=None) -> dict:
     info = (ctypes.c_int64 * 16)()
     _check(_load().sad_rank_info(_ptr(ws.buf), info, _stream(stream)), "sad_rank_info")
     keys = ("status", "k_eff", "k_pad", "t_max", "tiles", "k_chunks", "depth",
-            "residual_pairs", "residual_tiles")
+            "rem_entries", "rem_blocks", "heavy_entries", "bm_cols")
     return {k: int(info[i]) for i, k in enumerate(keys)}
 
 

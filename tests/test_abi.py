@@ -39,7 +39,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_host_only_queries(lib):
     lib.sad_abi_version.restype = ctypes.c_int
-    assert lib.sad_abi_version() == 4
+    assert lib.sad_abi_version() == 5
     lib.sad_status_string.restype = ctypes.c_char_p
     lib.sad_status_string.argtypes = [ctypes.c_int]
     assert lib.sad_status_string(0) == b"ok"
@@ -71,11 +71,15 @@ def test_argument_errors_need_no_gpu(lib):
 
 
 class _Plan(ctypes.Structure):
-    _fields_ = [("depth", ctypes.c_int32), ("t_max", ctypes.c_int32),
+    """sad_rank_plan as include/sad.h declares it (written out here, independently
+    of the binding's copy)."""
+    _fields_ = [("depth", ctypes.c_int32), ("budget", ctypes.c_int32),
+                ("t_max", ctypes.c_int32), ("t_bits", ctypes.c_int32),
                 ("k_eff", ctypes.c_int64), ("list_entries", ctypes.c_int64),
-                ("residual_pairs", ctypes.c_int64), ("k_cap", ctypes.c_int64),
-                ("list_cap", ctypes.c_int64), ("block_cap", ctypes.c_int64),
-                ("ws_bytes", ctypes.c_size_t)]
+                ("rem_bound", ctypes.c_int64), ("heavy_entries", ctypes.c_int64),
+                ("k_cap", ctypes.c_int64), ("list_cap", ctypes.c_int64),
+                ("rem_cap", ctypes.c_int64), ("heavy_cap", ctypes.c_int64),
+                ("bm_cols", ctypes.c_int64), ("ws_bytes", ctypes.c_size_t)]
 
 
 def _bound(lib, n, total_len, depth, k=3, alphabet=20):
@@ -89,13 +93,19 @@ def _bound(lib, n, total_len, depth, k=3, alphabet=20):
 
 def test_rank_plan_bound_is_host_only(lib):
     rc, plan = _bound(lib, 20000, 6_000_000, 1)
+    w = 6_000_000 - 2 * 20000                            # windows
     assert rc == 0
     assert plan.k_cap == 8192                            # eps * 1 rounded up to 256
-    assert plan.list_cap == (6_000_000 - 2 * 20000) // 2
-    assert plan.block_cap == 157 * 158 // 2              # every upper-triangle tile
-    assert plan.ws_bytes > 20096 * 8192 // 2 + 32768 * plan.block_cap
-    assert plan.k_eff == -1 and plan.t_max == -1
+    assert plan.list_cap == w // 2
+    assert plan.rem_cap == w - 20000
+    assert plan.heavy_cap == w // 6                      # T_b = 1 + 4
+    assert plan.bm_cols == 4 * 8000                      # sections 2..5, eps words each
+    assert plan.ws_bytes > 20096 * 8192 // 2 + plan.bm_cols * 20096 // 8
+    assert plan.k_eff == -1 and plan.t_max == -1 and plan.t_bits == -1
     assert _bound(lib, 20000, 6_000_000, 2)[1].k_cap == 16128       # 16000 rounded up
+    assert _bound(lib, 20000, 6_000_000, 12)[1].k_cap == 64000      # at most 8 sections
+    small = _bound(lib, 10, 1000, 1)[1]                  # few windows bound the bitmap
+    assert small.bm_cols == sum(min(8000, 980 // t) for t in range(2, 6))
     assert _bound(lib, 10, 100, 0)[0] == 1               # all planes need the word maxima
     assert _bound(lib, -1, 100, 1)[0] == 1
     assert _bound(lib, 10, 100, 1, k=9)[0] == 5
@@ -106,9 +116,11 @@ def test_rank_plan_bound_is_host_only(lib):
 
 @pytest.mark.parametrize("depth", [1, 2, 3])
 def test_rank_plan_bound_holds_for_the_data(lib, oracle_mod, depth):
-    """The capacities bound what the data need: K_eff = sum_tau min(T_tau, D) and
-    the excess entries #{(x, tau): c_x(tau) > D} (counted here from the oracle's
-    counts), on sets with long repeats and on a family set."""
+    """The capacities bound what the data need (counted here from the oracle's
+    counts): K_eff = sum_tau min(T_tau, D), the entries counted twice or more, the
+    remainder entries sum of min(c, T_b) - 1 over them, the counts above T_b and
+    the bitmap columns sum_{t=2..T_b} #{tau : T_tau >= t}; on sets with long
+    repeats and on a family set."""
     import numpy as np
     from paper_0905_1744_gb300 import datagen
     sets = [datagen.from_strings(["A" * 3000, "AC" * 900, "ACD" * 400, "W" * 5, "ACDEFGHIK"]),
@@ -121,8 +133,13 @@ def test_rank_plan_bound_holds_for_the_data(lib, oracle_mod, depth):
         c = oracle_mod.kmer_count(s.codes, s.offsets, 3, alphabet)
         rc, plan = _bound(lib, s.n, int(s.codes.size), depth, 3, alphabet)
         assert rc == 0
+        tb = min(depth + 4, 16)
         assert np.minimum(c.max(axis=0), depth).sum() <= plan.k_cap
-        assert int((c > depth).sum()) <= plan.list_cap
+        assert int((c >= 2).sum()) <= plan.list_cap
+        assert int((np.minimum(c, tb) - 1)[c >= 2].sum()) <= plan.rem_cap
+        assert int((c > tb).sum()) <= plan.heavy_cap
+        T = c.max(axis=0)
+        assert sum(int((T >= t).sum()) for t in range(2, tb + 1)) <= plan.bm_cols
 
 
 def test_every_kernel_waits_for_its_predecessor_first():
@@ -185,7 +202,7 @@ def test_every_entry_point_checks_its_arguments_on_the_host():
     assert L.kmer_rank_plan(None, 10, 3, 20, byref(plan), d, 0, None) == WS
     assert plan.ws_bytes > 0
     # kmer_rank: a plan's capacities are checked, then the workspace against them
-    good = sad.RankPlan(depth=1, k_cap=8192, list_cap=0, block_cap=0)
+    good = sad.RankPlan(depth=1, k_cap=8192, list_cap=0, rem_cap=0)
     args = (d, d, None, 300, 3, 20)
     outs = (d, d, None)
     assert L.kmer_rank(*args, byref(good), *outs, d, 0, None) == WS
@@ -228,7 +245,8 @@ def test_every_entry_point_checks_its_arguments_on_the_host():
     dist = lambda plan, delta=10, ws=1 << 30: L.kmer_rank_dist(  # noqa: E731
         d, d, None, 10, 3, 20, delta, plan, None, d, d, None, d, ws, None)
     assert dist(byref(good), delta=0) == INV
-    assert dist(byref(sad.RankPlan(depth=1, k_cap=8192, block_cap=-1))) == INV
+    assert dist(byref(sad.RankPlan(depth=1, k_cap=8192, rem_cap=-1))) == INV
+    assert dist(byref(sad.RankPlan(depth=1, k_cap=8192, budget=-1))) == INV
     assert dist(byref(good), ws=0) == WS
     assert L.sad_ln_q(None, -1, None, None) == INV
     assert L.sad_ln_q(None, 5, None, None) == INV

@@ -93,8 +93,7 @@ def test_c2_counts_in_full(sad, c2_oracle):
 def test_c2_bench_path_every_key_and_bucket(sad, c2_oracle, depth):
     s, _, ref = c2_oracle
     res = bench_path(sad, s, depth)
-    if depth:
-        assert res["depth"] == min(depth, res["t_max"])
+    assert res["depth"] == depth
     assert_c2(res, ref, f"depth {depth}")
 
 

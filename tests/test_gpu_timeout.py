@@ -32,7 +32,8 @@ def dev(a):
 
 @pytest.mark.parametrize("depth", (0, 1))
 def test_short_wait_budget_returns_timeout_then_recovers(sad, oracle_mod, depth):
-    s = datagen.family_set(4, 150, lambda r: int(r.integers(120, 700)), p=4, seed=11,
+    # long sequences: each tile's MMAs take microseconds, longer than the budget
+    s = datagen.family_set(6, 150, lambda r: int(r.integers(600, 1800)), p=4, seed=11,
                            stream=21)
     codes, offsets = dev(s.codes), dev(s.offsets)
     lengths = dev(s.lengths.astype(np.int32))

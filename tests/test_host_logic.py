@@ -74,12 +74,12 @@ def test_latency_stats():
 
 # ---------------------------------------------------------------- autotuner ---
 
-def _fake_plans(monkeypatch, t_max, ws_bytes, residual_pairs=1000):
+def _fake_plans(monkeypatch, t_max, ws_bytes, rem_bound=1000):
     calls = []
 
     def plan(counts, k=3, alphabet=20, depth=0, ws=None, stream=None):
         calls.append(depth)
-        return types.SimpleNamespace(depth=depth, t_max=t_max, residual_pairs=residual_pairs,
+        return types.SimpleNamespace(depth=depth, t_max=t_max, rem_bound=rem_bound,
                                      ws_bytes=ws_bytes(depth))
     monkeypatch.setattr(autotune.sad, "kmer_rank_plan", plan)
     return calls
@@ -123,7 +123,7 @@ def test_choose_depth_cache_by_size_class(monkeypatch, tmp_path):
     counts = torch.zeros(1000, 1, dtype=torch.int32)
     best, trials = autotune.choose_depth(counts, None, _FakeWs())
     assert best == 1 and trials
-    # same size class (log2 N, t_max, log2 residual pairs): answered from the cache
+    # same size class (log2 N, t_max, log2 remainder bound): answered from the cache
     best2, trials2 = autotune.choose_depth(torch.zeros(1023, 1, dtype=torch.int32), None,
                                            _FakeWs())
     assert best2 == 1 and trials2 == {}
@@ -131,7 +131,7 @@ def test_choose_depth_cache_by_size_class(monkeypatch, tmp_path):
     autotune.save_cache(path)
     with open(path) as f:
         saved = json.load(f)
-    plan1 = types.SimpleNamespace(t_max=3, residual_pairs=1000)
+    plan1 = types.SimpleNamespace(t_max=3, rem_bound=1000)
     assert saved == {autotune.signature(1000, plan1): 1}
     autotune._cache.clear()
     autotune.load_cache(path)
@@ -140,10 +140,10 @@ def test_choose_depth_cache_by_size_class(monkeypatch, tmp_path):
 
 
 def test_signature_buckets():
-    p = types.SimpleNamespace(t_max=5, residual_pairs=0)
+    p = types.SimpleNamespace(t_max=5, rem_bound=0)
     assert autotune.signature(1024, p) == autotune.signature(2047, p) == "n10_t5_r0"
     assert autotune.signature(2048, p) == "n11_t5_r0"
-    assert autotune.signature(0, types.SimpleNamespace(t_max=1, residual_pairs=3)) == "n0_t1_r1"
+    assert autotune.signature(0, types.SimpleNamespace(t_max=1, rem_bound=3)) == "n0_t1_r1"
 
 
 # ------------------------------------------------------------ bench helpers ---
