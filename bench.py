@@ -110,6 +110,8 @@ def parse(argv=None):
     ap.add_argument("--impl", default="sad", choices=["sad", "reference"])
     ap.add_argument("--config", type=int, default=3, choices=[1, 2, 3],
                     help="the main line's workload (default: the largest, N = 100000)")
+    ap.add_argument("--subset", type=int, default=0,
+                    help="profiling: evenly spaced N sequences of the workload instead of all")
     ap.add_argument("--no-extra-configs", action="store_true",
                     help="skip the c1/c2 lines (and the legs that run on the paper-scale set)")
     ap.add_argument("--seed", type=int, default=0)
@@ -587,6 +589,9 @@ def measure_config(cfg: int, args, dev, world: int, steps: int, warmup: int,
     from paper_0905_1744_gb300 import autotune, sad
 
     s = datagen.config(cfg, args.seed)
+    if args.subset and args.subset < s.n:
+        # every (n / subset)-th sequence: the same family and length mix, fewer members
+        s = s.take(np.linspace(0, s.n - 1, args.subset).astype(np.int64))
     n, p = s.n, s.p
     pairs = n * (n - 1) / 2
     stream = torch.cuda.current_stream()
@@ -819,7 +824,8 @@ def run_sad(args):
             "ms_per_step": main["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "e2m1 0/1 planes (fp4), f32 acc (exact), u128 keys",
             "data": "synthetic",
-            "config": bench_config(args.config, s, args.seed),
+            "config": {**bench_config(args.config, s, args.seed),
+                       **({"subset": args.subset} if args.subset else {})},
             "parallelism": "replicas" if world > 1 else "single GPU",
             "gpu_launches": main["launches"],
             "autotune": main["autotune"],

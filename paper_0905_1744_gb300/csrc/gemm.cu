@@ -37,15 +37,16 @@
 //               that lands as two 128-row tiles with the 128-byte swizzle; a
 //               3-stage mbarrier ring (64 KB a stage: the cost of a stage is
 //               mostly fixed, so fewer, larger stages run faster)
-//   warp 1      MMA issuer: 8 x (M=128, N=128, K=64) per stage into one of two
-//               TMEM accumulators (2 x 128 columns), commit frees the stage
+//   warp 1      MMA issuer: 8 x (M=128, N=128, K=64) per stage into one of three
+//               TMEM accumulators (3 x 128 columns), commit frees the stage
 //   warp 2      TMEM allocator, then with warp 3 the remainder builder
 //   warps 4-7   also fill the scale-factor columns of TMEM with 1.0 before the
 //               first MMA
 //   warps 4-11  epilogue: tcgen05.ld of the accumulator (lane quadrant = warp % 4,
 //               two warps per quadrant, each on half of the 128 columns)
-// The double TMEM accumulator lets the epilogue of one tile overlap the MMAs of
-// the next.
+// A tile's remainder chunks are issued after the next tile's plane chunks (the
+// builder prepares them meanwhile); the three TMEM accumulators let the epilogue of
+// one tile overlap the MMAs of the next two.
 //
 // Every wait is bounded (globaltimer; the budget of the main-loop waits is
 // P.wait_ns, 2 s unless a test shortens it); on a timeout the CTA records
@@ -70,8 +71,11 @@ constexpr uint32_t kTxBytes = kABytes + kBBytes;
 constexpr int kThreads = 384;
 constexpr int kEpiThreads = 256;  // warps 4-11: two per TMEM lane quadrant
 constexpr uint32_t kTmemCols = 512;
-// TMEM columns: accumulators [0, 2 kColBlock), then the scale factors of A and B
-constexpr uint32_t kSfaCol = 2 * kColBlock;
+// three accumulators: a tile's remainder chunks run after the next tile's plane
+// chunks, and the epilogue of a tile overlaps the MMAs of the two after it
+constexpr int kAccs = 3;
+// TMEM columns: accumulators [0, 3 kColBlock), then the scale factors of A and B
+constexpr uint32_t kSfaCol = kAccs * kColBlock;
 constexpr uint32_t kSfbCol = kSfaCol + 32;
 constexpr uint32_t kSfCols = 64;  // filled with 1.0
 static_assert(kSfaCol + kSfCols <= kTmemCols, "TMEM columns");
@@ -105,8 +109,8 @@ struct GemmSmem {
   uint64_t full[kStages];
   uint64_t empty[kStages];
   uint64_t bfree[kStages];  // the producer hands a free slot to the builder
-  uint64_t tfull[2];
-  uint64_t tempty[2];
+  uint64_t tfull[kAccs];
+  uint64_t tempty[kAccs];
   uint64_t drain;
   uint32_t tmem_base;
   int32_t abort;
@@ -173,11 +177,6 @@ __device__ __forceinline__ void tile_at(const RankPtrs &P, const RectArgs &X, in
   }
 }
 
-// Stages of a tile: its plane chunks, then its remainder chunks, kCps to a stage.
-__device__ __forceinline__ int32_t stages_of(int32_t nk, int32_t nx) {
-  return (nk + kCps - 1) / kCps + (nx + kCps - 1) / kCps;
-}
-
 // 32 x 32 bit transpose across a warp: lane l holds row l (bit b = column b); on
 // return lane u holds column u (bit l = row l). Recursive swap of the off-diagonal
 // blocks of 16, 8, 4, 2 and 1.
@@ -206,18 +205,20 @@ __device__ __forceinline__ uint32_t bit_range(int32_t a, int32_t b) {
 }
 
 // One remainder K chunk x (entries [256 x, 256 x + 256) of the column block's list,
-// rn entries in all) into the operand tiles a (128 rows u of the tile) and b (128
+// rn entries in all) as the operand tiles a (128 rows u of the tile) and b (128
 // rows v = tile columns), 128 bytes a row, 16-byte unit j of row r at unit j ^ (r & 7)
 // (the 128-byte swizzle). A unit holds 32 entries of one row as 4-bit values. Row u
 // of a: the bitmap bits of the tile's rows, transposed 32 x 32 at a time per warp;
 // row v of b: 1.0 for the entries of column v (a contiguous range).
-__device__ __forceinline__ void build_chunk(const RankPtrs &P, const GemmSmem &S, uint8_t *a,
-                                            uint8_t *b, int32_t x, int32_t rn, bool staged,
-                                            int64_t rbase, int64_t bm_stride, int32_t I,
-                                            uint32_t bt, uint32_t lane) {
+//
+// prep_chunk_a computes this builder thread's 16 units of a into registers (before
+// the ring slot is free); store_chunk writes them and the thread's 16 units of b.
+// Builder warp bw takes the units j = 2 i + bw of every lane quadrant q.
+__device__ __forceinline__ void prep_chunk_a(const RankPtrs &P, const GemmSmem &S, int32_t x,
+                                             int32_t rn, bool staged, int64_t rbase,
+                                             int64_t bm_stride, int32_t I, uint32_t bt,
+                                             uint32_t lane, uint4 (&ua)[16]) {
   const uint32_t bw = bt >> 5;
-  // a: 4 lane quadrants q x 8 units j; builder warp bw takes the units j = 2 i + bw
-  // of every quadrant (16 items), all of whose words are loaded before any is used
   uint32_t w[16];
   if (staged) {
 #pragma unroll
@@ -243,19 +244,28 @@ __device__ __forceinline__ void build_chunk(const RankPtrs &P, const GemmSmem &S
                            : 0u;
   }
 #pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const uint32_t m = warp_transpose32(w[k], lane);  // bit l: entry 32 j + l, row 32 q + lane
+    ua[k] = make_uint4(S.nib[m & 0xFF], S.nib[(m >> 8) & 0xFF], S.nib[(m >> 16) & 0xFF],
+                       S.nib[m >> 24]);
+  }
+}
+
+__device__ __forceinline__ void store_chunk(const GemmSmem &S, uint8_t *a, uint8_t *b,
+                                            const uint4 (&ua)[16], int32_t x, uint32_t bt,
+                                            uint32_t lane) {
+  const uint32_t bw = bt >> 5;
+#pragma unroll
   for (int i = 0; i < 4; ++i) {
     const uint32_t j = 2 * i + bw;
 #pragma unroll
     for (uint32_t q = 0; q < 4; ++q) {
-      const uint32_t m = warp_transpose32(w[4 * i + q], lane);  // bit l: entry 32 j + l
-      const uint32_t r = q * 32 + lane;                         // of row 32 q + lane
-      *reinterpret_cast<uint4 *>(a + r * 128 + ((j ^ (r & 7)) * 16)) =
-          make_uint4(S.nib[m & 0xFF], S.nib[(m >> 8) & 0xFF], S.nib[(m >> 16) & 0xFF],
-                     S.nib[m >> 24]);
+      const uint32_t r = q * 32 + lane;
+      *reinterpret_cast<uint4 *>(a + r * 128 + ((j ^ (r & 7)) * 16)) = ua[4 * i + q];
     }
   }
   // b: rows v, two per builder thread
-#pragma unroll 1
+#pragma unroll
   for (uint32_t v = bt; v < (uint32_t)kColBlock; v += kBuildThreads) {
     const int32_t lo = S.remoff[v] - x * kRemChunk, hi = S.remoff[v + 1] - x * kRemChunk;
 #pragma unroll
@@ -350,7 +360,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&S.empty[s], 1);
       mbar_init(&S.bfree[s], 1);
     }
-    for (int a = 0; a < 2; ++a) {
+    for (int a = 0; a < kAccs; ++a) {
       mbar_init(&S.tfull[a], 1);
       mbar_init(&S.tempty[a], kEpiThreads);
     }
@@ -393,14 +403,19 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (!skip && warp == 0 && lane == 0) {
     // ------------------------------------------------------------ producer --
+    // Position sequence of the CTA (shared with the MMA issuer and the builder): for
+    // each of its tiles in turn, the tile's plane stages, then the remainder stages
+    // of the tile before (after the last tile, its remainder stages).
     int stage = 0;
     uint32_t phase = 0, used = 0, par = 0;
     bool aborted = false;
-    for (int32_t t = blockIdx.x; t < n_tiles && !aborted; t += gridDim.x) {
-      int32_t I, J, nk, nx;
-      tile_at(P, X, rect_nk, t, I, J, nk, nx);
-      const int32_t sk = (nk + kCps - 1) / kCps;
-      for (int32_t kc = 0; kc < sk + (nx + kCps - 1) / kCps; ++kc) {
+    int32_t pnx = 0;  // remainder chunks of the previous tile
+    for (int32_t t = blockIdx.x; !aborted; t += gridDim.x) {
+      const bool have = t < n_tiles;
+      int32_t I = 0, J = 0, nk = 0, nx = 0;
+      if (have) tile_at(P, X, rect_nk, t, I, J, nk, nx);
+      const int32_t sk = have ? (nk + kCps - 1) / kCps : 0;
+      for (int32_t kc = 0; kc < sk + pnx; ++kc) {
         if (!mbar_wait_bounded(&S.empty[stage], phase ^ 1u, abort_flag, wait_ns)) {
           set_abort(S, P.hdr);
           aborted = true;
@@ -410,22 +425,22 @@ __global__ void __launch_bounds__(kThreads, 1)
           // a remainder stage: the slot is free; the builder fills it and arrives on
           // its full barrier (slots are handed over in order, one round at a time)
           mbar_arrive(&S.bfree[stage]);
-          if (++stage == kStages) {
-            stage = 0;
-            phase ^= 1u;
-          }
-          continue;
+          // the copy last made into this slot has been consumed: nothing to drain
+          used &= ~(1u << stage);
+        } else {
+          mbar_arrive_expect_tx(&S.full[stage], kTxBytes);
+          tma_load_3d(S.a[stage], &tmA, &S.full[stage], 0, I * kRowBlock, kc * kCps);
+          tma_load_3d(S.b[stage], &tmB, &S.full[stage], 0, J * kColBlock, kc * kCps);
+          used |= 1u << stage;
+          par = (par & ~(1u << stage)) | (phase << stage);
         }
-        mbar_arrive_expect_tx(&S.full[stage], kTxBytes);
-        tma_load_3d(S.a[stage], &tmA, &S.full[stage], 0, I * kRowBlock, kc * kCps);
-        tma_load_3d(S.b[stage], &tmB, &S.full[stage], 0, J * kColBlock, kc * kCps);
-        used |= 1u << stage;
-        par = (par & ~(1u << stage)) | (phase << stage);
         if (++stage == kStages) {
           stage = 0;
           phase ^= 1u;
         }
       }
+      if (!have) break;
+      pnx = nx;
     }
     // let every copy this thread started land before the CTA exits (after a normal
     // run the MMAs have consumed them all and these waits return at once)
@@ -433,51 +448,76 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (used & (1u << s)) mbar_wait_bounded(&S.full[s], (par >> s) & 1u, &S.never, kDrainBudgetNs);
   } else if (!skip && warp == 1 && lane == 0) {
     // ----------------------------------------------------------------- MMA --
+    // Tile lt accumulates in TMEM accumulator lt % 3: its plane stages, then (after the
+    // next tile's plane stages) its remainder stages, then the commit to tfull.
     const uint32_t idesc = idesc_f4_e2m1(kRowBlock, kColBlock);
     const uint32_t sfa = tmem + kSfaCol, sfb = tmem + kSfbCol;
     int stage = 0;
     uint32_t phase = 0;
     bool aborted = false;
-    int32_t lt = 0;
-    for (int32_t t = blockIdx.x; t < n_tiles && !aborted; t += gridDim.x, ++lt) {
-      int32_t I, J, nk, nx;
-      tile_at(P, X, rect_nk, t, I, J, nk, nx);
-      const int32_t sk = (nk + kCps - 1) / kCps;
-      const uint32_t acc = lt & 1, aph = (lt >> 1) & 1;
-      if (!mbar_wait_bounded(&S.tempty[acc], aph ^ 1u, abort_flag, wait_ns)) {
-        set_abort(S, P.hdr);
-        aborted = true;
-        break;
+    int32_t pnx = 0;
+    auto issue_stage = [&](uint32_t d_tmem, int nsub, bool first) {
+      for (int sub = 0; sub < nsub; ++sub) {
+        const uint64_t adesc = sdesc_kmajor_sw128(smem_u32(S.a[stage] + sub * kSubA));
+        const uint64_t bdesc = sdesc_kmajor_sw128(smem_u32(S.b[stage] + sub * kSubB));
+        // per K chunk 4 MMAs of K = 64 values = 32 bytes per row (2 in 16-byte
+        // descriptor units)
+#pragma unroll
+        for (int kk = 0; kk < kKChunk / 32; ++kk)
+          mma_f4(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, idesc, sfa, sfb,
+                 (first && sub == 0 && kk == 0) ? 0u : 1u);
       }
-      tc_fence_after();
-      const uint32_t d_tmem = tmem + acc * (uint32_t)kColBlock;
-      for (int32_t kc = 0; kc < stages_of(nk, nx); ++kc) {
-        if (!mbar_wait_bounded(&S.full[stage], phase, abort_flag, wait_ns)) {
+      mma_commit(&S.empty[stage]);
+      if (++stage == kStages) {
+        stage = 0;
+        phase ^= 1u;
+      }
+    };
+    int32_t lt = 0;
+    for (int32_t t = blockIdx.x; !aborted; t += gridDim.x, ++lt) {
+      const bool have = t < n_tiles;
+      int32_t nx = 0;
+      if (have) {
+        int32_t I, J, nk;
+        tile_at(P, X, rect_nk, t, I, J, nk, nx);
+        const uint32_t acc = lt % kAccs, aph = (lt / kAccs) & 1;
+        if (!mbar_wait_bounded(&S.tempty[acc], aph ^ 1u, abort_flag, wait_ns)) {
           set_abort(S, P.hdr);
           aborted = true;
           break;
         }
         tc_fence_after();
-        // per K chunk 4 MMAs of K = 64 values = 32 bytes per row (2 in 16-byte
-        // descriptor units); a last chunk past the tile's extent (plane or
-        // remainder) is not used
-        const int nsub = kc < sk ? min(kCps, nk - kc * kCps) : min(kCps, nx - (kc - sk) * kCps);
-        for (int sub = 0; sub < nsub; ++sub) {
-          const uint64_t adesc = sdesc_kmajor_sw128(smem_u32(S.a[stage] + sub * kSubA));
-          const uint64_t bdesc = sdesc_kmajor_sw128(smem_u32(S.b[stage] + sub * kSubB));
-#pragma unroll
-          for (int kk = 0; kk < kKChunk / 32; ++kk)
-            mma_f4(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, idesc, sfa, sfb,
-                   (kc | sub | kk) != 0 ? 1u : 0u);
+        const uint32_t d_tmem = tmem + acc * (uint32_t)kColBlock;
+        const int32_t sk = (nk + kCps - 1) / kCps;
+        for (int32_t kc = 0; kc < sk; ++kc) {
+          if (!mbar_wait_bounded(&S.full[stage], phase, abort_flag, wait_ns)) {
+            set_abort(S, P.hdr);
+            aborted = true;
+            break;
+          }
+          tc_fence_after();
+          // a last chunk past the tile's extent is not used
+          issue_stage(d_tmem, min(kCps, nk - kc * kCps), kc == 0);
         }
-        mma_commit(&S.empty[stage]);
-        if (++stage == kStages) {
-          stage = 0;
-          phase ^= 1u;
-        }
+        if (aborted) break;
       }
-      if (aborted) break;
-      mma_commit(&S.tfull[acc]);
+      if (lt >= 1) {
+        // the previous tile: its remainder chunks, then its accumulator is complete
+        const uint32_t pacc = (lt - 1) % kAccs;
+        for (int32_t x = 0; x < pnx; ++x) {
+          if (!mbar_wait_bounded(&S.full[stage], phase, abort_flag, wait_ns)) {
+            set_abort(S, P.hdr);
+            aborted = true;
+            break;
+          }
+          tc_fence_after();
+          issue_stage(tmem + pacc * (uint32_t)kColBlock, 1, false);
+        }
+        if (aborted) break;
+        mma_commit(&S.tfull[pacc]);
+      }
+      if (!have) break;
+      pnx = nx;
     }
     // every MMA this thread issued has completed before TMEM is freed (after an
     // abort, and also when an epilogue gave up after this loop ended normally)
@@ -485,11 +525,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_wait_bounded(&S.drain, 0, &S.never, kDrainBudgetNs);
   } else if (!skip && (warp == 2 || warp == 3)) {
     // -------------------------------------------------------- remainder builder --
-    // Walks the same stage sequence as the producer; each remainder stage of a tile
-    // is handed over by the producer (bfree, after the slot's previous contents were
-    // consumed), written here and released to the MMA on the slot's full barrier.
-    // The hand-overs of one slot complete in order, so their parity is tracked per
-    // slot (bpar); no copy in flight ever leaves this role.
+    // Walks the same position sequence as the producer. A tile's remainder lists are
+    // staged and its first chunk prepared in registers while the next tile's plane
+    // stages run; each remainder stage is handed over by the producer (bfree, after
+    // the slot's previous contents were consumed), written here and released to the
+    // MMA on the slot's full barrier. The hand-overs of one slot complete in order,
+    // so their parity is tracked per slot (bpar); no copy in flight ever leaves
+    // this role.
     const uint32_t bt = threadIdx.x - 64;
     for (uint32_t i = bt; i < 256; i += kBuildThreads) {
       uint32_t v = 0;
@@ -500,24 +542,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     int stage = 0;
     uint32_t bpar = 0;
     bool aborted = false;
-    for (int32_t t = blockIdx.x; t < n_tiles && !aborted; t += gridDim.x) {
-      int32_t I, J, nk, nx;
-      tile_at(P, X, rect_nk, t, I, J, nk, nx);
-      const int32_t sk = (nk + kCps - 1) / kCps;
-      stage = (stage + sk) % kStages;
-      if (nx == 0) continue;
-      const int64_t rbase = P.blkrem[2 * J];
-      const int32_t rn = (int32_t)(P.blkrem[2 * J + 2] - rbase);
-      const bool staged = rn <= kRemStage;
-      // the column offsets and (when they fit) the entries' bitmap slices of row block I
-      for (int c = (int)bt; c <= kColBlock; c += kBuildThreads)
-        S.remoff[c] = c < kColBlock ? P.rowrem[2 * ((int64_t)J * kColBlock + c)] : rn;
-      if (staged)
-        for (int e = (int)bt; e < rn; e += kBuildThreads)
-          S.remsl[e] = __ldg(reinterpret_cast<const uint4 *>(
-              P.bitmap + (int64_t)__ldg(P.rem + rbase + e) * bm_stride + (int64_t)I * 4));
-      named_bar_sync(3, kBuildThreads);
-      for (int32_t xs = 0; xs < (nx + kCps - 1) / kCps; ++xs) {
+    // the previous tile's remainder: chunks, list base and size, staged or not,
+    // row block; its first chunk's A units prepared in ua
+    int32_t pnx = 0, prn = 0, pI = 0;
+    int64_t prbase = 0;
+    bool pstaged = true;
+    uint4 ua[16];
+    for (int32_t t = blockIdx.x; !aborted; t += gridDim.x) {
+      const bool have = t < n_tiles;
+      int32_t I = 0, J = 0, nk = 0, nx = 0;
+      if (have) {
+        tile_at(P, X, rect_nk, t, I, J, nk, nx);
+        stage = (stage + (nk + kCps - 1) / kCps) % kStages;
+      }
+      for (int32_t x = 0; x < pnx; ++x) {
         bool ok = true;
         if (bt == 0) {
           ok = mbar_wait_bounded(&S.bfree[stage], (bpar >> stage) & 1u, abort_flag, wait_ns);
@@ -528,18 +566,33 @@ __global__ void __launch_bounds__(kThreads, 1)
           aborted = true;
           break;
         }
-        const int nsub = min(kCps, nx - xs * kCps);
-        for (int sub = 0; sub < nsub; ++sub)
-          build_chunk(P, S, S.a[stage] + sub * kSubA, S.b[stage] + sub * kSubB, xs * kCps + sub,
-                      rn, staged, rbase, bm_stride, I, bt, lane);
+        store_chunk(S, S.a[stage], S.b[stage], ua, x, bt, lane);
         // the tensor cores read the stage through the async proxy
         fence_proxy_async_smem();
         named_bar_sync(3, kBuildThreads);
         if (bt == 0) mbar_arrive(&S.full[stage]);
         if (++stage == kStages) stage = 0;
+        if (x + 1 < pnx)
+          prep_chunk_a(P, S, x + 1, prn, pstaged, prbase, bm_stride, pI, bt, lane, ua);
       }
-      // the next tile's staging overwrites remoff and remsl
-      named_bar_sync(3, kBuildThreads);
+      if (!have || aborted) break;
+      pnx = nx;
+      if (nx > 0) {
+        // this tile's lists replace the previous tile's (all of whose chunks are written)
+        named_bar_sync(3, kBuildThreads);
+        prbase = P.blkrem[2 * J];
+        prn = (int32_t)(P.blkrem[2 * J + 2] - prbase);
+        pstaged = prn <= kRemStage;
+        pI = I;
+        for (int c = (int)bt; c <= kColBlock; c += kBuildThreads)
+          S.remoff[c] = c < kColBlock ? P.rowrem[2 * ((int64_t)J * kColBlock + c)] : prn;
+        if (pstaged)
+          for (int e = (int)bt; e < prn; e += kBuildThreads)
+            S.remsl[e] = __ldg(reinterpret_cast<const uint4 *>(
+                P.bitmap + (int64_t)__ldg(P.rem + prbase + e) * bm_stride + (int64_t)pI * 4));
+        named_bar_sync(3, kBuildThreads);
+        prep_chunk_a(P, S, 0, prn, pstaged, prbase, bm_stride, pI, bt, lane, ua);
+      }
     }
   } else if (!skip && warp >= 4 && warp < 12) {
     // ------------------------------------------------------------ epilogue --
@@ -579,7 +632,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         hn = (int32_t)(P.blkrem[2 * J + 3] - hbase);
       }
       const int32_t row_x = hn > 0 ? P.perm[row_pos] : -1;
-      const uint32_t acc = lt & 1, aph = (lt >> 1) & 1;
+      const uint32_t acc = lt % kAccs, aph = (lt / kAccs) & 1;
       const bool got = mbar_wait_bounded(&S.tfull[acc], aph, abort_flag, wait_ns);
       if (!got) set_abort(S, P.hdr);
       // column records staged; the abort decision is the same for every epilogue thread

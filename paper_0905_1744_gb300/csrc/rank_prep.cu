@@ -1054,25 +1054,34 @@ __global__ void __launch_bounds__(256) rem_scatter_kernel(RankPtrs P) {
 // Upper-triangle tile list of every set (blocks per set and column group). Tile (I, J) of a
 // set covers its stored rows [128 I, 128 I + 128) and columns [128 J, 128 J + 128)
 // (set-local, kColBlock = 128); it is needed when some pair i <= j lies in it
-// (I <= J) and both ranges hold real rows. Tiles are grouped by kGroupCols column blocks,
+// (I <= J) and both ranges hold real rows. Tiles are grouped by G column blocks,
 // rows ascending inside a group, so that the tiles running at the same time share
-// their operand panels in L2. Each entry is (I | J << 16, nk | nx << 16) with global
+// their operand panels in L2: a group's G column panels stay in L2 while the row
+// panels stream past them once per group, so G is as large as an L2 budget allows
+// for the panel size (group_cols). Each entry is (I | J << 16, nk | nx << 16) with global
 // block indices: nk plane K chunks, up to the end of section e = min(largest count
 // of I, largest count of J, plane depth of J) (the kept depth when nothing is cut),
 // and nx remainder K chunks of 256 entries of column block J.
-constexpr int kGroupCols = 8;
+// Column blocks per tile group: G panels of 128 rows x K_cap / 2 bytes within
+// kGroupL2Bytes, between 8 and 64.
+constexpr int64_t kGroupL2Bytes = 40ll << 20;
+inline int32_t group_cols(int64_t k_cap) {
+  const int64_t panel = (int64_t)kColBlock * (k_cap > 0 ? k_cap : kKCols) / 2;
+  const int64_t g = kGroupL2Bytes / panel;
+  return (int32_t)(g < 8 ? 8 : (g > 64 ? 64 : g));
+}
 // remainder entries per extra K chunk of a tile: one K column each
 constexpr int kRemChunkCols = kKCols;
 
 // Tiles of column group g of a set: rows I with J in [8g, 8g + 8) and J >= I / kColRatio.
-__device__ __forceinline__ int32_t group_row_tiles(int32_t g, int32_t I, int32_t C) {
-  const int32_t j0 = max(g * kGroupCols, I / kColRatio);
-  const int32_t j1 = min((g + 1) * kGroupCols, C);
+__device__ __forceinline__ int32_t group_row_tiles(int32_t g, int32_t I, int32_t C, int32_t G) {
+  const int32_t j0 = max(g * G, I / kColRatio);
+  const int32_t j1 = min((g + 1) * G, C);
   return max(0, j1 - j0);
 }
 
 // (blockIdx.y: sets in a grid stride; blockIdx.x: column groups in a grid stride)
-__global__ void __launch_bounds__(256) tiles_kernel(RankPtrs P) {
+__global__ void __launch_bounds__(256) tiles_kernel(RankPtrs P, int32_t G) {
   pdl_enter();
   __shared__ int32_t s_warp[32];
   __shared__ int32_t s_carry;
@@ -1086,12 +1095,12 @@ __global__ void __launch_bounds__(256) tiles_kernel(RankPtrs P) {
     const int32_t R = (n + kRowBlock - 1) / kRowBlock;
     const int32_t C = (n + kColBlock - 1) / kColBlock;
     const int32_t I0 = (int32_t)(e.row_base / kRowBlock), J0 = (int32_t)(e.row_base / kColBlock);
-    const int32_t groups = (C + kGroupCols - 1) / kGroupCols;
+    const int32_t groups = (C + G - 1) / G;
     for (int32_t g = blockIdx.x; g < groups; g += gridDim.x) {
       // tiles of the groups before g come first
       int32_t before = 0;
       for (int64_t gi = tid; gi < (int64_t)g * R; gi += blockDim.x)
-        before += group_row_tiles((int32_t)(gi / R), (int32_t)(gi % R), C);
+        before += group_row_tiles((int32_t)(gi / R), (int32_t)(gi % R), C, G);
       int32_t tot;
       block_scan_incl<int32_t>(before, s_warp, &tot);
       if (tid == 0) s_carry = tot;
@@ -1100,12 +1109,12 @@ __global__ void __launch_bounds__(256) tiles_kernel(RankPtrs P) {
       int32_t group_tiles = 0;
       for (int32_t base = 0; base < R; base += blockDim.x) {
         const int32_t I = base + tid;
-        const int32_t cnt = I < R ? group_row_tiles(g, I, C) : 0;
+        const int32_t cnt = I < R ? group_row_tiles(g, I, C, G) : 0;
         const int32_t incl = block_scan_incl<int32_t>(cnt, s_warp, &tot);
         int64_t out = e.tile_base + s_carry + incl - cnt;
         if (cnt > 0) {
           const int32_t dI = P.depth[I0 + I];
-          const int32_t j0 = max(g * kGroupCols, I / kColRatio);
+          const int32_t j0 = max(g * G, I / kColRatio);
           for (int32_t J = j0; J < j0 + cnt; ++J) {
             // the column block spans row blocks kColRatio (J0 + J) .. + kColRatio - 1
             int32_t dJ = 0;
@@ -1268,9 +1277,10 @@ int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *le
   }
   {
     // one set: a CTA per column group; batches: a few per set
-    const int64_t groups1 = ((n + kColBlock - 1) / kColBlock + kGroupCols - 1) / kGroupCols;
+    const int32_t G = group_cols(Q.k_cap);
+    const int64_t groups1 = ((n + kColBlock - 1) / kColBlock + G - 1) / G;
     dim3 g((unsigned)(Q.n_sets == 1 ? (groups1 > 0 ? groups1 : 1) : 4), gsets);
-    pdl_launch(tiles_kernel, g, 256, 0, st, Q);
+    pdl_launch(tiles_kernel, g, 256, 0, st, Q, G);
   }
   SAD_LAUNCH_CHECK();
   return SAD_OK;

@@ -71,6 +71,15 @@ class SeqSet:
     def seq(self, i: int) -> np.ndarray:
         return self.codes[self.offsets[i]:self.offsets[i + 1]]
 
+    def take(self, idx, p: int | None = None) -> "SeqSet":
+        """The sequences idx (in that order) as a set of their own."""
+        idx = np.asarray(idx, dtype=np.int64)
+        lens = self.lengths[idx]
+        offs = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+        codes = np.concatenate([self.seq(i) for i in idx]) if idx.size else self.codes[:0]
+        return SeqSet(codes=codes, offsets=offs, p=self.p if p is None else p,
+                      name=f"{self.name}[{idx.size}]")
+
 
 def rng_for(seed: int, *stream: int) -> np.random.Generator:
     return np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, *stream])))
