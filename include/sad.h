@@ -34,7 +34,7 @@
 extern "C" {
 #endif
 
-#define SAD_ABI_VERSION 5
+#define SAD_ABI_VERSION 6
 
 typedef enum sad_status {
   SAD_OK = 0,
@@ -111,6 +111,11 @@ int kmer_count(const uint8_t *d_codes, const int64_t *d_offsets, int32_t n_seq,
  *                the epilogue from per-row remainder lists, so the keys are
  *                identical for every depth and budget.
  *   budget       remainder entries per column block (0 = the default, 768).
+ *   tile         rows of a GEMM tile: 0 or 128 runs one CTA per 128 x 128 tile;
+ *                256 runs pairs of CTAs (tcgen05 cta_group::2) on 256 x 256
+ *                tiles, for one set (kmer_rank, not the batched or distance
+ *                forms), its rows padded to 256 and the plane depths chosen per
+ *                256-row column block. The keys are the same for either.
  *   t_max        largest count of any word in any sequence.
  *   t_bits       largest threshold of the remainder bitmap, min(D + 4, 16);
  *                counts above it are heavy entries, read from the counts.
@@ -128,8 +133,10 @@ int kmer_count(const uint8_t *d_codes, const int64_t *d_offsets, int32_t n_seq,
 typedef struct sad_rank_plan {
   int32_t depth;
   int32_t budget;
+  int32_t tile;
   int32_t t_max;
   int32_t t_bits;
+  int32_t reserved;
   int64_t k_eff;
   int64_t list_entries;
   int64_t rem_bound;

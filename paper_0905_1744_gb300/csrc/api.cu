@@ -36,11 +36,14 @@ int64_t eps_of(int32_t k, int32_t alphabet) {
 
 bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
-RankCaps planes_only(int64_t k_cap) { return RankCaps{0, 0, k_cap, 0, 0, 0, 0}; }
+RankCaps planes_only(int64_t k_cap) { return RankCaps{0, 0, kRowBlock, k_cap, 0, 0, 0, 0}; }
+
+// GEMM tile rows of a plan: 0 means 128 (one CTA a tile); 256 runs CTA pairs.
+int32_t tile_of(const sad_rank_plan *plan) { return plan->tile == 2 * kRowBlock ? 2 * kRowBlock : kRowBlock; }
 
 RankCaps caps_of(const sad_rank_plan *plan) {
-  return RankCaps{plan->depth, plan->budget, plan->k_cap, plan->list_cap, plan->rem_cap,
-                  plan->heavy_cap, plan->bm_cols};
+  return RankCaps{plan->depth, plan->budget, tile_of(plan), plan->k_cap, plan->list_cap,
+                  plan->rem_cap, plan->heavy_cap, plan->bm_cols};
 }
 
 // Largest K_cap (multiple of kKCols) whose planes-only rank layout fits in ws_bytes.
@@ -237,7 +240,9 @@ int rank_plan_impl(const int32_t *d_counts, const RankShape &sh, const int32_t *
 }
 
 bool plan_valid(const sad_rank_plan *plan) {
-  return plan->depth >= 0 && plan->budget >= 0 && plan->k_cap >= kKCols &&
+  return plan->depth >= 0 && plan->budget >= 0 &&
+         (plan->tile == 0 || plan->tile == kRowBlock || plan->tile == 2 * kRowBlock) &&
+         plan->k_cap >= kKCols &&
          plan->k_cap % kKCols == 0 && plan->list_cap >= 0 && plan->rem_cap >= 0 &&
          plan->heavy_cap >= 0 && plan->bm_cols >= 0;
 }
@@ -301,18 +306,21 @@ int kmer_rank_plan(const int32_t *d_counts, int32_t n_seq, int32_t k, int32_t al
                    sad_rank_plan *plan, void *d_ws, size_t ws_bytes, void *stream) {
   const int64_t eps = eps_of(k, alphabet);
   if (eps < 0) return SAD_ERR_UNSUPPORTED;
-  if (n_seq < 0 || !plan || !d_ws || !aligned(d_ws, 256) || plan->depth < 0)
+  if (n_seq < 0 || !plan || !d_ws || !aligned(d_ws, 256) || plan->depth < 0 ||
+      !(plan->tile == 0 || plan->tile == kRowBlock || plan->tile == 2 * kRowBlock))
     return SAD_ERR_INVALID_ARGUMENT;
-  return rank_plan_impl(d_counts, shape_single(n_seq), nullptr, eps, k, plan, d_ws, ws_bytes,
-                        static_cast<cudaStream_t>(stream));
+  return rank_plan_impl(d_counts, shape_single(n_seq, tile_of(plan)), nullptr, eps, k, plan,
+                        d_ws, ws_bytes, static_cast<cudaStream_t>(stream));
 }
 
 int kmer_rank_plan_bound(int32_t n_seq, int64_t total_len, int32_t k, int32_t alphabet,
                          sad_rank_plan *plan) {
   const int64_t eps = eps_of(k, alphabet);
   if (eps < 0) return SAD_ERR_UNSUPPORTED;
-  if (n_seq < 0 || total_len < 0 || !plan || plan->depth < 1) return SAD_ERR_INVALID_ARGUMENT;
-  const RankShape sh = shape_single(n_seq);
+  if (n_seq < 0 || total_len < 0 || !plan || plan->depth < 1 ||
+      !(plan->tile == 0 || plan->tile == kRowBlock || plan->tile == 2 * kRowBlock))
+    return SAD_ERR_INVALID_ARGUMENT;
+  const RankShape sh = shape_single(n_seq, tile_of(plan));
   if (sh.rows_total / kRowBlock > kMaxRowBlocks) return SAD_ERR_UNSUPPORTED;
   const int64_t d = plan->depth < kMaxPlaneDepth ? plan->depth : kMaxPlaneDepth;
   const int64_t tb = t_bits_of((int32_t)d);
@@ -346,7 +354,8 @@ int kmer_rank(const int32_t *d_counts, const int32_t *d_lengths, const int32_t *
   if (n_seq < 0 || !d_ws || !aligned(d_ws, 256)) return SAD_ERR_INVALID_ARGUMENT;
   if (n_seq == 0) return SAD_OK;
   if (!d_counts || !d_lengths || !d_key_hi || !d_key_lo) return SAD_ERR_INVALID_ARGUMENT;
-  return rank_run_impl(d_counts, d_lengths, d_word_max, shape_single(n_seq), nullptr, eps, k,
+  return rank_run_impl(d_counts, d_lengths, d_word_max,
+                       shape_single(n_seq, plan ? tile_of(plan) : kRowBlock), nullptr, eps, k,
                        plan,
                        d_key_hi, d_key_lo, d_rank, d_ws, ws_bytes,
                        static_cast<cudaStream_t>(stream));
@@ -412,7 +421,8 @@ int kmer_rank_dist(const int32_t *d_counts, const int32_t *d_lengths, const int3
   if (n_seq < 1 || !plan || !d_counts || !d_lengths || !d_key_hi || !d_key_lo || !d_ws ||
       !aligned(d_ws, 256) || delta_den < 1 || delta_den > 1024)
     return SAD_ERR_INVALID_ARGUMENT;
-  if (!plan_valid(plan)) return SAD_ERR_INVALID_ARGUMENT;
+  // the distance form runs one CTA per tile
+  if (!plan_valid(plan) || tile_of(plan) != kRowBlock) return SAD_ERR_INVALID_ARGUMENT;
   const RankShape sh = shape_single(n_seq);
   if (sh.rows_total / kRowBlock > kMaxRowBlocks) return SAD_ERR_UNSUPPORTED;
   const RankLayout L = rank_layout(sh, eps, caps_of(plan));
@@ -481,7 +491,9 @@ int sad_batch_plan_make(const int32_t *d_counts, const int32_t *h_n, const int32
                         sad_batch_plan *plan, void *d_ws, size_t ws_bytes, void *stream) {
   const int64_t eps = eps_of(k, alphabet);
   if (eps < 0) return SAD_ERR_UNSUPPORTED;
-  if (!plan || !h_p || !d_n || !d_ws || !aligned(d_ws, 256) || plan->rank.depth < 0)
+  // batches run one CTA per tile (a set's rows are 128-aligned)
+  if (!plan || !h_p || !d_n || !d_ws || !aligned(d_ws, 256) || plan->rank.depth < 0 ||
+      tile_of(&plan->rank) != kRowBlock)
     return SAD_ERR_INVALID_ARGUMENT;
   RankShape sh;
   PartTotals pt;
@@ -510,7 +522,7 @@ int sad_batch_rank(const int32_t *d_counts, const int32_t *d_lengths, const int3
   const int64_t eps = eps_of(k, alphabet);
   if (eps < 0) return SAD_ERR_UNSUPPORTED;
   if (!plan || plan->n_sets < 1 || !d_n || !d_counts || !d_lengths || !d_key_hi || !d_key_lo ||
-      !d_ws || !aligned(d_ws, 256))
+      !d_ws || !aligned(d_ws, 256) || tile_of(&plan->rank) != kRowBlock)
     return SAD_ERR_INVALID_ARGUMENT;
   const RankShape sh{plan->n_sets, plan->n_total, plan->rows_total, plan->tiles_total,
                      plan->tileof_total};

@@ -214,20 +214,25 @@ __device__ __forceinline__ uint32_t bit_range(int32_t a, int32_t b) {
 // prep_chunk_a computes this builder thread's 16 units of a into registers (before
 // the ring slot is free); store_chunk writes them and the thread's 16 units of b.
 // Builder warp bw takes the units j = 2 i + bw of every lane quadrant q.
-__device__ __forceinline__ void prep_chunk_a(const RankPtrs &P, const GemmSmem &S, int32_t x,
+template <bool kCanStage, typename SmemT>
+__device__ __forceinline__ void prep_chunk_a(const RankPtrs &P, const SmemT &S, int32_t x,
                                              int32_t rn, bool staged, int64_t rbase,
                                              int64_t bm_stride, int32_t I, uint32_t bt,
                                              uint32_t lane, uint4 (&ua)[16]) {
   const uint32_t bw = bt >> 5;
   uint32_t w[16];
-  if (staged) {
+  bool from_smem = false;
+  if constexpr (kCanStage) from_smem = staged;
+  if (from_smem) {
+    if constexpr (kCanStage) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int32_t e = x * kRemChunk + (int32_t)((2 * i + bw) * 32 + lane);
-        w[4 * i + q] = e < rn ? (&S.remsl[e].x)[q] : 0u;
-      }
+        for (int q = 0; q < 4; ++q) {
+          const int32_t e = x * kRemChunk + (int32_t)((2 * i + bw) * 32 + lane);
+          w[4 * i + q] = e < rn ? (&S.remsl[e].x)[q] : 0u;
+        }
+    }
   } else {
     uint32_t col[4];
 #pragma unroll
@@ -251,7 +256,8 @@ __device__ __forceinline__ void prep_chunk_a(const RankPtrs &P, const GemmSmem &
   }
 }
 
-__device__ __forceinline__ void store_chunk(const GemmSmem &S, uint8_t *a, uint8_t *b,
+template <typename SmemT>
+__device__ __forceinline__ void store_chunk(const SmemT &S, uint8_t *a, uint8_t *b,
                                             const uint4 (&ua)[16], int32_t x, uint32_t bt,
                                             uint32_t lane) {
   const uint32_t bw = bt >> 5;
@@ -288,7 +294,7 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 // remainder r of the column. The row keeps sum s Qlo, sum s Qhi (each below 2^54 over 64 columns)
 // and the sum of the floors; cs, cq get what the columns add (s and the floor).
 // On a diagonal tile the row takes j >= i only and the columns j > i only.
-template <bool kDiag>
+template <bool kDiag, bool kInt = false>
 __device__ __forceinline__ void f_block16(const uint32_t (&v)[16], const uint32_t (&rr)[16],
                                           const uint4 *colrec, int64_t row_pos, int64_t jpos0,
                                           uint64_t &sql, uint64_t &sqh, uint32_t &qsum,
@@ -297,7 +303,9 @@ __device__ __forceinline__ void f_block16(const uint32_t (&v)[16], const uint32_
   for (int cc = 0; cc < 16; ++cc) {
     const uint4 rec = colrec[cc];
     // the accumulator is an integer below 2^16: + 2^23 puts it in the low mantissa bits
-    const uint32_t sv = __float_as_uint(__fadd_rn(__uint_as_float(v[cc]), 8388608.0f)) - 0x4B000000u;
+    // (kInt: v holds the integers already)
+    const uint32_t sv =
+        kInt ? v[cc] : __float_as_uint(__fadd_rn(__uint_as_float(v[cc]), 8388608.0f)) - 0x4B000000u;
     const uint32_t s = sv + rr[cc];
     const uint32_t q = (uint32_t)(((uint64_t)s * rec.w + __umulhi(s, rec.z)) >> 31);
     uint32_t sr = s, qr = q, sc = s, qc = q;
@@ -317,17 +325,34 @@ __device__ __forceinline__ void f_block16(const uint32_t (&v)[16], const uint32_
 // Heavy remainder of S for this lane's row and the 16 tile columns c0..c0 + 15:
 // for each heavy entry (tau, c) of column v, max(0, min(c_u(tau), c) - T_b) from
 // the counts (the thresholds up to T_b come through the remainder chunks).
+// The heavy remainder of one tile column v (global index) for this lane's row: for
+// each heavy entry (tau, c) of v, max(0, min(c_u(tau), c) - T_b). h1 is the end of
+// v's entries (the next column's first, or the block's count).
+__device__ __noinline__ uint32_t heavy_of_column(const RankPtrs &P, int64_t hbase, int64_t v,
+                                                 int32_t h1, int32_t row_x, int32_t tbits) {
+  uint32_t r = 0;
+  for (int32_t h = P.rowrem[2 * v + 1]; h < h1; ++h) {
+    const int2 e = __ldg(P.heavy + hbase + h);
+    const int32_t cu = row_x >= 0 ? __ldg(P.counts + (int64_t)row_x * P.eps + e.x) : 0;
+    const int32_t x = min(cu, e.y) - tbits;
+    r += x > 0 ? (uint32_t)x : 0u;
+  }
+  return r;
+}
+
+// kW: columns of the tile's column block (its remainder lists' block).
+template <int kW = kColBlock>
 __device__ __forceinline__ void tile_heavy(const RankPtrs &P, int32_t hn, int64_t hbase,
                                            int32_t row_x, int32_t tbits, int32_t J, int c0,
                                            uint32_t (&rr)[16]) {
 #pragma unroll
   for (int cc = 0; cc < 16; ++cc) rr[cc] = 0;
   if (hn > 0) {
-    const int64_t v0 = (int64_t)J * kColBlock + c0;
+    const int64_t v0 = (int64_t)J * kW + c0;
 #pragma unroll
     for (int cc = 0; cc < 16; ++cc) {
       const int32_t h0 = P.rowrem[2 * (v0 + cc) + 1];
-      const int32_t h1 = (c0 + cc + 1 < kColBlock) ? P.rowrem[2 * (v0 + cc + 1) + 1] : hn;
+      const int32_t h1 = (c0 + cc + 1 < kW) ? P.rowrem[2 * (v0 + cc + 1) + 1] : hn;
       for (int32_t h = h0; h < h1; ++h) {
         const int2 e = __ldg(P.heavy + hbase + h);
         const int32_t cu = row_x >= 0 ? __ldg(P.counts + (int64_t)row_x * P.eps + e.x) : 0;
@@ -573,7 +598,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (bt == 0) mbar_arrive(&S.full[stage]);
         if (++stage == kStages) stage = 0;
         if (x + 1 < pnx)
-          prep_chunk_a(P, S, x + 1, prn, pstaged, prbase, bm_stride, pI, bt, lane, ua);
+          prep_chunk_a<true>(P, S, x + 1, prn, pstaged, prbase, bm_stride, pI, bt, lane, ua);
       }
       if (!have || aborted) break;
       pnx = nx;
@@ -591,7 +616,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             S.remsl[e] = __ldg(reinterpret_cast<const uint4 *>(
                 P.bitmap + (int64_t)__ldg(P.rem + prbase + e) * bm_stride + (int64_t)pI * 4));
         named_bar_sync(3, kBuildThreads);
-        prep_chunk_a(P, S, 0, prn, pstaged, prbase, bm_stride, pI, bt, lane, ua);
+        prep_chunk_a<true>(P, S, 0, prn, pstaged, prbase, bm_stride, pI, bt, lane, ua);
       }
     }
   } else if (!skip && warp >= 4 && warp < 12) {
@@ -863,6 +888,430 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// ------------------------------------------------------------- CTA pairs ----
+// 256 x 256 tiles on clusters of two CTAs (tcgen05 cta_group::2, M = 256): CTA r of
+// the pair holds the 128 rows 256 I + 128 r of A and the 128 rows 256 J + 128 r of
+// B, one K chunk (256 plane columns) a stage, and the lanes of its 128 rows of the
+// 128 x 256 accumulator in its TMEM; the even CTA issues the MMAs for both. Per
+// MMA cycle a CTA takes in half the operand bytes of a one-CTA 128 x 128 tile.
+// One accumulator (256 columns; the scale factors need the rest of TMEM): the
+// epilogue drains it into registers (packed 16-bit counts) and releases it before
+// the arithmetic, so the next tile's MMAs wait only for the drain. A tile's
+// remainder chunks go through two buffers of their own (not the operand ring), so
+// the builder writes them while the tile's plane chunks run. Everything else is
+// as in plane_gemm_kernel: rows in decreasing length, D_ij = m_j, the same term
+// arithmetic, sums per row and column of a tile, bounded waits.
+namespace pairk {
+
+constexpr int kStages = 4;                               // one K chunk a stage
+constexpr uint32_t kSub = kRowBlock * kKChunk;           // 16 KB: 128 rows x 128 bytes
+constexpr uint32_t kTx = 2 * kSub;                       // A and B bytes of one CTA
+constexpr int kXSlots = 2;                               // remainder chunk buffers
+constexpr int kThreads = 384;
+constexpr int kEpiThreads = 256;                         // warps 4-11
+constexpr int kEpiWarps = kEpiThreads / 32;
+constexpr int kCols = 2 * kColBlock;                     // tile columns (N = 256)
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kSfaCol = kCols, kSfbCol = kCols + 32, kSfCols = 64;
+static_assert(kSfaCol + kSfCols <= kTmemCols, "TMEM columns");
+
+struct Smem {
+  uint8_t a[kStages][kSub];
+  uint8_t b[kStages][kSub];
+  uint8_t xa[kXSlots][kSub];
+  uint8_t xb[kXSlots][kSub];
+  uint4 colrec[2][kCols];
+  int32_t colorig[2][kCols];
+  uint2 colpart[4][kCols];  // the four lane quadrants' column sums (s, floor)
+  uint4 rowpart[kRowBlock];  // the second column half's row sums
+  int32_t remoff[kColBlock + 1];
+  uint32_t nib[256];
+  uint64_t full[kStages];    // the even CTA's count the copies of both CTAs
+  uint64_t empty[kStages];
+  uint64_t xfull[kXSlots];   // the even CTA's: one arrival from each CTA's builder
+  uint64_t xempty[kXSlots];
+  uint64_t tfull;
+  uint64_t tempty;           // the even CTA's: one arrival per epilogue warp of both CTAs
+  uint64_t drain;
+  uint32_t tmem_base;
+  int32_t abort;
+  int32_t skip;
+  int32_t never;
+};
+constexpr size_t kSmemBytes = sizeof(Smem) + 1024;
+static_assert(kSmemBytes <= 232448, "227 KB of shared memory per CTA");
+
+__device__ __forceinline__ void set_abort(Smem &S, WsHeader *hdr) {
+  *reinterpret_cast<volatile int32_t *>(&S.abort) = 1;
+  record_error(hdr, SAD_ERR_TIMEOUT, (int)blockIdx.x);
+}
+
+}  // namespace pairk
+
+__global__ void __launch_bounds__(pairk::kThreads, 1)
+    pair_gemm_kernel(const __grid_constant__ CUtensorMap tm, RankPtrs P) {
+  pdl_enter();
+  extern __shared__ uint8_t smem_raw[];
+  pairk::Smem &S = *reinterpret_cast<pairk::Smem *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  volatile int32_t *abort_flag = &S.abort;
+  const uint64_t wait_ns = P.wait_ns;
+  const uint32_t crank = cluster_ctarank();
+  const bool leader = crank == 0;
+  const int32_t unit0 = (int32_t)cluster_id_x(), ustride = (int32_t)cluster_count_x();
+
+  if (threadIdx.x == 0) {
+    S.abort = 0;
+    S.never = 0;
+    S.skip = (P.hdr->status != 0) ? 1 : 0;
+    for (int s = 0; s < pairk::kStages; ++s) {
+      mbar_init(&S.full[s], 1);
+      mbar_init(&S.empty[s], 1);
+    }
+    for (int x = 0; x < pairk::kXSlots; ++x) {
+      mbar_init(&S.xfull[x], 2);
+      mbar_init(&S.xempty[x], 1);
+    }
+    mbar_init(&S.tfull, 1);
+    mbar_init(&S.tempty, 2 * pairk::kEpiWarps);
+    mbar_init(&S.drain, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0 && lane == 0) tma_prefetch_desc(&tm);
+  __syncthreads();
+  const bool skip = S.skip != 0;
+  // the allocation is a collective of both CTAs, whatever either decides
+  if (warp == 2) {
+    tmem_alloc_pair(&S.tmem_base, pairk::kTmemCols);
+    tmem_relinquish_pair();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = S.tmem_base;
+  if (warp >= 4 && warp < 8) {
+    // every block scale of A and B is 1.0: fill their columns in this warp's lanes
+    const uint32_t lanes = ((warp & 3u) * 32u) << 16;
+#pragma unroll
+    for (uint32_t c = 0; c < pairk::kSfCols; c += 16)
+      tmem_st_32x32b_x16_fill(tmem + lanes + pairk::kSfaCol + c, kScaleOne4);
+    tmem_st_wait();
+  }
+  tc_fence_before();
+  __syncthreads();
+  // both CTAs' barriers and TMEM are ready before either uses the other's
+  cluster_sync_all();
+  tc_fence_after();
+  const int32_t n_tiles = skip ? 0 : P.hdr->n_tiles;
+  const bool residual = !skip && P.depth_cap >= 1;
+  const int64_t bm_stride = P.n_pad / 32;
+  const int32_t tbits = t_bits_of(min(P.depth_cap, kMaxPlaneDepth));
+  const RectArgs X{};
+
+  if (!skip && warp == 0 && lane == 0) {
+    // ------------------------------------------------------------ producer --
+    // both CTAs count their copies on the even CTA's full barrier, which expects
+    // the bytes of both
+    int stage = 0;
+    uint32_t phase = 0, used = 0, par = 0;
+    bool aborted = false;
+    for (int32_t p = unit0; p < n_tiles && !aborted; p += ustride) {
+      int32_t I2, J2, nk, nx;
+      tile_at(P, X, 0, p, I2, J2, nk, nx);
+      for (int32_t kc = 0; kc < nk; ++kc) {
+        if (!mbar_wait_bounded_cluster(&S.empty[stage], phase ^ 1u, abort_flag, wait_ns)) {
+          pairk::set_abort(S, P.hdr);
+          aborted = true;
+          break;
+        }
+        if (leader) mbar_arrive_expect_tx(&S.full[stage], 2 * pairk::kTx);
+        const uint32_t fb = mapa_shared(&S.full[stage], 0);
+        tma_load_3d_pair(S.a[stage], &tm, fb, 0, (2 * I2 + (int32_t)crank) * kRowBlock, kc);
+        tma_load_3d_pair(S.b[stage], &tm, fb, 0, (2 * J2 + (int32_t)crank) * kRowBlock, kc);
+        used |= 1u << stage;
+        par = (par & ~(1u << stage)) | (phase << stage);
+        if (++stage == pairk::kStages) {
+          stage = 0;
+          phase ^= 1u;
+        }
+      }
+    }
+    if (aborted || *abort_flag) {
+      if (leader) {
+        // the even CTA's full barriers count the copies of both CTAs
+        for (int s = 0; s < pairk::kStages; ++s)
+          if (used & (1u << s))
+            mbar_wait_bounded(&S.full[s], (par >> s) & 1u, &S.never, kDrainBudgetNs);
+      } else {
+        // this CTA cannot see its copies land: give them time (they take microseconds)
+        const uint64_t t0 = globaltimer_ns();
+        while (globaltimer_ns() - t0 < 200000ull) {
+        }
+      }
+    }
+  } else if (!skip && warp == 1 && lane == 0 && leader) {
+    // ----------------------------------------------------------------- MMA --
+    const uint32_t idesc = idesc_f4_e2m1(2 * kRowBlock, pairk::kCols);
+    const uint32_t sfa = tmem + pairk::kSfaCol, sfb = tmem + pairk::kSfbCol;
+    int stage = 0;
+    uint32_t phase = 0;
+    uint32_t xcount = 0;
+    bool aborted = false;
+    int32_t lt = 0;
+    for (int32_t p = unit0; p < n_tiles && !aborted; p += ustride, ++lt) {
+      int32_t I2, J2, nk, nx;
+      tile_at(P, X, 0, p, I2, J2, nk, nx);
+      if (!mbar_wait_bounded_cluster(&S.tempty, (lt & 1) ^ 1u, abort_flag, wait_ns)) {
+        pairk::set_abort(S, P.hdr);
+        aborted = true;
+        break;
+      }
+      tc_fence_after();
+      for (int32_t kc = 0; kc < nk; ++kc) {
+        if (!mbar_wait_bounded_cluster(&S.full[stage], phase, abort_flag, wait_ns)) {
+          pairk::set_abort(S, P.hdr);
+          aborted = true;
+          break;
+        }
+        tc_fence_after();
+        const uint64_t adesc = sdesc_kmajor_sw128(smem_u32(S.a[stage]));
+        const uint64_t bdesc = sdesc_kmajor_sw128(smem_u32(S.b[stage]));
+#pragma unroll
+        for (int kk = 0; kk < kKChunk / 32; ++kk)
+          mma_f4_pair(tmem, adesc + 2u * kk, bdesc + 2u * kk, idesc, sfa, sfb,
+                      (kc | kk) != 0 ? 1u : 0u);
+        mma_commit_pair(&S.empty[stage], 0x3);
+        if (++stage == pairk::kStages) {
+          stage = 0;
+          phase ^= 1u;
+        }
+      }
+      if (aborted) break;
+      for (int32_t x = 0; x < nx; ++x, ++xcount) {
+        const uint32_t xs = xcount % pairk::kXSlots, xph = (xcount / pairk::kXSlots) & 1u;
+        if (!mbar_wait_bounded_cluster(&S.xfull[xs], xph, abort_flag, wait_ns)) {
+          pairk::set_abort(S, P.hdr);
+          aborted = true;
+          break;
+        }
+        tc_fence_after();
+        const uint64_t adesc = sdesc_kmajor_sw128(smem_u32(S.xa[xs]));
+        const uint64_t bdesc = sdesc_kmajor_sw128(smem_u32(S.xb[xs]));
+#pragma unroll
+        for (int kk = 0; kk < kKChunk / 32; ++kk)
+          mma_f4_pair(tmem, adesc + 2u * kk, bdesc + 2u * kk, idesc, sfa, sfb, 1u);
+        mma_commit_pair(&S.xempty[xs], 0x3);
+      }
+      if (aborted) break;
+      mma_commit_pair(&S.tfull, 0x3);
+    }
+    // every MMA into either CTA's TMEM, reading either CTA's shared memory, completes
+    mma_commit_pair(&S.drain, 0x1);
+    mbar_wait_bounded(&S.drain, 0, &S.never, kDrainBudgetNs);
+  } else if (!skip && (warp == 2 || warp == 3)) {
+    // -------------------------------------------------------- remainder builder --
+    // Each CTA writes its halves of a tile's remainder chunks into the chunk buffers:
+    // A rows = its 128 rows, B rows = its 128 of the tile's 256 columns. A buffer is
+    // written once the MMAs that read it last have completed (xempty, committed to
+    // both CTAs) and released to the even CTA's MMA issuer on xfull.
+    const uint32_t bt = threadIdx.x - 64;
+    for (uint32_t i = bt; i < 256; i += kBuildThreads) {
+      uint32_t v = 0;
+      for (int k = 0; k < 8; ++k) v |= ((i >> k) & 1u) * (kE2M1One << (4 * k));
+      S.nib[i] = v;
+    }
+    named_bar_sync(3, kBuildThreads);
+    uint32_t xcount = 0;
+    bool aborted = false;
+    for (int32_t p = unit0; p < n_tiles && !aborted; p += ustride) {
+      int32_t I2, J2, nk, nx;
+      tile_at(P, X, 0, p, I2, J2, nk, nx);
+      if (nx == 0) continue;
+      const int64_t rbase = P.blkrem[2 * J2];
+      const int32_t rn = (int32_t)(P.blkrem[2 * J2 + 2] - rbase);
+      const int32_t I = 2 * I2 + (int32_t)crank;
+      const int64_t v0 = (int64_t)J2 * pairk::kCols + (int64_t)crank * kColBlock;
+      // first entry of each of this CTA's columns, relative to the column block
+      for (int c = (int)bt; c <= kColBlock; c += kBuildThreads)
+        S.remoff[c] = (crank == 0 || c < kColBlock) ? P.rowrem[2 * (v0 + c)] : rn;
+      named_bar_sync(3, kBuildThreads);
+      for (int32_t x = 0; x < nx; ++x, ++xcount) {
+        const uint32_t xs = xcount % pairk::kXSlots, xph = (xcount / pairk::kXSlots) & 1u;
+        uint4 ua[16];
+        prep_chunk_a<false>(P, S, x, rn, false, rbase, bm_stride, I, bt, lane, ua);
+        bool ok = true;
+        if (bt == 0) {
+          ok = mbar_wait_bounded_cluster(&S.xempty[xs], xph ^ 1u, abort_flag, wait_ns);
+          if (!ok) pairk::set_abort(S, P.hdr);
+        }
+        if (named_bar_sync_or(3, kBuildThreads, !ok || *abort_flag != 0)) {
+          aborted = true;
+          break;
+        }
+        store_chunk(S, S.xa[xs], S.xb[xs], ua, x, bt, lane);
+        // the tensor cores read the buffer through the async proxy
+        fence_proxy_async_smem();
+        named_bar_sync(3, kBuildThreads);
+        if (bt == 0) {
+          if (leader)
+            mbar_arrive(&S.xfull[xs]);
+          else
+            mbar_arrive_cluster(mapa_shared(&S.xfull[xs], 0));
+        }
+      }
+      // the next tile's offsets overwrite remoff
+      named_bar_sync(3, kBuildThreads);
+    }
+  } else if (!skip && warp >= 4 && warp < 12) {
+    // ------------------------------------------------------------ epilogue --
+    // warp w: TMEM lanes 32 (w % 4).. (its quadrant of this CTA's 128 rows) and tile
+    // columns [128 h, 128 h + 128), h = (w - 4) / 4: drained into 64 registers of
+    // two 16-bit counts, then summed in sub-chunks of 16 columns.
+    const uint32_t q = warp & 3;
+    const uint32_t half = (warp - 4) >> 2;
+    const uint32_t etid = threadIdx.x - 128;
+    int32_t lt = 0;
+    for (int32_t p = unit0; p < n_tiles; p += ustride, ++lt) {
+      int32_t I2, J2, nk, nx;
+      tile_at(P, X, 0, p, I2, J2, nk, nx);
+      const int buf = lt & 1;
+      const int32_t I = 2 * I2 + (int32_t)crank;
+      for (uint32_t c = etid; c < (uint32_t)pairk::kCols; c += pairk::kEpiThreads) {
+        const int64_t jpos = (int64_t)J2 * pairk::kCols + c;
+        const uint4 rc = P.rec[jpos];
+        const uint2 w = P.recw[jpos];
+        S.colrec[buf][c] = make_uint4(rc.x, rc.y, w.x, w.y);
+        S.colorig[buf][c] = P.perm[jpos];
+      }
+      const int64_t row_pos = (int64_t)I * kRowBlock + q * 32 + lane;
+      const int32_t row_orig = P.perm[row_pos];
+      const bool diag = I2 == J2;
+      int64_t hbase = 0;
+      int32_t hn = 0;
+      if (residual) {
+        hbase = P.blkrem[2 * J2 + 1];
+        hn = (int32_t)(P.blkrem[2 * J2 + 3] - hbase);
+      }
+      const int32_t row_x = hn > 0 ? row_orig : -1;
+      const bool got = mbar_wait_bounded_cluster(&S.tfull, lt & 1, abort_flag, wait_ns);
+      if (!got) pairk::set_abort(S, P.hdr);
+      if (named_bar_sync_or(1, pairk::kEpiThreads, *abort_flag != 0)) break;
+      tc_fence_after();
+      // drain this thread's 128 accumulator columns
+      uint32_t pk[64];
+#pragma unroll
+      for (int sc = 0; sc < 8; ++sc) {
+        uint32_t v[16];
+        tmem_ld_32x32b_x16(tmem + ((q * 32u) << 16) + half * 128u + (uint32_t)(sc * 16), v);
+        tmem_ld_wait();
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const uint32_t a = __float_as_uint(__fadd_rn(__uint_as_float(v[2 * j]), 8388608.0f));
+          const uint32_t b = __float_as_uint(__fadd_rn(__uint_as_float(v[2 * j + 1]), 8388608.0f));
+          // the counts are below 2^16: the low mantissa halves of a and b
+          pk[sc * 8 + j] = __byte_perm(a, b, 0x5410);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        if (leader)
+          mbar_arrive(&S.tempty);
+        else
+          mbar_arrive_cluster(mapa_shared(&S.tempty, 0));
+      }
+      if (hn > 0) {
+        // heavy remainder entries (rare): added to the counts (S + heavy <= min(m_i, m_j)
+        // < 2^16, so each half stays within its 16 bits)
+        const int64_t vb = (int64_t)J2 * pairk::kCols + half * 128;
+#pragma unroll
+        for (int j = 0; j < 64; ++j) {
+          const int c = (int)half * 128 + 2 * j;
+          const int32_t e1 = P.rowrem[2 * (vb + 2 * j + 1) + 1];
+          const int32_t e2 = c + 2 < pairk::kCols ? P.rowrem[2 * (vb + 2 * j + 2) + 1] : hn;
+          const uint32_t lo = heavy_of_column(P, hbase, vb + 2 * j, e1, row_x, tbits);
+          const uint32_t hi = heavy_of_column(P, hbase, vb + 2 * j + 1, e2, row_x, tbits);
+          pk[j] += lo | (hi << 16);
+        }
+      }
+      uint64_t sql = 0, sqh = 0;  // sum s Qlo, sum s Qhi
+      uint32_t qsum = 0;          // sum floor(s W / 2^63)
+#pragma unroll
+      for (int sc = 0; sc < 8; ++sc) {
+        const int c0 = (int)half * 128 + sc * 16;
+        uint32_t v[16];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          v[2 * j] = pk[sc * 8 + j] & 0xFFFFu;
+          v[2 * j + 1] = pk[sc * 8 + j] >> 16;
+        }
+        uint32_t rr[16];
+#pragma unroll
+        for (int cc = 0; cc < 16; ++cc) rr[cc] = 0;
+        uint32_t cs[16], cq[16];
+        if (diag)
+          f_block16<true, true>(v, rr, &S.colrec[buf][c0], row_pos, (int64_t)J2 * pairk::kCols + c0, sql,
+                                sqh, qsum, cs, cq);
+        else
+          f_block16<false, true>(v, rr, &S.colrec[buf][c0], row_pos, 0, sql, sqh, qsum, cs, cq);
+        // column sums over the warp's 32 rows: one warp-wide reduction per column
+        uint32_t mcs = 0, mcq = 0;
+#pragma unroll
+        for (int cc = 0; cc < 16; ++cc) {
+          const uint32_t a = __reduce_add_sync(0xffffffffu, cs[cc]);
+          const uint32_t b = __reduce_add_sync(0xffffffffu, cq[cc]);
+          if (lane == (uint32_t)cc) {
+            mcs = a;
+            mcq = b;
+          }
+        }
+        if (lane < 16) S.colpart[q][c0 + (int)lane] = make_uint2(mcs, mcq);
+      }
+      // the row's sum of terms sql + sqh 2^32 + qsum as Rc 2^64 + Rlo
+      const uint64_t ra = sql + (sqh << 32);
+      const uint64_t Rlo = ra + qsum;
+      const uint32_t Rc = (uint32_t)(sqh >> 32) + (ra < sql ? 1u : 0u) + (Rlo < ra ? 1u : 0u);
+      if (half == 1)
+        S.rowpart[q * 32 + lane] = make_uint4((uint32_t)Rlo, (uint32_t)(Rlo >> 32), Rc, 0u);
+      named_bar_sync(2, pairk::kEpiThreads);
+      if (half == 0 && row_orig >= 0) {
+        const uint4 o = S.rowpart[q * 32 + lane];
+        const uint64_t lo = Rlo + (((uint64_t)o.y << 32) | o.x);
+        const uint64_t hi = (uint64_t)Rc + o.z + (lo < Rlo ? 1u : 0u);
+        red_key(P.acc + 3 * (int64_t)row_orig, lo, hi);
+      }
+      {
+        // one column of the 256 per epilogue thread: the four quadrants' sums
+        const int c = (int)etid;
+        const int32_t jorig = S.colorig[buf][c];
+        uint32_t cs = 0, cq = 0;
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) {
+          const uint2 v2 = S.colpart[qq][c];
+          cs += v2.x;
+          cq += v2.y;
+        }
+        if (jorig >= 0 && (cs | cq) != 0) {
+          const uint4 rec = S.colrec[buf][c];
+          const uint64_t Q = ((uint64_t)rec.y << 32) | rec.x;
+          const unsigned __int128 sum = (unsigned __int128)Q * cs + cq;
+          red_key(P.acc + 3 * (int64_t)jorig, (uint64_t)sum, (uint64_t)(sum >> 64));
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  // every MMA into either CTA's TMEM, reading either CTA's shared memory, is done
+  cluster_sync_all();
+  if (warp == 2) {
+    tc_fence_after();
+    tmem_dealloc_pair(tmem, pairk::kTmemCols);
+  }
+}
+
 }  // namespace
 
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -878,15 +1327,17 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// The planes as bytes: n_pad rows of K_cap / 2 bytes (two 4-bit values each).
-int make_plane_map(CUtensorMap *map, uint8_t *planes, int64_t n_pad, int64_t k_cap, int rows) {
+// The planes as bytes: n_pad rows of K_cap / 2 bytes (two 4-bit values each); a box
+// is `chunks` K chunks of `rows` rows.
+int make_plane_map(CUtensorMap *map, uint8_t *planes, int64_t n_pad, int64_t k_cap, int rows,
+                   int chunks) {
   auto fn = encode_fn();
   if (!fn) return SAD_ERR_CUDA;
   // (byte in chunk, row, chunk): a box of kCps chunks lands as kCps row-major tiles
   const cuuint64_t dims[3] = {(cuuint64_t)kKChunk, (cuuint64_t)n_pad,
                               (cuuint64_t)(k_cap / 2 / kKChunk)};
   const cuuint64_t strides[2] = {(cuuint64_t)(k_cap / 2), (cuuint64_t)kKChunk};
-  const cuuint32_t box[3] = {(cuuint32_t)kKChunk, (cuuint32_t)rows, (cuuint32_t)kCps};
+  const cuuint32_t box[3] = {(cuuint32_t)kKChunk, (cuuint32_t)rows, (cuuint32_t)chunks};
   const cuuint32_t estr[3] = {1, 1, 1};
   const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, planes, dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -912,13 +1363,80 @@ int gemm_attr() {
 
 }  // namespace
 
+namespace {
+// Largest number of co-resident clusters of two for the pair kernel (0: none).
+int pair_clusters() {
+  static int cached = -1;
+  if (cached < 0) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)(2 * num_sms()), 1, 1);
+    cfg.blockDim = dim3(pairk::kThreads, 1, 1);
+    cfg.dynamicSmemBytes = pairk::kSmemBytes;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, pair_gemm_kernel, &cfg) != cudaSuccess) {
+      (void)cudaGetLastError();
+      n = 0;
+    }
+    cached = n;
+  }
+  return cached;
+}
+
+// One set on CTA pairs: the 256 x 256 tiles of the plan (P.tile == 256).
+int rank_gemm_pair_launch(const RankPtrs &P, cudaStream_t st) {
+  const int64_t tiles = P.tiles_total;
+  if (tiles == 0) return SAD_OK;
+  static bool attr_set = false;
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(pair_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)pairk::kSmemBytes) != cudaSuccess)
+      return SAD_ERR_CUDA;
+    attr_set = true;
+  }
+  const int ncl = pair_clusters();
+  if (ncl < 1) return SAD_ERR_UNSUPPORTED;
+  CUtensorMap m;  // 128-row boxes of one K chunk: A and B rows of either CTA
+  int rc = make_plane_map(&m, P.planes, P.n_pad, P.k_cap, kRowBlock, 1);
+  if (rc) return rc;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  const int64_t clusters = tiles < ncl ? tiles : ncl;
+  cfg.gridDim = dim3((unsigned)(2 * clusters), 1, 1);
+  cfg.blockDim = dim3(pairk::kThreads, 1, 1);
+  cfg.dynamicSmemBytes = pairk::kSmemBytes;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  prof_begin(st);
+  if (cudaLaunchKernelEx(&cfg, pair_gemm_kernel, m, P) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return SAD_ERR_CUDA;
+  }
+  note_launch();
+  prof_end(st);
+  return SAD_OK;
+}
+}  // namespace
+
 int rank_gemm_launch(const RankPtrs &P, cudaStream_t st) {
+  if (P.tile == 2 * kRowBlock) return rank_gemm_pair_launch(P, st);
   const int64_t tiles = P.tiles_total;
   if (tiles == 0) return SAD_OK;
   CUtensorMap mA, mB;
-  int rc = make_plane_map(&mA, P.planes, P.n_pad, P.k_cap, kRowBlock);
+  int rc = make_plane_map(&mA, P.planes, P.n_pad, P.k_cap, kRowBlock, kCps);
   if (rc) return rc;
-  rc = make_plane_map(&mB, P.planes, P.n_pad, P.k_cap, kColBlock);
+  rc = make_plane_map(&mB, P.planes, P.n_pad, P.k_cap, kColBlock, kCps);
   if (rc) return rc;
   if ((rc = gemm_attr())) return rc;
   const int64_t grid = tiles < num_sms() ? tiles : num_sms();
@@ -935,9 +1453,9 @@ int rank_dist_gemm_launch(const RankPtrs &P, const int64_t *ln_table, int32_t b,
   const int64_t tiles = P.tiles_total;
   if (tiles == 0) return SAD_OK;
   CUtensorMap mA, mB;
-  int rc = make_plane_map(&mA, P.planes, P.n_pad, P.k_cap, kRowBlock);
+  int rc = make_plane_map(&mA, P.planes, P.n_pad, P.k_cap, kRowBlock, kCps);
   if (rc) return rc;
-  rc = make_plane_map(&mB, P.planes, P.n_pad, P.k_cap, kColBlock);
+  rc = make_plane_map(&mB, P.planes, P.n_pad, P.k_cap, kColBlock, kCps);
   if (rc) return rc;
   if ((rc = gemm_attr())) return rc;
   DistArgs Z;
@@ -962,9 +1480,9 @@ int rank_rect_gemm_launch(const RankPtrs &P, uint8_t *ref_planes, const uint4 *r
   if (tiles > 0x7FFFFFFF) return SAD_ERR_UNSUPPORTED;
   X.n_tiles = (int32_t)tiles;
   CUtensorMap mA, mB;
-  int rc = make_plane_map(&mA, P.planes, P.n_pad, P.k_cap, kRowBlock);
+  int rc = make_plane_map(&mA, P.planes, P.n_pad, P.k_cap, kRowBlock, kCps);
   if (rc) return rc;
-  rc = make_plane_map(&mB, ref_planes, ref_rows, P.k_cap, kColBlock);
+  rc = make_plane_map(&mB, ref_planes, ref_rows, P.k_cap, kColBlock, kCps);
   if (rc) return rc;
   if ((rc = gemm_attr())) return rc;
   const int64_t grid = tiles < num_sms() ? tiles : num_sms();

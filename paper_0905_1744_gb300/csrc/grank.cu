@@ -199,7 +199,7 @@ int local_samples_launch(const uint64_t *key_hi, const uint64_t *key_lo, int32_t
 }
 
 size_t rank_vs_ws_bytes(int64_t n, int64_t eps, int64_t k_cap, int64_t n_ref, int32_t delta_den) {
-  const RankLayout L = rank_layout(shape_single(n), eps, RankCaps{0, 0, k_cap, 0, 0, 0, 0});
+  const RankLayout L = rank_layout(shape_single(n), eps, RankCaps{0, 0, 0, k_cap, 0, 0, 0, 0});
   return ref_layout(L.bytes, L.shape.rows_total, n_ref, k_cap, delta_den).bytes;
 }
 
@@ -207,7 +207,7 @@ int rank_vs_launch(const int32_t *counts, const int32_t *lengths, const int32_t 
                    int32_t n, int32_t k, int64_t eps, const int32_t *ref, int32_t n_ref,
                    int64_t k_cap, int32_t delta_den, int64_t *key, uint64_t *key_hi,
                    uint64_t *key_lo, double *rank, void *ws, size_t ws_bytes, cudaStream_t st) {
-  const RankLayout L = rank_layout(shape_single(n), eps, RankCaps{0, 0, k_cap, 0, 0, 0, 0});
+  const RankLayout L = rank_layout(shape_single(n), eps, RankCaps{0, 0, 0, k_cap, 0, 0, 0, 0});
   const RefLayout R = ref_layout(L.bytes, L.shape.rows_total, n_ref, k_cap, delta_den);
   if (ws_bytes < R.bytes) return SAD_ERR_WORKSPACE;
   if (L.shape.rows_total / kRowBlock > kMaxRowBlocks) return SAD_ERR_UNSUPPORTED;

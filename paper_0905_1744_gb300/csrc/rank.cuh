@@ -76,6 +76,7 @@ struct RankPtrs {
   int64_t n_total, n_sets, tiles_total, k_cap, list_cap, rem_cap, heavy_cap, bm_cols;
   int32_t depth_cap;     // 0 = all planes
   int32_t budget;        // remainder entries per column block
+  int32_t tile;          // rows of a GEMM tile (and of a remainder block): 128 or 256
   int32_t eps;
   uint64_t wait_ns;      // budget of the GEMM's main-loop waits
 };
@@ -137,8 +138,9 @@ int sparse_rank_launch(const int32_t *counts, const int32_t *lengths, int32_t n,
                        double *rank, void *ws, size_t ws_bytes, cudaStream_t st);
 
 // TMA map of a plane matrix (rows x K_cap / 2 bytes, 128-byte swizzle, boxes of
-// 128 bytes x box_rows rows).
-int make_plane_map(CUtensorMap *map, uint8_t *planes, int64_t rows, int64_t k_cap, int box_rows);
+// 128 bytes x box_rows rows x box_chunks K chunks).
+int make_plane_map(CUtensorMap *map, uint8_t *planes, int64_t rows, int64_t k_cap, int box_rows,
+                   int box_chunks);
 int rank_finalize_launch(const RankPtrs &P, uint64_t *key_hi, uint64_t *key_lo, double *rank,
                          cudaStream_t st);
 int64_t host_tile_count(int32_t n);

@@ -101,6 +101,7 @@ RankPtrs rank_ptrs(void *ws, const RankLayout &L) {
   P.bm_cols = L.caps.bm_cols;
   P.depth_cap = L.caps.depth;
   P.budget = L.caps.budget > 0 ? L.caps.budget : kRemBudgetDefault;
+  P.tile = L.caps.tile == 2 * kRowBlock ? 2 * kRowBlock : kRowBlock;
   P.eps = 0;
   P.wait_ns = gemm_wait_ns();
   return P;
@@ -910,7 +911,7 @@ __global__ void __launch_bounds__(256) planes_stream_kernel(const int32_t *__res
 }
 
 // ------------------------------------------------------------ remainder ----
-// Per column block b (128 stored rows, one thread each): N_b(d) = the block's
+// Per column block b (B = P.tile stored rows, one thread each): N_b(d) = the block's
 // remainder entries at plane depth d (its rows' thresholds whose covering depth is
 // above d), for d = 1..min(dkeep, largest count); the block's depth d_b is the
 // smallest d with N_b(d) <= budget (else the largest). Each row's entries at d_b
@@ -918,7 +919,7 @@ __global__ void __launch_bounds__(256) planes_stream_kernel(const int32_t *__res
 // blkrem for the scan. Profile slot j of a row counts the thresholds whose
 // covering depth is j + 1 (slot dkeep: above the planes); at depth d the slots
 // j >= d are uncovered.
-constexpr int kRemThreads = kColBlock;
+constexpr int kRemThreads = 2 * kColBlock;  // largest block (CTA-pair tiles)
 
 __global__ void __launch_bounds__(kRemThreads) rem_depth_kernel(RankPtrs P) {
   pdl_enter();
@@ -927,9 +928,10 @@ __global__ void __launch_bounds__(kRemThreads) rem_depth_kernel(RankPtrs P) {
   __shared__ int32_t s_warp[32];
   if (P.hdr->status != 0) return;
   const int32_t dkeep = P.hdr->depth;
-  const int64_t nblk = P.n_pad / kColBlock;
+  const int64_t B = P.tile;  // == blockDim.x
+  const int64_t nblk = P.n_pad / B;
   for (int64_t b = blockIdx.x; b < nblk; b += gridDim.x) {
-    const int64_t v = b * kColBlock + threadIdx.x;
+    const int64_t v = b * B + threadIdx.x;
     uint32_t pr[kProf];
 #pragma unroll
     for (int j = 0; j < kProf; ++j) pr[j] = P.prof[v * kProf + j];
@@ -947,7 +949,9 @@ __global__ void __launch_bounds__(kRemThreads) rem_depth_kernel(RankPtrs P) {
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      const int32_t bmax = P.depth[b];
+      int32_t bmax = 0;
+      for (int64_t b1 = b * (B / kRowBlock); b1 < (b + 1) * (B / kRowBlock); ++b1)
+        bmax = max(bmax, P.depth[b1]);
       const int32_t dcap = max(1, min(dkeep, bmax));
       int32_t d = dcap;
       for (int32_t dd = 1; dd < dcap; ++dd)
@@ -956,7 +960,7 @@ __global__ void __launch_bounds__(kRemThreads) rem_depth_kernel(RankPtrs P) {
           break;
         }
       s_d = d;
-      P.bdepth[b] = d;
+      for (int64_t b1 = b * (B / kRowBlock); b1 < (b + 1) * (B / kRowBlock); ++b1) P.bdepth[b1] = d;
       if (d < bmax) atomicAdd(&P.hdr->rem_blocks, 1);
     }
     __syncthreads();
@@ -986,7 +990,7 @@ __global__ void __launch_bounds__(1024) rem_scan_kernel(RankPtrs P) {
   __shared__ int64_t s_warp[32];
   __shared__ int64_t s_carry[2];
   if (P.hdr->status != 0) return;
-  const int64_t nblk = P.n_pad / kColBlock;
+  const int64_t nblk = P.n_pad / P.tile;
   if (threadIdx.x < 2) s_carry[threadIdx.x] = 0;
   __syncthreads();
   for (int64_t base = 0; base < nblk; base += blockDim.x) {
@@ -1032,8 +1036,8 @@ __global__ void __launch_bounds__(256) rem_scatter_kernel(RankPtrs P) {
     const int64_t pos = f.x;
     const int32_t tau = f.y & 0xFFFF;
     const int32_t c = (int32_t)((uint32_t)f.y >> 16);
-    const int64_t b = pos / kColBlock;
-    const int32_t d = P.bdepth[b];
+    const int64_t b = pos / P.tile;
+    const int32_t d = P.bdepth[pos / kRowBlock];
     const int64_t base = P.blkrem[2 * b] + P.rowrem[2 * pos];
     const int32_t top = min(c, tb);
     for (int32_t t = 2; t <= top; ++t) {
@@ -1052,8 +1056,8 @@ __global__ void __launch_bounds__(256) rem_scatter_kernel(RankPtrs P) {
 }
 
 // Upper-triangle tile list of every set (blocks per set and column group). Tile (I, J) of a
-// set covers its stored rows [128 I, 128 I + 128) and columns [128 J, 128 J + 128)
-// (set-local, kColBlock = 128); it is needed when some pair i <= j lies in it
+// set covers its stored rows [B I, B I + B) and columns [B J, B J + B), B = P.tile
+// (set-local; 128, or 256 for CTA pairs); it is needed when some pair i <= j lies in it
 // (I <= J) and both ranges hold real rows. Tiles are grouped by G column blocks,
 // rows ascending inside a group, so that the tiles running at the same time share
 // their operand panels in L2: a group's G column panels stay in L2 while the row
@@ -1062,20 +1066,20 @@ __global__ void __launch_bounds__(256) rem_scatter_kernel(RankPtrs P) {
 // block indices: nk plane K chunks, up to the end of section e = min(largest count
 // of I, largest count of J, plane depth of J) (the kept depth when nothing is cut),
 // and nx remainder K chunks of 256 entries of column block J.
-// Column blocks per tile group: G panels of 128 rows x K_cap / 2 bytes within
+// Column blocks per tile group: G panels of `rows` rows x K_cap / 2 bytes within
 // kGroupL2Bytes, between 8 and 64.
 constexpr int64_t kGroupL2Bytes = 40ll << 20;
-inline int32_t group_cols(int64_t k_cap) {
-  const int64_t panel = (int64_t)kColBlock * (k_cap > 0 ? k_cap : kKCols) / 2;
+inline int32_t group_cols(int64_t k_cap, int64_t rows) {
+  const int64_t panel = rows * (k_cap > 0 ? k_cap : kKCols) / 2;
   const int64_t g = kGroupL2Bytes / panel;
   return (int32_t)(g < 8 ? 8 : (g > 64 ? 64 : g));
 }
 // remainder entries per extra K chunk of a tile: one K column each
 constexpr int kRemChunkCols = kKCols;
 
-// Tiles of column group g of a set: rows I with J in [8g, 8g + 8) and J >= I / kColRatio.
+// Tiles of column group g of a set: rows I with J in [G g, G g + G) and J >= I.
 __device__ __forceinline__ int32_t group_row_tiles(int32_t g, int32_t I, int32_t C, int32_t G) {
-  const int32_t j0 = max(g * G, I / kColRatio);
+  const int32_t j0 = max(g * G, I);
   const int32_t j1 = min((g + 1) * G, C);
   return max(0, j1 - j0);
 }
@@ -1089,12 +1093,13 @@ __global__ void __launch_bounds__(256) tiles_kernel(RankPtrs P, int32_t G) {
   const int32_t nblk = (int32_t)(P.n_pad / kRowBlock);
   const int32_t dkeep = P.hdr->depth;
   const bool rem = remainder_mode(P);
+  const int32_t B = P.tile, sub = P.tile / kRowBlock;  // tile rows, 128-row blocks in one
   for (int32_t si = blockIdx.y; si < (int32_t)P.n_sets; si += gridDim.y) {
     const RankSet e = P.sets[si];
     const int32_t n = e.n;
-    const int32_t R = (n + kRowBlock - 1) / kRowBlock;
-    const int32_t C = (n + kColBlock - 1) / kColBlock;
-    const int32_t I0 = (int32_t)(e.row_base / kRowBlock), J0 = (int32_t)(e.row_base / kColBlock);
+    const int32_t R = (n + B - 1) / B;
+    const int32_t C = R;
+    const int32_t I0 = (int32_t)(e.row_base / B), J0 = (int32_t)(e.row_base / B);
     const int32_t groups = (C + G - 1) / G;
     for (int32_t g = blockIdx.x; g < groups; g += gridDim.x) {
       // tiles of the groups before g come first
@@ -1113,14 +1118,16 @@ __global__ void __launch_bounds__(256) tiles_kernel(RankPtrs P, int32_t G) {
         const int32_t incl = block_scan_incl<int32_t>(cnt, s_warp, &tot);
         int64_t out = e.tile_base + s_carry + incl - cnt;
         if (cnt > 0) {
-          const int32_t dI = P.depth[I0 + I];
-          const int32_t j0 = max(g * G, I / kColRatio);
+          // largest counts of the tile's row and column blocks (sub 128-row blocks each)
+          int32_t dI = 0;
+          for (int32_t b = sub * (I0 + I); b < sub * (I0 + I + 1) && b < nblk; ++b)
+            dI = max(dI, P.depth[b]);
+          const int32_t j0 = max(g * G, I);
           for (int32_t J = j0; J < j0 + cnt; ++J) {
-            // the column block spans row blocks kColRatio (J0 + J) .. + kColRatio - 1
             int32_t dJ = 0;
-            for (int32_t b = kColRatio * (J0 + J); b < kColRatio * (J0 + J + 1) && b < nblk; ++b)
+            for (int32_t b = sub * (J0 + J); b < sub * (J0 + J + 1) && b < nblk; ++b)
               dJ = max(dJ, P.depth[b]);
-            const int32_t cut = rem ? P.bdepth[J0 + J] : dkeep;
+            const int32_t cut = rem ? P.bdepth[sub * (J0 + J)] : dkeep;
             const int32_t d = min(min(dI, dJ), cut);
             const int32_t kend = P.secend[max(d, 0)];
             const int32_t nk = max(1, (kend + kKCols - 1) / kKCols);
@@ -1267,8 +1274,9 @@ int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *le
     SAD_LAUNCH_CHECK();
   }
   if (rem) {
-    const int64_t nblk = Q.n_pad / kColBlock;
-    pdl_launch(rem_depth_kernel, (unsigned)(nblk < 65535 ? nblk : 65535), kRemThreads, 0, st, Q);
+    const int64_t nblk = Q.n_pad / Q.tile;
+    pdl_launch(rem_depth_kernel, (unsigned)(nblk < 65535 ? nblk : 65535), (unsigned)Q.tile, 0, st,
+               Q);
     SAD_LAUNCH_CHECK();
     pdl_launch(rem_scan_kernel, 1, 1024, 0, st, Q);
     SAD_LAUNCH_CHECK();
@@ -1277,8 +1285,8 @@ int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *le
   }
   {
     // one set: a CTA per column group; batches: a few per set
-    const int32_t G = group_cols(Q.k_cap);
-    const int64_t groups1 = ((n + kColBlock - 1) / kColBlock + G - 1) / G;
+    const int32_t G = group_cols(Q.k_cap, Q.tile);
+    const int64_t groups1 = ((n + Q.tile - 1) / Q.tile + G - 1) / G;
     dim3 g((unsigned)(Q.n_sets == 1 ? (groups1 > 0 ? groups1 : 1) : 4), gsets);
     pdl_launch(tiles_kernel, g, 256, 0, st, Q, G);
   }

@@ -92,6 +92,7 @@ __host__ __device__ __forceinline__ bool item_less(const Item &a, const Item &b)
 struct RankCaps {
   int32_t depth;         // plane depth D; 0 = all sections, no remainder
   int32_t budget;        // remainder entries per column block (0 = kRemBudgetDefault)
+  int32_t tile;          // GEMM tile rows: 128 (one CTA a tile) or 256 (CTA pairs)
   int64_t k_cap;         // plane columns
   int64_t list_cap;      // entries (sequence, word) counted twice or more
   int64_t rem_cap;       // remainder entries (bitmap columns)
@@ -121,16 +122,14 @@ struct RankShape {
   int64_t n_sets, n_total, rows_total, tiles_total, tileof_total;
 };
 
-inline int64_t n_pad_of(int64_t n) { return (int64_t)align_up((size_t)(n > 0 ? n : 1), kNPad); }
+inline int64_t n_pad_of(int64_t n, int64_t align = kNPad) {
+  return (int64_t)align_up((size_t)(n > 0 ? n : 1), (size_t)align);
+}
 
-inline int64_t tiles_of_set(int64_t n) {
-  const int64_t R = (n + kRowBlock - 1) / kRowBlock, C = (n + kColBlock - 1) / kColBlock;
-  int64_t total = 0;
-  for (int64_t I = 0; I < R; ++I) {
-    const int64_t j0 = I / kColRatio;  // smallest J whose columns reach row block I
-    if (j0 < C) total += C - j0;
-  }
-  return total;
+// Upper-triangle tiles of a set of n rows in square tiles of B rows.
+inline int64_t tiles_of_set(int64_t n, int64_t B = kRowBlock) {
+  const int64_t R = (n + B - 1) / B;
+  return R * (R + 1) / 2;
 }
 
 inline void shape_add_set(RankShape &sh, int64_t n) {
@@ -142,9 +141,15 @@ inline void shape_add_set(RankShape &sh, int64_t n) {
   sh.tileof_total += (np / kRowBlock) * (np / kColBlock);
 }
 
-inline RankShape shape_single(int64_t n) {
+// One set; with tile = 256 (CTA pairs) its rows are padded to 256 and its tiles are
+// the 256 x 256 tiles of the upper triangle.
+inline RankShape shape_single(int64_t n, int64_t tile = kRowBlock) {
   RankShape sh{0, 0, 0, 0, 0};
   shape_add_set(sh, n);
+  if (tile == 2 * kRowBlock) {
+    sh.rows_total = n_pad_of(n, tile);
+    sh.tiles_total = tiles_of_set(n, tile);
+  }
   return sh;
 }
 

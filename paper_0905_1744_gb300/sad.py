@@ -26,7 +26,8 @@ _DEVICE_TYPE = "cuda"       # where every tensor handed to the library must live
 class RankPlan(ctypes.Structure):
     """sad_rank_plan: depth and budget in; sizes and capacities out (see include/sad.h)."""
     _fields_ = [("depth", ctypes.c_int32), ("budget", ctypes.c_int32),
-                ("t_max", ctypes.c_int32), ("t_bits", ctypes.c_int32),
+                ("tile", ctypes.c_int32), ("t_max", ctypes.c_int32),
+                ("t_bits", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("k_eff", ctypes.c_int64), ("list_entries", ctypes.c_int64),
                 ("rem_bound", ctypes.c_int64), ("heavy_entries", ctypes.c_int64),
                 ("k_cap", ctypes.c_int64), ("list_cap", ctypes.c_int64),
@@ -253,26 +254,35 @@ def kmer_count(codes: torch.Tensor, offsets: torch.Tensor, k: int = 3, alphabet:
 
 
 def kmer_rank_plan(counts: torch.Tensor, k: int = 3, alphabet: int = 20, depth: int = 0,
-                   ws: Workspace | None = None, stream=None, budget: int = 0) -> RankPlan:
+                   ws: Workspace | None = None, stream=None, budget: int = 0,
+                   tile: int = 0) -> RankPlan:
     """Sizes and capacities for kmer_rank at plane depth ``depth`` (0 = all
-    planes) with ``budget`` remainder entries per column block (0 = default).
+    planes) with ``budget`` remainder entries per column block (0 = default) and
+    GEMM tiles of ``tile`` rows (0/128: one CTA a tile; 256: CTA pairs).
     Synchronous."""
     _need_counts(counts, k, alphabet, "kmer_rank_plan")
     n = counts.shape[0]
     ws = ws or Workspace(counts.device)
     ws.ensure(workspace_bytes(OP_RANK, n, k, alphabet, depth=0))
-    plan = RankPlan(depth=int(depth), budget=int(budget))
-    _check(_load().kmer_rank_plan(_ptr(counts), n, k, alphabet, ctypes.byref(plan),
-                                  _ptr(ws.buf), ws.nbytes, _stream(stream)), "kmer_rank_plan")
+    plan = RankPlan(depth=int(depth), budget=int(budget), tile=int(tile))
+    rc = _load().kmer_rank_plan(_ptr(counts), n, k, alphabet, ctypes.byref(plan), _ptr(ws.buf),
+                                ws.nbytes, _stream(stream))
+    if rc == ERR_WORKSPACE and plan.ws_bytes > ws.nbytes:
+        # the fixed part of a layout with other padding (tile = 256): the size it needs
+        ws.ensure(plan.ws_bytes)
+        plan = RankPlan(depth=int(depth), budget=int(budget), tile=int(tile))
+        rc = _load().kmer_rank_plan(_ptr(counts), n, k, alphabet, ctypes.byref(plan),
+                                    _ptr(ws.buf), ws.nbytes, _stream(stream))
+    _check(rc, "kmer_rank_plan")
     return plan
 
 
 def kmer_rank_plan_bound(n: int, total_len: int, k: int = 3, alphabet: int = 20,
-                         depth: int = 1, budget: int = 0) -> RankPlan:
+                         depth: int = 1, budget: int = 0, tile: int = 0) -> RankPlan:
     """Capacities for kmer_rank at plane depth ``depth`` >= 1 that hold for any
     counts of ``n`` sequences of ``total_len`` residues in all: no device work and
     no synchronisation (bounds from the number of windows; see include/sad.h)."""
-    plan = RankPlan(depth=int(depth), budget=int(budget))
+    plan = RankPlan(depth=int(depth), budget=int(budget), tile=int(tile))
     _check(_load().kmer_rank_plan_bound(int(n), int(total_len), k, alphabet, ctypes.byref(plan)),
            "kmer_rank_plan_bound")
     return plan

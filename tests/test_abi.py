@@ -39,7 +39,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_host_only_queries(lib):
     lib.sad_abi_version.restype = ctypes.c_int
-    assert lib.sad_abi_version() == 5
+    assert lib.sad_abi_version() == 6
     lib.sad_status_string.restype = ctypes.c_char_p
     lib.sad_status_string.argtypes = [ctypes.c_int]
     assert lib.sad_status_string(0) == b"ok"
@@ -74,7 +74,8 @@ class _Plan(ctypes.Structure):
     """sad_rank_plan as include/sad.h declares it (written out here, independently
     of the binding's copy)."""
     _fields_ = [("depth", ctypes.c_int32), ("budget", ctypes.c_int32),
-                ("t_max", ctypes.c_int32), ("t_bits", ctypes.c_int32),
+                ("tile", ctypes.c_int32), ("t_max", ctypes.c_int32),
+                ("t_bits", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("k_eff", ctypes.c_int64), ("list_entries", ctypes.c_int64),
                 ("rem_bound", ctypes.c_int64), ("heavy_entries", ctypes.c_int64),
                 ("k_cap", ctypes.c_int64), ("list_cap", ctypes.c_int64),
