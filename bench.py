@@ -119,16 +119,18 @@ def parse(argv=None):
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tile", type=int, default=256, choices=[128, 256],
+                    help="GEMM tile rows with --depth (default: the autotuner's choice)")
     ap.add_argument("--depth", type=int, default=None,
                     help="threshold-plane depth (default: the autotuner's choice)")
     ap.add_argument("--no-batching", action="store_true")
     ap.add_argument("--no-global", action="store_true",
                     help="skip the globalised-rank, distance-form and Table 1 legs")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=2000)
-    ap.add_argument("--serve-warmup", type=int, default=200)
+    ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--serve-warmup", type=int, default=100)
     ap.add_argument("--serve-rate", type=float, default=200.0)
-    ap.add_argument("--serve-pool", type=int, default=64)
+    ap.add_argument("--serve-pool", type=int, default=256)
     ap.add_argument("--serve-burst", type=int, default=400)
     ap.add_argument("--batch-sets", type=int, default=512)
     ap.add_argument("--batch-reps", type=int, default=10)
@@ -326,72 +328,111 @@ def gemm_traffic_per_launch(n: int, k_eff: int):
 
 
 def run_batching(args, dev):
-    """512 uneven sets: one plan, one captured CUDA graph per batch (count ->
-    block-diagonal rank -> batched partition), against the plain per-set path."""
+    """512 uneven sets in one block-diagonal launch. The tile shape and plane depth
+    come from the batching autotuner (timed on plans from host-side bounds); then
+    every timed batch is a NEW batch as a user sees it: its inputs go up from
+    pinned memory, its plan comes from host-side bounds (no synchronisation), its
+    launches are captured into the one library graph (updated in place, not
+    re-instantiated) and launched, and its bucket lists come back to pinned host
+    memory. Two different 512-set batches alternate, so each launch of the graph
+    runs other buffers and sizes than the one before. Against the plain per-set
+    path: each set's inputs up, partition_set with the same plan shape, its
+    bucket lists back."""
     import torch
 
-    from paper_0905_1744_gb300 import sad
-    sets = datagen.config4(args.seed, n_sets=args.batch_sets)
-    n = np.array([x.n for x in sets], dtype=np.int64)
-    pairs = float((n * (n - 1) // 2).sum())
-    b = sad.Batch(sets, device=dev)
-    # plane depth for the whole batch: timed eager runs of each candidate
-    trials = {}
-    for d in (1, 2, 3, 0):
-        b.plan(depth=d)
-        b.run()
-        torch.cuda.synchronize(dev)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        b.run()
-        e1.record()
-        e1.synchronize()
-        b.check()
-        trials[d] = e0.elapsed_time(e1)
-    depth = min(trials, key=trials.get)
-    plan = b.plan(depth=depth)
-    b.capture()
-    for _ in range(3):
-        b.replay()
+    from paper_0905_1744_gb300 import autotune, sad
+    sets_a = datagen.config4(args.seed, n_sets=args.batch_sets)
+    sets_b = datagen.config4(args.seed + 1, n_sets=args.batch_sets)
+    st = torch.cuda.Stream(dev)
+    ws = (sad.Workspace(dev, 256), sad.Workspace(dev), sad.Workspace(dev))
+    ba = sad.Batch(sets_a, device=dev, workspaces=ws, stream=st)
+    bb = sad.Batch(sets_b, device=dev, workspaces=ws, stream=st)
+    shape, trials = autotune.choose_batch_shape(ba, use_cache=False, stream=st)
+    g = sad.Graph()
+    outs = {}
+    for b in (ba, bb):
+        outs[id(b)] = (torch.empty(b.members.shape, dtype=torch.int32).pin_memory(),
+                       torch.empty(b.bucket_offsets.shape, dtype=torch.int32).pin_memory())
+
+    def new_batch(b):
+        b.upload(st)
+        b.plan(depth=shape.depth, tile=shape.tile, budget=shape.budget, stream=st)
+        b.capture(g, stream=st)
+        g.launch(st)
+        h_mem, h_boff = outs[id(b)]
+        with torch.cuda.stream(st):
+            h_mem.copy_(b.members, non_blocking=True)
+            h_boff.copy_(b.bucket_offsets, non_blocking=True)
+
+    for b in (ba, bb, ba, bb):
+        new_batch(b)
+        st.synchronize()
+        b.check(st)
     torch.cuda.synchronize(dev)
-    times = []
-    for _ in range(args.batch_reps):
+    launches0 = sad.launch_count()
+    dev_ms, wall_ms = [], []
+    for r in range(args.batch_reps):
+        b = ba if r % 2 == 0 else bb
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        b.replay()
-        e1.record()
-        e1.synchronize()
-        times.append(e0.elapsed_time(e1))
-    b.check()
-    ms = statistics.median(times)
-    # plain per-set path: the public per-set call, one set after the other
-    ws = sad.Workspace(dev)
-    d_sets = [(torch.from_numpy(x.codes).to(dev), torch.from_numpy(x.offsets).to(dev), x.p)
-              for x in sets]
-    torch.cuda.synchronize(dev)
-    for c, o, p in d_sets[:4]:
-        sad.partition_set(c, o, p, ws=ws, depth=depth)
+        t0 = time.perf_counter()
+        e0.record(st)
+        new_batch(b)
+        e1.record(st)
+        st.synchronize()
+        wall_ms.append(1e3 * (time.perf_counter() - t0))
+        dev_ms.append(e0.elapsed_time(e1))
+        b.check(st)
+    launches = sad.launch_count() - launches0
+    gstats = g.stats()
+    ms = statistics.median(wall_ms)
+    n_a = np.array([x.n for x in sets_a], dtype=np.int64)
+    n_b = np.array([x.n for x in sets_b], dtype=np.int64)
+    pairs = float(((n_a * (n_a - 1) // 2).sum() + (n_b * (n_b - 1) // 2).sum()) / 2)
+    # plain per-set path on batch A: inputs up, the public per-set call, buckets back
+    wsp = sad.Workspace(dev)
+    h_sets = [(torch.from_numpy(x.codes).pin_memory(), torch.from_numpy(x.offsets).pin_memory(),
+               x.p) for x in sets_a]
+
+    def plain_one(c, o, p):
+        res = sad.partition_set(c.to(dev, non_blocking=True), o.to(dev, non_blocking=True), p,
+                                ws=wsp, depth=shape.depth, tile=shape.tile,
+                                budget=shape.budget)
+        return {k: res[k].cpu() for k in ("members", "bucket_offsets", "key_hi", "key_lo",
+                                          "pivot_idx")}
+    for c, o, p in h_sets[:4]:
+        plain_one(c, o, p)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    plain = [sad.partition_set(c, o, p, ws=ws, depth=depth) for c, o, p in d_sets]
+    plain = [plain_one(c, o, p) for c, o, p in h_sets]
     torch.cuda.synchronize(dev)
     t_plain = time.perf_counter() - t0
+    # batch A's results (its last run) against the plain per-set results
+    new_batch(ba)
+    st.synchronize()
+    ba.check(st)
     exact = True
-    for i in range(0, len(sets), max(1, len(sets) // 16)):
-        got = b.result(i)
+    for i in range(0, len(sets_a), max(1, len(sets_a) // 32)):
+        got = ba.result(i)
         for key in ("key_hi", "key_lo", "bucket_offsets", "members", "pivot_idx"):
-            exact &= bool(np.array_equal(got[key], plain[i][key].cpu().numpy()))
+            exact &= bool(np.array_equal(got[key], plain[i][key].numpy()))
+    h2d = (ba.h2d_bytes + bb.h2d_bytes) / 2
+    d2h = sum(t.numel() * 4 for t in outs[id(ba)]) / 2 + sum(t.numel() * 4 for t in outs[id(bb)]) / 2
     return {
-        "workload": f"{len(sets)} sets, N log-uniform 50-5000, L log-uniform 50-2000, "
-                    "5-100 families per set, p = ceil(N/500)",
-        "sets": len(sets), "sequences": int(n.sum()), "pairs": pairs,
-        "ms_per_batch": ms, "sets_per_s": len(sets) / (ms / 1e3),
-        "pairs_per_s": pairs / (ms / 1e3),
-        "plain_ms_per_batch": 1e3 * t_plain, "plain_sets_per_s": len(sets) / t_plain,
+        "workload": f"{len(sets_a)} sets a batch, N log-uniform 50-5000, L log-uniform 50-2000, "
+                    "5-100 families per set, p = ceil(N/500); two batches (seeds "
+                    f"{args.seed}, {args.seed + 1}) alternate",
+        "sets": len(sets_a), "sequences": int((n_a.sum() + n_b.sum()) // 2), "pairs": pairs,
+        "ms_per_batch": ms, "device_ms_per_batch": statistics.median(dev_ms),
+        "sets_per_s": len(sets_a) / (ms / 1e3), "pairs_per_s": pairs / (ms / 1e3),
+        "plain_ms_per_batch": 1e3 * t_plain, "plain_sets_per_s": len(sets_a) / t_plain,
         "speedup_vs_plain": (t_plain * 1e3) / ms,
-        "depth": depth, "depth_trials_ms": {str(k): v for k, v in trials.items()},
-        "graph": "one CUDA graph replay per batch",
-        "rows": int(plan.rows_total), "tiles": int(plan.tiles_total),
+        "timing": "per new batch, host wall clock: pinned H2D of codes/offsets/sizes, bound "
+                  "plan, graph capture + in-place update, graph launch, D2H of members and "
+                  "bucket offsets, stream synchronize; plain: per set H2D, partition_set, D2H",
+        "h2d_bytes_per_batch": int(h2d), "d2h_bytes_per_batch": int(d2h),
+        "shape": shape._asdict(), "autotune_trial_ms": trials,
+        "graph": gstats, "gpu_launches_per_batch": launches / max(args.batch_reps, 1),
+        "rows": int(ba.plan_.rows_total), "tiles": int(ba.plan_.tiles_total),
         "exact_vs_plain": exact,
     }
 
@@ -539,37 +580,51 @@ def run_table1(args, dev, seed: int = 0):
                                           np.argsort(np.argsort(gl)))[0, 1])}
 
 
-def run_serving(args, dev, depth):
+def run_serving(args, dev, shape=None):
     """Poisson arrivals of sets (N log-uniform 100-20000, p = 16) served with
-    continuous batching under a 150 GB HBM budget, and the same arrivals served
-    one at a time with the plain per-set calls."""
+    continuous batching under a 150 GB HBM budget (plan-free admission, one reusable
+    graph per slot), and the same arrivals served one at a time with the plain
+    per-set calls, both with the same plan shape (the batching autotuner's, on a
+    batch of serving sets when none is given)."""
     import torch
 
-    from paper_0905_1744_gb300 import serve
+    from paper_0905_1744_gb300 import autotune, sad, serve
     pool = datagen.many_sets("serve", range(args.serve_pool), args.seed)
+    if shape is None:
+        probe = sad.Batch(pool[:8], device=dev)
+        shape, _ = autotune.choose_batch_shape(probe, use_cache=False)
+        shape = tuple(shape)
+        del probe
     total = args.serve_warmup + args.serve_requests
     arrivals = datagen.poisson_arrivals(total, args.serve_rate, args.seed)
     out = {"workload": f"Poisson arrivals at {args.serve_rate:g} sets/s, {args.serve_requests} "
-                       f"timed after {args.serve_warmup} warm-up, sets drawn from a pool of "
-                       f"{len(pool)} (N log-uniform 100-20000, L log-uniform 50-2000, p = 16)",
-           "budget_gb": 150, "depth": depth}
-    mixed = serve.serve(serve.make_requests(pool, arrivals), depth=depth, device=dev)
-    plain = serve.serve_plain(serve.make_requests(pool, arrivals), depth=depth, device=dev)
-    out["continuous_batching"] = serve.latency_stats(mixed, args.serve_warmup)
+                       f"timed after {args.serve_warmup} warm-up, request i is set i mod "
+                       f"{len(pool)} of a pool of {len(pool)} distinct sets (N log-uniform "
+                       "100-20000, L log-uniform 50-2000, p = 16)",
+           "budget_gb": 150, "shape": dict(zip(("tile", "depth", "budget"), shape))}
+    st_mixed = {}
+    mixed = serve.serve(serve.make_requests(pool, arrivals), shape=shape, device=dev,
+                        stats=st_mixed)
+    plain = serve.serve_plain(serve.make_requests(pool, arrivals), shape=shape, device=dev)
+    out["continuous_batching"] = {**serve.latency_stats(mixed, args.serve_warmup), **st_mixed}
     out["plain_per_set"] = serve.latency_stats(plain, args.serve_warmup)
     pairs = np.array([r.seqset.n * (r.seqset.n - 1) / 2 for r in mixed[args.serve_warmup:]])
     out["offered_pairs_per_s"] = float(pairs.mean() * args.serve_rate)
     # capacity: a burst of requests all arriving at once (saturated server)
     burst = np.zeros(args.serve_burst)
-    mixed_b = serve.serve(serve.make_requests(pool, burst), depth=depth, device=dev)
-    plain_b = serve.serve_plain(serve.make_requests(pool, burst), depth=depth, device=dev)
+    st_burst = {}
+    mixed_b = serve.serve(serve.make_requests(pool, burst), shape=shape, device=dev,
+                          stats=st_burst)
+    plain_b = serve.serve_plain(serve.make_requests(pool, burst), shape=shape, device=dev)
     out["saturated"] = {
         "requests": int(args.serve_burst),
-        "continuous_batching": serve.latency_stats(mixed_b),
+        "continuous_batching": {**serve.latency_stats(mixed_b), **st_burst},
         "plain_per_set": serve.latency_stats(plain_b),
     }
     out["saturated"]["sets_per_s_ratio"] = (out["saturated"]["continuous_batching"]["sets_per_s"]
                                             / out["saturated"]["plain_per_set"]["sets_per_s"])
+    out["p50_ratio_vs_plain"] = (out["continuous_batching"]["p50_ms"]
+                                 / out["plain_per_set"]["p50_ms"])
     out["exact_vs_plain"] = all(
         np.array_equal(a.result[k], b.result[k]) for a, b in zip(mixed + mixed_b, plain + plain_b)
         for k in ("bucket_offsets", "members", "key_hi", "key_lo"))
@@ -603,14 +658,15 @@ def measure_config(cfg: int, args, dev, world: int, steps: int, warmup: int,
     counts = torch.empty((n, 8000), dtype=torch.int32, device=dev)
     word_max = torch.empty(8000, dtype=torch.int32, device=dev)
     sad.kmer_count(codes, offsets, ws=ws, out=counts, word_max=word_max)
-    # plane depth chosen by the autotuner (timed trials, outside the timed region)
+    # GEMM tile shape, plane depth and remainder budget chosen by the autotuner (timed
+    # trials, outside the timed region)
     if args.depth is None:
-        depth, trials = autotune.choose_depth(counts, lengths, ws, use_cache=False,
+        shape, trials = autotune.choose_shape(counts, lengths, ws, use_cache=False,
                                               word_max=word_max)
     else:
-        depth, trials = args.depth, {}
-    plan = sad.kmer_rank_plan(counts, depth=depth, ws=ws)
-    ws.ensure(plan.ws_bytes)
+        shape, trials = autotune.Shape(args.tile, args.depth, 0), {}
+    depth = shape.depth
+    plan = autotune.plan_for(counts, shape, ws)
     keys = (torch.empty(n, dtype=torch.uint64, device=dev),
             torch.empty(n, dtype=torch.uint64, device=dev),
             torch.empty(n, dtype=torch.float64, device=dev))
@@ -621,6 +677,7 @@ def measure_config(cfg: int, args, dev, world: int, steps: int, warmup: int,
 
     def step():
         sad.kmer_count(codes, offsets, ws=ws, out=counts, check=False, word_max=word_max)
+        sad.seq_lengths(offsets, out=lengths, ws=ws)
         sad.kmer_rank(counts, lengths, ws=ws, out=keys, check=False, plan=plan,
                       word_max=word_max)
         sad.partition(keys[0], keys[1], p, ws=ws_part, out=part, check=False)
@@ -668,11 +725,15 @@ def measure_config(cfg: int, args, dev, world: int, steps: int, warmup: int,
     f4_peak = f4_ratio * pk["bf16_tflops"]
     gemm_launch_ms = gemm_ms / max(gemm_n, 1)
     useful_flops = 2.0 * 8000 * pairs                    # Eq. 1 as written: 2 eps per pair
-    exec_flops = 2.0 * 128 * 128 * 256 * info["k_chunks"]  # MMA work actually issued
+    # MMA work actually issued: K chunks of 256 plane columns over tile x tile tiles
+    exec_flops = 2.0 * shape.tile * shape.tile * 256 * info["k_chunks"]
     achieved = useful_flops / (gemm_launch_ms / 1e3) / 1e12
+    kernel = ("pair_gemm_kernel (CTA pairs, tcgen05.mma.cta_group::2 kind::mxf4nvf4, 256 x 256 "
+              "tiles" if shape.tile == 256 else
+              "plane_gemm_kernel (tcgen05.mma kind::mxf4nvf4, 128 x 128 tiles")
     roofline = {
         "bound": "tensor",
-        "kernel": "plane_gemm_kernel (tcgen05 kind::mxf4nvf4, e2m1 0/1 planes, unit scales)",
+        "kernel": kernel + ", e2m1 0/1 planes, unit scales)",
         "achieved": achieved, "peak": f4_peak, "unit": "TFLOP/s", "frac": achieved / f4_peak,
         "work": "Eq. 1 as written: 2 x 8000 ops (min and add over the 8000 words) per "
                 "unordered pair, N(N-1)/2 pairs per launch",
@@ -725,7 +786,8 @@ def measure_config(cfg: int, args, dev, world: int, steps: int, warmup: int,
         def e2e_step():
             d_codes = h_codes.to(dev, non_blocking=True)
             d_offs = h_offs.to(dev, non_blocking=True)
-            res = sad.partition_set(d_codes, d_offs, p, ws=ws_e, depth=depth)
+            res = sad.partition_set(d_codes, d_offs, p, ws=ws_e, depth=shape.depth,
+                                    tile=shape.tile, budget=shape.budget)
             h_mem.copy_(res["members"], non_blocking=True)
             h_boff.copy_(res["bucket_offsets"], non_blocking=True)
             h_hi.copy_(res["key_hi"], non_blocking=True)
@@ -756,10 +818,12 @@ def measure_config(cfg: int, args, dev, world: int, steps: int, warmup: int,
 
     return {"s": s, "value": value, "ms_per_step": ms_per_step, "steps": steps,
             "warmup": warmup, "launches": int(launches), "clocks": clocks,
-            "autotune": {"depth": depth, "trial_ms": {str(d): t for d, t in trials.items()}},
+            "autotune": {"shape": shape._asdict(), "trial_ms": trials,
+                         "searched": "tile {256, 128} x depth {0,1,2,3,4,6} at the default "
+                                     "budget, then budgets {256, 1536} at the best"},
             "roofline": roofline, "calls": calls, "e2e": e2e, "cpu_baseline": cpu,
             "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms),
-            "tensors": (counts, lengths, word_max, keys, depth, trials)}
+            "tensors": (counts, lengths, word_max, keys, shape, trials)}
 
 
 def extra_line(m: dict) -> dict:
@@ -801,11 +865,11 @@ def run_sad(args):
 
     globalised = distance = table1 = sparse = None
     if not args.no_global and world == 1 and side is not None:
-        counts, lengths, word_max, keys, depth2, trials2 = side["tensors"]
+        counts, lengths, word_max, keys, shape2, trials2 = side["tensors"]
         p2 = side["s"].p
         globalised = run_global(args, dev, counts, lengths, word_max, keys, p2)
-        distance = run_distance(args, dev, counts, lengths, word_max, depth2)
-        sparse = run_sparse(args, dev, counts, lengths, trials2.get(depth2))
+        distance = run_distance(args, dev, counts, lengths, word_max, shape2.depth)
+        sparse = run_sparse(args, dev, counts, lengths, trials2.get(shape2.key))
         table1 = run_table1(args, dev, args.seed)
         for leg in (globalised, distance, sparse):
             leg["on"] = "the paper-scale set: " + WORKLOADS[2]
@@ -814,7 +878,7 @@ def run_sad(args):
         batching = run_batching(args, dev)
     serving = None
     if not args.no_serving and world == 1:
-        serving = run_serving(args, dev, depth=batching["depth"] if batching else 0)
+        serving = run_serving(args, dev)
 
     if rank == 0:
         s = main["s"]

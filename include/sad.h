@@ -34,7 +34,7 @@
 extern "C" {
 #endif
 
-#define SAD_ABI_VERSION 6
+#define SAD_ABI_VERSION 7
 
 typedef enum sad_status {
   SAD_OK = 0,
@@ -280,8 +280,8 @@ int partition_noalloc(const uint64_t *d_key_hi, const uint64_t *d_key_lo, int32_
  *                   workspace).
  *   n_sets, max_p   sets and the largest p_s.
  *   n_total, rows_total, tiles_total, tileof_total  sums over sets of n_s,
- *                   stored rows (n_s rounded up to 128), GEMM tiles and
- *                   tile-map entries.
+ *                   stored rows (n_s rounded up to the plan's tile rows, 128
+ *                   or 256), GEMM tiles and tile-map entries.
  *   sum_p, sum_p1, sum_pp1, sum_pp  sums of p_s, p_s - 1, p_s (p_s - 1), p_s^2.
  *   part_ws_bytes   workspace bytes of sad_batch_partition.
  */
@@ -339,6 +339,59 @@ int sad_batch_partition(const uint64_t *d_key_hi, const uint64_t *d_key_lo, cons
                         const int32_t *d_p, const sad_batch_plan *plan,
                         int32_t *d_bucket_offsets, int32_t *d_members, int32_t *d_pivot_idx,
                         void *d_ws, size_t ws_bytes, void *stream);
+
+/*
+ * sad_batch_plan_bound - the plan of a batch from host-side bounds alone: no
+ * device work, no synchronisation, no look at the counts (the batched form of
+ * kmer_rank_plan_bound, whose capacity rules it applies to the whole batch).
+ *   h_n, h_p   host int32 [n_sets] as for sad_batch_plan_make.
+ *   total_len  residues of all sequences of the batch (off[n_total] - off[0]).
+ *   plan       plan->rank.depth (>= 1), budget and tile in; the rest out
+ *              (rank.t_max, t_bits, k_eff, list_entries, rem_bound and
+ *              heavy_entries are -1: unknown without the counts).
+ * Returns SAD_ERR_INVALID_ARGUMENT for depth < 1, a tile other than 0, 128,
+ * 256, or sizes outside those of sad_batch_plan_make. Batches of the same
+ * per-set sizes and total length get the same plan, so a CUDA graph captured
+ * for one of them (sad_graph_*) can be updated to the next without any device
+ * synchronisation.
+ */
+int sad_batch_plan_bound(const int32_t *h_n, const int32_t *h_p, int32_t n_sets,
+                         int64_t total_len, int32_t k, int32_t alphabet, sad_batch_plan *plan);
+
+/*
+ * sad_seq_lengths - d_lengths[i] = off[i + 1] - off[i] for the n_seq sequences
+ * of an offsets array (the L of Sec. 2's F denominator, as kmer_rank takes it).
+ *   d_offsets  device int64 [n_seq + 1].
+ *   d_lengths  device int32 [n_seq] output.
+ *   d_ws       (nullable) a workspace whose header records SAD_ERR_BAD_INPUT
+ *              for a negative or too long length (that entry is written 0).
+ * Launches one kernel on `stream`; no synchronisation.
+ */
+int sad_seq_lengths(const int64_t *d_offsets, int32_t n_seq, int32_t *d_lengths, void *d_ws,
+                    void *stream);
+
+/*
+ * Reusable CUDA graphs. sad_graph_begin starts stream capture on `stream`
+ * (thread-local mode); the caller then makes asynchronous library calls on it
+ * (for example sad_batch_rank and sad_batch_partition on a bound plan);
+ * sad_graph_end ends the capture. On the first end (*g == NULL) the captured
+ * graph is instantiated into a new handle; on later ends with the same handle
+ * it replaces the instantiated graph's parameters in place when the launch
+ * sequence has the same topology (a new batch of the same plan shape: new
+ * buffers and sizes, no re-instantiation), and is instantiated afresh
+ * otherwise. sad_graph_launch runs the current graph on `stream`.
+ * sad_graph_stats: updates and instantiations so far, kernel nodes of the
+ * current graph. sad_graph_destroy frees the handle (NULL is accepted).
+ * No call made between begin and end may synchronise (the capture fails and
+ * sad_graph_end returns SAD_ERR_CUDA, leaving the handle's graph as it was).
+ * The library's own launches inside a capture are recorded, not run.
+ */
+typedef struct sad_graph_s *sad_graph;
+int sad_graph_begin(void *stream);
+int sad_graph_end(void *stream, sad_graph *g);
+int sad_graph_launch(sad_graph g, void *stream);
+int sad_graph_stats(sad_graph g, int64_t *updates, int64_t *instantiations, int32_t *kernels);
+int sad_graph_destroy(sad_graph g);
 
 /*
  * sad_status_read - SYNCHRONOUS: waits for `stream`, then returns the status

@@ -274,15 +274,15 @@ int rank_run_impl(const int32_t *d_counts, const int32_t *d_lengths, const int32
 }
 
 // Host-side shape of a batch; validates the per-set sizes.
-int batch_shape(const int32_t *h_n, const int32_t *h_p, int32_t n_sets, RankShape *sh,
-                PartTotals *pt, int32_t *max_p) {
+int batch_shape(const int32_t *h_n, const int32_t *h_p, int32_t n_sets, int64_t tile,
+                RankShape *sh, PartTotals *pt, int32_t *max_p) {
   if (n_sets < 1 || !h_n) return SAD_ERR_INVALID_ARGUMENT;
   *sh = RankShape{0, 0, 0, 0, 0};
   *pt = PartTotals{0, 0, 0, 0, 0};
   *max_p = 1;
   for (int32_t s = 0; s < n_sets; ++s) {
     if (h_n[s] < 1) return SAD_ERR_INVALID_ARGUMENT;
-    shape_add_set(*sh, h_n[s]);
+    shape_add_set(*sh, h_n[s], tile);
     if (h_p) {
       const int64_t p = h_p[s];
       if (p < 1 || p > kMaxP || p > h_n[s]) return SAD_ERR_INVALID_ARGUMENT;
@@ -295,6 +295,36 @@ int batch_shape(const int32_t *h_n, const int32_t *h_p, int32_t n_sets, RankShap
     }
   }
   if (sh->n_total > 0x7FFFFFFF) return SAD_ERR_UNSUPPORTED;
+  return SAD_OK;
+}
+
+// Capacities of a plan from host-side bounds alone (no look at the counts): shape
+// sh, total_len residues in all its sequences. Section 3.1.2's counts give
+// K_eff = sum over words of min(T, d) <= eps d; every remainder entry, heavy entry
+// and bitmap column belongs to a k-mer window (total_len - n (k - 1) of them).
+int plan_bound_caps(const RankShape &sh, int64_t total_len, int32_t k, int64_t eps,
+                    sad_rank_plan *plan) {
+  if (sh.rows_total / kRowBlock > kMaxRowBlocks) return SAD_ERR_UNSUPPORTED;
+  const int64_t d = plan->depth < kMaxPlaneDepth ? plan->depth : kMaxPlaneDepth;
+  const int64_t tb = t_bits_of((int32_t)d);
+  int64_t k_cap = (int64_t)align_up((size_t)(eps * d), kKCols);
+  if (k_cap < kKCols) k_cap = kKCols;
+  const int64_t n_seq = sh.n_total;
+  const int64_t windows = total_len - n_seq * (k - 1);
+  int64_t bm = 0;
+  for (int64_t t = 2; t <= tb && windows > 0; ++t) bm += windows / t < eps ? windows / t : eps;
+  plan->t_max = -1;
+  plan->t_bits = -1;
+  plan->k_eff = -1;
+  plan->list_entries = -1;
+  plan->rem_bound = -1;
+  plan->heavy_entries = -1;
+  plan->k_cap = k_cap;
+  plan->list_cap = windows > 0 ? windows / 2 : 0;
+  plan->rem_cap = windows > n_seq ? windows - n_seq : 0;
+  plan->heavy_cap = windows > 0 ? windows / (tb + 1) : 0;
+  plan->bm_cols = bm;
+  plan->ws_bytes = rank_layout(sh, eps, caps_of(plan)).bytes;
   return SAD_OK;
 }
 
@@ -320,29 +350,7 @@ int kmer_rank_plan_bound(int32_t n_seq, int64_t total_len, int32_t k, int32_t al
   if (n_seq < 0 || total_len < 0 || !plan || plan->depth < 1 ||
       !(plan->tile == 0 || plan->tile == kRowBlock || plan->tile == 2 * kRowBlock))
     return SAD_ERR_INVALID_ARGUMENT;
-  const RankShape sh = shape_single(n_seq, tile_of(plan));
-  if (sh.rows_total / kRowBlock > kMaxRowBlocks) return SAD_ERR_UNSUPPORTED;
-  const int64_t d = plan->depth < kMaxPlaneDepth ? plan->depth : kMaxPlaneDepth;
-  const int64_t tb = t_bits_of((int32_t)d);
-  // K_eff = sum over words of min(T, d) <= eps d
-  int64_t k_cap = (int64_t)align_up((size_t)(eps * d), kKCols);
-  if (k_cap < kKCols) k_cap = kKCols;
-  const int64_t windows = total_len - (int64_t)n_seq * (k - 1);
-  int64_t bm = 0;
-  for (int64_t t = 2; t <= tb && windows > 0; ++t) bm += windows / t < eps ? windows / t : eps;
-  plan->t_max = -1;
-  plan->t_bits = -1;
-  plan->k_eff = -1;
-  plan->list_entries = -1;
-  plan->rem_bound = -1;
-  plan->heavy_entries = -1;
-  plan->k_cap = k_cap;
-  plan->list_cap = windows > 0 ? windows / 2 : 0;
-  plan->rem_cap = windows > n_seq ? windows - n_seq : 0;
-  plan->heavy_cap = windows > 0 ? windows / (tb + 1) : 0;
-  plan->bm_cols = bm;
-  plan->ws_bytes = rank_layout(sh, eps, caps_of(plan)).bytes;
-  return SAD_OK;
+  return plan_bound_caps(shape_single(n_seq, tile_of(plan)), total_len, k, eps, plan);
 }
 
 int kmer_rank(const int32_t *d_counts, const int32_t *d_lengths, const int32_t *d_word_max,
@@ -486,33 +494,65 @@ int sad_ln_q(const uint64_t *d_x, int64_t n, int64_t *d_out, void *stream) {
   return ln_q_launch(d_x, n, d_out, static_cast<cudaStream_t>(stream));
 }
 
-int sad_batch_plan_make(const int32_t *d_counts, const int32_t *h_n, const int32_t *h_p,
-                        const int32_t *d_n, int32_t n_sets, int32_t k, int32_t alphabet,
-                        sad_batch_plan *plan, void *d_ws, size_t ws_bytes, void *stream) {
-  const int64_t eps = eps_of(k, alphabet);
-  if (eps < 0) return SAD_ERR_UNSUPPORTED;
-  // batches run one CTA per tile (a set's rows are 128-aligned)
-  if (!plan || !h_p || !d_n || !d_ws || !aligned(d_ws, 256) || plan->rank.depth < 0 ||
-      tile_of(&plan->rank) != kRowBlock)
-    return SAD_ERR_INVALID_ARGUMENT;
-  RankShape sh;
+}  // extern "C"
+
+namespace {
+
+// The host-known part of a batch plan (set totals, partition sizes) from the
+// per-set sizes; the shape for its rank.
+int batch_plan_shape(const int32_t *h_n, const int32_t *h_p, int32_t n_sets,
+                     sad_batch_plan *plan, RankShape *sh) {
   PartTotals pt;
   int32_t max_p;
-  int rc = batch_shape(h_n, h_p, n_sets, &sh, &pt, &max_p);
+  int rc = batch_shape(h_n, h_p, n_sets, tile_of(&plan->rank), sh, &pt, &max_p);
   if (rc) return rc;
   plan->n_sets = n_sets;
   plan->max_p = max_p;
-  plan->n_total = sh.n_total;
-  plan->rows_total = sh.rows_total;
-  plan->tiles_total = sh.tiles_total;
-  plan->tileof_total = sh.tileof_total;
+  plan->n_total = sh->n_total;
+  plan->rows_total = sh->rows_total;
+  plan->tiles_total = sh->tiles_total;
+  plan->tileof_total = sh->tileof_total;
   plan->sum_p = pt.p;
   plan->sum_p1 = pt.p1;
   plan->sum_pp1 = pt.pp1;
   plan->sum_pp = pt.pp;
   plan->part_ws_bytes = part_layout_sets(n_sets, pt).bytes;
+  return SAD_OK;
+}
+
+bool tile_valid(const sad_rank_plan *plan) {
+  return plan->tile == 0 || plan->tile == kRowBlock || plan->tile == 2 * kRowBlock;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sad_batch_plan_make(const int32_t *d_counts, const int32_t *h_n, const int32_t *h_p,
+                        const int32_t *d_n, int32_t n_sets, int32_t k, int32_t alphabet,
+                        sad_batch_plan *plan, void *d_ws, size_t ws_bytes, void *stream) {
+  const int64_t eps = eps_of(k, alphabet);
+  if (eps < 0) return SAD_ERR_UNSUPPORTED;
+  if (!plan || !h_p || !d_n || !d_ws || !aligned(d_ws, 256) || plan->rank.depth < 0 ||
+      !tile_valid(&plan->rank))
+    return SAD_ERR_INVALID_ARGUMENT;
+  RankShape sh;
+  int rc = batch_plan_shape(h_n, h_p, n_sets, plan, &sh);
+  if (rc) return rc;
   return rank_plan_impl(d_counts, sh, d_n, eps, k, &plan->rank, d_ws, ws_bytes,
                         static_cast<cudaStream_t>(stream));
+}
+
+int sad_batch_plan_bound(const int32_t *h_n, const int32_t *h_p, int32_t n_sets,
+                         int64_t total_len, int32_t k, int32_t alphabet, sad_batch_plan *plan) {
+  const int64_t eps = eps_of(k, alphabet);
+  if (eps < 0) return SAD_ERR_UNSUPPORTED;
+  if (!plan || !h_p || total_len < 0 || plan->rank.depth < 1 || !tile_valid(&plan->rank))
+    return SAD_ERR_INVALID_ARGUMENT;
+  RankShape sh;
+  int rc = batch_plan_shape(h_n, h_p, n_sets, plan, &sh);
+  if (rc) return rc;
+  return plan_bound_caps(sh, total_len, k, eps, &plan->rank);
 }
 
 int sad_batch_rank(const int32_t *d_counts, const int32_t *d_lengths, const int32_t *d_word_max,
@@ -522,7 +562,7 @@ int sad_batch_rank(const int32_t *d_counts, const int32_t *d_lengths, const int3
   const int64_t eps = eps_of(k, alphabet);
   if (eps < 0) return SAD_ERR_UNSUPPORTED;
   if (!plan || plan->n_sets < 1 || !d_n || !d_counts || !d_lengths || !d_key_hi || !d_key_lo ||
-      !d_ws || !aligned(d_ws, 256) || tile_of(&plan->rank) != kRowBlock)
+      !d_ws || !aligned(d_ws, 256))
     return SAD_ERR_INVALID_ARGUMENT;
   const RankShape sh{plan->n_sets, plan->n_total, plan->rows_total, plan->tiles_total,
                      plan->tileof_total};

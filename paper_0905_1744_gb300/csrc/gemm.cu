@@ -1411,8 +1411,12 @@ int rank_gemm_pair_launch(const RankPtrs &P, cudaStream_t st) {
   attr[0].val.clusterDim.x = 2;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
-  const int64_t clusters = tiles < ncl ? tiles : ncl;
-  cfg.gridDim = dim3((unsigned)(2 * clusters), 1, 1);
+  // Always every co-resident cluster, whatever the number of tiles (clusters without
+  // a tile exit after setting up): the grid of this launch then never changes between
+  // batches, so a CUDA graph that recorded it can be updated in place for another
+  // batch (an in-place update did not grow the grid of this cluster launch beyond
+  // the instantiated one, which left the extra tiles uncomputed).
+  cfg.gridDim = dim3((unsigned)(2 * ncl), 1, 1);
   cfg.blockDim = dim3(pairk::kThreads, 1, 1);
   cfg.dynamicSmemBytes = pairk::kSmemBytes;
   cfg.stream = st;

@@ -142,18 +142,15 @@ __device__ __forceinline__ V block_scan_incl(V x, V *s_warp, V *total) {
   return r;
 }
 
-__device__ __forceinline__ int64_t dev_n_pad(int64_t n) {
-  return ((n > 0 ? n : 1) + kNPad - 1) / kNPad * kNPad;
+// Stored rows of a set of n sequences: padded to the GEMM tile rows B.
+__device__ __forceinline__ int64_t dev_n_pad(int64_t n, int64_t B) {
+  return ((n > 0 ? n : 1) + B - 1) / B * B;
 }
 
-__device__ __forceinline__ int64_t dev_tiles_of_set(int64_t n) {
-  const int64_t R = (n + kRowBlock - 1) / kRowBlock, C = (n + kColBlock - 1) / kColBlock;
-  int64_t total = 0;  // sum over I < R of max(0, C - floor(I / kColRatio))
-  for (int64_t I = 0; I < R; ++I) {
-    const int64_t j0 = I / kColRatio;
-    if (j0 < C) total += C - j0;
-  }
-  return total;
+// Upper-triangle tiles of a set of n rows in square tiles of B rows.
+__device__ __forceinline__ int64_t dev_tiles_of_set(int64_t n, int64_t B) {
+  const int64_t R = (n + B - 1) / B;
+  return R * (R + 1) / 2;
 }
 
 __device__ __forceinline__ int32_t set_of_seq(const RankPtrs &P, int64_t x) {
@@ -186,8 +183,8 @@ __global__ void __launch_bounds__(1024) rank_setup_kernel(const int32_t *d_n, in
   for (int base = 0; base < S; base += blockDim.x) {
     const int s = base + tid;
     const int64_t n = s < S ? (d_n ? d_n[s] : n1) : 0;
-    const int64_t np = s < S ? dev_n_pad(n) : 0;
-    const int64_t v[4] = {n, np, s < S ? dev_tiles_of_set(n) : 0,
+    const int64_t np = s < S ? dev_n_pad(n, P.tile) : 0;
+    const int64_t v[4] = {n, np, s < S ? dev_tiles_of_set(n, P.tile) : 0,
                           (np / kRowBlock) * (np / kColBlock)};
     int64_t ex[4];
 #pragma unroll
@@ -218,7 +215,7 @@ __global__ void rank_setmaps_kernel(RankPtrs P) {
   for (int32_t s = blockIdx.x; s < (int32_t)P.n_sets; s += gridDim.x) {
     const RankSet e = P.sets[s];
     for (int64_t i = threadIdx.x; i < e.n; i += blockDim.x) P.seq_set[e.seq_begin + i] = s;
-    const int64_t np = dev_n_pad(e.n);
+    const int64_t np = dev_n_pad(e.n, P.tile);
     for (int64_t i = threadIdx.x; i < np; i += blockDim.x) P.row_set[e.row_base + i] = s;
   }
 }
@@ -537,7 +534,7 @@ __global__ void __launch_bounds__(kSortThreads) lensort_sets_kernel(
     }
     __syncthreads();
     cta_sort(buf + e.seq_begin, scratch + e.seq_begin, e.n, sm);
-    const int64_t np = dev_n_pad(e.n);
+    const int64_t np = dev_n_pad(e.n, P.tile);
     for (int64_t i = threadIdx.x; i < np; i += blockDim.x) {
       const int64_t row = e.row_base + i;
       if (i < e.n) {

@@ -107,11 +107,11 @@ __host__ __device__ constexpr int32_t t_bits_of(int32_t depth) {
 
 // One set of a (possibly batched) rank call, built on the device by rank_setup.
 // Sets are consecutive in the input order; each set's stored rows are a
-// contiguous, 128-aligned range of the global plane matrix, so every GEMM tile
-// stays inside one set (the batch is block-diagonal).
+// contiguous range of the global plane matrix aligned to the GEMM tile (128 or
+// 256 rows), so every GEMM tile stays inside one set (the batch is block-diagonal).
 struct RankSet {
   int64_t seq_begin;     // first input sequence of the set
-  int64_t row_base;      // first stored row (multiple of 128)
+  int64_t row_base;      // first stored row (multiple of the tile rows)
   int64_t tile_base;     // first entry of the set's tiles in the tile list
   int64_t tileof_base;   // first entry of the set's (I, J) -> tile map
   int32_t n, pad;
@@ -132,24 +132,20 @@ inline int64_t tiles_of_set(int64_t n, int64_t B = kRowBlock) {
   return R * (R + 1) / 2;
 }
 
-inline void shape_add_set(RankShape &sh, int64_t n) {
-  const int64_t np = n_pad_of(n);
+// One more set of n sequences; with tile = 256 (CTA pairs) its rows are padded to 256
+// and its tiles are the 256 x 256 tiles of its upper triangle.
+inline void shape_add_set(RankShape &sh, int64_t n, int64_t tile = kRowBlock) {
+  const int64_t np = n_pad_of(n, tile);
   sh.n_sets += 1;
   sh.n_total += n;
   sh.rows_total += np;
-  sh.tiles_total += tiles_of_set(n);
+  sh.tiles_total += tiles_of_set(n, tile);
   sh.tileof_total += (np / kRowBlock) * (np / kColBlock);
 }
 
-// One set; with tile = 256 (CTA pairs) its rows are padded to 256 and its tiles are
-// the 256 x 256 tiles of the upper triangle.
 inline RankShape shape_single(int64_t n, int64_t tile = kRowBlock) {
   RankShape sh{0, 0, 0, 0, 0};
-  shape_add_set(sh, n);
-  if (tile == 2 * kRowBlock) {
-    sh.rows_total = n_pad_of(n, tile);
-    sh.tiles_total = tiles_of_set(n, tile);
-  }
+  shape_add_set(sh, n, tile);
   return sh;
 }
 

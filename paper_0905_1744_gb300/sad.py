@@ -6,6 +6,7 @@ missing or fails to load, the call raises -- there is no fallback.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import threading
@@ -133,6 +134,21 @@ def _load():
         lib.sad_profile_read.restype = ctypes.c_int
         lib.sad_debug_wait_budget_ns.argtypes = [ctypes.c_uint64]
         lib.sad_debug_wait_budget_ns.restype = ctypes.c_int
+        lib.sad_batch_plan_bound.argtypes = [P, P, i32, i64, i32, i32, ctypes.POINTER(BatchPlan)]
+        lib.sad_batch_plan_bound.restype = ctypes.c_int
+        lib.sad_seq_lengths.argtypes = [P, i32, P, P, P]
+        lib.sad_seq_lengths.restype = ctypes.c_int
+        lib.sad_graph_begin.argtypes = [P]
+        lib.sad_graph_begin.restype = ctypes.c_int
+        lib.sad_graph_end.argtypes = [P, ctypes.POINTER(P)]
+        lib.sad_graph_end.restype = ctypes.c_int
+        lib.sad_graph_launch.argtypes = [P, P]
+        lib.sad_graph_launch.restype = ctypes.c_int
+        lib.sad_graph_stats.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                        ctypes.POINTER(i32)]
+        lib.sad_graph_stats.restype = ctypes.c_int
+        lib.sad_graph_destroy.argtypes = [P]
+        lib.sad_graph_destroy.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -253,6 +269,65 @@ def kmer_count(codes: torch.Tensor, offsets: torch.Tensor, k: int = 3, alphabet:
     return out
 
 
+def seq_lengths(offsets: torch.Tensor, out: torch.Tensor | None = None, ws: Workspace | None = None,
+                stream=None) -> torch.Tensor:
+    """int32 lengths off[i + 1] - off[i] of an int64 offsets array, on the device
+    (sad_seq_lengths; no synchronisation). ``ws``: a workspace whose status
+    records a negative or oversized length."""
+    _need(offsets, 8, "offsets", "sad_seq_lengths")
+    n = offsets.numel() - 1
+    if out is None:
+        out = torch.empty(max(n, 0), dtype=torch.int32, device=offsets.device)
+    _need(out, 4, "lengths", "sad_seq_lengths")
+    if out.numel() < n:
+        raise ValueError(f"sad_seq_lengths: out must hold {n} entries")
+    _check(_load().sad_seq_lengths(_ptr(offsets), n, _ptr(out), _ptr(ws.buf) if ws else None,
+                                   _stream(stream)), "sad_seq_lengths")
+    return out
+
+
+class Graph:
+    """A reusable CUDA graph of library calls (sad_graph_*). ``capture(fn, stream)``
+    records fn(stream) (which must only make asynchronous library calls on that
+    stream: no torch operation, no synchronisation); the first capture is
+    instantiated and every later one updates the instantiated graph in place when
+    its launch sequence has the same topology. ``launch(stream)`` runs it."""
+
+    def __init__(self):
+        self.h = ctypes.c_void_p()
+
+    def capture(self, fn, stream):
+        lib, st = _load(), _stream(stream)
+        _check(lib.sad_graph_begin(st), "sad_graph_begin")
+        try:
+            fn(stream)
+        except BaseException:
+            # end the broken capture (its graph is dropped; the handle keeps its last one)
+            lib.sad_graph_end(st, ctypes.byref(self.h))
+            raise
+        _check(lib.sad_graph_end(st, ctypes.byref(self.h)), "sad_graph_end")
+
+    def launch(self, stream=None):
+        _check(_load().sad_graph_launch(self.h, _stream(stream)), "sad_graph_launch")
+
+    def stats(self) -> dict:
+        u, i, k = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        _check(_load().sad_graph_stats(self.h, ctypes.byref(u), ctypes.byref(i), ctypes.byref(k)),
+               "sad_graph_stats")
+        return dict(updates=u.value, instantiations=i.value, kernels=k.value)
+
+    def close(self):
+        if self.h:
+            _load().sad_graph_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def kmer_rank_plan(counts: torch.Tensor, k: int = 3, alphabet: int = 20, depth: int = 0,
                    ws: Workspace | None = None, stream=None, budget: int = 0,
                    tile: int = 0) -> RankPlan:
@@ -291,11 +366,12 @@ def kmer_rank_plan_bound(n: int, total_len: int, k: int = 3, alphabet: int = 20,
 def kmer_rank(counts: torch.Tensor, lengths: torch.Tensor, k: int = 3, alphabet: int = 20,
               ws: Workspace | None = None, with_rank: bool = True, stream=None,
               out=None, check: bool = True, plan: RankPlan | None = None, depth: int = 0,
-              word_max: torch.Tensor | None = None):
+              word_max: torch.Tensor | None = None, tile: int = 0, budget: int = 0):
     """(key_hi uint64, key_lo uint64, rank float64 | None), Eq. 1 and Eq. 3.
 
     ``plan``: a RankPlan from kmer_rank_plan (reused as is); if None, one is made
-    here for ``depth`` (0 = all planes), which synchronises the stream.
+    here for ``depth`` (0 = all planes), ``tile`` and ``budget``, which
+    synchronises the stream.
     """
     _need_counts(counts, k, alphabet, "kmer_rank", word_max)
     n = counts.shape[0]
@@ -308,7 +384,7 @@ def kmer_rank(counts: torch.Tensor, lengths: torch.Tensor, k: int = 3, alphabet:
             raise ValueError(f"kmer_rank: outputs must hold {n} entries")
     ws = ws or Workspace(dev)
     if plan is None:
-        plan = kmer_rank_plan(counts, k, alphabet, depth, ws, stream)
+        plan = kmer_rank_plan(counts, k, alphabet, depth, ws, stream, budget=budget, tile=tile)
     ws.ensure(plan.ws_bytes)
     if out is None:
         hi = torch.empty(n, dtype=torch.uint64, device=dev)
@@ -358,15 +434,17 @@ def partition(key_hi: torch.Tensor, key_lo: torch.Tensor, p: int, ws: Workspace 
 
 def partition_set(codes: torch.Tensor, offsets: torch.Tensor, p: int, k: int = 3,
                   alphabet: int = 20, ws: Workspace | None = None, stream=None,
-                  depth: int = 0):
-    """count -> rank -> partition of one sequence set on the device. With
-    ``depth`` >= 1 the rank runs on the host-side capacity bounds
-    (kmer_rank_plan_bound), so the three calls queue without a synchronisation;
-    the workspace status (the first error any of them recorded) is read once at
-    the end."""
+                  depth: int = 0, tile: int = 0, budget: int = 0):
+    """count -> lengths -> rank -> partition of one sequence set on the device,
+    with a rank plan of ``depth``, ``tile`` and ``budget`` (see kmer_rank_plan).
+    With ``depth`` >= 1 the rank runs on the host-side capacity bounds
+    (kmer_rank_plan_bound), so the calls queue without a synchronisation; the
+    workspace status (the first error any of them recorded) is read once at the
+    end."""
     ws = ws or Workspace(codes.device)
     n = offsets.numel() - 1
-    plan = kmer_rank_plan_bound(n, codes.numel(), k, alphabet, depth) if depth >= 1 else None
+    plan = (kmer_rank_plan_bound(n, codes.numel(), k, alphabet, depth, budget=budget, tile=tile)
+            if depth >= 1 else None)
     if plan is not None:
         # one size for the three calls: a later growth would drop an earlier status
         ws.ensure(max(plan.ws_bytes, workspace_bytes(OP_COUNT, n, k, alphabet),
@@ -374,9 +452,10 @@ def partition_set(codes: torch.Tensor, offsets: torch.Tensor, p: int, k: int = 3
     word_max = torch.empty(alphabet ** k, dtype=torch.int32, device=codes.device)
     counts = kmer_count(codes, offsets, k, alphabet, ws=ws, stream=stream, word_max=word_max,
                         check=plan is None)
-    lengths = (offsets[1:] - offsets[:-1]).to(torch.int32)
+    lengths = seq_lengths(offsets, ws=ws, stream=stream)
     hi, lo, rank = kmer_rank(counts, lengths, k, alphabet, ws=ws, stream=stream, depth=depth,
-                             word_max=word_max, plan=plan, check=plan is None)
+                             word_max=word_max, plan=plan, check=plan is None, tile=tile,
+                             budget=budget)
     offs, mem, piv = partition(hi, lo, p, ws=ws, stream=stream, check=False)
     ws.check("partition_set", stream)
     return dict(counts=counts, key_hi=hi, key_lo=lo, rank=rank, bucket_offsets=offs,
@@ -713,7 +792,7 @@ def global_partition_set(codes: torch.Tensor, offsets: torch.Tensor, p: int, ks:
     ws = Workspace(codes.device)
     word_max = torch.empty(alphabet ** k, dtype=torch.int32, device=codes.device)
     counts = kmer_count(codes, offsets, k, alphabet, ws=ws, stream=stream, word_max=word_max)
-    lengths = (offsets[1:] - offsets[:-1]).to(torch.int32)
+    lengths = seq_lengths(offsets, ws=ws, stream=stream)
     hi, lo, rank, samples = global_rank(counts, lengths, p, ks, k, alphabet, word_max,
                                         stream=stream)
     offs, mem, piv = partition(hi, lo, p, ws=ws, stream=stream)
@@ -726,13 +805,22 @@ class Batch:
 
     ``sets``: objects with ``codes`` (uint8), ``offsets`` (int64, N+1) and ``p``.
     All sets share one count launch, one block-diagonal rank (one persistent
-    GEMM launch over every set's tiles) and one batched partition. ``plan()``
-    sizes everything (synchronous); ``run()`` then launches without any host
-    synchronisation, so ``capture()`` can record it in a CUDA graph and
-    ``replay()`` re-runs the whole batch with one graph launch.
+    GEMM launch over every set's tiles) and one batched partition.
+
+    The host arrays are staged in pinned memory and copied with ``upload()``
+    (asynchronous, on the given stream). ``plan(depth, tile, budget)`` sizes the
+    work: with ``bound=True`` (depth >= 1) from host-side bounds alone
+    (sad_batch_plan_bound: no device work, no synchronisation), otherwise from the
+    counts (sad_batch_plan_make: counts the batch and synchronises). ``run()``
+    then launches count -> lengths -> rank -> partition without any host
+    synchronisation, so ``capture(graph)`` records it into a library Graph:
+    the first batch instantiates it and each later batch captured into the same
+    Graph only updates its parameters. ``workspaces`` (count, rank, partition)
+    may be shared by batches that never run at the same time.
     """
 
-    def __init__(self, sets, device=None, k: int = 3, alphabet: int = 20):
+    def __init__(self, sets, device=None, k: int = 3, alphabet: int = 20, workspaces=None,
+                 stream=None, pin: bool = True):
         import numpy as np
         self.device = torch.device(device or "cuda")
         self.k, self.alphabet = k, alphabet
@@ -746,13 +834,24 @@ class Batch:
         self.boff_begin = np.concatenate([[0], np.cumsum(self.p + 1)]).astype(np.int64)
         self.piv_begin = np.concatenate([[0], np.cumsum(self.p - 1)]).astype(np.int64)
         self.h_codes, self.h_offsets = codes, offsets
+        self.total_len = int(offsets[-1])
         dev = self.device
-        self.codes = torch.from_numpy(codes).to(dev)
-        self.offsets = torch.from_numpy(offsets).to(dev)
-        self.lengths = torch.from_numpy(np.concatenate(lens).astype(np.int32)).to(dev)
-        self.d_n = torch.from_numpy(self.n).to(dev)
-        self.d_p = torch.from_numpy(self.p).to(dev)
+        on_gpu = dev.type == "cuda"
+        pin = pin and on_gpu
+
+        def host(a):
+            t = torch.from_numpy(np.ascontiguousarray(a))
+            return t.pin_memory() if pin else t
+        self.h_in = dict(codes=host(codes), offsets=host(offsets), n=host(self.n),
+                         p=host(self.p))
         nt = int(self.n.sum())
+        self.codes = torch.empty(max(codes.shape[0], 1), dtype=torch.uint8, device=dev)
+        self.offsets = torch.empty(nt + 1, dtype=torch.int64, device=dev)
+        self.d_n = torch.empty(self.n_sets, dtype=torch.int32, device=dev)
+        self.d_p = torch.empty(self.n_sets, dtype=torch.int32, device=dev)
+        # lengths: derived on the device by the library in run(); host-built off the GPU
+        self.lengths = (torch.empty(nt, dtype=torch.int32, device=dev) if on_gpu else
+                        torch.from_numpy(np.concatenate(lens).astype(np.int32)))
         self.counts = torch.empty((nt, alphabet ** k), dtype=torch.int32, device=dev)
         self.word_max = torch.empty(alphabet ** k, dtype=torch.int32, device=dev)
         self.key_hi = torch.empty(nt, dtype=torch.uint64, device=dev)
@@ -762,54 +861,86 @@ class Batch:
         self.members = torch.empty(nt, dtype=torch.int32, device=dev)
         self.pivot_idx = torch.empty(max(int(self.piv_begin[-1]), 1), dtype=torch.int32,
                                      device=dev)
-        self.ws_count = Workspace(dev, 256)
-        self.ws_rank = Workspace(dev)
-        self.ws_part = Workspace(dev)
+        if workspaces is None:
+            workspaces = (Workspace(dev, 256), Workspace(dev), Workspace(dev))
+        self.ws_count, self.ws_rank, self.ws_part = workspaces
         self.plan_ = None
         self.graph = None
+        self.upload(stream)
 
     @property
     def n_sets(self) -> int:
         return int(self.n.shape[0])
 
+    @property
+    def h2d_bytes(self) -> int:
+        return sum(t.numel() * t.element_size() for t in self.h_in.values())
+
+    def upload(self, stream=None):
+        """Host -> device copies of the batch's inputs (asynchronous from pinned memory)."""
+        nb = self.device.type == "cuda"
+        ctx = torch.cuda.stream(stream) if (nb and stream is not None) else contextlib.nullcontext()
+        with ctx:
+            self.codes[:self.h_in["codes"].numel()].copy_(self.h_in["codes"], non_blocking=nb)
+            self.offsets.copy_(self.h_in["offsets"], non_blocking=nb)
+            self.d_n.copy_(self.h_in["n"], non_blocking=nb)
+            self.d_p.copy_(self.h_in["p"], non_blocking=nb)
+
     def count(self, stream=None):
         kmer_count(self.codes, self.offsets, self.k, self.alphabet, ws=self.ws_count,
                    out=self.counts, stream=stream, check=False, word_max=self.word_max)
 
-    def plan(self, depth: int = 0, stream=None) -> BatchPlan:
-        """Counts the batch and sizes the rank and partition workspaces (synchronous)."""
+    def plan(self, depth: int = 1, stream=None, tile: int = 0, budget: int = 0,
+             bound: bool | None = None) -> BatchPlan:
+        """Sizes the rank and partition workspaces. ``bound`` (default: depth >= 1):
+        from host-side bounds, asynchronous; otherwise counts the batch and reads
+        the exact sizes back (synchronous)."""
         import numpy as np
-        self.count(stream)
-        self.ws_count.check("kmer_count (batch)", stream)
+        if bound is None:
+            bound = depth >= 1
         plan = BatchPlan()
-        plan.rank.depth = int(depth)
+        plan.rank.depth, plan.rank.budget, plan.rank.tile = int(depth), int(budget), int(tile)
         h_n = np.ascontiguousarray(self.n)
         h_p = np.ascontiguousarray(self.p)
-        args = (_ptr(self.counts), h_n.ctypes.data_as(ctypes.c_void_p),
-                h_p.ctypes.data_as(ctypes.c_void_p), _ptr(self.d_n), self.n_sets, self.k,
-                self.alphabet, ctypes.byref(plan))
-        self.ws_rank.ensure(256)
-        rc = _load().sad_batch_plan_make(*args, _ptr(self.ws_rank.buf), self.ws_rank.nbytes,
-                                         _stream(stream))
-        if rc == ERR_WORKSPACE:
-            self.ws_rank.ensure(plan.rank.ws_bytes)
-            plan.rank.depth = int(depth)
+        n_ptr = h_n.ctypes.data_as(ctypes.c_void_p)
+        p_ptr = h_p.ctypes.data_as(ctypes.c_void_p)
+        if bound:
+            _check(_load().sad_batch_plan_bound(n_ptr, p_ptr, self.n_sets, self.total_len, self.k,
+                                                self.alphabet, ctypes.byref(plan)),
+                   "sad_batch_plan_bound")
+        else:
+            self.count(stream)
+            self.ws_count.check("kmer_count (batch)", stream)
+            args = (_ptr(self.counts), n_ptr, p_ptr, _ptr(self.d_n), self.n_sets, self.k,
+                    self.alphabet, ctypes.byref(plan))
+            self.ws_rank.ensure(256)
             rc = _load().sad_batch_plan_make(*args, _ptr(self.ws_rank.buf), self.ws_rank.nbytes,
                                              _stream(stream))
-        _check(rc, "sad_batch_plan_make")
+            if rc == ERR_WORKSPACE:
+                self.ws_rank.ensure(plan.rank.ws_bytes)
+                plan.rank.depth, plan.rank.budget = int(depth), int(budget)
+                plan.rank.tile = int(tile)
+                rc = _load().sad_batch_plan_make(*args, _ptr(self.ws_rank.buf),
+                                                 self.ws_rank.nbytes, _stream(stream))
+            _check(rc, "sad_batch_plan_make")
+        # every workspace at its size before run() (which a capture records: no
+        # allocation may happen inside it)
+        self.ws_count.ensure(workspace_bytes(OP_COUNT, int(self.n.sum()), self.k, self.alphabet))
         self.ws_rank.ensure(plan.rank.ws_bytes)
         self.ws_part.ensure(plan.part_ws_bytes)
         self.plan_ = plan
-        self.graph = None
         return plan
 
     def run(self, stream=None, count: bool = True):
-        """count -> rank -> partition of every set; no host synchronisation."""
+        """count -> lengths -> rank -> partition of every set; no host synchronisation."""
         if self.plan_ is None:
             raise RuntimeError("Batch.plan() first")
         lib, st = _load(), _stream(stream)
         if count:
             self.count(stream)
+        _check(lib.sad_seq_lengths(_ptr(self.offsets), int(self.offsets.numel() - 1),
+                                   _ptr(self.lengths), _ptr(self.ws_count.buf), st),
+               "sad_seq_lengths")
         _check(lib.sad_batch_rank(_ptr(self.counts), _ptr(self.lengths), _ptr(self.word_max),
                                   _ptr(self.d_n),
                                   self.k, self.alphabet, ctypes.byref(self.plan_),
@@ -822,23 +953,21 @@ class Batch:
                                        _ptr(self.pivot_idx), _ptr(self.ws_part.buf),
                                        self.ws_part.nbytes, st), "sad_batch_partition")
 
-    def capture(self):
-        """Records run() in a CUDA graph (after one eager run)."""
-        self.run()
-        torch.cuda.synchronize(self.device)
-        self.check()
-        g = torch.cuda.CUDAGraph()
-        s = torch.cuda.Stream(self.device)
-        s.wait_stream(torch.cuda.current_stream(self.device))
-        with torch.cuda.stream(s):
-            with torch.cuda.graph(g, stream=s):
-                self.run(stream=s)
-        torch.cuda.current_stream(self.device).wait_stream(s)
+    def capture(self, graph: Graph | None = None, stream=None) -> Graph:
+        """Records run() into ``graph`` (a new Graph if None): instantiated on its
+        first capture, updated in place on later ones. Capture needs a stream other
+        than the legacy default one: a side stream is used when none is given."""
+        g = graph or Graph()
+        s = stream or torch.cuda.Stream(self.device)
+        if stream is None:
+            s.wait_stream(torch.cuda.current_stream(self.device))
+        g.capture(lambda st: self.run(stream=st), s)
         self.graph = g
         return g
 
-    def replay(self):
-        self.graph.replay()
+    def replay(self, stream=None):
+        """Runs the batch's captured graph on ``stream`` (default: the current stream)."""
+        self.graph.launch(stream if stream is not None else torch.cuda.current_stream(self.device))
 
     def check(self, stream=None):
         self.ws_count.check("kmer_count (batch)", stream)

@@ -1,14 +1,19 @@
 """Serving: continuous batching of sequence-set requests on one GPU.
 
 Requests (one sequence set each, host memory) arrive over time. The server keeps
-up to ``slots`` batches in flight, each on its own CUDA stream. Whenever a slot
-is free, every request that has arrived and fits the HBM budget is admitted and
-launched as one batch (count -> block-diagonal rank -> batched partition, see
-``sad.Batch``); its device state (codes, counts, planes, keys, buckets) lives
-until the batch completes and its bucket lists have been copied back, and then
-its memory returns to the budget. Requests that arrive while batches run wait
-for the next free slot, and batches in flight on different streams overlap on
-the device. Latency = time the results are on the host - arrival time.
+up to ``slots`` batches in flight, each on its own CUDA stream with its own
+reusable CUDA graph. Whenever a slot is free, every request that has arrived and
+fits the HBM budget is admitted and launched as one batch (count -> lengths ->
+block-diagonal rank -> batched partition, see ``sad.Batch``) without any host
+synchronisation: the inputs go up from pinned memory, the plan comes from
+host-side bounds (``sad_batch_plan_bound``), the launches are captured into the
+slot's graph (which is updated in place, not re-instantiated, from one batch to
+the next) and the graph is launched; the bucket lists come back into pinned
+memory on the same stream. A batch's device state (codes, counts, planes, keys,
+buckets) lives until its results are on the host, and then its memory returns to
+the budget. Requests that arrive while batches run wait for the next free slot,
+and batches in flight on different streams overlap on the device. Latency = time
+the results are on the host - arrival time.
 
 The baseline (``serve_plain``) takes the same requests one at a time in arrival
 order and runs the plain per-set calls for each.
@@ -24,6 +29,7 @@ import torch
 from . import sad
 
 GB = 1 << 30
+DEFAULT_SHAPE = (256, 2, 0)     # (tile, depth >= 1, budget) when none is given
 
 
 @dataclasses.dataclass
@@ -35,31 +41,32 @@ class Request:
     result: dict | None = None
 
 
-def request_bytes(s, depth: int, k: int = 3, alphabet: int = 20) -> int:
-    """HBM a request holds while it is in flight, estimated for admission: codes,
-    offsets, counts, the rank workspace (4-bit planes of min(D, 4) full sections of
-    the word columns, which covers protein sets, where few words repeat more than
-    once in a sequence; padded rows; every 128 x 128 u16 residual block of the
-    upper triangle), keys, partition buffers, 64 MB of slack."""
+def request_bytes(s, depth: int, k: int = 3, alphabet: int = 20, tile: int = 256,
+                  budget: int = 0) -> int:
+    """HBM a request holds while it is in flight, for admission: codes, offsets,
+    lengths, counts, the rank workspace of its plan from host-side bounds
+    (kmer_rank_plan_bound: planes of ``depth`` sections, remainder and heavy lists
+    sized by its k-mer windows; a batch's bound plan is at most the sum of its
+    sets'), keys, ranks, partition buffers, and 64 MB of slack."""
     n = s.offsets.shape[0] - 1
+    total_len = int(s.offsets[-1] - s.offsets[0])
     eps = alphabet ** k
-    rows = (n + 127) // 128 * 128
-    d = depth if depth > 0 else 4
-    planes = rows * (eps * min(d, 4) + 256) // 2
-    blocks = (rows // 128) * (rows // 128 + 1) // 2
-    residual = blocks * 2 * 128 * 128 if depth > 0 else 0
-    return int(s.codes.nbytes + 8 * (n + 1) + 4 * n * eps + planes + residual + 96 * n
+    plan = sad.kmer_rank_plan_bound(n, total_len, k, alphabet, depth=max(depth, 1),
+                                    budget=budget, tile=tile)
+    part = sad.workspace_bytes(sad.OP_PARTITION, n, p=max(int(getattr(s, "p", 1)), 1))
+    return int(total_len + 12 * (n + 1) + 4 * n * eps + plan.ws_bytes + part + 40 * n
                + (64 << 20))
 
 
-def select_batch(queue, used: int, budget_bytes: int, max_batch: int, depth: int):
+def select_batch(queue, used: int, budget_bytes: int, max_batch: int, depth: int,
+                 tile: int = 256, budget: int = 0):
     """The next batch to admit: the longest prefix of the arrival-ordered queue
     (at most max_batch requests) whose bytes fit beside the ``used`` bytes of the
     batches in flight. Returns (requests, bytes); empty when the head of the queue
     does not fit yet (it is never overtaken, so admission stays in arrival order)."""
     take, nbytes = [], 0
     for r in queue:
-        rb = request_bytes(r.seqset, depth)
+        rb = request_bytes(r.seqset, depth, tile=tile, budget=budget)
         if len(take) >= max_batch or used + nbytes + rb > budget_bytes:
             break
         take.append(r)
@@ -67,18 +74,33 @@ def select_batch(queue, used: int, budget_bytes: int, max_batch: int, depth: int
     return take, nbytes
 
 
-class _InFlight:
-    def __init__(self, reqs, batch, stream, event, host, nbytes):
-        self.reqs, self.batch, self.stream, self.event = reqs, batch, stream, event
-        self.host, self.nbytes = host, nbytes
+class _Slot:
+    """One in-flight position: a stream, a reusable graph and (while busy) a batch."""
+
+    def __init__(self, device, ws_pool: bool):
+        self.stream = torch.cuda.Stream(device)
+        self.graph = sad.Graph()
+        self.workspaces = ((sad.Workspace(device, 256), sad.Workspace(device),
+                            sad.Workspace(device)) if ws_pool else None)
+        self.reqs = self.batch = self.host = self.event = None
+        self.ev0 = self.ev1 = None
+        self.nbytes = 0
 
 
-def _launch(reqs, depth, device, stream):
-    """Admit a batch: H2D, plan (synchronises this stream only), run, D2H."""
-    with torch.cuda.stream(stream):
-        b = sad.Batch([r.seqset for r in reqs], device=device)
-        b.plan(depth=depth, stream=stream)
-        b.run(stream=stream, count=False)
+def _launch(slot: _Slot, reqs, shape, device):
+    """Admit a batch on a free slot without synchronising the host: pinned H2D,
+    plan from bounds, capture into the slot's graph (an update after the first
+    batch), launch, D2H of the bucket lists and keys into pinned memory."""
+    tile, depth, budget = shape
+    st = slot.stream
+    with torch.cuda.stream(st):
+        slot.ev0 = torch.cuda.Event(enable_timing=True)
+        slot.ev0.record(st)
+        b = sad.Batch([r.seqset for r in reqs], device=device, workspaces=slot.workspaces,
+                      stream=st)
+        b.plan(depth=depth, tile=tile, budget=budget, stream=st, bound=True)
+        b.capture(slot.graph, stream=st)
+        slot.graph.launch(st)
         host = dict(bucket_offsets=torch.empty(b.bucket_offsets.shape, dtype=torch.int32,
                                                pin_memory=True),
                     members=torch.empty(b.members.shape, dtype=torch.int32, pin_memory=True),
@@ -86,73 +108,115 @@ def _launch(reqs, depth, device, stream):
                     key_lo=torch.empty(b.key_lo.shape, dtype=torch.uint64, pin_memory=True))
         for key, h in host.items():
             h.copy_(getattr(b, key), non_blocking=True)
-        ev = torch.cuda.Event()
-        ev.record(stream)
-    return b, host, ev
+        slot.ev1 = torch.cuda.Event(enable_timing=True)
+        slot.ev1.record(st)
+    slot.reqs, slot.batch, slot.host, slot.event = reqs, b, host, slot.ev1
 
 
-def _finish(f: _InFlight, now: float):
-    f.batch.check(f.stream)
-    for i, r in enumerate(f.reqs):
-        a, e = int(f.batch.seq_begin[i]), int(f.batch.seq_begin[i + 1])
-        oa, ob = int(f.batch.boff_begin[i]), int(f.batch.boff_begin[i + 1])
-        r.result = dict(bucket_offsets=f.host["bucket_offsets"][oa:ob].numpy().copy(),
-                        members=f.host["members"][a:e].numpy().copy(),
-                        key_hi=f.host["key_hi"][a:e].numpy().copy(),
-                        key_lo=f.host["key_lo"][a:e].numpy().copy())
+def _finish(slot: _Slot, now: float):
+    b = slot.batch
+    b.check(slot.stream)
+    for i, r in enumerate(slot.reqs):
+        a, e = int(b.seq_begin[i]), int(b.seq_begin[i + 1])
+        oa, ob = int(b.boff_begin[i]), int(b.boff_begin[i + 1])
+        r.result = dict(bucket_offsets=slot.host["bucket_offsets"][oa:ob].numpy().copy(),
+                        members=slot.host["members"][a:e].numpy().copy(),
+                        key_hi=slot.host["key_hi"][a:e].numpy().copy(),
+                        key_lo=slot.host["key_lo"][a:e].numpy().copy())
         r.done = now
 
 
-def serve(requests, depth: int = 2, budget_bytes: int = 150 * GB, slots: int = 3,
-          max_batch: int = 64, device=None, t0: float | None = None):
+def max_overlap(intervals) -> int:
+    """Largest number of (start, end) intervals open at one time."""
+    ev = sorted([(a, 1) for a, _ in intervals] + [(b, -1) for _, b in intervals],
+                key=lambda x: (x[0], x[1]))
+    best = cur = 0
+    for _, d in ev:
+        cur += d
+        best = max(best, cur)
+    return best
+
+
+def serve(requests, shape=DEFAULT_SHAPE, budget_bytes: int = 150 * GB, slots: int = 3,
+          max_batch: int = 64, device=None, t0: float | None = None, stats: dict | None = None,
+          ws_pool: bool = False):
     """Continuous batching over ``requests`` (sorted by arrival). Returns them with
-    ``done`` and ``result`` filled in. Arrival times are honoured in real time."""
+    ``done`` and ``result`` filled in. Arrival times are honoured in real time.
+    ``shape``: (tile, depth >= 1, budget) of every batch's rank plan. ``stats``
+    (a dict) receives the batches, the most batches in flight on the host and on
+    the device at once (from each batch's start and end events on its stream),
+    the most HBM bytes admitted at once, and the slots' graph updates and
+    instantiations. ``ws_pool``: each slot keeps its workspaces across batches."""
+    tile, depth, budget = shape
     if slots < 1 or max_batch < 1:
         raise ValueError("serve: slots and max_batch must be at least 1")
+    if depth < 1:
+        raise ValueError("serve: the plan-free path needs depth >= 1")
     for r in requests:
-        if request_bytes(r.seqset, depth) > budget_bytes:
+        need = request_bytes(r.seqset, depth, tile=tile, budget=budget)
+        if need > budget_bytes:
             # it could never be admitted, and the loop below would wait for it forever
-            raise ValueError(f"serve: request {r.rid} needs "
-                             f"{request_bytes(r.seqset, depth)} bytes, above the "
+            raise ValueError(f"serve: request {r.rid} needs {need} bytes, above the "
                              f"{budget_bytes}-byte budget")
     device = torch.device(device or "cuda")
-    streams = [torch.cuda.Stream(device) for _ in range(slots)]
-    free_streams = list(streams)
+    all_slots = [_Slot(device, ws_pool) for _ in range(slots)]
+    free = list(all_slots)
+    busy: list[_Slot] = []
     pending = list(requests)
     queue: list[Request] = []
-    inflight: list[_InFlight] = []
-    used = 0
+    used = peak_used = peak_busy = 0
+    done_ev = []
+    base = torch.cuda.Event(enable_timing=True)
+    base.record(torch.cuda.current_stream(device))
+    n_batches = 0
     start = time.perf_counter() if t0 is None else t0
-    while pending or queue or inflight:
+    while pending or queue or busy:
         now = time.perf_counter() - start
         while pending and pending[0].arrival <= now:
             queue.append(pending.pop(0))
         # completions
-        for f in list(inflight):
-            if f.event.query():
-                _finish(f, time.perf_counter() - start)
-                inflight.remove(f)
-                free_streams.append(f.stream)
-                used -= f.nbytes
+        for sl in list(busy):
+            if sl.event.query():
+                _finish(sl, time.perf_counter() - start)
+                done_ev.append((sl.ev0, sl.ev1))
+                busy.remove(sl)
+                free.append(sl)
+                used -= sl.nbytes
+                sl.batch = sl.host = sl.reqs = None
         # admissions: everything queued that fits, one batch per free slot
-        while queue and free_streams:
-            take, nbytes = select_batch(queue, used, budget_bytes, max_batch, depth)
+        while queue and free:
+            take, nbytes = select_batch(queue, used, budget_bytes, max_batch, depth, tile,
+                                        budget)
             if not take:
                 break
             queue = queue[len(take):]
-            st = free_streams.pop(0)
-            b, host, ev = _launch(take, depth, device, st)
-            inflight.append(_InFlight(take, b, st, ev, host, nbytes))
+            sl = free.pop(0)
+            _launch(sl, take, shape, device)
+            sl.nbytes = nbytes
+            busy.append(sl)
+            n_batches += 1
             used += nbytes
-        if not (queue and free_streams):
+            peak_used = max(peak_used, used)
+            peak_busy = max(peak_busy, len(busy))
+        if not (queue and free):
             # nothing to launch right now: wait a little for an arrival or a completion
             nxt = pending[0].arrival - (time.perf_counter() - start) if pending else 0.0
             time.sleep(min(max(nxt, 0.0), 2e-4))
+    if stats is not None:
+        torch.cuda.synchronize(device)
+        iv = [(base.elapsed_time(a), base.elapsed_time(b)) for a, b in done_ev]
+        g = [sl.graph.stats() for sl in all_slots if sl.graph.h]
+        stats.update(batches=n_batches, max_inflight_host=peak_busy,
+                     max_inflight_device=max_overlap(iv), peak_admitted_bytes=peak_used,
+                     graph_updates=sum(x["updates"] for x in g),
+                     graph_instantiations=sum(x["instantiations"] for x in g))
     return requests
 
 
-def serve_plain(requests, depth: int = 2, device=None, t0: float | None = None):
-    """Baseline: one request at a time, arrival order, plain per-set calls."""
+def serve_plain(requests, shape=DEFAULT_SHAPE, device=None, t0: float | None = None):
+    """Baseline: one request at a time, arrival order, plain per-set calls with
+    the same plan shape (tile, depth, budget)."""
+    tile, depth, budget = shape
     device = torch.device(device or "cuda")
     ws = sad.Workspace(device)
     start = time.perf_counter() if t0 is None else t0
@@ -163,7 +227,8 @@ def serve_plain(requests, depth: int = 2, device=None, t0: float | None = None):
         s = r.seqset
         codes = torch.from_numpy(s.codes).to(device, non_blocking=True)
         offsets = torch.from_numpy(s.offsets).to(device, non_blocking=True)
-        res = sad.partition_set(codes, offsets, s.p, ws=ws, depth=depth)
+        res = sad.partition_set(codes, offsets, s.p, ws=ws, depth=depth, tile=tile,
+                                budget=budget)
         r.result = dict(bucket_offsets=res["bucket_offsets"].cpu().numpy(),
                         members=res["members"].cpu().numpy(),
                         key_hi=res["key_hi"].cpu().numpy(), key_lo=res["key_lo"].cpu().numpy())

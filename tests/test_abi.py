@@ -39,7 +39,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_host_only_queries(lib):
     lib.sad_abi_version.restype = ctypes.c_int
-    assert lib.sad_abi_version() == 6
+    assert lib.sad_abi_version() == 7
     lib.sad_status_string.restype = ctypes.c_char_p
     lib.sad_status_string.argtypes = [ctypes.c_int]
     assert lib.sad_status_string(0) == b"ok"

@@ -1,10 +1,11 @@
 """Parity at full size, through the calls and plans the benchmark times.
 
-bench.py runs kmer_count (with the per-word maxima) -> kmer_rank_plan at the
-autotuner's depth -> kmer_rank on that plan -> partition. These tests run the same
+bench.py runs kmer_count (with the per-word maxima) -> sad_seq_lengths ->
+kmer_rank_plan at the autotuner's shape (GEMM tile 128 or 256 rows, plane depth,
+remainder budget) -> kmer_rank on that plan -> partition. These tests run the same
 sequence on the paper-scale set (N = 20000, 50 families, p = 16) and the large set
-(N = 100000, 500 families, p = 64) at every depth the autotuner may choose, plus
-the public partition_set path:
+(N = 100000, 500 families, p = 64) at every tile and depth the autotuner may
+choose and at the other budgets it tries, plus the public partition_set path:
 
   N = 20000   every key and rank against the oracle's full rank (Eq. 1, Eq. 3; all
               N(N-1)/2 pairs on the host cores, computed once for the module), and
@@ -26,6 +27,9 @@ torch = pytest.importorskip("torch")
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 DEPTHS = (0, 1, 2, 3, 4, 6)     # the autotuner's candidates
+TILES = (128, 256)
+SHAPES = [(t, d, 0) for t in TILES for d in DEPTHS] + [(256, 2, 256), (256, 6, 1536),
+                                                       (128, 4, 1536)]
 
 
 @pytest.fixture(scope="module")
@@ -45,14 +49,14 @@ def host(t):
     return t.cpu().numpy()
 
 
-def bench_path(sad, s, depth):
-    """The benchmark's step at plane depth `depth` (its plan made once, as there)."""
+def bench_path(sad, s, depth, tile=128, budget=0):
+    """The benchmark's step at this plan shape (its plan made once, as there)."""
     codes, offsets = dev(s.codes), dev(s.offsets)
-    lengths = dev(s.lengths.astype(np.int32))
     ws = sad.Workspace(codes.device)
     word_max = torch.empty(8000, dtype=torch.int32, device="cuda")
     counts = sad.kmer_count(codes, offsets, ws=ws, word_max=word_max)
-    plan = sad.kmer_rank_plan(counts, depth=depth, ws=ws)
+    lengths = sad.seq_lengths(offsets, ws=ws)
+    plan = sad.kmer_rank_plan(counts, depth=depth, ws=ws, tile=tile, budget=budget)
     hi, lo, rank = sad.kmer_rank(counts, lengths, ws=ws, plan=plan, word_max=word_max)
     offs, mem, piv = sad.partition(hi, lo, s.p)
     torch.cuda.synchronize()
@@ -89,32 +93,34 @@ def test_c2_counts_in_full(sad, c2_oracle):
     np.testing.assert_array_equal(host(res["counts"]), counts)
 
 
-@pytest.mark.parametrize("depth", DEPTHS)
-def test_c2_bench_path_every_key_and_bucket(sad, c2_oracle, depth):
+@pytest.mark.parametrize("tile,depth,budget", SHAPES)
+def test_c2_bench_path_every_key_and_bucket(sad, c2_oracle, tile, depth, budget):
     s, _, ref = c2_oracle
-    res = bench_path(sad, s, depth)
+    res = bench_path(sad, s, depth, tile, budget)
     assert res["depth"] == depth
-    assert_c2(res, ref, f"depth {depth}")
+    assert_c2(res, ref, f"tile {tile} depth {depth} budget {budget}")
 
 
-@pytest.mark.parametrize("depth", (1, 2))
-def test_c2_partition_set_on_host_bounds(sad, c2_oracle, depth):
+@pytest.mark.parametrize("tile,depth", [(128, 1), (256, 2), (256, 6)])
+def test_c2_partition_set_on_host_bounds(sad, c2_oracle, tile, depth):
     """The public call the end-to-end figure times (capacity bounds, no sync)."""
     s, _, ref = c2_oracle
-    out = sad.partition_set(dev(s.codes), dev(s.offsets), s.p, depth=depth)
+    out = sad.partition_set(dev(s.codes), dev(s.offsets), s.p, depth=depth, tile=tile)
     res = {k: host(out[k]) for k in ("key_hi", "key_lo", "rank", "bucket_offsets", "members",
                                      "pivot_idx")}
-    assert_c2(res, ref, f"partition_set depth {depth}")
+    assert_c2(res, ref, f"partition_set tile {tile} depth {depth}")
 
 
-def test_c2_autotuned_depth(sad, c2_oracle):
+def test_c2_autotuned_shape(sad, c2_oracle):
     from paper_0905_1744_gb300 import autotune
     s, _, ref = c2_oracle
     counts = sad.kmer_count(dev(s.codes), dev(s.offsets))
-    depth, trials = autotune.choose_depth(counts, dev(s.lengths.astype(np.int32)),
+    shape, trials = autotune.choose_shape(counts, dev(s.lengths.astype(np.int32)),
                                           use_cache=False)
-    assert depth in trials
-    assert_c2(bench_path(sad, s, depth), ref, f"autotuned depth {depth}")
+    assert shape.key in trials and len(trials) >= 8
+    assert {autotune.Shape.parse(k).tile for k in trials} == {128, 256}
+    assert_c2(bench_path(sad, s, shape.depth, shape.tile, shape.budget), ref,
+              f"autotuned {shape.key}")
 
 
 @pytest.fixture(scope="module")
@@ -133,10 +139,10 @@ def c3_oracle(oracle_mod):
     return s, rows, sample_counts, dict(key_hi=hi, key_lo=lo, rank=rank)
 
 
-@pytest.mark.parametrize("depth", (0, 1, 2, 3))
-def test_c3_bench_path_sampled_keys_and_buckets(sad, oracle_mod, c3_oracle, depth):
+@pytest.mark.parametrize("tile,depth,budget", SHAPES)
+def test_c3_bench_path_sampled_keys_and_buckets(sad, oracle_mod, c3_oracle, tile, depth, budget):
     s, rows, sample_counts, ref = c3_oracle
-    res = bench_path(sad, s, depth)
+    res = bench_path(sad, s, depth, tile, budget)
     np.testing.assert_array_equal(host(res["counts"][dev(rows)]), sample_counts)
     for key in ("key_hi", "key_lo", "rank"):
         np.testing.assert_array_equal(res[key][rows], ref[key], err_msg=f"depth {depth}: {key}")
@@ -145,7 +151,7 @@ def test_c3_bench_path_sampled_keys_and_buckets(sad, oracle_mod, c3_oracle, dept
 
 def test_c3_partition_set_on_host_bounds(sad, oracle_mod, c3_oracle):
     s, rows, _, ref = c3_oracle
-    out = sad.partition_set(dev(s.codes), dev(s.offsets), s.p, depth=2)
+    out = sad.partition_set(dev(s.codes), dev(s.offsets), s.p, depth=6, tile=256)
     res = {k: host(out[k]) for k in ("key_hi", "key_lo", "rank", "bucket_offsets", "members",
                                      "pivot_idx")}
     for key in ("key_hi", "key_lo", "rank"):

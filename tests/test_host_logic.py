@@ -25,10 +25,14 @@ def test_request_bytes_grows_with_set_size_and_depth():
         assert serve.request_bytes(small, d) < serve.request_bytes(big, d)
     b = [serve.request_bytes(big, d) for d in (1, 2, 3, 4)]
     assert b == sorted(b) and len(set(b)) == 4
-    # depth 0 keeps every plane: sized as four sections, with no residual blocks
-    assert serve.request_bytes(big, 0) < serve.request_bytes(big, 4)
     # the counts alone (4 bytes x 8000 words a sequence) are inside the estimate
     assert serve.request_bytes(big, 1) > 4 * 300 * 8000
+    # CTA-pair tiles pad rows to 256: never less than 128-row tiles
+    assert serve.request_bytes(big, 2, tile=256) >= serve.request_bytes(big, 2, tile=128)
+    # the rank workspace is the library's bound plan for the set
+    from paper_0905_1744_gb300 import sad
+    plan = sad.kmer_rank_plan_bound(300, int(big.offsets[-1]), 3, 20, depth=2, tile=256)
+    assert serve.request_bytes(big, 2) > plan.ws_bytes
 
 
 def test_select_batch_takes_the_fitting_prefix_in_arrival_order():
@@ -55,9 +59,19 @@ def test_serve_rejects_a_request_above_the_budget_before_any_device_call():
     reqs = serve.make_requests([_set(50)], [0.0])
     need = serve.request_bytes(reqs[0].seqset, 2)
     with pytest.raises(ValueError, match="budget"):
-        serve.serve(reqs, depth=2, budget_bytes=need - 1, device="cpu")
+        serve.serve(reqs, shape=(256, 2, 0), budget_bytes=need - 1, device="cpu")
     with pytest.raises(ValueError):
-        serve.serve(reqs, depth=2, slots=0, device="cpu")
+        serve.serve(reqs, shape=(256, 2, 0), slots=0, device="cpu")
+    # the plan-free path needs cut planes (depth >= 1)
+    with pytest.raises(ValueError, match="depth"):
+        serve.serve(reqs, shape=(256, 0, 0), device="cpu")
+
+
+def test_max_overlap_counts_open_intervals():
+    assert serve.max_overlap([]) == 0
+    assert serve.max_overlap([(0, 1), (1, 2)]) == 1          # touching ends do not overlap
+    assert serve.max_overlap([(0, 3), (1, 2), (2.5, 4)]) == 2
+    assert serve.max_overlap([(0, 5), (1, 4), (2, 3)]) == 3
 
 
 def test_latency_stats():
@@ -77,10 +91,10 @@ def test_latency_stats():
 def _fake_plans(monkeypatch, t_max, ws_bytes, rem_bound=1000):
     calls = []
 
-    def plan(counts, k=3, alphabet=20, depth=0, ws=None, stream=None):
-        calls.append(depth)
-        return types.SimpleNamespace(depth=depth, t_max=t_max, rem_bound=rem_bound,
-                                     ws_bytes=ws_bytes(depth))
+    def plan(counts, k=3, alphabet=20, depth=0, ws=None, stream=None, budget=0, tile=0):
+        calls.append((tile, depth, budget))
+        return types.SimpleNamespace(depth=depth, tile=tile, budget=budget, t_max=t_max,
+                                     rem_bound=rem_bound, ws_bytes=ws_bytes(tile, depth))
     monkeypatch.setattr(autotune.sad, "kmer_rank_plan", plan)
     return calls
 
@@ -93,46 +107,93 @@ class _FakeWs:
         self.ensured.append(nbytes)
 
 
-def test_choose_depth_times_each_distinct_depth_and_keeps_the_fastest(monkeypatch):
+S = autotune.Shape
+
+
+def test_search_picks_among_tile_shapes_then_budgets():
+    """Faked timings: the fastest (tile, depth) of the first round, then the other
+    budgets at that (tile, depth) only."""
+    ms = {S(256, 0, 0): 3.0, S(256, 2, 0): 1.4, S(128, 0, 0): 2.5, S(128, 2, 0): 1.6,
+          S(256, 2, 256): 1.5, S(256, 2, 1536): 1.3}
+    timed = []
+
+    def timer(sh):
+        timed.append(sh)
+        return ms[sh]
+    first = autotune.first_round(None, tiles=(256, 128), depths=(0, 2))
+    assert first == [S(256, 0, 0), S(256, 2, 0), S(128, 0, 0), S(128, 2, 0)]
+    best, trials = autotune.search(timer, first)
+    assert best == S(256, 2, 1536)
+    assert timed == first + [S(256, 2, 256), S(256, 2, 1536)]
+    assert trials == {k.key: v for k, v in ms.items()}
+    # the other tile shape wins when it is faster; depth 0 cuts nothing: no budget round
+    ms2 = {S(256, 0, 0): 2.0, S(128, 0, 0): 1.0}
+    best, trials = autotune.search(lambda sh: ms2[sh],
+                                   autotune.first_round(None, tiles=(256, 128), depths=(0,)))
+    assert best == S(128, 0, 0) and len(trials) == 2
+    # shapes that do not apply (None) are skipped; nothing at all is an error
+    best, _ = autotune.search(lambda sh: None if sh.tile == 256 else 1.0,
+                              autotune.first_round(None, tiles=(256, 128), depths=(0,)))
+    assert best == S(128, 0, 0)
+    with pytest.raises(RuntimeError):
+        autotune.search(lambda sh: None, [S(128, 0, 0)])
+    assert S.parse(S(256, 6, 768).key) == S(256, 6, 768)
+
+
+def test_first_round_skips_depths_that_keep_every_plane():
+    assert autotune.first_round(3, tiles=(128,), depths=(0, 1, 2, 3, 4)) == \
+        [S(128, 0, 0), S(128, 1, 0), S(128, 2, 0)]
+    assert autotune.first_round(None, tiles=(256,), depths=(0, 1, 2), min_depth=1) == \
+        [S(256, 1, 0), S(256, 2, 0)]
+
+
+def test_choose_shape_times_candidates_and_keeps_the_fastest(monkeypatch):
     autotune._cache.clear()
-    _fake_plans(monkeypatch, t_max=4, ws_bytes=lambda d: 100 * (d + 1))
-    ms = {0: 3.0, 1: 1.5, 2: 1.2, 3: 2.0}
+    _fake_plans(monkeypatch, t_max=4, ws_bytes=lambda t, d: 100 * (d + 1) + t)
+    ms = {(256, 0): 3.0, (256, 1): 1.5, (256, 2): 1.1, (256, 3): 2.0,
+          (128, 0): 3.5, (128, 1): 1.9, (128, 2): 1.2, (128, 3): 2.2}
+    bud = {256: 1.3, 1536: 1.0}
     timed = []
 
     def time_rank(counts, lengths, plan, ws, *a, **kw):
-        timed.append(plan.depth)
-        return ms[plan.depth]
+        timed.append((plan.tile, plan.depth, plan.budget))
+        return ms[(plan.tile, plan.depth)] if plan.budget == 0 else bud[plan.budget]
     monkeypatch.setattr(autotune, "time_rank", time_rank)
     ws = _FakeWs()
     counts = torch.zeros(300, 8000, dtype=torch.int32)
-    best, trials = autotune.choose_depth(counts, None, ws, use_cache=False)
-    # depths at or above t_max keep every plane, the same work as depth 0: not timed
-    assert timed == [0, 1, 2, 3] and trials == ms and best == 2
-    assert ws.ensured == [100, 200, 300, 400]
-    # a workspace limit drops the depths that need more
+    best, trials = autotune.choose_shape(counts, None, ws, use_cache=False,
+                                         depths=(0, 1, 2, 3, 4))
+    # depth 4 >= t_max keeps every plane (the work of depth 0): not timed
+    assert [t for t in timed if t[2] == 0] == [(t, d, 0) for t in (256, 128) for d in range(4)]
+    assert timed[-2:] == [(256, 2, 256), (256, 2, 1536)]
+    assert best == S(256, 2, 1536) and len(trials) == 10
+    # a workspace limit drops the shapes that need more
     timed.clear()
-    best, trials = autotune.choose_depth(counts, None, ws, use_cache=False, max_ws_bytes=250)
-    assert timed == [0, 1] and best == 1
+    best, trials = autotune.choose_shape(counts, None, ws, use_cache=False, max_ws_bytes=330,
+                                         depths=(0, 1, 2, 3, 4))
+    assert best == S(128, 1, 1536)
+    assert all(100 * (d + 1) + t <= 330 for t, d, b in timed)
 
 
-def test_choose_depth_cache_by_size_class(monkeypatch, tmp_path):
+def test_choose_shape_cache_by_size_class(monkeypatch, tmp_path):
     autotune._cache.clear()
-    _fake_plans(monkeypatch, t_max=3, ws_bytes=lambda d: 1)
+    _fake_plans(monkeypatch, t_max=3, ws_bytes=lambda t, d: 1)
     monkeypatch.setattr(autotune, "time_rank",
-                        lambda counts, lengths, plan, ws, *a, **kw: {0: 2.0, 1: 1.0, 2: 3.0}[plan.depth])
+                        lambda counts, lengths, plan, ws, *a, **kw:
+                        {0: 2.0, 1: 1.0, 2: 3.0}[plan.depth] + (0.5 if plan.tile == 128 else 0))
     counts = torch.zeros(1000, 1, dtype=torch.int32)
-    best, trials = autotune.choose_depth(counts, None, _FakeWs())
-    assert best == 1 and trials
+    best, trials = autotune.choose_shape(counts, None, _FakeWs())
+    assert best == S(256, 1, 0) and trials
     # same size class (log2 N, t_max, log2 remainder bound): answered from the cache
-    best2, trials2 = autotune.choose_depth(torch.zeros(1023, 1, dtype=torch.int32), None,
+    best2, trials2 = autotune.choose_shape(torch.zeros(1023, 1, dtype=torch.int32), None,
                                            _FakeWs())
-    assert best2 == 1 and trials2 == {}
+    assert best2 == best and trials2 == {}
     path = str(tmp_path / "tune.json")
     autotune.save_cache(path)
     with open(path) as f:
         saved = json.load(f)
     plan1 = types.SimpleNamespace(t_max=3, rem_bound=1000)
-    assert saved == {autotune.signature(1000, plan1): 1}
+    assert saved == {"set_" + autotune.signature(1000, plan1): best.key}
     autotune._cache.clear()
     autotune.load_cache(path)
     assert autotune._cache == saved
