@@ -518,11 +518,14 @@ uint64_t sad_launch_count(void);
 /*
  * Diagnostics.
  * sad_rank_info - SYNCHRONOUS: after kmer_rank on `stream`, copies the plan the
- *   device chose into info[0..8]: {status, K_eff, K_pad, t_max, tiles,
- *   executed K chunks (sum over tiles of K extent / 256), planes kept per word,
- *   residual pair contributions, residual tiles}.
+ *   device chose into info[0..10]: {status, K_eff, K_pad, t_max, tiles,
+ *   executed K chunks (sum over tiles of plane chunks + remainder chunks, 256
+ *   K columns each), planes kept per word (the plan's depth), remainder
+ *   entries, column blocks with remainder entries, heavy entries (counts above
+ *   the remainder bitmap), remainder bitmap columns}; info must hold 16 entries.
  * sad_profile - enable != 0 starts recording a CUDA event pair around every
- *   launch of the plane GEMM kernel (on its own stream); 0 stops.
+ *   launch of the GEMM kernel (one CTA or CTA-pair form, on its own stream);
+ *   0 stops.
  * sad_profile_read - SYNCHRONOUS: waits for the recorded events, returns the
  *   summed GEMM time in milliseconds and the number of launches, and clears them.
  */

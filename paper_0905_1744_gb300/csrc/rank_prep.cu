@@ -28,7 +28,7 @@
 // for row u, which the epilogue reads from the counts.
 //
 // Sets. A call ranks one or more independent sets (a batch). Each set's rows are
-// stored contiguously (128-aligned) and its tiles only pair rows of that set, so
+// stored contiguously (aligned to the GEMM tile) and its tiles only pair rows of that set, so
 // the GEMM is block-diagonal; the column layout is shared (T over all sets).
 // Within a set, rows are stored in order of decreasing length (the order of
 // equal lengths is free: it changes no result), so that for every stored pair
@@ -44,13 +44,15 @@
 //   colmap         t_max, section ends, K_eff, the column maps, the covering depth
 //                  of every plane column
 //   lensort_*      stored row of every sequence, per-row division records
-//   bitmap_zero    clear the remainder bitmap
 //   planes         P rows as packed e2m1 (2 = 1.0, 0 = 0.0), block largest counts;
-//                  depth >= 1: bitmap bits, per-row remainder profile, the
-//                  (row, word, count >= 2) entries
-//   rem_depth      per column block: plane depth d_J, per-row entry offsets
-//   rem_scan       block offsets of the remainder lists
-//   rem_scatter    the remainder lists, grouped by row
+//                  depth >= 1: per-row remainder profile, the (row, word,
+//                  count >= 2) entries
+//   rem_depth      per column block: plane depth d_J, per-row entry offsets; the
+//                  smallest depth of a block with remainder entries
+//   rem_scan       block offsets of the remainder lists; the lowest column a
+//                  remainder entry can name
+//   bitmap_zero    clear the remainder bitmap from that column on
+//   rem_scatter    the remainder lists, grouped by row, and the bitmap bits
 //   tiles          per set, the upper-triangle tile list with per-tile K extent
 #include "rank.cuh"
 #include "sort.cuh"
@@ -250,6 +252,8 @@ __global__ void rank_init_kernel(RankPtrs P, int32_t eps, int with_keys) {
     P.hdr->heavy_entries = 0;
     P.hdr->t_bits = 0;
     P.hdr->rem_blocks = 0;
+    P.hdr->dmin = 0x7FFFFFFF;
+    P.hdr->bm_lo = 0;
   }
 }
 
@@ -554,27 +558,42 @@ __global__ void __launch_bounds__(kSortThreads) lensort_sets_kernel(
 }
 
 // Remainder bookkeeping of a count c >= 2 of word tau in stored row pos (plans of
-// depth >= 1): the bitmap bits of thresholds 2..min(c, tb), the row's profile (each
-// threshold counted under the first plane depth that covers its column, dkeep + 1
-// when it is above the planes) and the row's heavy count (c > tb).
-__device__ __noinline__ void note_count(const RankPtrs &P, int64_t pos, int32_t tau, int32_t c,
-                                           int32_t dkeep, int32_t tb, int32_t n1,
-                                           int64_t bm_stride, uint32_t *s_prof) {
+// depth >= 1): the row's profile, each threshold 2..min(c, tb) counted under the
+// first plane depth that covers its column (dkeep + 1 when it is above the planes),
+// and the row's heavy count (c > tb). ru[d] = the K extent of depth d (the end of
+// section d rounded up to a K chunk, at most K_pad), d = 1..dkeep: the covering
+// depth of a column is the smallest d whose extent lies past it. (The remainder
+// bitmap is filled later, from the flat entries, once the block depths are known.)
+__device__ __noinline__ void note_count(const RankPtrs &P, int32_t tau, int32_t c, int32_t dkeep,
+                                        int32_t tb, const int32_t *ru, uint32_t *s_prof) {
   const int32_t top = min(c, tb);
   for (int32_t t = 2; t <= top; ++t) {
-    const int32_t col = P.coltab[(int64_t)(t - 1) * P.eps + tau];
-    atomicOr(&P.bitmap[(int64_t)(col - n1) * bm_stride + (pos >> 5)], 1u << (pos & 31));
-    const int32_t ds = t <= dkeep ? (int32_t)P.dstar[col] : dkeep + 1;
+    int32_t ds = dkeep + 1;
+    if (t <= dkeep) {
+      const int32_t col = P.coltab[(int64_t)(t - 1) * P.eps + tau];
+      ds = 1;
+      while (ds < dkeep && ru[ds] <= col) ++ds;
+    }
     atomicAdd(&s_prof[ds - 1], 1u);
   }
   if (c > tb) atomicAdd(&s_prof[kProf - 1], 1u);
 }
 
+// K extents of the kept depths into ru[1..dkeep] (shared; the calling block then
+// synchronises).
+__device__ __forceinline__ void fill_extents(const RankPtrs &P, int32_t dkeep, int32_t k_pad,
+                                             int32_t *ru) {
+  for (int d = threadIdx.x; d <= kMaxPlaneDepth; d += blockDim.x)
+    ru[d] = d >= 1 && d <= dkeep ? min((P.secend[d] + kKCols - 1) / kKCols * kKCols, k_pad) : 0;
+}
+
 __global__ void bitmap_zero_kernel(RankPtrs P) {
   pdl_enter();
   if (P.hdr->status != 0) return;
-  const int64_t words4 = (int64_t)P.hdr->bm_cols * (P.n_pad / 128);
-  uint4 *p = reinterpret_cast<uint4 *>(P.bitmap);
+  // the columns from bm_lo on (the only ones a remainder entry can name)
+  const int64_t c0 = max(P.hdr->bm_lo - P.secend[1], 0);
+  const int64_t words4 = max((int64_t)P.hdr->bm_cols - c0, (int64_t)0) * (P.n_pad / 128);
+  uint4 *p = reinterpret_cast<uint4 *>(P.bitmap) + c0 * (P.n_pad / 128);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words4;
        i += (int64_t)gridDim.x * blockDim.x)
     p[i] = make_uint4(0, 0, 0, 0);
@@ -604,14 +623,16 @@ __global__ void __launch_bounds__(256) planes_kernel(const int32_t *__restrict__
   __shared__ int32_t s_scan[32];
   __shared__ unsigned long long s_first;
   __shared__ uint32_t s_prof[kPlaneRows][kProf];
+  __shared__ int32_t s_ru[kMaxPlaneDepth + 1];
+  // the K extents first: every thread reaches the barrier
+  fill_extents(P, P.hdr->depth, P.hdr->k_pad, s_ru);
+  __syncthreads();
   if (P.hdr->status != 0) return;
   const int32_t k_eff = (int32_t)P.hdr->k_eff;
   const int32_t k_pad = P.hdr->k_pad;
   const int32_t dkeep = P.hdr->depth;
   const bool residual = remainder_mode(P);
   const int32_t tb = bit_depth(P);
-  const int32_t n1 = P.secend[1];
-  const int64_t bm_stride = P.n_pad / 32;
   const bool vec = (eps & 3) == 0 && (reinterpret_cast<uintptr_t>(counts) & 15) == 0;
   const int64_t groups = P.n_pad / kPlaneRows;
   for (int64_t g = blockIdx.x; g < groups; g += gridDim.x) {
@@ -692,7 +713,7 @@ __global__ void __launch_bounds__(256) planes_kernel(const int32_t *__restrict__
         for (int tau = threadIdx.x; tau < eps; tau += blockDim.x) {
           const int32_t c = s_cnt[r * eps + tau];
           if (c >= 2) {
-            note_count(P, pos, tau, c, dkeep, tb, n1, bm_stride, s_prof[r]);
+            note_count(P, tau, c, dkeep, tb, s_ru, s_prof[r]);
             if (slot < (unsigned long long)P.list_cap)
               P.flat[slot] = make_int2((int32_t)pos, tau | (c << 16));
             ++slot;
@@ -751,14 +772,8 @@ __global__ void __launch_bounds__(256) planes_kernel(const int32_t *__restrict__
   }
 }
 
-// Plane rows for plans of depth >= 1, streamed: one warp per stored row reads the
-// row's counts once (16 bytes per lane, four loads in flight). A plane value is
-// the 4-bit e2m1 [c >= t] (1.0 or 0), two columns to a byte. When every word
-// occurs somewhere, section 1 is the identity map and a lane writes its four words
-// as one 2-byte store; the columns past section 1 are zero-filled with 16-byte
-// stores first, and only the words counted twice or more then set their values in
-// sections 2..min(c, D) (atomic OR: neighbouring columns share bytes). Otherwise
-// the whole row is zero-filled and every 1 is set that way. Counts >= 2 also set
+// Plane rows for plans of depth >= 1 (the streaming writer below). A plane value is
+// the 4-bit e2m1 [c >= t] (1.0 or 0), two columns to a byte. Counts >= 2 also set
 // their remainder bitmap bits and the row's profile, and go to a per-warp buffer
 // that is appended to the flat entry list with one atomic per row; a row with more
 // than kExCap of them is scanned again for the append.
@@ -767,48 +782,60 @@ constexpr int kStreamUnroll = 4;
 
 __device__ __forceinline__ uint32_t plane_val(int32_t c, int32_t t) { return c >= t ? kE2M1One : 0u; }
 
-// Set plane column col of a row to 1.0 (the row bytes are zero there beforehand).
-__device__ __forceinline__ void plane_set(uint8_t *prow, int32_t col) {
-  atomicOr(reinterpret_cast<unsigned int *>(prow) + (col >> 3), kE2M1One << (4 * (col & 7)));
-}
+// The streaming plane writer: a warp per stored row, two passes over the row.
+// Pass 1 streams the row's counts once (16 bytes per lane, four loads in flight):
+// the row's largest count and sum, the remainder bookkeeping of every count >= 2,
+// section 1 written directly when it is the identity map (four words to one 2-byte
+// store), and the counts kept in the warp's shared memory as 4-bit values
+// saturated at 15 (every plane threshold is <= 8). Pass 2 writes every other
+// 32-bit word of the row (eight columns) once, in order: for each column its word
+// and threshold from the column map, its value [count >= t] from the shared 4-bit
+// counts. No global atomics, no zero fill: each byte is written once.
+constexpr int kStreamWarps = 8;
+constexpr int kStreamThreads = 32 * kStreamWarps;
 
-__global__ void __launch_bounds__(256) planes_stream_kernel(const int32_t *__restrict__ counts,
-                                                            int32_t eps, RankPtrs P) {
+__global__ void __launch_bounds__(kStreamThreads, 4) planes_stream_kernel(
+    const int32_t *__restrict__ counts, int32_t eps, RankPtrs P) {
   pdl_enter();
-  __shared__ int2 s_ex[8][kExCap];
-  __shared__ int32_t s_exn[8];
-  __shared__ uint32_t s_prof[8][kProf];
+  extern __shared__ uint4 s_nib4[];
+  __shared__ int2 s_ex[kStreamWarps][kExCap];
+  __shared__ int32_t s_exn[kStreamWarps];
+  __shared__ uint32_t s_prof[kStreamWarps][kProf];
+  __shared__ int32_t s_ru[kMaxPlaneDepth + 1];
+  // the K extents first: every thread reaches the barrier
+  fill_extents(P, P.hdr->depth, P.hdr->k_pad, s_ru);
+  __syncthreads();
   if (P.hdr->status != 0) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wa = blockDim.x >> 5;
   const int32_t k_pad = P.hdr->k_pad;
+  const int32_t k_eff = (int32_t)P.hdr->k_eff;
   const int32_t dkeep = P.hdr->depth;
   const bool residual = remainder_mode(P);
   const int32_t tb = bit_depth(P);
-  const int64_t bm_stride = P.n_pad / 32;
   const int q4 = eps >> 2;
   const int32_t s1 = P.secend[1];  // end of section 1
   const bool ident = s1 == eps;    // section 1 = every word, in order
-  const int32_t kb = k_pad / 2;    // row bytes in use
-  // bytes zero-filled before the ones are set: past section 1, or all of the row
-  const int32_t z0 = ident ? s1 / 2 : 0;
-  const int32_t z16 = min((z0 + 15) & ~15, kb);
+  const int32_t kw = k_pad / 8;    // 32-bit words of the row in use
+  // words [0, w1) hold section-1 columns only and are written in pass 1
+  const int32_t w1 = ident ? s1 / 8 : 0;
+  // the warp's 4-bit counts: eps / 2 bytes rounded up to 16
+  const int32_t nib_words = ((eps / 2 + 15) & ~15) / 4;
+  uint32_t *nib = reinterpret_cast<uint32_t *>(s_nib4) + (size_t)warp * nib_words;
+  uint16_t *nib16 = reinterpret_cast<uint16_t *>(nib);
   if (lane == 0) s_exn[warp] = 0;
   if (lane < kProf) s_prof[warp][lane] = 0u;
   __syncwarp();
-  for (int64_t pos = (int64_t)blockIdx.x * 8 + warp; pos < P.n_pad;
-       pos += (int64_t)gridDim.x * 8) {
+  for (int64_t pos = (int64_t)blockIdx.x * wa + warp; pos < P.n_pad;
+       pos += (int64_t)gridDim.x * wa) {
     const int32_t x = P.perm[pos];
     uint8_t *prow = P.planes + pos * (P.k_cap / 2);
     if (x < 0) {  // padding row: all zero
-      for (int c = 16 * lane; c < kb; c += 512)
+      for (int c = 16 * lane; c < k_pad / 2; c += 512)
         *reinterpret_cast<uint4 *>(prow + c) = make_uint4(0, 0, 0, 0);
       if (residual && lane < kProf) P.prof[pos * kProf + lane] = 0u;
       continue;
     }
-    for (int c = z0 + lane; c < z16; c += 32) prow[c] = 0;
-    for (int c = z16 + 16 * lane; c < kb; c += 512)
-      *reinterpret_cast<uint4 *>(prow + c) = make_uint4(0, 0, 0, 0);
-    __syncwarp();
     const int4 *row4 = reinterpret_cast<const int4 *>(counts + (int64_t)x * eps);
     int32_t mx = 0, sum = 0;
     for (int base = 0; base < q4; base += 32 * kStreamUnroll) {
@@ -825,30 +852,19 @@ __global__ void __launch_bounds__(256) planes_stream_kernel(const int32_t *__res
         const int32_t c[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
         mx = max(mx, max(max(c[0], c[1]), max(c[2], c[3])));
         sum += c[0] + c[1] + c[2] + c[3];
-        if (ident) {
+        nib16[q] = (uint16_t)(min(c[0], 15) | min(c[1], 15) << 4 | min(c[2], 15) << 8 |
+                              min(c[3], 15) << 12);
+        if (ident && q < 2 * w1) {
           // columns 4q..4q+3 = bytes 2q, 2q+1
           *reinterpret_cast<uint16_t *>(prow + 2 * q) =
               (uint16_t)(plane_val(c[0], 1) | plane_val(c[1], 1) << 4 | plane_val(c[2], 1) << 8 |
                          plane_val(c[3], 1) << 12);
-        } else {
-          const int4 col = __ldg(reinterpret_cast<const int4 *>(P.coltab) + q);
-          const int32_t cc[4] = {col.x, col.y, col.z, col.w};
-#pragma unroll
-          for (int b = 0; b < 4; ++b)
-            if (cc[b] >= 0 && c[b] >= 1) plane_set(prow, cc[b]);
-        }
-        if (dkeep >= 2) {
-          // a word counted c >= 2 times is in sections 2..T >= c: its values there are 1
-#pragma unroll
-          for (int b = 0; b < 4; ++b)
-            for (int t = 2; t <= min(c[b], dkeep); ++t)
-              plane_set(prow, P.coltab[(int64_t)(t - 1) * eps + 4 * q + b]);
         }
         if (residual) {
 #pragma unroll
           for (int b = 0; b < 4; ++b) {
             if (c[b] >= 2) {
-              note_count(P, pos, 4 * q + b, c[b], dkeep, tb, s1, bm_stride, s_prof[warp]);
+              note_count(P, 4 * q + b, c[b], dkeep, tb, s_ru, s_prof[warp]);
               const int slot = atomicAdd(&s_exn[warp], 1);
               if (slot < kExCap) s_ex[warp][slot] = make_int2((int32_t)pos, (4 * q + b) | (c[b] << 16));
             }
@@ -856,6 +872,32 @@ __global__ void __launch_bounds__(256) planes_stream_kernel(const int32_t *__res
         }
       }
     }
+    // pass 2: the row's words from w1 on, eight columns each, gathered from the
+    // column map and the 4-bit counts (columns past K_eff are 0)
+    __syncwarp();
+    uint32_t *prow32 = reinterpret_cast<uint32_t *>(prow);
+    for (int32_t w = w1 + lane; w < kw; w += 32) {
+      const int32_t c0 = 8 * w;
+      uint32_t val = 0;
+      if (c0 + 8 <= k_eff) {
+        const int4 e4a = __ldg(reinterpret_cast<const int4 *>(P.colmap + c0));
+        const int4 e4b = __ldg(reinterpret_cast<const int4 *>(P.colmap + c0 + 4));
+        const int32_t ev[8] = {e4a.x, e4a.y, e4a.z, e4a.w, e4b.x, e4b.y, e4b.z, e4b.w};
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+          const uint32_t tau = (uint32_t)ev[b] & 0xFFFFu, t = (uint32_t)ev[b] >> 16;
+          if (((nib[tau >> 3] >> (4 * (tau & 7))) & 15u) >= t) val |= kE2M1One << (4 * b);
+        }
+      } else {
+        for (int b = 0; b < 8 && c0 + b < k_eff; ++b) {
+          const int32_t e = __ldg(P.colmap + c0 + b);
+          const uint32_t tau = (uint32_t)e & 0xFFFFu, t = (uint32_t)e >> 16;
+          if (((nib[tau >> 3] >> (4 * (tau & 7))) & 15u) >= t) val |= kE2M1One << (4 * b);
+        }
+      }
+      prow32[w] = val;
+    }
+    __syncwarp();  // the next row's pass 1 rewrites the 4-bit counts
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -975,6 +1017,9 @@ __global__ void __launch_bounds__(kRemThreads) rem_depth_kernel(RankPtrs P) {
     if (threadIdx.x == 0) {
       P.blkrem[2 * b] = tot_e;
       P.blkrem[2 * b + 1] = tot_h;
+      // the smallest depth of a block that has remainder entries: no column covered at
+      // that depth is ever a remainder column
+      if (tot_e > 0) atomicMin(&P.hdr->dmin, d);
     }
     __syncthreads();
   }
@@ -1004,6 +1049,13 @@ __global__ void __launch_bounds__(1024) rem_scan_kernel(RankPtrs P) {
     }
   }
   if (threadIdx.x == 0) {
+    // lowest remainder column: past the planes (t > dkeep), or past the K extent of
+    // the smallest block depth; none when no block has remainder entries
+    const int32_t dkeep = P.hdr->depth, dmin = P.hdr->dmin;
+    int32_t lo = P.secend[dkeep];
+    if (dmin < dkeep)
+      lo = min(lo, min((P.secend[dmin] + kKCols - 1) / kKCols * kKCols, P.hdr->k_pad));
+    P.hdr->bm_lo = dmin == 0x7FFFFFFF ? P.secend[1] + P.hdr->bm_cols : lo;
     P.blkrem[2 * nblk] = s_carry[0];
     P.blkrem[2 * nblk + 1] = s_carry[1];
     P.hdr->rem_entries = s_carry[0];
@@ -1026,6 +1078,8 @@ __global__ void __launch_bounds__(256) rem_scatter_kernel(RankPtrs P) {
   const int32_t dkeep = P.hdr->depth;
   const int32_t tb = bit_depth(P);
   const int32_t n1 = P.secend[1];
+  const int32_t bm_lo = P.hdr->bm_lo;
+  const int64_t bm_stride = P.n_pad / 32;
   const int64_t nf = (int64_t)min(P.hdr->flat_count, (unsigned long long)P.list_cap);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -1039,6 +1093,9 @@ __global__ void __launch_bounds__(256) rem_scatter_kernel(RankPtrs P) {
     const int32_t top = min(c, tb);
     for (int32_t t = 2; t <= top; ++t) {
       const int32_t col = P.coltab[(int64_t)(t - 1) * P.eps + tau];
+      // the row's bit in the remainder bitmap (columns a remainder entry can name)
+      if (col >= bm_lo)
+        atomicOr(&P.bitmap[(int64_t)(col - n1) * bm_stride + (pos >> 5)], 1u << (pos & 31));
       const bool covered = t <= dkeep && (int32_t)P.dstar[col] <= d;
       if (!covered) {
         const int32_t slot = atomicAdd(&P.cursor[2 * pos], 1);
@@ -1238,21 +1295,29 @@ int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *le
     pdl_launch(lensort_sets_kernel, gsets, kSortThreads, kSortSmem, st, lengths, k, Q);
     SAD_LAUNCH_CHECK();
   }
-  if (rem && Q.bm_cols > 0) {
-    pdl_launch(bitmap_zero_kernel, (unsigned)num_sms() * 8, 256, 0, st, Q);
-    SAD_LAUNCH_CHECK();
-  }
   if (rem && (eps & 3) == 0 && (reinterpret_cast<uintptr_t>(counts) & 15) == 0 &&
       (Q.k_cap & 31) == 0) {
-    const int64_t warps = Q.n_pad;
+    // 4-bit counts of a row per warp: eps / 2 bytes rounded up to 16; as many warps a
+    // block as fit in 96 KB (eight for eps <= 24000)
+    const int64_t nib_bytes = ((eps / 2 + 15) & ~15);
+    const int64_t fit = (96 << 10) / nib_bytes;
+    const int warps = (int)std::max<int64_t>(1, std::min<int64_t>(kStreamWarps, fit));
+    const int dyn = (int)(warps * nib_bytes);
+    static bool attr_set = false;
+    if (!attr_set) {
+      if (cudaFuncSetAttribute(planes_stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               96 << 10) != cudaSuccess)
+        return SAD_ERR_CUDA;
+      attr_set = true;
+    }
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, planes_stream_kernel, 256, 0) !=
-        cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, planes_stream_kernel, 32 * warps,
+                                                      dyn) != cudaSuccess)
       return SAD_ERR_CUDA;
     const int64_t cap = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
-    const int64_t want = (warps + 7) / 8;
-    pdl_launch(planes_stream_kernel, (unsigned)(want < cap ? want : cap), 256, 0, st, counts, eps,
-               Q);
+    const int64_t want = (Q.n_pad + warps - 1) / warps;
+    pdl_launch(planes_stream_kernel, (unsigned)(want < cap ? want : cap), 32 * warps, (size_t)dyn,
+               st, counts, eps, Q);
     SAD_LAUNCH_CHECK();
   } else {
     const size_t smem = sizeof(uint16_t) * (size_t)eps * kPlaneRows;
@@ -1277,6 +1342,10 @@ int rank_prep_launch(const RankPtrs &P, const int32_t *counts, const int32_t *le
     SAD_LAUNCH_CHECK();
     pdl_launch(rem_scan_kernel, 1, 1024, 0, st, Q);
     SAD_LAUNCH_CHECK();
+    if (Q.bm_cols > 0) {
+      pdl_launch(bitmap_zero_kernel, (unsigned)num_sms() * 8, 256, 0, st, Q);
+      SAD_LAUNCH_CHECK();
+    }
     pdl_launch(rem_scatter_kernel, grid_for(Q.list_cap, 256), 256, 0, st, Q);
     SAD_LAUNCH_CHECK();
   }

@@ -67,7 +67,9 @@ struct WsHeader {
   int64_t heavy_entries; // heavy remainder entries in use
   int32_t t_bits;        // T_b: largest threshold held in the bitmap
   int32_t rem_blocks;    // column blocks whose plane depth is below their largest count
-  int32_t pad[38];
+  int32_t dmin;          // smallest plane depth of any column block
+  int32_t bm_lo;         // lowest plane column that can be a remainder column
+  int32_t pad[36];
 };
 static_assert(sizeof(WsHeader) == 256, "header is 256 bytes");
 

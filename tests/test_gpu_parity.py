@@ -108,7 +108,8 @@ def test_rank_family_set_several_tiles(sad, oracle_mod, depth, word_max):
                                             (1, True), (40, True)])
 def test_rank_small_alphabet_deep_planes(sad, oracle_mod, depth, word_max):
     # 4 letters, k = 3: 64 words, counts up to hundreds -> many threshold sections,
-    # and a residual of long excess lists when the planes are cut
+    # and, when the planes are cut, remainder chunks plus heavy entries (counts above
+    # the remainder bitmap) added in the epilogue
     s = datagen.random_small(300, 3, 2500, seed=11, alphabet=4)
     check_rank(sad, oracle_mod, s, k=3, alphabet=4, depth=depth, word_max=word_max)
 
@@ -116,8 +117,8 @@ def test_rank_small_alphabet_deep_planes(sad, oracle_mod, depth, word_max):
 @pytest.mark.parametrize("depth", [0, 1, 7])
 def test_rank_long_homopolymers_exact_accumulation(sad, oracle_mod, depth):
     """Shared counts close to the longest supported m (S = min(m_i, m_j) up to
-    19998): the f32 tensor-core accumulation and the u16 residual blocks must
-    stay exact."""
+    19998): the f32 tensor-core accumulation, the remainder chunks and the heavy
+    entries must stay exact."""
     seqs = ["A" * 20000, "A" * 15000, "A" * 19999, "AC" * 6000, "A" * 3, "C" * 9000,
             "A" * 12000 + "C" * 8000]
     s = datagen.from_strings(seqs)
