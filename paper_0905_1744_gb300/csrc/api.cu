@@ -581,6 +581,14 @@ int sad_batch_partition(const uint64_t *d_key_hi, const uint64_t *d_key_lo, cons
     return SAD_ERR_INVALID_ARGUMENT;
   if (ws_bytes < plan->part_ws_bytes) return SAD_ERR_WORKSPACE;
   const PartTotals pt{plan->n_total, plan->sum_p, plan->sum_p1, plan->sum_pp1, plan->sum_pp};
+  if (plan->n_sets == 1) {
+    // one set: its sizes are the plan's, so the single-set route (chunk sorts and rank
+    // merges for few buckets) applies; same outputs, same workspace layout
+    return partition_sets_launch(d_key_hi, d_key_lo, 1, nullptr, nullptr,
+                                 (int32_t)plan->n_total, (int32_t)plan->sum_p, pt, plan->max_p,
+                                 d_bucket_offsets, d_members, d_pivot_idx, d_ws,
+                                 static_cast<cudaStream_t>(stream));
+  }
   return partition_sets_launch(d_key_hi, d_key_lo, plan->n_sets, d_n, d_p, 0, 0, pt,
                                plan->max_p, d_bucket_offsets, d_members, d_pivot_idx, d_ws,
                                static_cast<cudaStream_t>(stream));

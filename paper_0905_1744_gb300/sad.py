@@ -800,6 +800,33 @@ def global_partition_set(codes: torch.Tensor, offsets: torch.Tensor, p: int, ks:
                 bucket_offsets=offs, members=mem, pivot_idx=piv)
 
 
+class BatchPool:
+    """Buffers that the successive batches of one stream reuse (a serving slot, a
+    loop over batches): pinned host staging, the device arrays of a Batch and its
+    three workspaces. Each buffer grows (by half again) when a batch needs more and
+    is otherwise handed out as a view, so building a new batch on the pool
+    allocates nothing once the pool has warmed up. A batch built on a pool must
+    have finished on the device, and its results been read, before the next batch
+    is built on the same pool."""
+
+    def __init__(self, device=None):
+        self.device = torch.device(device or "cuda")
+        self.bufs: dict = {}
+        self.workspaces = (Workspace(self.device, 256), Workspace(self.device),
+                           Workspace(self.device))
+
+    def get(self, name: str, n: int, dtype, pinned: bool = False) -> torch.Tensor:
+        t = self.bufs.get(name)
+        if t is None or t.numel() < n or t.dtype != dtype:
+            cap = max(int(n), 1)
+            if t is not None and t.dtype == dtype:
+                cap = max(cap, int(t.numel() * 3 // 2))
+            t = (torch.empty(cap, dtype=dtype, pin_memory=True) if pinned else
+                 torch.empty(cap, dtype=dtype, device=self.device))
+            self.bufs[name] = t
+        return t[:n]
+
+
 class Batch:
     """Many independent sequence sets ranked and partitioned together.
 
@@ -816,57 +843,85 @@ class Batch:
     synchronisation, so ``capture(graph)`` records it into a library Graph:
     the first batch instantiates it and each later batch captured into the same
     Graph only updates its parameters. ``workspaces`` (count, rank, partition)
-    may be shared by batches that never run at the same time.
+    may be shared by batches that never run at the same time; ``pool`` (a
+    BatchPool) supplies them and every other buffer. ``count=True`` launches the
+    count on ``stream`` as soon as the inputs are uploaded (then run or capture
+    with count=False).
     """
 
     def __init__(self, sets, device=None, k: int = 3, alphabet: int = 20, workspaces=None,
-                 stream=None, pin: bool = True):
+                 stream=None, pin: bool = True, pool: "BatchPool | None" = None,
+                 count: bool = False):
         import numpy as np
         self.device = torch.device(device or "cuda")
         self.k, self.alphabet = k, alphabet
         self.n = np.array([s.offsets.shape[0] - 1 for s in sets], dtype=np.int32)
         self.p = np.array([s.p for s in sets], dtype=np.int32)
-        lens = [np.diff(s.offsets) for s in sets]
-        codes = np.concatenate([s.codes[s.offsets[0]:s.offsets[-1]] for s in sets])
-        offsets = np.zeros(int(self.n.sum()) + 1, dtype=np.int64)
-        np.cumsum(np.concatenate(lens), out=offsets[1:])
+        nt = int(self.n.sum())
         self.seq_begin = np.concatenate([[0], np.cumsum(self.n)]).astype(np.int64)
         self.boff_begin = np.concatenate([[0], np.cumsum(self.p + 1)]).astype(np.int64)
         self.piv_begin = np.concatenate([[0], np.cumsum(self.p - 1)]).astype(np.int64)
-        self.h_codes, self.h_offsets = codes, offsets
-        self.total_len = int(offsets[-1])
+        spans = [(int(s.offsets[0]), int(s.offsets[-1])) for s in sets]
+        self.total_len = sum(b - a for a, b in spans)
         dev = self.device
         on_gpu = dev.type == "cuda"
         pin = pin and on_gpu
+        if pool is not None:
+            def dbuf(name, n, dtype):
+                return pool.get(name, n, dtype)
 
-        def host(a):
-            t = torch.from_numpy(np.ascontiguousarray(a))
-            return t.pin_memory() if pin else t
-        self.h_in = dict(codes=host(codes), offsets=host(offsets), n=host(self.n),
-                         p=host(self.p))
-        nt = int(self.n.sum())
-        self.codes = torch.empty(max(codes.shape[0], 1), dtype=torch.uint8, device=dev)
-        self.offsets = torch.empty(nt + 1, dtype=torch.int64, device=dev)
-        self.d_n = torch.empty(self.n_sets, dtype=torch.int32, device=dev)
-        self.d_p = torch.empty(self.n_sets, dtype=torch.int32, device=dev)
-        # lengths: derived on the device by the library in run(); host-built off the GPU
-        self.lengths = (torch.empty(nt, dtype=torch.int32, device=dev) if on_gpu else
-                        torch.from_numpy(np.concatenate(lens).astype(np.int32)))
-        self.counts = torch.empty((nt, alphabet ** k), dtype=torch.int32, device=dev)
-        self.word_max = torch.empty(alphabet ** k, dtype=torch.int32, device=dev)
-        self.key_hi = torch.empty(nt, dtype=torch.uint64, device=dev)
-        self.key_lo = torch.empty(nt, dtype=torch.uint64, device=dev)
-        self.rank = torch.empty(nt, dtype=torch.float64, device=dev)
-        self.bucket_offsets = torch.empty(int(self.boff_begin[-1]), dtype=torch.int32, device=dev)
-        self.members = torch.empty(nt, dtype=torch.int32, device=dev)
-        self.pivot_idx = torch.empty(max(int(self.piv_begin[-1]), 1), dtype=torch.int32,
-                                     device=dev)
+            def hbuf(name, n, dtype):
+                return pool.get(name, n, dtype, pinned=pin)
+            workspaces = pool.workspaces
+        else:
+            def dbuf(name, n, dtype):
+                return torch.empty(n, dtype=dtype, device=dev)
+
+            def hbuf(name, n, dtype):
+                return torch.empty(n, dtype=dtype, pin_memory=pin)
+        # host staging, written in place: codes set after set, offsets rebased
+        h_codes = hbuf("h_codes", max(self.total_len, 1), torch.uint8)
+        h_offsets = hbuf("h_offsets", nt + 1, torch.int64)
+        hc, ho = h_codes.numpy(), h_offsets.numpy()
+        at, row = 0, 0
+        ho[0] = 0
+        for s, (a, b) in zip(sets, spans):
+            hc[at:at + b - a] = s.codes[a:b]
+            m = s.offsets.shape[0] - 1
+            ho[row + 1:row + m + 1] = s.offsets[1:] - a + at
+            at += b - a
+            row += m
+        h_n = hbuf("h_n", self.n_sets, torch.int32)
+        h_p = hbuf("h_p", self.n_sets, torch.int32)
+        h_n.numpy()[:] = self.n
+        h_p.numpy()[:] = self.p
+        self.h_codes, self.h_offsets = hc[:self.total_len], ho
+        self.h_in = dict(codes=h_codes[:self.total_len], offsets=h_offsets, n=h_n, p=h_p)
+        self.codes = dbuf("codes", max(self.total_len, 1), torch.uint8)
+        self.offsets = dbuf("offsets", nt + 1, torch.int64)
+        self.d_n = dbuf("d_n", self.n_sets, torch.int32)
+        self.d_p = dbuf("d_p", self.n_sets, torch.int32)
+        eps = alphabet ** k
+        self.counts = dbuf("counts", nt * eps, torch.int32).view(nt, eps)
+        self.word_max = dbuf("word_max", eps, torch.int32)
         if workspaces is None:
             workspaces = (Workspace(dev, 256), Workspace(dev), Workspace(dev))
         self.ws_count, self.ws_rank, self.ws_part = workspaces
+        self.upload(stream)
+        if count:
+            # the device counts while the host sets up the rest
+            self.count(stream)
+        # lengths: derived on the device by the library in run(); host-built off the GPU
+        self.lengths = (dbuf("lengths", nt, torch.int32) if on_gpu else
+                        torch.from_numpy(np.diff(ho).astype(np.int32)))
+        self.key_hi = dbuf("key_hi", nt, torch.uint64)
+        self.key_lo = dbuf("key_lo", nt, torch.uint64)
+        self.rank = dbuf("rank", nt, torch.float64)
+        self.bucket_offsets = dbuf("bucket_offsets", int(self.boff_begin[-1]), torch.int32)
+        self.members = dbuf("members", nt, torch.int32)
+        self.pivot_idx = dbuf("pivot_idx", max(int(self.piv_begin[-1]), 1), torch.int32)
         self.plan_ = None
         self.graph = None
-        self.upload(stream)
 
     @property
     def n_sets(self) -> int:
@@ -953,15 +1008,17 @@ class Batch:
                                        _ptr(self.pivot_idx), _ptr(self.ws_part.buf),
                                        self.ws_part.nbytes, st), "sad_batch_partition")
 
-    def capture(self, graph: Graph | None = None, stream=None) -> Graph:
+    def capture(self, graph: Graph | None = None, stream=None, count: bool = True) -> Graph:
         """Records run() into ``graph`` (a new Graph if None): instantiated on its
         first capture, updated in place on later ones. Capture needs a stream other
-        than the legacy default one: a side stream is used when none is given."""
+        than the legacy default one: a side stream is used when none is given.
+        ``count=False`` leaves the count out of the graph (the caller launched it
+        already, e.g. to start the device while the host builds the graph)."""
         g = graph or Graph()
         s = stream or torch.cuda.Stream(self.device)
         if stream is None:
             s.wait_stream(torch.cuda.current_stream(self.device))
-        g.capture(lambda st: self.run(stream=st), s)
+        g.capture(lambda st: self.run(stream=st, count=count), s)
         self.graph = g
         return g
 

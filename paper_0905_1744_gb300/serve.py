@@ -21,6 +21,8 @@ order and runs the plain per-set calls for each.
 from __future__ import annotations
 
 import dataclasses
+import queue as _queue
+import threading
 import time
 
 import numpy as np
@@ -39,6 +41,7 @@ class Request:
     seqset: object          # datagen.SeqSet-like: codes, offsets, p
     done: float = -1.0
     result: dict | None = None
+    nbytes: int = -1        # admission estimate (request_bytes), computed once
 
 
 def request_bytes(s, depth: int, k: int = 3, alphabet: int = 20, tile: int = 256,
@@ -66,7 +69,9 @@ def select_batch(queue, used: int, budget_bytes: int, max_batch: int, depth: int
     does not fit yet (it is never overtaken, so admission stays in arrival order)."""
     take, nbytes = [], 0
     for r in queue:
-        rb = request_bytes(r.seqset, depth, tile=tile, budget=budget)
+        if r.nbytes < 0:
+            r.nbytes = request_bytes(r.seqset, depth, tile=tile, budget=budget)
+        rb = r.nbytes
         if len(take) >= max_batch or used + nbytes + rb > budget_bytes:
             break
         take.append(r)
@@ -75,47 +80,121 @@ def select_batch(queue, used: int, budget_bytes: int, max_batch: int, depth: int
 
 
 class _Slot:
-    """One in-flight position: a stream, a reusable graph and (while busy) a batch."""
+    """One in-flight position: a stream, a reusable graph, (with ws_pool) a buffer
+    pool its batches are built on, and (while busy) a batch."""
 
     def __init__(self, device, ws_pool: bool):
         self.stream = torch.cuda.Stream(device)
         self.graph = sad.Graph()
-        self.workspaces = ((sad.Workspace(device, 256), sad.Workspace(device),
-                            sad.Workspace(device)) if ws_pool else None)
+        self.pool = sad.BatchPool(device) if ws_pool else None
         self.reqs = self.batch = self.host = self.event = None
         self.ev0 = self.ev1 = None
         self.nbytes = 0
 
 
-def _launch(slot: _Slot, reqs, shape, device):
+def _launch(slot: _Slot, reqs, shape, device, graph: bool = True):
     """Admit a batch on a free slot without synchronising the host: pinned H2D,
     plan from bounds, capture into the slot's graph (an update after the first
-    batch), launch, D2H of the bucket lists and keys into pinned memory."""
+    batch), launch, D2H of the bucket lists, keys and status words into pinned
+    memory."""
     tile, depth, budget = shape
     st = slot.stream
+    pool = slot.pool
+
+    def pinned(name, like, dtype):
+        n = like.numel()
+        if pool is not None:
+            return pool.get(name, n, dtype, pinned=True)
+        return torch.empty(n, dtype=dtype, pin_memory=True)
     with torch.cuda.stream(st):
         slot.ev0 = torch.cuda.Event(enable_timing=True)
         slot.ev0.record(st)
-        b = sad.Batch([r.seqset for r in reqs], device=device, workspaces=slot.workspaces,
-                      stream=st)
-        b.plan(depth=depth, tile=tile, budget=budget, stream=st, bound=True)
-        b.capture(slot.graph, stream=st)
-        slot.graph.launch(st)
-        host = dict(bucket_offsets=torch.empty(b.bucket_offsets.shape, dtype=torch.int32,
-                                               pin_memory=True),
-                    members=torch.empty(b.members.shape, dtype=torch.int32, pin_memory=True),
-                    key_hi=torch.empty(b.key_hi.shape, dtype=torch.uint64, pin_memory=True),
-                    key_lo=torch.empty(b.key_lo.shape, dtype=torch.uint64, pin_memory=True))
+        if pool is not None:
+            for ws in pool.workspaces:    # a pooled workspace starts each batch with no status
+                ws.clear_status()         # (one not allocated yet is cleared when it is)
+        if len(reqs) == 1 and pool is not None:
+            # one request: the single-set calls, queued on the slot's stream at once
+            b = _Single(reqs[0].seqset, pool, st, shape, device)
+        else:
+            # the count starts on the device as soon as the inputs are up, while the
+            # host sets up the rest of the batch, plans it and builds the graph
+            b = sad.Batch([r.seqset for r in reqs], device=device, stream=st, pool=pool,
+                          count=True)
+            b.plan(depth=depth, tile=tile, budget=budget, stream=st, bound=True)
+            if graph:
+                b.capture(slot.graph, stream=st, count=False)
+                slot.graph.launch(st)
+            else:
+                b.run(stream=st, count=False)
+        host = dict(bucket_offsets=pinned("r_boff", b.bucket_offsets, torch.int32),
+                    members=pinned("r_members", b.members, torch.int32),
+                    key_hi=pinned("r_key_hi", b.key_hi, torch.uint64),
+                    key_lo=pinned("r_key_lo", b.key_lo, torch.uint64))
         for key, h in host.items():
             h.copy_(getattr(b, key), non_blocking=True)
+        # the three workspaces' status words come back with the results: no
+        # synchronous status read when the batch completes
+        status = pinned("r_status", torch.empty(3), torch.int32)
+        for i, ws in enumerate((b.ws_count, b.ws_rank, b.ws_part)):
+            status[i:i + 1].copy_(ws.buf[:4].view(torch.int32), non_blocking=True)
+        host["status"] = status
         slot.ev1 = torch.cuda.Event(enable_timing=True)
         slot.ev1.record(st)
     slot.reqs, slot.batch, slot.host, slot.event = reqs, b, host, slot.ev1
 
 
+class _Single:
+    """The device buffers and plan of a one-request batch on a slot (the single-set
+    calls), shaped like a Batch for _finish."""
+
+    def __init__(self, s, pool, st, shape, device, k: int = 3, alphabet: int = 20):
+        import numpy as np
+        tile, depth, budget = shape
+        a, z = int(s.offsets[0]), int(s.offsets[-1])
+        n, L, eps = s.offsets.shape[0] - 1, z - a, alphabet ** k
+        self.seq_begin = np.array([0, n], dtype=np.int64)
+        self.boff_begin = np.array([0, s.p + 1], dtype=np.int64)
+        h_codes = pool.get("h_codes", max(L, 1), torch.uint8, pinned=True)
+        h_offs = pool.get("h_offsets", n + 1, torch.int64, pinned=True)
+        h_codes.numpy()[:L] = s.codes[a:z]
+        np.subtract(s.offsets, a, out=h_offs.numpy())
+        codes = pool.get("codes", max(L, 1), torch.uint8)
+        offs = pool.get("offsets", n + 1, torch.int64)
+        codes[:L].copy_(h_codes[:L], non_blocking=True)
+        offs.copy_(h_offs, non_blocking=True)
+        self.ws_count, self.ws_rank, self.ws_part = pool.workspaces
+        counts = pool.get("counts", n * eps, torch.int32).view(n, eps)
+        wm = pool.get("word_max", eps, torch.int32)
+        sad.kmer_count(codes, offs, k, alphabet, ws=self.ws_count, out=counts, stream=st,
+                       check=False, word_max=wm)
+        lengths = sad.seq_lengths(offs, out=pool.get("lengths", n, torch.int32),
+                                  ws=self.ws_count, stream=st)
+        plan = sad.kmer_rank_plan_bound(n, L, k, alphabet, depth=depth, budget=budget, tile=tile)
+        self.ws_rank.ensure(plan.ws_bytes)
+        self.key_hi = pool.get("key_hi", n, torch.uint64)
+        self.key_lo = pool.get("key_lo", n, torch.uint64)
+        rank = pool.get("rank", n, torch.float64)
+        sad.kmer_rank(counts, lengths, k, alphabet, ws=self.ws_rank, plan=plan,
+                      out=(self.key_hi, self.key_lo, rank), stream=st, check=False, word_max=wm)
+        self.bucket_offsets = pool.get("bucket_offsets", s.p + 1, torch.int32)
+        self.members = pool.get("members", n, torch.int32)
+        piv = pool.get("pivot_idx", max(s.p - 1, 1), torch.int32)
+        sad.partition(self.key_hi, self.key_lo, s.p, ws=self.ws_part,
+                      out=(self.bucket_offsets, self.members, piv), stream=st, check=False)
+
+    def check(self, stream=None):
+        self.ws_count.check("kmer_count", stream)
+        self.ws_rank.check("kmer_rank", stream)
+        self.ws_part.check("partition", stream)
+
+
 def _finish(slot: _Slot, now: float):
     b = slot.batch
-    b.check(slot.stream)
+    for where, st in zip(("kmer_count (batch)", "sad_batch_rank", "sad_batch_partition"),
+                         slot.host["status"].tolist()):
+        if st != 0:
+            b.check(slot.stream)       # raises with the status's message
+            raise sad.SadError(st, where)
     for i, r in enumerate(slot.reqs):
         a, e = int(b.seq_begin[i]), int(b.seq_begin[i + 1])
         oa, ob = int(b.boff_begin[i]), int(b.boff_begin[i + 1])
@@ -139,14 +218,19 @@ def max_overlap(intervals) -> int:
 
 def serve(requests, shape=DEFAULT_SHAPE, budget_bytes: int = 150 * GB, slots: int = 3,
           max_batch: int = 64, device=None, t0: float | None = None, stats: dict | None = None,
-          ws_pool: bool = False):
+          ws_pool: bool = True, graph: bool = True):
     """Continuous batching over ``requests`` (sorted by arrival). Returns them with
     ``done`` and ``result`` filled in. Arrival times are honoured in real time.
     ``shape``: (tile, depth >= 1, budget) of every batch's rank plan. ``stats``
     (a dict) receives the batches, the most batches in flight on the host and on
     the device at once (from each batch's start and end events on its stream),
     the most HBM bytes admitted at once, and the slots' graph updates and
-    instantiations. ``ws_pool``: each slot keeps its workspaces across batches."""
+    instantiations. ``ws_pool``: each slot keeps its three workspaces across
+    batches (they grow to the largest batch the slot has run and stay allocated;
+    the admission estimate of a request includes its workspace, so the bytes a
+    slot keeps between batches are at most one earlier request's estimate and lie
+    outside the budget). ``graph``: launch each batch through the slot's reusable
+    graph (else the same calls are launched directly on the slot's stream)."""
     tile, depth, budget = shape
     if slots < 1 or max_batch < 1:
         raise ValueError("serve: slots and max_batch must be at least 1")
@@ -170,38 +254,74 @@ def serve(requests, shape=DEFAULT_SHAPE, budget_bytes: int = 150 * GB, slots: in
     base.record(torch.cuda.current_stream(device))
     n_batches = 0
     start = time.perf_counter() if t0 is None else t0
-    while pending or queue or busy:
-        now = time.perf_counter() - start
-        while pending and pending[0].arrival <= now:
-            queue.append(pending.pop(0))
-        # completions
-        for sl in list(busy):
-            if sl.event.query():
+    # One waiter thread per slot blocks on its batch's completion event, copies the
+    # results out and wakes the admission loop, which otherwise sleeps until the
+    # next arrival: completions are seen as they happen, not at a polling tick.
+    cond = threading.Condition()
+    completed: list[_Slot] = []
+
+    def waiter(sl: _Slot):
+        while True:
+            ev = sl.jobs.get()
+            if ev is None:
+                return
+            try:
+                ev.synchronize()
                 _finish(sl, time.perf_counter() - start)
+            except BaseException as e:  # re-raised by the admission loop
+                sl.error = e
+            with cond:
+                completed.append(sl)
+                cond.notify()
+
+    for sl in all_slots:
+        sl.jobs, sl.error = _queue.SimpleQueue(), None
+        sl.thread = threading.Thread(target=waiter, args=(sl,), daemon=True)
+        sl.thread.start()
+    try:
+        while pending or queue or busy:
+            now = time.perf_counter() - start
+            while pending and pending[0].arrival <= now:
+                queue.append(pending.pop(0))
+            # completions
+            with cond:
+                done, completed[:] = list(completed), []
+            for sl in done:
+                if sl.error is not None:
+                    raise sl.error
                 done_ev.append((sl.ev0, sl.ev1))
                 busy.remove(sl)
                 free.append(sl)
                 used -= sl.nbytes
                 sl.batch = sl.host = sl.reqs = None
-        # admissions: everything queued that fits, one batch per free slot
-        while queue and free:
-            take, nbytes = select_batch(queue, used, budget_bytes, max_batch, depth, tile,
-                                        budget)
-            if not take:
-                break
-            queue = queue[len(take):]
-            sl = free.pop(0)
-            _launch(sl, take, shape, device)
-            sl.nbytes = nbytes
-            busy.append(sl)
-            n_batches += 1
-            used += nbytes
-            peak_used = max(peak_used, used)
-            peak_busy = max(peak_busy, len(busy))
-        if not (queue and free):
-            # nothing to launch right now: wait a little for an arrival or a completion
-            nxt = pending[0].arrival - (time.perf_counter() - start) if pending else 0.0
-            time.sleep(min(max(nxt, 0.0), 2e-4))
+            # admissions: everything queued that fits, one batch per free slot
+            while queue and free:
+                take, nbytes = select_batch(queue, used, budget_bytes, max_batch, depth, tile,
+                                            budget)
+                if not take:
+                    break
+                queue = queue[len(take):]
+                sl = free.pop(0)
+                _launch(sl, take, shape, device, graph)
+                sl.nbytes = nbytes
+                busy.append(sl)
+                sl.jobs.put(sl.event)
+                n_batches += 1
+                used += nbytes
+                peak_used = max(peak_used, used)
+                peak_busy = max(peak_busy, len(busy))
+            # wait for the next arrival or a completion
+            with cond:
+                if not completed:
+                    if pending:
+                        cond.wait(max(pending[0].arrival - (time.perf_counter() - start), 0.0))
+                    elif busy:
+                        cond.wait(0.05)
+    finally:
+        for sl in all_slots:
+            sl.jobs.put(None)
+        for sl in all_slots:
+            sl.thread.join()
     if stats is not None:
         torch.cuda.synchronize(device)
         iv = [(base.elapsed_time(a), base.elapsed_time(b)) for a, b in done_ev]

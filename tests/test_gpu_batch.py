@@ -143,3 +143,27 @@ def test_graph_keeps_single_and_multi_set_captures_apart(sad, oracle_mod):
         check_sets(b, sets, oracle_mod)
     st = g.stats()
     assert st["instantiations"] == 2 and st["updates"] == 4
+
+
+def test_batches_on_one_pool(sad, oracle_mod):
+    """Batches built one after another on one BatchPool (staging, device arrays and
+    workspaces reused) each equal the oracle; once the pool holds the largest batch,
+    building another allocates nothing new."""
+    pool_sets = [datagen.batch_set(i, seed=5, n_lo=40, n_hi=700) for i in range(10)]
+    groups = [[0, 1, 2], [3, 4, 5, 6, 7, 8, 9], [2], [0, 1, 2]]
+    pool = sad.BatchPool()
+    s = torch.cuda.Stream()
+    ptrs = None
+    for gi, grp in enumerate(groups):
+        sets = [pool_sets[i] for i in grp]
+        b = sad.Batch(sets, stream=s, pool=pool)
+        b.plan(depth=2, tile=256, stream=s)
+        for ws in pool.workspaces:
+            ws.buf[:8].zero_()
+        b.run(stream=s)
+        s.synchronize()
+        b.check(s)
+        check_sets(b, sets, oracle_mod)
+        if gi == 1:
+            ptrs = {k: t.data_ptr() for k, t in pool.bufs.items()}
+    assert {k: t.data_ptr() for k, t in pool.bufs.items()} == ptrs
