@@ -803,7 +803,7 @@ def global_partition_set(codes: torch.Tensor, offsets: torch.Tensor, p: int, ks:
 class BatchPool:
     """Buffers that the successive batches of one stream reuse (a serving slot, a
     loop over batches): pinned host staging, the device arrays of a Batch and its
-    three workspaces. Each buffer grows (by half again) when a batch needs more and
+    three workspaces. Each buffer grows (at least doubling) when a batch needs more and
     is otherwise handed out as a view, so building a new batch on the pool
     allocates nothing once the pool has warmed up. A batch built on a pool must
     have finished on the device, and its results been read, before the next batch
@@ -820,7 +820,7 @@ class BatchPool:
         if t is None or t.numel() < n or t.dtype != dtype:
             cap = max(int(n), 1)
             if t is not None and t.dtype == dtype:
-                cap = max(cap, int(t.numel() * 3 // 2))
+                cap = max(cap, 2 * t.numel())
             t = (torch.empty(cap, dtype=dtype, pin_memory=True) if pinned else
                  torch.empty(cap, dtype=dtype, device=self.device))
             self.bufs[name] = t

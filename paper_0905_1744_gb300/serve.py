@@ -218,7 +218,7 @@ def max_overlap(intervals) -> int:
 
 def serve(requests, shape=DEFAULT_SHAPE, budget_bytes: int = 150 * GB, slots: int = 3,
           max_batch: int = 64, device=None, t0: float | None = None, stats: dict | None = None,
-          ws_pool: bool = True, graph: bool = True):
+          ws_pool: bool = True, graph: bool = True, warm=None):
     """Continuous batching over ``requests`` (sorted by arrival). Returns them with
     ``done`` and ``result`` filled in. Arrival times are honoured in real time.
     ``shape``: (tile, depth >= 1, budget) of every batch's rank plan. ``stats``
@@ -230,7 +230,11 @@ def serve(requests, shape=DEFAULT_SHAPE, budget_bytes: int = 150 * GB, slots: in
     the admission estimate of a request includes its workspace, so the bytes a
     slot keeps between batches are at most one earlier request's estimate and lie
     outside the budget). ``graph``: launch each batch through the slot's reusable
-    graph (else the same calls are launched directly on the slot's stream)."""
+    graph (else the same calls are launched directly on the slot's stream).
+    ``warm``: sequence sets that every slot runs once before the clock starts, alone
+    and (two or more) together, so that its buffer pool, workspaces and graphs are
+    sized and instantiated for them; a server warms with its largest expected
+    requests so that no large allocation falls inside a request's latency."""
     tile, depth, budget = shape
     if slots < 1 or max_batch < 1:
         raise ValueError("serve: slots and max_batch must be at least 1")
@@ -253,7 +257,6 @@ def serve(requests, shape=DEFAULT_SHAPE, budget_bytes: int = 150 * GB, slots: in
     base = torch.cuda.Event(enable_timing=True)
     base.record(torch.cuda.current_stream(device))
     n_batches = 0
-    start = time.perf_counter() if t0 is None else t0
     # One waiter thread per slot blocks on its batch's completion event, copies the
     # results out and wakes the admission loop, which otherwise sleeps until the
     # next arrival: completions are seen as they happen, not at a polling tick.
@@ -274,6 +277,17 @@ def serve(requests, shape=DEFAULT_SHAPE, budget_bytes: int = 150 * GB, slots: in
                 completed.append(sl)
                 cond.notify()
 
+    if warm:
+        # each slot once with the largest warm set alone, once with all of them
+        big = max(warm, key=lambda x: int(x.offsets[-1] - x.offsets[0]))
+        for sl in all_slots:
+            for group in ([big], list(warm)) if len(warm) > 1 else ([big],):
+                _launch(sl, [Request(-1, 0.0, x) for x in group], shape, device, graph)
+                sl.event.synchronize()
+                _finish(sl, 0.0)
+                sl.batch = sl.host = sl.reqs = None
+        torch.cuda.synchronize(device)
+    start = time.perf_counter() if t0 is None else t0
     for sl in all_slots:
         sl.jobs, sl.error = _queue.SimpleQueue(), None
         sl.thread = threading.Thread(target=waiter, args=(sl,), daemon=True)
