@@ -872,11 +872,21 @@ __global__ void __launch_bounds__(kStreamThreads, 4) planes_stream_kernel(
         }
       }
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    }
     // pass 2: the row's words from w1 on, eight columns each, gathered from the
-    // column map and the 4-bit counts (columns past K_eff are 0)
+    // column map and the 4-bit counts (columns past K_eff are 0). A section above the
+    // row's largest count holds no 1 of the row: the gather stops at the end of
+    // section min(largest count, D) and the words past it are zero.
     __syncwarp();
     uint32_t *prow32 = reinterpret_cast<uint32_t *>(prow);
-    for (int32_t w = w1 + lane; w < kw; w += 32) {
+    const int32_t top = min(mx, dkeep);
+    const int32_t wg = top >= 1 ? min((P.secend[top] + 7) / 8, kw) : w1;
+    for (int32_t w = max(wg, w1) + lane; w < kw; w += 32) prow32[w] = 0u;
+    for (int32_t w = w1 + lane; w < wg; w += 32) {
       const int32_t c0 = 8 * w;
       uint32_t val = 0;
       if (c0 + 8 <= k_eff) {
@@ -898,11 +908,6 @@ __global__ void __launch_bounds__(kStreamThreads, 4) planes_stream_kernel(
       prow32[w] = val;
     }
     __syncwarp();  // the next row's pass 1 rewrites the 4-bit counts
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    }
     if (lane == 0) {
       atomicMax(&P.depth[pos / kRowBlock], mx);
       // the counts of a row must add up to its number of windows, m
