@@ -310,10 +310,11 @@ def run_reference(args):
 
 # --------------------------------------------------------------------- GPU ---
 
-def gemm_traffic_per_launch(n: int, k_eff: int):
-    """Scaled DRAM traffic of the plane GEMM from the committed ncu summary, or
-    None when the kernel source changed since that capture."""
-    path = os.path.join(ROOT, "profiles", "plane_gemm_traffic.json")
+def gemm_traffic_per_launch(n: int, tile: int, depth: int):
+    """DRAM bytes (read + write) of one GEMM launch from the committed ncu capture,
+    or None for another workload or plan shape, or when the kernel source changed
+    since that capture."""
+    path = os.path.join(ROOT, "profiles", "pair_gemm_traffic.json")
     src = os.path.join(ROOT, "paper_0905_1744_gb300", "csrc", "gemm.cu")
     try:
         with open(path) as f:
@@ -322,9 +323,10 @@ def gemm_traffic_per_launch(n: int, k_eff: int):
             sha = hashlib.sha256(f.read()).hexdigest()
     except (OSError, ValueError):
         return None
-    if d.get("gemm_cu_sha256") != sha or d.get("N") != n:
+    if d.get("gemm_cu_sha256") != sha or (d.get("N"), d.get("tile"), d.get("depth")) != (n, tile,
+                                                                                          depth):
         return None
-    return d.get("dram_bytes_per_launch")
+    return d["dram_bytes_read_per_launch"] + d["dram_bytes_write_per_launch"]
 
 
 def run_batching(args, dev):
@@ -744,7 +746,7 @@ def measure_config(cfg: int, args, dev, world: int, steps: int, warmup: int,
         "peak_source": f"{pk_kind}: 6 x bf16_tflops burst (e2m1/bf16 nominal ratio "
                        f"13.5/2.25); sustained would be "
                        f"{f4_ratio * pk['bf16_tflops_sustained']:.1f}",
-        "traffic": gemm_traffic_per_launch(n, info["k_eff"]),
+        "traffic": gemm_traffic_per_launch(n, shape.tile, shape.depth),
         "gemm_ms_per_launch": gemm_launch_ms, "gemm_share_of_step": gemm_launch_ms / ms_per_step,
         "executed_tflops": exec_flops / (gemm_launch_ms / 1e3) / 1e12,
         "executed_frac": exec_flops / (gemm_launch_ms / 1e3) / 1e12 / f4_peak,
