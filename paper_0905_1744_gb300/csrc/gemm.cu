@@ -1198,19 +1198,28 @@ __global__ void __launch_bounds__(pairk::kThreads, 1)
       if (!got) pairk::set_abort(S, P.hdr);
       if (named_bar_sync_or(1, pairk::kEpiThreads, *abort_flag != 0)) break;
       tc_fence_after();
-      // drain this thread's 128 accumulator columns
+      // drain this thread's 128 accumulator columns: two rounds of four loads, one wait
+      // each (the next tile's MMAs wait for this drain)
       uint32_t pk[64];
 #pragma unroll
-      for (int sc = 0; sc < 8; ++sc) {
-        uint32_t v[16];
-        tmem_ld_32x32b_x16(tmem + ((q * 32u) << 16) + half * 128u + (uint32_t)(sc * 16), v);
+      for (int hh = 0; hh < 2; ++hh) {
+        uint32_t v[4][16];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          tmem_ld_32x32b_x16(tmem + ((q * 32u) << 16) + half * 128u + (uint32_t)((4 * hh + u) * 16),
+                             v[u]);
         tmem_ld_wait();
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const uint32_t a = __float_as_uint(__fadd_rn(__uint_as_float(v[2 * j]), 8388608.0f));
-          const uint32_t b = __float_as_uint(__fadd_rn(__uint_as_float(v[2 * j + 1]), 8388608.0f));
-          // the counts are below 2^16: the low mantissa halves of a and b
-          pk[sc * 8 + j] = __byte_perm(a, b, 0x5410);
+        for (int u = 0; u < 4; ++u) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const uint32_t a =
+                __float_as_uint(__fadd_rn(__uint_as_float(v[u][2 * j]), 8388608.0f));
+            const uint32_t b =
+                __float_as_uint(__fadd_rn(__uint_as_float(v[u][2 * j + 1]), 8388608.0f));
+            // the counts are below 2^16: the low mantissa halves of a and b
+            pk[(4 * hh + u) * 8 + j] = __byte_perm(a, b, 0x5410);
+          }
         }
       }
       tc_fence_before();
