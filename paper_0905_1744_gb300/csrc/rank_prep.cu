@@ -564,7 +564,7 @@ __global__ void __launch_bounds__(kSortThreads) lensort_sets_kernel(
 // section d rounded up to a K chunk, at most K_pad), d = 1..dkeep: the covering
 // depth of a column is the smallest d whose extent lies past it. (The remainder
 // bitmap is filled later, from the flat entries, once the block depths are known.)
-__device__ __noinline__ void note_count(const RankPtrs &P, int32_t tau, int32_t c, int32_t dkeep,
+__device__ __forceinline__ void note_count(const RankPtrs &P, int32_t tau, int32_t c, int32_t dkeep,
                                         int32_t tb, const int32_t *ru, uint32_t *s_prof) {
   const int32_t top = min(c, tb);
   for (int32_t t = 2; t <= top; ++t) {
