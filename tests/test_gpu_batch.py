@@ -44,7 +44,7 @@ def check_sets(b, sets, oracle_mod, which=None):
 
 @pytest.mark.parametrize("tile", [128, 256])
 @pytest.mark.parametrize("depth,bound", [(0, False), (1, True), (2, True), (2, False),
-                                         (6, True)])
+                                         (3, True), (4, True), (6, True)])
 def test_batch_matches_oracle_per_set(sad, oracle_mod, tile, depth, bound):
     """Every (tile, depth) the autotuner can pick for a batch, on bound plans (the
     plan-free path) and on exact plans."""

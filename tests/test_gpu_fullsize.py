@@ -3,9 +3,10 @@
 bench.py runs kmer_count (with the per-word maxima) -> sad_seq_lengths ->
 kmer_rank_plan at the autotuner's shape (GEMM tile 128 or 256 rows, plane depth,
 remainder budget) -> kmer_rank on that plan -> partition. These tests run the same
-sequence on the paper-scale set (N = 20000, 50 families, p = 16) and the large set
-(N = 100000, 500 families, p = 64) at every tile and depth the autotuner may
-choose and at the other budgets it tries, plus the public partition_set path:
+sequence on the paper-scale set (N = 20000, 50 families, p = 16) at every shape the
+autotuner may choose (tile x depth x budget) and on the large set (N = 100000, 500
+families, p = 64) at every tile and depth and some of the other budgets, plus the
+public partition_set path:
 
   N = 20000   every key and rank against the oracle's full rank (Eq. 1, Eq. 3; all
               N(N-1)/2 pairs on the host cores, computed once for the module), and
@@ -30,6 +31,9 @@ DEPTHS = (0, 1, 2, 3, 4, 6)     # the autotuner's candidates
 TILES = (128, 256)
 SHAPES = [(t, d, 0) for t in TILES for d in DEPTHS] + [(256, 2, 256), (256, 6, 1536),
                                                        (128, 4, 1536)]
+# every shape the autotuner can pick: both tiles, every depth, and at depths >= 1 the
+# budgets it tries (the default, 256, 1536)
+ALL_SHAPES = [(t, d, b) for t in TILES for d in DEPTHS for b in ((0,) if d == 0 else (0, 256, 1536))]
 
 
 @pytest.fixture(scope="module")
@@ -93,7 +97,7 @@ def test_c2_counts_in_full(sad, c2_oracle):
     np.testing.assert_array_equal(host(res["counts"]), counts)
 
 
-@pytest.mark.parametrize("tile,depth,budget", SHAPES)
+@pytest.mark.parametrize("tile,depth,budget", ALL_SHAPES)
 def test_c2_bench_path_every_key_and_bucket(sad, c2_oracle, tile, depth, budget):
     s, _, ref = c2_oracle
     res = bench_path(sad, s, depth, tile, budget)
