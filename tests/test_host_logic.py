@@ -413,3 +413,73 @@ def test_reference_arm_prints_the_contract_line(monkeypatch, capsys):
     assert "sample" in cb
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
+
+
+# ------------------------------------------------------------- buffer pool ---
+
+def test_batch_pool_hands_out_views_and_grows_by_doubling():
+    from paper_0905_1744_gb300 import sad
+    pool = sad.BatchPool("cpu")
+    a = pool.get("x", 10, torch.int32)
+    assert a.numel() == 10 and a.dtype == torch.int32
+    base = pool.bufs["x"]
+    # a smaller request is a view of the same buffer
+    b = pool.get("x", 7, torch.int32)
+    assert b.data_ptr() == base.data_ptr() and b.numel() == 7
+    # a larger one at least doubles the buffer
+    c = pool.get("x", 11, torch.int32)
+    assert pool.bufs["x"].numel() >= 20 and c.numel() == 11
+    # another dtype under the same name replaces the buffer
+    d = pool.get("x", 5, torch.float64)
+    assert d.dtype == torch.float64 and pool.bufs["x"].dtype == torch.float64
+    # the three workspaces come with the pool
+    assert len(pool.workspaces) == 3
+
+
+# --------------------------------------------------------- batch autotuner ---
+
+class _FakeBatch:
+    """The parts of sad.Batch that choose_batch_shape touches."""
+
+    def __init__(self):
+        import numpy as np
+        self.n_sets, self.n, self.total_len = 4, np.array([100, 200, 300, 400]), 500000
+        self.device = torch.device("cpu")
+        self.planned = []
+
+    def plan(self, depth, tile, budget, stream=None):
+        self.planned.append((tile, depth, budget))
+        return types.SimpleNamespace(rank=types.SimpleNamespace(ws_bytes=depth * 10 + tile))
+
+    def run(self, stream=None):
+        pass
+
+    def check(self, stream=None):
+        pass
+
+
+def test_choose_batch_shape_times_bound_plans_and_leaves_the_best_planned(monkeypatch):
+    autotune._cache.clear()
+    b = _FakeBatch()
+    ms = {(256, 1): 5.0, (256, 2): 3.0, (256, 3): 4.0, (256, 4): 4.5, (256, 6): 6.0,
+          (128, 1): 5.5, (128, 2): 2.5, (128, 3): 3.5, (128, 4): 4.0, (128, 6): 5.0}
+
+    def events_ms(fn, stream, reps):
+        tile, depth, budget = b.planned[-1]
+        return ms[(tile, depth)] - (0.2 if budget == 1536 else 0.0)
+    monkeypatch.setattr(autotune, "_events_ms", events_ms)
+    monkeypatch.setattr(autotune.torch.cuda, "current_stream", lambda device=None: None)
+    best, trials = autotune.choose_batch_shape(b, use_cache=False)
+    # bound plans need cut planes: depth 0 is never tried
+    assert all(autotune.Shape.parse(k).depth >= 1 for k in trials)
+    assert best == autotune.Shape(128, 2, 1536)
+    assert b.planned[-1] == (128, 2, 1536)          # left planned with the choice
+    # the size class is cached: a second call answers without timing
+    best2, trials2 = autotune.choose_batch_shape(b)
+    assert best2 == best and trials2 == {} and b.planned[-1] == (128, 2, 1536)
+    # a workspace limit drops the shapes that need more
+    autotune._cache.clear()
+    best3, trials3 = autotune.choose_batch_shape(b, use_cache=False, max_ws_bytes=160)
+    assert all(10 * autotune.Shape.parse(k).depth + autotune.Shape.parse(k).tile <= 160
+               for k in trials3)
+    autotune._cache.clear()
