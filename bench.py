@@ -826,7 +826,8 @@ def measure_config(cfg: int, args, dev, world: int, steps: int, warmup: int,
             "warmup": warmup, "launches": int(launches), "clocks": clocks,
             "autotune": {"shape": shape._asdict(), "trial_ms": trials,
                          "searched": "tile {256, 128} x depth {0,1,2,3,4,6} at the default "
-                                     "budget, then budgets {256, 1536} at the best"},
+                                     "budget, then budgets {256, 1536} at the best, then the "
+                                     "three fastest twice more in turn; trial_ms = medians"},
             "roofline": roofline, "calls": calls, "e2e": e2e, "cpu_baseline": cpu,
             "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms),
             "tensors": (counts, lengths, word_max, keys, shape, trials)}

@@ -11,9 +11,10 @@ A rank plan has three knobs that change speed and never the keys:
           (0 = the library's default).
 Which combination is fastest depends on the set (its size, its repeat structure,
 the mix of set sizes in a batch), so candidates are timed on the device with CUDA
-events and the fastest kept: first every (tile, depth) at the default budget, then
-the other budgets at the best (tile, depth). Results are cached per size class in
-memory and, if a path is given, in a JSON file.
+events: first every (tile, depth) at the default budget, then the other budgets at
+the best (tile, depth), then the three fastest again, side by side; the shape with the
+smallest median is kept. Results are cached per size class in memory and, if a path
+is given, in a JSON file.
 """
 from __future__ import annotations
 
@@ -70,27 +71,37 @@ def first_round(t_max: int | None, tiles=TILES, depths=DEPTHS, min_depth: int = 
 
 
 def search(timer: Callable[[Shape], float | None], first: list[Shape],
-           budgets=BUDGETS) -> tuple[Shape, dict[str, float]]:
+           budgets=BUDGETS, confirm: int = 3, rounds: int = 2) -> tuple[Shape, dict[str, float]]:
     """Times every shape of ``first``, then the other budgets at the best one
-    (when it cuts planes: depth >= 1). ``timer`` returns milliseconds, or None for
-    a shape that does not apply (too large a workspace). Returns the fastest shape
-    and every trial."""
-    trials: dict[str, float] = {}
-    for sh in first:
+    (when it cuts planes: depth >= 1), then the ``confirm`` fastest shapes again,
+    ``rounds`` times in turn (single timings taken minutes apart in a long search
+    can favour a shape that happened to run at a better moment; the re-timings
+    compare the finalists side by side). ``timer`` returns milliseconds, or None for
+    a shape that does not apply (too large a workspace). Returns the shape with the
+    smallest median over its timings, and that median for every shape tried."""
+    times: dict[str, list[float]] = {}
+
+    def run(sh: Shape):
         ms = timer(sh)
         if ms is not None:
-            trials[sh.key] = ms
-    if not trials:
+            times.setdefault(sh.key, []).append(ms)
+
+    for sh in first:
+        run(sh)
+    if not times:
         raise RuntimeError("autotune: no candidate shape could run")
-    best = Shape.parse(min(trials, key=trials.get))
+    best = Shape.parse(min(times, key=lambda k: times[k][0]))
     if best.depth >= 1:
         for b in budgets:
             sh = Shape(best.tile, best.depth, b)
-            if sh.key in trials:
-                continue
-            ms = timer(sh)
-            if ms is not None:
-                trials[sh.key] = ms
+            if sh.key not in times:
+                run(sh)
+    finalists = sorted(times, key=lambda k: times[k][0])[:confirm]
+    if len(finalists) > 1:
+        for _ in range(rounds):
+            for k in finalists:
+                run(Shape.parse(k))
+    trials = {k: statistics.median(v) for k, v in times.items()}
     return Shape.parse(min(trials, key=trials.get)), trials
 
 

@@ -124,7 +124,9 @@ def test_search_picks_among_tile_shapes_then_budgets():
     assert first == [S(256, 0, 0), S(256, 2, 0), S(128, 0, 0), S(128, 2, 0)]
     best, trials = autotune.search(timer, first)
     assert best == S(256, 2, 1536)
-    assert timed == first + [S(256, 2, 256), S(256, 2, 1536)]
+    # first round, the budgets at the best, then the three fastest twice more in turn
+    finalists = [S(256, 2, 1536), S(256, 2, 0), S(256, 2, 256)]
+    assert timed == first + [S(256, 2, 256), S(256, 2, 1536)] + finalists + finalists
     assert trials == {k.key: v for k, v in ms.items()}
     # the other tile shape wins when it is faster; depth 0 cuts nothing: no budget round
     ms2 = {S(256, 0, 0): 2.0, S(128, 0, 0): 1.0}
@@ -138,6 +140,16 @@ def test_search_picks_among_tile_shapes_then_budgets():
     with pytest.raises(RuntimeError):
         autotune.search(lambda sh: None, [S(128, 0, 0)])
     assert S.parse(S(256, 6, 768).key) == S(256, 6, 768)
+
+
+def test_search_confirms_the_finalists():
+    """A shape whose first timing was lucky loses to one that is steadily faster when
+    the finalists are timed again side by side (medians decide)."""
+    seq = {S(256, 4, 0): iter([1.0, 2.0, 2.1]), S(256, 6, 0): iter([1.2, 1.2, 1.2]),
+           S(128, 4, 0): iter([3.0, 3.0, 3.0])}
+    best, trials = autotune.search(lambda sh: next(seq[sh]), list(seq), budgets=())
+    assert best == S(256, 6, 0)
+    assert trials[S(256, 4, 0).key] == 2.0 and trials[S(256, 6, 0).key] == 1.2
 
 
 def test_first_round_skips_depths_that_keep_every_plane():
@@ -164,8 +176,10 @@ def test_choose_shape_times_candidates_and_keeps_the_fastest(monkeypatch):
     best, trials = autotune.choose_shape(counts, None, ws, use_cache=False,
                                          depths=(0, 1, 2, 3, 4))
     # depth 4 >= t_max keeps every plane (the work of depth 0): not timed
-    assert [t for t in timed if t[2] == 0] == [(t, d, 0) for t in (256, 128) for d in range(4)]
-    assert timed[-2:] == [(256, 2, 256), (256, 2, 1536)]
+    assert timed[:8] == [(t, d, 0) for t in (256, 128) for d in range(4)]
+    assert timed[8:10] == [(256, 2, 256), (256, 2, 1536)]
+    # the three fastest again, twice, in turn
+    assert timed[10:] == [(256, 2, 1536), (256, 2, 0), (128, 2, 0)] * 2
     assert best == S(256, 2, 1536) and len(trials) == 10
     # a workspace limit drops the shapes that need more
     timed.clear()
