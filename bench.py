@@ -121,6 +121,8 @@ def parse(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tile", type=int, default=256, choices=[128, 256],
                     help="GEMM tile rows with --depth (default: the autotuner's choice)")
+    ap.add_argument("--budget", type=int, default=0,
+                    help="remainder budget with --depth (0 = the library default)")
     ap.add_argument("--depth", type=int, default=None,
                     help="threshold-plane depth (default: the autotuner's choice)")
     ap.add_argument("--no-batching", action="store_true")
@@ -310,10 +312,10 @@ def run_reference(args):
 
 # --------------------------------------------------------------------- GPU ---
 
-def gemm_traffic_per_launch(n: int, tile: int, depth: int):
-    """DRAM bytes (read + write) of one GEMM launch from the committed ncu capture,
-    or None for another workload or plan shape, or when the kernel source changed
-    since that capture."""
+def gemm_traffic_per_launch(n: int, tile: int, depth: int, budget: int):
+    """DRAM bytes (read + write) of one GEMM launch from the committed ncu captures,
+    or None for a workload or plan shape not captured, or when the kernel source
+    changed since the capture."""
     path = os.path.join(ROOT, "profiles", "pair_gemm_traffic.json")
     src = os.path.join(ROOT, "paper_0905_1744_gb300", "csrc", "gemm.cu")
     try:
@@ -323,10 +325,13 @@ def gemm_traffic_per_launch(n: int, tile: int, depth: int):
             sha = hashlib.sha256(f.read()).hexdigest()
     except (OSError, ValueError):
         return None
-    if d.get("gemm_cu_sha256") != sha or (d.get("N"), d.get("tile"), d.get("depth")) != (n, tile,
-                                                                                          depth):
+    if d.get("gemm_cu_sha256") != sha:
         return None
-    return d["dram_bytes_read_per_launch"] + d["dram_bytes_write_per_launch"]
+    for e in d.get("captures", []):
+        if (e.get("N"), e.get("tile"), e.get("depth"), e.get("budget")) == (n, tile, depth,
+                                                                              budget):
+            return e["dram_bytes_read_per_launch"] + e["dram_bytes_write_per_launch"]
+    return None
 
 
 def run_batching(args, dev):
@@ -670,7 +675,7 @@ def measure_config(cfg: int, args, dev, world: int, steps: int, warmup: int,
         shape, trials = autotune.choose_shape(counts, lengths, ws, use_cache=False,
                                               word_max=word_max)
     else:
-        shape, trials = autotune.Shape(args.tile, args.depth, 0), {}
+        shape, trials = autotune.Shape(args.tile, args.depth, args.budget), {}
     depth = shape.depth
     plan = autotune.plan_for(counts, shape, ws)
     keys = (torch.empty(n, dtype=torch.uint64, device=dev),
@@ -746,7 +751,7 @@ def measure_config(cfg: int, args, dev, world: int, steps: int, warmup: int,
         "peak_source": f"{pk_kind}: 6 x bf16_tflops burst (e2m1/bf16 nominal ratio "
                        f"13.5/2.25); sustained would be "
                        f"{f4_ratio * pk['bf16_tflops_sustained']:.1f}",
-        "traffic": gemm_traffic_per_launch(n, shape.tile, shape.depth),
+        "traffic": gemm_traffic_per_launch(n, shape.tile, shape.depth, shape.budget),
         "gemm_ms_per_launch": gemm_launch_ms, "gemm_share_of_step": gemm_launch_ms / ms_per_step,
         "executed_tflops": exec_flops / (gemm_launch_ms / 1e3) / 1e12,
         "executed_frac": exec_flops / (gemm_launch_ms / 1e3) / 1e12 / f4_peak,

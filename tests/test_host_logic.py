@@ -375,7 +375,7 @@ def test_batch_layout_and_per_set_results_on_the_host():
 def test_gemm_traffic_is_reported_only_for_the_captured_source(tmp_path, monkeypatch):
     """The DRAM traffic in the roofline comes from a committed ncu capture and is
     reported only while the GEMM source is byte-identical to the captured one and
-    the set size and plan shape (tile, depth) match; otherwise it is null."""
+    the set size and plan shape (tile, depth, budget) match; otherwise it is null."""
     import hashlib
 
     import bench
@@ -385,15 +385,19 @@ def test_gemm_traffic_is_reported_only_for_the_captured_source(tmp_path, monkeyp
     (tmp_path / "profiles").mkdir()
     sha = hashlib.sha256(b"// kernel v1\n").hexdigest()
     (tmp_path / "profiles" / "pair_gemm_traffic.json").write_text(json.dumps(
-        {"N": 20000, "tile": 256, "depth": 6, "gemm_cu_sha256": sha,
-         "dram_bytes_read_per_launch": 100, "dram_bytes_write_per_launch": 23}))
+        {"gemm_cu_sha256": sha, "captures": [
+            {"N": 20000, "tile": 256, "depth": 6, "budget": 0,
+             "dram_bytes_read_per_launch": 100, "dram_bytes_write_per_launch": 23},
+            {"N": 20000, "tile": 256, "depth": 6, "budget": 1536,
+             "dram_bytes_read_per_launch": 200, "dram_bytes_write_per_launch": 1}]}))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench.gemm_traffic_per_launch(20000, 256, 6) == 123
-    assert bench.gemm_traffic_per_launch(200, 256, 6) is None
-    assert bench.gemm_traffic_per_launch(20000, 128, 6) is None
-    assert bench.gemm_traffic_per_launch(20000, 256, 4) is None
+    assert bench.gemm_traffic_per_launch(20000, 256, 6, 0) == 123
+    assert bench.gemm_traffic_per_launch(20000, 256, 6, 1536) == 201
+    assert bench.gemm_traffic_per_launch(200, 256, 6, 0) is None
+    assert bench.gemm_traffic_per_launch(20000, 128, 6, 0) is None
+    assert bench.gemm_traffic_per_launch(20000, 256, 4, 0) is None
     (src / "gemm.cu").write_bytes(b"// kernel v2\n")
-    assert bench.gemm_traffic_per_launch(20000, 256, 6) is None
+    assert bench.gemm_traffic_per_launch(20000, 256, 6, 0) is None
 
 
 def test_reference_arm_prints_the_contract_line(monkeypatch, capsys):
