@@ -275,9 +275,9 @@ int partition_noalloc(const uint64_t *d_key_hi, const uint64_t *d_key_lo, int32_
  * After sad_batch_plan_make the two calls launch no synchronising operation, so
  * the whole batch can be captured in a CUDA graph and replayed.
  *
- *   rank            depth in (see sad_rank_plan); sizes and capacities out,
- *                   for all sets together (rank.ws_bytes: sad_batch_rank's
- *                   workspace).
+ *   rank            depth, budget and tile in (see sad_rank_plan); sizes and
+ *                   capacities out, for all sets together (rank.ws_bytes:
+ *                   sad_batch_rank's workspace).
  *   n_sets, max_p   sets and the largest p_s.
  *   n_total, rows_total, tiles_total, tileof_total  sums over sets of n_s,
  *                   stored rows (n_s rounded up to the plan's tile rows, 128
@@ -303,7 +303,7 @@ typedef struct sad_batch_plan {
  *   h_n, h_p   host int32 [n_sets]: sequences and buckets per set
  *              (1 <= p_s <= min(n_s, 4096)).
  *   d_n        device copy of h_n.
- *   plan       plan->rank.depth in; the rest out.
+ *   plan       plan->rank.depth, budget and tile in; the rest out.
  *   d_ws       rank workspace; if smaller than the fixed part, returns
  *              SAD_ERR_WORKSPACE with plan->rank.ws_bytes = the bytes needed.
  */
